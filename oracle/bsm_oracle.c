@@ -1,0 +1,481 @@
+/*
+ * Plain CPU oracle for the block-sparse product C = A*B over a sparse quadtree.
+ *
+ * TEST INFRASTRUCTURE.  Only the tests, the smoke check and the benchmark's CPU
+ * baseline use this file; the product library never links or calls it, and it
+ * shares no code, header or table with the CUDA path.
+ *
+ * What it computes (Rubensson & Rudberg, arXiv 1501.07800):
+ *   - A matrix is a quadtree of nodes, each holding four child pointers; a NULL
+ *     child is a NIL chunk id, i.e. a zero submatrix, at any level (Sec. 3.1,
+ *     "Matrix" chunk type).  Every level halves the submatrix side, starting
+ *     from a power-of-two number of leaf blocks so that A and B submatrices
+ *     always match (Sec. 3.1).  Child c = 2*rowhalf + colhalf.
+ *   - The lowest level holds a block-sparse leaf matrix: a 2-D array of
+ *     optional bs x bs blocks, only nonzero blocks allocated (Sec. 4.1).
+ *   - multiply() is Algorithm 1: NIL if either input is NIL; the leaf multiply
+ *     at the lowest level; otherwise C_mn = add(A_m1 B_1n, A_m2 B_2n) for
+ *     m, n in {1, 2} and the four results assembled into a new node
+ *     (createFromIds, Sec. 3.2).
+ *   - add() is Algorithm 2: recurse (or leaf add) when both inputs are
+ *     non-NIL, otherwise the non-NIL input or NIL.
+ *   - The leaf multiply is a sum of outer products over the inner block index
+ *     (Sec. 4.1, Fig. 3), each block product a naive triple loop.
+ *   - Blocks whose entries are all exactly 0.0 are not stored: input blocks
+ *     are dropped when the matrix is built, product blocks after the multiply
+ *     (sparsity "dynamically detected", abstract; only nonzero submatrices
+ *     stored, Sec. 4.1).  -0.0 counts as zero, NaN does not.
+ *   - Multiply-task counts per level (tasks whose inputs are both non-NIL) are
+ *     the quantities C_l of Sec. 5.1, Eq. 1 - Eq. 5.
+ *
+ * Single threaded and deliberately unoptimised.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum {
+  ORC_OK = 0,
+  ORC_ERR_INVALID_ARG = -1,
+  ORC_ERR_DIM_MISMATCH = -2,
+  ORC_ERR_BLOCKSIZE = -3,
+  ORC_ERR_OUT_OF_RANGE = -4,
+  ORC_ERR_DUPLICATE = -5,
+  ORC_ERR_OOM = -6
+};
+
+typedef struct orc_node {
+  struct orc_node *child[4]; /* NULL = NIL */
+  double **blk;              /* leaf only: leaf_nb*leaf_nb optional blocks */
+} orc_node;
+
+typedef struct orc_matrix {
+  int64_t nrows, ncols;
+  int bs;
+  int L;       /* the tree spans 2^L leaf blocks per side */
+  int leaf_nb; /* leaf matrix side in blocks, 2^(L - depth) */
+  int depth;   /* level index of the leaves; the root is level 0 */
+  orc_node *root;
+} orc_matrix;
+
+typedef struct {
+  int64_t *tasks; /* per level, or NULL */
+  int64_t triples;
+  int oom;
+} orc_ctx;
+
+/* ------------------------------------------------------------ node helpers */
+static orc_node *new_node(const orc_matrix *m, int leaf) {
+  orc_node *n = (orc_node *)calloc(1, sizeof(orc_node));
+  if (!n) return NULL;
+  if (leaf) {
+    n->blk = (double **)calloc((size_t)m->leaf_nb * m->leaf_nb, sizeof(double *));
+    if (!n->blk) {
+      free(n);
+      return NULL;
+    }
+  }
+  return n;
+}
+
+static void free_node(const orc_matrix *m, orc_node *n) {
+  if (!n) return;
+  if (n->blk) {
+    for (int64_t t = 0; t < (int64_t)m->leaf_nb * m->leaf_nb; t++) free(n->blk[t]);
+    free(n->blk);
+  }
+  for (int c = 0; c < 4; c++) free_node(m, n->child[c]);
+  free(n);
+}
+
+static int leaf_is_empty(const orc_matrix *m, const orc_node *n) {
+  for (int64_t t = 0; t < (int64_t)m->leaf_nb * m->leaf_nb; t++)
+    if (n->blk[t]) return 0;
+  return 1;
+}
+
+static int block_is_zero(const double *b, int bs) {
+  for (int64_t t = 0; t < (int64_t)bs * bs; t++)
+    if (!(b[t] == 0.0)) return 0;
+  return 1;
+}
+
+/* --------------------------------------------------------------- building */
+static int ceil_log2(int64_t x) {
+  int l = 0;
+  while (((int64_t)1 << l) < x) l++;
+  return l;
+}
+
+void orc_free(orc_matrix *m) {
+  if (!m) return;
+  free_node(m, m->root);
+  free(m);
+}
+
+static orc_matrix *alloc_matrix(int64_t nrows, int64_t ncols, int bs, int L, int leaf_nb) {
+  orc_matrix *m = (orc_matrix *)calloc(1, sizeof(orc_matrix));
+  if (!m) return NULL;
+  m->nrows = nrows;
+  m->ncols = ncols;
+  m->bs = bs;
+  m->L = L;
+  if (leaf_nb > (1 << L)) leaf_nb = 1 << L;
+  m->leaf_nb = leaf_nb;
+  m->depth = L - ceil_log2(leaf_nb);
+  return m;
+}
+
+/* Build from a COO list of dense row-major blocks.  L is the common tree depth
+ * in blocks (callers pass the same L for the operands of one product);
+ * leaf_nb must be a power of two.  Exactly-zero blocks are dropped. */
+orc_matrix *orc_build(int64_t nrows, int64_t ncols, int bs, int L, int leaf_nb, int64_t nblk,
+                      const int32_t *brow, const int32_t *bcol, const double *vals,
+                      int *status) {
+  *status = ORC_OK;
+  if (nrows < 0 || ncols < 0 || bs < 1 || nblk < 0 || L < 0 || L > 30 || leaf_nb < 1 ||
+      (leaf_nb & (leaf_nb - 1))) {
+    *status = ORC_ERR_INVALID_ARG;
+    return NULL;
+  }
+  int64_t mb = (nrows + bs - 1) / bs, nb = (ncols + bs - 1) / bs;
+  if (mb > ((int64_t)1 << L) || nb > ((int64_t)1 << L)) {
+    *status = ORC_ERR_INVALID_ARG;
+    return NULL;
+  }
+  orc_matrix *m = alloc_matrix(nrows, ncols, bs, L, leaf_nb);
+  if (!m) {
+    *status = ORC_ERR_OOM;
+    return NULL;
+  }
+  int lbits = L - m->depth; /* log2(leaf_nb) */
+  size_t bbytes = (size_t)bs * bs * sizeof(double);
+  for (int64_t t = 0; t < nblk; t++) {
+    int64_t I = brow[t], J = bcol[t];
+    if (I < 0 || I >= mb || J < 0 || J >= nb) {
+      *status = ORC_ERR_OUT_OF_RANGE;
+      orc_free(m);
+      return NULL;
+    }
+  }
+  /* duplicate detection over all listed keys (zero or not) */
+  {
+    int64_t *keys = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nblk > 0 ? nblk : 1));
+    if (!keys) {
+      *status = ORC_ERR_OOM;
+      orc_free(m);
+      return NULL;
+    }
+    for (int64_t t = 0; t < nblk; t++) keys[t] = ((int64_t)brow[t] << 32) | (uint32_t)bcol[t];
+    /* insertion into the tree below catches duplicates among nonzero blocks;
+     * a simple sort catches the rest */
+    for (int64_t gap = nblk / 2; gap > 0; gap /= 2) /* shell sort */
+      for (int64_t i = gap; i < nblk; i++) {
+        int64_t v = keys[i], j = i;
+        while (j >= gap && keys[j - gap] > v) {
+          keys[j] = keys[j - gap];
+          j -= gap;
+        }
+        keys[j] = v;
+      }
+    for (int64_t t = 1; t < nblk; t++)
+      if (keys[t] == keys[t - 1]) {
+        free(keys);
+        *status = ORC_ERR_DUPLICATE;
+        orc_free(m);
+        return NULL;
+      }
+    free(keys);
+  }
+  for (int64_t t = 0; t < nblk; t++) {
+    const double *src = vals + (size_t)t * bs * bs;
+    if (block_is_zero(src, bs)) continue;
+    int64_t I = brow[t], J = bcol[t];
+    orc_node **slot = &m->root;
+    for (int level = 0; level <= m->depth; level++) {
+      int leaf = (level == m->depth);
+      if (!*slot) {
+        *slot = new_node(m, leaf);
+        if (!*slot) {
+          *status = ORC_ERR_OOM;
+          orc_free(m);
+          return NULL;
+        }
+      }
+      if (leaf) break;
+      int shift = L - level - 1; /* bit of I, J that selects the child */
+      int c = (int)(2 * ((I >> shift) & 1) + ((J >> shift) & 1));
+      slot = &(*slot)->child[c];
+    }
+    int64_t li = I & ((1 << lbits) - 1), lj = J & ((1 << lbits) - 1);
+    double **b = &(*slot)->blk[li * m->leaf_nb + lj];
+    *b = (double *)malloc(bbytes);
+    if (!*b) {
+      *status = ORC_ERR_OOM;
+      orc_free(m);
+      return NULL;
+    }
+    memcpy(*b, src, bbytes);
+  }
+  return m;
+}
+
+/* ------------------------------------------------------------ leaf library */
+/* Sum of outer products over the inner block index k (Sec. 4.1, Fig. 3). */
+static orc_node *leaf_multiply(const orc_matrix *m, const orc_node *a, const orc_node *b,
+                               orc_ctx *cx) {
+  int nb = m->leaf_nb, bs = m->bs;
+  orc_node *x = new_node(m, 1);
+  if (!x) {
+    cx->oom = 1;
+    return NULL;
+  }
+  for (int k = 0; k < nb; k++)
+    for (int i = 0; i < nb; i++) {
+      const double *aik = a->blk[i * nb + k];
+      if (!aik) continue;
+      for (int j = 0; j < nb; j++) {
+        const double *bkj = b->blk[k * nb + j];
+        if (!bkj) continue;
+        double **xij = &x->blk[i * nb + j];
+        if (!*xij) {
+          *xij = (double *)calloc((size_t)bs * bs, sizeof(double));
+          if (!*xij) {
+            cx->oom = 1;
+            return x;
+          }
+        }
+        cx->triples++;
+        double *c = *xij;
+        for (int r = 0; r < bs; r++)
+          for (int kk = 0; kk < bs; kk++) {
+            double av = aik[r * bs + kk];
+            for (int q = 0; q < bs; q++) c[r * bs + q] += av * bkj[kk * bs + q];
+          }
+      }
+    }
+  if (leaf_is_empty(m, x)) {
+    free_node(m, x);
+    return NULL;
+  }
+  return x;
+}
+
+/* Algorithm 2 on temporaries: consumes x and y, returns their sum. */
+static orc_node *add(const orc_matrix *m, orc_node *x, orc_node *y, int level) {
+  if (x && y) {
+    if (level == m->depth) {
+      int64_t nn = (int64_t)m->leaf_nb * m->leaf_nb, bb = (int64_t)m->bs * m->bs;
+      for (int64_t t = 0; t < nn; t++) {
+        if (!y->blk[t]) continue;
+        if (!x->blk[t]) {
+          x->blk[t] = y->blk[t];
+        } else {
+          for (int64_t e = 0; e < bb; e++) x->blk[t][e] += y->blk[t][e];
+          free(y->blk[t]);
+        }
+        y->blk[t] = NULL;
+      }
+    } else {
+      for (int c = 0; c < 4; c++) {
+        x->child[c] = add(m, x->child[c], y->child[c], level + 1);
+        y->child[c] = NULL;
+      }
+    }
+    free_node(m, y);
+    return x;
+  }
+  if (x) return x;
+  if (y) return y;
+  return NULL;
+}
+
+/* Algorithm 1. */
+static orc_node *multiply(const orc_matrix *m, const orc_node *a, const orc_node *b, int level,
+                          orc_ctx *cx) {
+  if (!a || !b) return NULL; /* fallback: C = NIL */
+  if (cx->tasks) cx->tasks[level]++;
+  if (level == m->depth) return leaf_multiply(m, a, b, cx);
+  orc_node *c = new_node(m, 0); /* createFromIds */
+  if (!c) {
+    cx->oom = 1;
+    return NULL;
+  }
+  int any = 0;
+  for (int mm = 0; mm < 2; mm++)
+    for (int n = 0; n < 2; n++) {
+      orc_node *y1 = multiply(m, a->child[2 * mm + 0], b->child[2 * 0 + n], level + 1, cx);
+      orc_node *y2 = multiply(m, a->child[2 * mm + 1], b->child[2 * 1 + n], level + 1, cx);
+      c->child[2 * mm + n] = add(m, y1, y2, level + 1);
+      any |= c->child[2 * mm + n] != NULL;
+    }
+  if (!any) {
+    free_node(m, c);
+    return NULL;
+  }
+  return c;
+}
+
+/* Remove exactly-zero product blocks, then empty leaves and nodes. */
+static orc_node *drop_zero(const orc_matrix *m, orc_node *n, int level) {
+  if (!n) return NULL;
+  if (level == m->depth) {
+    for (int64_t t = 0; t < (int64_t)m->leaf_nb * m->leaf_nb; t++)
+      if (n->blk[t] && block_is_zero(n->blk[t], m->bs)) {
+        free(n->blk[t]);
+        n->blk[t] = NULL;
+      }
+    if (leaf_is_empty(m, n)) {
+      free_node(m, n);
+      return NULL;
+    }
+    return n;
+  }
+  int any = 0;
+  for (int c = 0; c < 4; c++) {
+    n->child[c] = drop_zero(m, n->child[c], level + 1);
+    any |= n->child[c] != NULL;
+  }
+  if (!any) {
+    free_node(m, n);
+    return NULL;
+  }
+  return n;
+}
+
+/* C = A*B.  tasks (optional) receives the multiply-task count of each level
+ * 0..depth; triples receives the number of leaf block products. */
+orc_matrix *orc_multiply(const orc_matrix *A, const orc_matrix *B, int64_t *tasks,
+                         int64_t *triples, int *status) {
+  *status = ORC_OK;
+  if (!A || !B) {
+    *status = ORC_ERR_INVALID_ARG;
+    return NULL;
+  }
+  if (A->ncols != B->nrows) {
+    *status = ORC_ERR_DIM_MISMATCH;
+    return NULL;
+  }
+  if (A->bs != B->bs) {
+    *status = ORC_ERR_BLOCKSIZE;
+    return NULL;
+  }
+  if (A->L != B->L || A->leaf_nb != B->leaf_nb) {
+    *status = ORC_ERR_INVALID_ARG;
+    return NULL;
+  }
+  orc_matrix *C = alloc_matrix(A->nrows, B->ncols, A->bs, A->L, A->leaf_nb);
+  if (!C) {
+    *status = ORC_ERR_OOM;
+    return NULL;
+  }
+  orc_ctx cx = {tasks, 0, 0};
+  if (tasks) memset(tasks, 0, sizeof(int64_t) * (size_t)(A->depth + 1));
+  C->root = multiply(C, A->root, B->root, 0, &cx);
+  if (triples) *triples = cx.triples;
+  if (cx.oom) {
+    *status = ORC_ERR_OOM;
+    orc_free(C);
+    return NULL;
+  }
+  C->root = drop_zero(C, C->root, 0);
+  return C;
+}
+
+/* ---------------------------------------------------------------- output */
+static int64_t count_blocks(const orc_matrix *m, const orc_node *n, int level) {
+  if (!n) return 0;
+  int64_t s = 0;
+  if (level == m->depth) {
+    for (int64_t t = 0; t < (int64_t)m->leaf_nb * m->leaf_nb; t++) s += n->blk[t] != NULL;
+    return s;
+  }
+  for (int c = 0; c < 4; c++) s += count_blocks(m, n->child[c], level + 1);
+  return s;
+}
+
+int64_t orc_nblocks(const orc_matrix *m) { return m ? count_blocks(m, m->root, 0) : 0; }
+
+int orc_depth(const orc_matrix *m) { return m->depth; }
+
+typedef struct {
+  int64_t key;
+  const double *p;
+} orc_item;
+
+static void collect(const orc_matrix *m, const orc_node *n, int level, int64_t I0, int64_t J0,
+                    orc_item *out, int64_t *pos) {
+  if (!n) return;
+  if (level == m->depth) {
+    for (int i = 0; i < m->leaf_nb; i++)
+      for (int j = 0; j < m->leaf_nb; j++) {
+        const double *b = n->blk[i * m->leaf_nb + j];
+        if (!b) continue;
+        int64_t I = I0 * m->leaf_nb + i, J = J0 * m->leaf_nb + j;
+        out[*pos].key = (I << 32) | J;
+        out[*pos].p = b;
+        (*pos)++;
+      }
+    return;
+  }
+  for (int c = 0; c < 4; c++)
+    collect(m, n->child[c], level + 1, 2 * I0 + (c >> 1), 2 * J0 + (c & 1), out, pos);
+}
+
+static int cmp_item(const void *a, const void *b) {
+  int64_t x = ((const orc_item *)a)->key, y = ((const orc_item *)b)->key;
+  return (x > y) - (x < y);
+}
+
+/* Stored blocks in canonical row-major (I, J) order.  Buffers hold
+ * orc_nblocks(m) entries. */
+int orc_to_blocks(const orc_matrix *m, int32_t *brow, int32_t *bcol, double *vals) {
+  int64_t n = orc_nblocks(m), pos = 0;
+  orc_item *it = (orc_item *)malloc(sizeof(orc_item) * (size_t)(n > 0 ? n : 1));
+  if (!it) return ORC_ERR_OOM;
+  collect(m, m->root, 0, 0, 0, it, &pos);
+  qsort(it, (size_t)n, sizeof(orc_item), cmp_item);
+  size_t bb = (size_t)m->bs * m->bs;
+  for (int64_t t = 0; t < n; t++) {
+    brow[t] = (int32_t)(it[t].key >> 32);
+    bcol[t] = (int32_t)(it[t].key & 0xFFFFFFFF);
+    memcpy(vals + (size_t)t * bb, it[t].p, bb * sizeof(double));
+  }
+  free(it);
+  return ORC_OK;
+}
+
+/* --------------------------------------------- single block, by definition */
+static const double *find_block(const orc_matrix *m, int64_t I, int64_t J) {
+  const orc_node *n = m->root;
+  for (int level = 0; level < m->depth && n; level++) {
+    int shift = m->L - level - 1;
+    n = n->child[2 * ((I >> shift) & 1) + ((J >> shift) & 1)];
+  }
+  if (!n) return NULL;
+  int64_t mask = m->leaf_nb - 1;
+  return n->blk[(I & mask) * m->leaf_nb + (J & mask)];
+}
+
+/* C_IJ = sum_K A_IK B_KJ over the stored blocks (the plain definition of one
+ * product block, for sampled checks of large products).  Returns 1 if some K
+ * contributes, 0 if the block is structurally NIL. */
+int orc_block_product(const orc_matrix *A, const orc_matrix *B, int64_t I, int64_t J,
+                      double *out) {
+  int bs = A->bs, any = 0;
+  memset(out, 0, sizeof(double) * (size_t)bs * bs);
+  int64_t kb = (A->ncols + bs - 1) / bs;
+  for (int64_t K = 0; K < kb; K++) {
+    const double *a = find_block(A, I, K);
+    if (!a) continue;
+    const double *b = find_block(B, K, J);
+    if (!b) continue;
+    any = 1;
+    for (int r = 0; r < bs; r++)
+      for (int kk = 0; kk < bs; kk++) {
+        double av = a[r * bs + kk];
+        for (int q = 0; q < bs; q++) out[r * bs + q] += av * b[kk * bs + q];
+      }
+  }
+  return any;
+}
