@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Throughput of block-sparse C = A*B on GB300: time per product and useful GFLOP/s.
+
+Workload (one "step" = one full bsm_multiply: symbolic phase, numeric phase,
+exact-zero removal and C's level build, inputs resident in HBM):
+  random block-sparse N = 65536, 32 x 32 leaf blocks, every block position
+  nonzero with probability 0.02 (uniform placement), entries N(0,1), C = A*B.
+Useful flops = 2 * bs^3 per nonzero (A_IK, B_KJ) block pair.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank runs an independent product of the same size
+(weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+from synth import metrics  # noqa: E402
+
+METRIC = "useful GFLOP/s of C=A*B (2*bs^3 per nonzero block pair), FP64"
+WORKLOAD = {"workload": "random block-sparse N=65536, bs=32, block density 0.02, N(0,1)",
+            "n": 65536, "bs": 32, "p": 0.02, "global_batch": 1,
+            "l2": "inputs larger than L2 (A+B 1.4 GB, C 19 GB)"}
+# FP64 tensor peak: no FP64 entry in the measured peaks, so the bf16 measured
+# burst peak is scaled by the nominal FP64 / bf16 dense ratio (1.25 / 2250).
+FP64_NOMINAL_RATIO = 1.25 / 2250.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "of measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
+
+
+def workload(rank: int, n: int, bs: int, p: float):
+    sa = synth.BASE_SEED + 1 + 1000 * rank
+    A = synth.random_blocks(n, bs, p, sa)
+    B = synth.random_blocks(n, bs, p, sa + 7919)
+    return A, B
+
+
+# ------------------------------------------------------------- clock probe
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ traffic table
+def recorded_traffic(kernel: str, src: str):
+    """Per-launch DRAM bytes from an ncu capture, valid only while the kernel's
+    source file is unchanged since the capture (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d:
+        return None
+    sha = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+    return d.get("bytes_per_launch") if d.get("src_sha") == sha else None
+
+
+# ------------------------------------------------------------ CPU baseline
+def cpu_baseline(A, B, target_s: float = 12.0):
+    """The oracle, as it stands, on a bounded sample: the first R block rows of A
+    times the whole of B (same workload, fewer C rows)."""
+    import oracle
+
+    L = oracle.common_depth(A, B)
+    tb = oracle.tree(B, L)
+    rows = 8
+    while True:
+        keep = A.brow < rows
+        As = synth.BlockCOO(A.nrows, A.ncols, A.bs, A.brow[keep], A.bcol[keep], A.vals[keep])
+        ta = oracle.tree(As, L)
+        t0 = time.perf_counter()
+        P = oracle.multiply_trees(ta, tb)
+        dt = time.perf_counter() - t0
+        if dt > target_s / 4 or rows >= A.mb:
+            break
+        rows = min(A.mb, rows * 4)
+    flops = metrics.block_flops(A.bs, P.triples)
+    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {rows} of {A.mb} block rows of A times all of B "
+                      f"({P.triples} block products, {dt:.2f} s single-threaded)"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle timed on the host on bounded samples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    n, bs, p = WORKLOAD["n"], WORKLOAD["bs"], WORKLOAD["p"]
+    A, B = workload(0, n, bs, p)
+    L = oracle.common_depth(A, B)
+    tb = oracle.tree(B, L)
+    rows = 16
+    keep = A.brow < rows
+    As = synth.BlockCOO(A.nrows, A.ncols, bs, A.brow[keep], A.bcol[keep], A.vals[keep])
+    ta = oracle.tree(As, L)
+    for _ in range(args.warmup):
+        oracle.multiply_trees(ta, tb)
+    times, trip = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        P = oracle.multiply_trees(ta, tb)
+        times.append(time.perf_counter() - t0)
+        trip = P.triples
+    flops = metrics.block_flops(bs, trip)
+    tot = sum(times)
+    val = flops * len(times) / tot / 1e9
+    sample = f"first {rows} of {A.mb} block rows of A times all of B ({trip} block products)"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": WORKLOAD,
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": val,
+                             "unit": "GFLOP/s"},
+            "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+
+    import paper_1501_07800_gb300 as bsm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    bsm.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def allmax(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def allsum(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    n, bs, p = WORKLOAD["n"], WORKLOAD["bs"], WORKLOAD["p"]
+    t0 = time.time()
+    A, B = workload(rank, n, bs, p)
+    log(f"[rank {rank}] generated A {A.nblk} blocks, B {B.nblk} blocks in {time.time() - t0:.1f} s")
+    ga = bsm.bsm_build(n, n, bs, torch.from_numpy(A.brow).to(dev), torch.from_numpy(A.bcol).to(dev),
+                       torch.from_numpy(A.vals).to(dev))
+    gb = bsm.bsm_build(n, n, bs, torch.from_numpy(B.brow).to(dev), torch.from_numpy(B.bcol).to(dev),
+                       torch.from_numpy(B.vals).to(dev))
+    torch.cuda.synchronize()
+
+    bsm.bsm_set_timing(True)
+    prec = bsm.BSM_SPLIT_BF16 if args.mode == "split" else bsm.BSM_FP64
+    for _ in range(args.warmup):
+        C = bsm.bsm_multiply(ga, gb, prec=prec)
+        del C
+    torch.cuda.synchronize()
+    _, triples, nc_sym = bsm.bsm_last_stats()
+    flops = metrics.block_flops(bs, triples)
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    numeric_ms, launches = [], 0
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        C = bsm.bsm_multiply(ga, gb, prec=prec)
+        ev[i][1].record(stream)
+        ms, nl = bsm.bsm_last_phase_ms()
+        numeric_ms.append(ms[1])
+        launches += nl
+        nblk_c = C.nblk
+        del C
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_s = allmax(sum(step_ms) / 1e3)
+    total_flops = allsum(flops * args.steps)
+    value = total_flops / tot_s / 1e9
+
+    peaks, which = measured_peaks()
+    fp64_peak = peaks["bf16_tflops"] * FP64_NOMINAL_RATIO
+    t_num = statistics.mean(numeric_ms) / 1e3
+    achieved = flops / t_num / 1e12
+    roofline = {"bound": "tensor", "kernel": "k_numeric_fp64 (DMMA f64)",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak,
+                "peak_source": f"{which} bf16 burst {peaks['bf16_tflops']} TFLOP/s x nominal "
+                               f"FP64/bf16 ratio 1.25/2250",
+                "traffic": recorded_traffic("k_numeric_fp64",
+                                            "paper_1501_07800_gb300/csrc/bsm_numeric_fp64.cu")}
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "bf16x-split",
+                "data": "synthetic", "config": dict(WORKLOAD, parallelism=f"replicas{world}"),
+                "triples": triples, "c_blocks": nblk_c, "c_blocks_symbolic": nc_sym,
+                "phase_ms_last": [float(x) for x in bsm.bsm_last_phase_ms()[0]],
+                "roofline": roofline, "gpu_launches": launches, "clocks": clk}
+
+    # end to end through the public API with host buffers (pinned)
+    if not args.no_e2e:
+        e2e = run_e2e(bsm, torch, A, B, prec, max(1, min(args.steps, 3)))
+        e2e_v = allsum(flops * e2e["steps"]) / allmax(e2e["seconds"]) / 1e9
+        if line is not None:
+            line["e2e"] = {"value": e2e_v, "unit": "GFLOP/s",
+                           "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                           "ms_per_step": 1e3 * e2e["seconds"] / e2e["steps"]}
+    if line is not None and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(A, B)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(bsm, torch, A, B, prec, steps):
+    """Host COO in pinned memory -> bsm_build x2 -> bsm_multiply -> bsm_to_blocks
+    into pinned host buffers, every step."""
+    def pinned(a: np.ndarray) -> np.ndarray:
+        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    pa = [pinned(x) for x in (A.brow, A.bcol, A.vals)]
+    pb = [pinned(x) for x in (B.brow, B.bcol, B.vals)]
+    h2d = sum(x.nbytes for x in pa + pb)
+    out = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(steps):
+        ga = bsm.bsm_build(A.nrows, A.ncols, A.bs, *pa)
+        gb = bsm.bsm_build(B.nrows, B.ncols, B.bs, *pb)
+        C = bsm.bsm_multiply(ga, gb, prec=prec)
+        n = C.nblk
+        if out is None or out[0].shape[0] < n:
+            out = (torch.empty(n, dtype=torch.int32, pin_memory=True).numpy(),
+                   torch.empty(n, dtype=torch.int32, pin_memory=True).numpy(),
+                   torch.empty((n, A.bs, A.bs), dtype=torch.float64, pin_memory=True).numpy())
+            torch.cuda.synchronize()
+            t0 -= 0.0
+        bsm.bsm_to_blocks(C, out=out)
+        d2h = n * (8 + 8 * A.bs * A.bs)
+        del C, ga, gb
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"seconds": dt, "steps": steps, "h2d": h2d, "d2h": d2h}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="bsm", choices=["bsm", "reference"])
+    ap.add_argument("--mode", default="fp64", choices=["fp64", "split"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("warm-up raised to 3 steps")
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * bsm.h -- block-sparse matrix-matrix multiply C = A*B over a sparse quadtree,
+ * single GB300 GPU (sm_103a).
+ *
+ * Method: Rubensson & Rudberg, "Locality-aware parallel block-sparse
+ * matrix-matrix multiplication using the Chunks and Tasks programming model"
+ * (arXiv 1501.07800).  A matrix is a quadtree whose zero submatrices are NIL at
+ * any level (Sec. 3.1) and whose leaves hold dense bs x bs blocks (Sec. 4.1).
+ * The product recurses over pairs of non-NIL children (Algorithm 1); sums of
+ * partial products follow Algorithm 2.  Here the tree is stored on the device
+ * as Morton-ordered block keys plus per-level child bitmasks, the recursion
+ * runs level by level over all node pairs at once, and every C block is
+ * computed by a single owner with no atomics.
+ *
+ * Conventions shared by every call
+ *   - All calls return a bsm_status; no exception crosses this boundary.
+ *   - Work is ordered on `stream` (a cudaStream_t passed as void*; NULL = the
+ *     legacy default stream).  Calls that must size an output (build, multiply)
+ *     synchronise `stream` before returning; the data of a returned handle is
+ *     ready for any later work on the same stream.
+ *   - Argument errors are detected before any device work is queued and leave
+ *     outputs untouched (output handles set to NULL).  Errors found in the data
+ *     on the device (a block coordinate out of range, a duplicate key) are
+ *     reported by the same call after it synchronises.
+ *   - Block payloads are row-major bs x bs float64.  Matrix sides need not be
+ *     multiples of bs: edge blocks are stored full size and their entries
+ *     outside the matrix must be zero (the quadtree pads the matrix to 2^L
+ *     blocks per side, Sec. 3.1 "uniform blocksize ... as far as possible").
+ *   - A block is "zero" when every entry compares equal to 0.0 (so -0.0 is
+ *     zero and NaN is not).  Zero blocks are never stored (Sec. 4.1).
+ *   - Handles are immutable after creation, owned by the caller, freed with
+ *     bsm_destroy, and bound to the device that was current at creation.
+ */
+#ifndef BSM_H
+#define BSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bsm_matrix_s *bsm_matrix;
+
+typedef enum {
+  BSM_OK = 0,
+  BSM_ERR_INVALID_ARG = -1,      /* NULL pointer, negative size, bad option */
+  BSM_ERR_DIM_MISMATCH = -2,     /* A.ncols != B.nrows */
+  BSM_ERR_BLOCKSIZE = -3,        /* unsupported bs, or A.bs != B.bs */
+  BSM_ERR_OUT_OF_RANGE = -4,     /* a block coordinate outside the matrix */
+  BSM_ERR_DUPLICATE = -5,        /* the same (I, J) listed twice */
+  BSM_ERR_OOM = -6,              /* device allocation failed */
+  BSM_ERR_CUDA = -7,             /* a CUDA runtime error */
+  BSM_ERR_TIMEOUT = -8,          /* a bounded device wait gave up */
+  BSM_ERR_BUFFER_TOO_SMALL = -9, /* caller buffer smaller than the result */
+  BSM_ERR_UNSUPPORTED = -10      /* valid request this build cannot run */
+} bsm_status;
+
+typedef enum {
+  BSM_FP64 = 0,       /* FP64 tensor-core (DMMA) products, FP64 accumulation */
+  BSM_SPLIT_BF16 = 1  /* FP64 blocks split into BF16 slices on tcgen05 */
+} bsm_precision;
+
+/* Options of one product (NULL = all defaults: FP64). */
+typedef struct {
+  int prec;   /* bsm_precision */
+  int slices; /* split modes: number of slices per operand, 0 = default (6) */
+  int flags;  /* reserved, must be 0 */
+} bsm_mult_opts;
+
+/* Supported leaf block sides. */
+#define BSM_BS_MIN 16
+#define BSM_BS_MAX 64
+
+/*
+ * bsm_build -- create a matrix from a COO list of dense leaf blocks
+ * (the "Matrix" chunk hierarchy of Sec. 3.1 built from the leaves up).
+ *
+ *   nrows, ncols  matrix size in elements (>= 0)
+ *   bs            leaf block side: 16, 32 or 64
+ *   nblk          number of listed blocks (>= 0)
+ *   brow, bcol    int32[nblk] block coordinates, 0 <= brow < ceil(nrows/bs),
+ *                 0 <= bcol < ceil(ncols/bs); any order; duplicates rejected
+ *   vals          float64[nblk][bs][bs], block t row-major at vals + t*bs*bs
+ *   on_device     0: the three arrays are host memory (copied in this call);
+ *                 1: they are device memory of the current device
+ *   stream        cudaStream_t or NULL
+ *   out           receives the new handle (NULL on error)
+ *
+ * Exactly-zero blocks are dropped.  The library copies the inputs; the caller
+ * may reuse its buffers when the call returns.
+ * Errors: INVALID_ARG, BLOCKSIZE, OUT_OF_RANGE, DUPLICATE, OOM, CUDA.
+ */
+bsm_status bsm_build(int64_t nrows, int64_t ncols, int bs, int64_t nblk, const int32_t *brow,
+                     const int32_t *bcol, const double *vals, int on_device, void *stream,
+                     bsm_matrix *out);
+
+/*
+ * bsm_multiply -- C = A*B (Algorithm 1 with the leaf product of Sec. 4.1).
+ *
+ * Symbolic phase: node pairs are expanded level by level from the roots down
+ * to the leaf blocks, skipping NIL children, giving every C block its ordered
+ * list of (A block, B block) products.  Numeric phase: each C block is summed
+ * by one owner.  C blocks whose entries are all exactly zero are removed.
+ * The depth of the product is the larger depth of A and B.
+ *
+ *   A, B   operands, A.ncols == B.nrows, same bs
+ *   C      receives the new handle (NULL on error); C.nrows = A.nrows,
+ *          C.ncols = B.ncols, C.bs = A.bs
+ *   opts   NULL or options (precision mode, slice count)
+ * Errors: INVALID_ARG, DIM_MISMATCH, BLOCKSIZE, OOM, CUDA, TIMEOUT, UNSUPPORTED.
+ */
+bsm_status bsm_multiply(bsm_matrix A, bsm_matrix B, bsm_matrix *C, const bsm_mult_opts *opts,
+                        void *stream);
+
+/*
+ * bsm_multiply_batched -- C[i] = A[i]*B[i] for n independent products.
+ * Symbolic phases run per product; the numeric phase of all products runs as
+ * one persistent launch over a single work list ordered by decreasing work.
+ * Results are identical to n calls of bsm_multiply with the same options.
+ *   n          number of products (>= 0)
+ *   A, B       arrays of n handles
+ *   C          array of n handle slots, filled on success (all NULL on error)
+ * Errors: as bsm_multiply.
+ */
+bsm_status bsm_multiply_batched(int n, const bsm_matrix *A, const bsm_matrix *B, bsm_matrix *C,
+                                const bsm_mult_opts *opts, void *stream);
+
+/*
+ * bsm_to_blocks -- copy the stored blocks out in canonical row-major (I, J)
+ * order.
+ *   nblk_inout  in: capacity of the caller buffers in blocks;
+ *               out: number of stored blocks
+ *   brow, bcol  int32[capacity] or NULL
+ *   vals        float64[capacity][bs][bs] or NULL
+ *   on_device   0: host buffers (the call synchronises `stream`);
+ *               1: device buffers of the handle's device
+ * With all three buffers NULL the call only reports the block count.
+ * Errors: INVALID_ARG, BUFFER_TOO_SMALL (count still reported), OOM, CUDA.
+ */
+bsm_status bsm_to_blocks(bsm_matrix M, int64_t *nblk_inout, int32_t *brow, int32_t *bcol,
+                         double *vals, int on_device, void *stream);
+
+/* bsm_info -- sizes of a handle; any output pointer may be NULL. */
+bsm_status bsm_info(bsm_matrix M, int64_t *nrows, int64_t *ncols, int *bs, int64_t *nblk);
+
+/*
+ * bsm_level_counts -- nodes per quadtree level of a handle, root level first
+ * (the NIL-free node sets whose pairings are the multiply tasks of Sec. 5.1).
+ *   counts  int64[cap] receives counts for levels 0..L (L+1 values)
+ *   nlev    receives L+1
+ * Errors: INVALID_ARG, BUFFER_TOO_SMALL.
+ */
+bsm_status bsm_level_counts(bsm_matrix M, int64_t *counts, int cap, int *nlev);
+
+/*
+ * bsm_last_stats -- statistics of the last bsm_multiply on this thread:
+ *   tasks    int64[cap]: multiply tasks (non-NIL node pairs) per level of the
+ *            product tree, root level first (Sec. 5.1, C_l); may be NULL
+ *   nlev     receives the number of levels
+ *   triples  receives the number of leaf block products
+ *   nc_sym   receives the number of C blocks before zero-block removal
+ */
+bsm_status bsm_last_stats(int64_t *tasks, int cap, int *nlev, int64_t *triples, int64_t *nc_sym);
+
+/*
+ * bsm_set_timing -- per-phase CUDA-event timing of bsm_multiply on the calling
+ * thread: 1 = on, 0 = off (default off; the environment variable
+ * BSM_TIMING=1 turns it on for every thread).  Timing adds events on the
+ * product's stream and one event synchronisation per product.
+ */
+bsm_status bsm_set_timing(int on);
+
+/*
+ * bsm_last_phase_ms -- results of the last timed bsm_multiply on this thread.
+ *   ms        double[cap]: ms[0] symbolic phase, ms[1] numeric phase (the
+ *             numeric kernel plus, in split modes, the slicing kernels),
+ *             ms[2] zero-block removal and level build of C; may be NULL
+ *   nphase    receives 3
+ *   launches  receives the number of kernel launches the product issued
+ *             (timed or not); may be NULL
+ * Errors: BUFFER_TOO_SMALL if cap < 3 with ms != NULL.
+ */
+bsm_status bsm_last_phase_ms(double *ms, int cap, int *nphase, int64_t *launches);
+
+/* bsm_destroy -- free a handle (NULL is accepted).  Work queued on other
+ * streams that still reads the handle must be complete. */
+bsm_status bsm_destroy(bsm_matrix M);
+
+/* bsm_status_string -- static description of a status code. */
+const char *bsm_status_string(bsm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSM_H */

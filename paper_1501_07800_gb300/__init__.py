@@ -1,0 +1,260 @@
+"""Python binding of libbsm: block-sparse C = A*B over a sparse quadtree on GB300.
+
+Argument marshalling only: every step of the product runs in the CUDA library
+(``csrc/``), declared in ``include/bsm.h``.  Function names match the C ABI.
+Host inputs are numpy arrays; device inputs and outputs are torch CUDA tensors
+(PyTorch supplies device memory and streams, nothing else).  If libbsm.so is
+missing the import fails: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbsm.so")
+
+BSM_FP64 = 0
+BSM_SPLIT_BF16 = 1
+
+STATUS = {
+    0: "BSM_OK", -1: "BSM_ERR_INVALID_ARG", -2: "BSM_ERR_DIM_MISMATCH", -3: "BSM_ERR_BLOCKSIZE",
+    -4: "BSM_ERR_OUT_OF_RANGE", -5: "BSM_ERR_DUPLICATE", -6: "BSM_ERR_OOM", -7: "BSM_ERR_CUDA",
+    -8: "BSM_ERR_TIMEOUT", -9: "BSM_ERR_BUFFER_TOO_SMALL", -10: "BSM_ERR_UNSUPPORTED",
+}
+
+# function name -> (restype, argtypes)
+_P, _I64, _I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+_PROTOS = {
+    "bsm_build": (_I32, [_I64, _I64, _I32, _I64, _P, _P, _P, _I32, _P, _P]),
+    "bsm_multiply": (_I32, [_P, _P, _P, _P, _P]),
+    "bsm_multiply_batched": (_I32, [_I32, _P, _P, _P, _P, _P]),
+    "bsm_to_blocks": (_I32, [_P, _P, _P, _P, _P, _I32, _P]),
+    "bsm_info": (_I32, [_P, _P, _P, _P, _P]),
+    "bsm_level_counts": (_I32, [_P, _P, _I32, _P]),
+    "bsm_last_stats": (_I32, [_P, _I32, _P, _P, _P]),
+    "bsm_set_timing": (_I32, [_I32]),
+    "bsm_last_phase_ms": (_I32, [_P, _I32, _P, _P]),
+    "bsm_destroy": (_I32, [_P]),
+    "bsm_status_string": (ctypes.c_char_p, [_I32]),
+}
+
+_lib = None
+
+
+class BsmError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        name = STATUS.get(code, str(code))
+        super().__init__(f"{what}: {name}" if what else name)
+        self.code = code
+        self.name = name
+
+
+class bsm_mult_opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("slices", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+def load(path: str | None = None):
+    """Load libbsm.so (built by ``build.build()``); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"libbsm.so not built ({path}); run paper_1501_07800_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _PROTOS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise BsmError(code, what)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+class Matrix:
+    """Owning wrapper of a bsm_matrix handle (freed with bsm_destroy)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.bsm_destroy(h)
+            self.handle = None
+
+    def destroy(self):
+        self.__del__()
+
+    def info(self):
+        return bsm_info(self)
+
+    @property
+    def nblk(self) -> int:
+        return bsm_info(self)[3]
+
+
+def bsm_status_string(code: int) -> str:
+    return load().bsm_status_string(code).decode()
+
+
+def bsm_build(nrows: int, ncols: int, bs: int, brow, bcol, vals, stream=None) -> Matrix:
+    """Build from COO blocks: numpy (host) or torch CUDA tensors (device)."""
+    lib = load()
+    out = ctypes.c_void_p()
+    if _is_torch_cuda(vals):
+        import torch
+        brow = brow.to(torch.int32).contiguous()
+        bcol = bcol.to(torch.int32).contiguous()
+        vals = vals.to(torch.float64).contiguous()
+        n = int(brow.numel())
+        code = lib.bsm_build(nrows, ncols, bs, n, brow.data_ptr(), bcol.data_ptr(),
+                             vals.data_ptr(), 1, _stream_ptr(stream), ctypes.byref(out))
+    else:
+        brow = np.ascontiguousarray(brow, np.int32)
+        bcol = np.ascontiguousarray(bcol, np.int32)
+        vals = np.ascontiguousarray(vals, np.float64)
+        n = int(brow.shape[0])
+        code = lib.bsm_build(nrows, ncols, bs, n, brow.ctypes.data, bcol.ctypes.data,
+                             vals.ctypes.data, 0, _stream_ptr(stream), ctypes.byref(out))
+    _check(code, "bsm_build")
+    return Matrix(out.value)
+
+
+def _opts(prec: int, slices: int):
+    if prec == BSM_FP64 and slices == 0:
+        return None
+    return ctypes.byref(bsm_mult_opts(prec, slices, 0))
+
+
+def bsm_multiply(A: Matrix, B: Matrix, prec: int = BSM_FP64, slices: int = 0,
+                 stream=None) -> Matrix:
+    lib = load()
+    out = ctypes.c_void_p()
+    code = lib.bsm_multiply(A.handle, B.handle, ctypes.byref(out), _opts(prec, slices),
+                            _stream_ptr(stream))
+    _check(code, "bsm_multiply")
+    return Matrix(out.value)
+
+
+def bsm_multiply_batched(As, Bs, prec: int = BSM_FP64, slices: int = 0, stream=None):
+    lib = load()
+    n = len(As)
+    if len(Bs) != n:
+        raise ValueError("As and Bs differ in length")
+    ha = (ctypes.c_void_p * max(n, 1))(*[a.handle for a in As])
+    hb = (ctypes.c_void_p * max(n, 1))(*[b.handle for b in Bs])
+    hc = (ctypes.c_void_p * max(n, 1))()
+    code = lib.bsm_multiply_batched(n, ha, hb, hc, _opts(prec, slices), _stream_ptr(stream))
+    _check(code, "bsm_multiply_batched")
+    return [Matrix(hc[i]) for i in range(n)]
+
+
+def bsm_info(M: Matrix):
+    """(nrows, ncols, bs, nblk)."""
+    nr, nc, nb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    bs = ctypes.c_int()
+    _check(load().bsm_info(M.handle, ctypes.byref(nr), ctypes.byref(nc), ctypes.byref(bs),
+                           ctypes.byref(nb)), "bsm_info")
+    return nr.value, nc.value, bs.value, nb.value
+
+
+def bsm_to_blocks(M: Matrix, device: bool = False, stream=None, out=None):
+    """Stored blocks in row-major (I, J) order: (brow, bcol, vals).
+
+    device=False: numpy arrays (the call synchronises the stream);
+    device=True: torch CUDA tensors on the current device.  `out` may supply
+    preallocated (brow, bcol, vals) buffers of either kind.
+    """
+    lib = load()
+    nr, nc, bs, n = bsm_info(M)
+    if out is not None:
+        # capacity = the smallest caller buffer, in blocks
+        caps = [int(out[0].shape[0]), int(out[1].shape[0]), int(out[2].shape[0])]
+        if tuple(out[2].shape[1:]) != (bs, bs):
+            raise ValueError("vals buffer must be [n, bs, bs]")
+        want = ("int32", "int32", "float64")
+        for o, w in zip(out, want):
+            if str(o.dtype).replace("torch.", "") != w:
+                raise ValueError(f"buffer dtype {o.dtype}, expected {w}")
+        cnt = ctypes.c_int64(min(caps))
+    else:
+        cnt = ctypes.c_int64(n)
+    if device:
+        import torch
+        if out is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+            out = (torch.empty(n, dtype=torch.int32, device=dev),
+                   torch.empty(n, dtype=torch.int32, device=dev),
+                   torch.empty((n, bs, bs), dtype=torch.float64, device=dev))
+        ptrs = [t.data_ptr() for t in out]
+        code = lib.bsm_to_blocks(M.handle, ctypes.byref(cnt), *ptrs, 1, _stream_ptr(stream))
+    else:
+        if out is None:
+            out = (np.empty(n, np.int32), np.empty(n, np.int32), np.empty((n, bs, bs), np.float64))
+        ptrs = [o.data_ptr() if hasattr(o, "data_ptr") else o.ctypes.data for o in out]
+        code = lib.bsm_to_blocks(M.handle, ctypes.byref(cnt), *ptrs, 0, _stream_ptr(stream))
+    _check(code, "bsm_to_blocks")
+    return out
+
+
+def bsm_level_counts(M: Matrix) -> np.ndarray:
+    lib = load()
+    nlev = ctypes.c_int()
+    _check(lib.bsm_level_counts(M.handle, None, 0, ctypes.byref(nlev)), "bsm_level_counts")
+    c = np.zeros(nlev.value, np.int64)
+    _check(lib.bsm_level_counts(M.handle, c.ctypes.data, nlev.value, ctypes.byref(nlev)),
+           "bsm_level_counts")
+    return c
+
+
+def bsm_last_stats():
+    """(tasks per level root first, triples, C blocks before zero removal)."""
+    lib = load()
+    nlev, trip, ncs = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+    t = np.zeros(64, np.int64)
+    _check(lib.bsm_last_stats(t.ctypes.data, 64, ctypes.byref(nlev), ctypes.byref(trip),
+                              ctypes.byref(ncs)), "bsm_last_stats")
+    return t[: nlev.value].copy(), trip.value, ncs.value
+
+
+def bsm_set_timing(on: bool):
+    _check(load().bsm_set_timing(1 if on else 0), "bsm_set_timing")
+
+
+def bsm_last_phase_ms():
+    """([symbolic, numeric, finish] ms of the last timed product, kernel launches)."""
+    ms = np.zeros(3, np.float64)
+    n, launches = ctypes.c_int(), ctypes.c_int64()
+    _check(load().bsm_last_phase_ms(ms.ctypes.data, 3, ctypes.byref(n), ctypes.byref(launches)),
+           "bsm_last_phase_ms")
+    return ms, launches.value
+
+
+def bsm_destroy(M: Matrix):
+    M.destroy()

@@ -1,0 +1,158 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/bsm.h"
+
+#define BSM_MAXH 31  // tree heights 0..31: up to 2^31 blocks per side
+
+// ------------------------------------------------------------- device errors
+// Device code never traps: it records the first problem in an error word that
+// the host reads after the kernel.
+enum : unsigned {
+  DERR_NONE = 0,
+  DERR_OUT_OF_RANGE = 1,
+  DERR_DUPLICATE = 2,
+  DERR_TIMEOUT = 3,
+  DERR_BOUNDS = 4,
+};
+
+// Spin limit of every mbarrier wait (each try_wait may itself suspend for a
+// while); ~seconds at GB300 clocks, far beyond any legitimate wait.
+#define BSM_SPIN_LIMIT (1u << 26)
+
+struct bsm_matrix_s {
+  int64_t nrows = 0, ncols = 0, mb = 0, nb = 0;
+  int bs = 0;
+  int L = 0;         // the tree spans 2^L blocks per side
+  int device = 0;
+  int64_t nblk = 0;  // stored (nonzero) blocks
+  uint64_t *keys = nullptr;  // [nblk] Morton keys, ascending
+  double *vals = nullptr;    // [nblk][bs][bs]
+  // levels h = 1..L (height above the leaves); level L is the root
+  int64_t nlev[BSM_MAXH + 1] = {};
+  uint64_t *lkeys[BSM_MAXH + 1] = {};
+  uint8_t *lmask[BSM_MAXH + 1] = {};
+  int32_t *lcstart[BSM_MAXH + 1] = {};
+  // every device allocation owned by the handle
+  std::vector<void *> owned;
+};
+
+// Morton key: bit 2b+1 = bit b of the block row, bit 2b = bit b of the block
+// column, so the two low bits of a key are the child index 2*rowbit + colbit.
+__host__ __device__ inline uint64_t morton_spread(uint64_t x) {
+  x &= 0xFFFFFFFFull;
+  x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+__host__ __device__ inline uint64_t morton_key(uint64_t I, uint64_t J) {
+  return (morton_spread(I) << 1) | morton_spread(J);
+}
+__host__ __device__ inline uint32_t morton_compact(uint64_t x) {
+  x &= 0x5555555555555555ull;
+  x = (x | (x >> 1)) & 0x3333333333333333ull;
+  x = (x | (x >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x >> 4)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x >> 8)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x >> 16)) & 0x00000000FFFFFFFFull;
+  return (uint32_t)x;
+}
+
+inline int ceil_log2_i64(int64_t x) {
+  int l = 0;
+  while (((int64_t)1 << l) < x) l++;
+  return l;
+}
+
+// ----------------------------------------------------------- host utilities
+// Stream-ordered allocation from the device's default memory pool.
+bsm_status dev_alloc(void **p, size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+bsm_status cuda_status(cudaError_t e);
+
+// Reusable pinned host scratch for small readbacks (per thread).
+struct HostScratch {
+  void *p = nullptr;
+  size_t n = 0;
+  void *get(size_t bytes);
+  ~HostScratch();
+};
+HostScratch &host_scratch();
+
+// Exclusive prefix sums on the device (CUB), sized on first use.
+bsm_status scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+bsm_status scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+bsm_status scan_exclusive_int4(const int4 *in, int4 *out, int64_t n, cudaStream_t s);
+bsm_status sort_keys_u64(const uint64_t *kin, uint64_t *kout, const int32_t *vin, int32_t *vout,
+                         int64_t n, int end_bit, cudaStream_t s);
+
+// Builds the level arrays of a handle whose keys are set (bsm_tree.cu).
+bsm_status build_levels(bsm_matrix M, cudaStream_t s);
+// Copies blocks: dst[t] = src[idx[t]] (bs*bs doubles each).
+void launch_gather_blocks(const double *src, const int32_t *idx, double *dst, int64_t n, int bs,
+                          cudaStream_t s);
+
+// ---------------------------------------------------------- symbolic result
+// Leaf-level task list of one product: C blocks in Morton order, each with the
+// ordered (A block, B block) pairs that contribute to it (k ascending).
+struct SymbolicResult {
+  int64_t nc = 0;           // C blocks (before zero removal)
+  int64_t nt = 0;           // triples
+  uint64_t *ckeys = nullptr;  // [nc]
+  int32_t *seg = nullptr;     // [nc+1] start of each C block's pairs
+  int32_t *ta = nullptr;      // [nt] A leaf index
+  int32_t *tb = nullptr;      // [nt] B leaf index
+  int H = 0;                  // product tree height
+  int64_t tasks[BSM_MAXH + 1] = {};  // pairs per height (index = height)
+};
+bsm_status symbolic_multiply(bsm_matrix A, bsm_matrix B, SymbolicResult *out, cudaStream_t s);
+void free_symbolic(SymbolicResult *r, cudaStream_t s);
+
+// ----------------------------------------------------------- numeric phase
+// Computes every C block of `sym` into cvals and sets nzflag[c] = 1 if the
+// block has an entry != 0.0.  errword receives DERR_* codes.
+bsm_status numeric_fp64(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, double *cvals,
+                        int32_t *nzflag, unsigned *errword, cudaStream_t s);
+
+// Split-precision numeric phase (BF16 slices on tcgen05, exact FP32
+// accumulation, integer recombination).
+bsm_status numeric_split(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, int slices,
+                         double *cvals, int32_t *nzflag, unsigned *errword, cudaStream_t s);
+
+// Handle shells for results (bsm_tree.cu).
+bsm_matrix new_matrix_shell(int64_t nrows, int64_t ncols, int bs, int L);
+void free_matrix_shell(bsm_matrix M, cudaStream_t s);
+
+// Thread-local statistics of the last product.
+struct LastStats {
+  int nlev = 0;
+  int64_t tasks[BSM_MAXH + 1] = {};
+  int64_t triples = 0, nc_sym = 0;
+  double phase_ms[3] = {0, 0, 0};
+  int64_t launches = 0;
+};
+LastStats &last_stats();
+
+// Kernel-launch counter of the calling thread (every launch site adds to it).
+int64_t &launch_counter();
+inline void count_launch(int n = 1) { launch_counter() += n; }
+bool timing_enabled();
+
+#define BSM_TRY(x)                       \
+  do {                                   \
+    bsm_status _st = (x);                \
+    if (_st != BSM_OK) return _st;       \
+  } while (0)
+#define BSM_CUDA(x)                                   \
+  do {                                                \
+    cudaError_t _e = (x);                             \
+    if (_e != cudaSuccess) return cuda_status(_e);    \
+  } while (0)

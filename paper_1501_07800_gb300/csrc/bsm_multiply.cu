@@ -1,0 +1,249 @@
+// C = A*B: symbolic phase, numeric phase, exact-zero block removal, C levels.
+#include <cstring>
+
+#include "bsm_internal.cuh"
+
+namespace {
+
+__global__ void k_compact_c(const int32_t *__restrict__ nz, const int32_t *__restrict__ pos,
+                            int64_t nc, const uint64_t *__restrict__ ckeys,
+                            uint64_t *__restrict__ okeys, int32_t *__restrict__ idx) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc || !nz[c]) return;
+  okeys[pos[c]] = ckeys[c];
+  idx[pos[c]] = (int32_t)c;
+}
+
+inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+bsm_status check_pair(bsm_matrix A, bsm_matrix B) {
+  if (!A || !B) return BSM_ERR_INVALID_ARG;
+  if (A->ncols != B->nrows) return BSM_ERR_DIM_MISMATCH;
+  if (A->bs != B->bs) return BSM_ERR_BLOCKSIZE;
+  if (A->device != B->device) return BSM_ERR_INVALID_ARG;
+  return BSM_OK;
+}
+
+bsm_status check_opts(const bsm_mult_opts *o, int *prec, int *slices) {
+  *prec = BSM_FP64;
+  *slices = 0;
+  if (!o) return BSM_OK;
+  if (o->flags != 0) return BSM_ERR_INVALID_ARG;
+  if (o->prec != BSM_FP64 && o->prec != BSM_SPLIT_BF16) return BSM_ERR_INVALID_ARG;
+  if (o->slices < 0 || o->slices > 8) return BSM_ERR_INVALID_ARG;
+  *prec = o->prec;
+  *slices = o->slices == 0 ? 7 : o->slices;
+  return BSM_OK;
+}
+
+}  // namespace
+
+// Assembles C from the numeric result: drops exactly-zero blocks and builds
+// the level arrays.  Takes ownership of sym->ckeys and cvals.
+static bsm_status finish_product(bsm_matrix C, SymbolicResult *sym, double *cvals, int32_t *nz,
+                                 unsigned *err, cudaStream_t s) {
+  int64_t nc = sym->nc;
+  int bs = C->bs;
+  int32_t *pos = nullptr;
+  bsm_status st = dev_alloc((void **)&pos, 4 * (nc + 1), s);
+  if (st != BSM_OK) return st;
+  st = scan_exclusive_i32(nz, pos, nc, s);
+  int32_t *h = (int32_t *)host_scratch().get(16);
+  if (st == BSM_OK && !h) st = BSM_ERR_OOM;
+  if (st == BSM_OK) {
+    cudaMemcpyAsync(h, pos + nc - 1, 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h + 1, nz + nc - 1, 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h + 2, err, 4, cudaMemcpyDeviceToHost, s);
+    st = cuda_status(cudaStreamSynchronize(s));
+  }
+  if (st == BSM_OK && h[2] == DERR_TIMEOUT) st = BSM_ERR_TIMEOUT;
+  if (st == BSM_OK && h[2] != DERR_NONE) st = BSM_ERR_CUDA;
+  if (st != BSM_OK) {
+    dev_free(pos, s);
+    return st;
+  }
+  int64_t nkeep = (int64_t)h[0] + h[1];
+  if (nkeep == nc) {
+    C->keys = sym->ckeys;
+    C->vals = cvals;
+    sym->ckeys = nullptr;
+    C->owned.push_back(C->keys);
+    C->owned.push_back(C->vals);
+  } else {
+    uint64_t *okeys = nullptr;
+    double *ovals = nullptr;
+    int32_t *idx = nullptr;
+    if ((st = dev_alloc((void **)&okeys, 8 * (nkeep > 0 ? nkeep : 1), s)) ||
+        (st = dev_alloc((void **)&ovals, sizeof(double) * bs * bs * (nkeep > 0 ? nkeep : 1), s)) ||
+        (st = dev_alloc((void **)&idx, 4 * (nkeep > 0 ? nkeep : 1), s))) {
+      dev_free(okeys, s);
+      dev_free(ovals, s);
+      dev_free(idx, s);
+      dev_free(pos, s);
+      return st;
+    }
+    count_launch();
+    k_compact_c<<<grid_for(nc, 256), 256, 0, s>>>(nz, pos, nc, sym->ckeys, okeys, idx);
+    launch_gather_blocks(cvals, idx, ovals, nkeep, bs, s);
+    dev_free(idx, s);
+    dev_free(cvals, s);
+    C->keys = okeys;
+    C->vals = ovals;
+    C->owned.push_back(okeys);
+    C->owned.push_back(ovals);
+  }
+  dev_free(pos, s);
+  C->nblk = nkeep;
+  return build_levels(C, s);
+}
+
+// Per-phase CUDA events of one product (only when timing is enabled).
+struct PhaseTimer {
+  bool on;
+  cudaEvent_t ev[4] = {};
+  int n = 0;
+  explicit PhaseTimer(bool enabled) : on(enabled) {
+    if (on)
+      for (auto &e : ev) cudaEventCreate(&e);
+  }
+  void mark(cudaStream_t s) {
+    if (on && n < 4) cudaEventRecord(ev[n++], s);
+  }
+  void collect(double *ms) {
+    if (!on) return;
+    if (n == 4 && cudaEventSynchronize(ev[3]) == cudaSuccess)
+      for (int i = 0; i < 3; i++) {
+        float t = 0;
+        cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+        ms[i] = t;
+      }
+  }
+  ~PhaseTimer() {
+    if (on)
+      for (auto &e : ev) cudaEventDestroy(e);
+  }
+};
+
+// One product with an explicit numeric routine (shared by single and batched
+// entry points).
+static bsm_status multiply_one(bsm_matrix A, bsm_matrix B, int prec, int slices, cudaStream_t s,
+                               bsm_matrix *out) {
+  *out = nullptr;
+  LastStats &ls = last_stats();
+  ls = LastStats();
+  int64_t l0 = launch_counter();
+  PhaseTimer timer(timing_enabled());
+  timer.mark(s);
+  SymbolicResult sym;
+  bsm_status st = symbolic_multiply(A, B, &sym, s);
+  if (st != BSM_OK) {
+    free_symbolic(&sym, s);
+    return st;
+  }
+  ls.nlev = sym.H + 1;
+  for (int l = 0; l <= sym.H; l++) ls.tasks[l] = sym.tasks[sym.H - l];
+  ls.triples = sym.nt;
+  ls.nc_sym = sym.nc;
+  int64_t mb = A->mb, nb = B->nb;
+  int64_t side = mb > nb ? mb : nb;
+  bsm_matrix C = new_matrix_shell(A->nrows, B->ncols, A->bs, ceil_log2_i64(side < 1 ? 1 : side));
+  if (sym.nc == 0) {
+    free_symbolic(&sym, s);
+    st = build_levels(C, s);
+    if (st != BSM_OK) {
+      free_matrix_shell(C, s);
+      return st;
+    }
+    ls.launches = launch_counter() - l0;
+    *out = C;
+    return BSM_OK;
+  }
+  if (sym.nc > 0x7FFFFFFF) {
+    free_symbolic(&sym, s);
+    free_matrix_shell(C, s);
+    return BSM_ERR_UNSUPPORTED;
+  }
+  double *cvals = nullptr;
+  int32_t *nz = nullptr;
+  unsigned *err = nullptr;
+  int bs = A->bs;
+  if ((st = dev_alloc((void **)&cvals, sizeof(double) * bs * bs * sym.nc, s)) ||
+      (st = dev_alloc((void **)&nz, 4 * sym.nc, s)) ||
+      (st = dev_alloc((void **)&err, sizeof(unsigned), s))) {
+    dev_free(cvals, s);
+    dev_free(nz, s);
+    dev_free(err, s);
+    free_symbolic(&sym, s);
+    free_matrix_shell(C, s);
+    return st;
+  }
+  cudaMemsetAsync(err, 0, sizeof(unsigned), s);
+  timer.mark(s);
+  if (prec == BSM_FP64)
+    st = numeric_fp64(A, B, sym, cvals, nz, err, s);
+  else
+    st = numeric_split(A, B, sym, slices, cvals, nz, err, s);
+  timer.mark(s);
+  if (st == BSM_OK) {
+    st = finish_product(C, &sym, cvals, nz, err, s);  // owns cvals from here
+    cvals = nullptr;
+  }
+  timer.mark(s);
+  dev_free(cvals, s);
+  dev_free(nz, s);
+  dev_free(err, s);
+  free_symbolic(&sym, s);
+  if (st != BSM_OK) {
+    free_matrix_shell(C, s);
+    return st;
+  }
+  timer.collect(ls.phase_ms);
+  ls.launches = launch_counter() - l0;
+  *out = C;
+  return BSM_OK;
+}
+
+extern "C" bsm_status bsm_multiply(bsm_matrix A, bsm_matrix B, bsm_matrix *C,
+                                   const bsm_mult_opts *opts, void *stream) {
+  if (!C) return BSM_ERR_INVALID_ARG;
+  *C = nullptr;
+  BSM_TRY(check_pair(A, B));
+  int prec, slices;
+  BSM_TRY(check_opts(opts, &prec, &slices));
+  return multiply_one(A, B, prec, slices, (cudaStream_t)stream, C);
+}
+
+extern "C" bsm_status bsm_last_stats(int64_t *tasks, int cap, int *nlev, int64_t *triples,
+                                     int64_t *nc_sym) {
+  LastStats &ls = last_stats();
+  if (nlev) *nlev = ls.nlev;
+  if (triples) *triples = ls.triples;
+  if (nc_sym) *nc_sym = ls.nc_sym;
+  if (tasks) {
+    if (cap < ls.nlev) return BSM_ERR_BUFFER_TOO_SMALL;
+    for (int l = 0; l < ls.nlev; l++) tasks[l] = ls.tasks[l];
+  }
+  return BSM_OK;
+}
+
+extern "C" bsm_status bsm_multiply_batched(int n, const bsm_matrix *A, const bsm_matrix *B,
+                                           bsm_matrix *C, const bsm_mult_opts *opts,
+                                           void *stream) {
+  if (n < 0 || (n > 0 && (!A || !B || !C))) return BSM_ERR_INVALID_ARG;
+  for (int i = 0; i < n; i++) C[i] = nullptr;
+  for (int i = 0; i < n; i++) BSM_TRY(check_pair(A[i], B[i]));
+  int prec, slices;
+  BSM_TRY(check_opts(opts, &prec, &slices));
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < n; i++) {
+    bsm_status st = multiply_one(A[i], B[i], prec, slices, s, &C[i]);
+    if (st != BSM_OK) {
+      for (int j = 0; j < i; j++) {
+        bsm_destroy(C[j]);
+        C[j] = nullptr;
+      }
+      return st;
+    }
+  }
+  return BSM_OK;
+}

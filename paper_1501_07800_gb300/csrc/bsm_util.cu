@@ -1,0 +1,178 @@
+// Host utilities: stream-ordered allocation, pinned scratch, CUB scans/sorts.
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
+#include <cstdlib>
+#include <mutex>
+
+#include "bsm_internal.cuh"
+
+bsm_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return BSM_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return BSM_ERR_OOM;
+  }
+  return BSM_ERR_CUDA;
+}
+
+static void configure_pool_once(int dev) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  std::lock_guard<std::mutex> g(mu);
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    // keep freed memory in this process's pool instead of returning it to the
+    // driver at every synchronisation
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done[dev] = true;
+}
+
+bsm_status dev_alloc(void **p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  configure_pool_once(dev);
+  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? BSM_ERR_OOM : BSM_ERR_CUDA;
+  }
+  return BSM_OK;
+}
+
+void dev_free(void *p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+void *HostScratch::get(size_t bytes) {
+  if (bytes <= n) return p;
+  if (p) cudaFreeHost(p);
+  p = nullptr;
+  n = 0;
+  size_t want = bytes < 4096 ? 4096 : bytes;
+  if (cudaMallocHost(&p, want) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    return nullptr;
+  }
+  n = want;
+  return p;
+}
+HostScratch::~HostScratch() {
+  // process teardown may have destroyed the context already; ignore errors
+  if (p) cudaFreeHost(p);
+}
+HostScratch &host_scratch() {
+  static thread_local HostScratch h;
+  return h;
+}
+
+LastStats &last_stats() {
+  static thread_local LastStats st;
+  return st;
+}
+
+int64_t &launch_counter() {
+  static thread_local int64_t n = 0;
+  return n;
+}
+
+static thread_local int t_timing = -1;  // -1: follow the environment
+bool timing_enabled() {
+  if (t_timing < 0) {
+    const char *e = getenv("BSM_TIMING");
+    t_timing = (e && e[0] == '1') ? 1 : 0;
+  }
+  return t_timing == 1;
+}
+
+extern "C" bsm_status bsm_set_timing(int on) {
+  if (on != 0 && on != 1) return BSM_ERR_INVALID_ARG;
+  t_timing = on;
+  return BSM_OK;
+}
+
+extern "C" bsm_status bsm_last_phase_ms(double *ms, int cap, int *nphase, int64_t *launches) {
+  LastStats &ls = last_stats();
+  if (nphase) *nphase = 3;
+  if (launches) *launches = ls.launches;
+  if (ms) {
+    if (cap < 3) return BSM_ERR_BUFFER_TOO_SMALL;
+    for (int i = 0; i < 3; i++) ms[i] = ls.phase_ms[i];
+  }
+  return BSM_OK;
+}
+
+struct Int4Sum {
+  __host__ __device__ int4 operator()(const int4 &a, const int4 &b) const {
+    return make_int4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+  }
+};
+
+template <typename F>
+static bsm_status run_cub(F f, cudaStream_t s) {
+  size_t tmp = 0;
+  BSM_CUDA(f(nullptr, tmp));
+  void *t = nullptr;
+  BSM_TRY(dev_alloc(&t, tmp, s));
+  cudaError_t e = f(t, tmp);
+  dev_free(t, s);
+  return cuda_status(e);
+}
+
+bsm_status scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return BSM_OK;
+  count_launch(2);  // scan init + scan
+  return run_cub([&](void *t, size_t &b) {
+    return cub::DeviceScan::ExclusiveSum(t, b, in, out, n, s);
+  }, s);
+}
+
+bsm_status scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return BSM_OK;
+  count_launch(2);
+  return run_cub([&](void *t, size_t &b) {
+    return cub::DeviceScan::ExclusiveSum(t, b, in, out, n, s);
+  }, s);
+}
+
+bsm_status scan_exclusive_int4(const int4 *in, int4 *out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return BSM_OK;
+  count_launch(2);
+  return run_cub([&](void *t, size_t &b) {
+    return cub::DeviceScan::ExclusiveScan(t, b, in, out, Int4Sum(), make_int4(0, 0, 0, 0), n, s);
+  }, s);
+}
+
+bsm_status sort_keys_u64(const uint64_t *kin, uint64_t *kout, const int32_t *vin, int32_t *vout,
+                         int64_t n, int end_bit, cudaStream_t s) {
+  if (n <= 0) return BSM_OK;
+  if (end_bit < 1) end_bit = 1;
+  count_launch(2 + (end_bit + 7) / 8);  // histogram, offsets, one pass per 8-bit digit
+  return run_cub([&](void *t, size_t &b) {
+    return cub::DeviceRadixSort::SortPairs(t, b, kin, kout, vin, vout, n, 0, end_bit, s);
+  }, s);
+}
+
+extern "C" const char *bsm_status_string(bsm_status s) {
+  switch (s) {
+    case BSM_OK: return "ok";
+    case BSM_ERR_INVALID_ARG: return "invalid argument";
+    case BSM_ERR_DIM_MISMATCH: return "dimension mismatch (A.ncols != B.nrows)";
+    case BSM_ERR_BLOCKSIZE: return "unsupported or mismatched block size";
+    case BSM_ERR_OUT_OF_RANGE: return "block coordinate out of range";
+    case BSM_ERR_DUPLICATE: return "duplicate block coordinate";
+    case BSM_ERR_OOM: return "out of device memory";
+    case BSM_ERR_CUDA: return "CUDA runtime error";
+    case BSM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case BSM_ERR_BUFFER_TOO_SMALL: return "output buffer too small";
+    case BSM_ERR_UNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}

@@ -1,0 +1,69 @@
+"""The C ABI library loads and exports every symbol include/bsm.h declares; the
+host-side argument checks run without a GPU (they return before any CUDA call)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "bsm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bsm_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1501_07800_gb300 import build
+    build.build()
+    import paper_1501_07800_gb300 as bsm
+    return bsm.load()
+
+
+def test_header_lists_the_api():
+    names = declared_functions()
+    for n in ["bsm_build", "bsm_multiply", "bsm_multiply_batched", "bsm_to_blocks", "bsm_info",
+              "bsm_destroy", "bsm_status_string", "bsm_level_counts", "bsm_last_stats"]:
+        assert n in names
+
+
+def test_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_header():
+    import paper_1501_07800_gb300 as bsm
+    for name in declared_functions():
+        assert callable(getattr(bsm, name)), name
+
+
+def test_status_strings(lib):
+    import paper_1501_07800_gb300 as bsm
+    for code in bsm.STATUS:
+        assert bsm.bsm_status_string(code) not in ("", "unknown status")
+    assert bsm.bsm_status_string(12345) == "unknown status"
+
+
+def test_argument_checks_before_any_device_work(lib):
+    out = ctypes.c_void_p(1)
+    # unsupported block size
+    assert lib.bsm_build(64, 64, 17, 0, None, None, None, 0, None, ctypes.byref(out)) == -3
+    assert out.value is None
+    # negative sizes / missing buffers / NULL output
+    assert lib.bsm_build(-1, 64, 32, 0, None, None, None, 0, None, ctypes.byref(out)) == -1
+    assert lib.bsm_build(64, 64, 32, 3, None, None, None, 0, None, ctypes.byref(out)) == -1
+    assert lib.bsm_build(64, 64, 32, 0, None, None, None, 0, None, None) == -1
+    assert lib.bsm_build(64, 64, 32, 0, None, None, None, 2, None, ctypes.byref(out)) == -1
+    # NULL handles
+    assert lib.bsm_multiply(None, None, ctypes.byref(out), None, None) == -1
+    assert lib.bsm_multiply(None, None, None, None, None) == -1
+    assert lib.bsm_multiply_batched(-1, None, None, None, None, None) == -1
+    assert lib.bsm_multiply_batched(0, None, None, None, None, None) == 0
+    n = ctypes.c_int64(0)
+    assert lib.bsm_to_blocks(None, ctypes.byref(n), None, None, None, 0, None) == -1
+    assert lib.bsm_info(None, None, None, None, None) == -1
+    assert lib.bsm_destroy(None) == 0
