@@ -355,7 +355,14 @@ def main():
     ap.add_argument("--mode", default="fp64", choices=["fp64", "split"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="matrix side (profiling runs only)")
+    ap.add_argument("--p", type=float, default=None, help="block density (profiling runs only)")
     args = ap.parse_args()
+    if args.n is not None or args.p is not None:
+        WORKLOAD["n"] = args.n or WORKLOAD["n"]
+        WORKLOAD["p"] = args.p or WORKLOAD["p"]
+        WORKLOAD["workload"] = (f"random block-sparse N={WORKLOAD['n']}, bs=32, block density "
+                                f"{WORKLOAD['p']}, N(0,1) (reduced profiling case)")
     if args.warmup < 3:
         log("warm-up raised to 3 steps")
         args.warmup = 3

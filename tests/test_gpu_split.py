@@ -1,0 +1,143 @@
+"""GPU parity of the split-precision mode (BF16 slices on tcgen05) vs the oracle.
+
+Structure must match the oracle exactly.  Values: small-integer inputs are
+represented exactly by one slice, so every digit product and every
+accumulation is exact and the result equals the FP64 oracle bit for bit, for
+any slice count.  For real-valued inputs the error bound is set by the 7s-bit
+fixed point of each operand row/column: with the default s = 7 (49 bits) the
+relative Frobenius error stays far below the 1e-11 target, and it must shrink
+as s grows.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1501_07800_gb300 as bsm
+import synth
+from helpers import assert_same_structure, from_bsm, relerr, to_bsm
+
+pytestmark = pytest.mark.gpu
+TOL_SPLIT = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    torch.cuda.init()
+    bsm.load()
+
+
+def split_product(A, B, slices=0):
+    return from_bsm(bsm.bsm_multiply(to_bsm(A), to_bsm(B), prec=bsm.BSM_SPLIT_BF16,
+                                     slices=slices))
+
+
+@pytest.mark.parametrize("bs", [32, 16])
+def test_single_block_integers_exact(bs):
+    A = synth.random_blocks(bs, bs, 1.0, 1, dist="int8")
+    B = synth.random_blocks(bs, bs, 1.0, 2, dist="int8")
+    C = split_product(A, B, slices=1)
+    E = oracle.multiply(A, B).C
+    assert_same_structure(C, E)
+    assert np.array_equal(C.vals, E.vals)
+
+
+@pytest.mark.parametrize("bs", [16, 32])
+@pytest.mark.parametrize("slices", [1, 3, 7])
+def test_integers_exact_any_slice_count(bs, slices):
+    A = synth.random_blocks(40 * bs + 5, bs, 0.3, 3, dist="int8")
+    B = synth.random_blocks(40 * bs + 5, bs, 0.3, 4, dist="int8")
+    C = split_product(A, B, slices=slices)
+    E = oracle.multiply(A, B).C
+    assert_same_structure(C, E)
+    assert np.array_equal(C.vals, E.vals)
+
+
+def test_integer_cancellation_removed():
+    bs = 32
+    x = synth.random_blocks(2 * bs, bs, 1.0, 61, dist="int8").to_dense()
+    y = synth.random_blocks(2 * bs, bs, 1.0, 62, dist="int8").to_dense()
+    z = synth.random_blocks(2 * bs, bs, 1.0, 63, dist="int8").to_dense()
+    a = np.block([[x, x], [z, np.zeros_like(z)]])
+    b = np.vstack([y, -y])
+    A, B = synth.from_dense(a, bs), synth.from_dense(b, bs)
+    C = split_product(A, B)
+    E = oracle.multiply(A, B).C
+    assert_same_structure(C, E)
+    assert np.array_equal(C.vals, E.vals)
+
+
+@pytest.mark.parametrize("bs", [16, 32])
+def test_random_normal_default_slices(bs):
+    A = synth.random_blocks(2048, bs, 0.05, 100 + bs)
+    B = synth.random_blocks(2048, bs, 0.05, 200 + bs)
+    C = split_product(A, B)
+    E = oracle.multiply(A, B).C
+    assert_same_structure(C, E)
+    assert relerr(C.vals, E.vals) < TOL_SPLIT
+
+
+def test_error_decreases_with_slices():
+    A = synth.random_blocks(1024, 32, 0.1, 7)
+    B = synth.random_blocks(1024, 32, 0.1, 8)
+    E = oracle.multiply(A, B).C
+    errs = []
+    for s in range(2, 8):
+        C = split_product(A, B, slices=s)
+        assert_same_structure(C, E)
+        errs.append(relerr(C.vals, E.vals))
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < TOL_SPLIT
+
+
+def test_banded_4096_split():
+    A = synth.banded(4096, 64, 32, synth.BASE_SEED)
+    B = synth.banded(4096, 64, 32, synth.BASE_SEED + 100)
+    C = split_product(A, B)
+    E = oracle.multiply(A, B).C
+    assert_same_structure(C, E)
+    assert C.nblk == 1132
+    assert relerr(C.vals, E.vals) < TOL_SPLIT
+
+
+def test_long_k_lists_split():
+    """Hundreds of products per C block: many exact-accumulation flushes."""
+    A = synth.random_blocks(256, 32, 1.0, 34, ncols=32 * 200)
+    B = synth.random_blocks(32 * 200, 32, 1.0, 35, ncols=256)
+    C = split_product(A, B)
+    E = oracle.multiply(A, B).C
+    assert_same_structure(C, E)
+    assert relerr(C.vals, E.vals) < TOL_SPLIT
+
+
+def test_decay_square_split():
+    A = synth.decay(300, 16, 33)
+    C = split_product(A, A)
+    E = oracle.multiply(A, A).C
+    assert_same_structure(C, E)
+    assert relerr(C.vals, E.vals) < TOL_SPLIT
+
+
+def test_rectangular_ragged_split():
+    A = synth.random_blocks(1000, 32, 0.15, 31, ncols=777)
+    B = synth.random_blocks(777, 32, 0.15, 32, ncols=1234)
+    C = split_product(A, B)
+    E = oracle.multiply(A, B).C
+    assert_same_structure(C, E)
+    assert relerr(C.vals, E.vals) < TOL_SPLIT
+
+
+def test_split_is_deterministic():
+    A = synth.random_blocks(1500, 32, 0.1, 41)
+    B = synth.random_blocks(1500, 32, 0.1, 42)
+    C1 = split_product(A, B)
+    C2 = split_product(A, B)
+    assert np.array_equal(C1.vals, C2.vals)
+
+
+def test_split_rejects_bs64():
+    A = to_bsm(synth.random_blocks(128, 64, 1.0, 5))
+    with pytest.raises(bsm.BsmError) as e:
+        bsm.bsm_multiply(A, A, prec=bsm.BSM_SPLIT_BF16)
+    assert e.value.name == "BSM_ERR_UNSUPPORTED"
