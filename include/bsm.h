@@ -183,6 +183,47 @@ bsm_status bsm_set_timing(int on);
  */
 bsm_status bsm_last_phase_ms(double *ms, int cap, int *nphase, int64_t *launches);
 
+/*
+ * bsm_block_products_fp64_noalloc -- the FP64 numeric phase for a task list the
+ * caller supplies, allocating nothing.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory on
+ * their own path -- e.g. a process whose device memory is reserved in full by
+ * another allocator (so any cudaMalloc fails), or a latency-critical loop that
+ * cannot afford an allocation's implicit synchronisation.  It issues no
+ * cudaMalloc, cudaMallocAsync, cudaMallocHost, cudaFree or allocating library
+ * call; the caller passes every input and output.
+ *
+ *   bs            16, 32 or 64
+ *   nc            number of C blocks, 0 <= nc <= BSM_NOALLOC_MAX_CBLOCKS
+ *   seg           device int32[nc+1]: C block c is the sum of products
+ *                 seg[c] .. seg[c+1]-1 (non-decreasing, seg[0] >= 0)
+ *   ta, tb        device int32[seg[nc]]: A and B block index of each product
+ *   a_vals, na    device float64[na][bs][bs], row-major blocks of A
+ *   b_vals, nb    device float64[nb][bs][bs], row-major blocks of B
+ *   c_vals        device float64[nc][bs][bs], output: C block c = sum over its
+ *                 products of A[ta] * B[tb], summed in list order
+ *   nnz_out       device int64, output: number of C blocks with an entry
+ *                 != 0.0, or -1 if an index was out of range or a bounded
+ *                 device wait gave up (then c_vals is undefined)
+ *   stream        cudaStream_t or NULL; the call is asynchronous on it
+ *
+ * Scratch: a static device array of BSM_NOALLOC_MAX_CBLOCKS + 64 int32 (about
+ * 4 MiB) compiled into the library; every GPU that loads the library holds it
+ * until the process exits.  The first call on a device looks up its address
+ * with that device current; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents, so calls
+ * whose work overlaps on the GPU race on it: serialise them (one stream, or
+ * events between streams).
+ * Errors: BLOCKSIZE, INVALID_ARG, UNSUPPORTED (nc above the maximum, or a
+ * device ordinal >= 64), CUDA.
+ */
+#define BSM_NOALLOC_MAX_CBLOCKS (1 << 20)
+bsm_status bsm_block_products_fp64_noalloc(int bs, int64_t nc, const int32_t *seg,
+                                           const int32_t *ta, const int32_t *tb,
+                                           const double *a_vals, int64_t na, const double *b_vals,
+                                           int64_t nb, double *c_vals, int64_t *nnz_out,
+                                           void *stream);
+
 /* bsm_destroy -- free a handle (NULL is accepted).  Work queued on other
  * streams that still reads the handle must be complete. */
 bsm_status bsm_destroy(bsm_matrix M);

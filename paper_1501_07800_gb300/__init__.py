@@ -37,6 +37,8 @@ _PROTOS = {
     "bsm_last_stats": (_I32, [_P, _I32, _P, _P, _P]),
     "bsm_set_timing": (_I32, [_I32]),
     "bsm_last_phase_ms": (_I32, [_P, _I32, _P, _P]),
+    "bsm_block_products_fp64_noalloc": (_I32, [_I32, _I64, _P, _P, _P, _P, _I64, _P, _I64, _P,
+                                                _P, _P]),
     "bsm_destroy": (_I32, [_P]),
     "bsm_status_string": (ctypes.c_char_p, [_I32]),
 }
@@ -254,6 +256,21 @@ def bsm_last_phase_ms():
     _check(load().bsm_last_phase_ms(ms.ctypes.data, 3, ctypes.byref(n), ctypes.byref(launches)),
            "bsm_last_phase_ms")
     return ms, launches.value
+
+
+BSM_NOALLOC_MAX_CBLOCKS = 1 << 20
+
+
+def bsm_block_products_fp64_noalloc(bs: int, seg, ta, tb, a_vals, b_vals, c_vals, nnz_out,
+                                    stream=None):
+    """FP64 block products of a caller-supplied task list into caller buffers,
+    with no allocation (all arguments are torch CUDA tensors; see bsm.h)."""
+    nc = int(seg.numel()) - 1
+    code = load().bsm_block_products_fp64_noalloc(
+        bs, nc, seg.data_ptr(), ta.data_ptr(), tb.data_ptr(), a_vals.data_ptr(),
+        int(a_vals.shape[0]), b_vals.data_ptr(), int(b_vals.shape[0]), c_vals.data_ptr(),
+        nnz_out.data_ptr(), _stream_ptr(stream))
+    _check(code, "bsm_block_products_fp64_noalloc")
 
 
 def bsm_destroy(M: Matrix):
