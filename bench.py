@@ -275,6 +275,9 @@ def run_gpu(args):
     fp64_peak = peaks["bf16_tflops"] * FP64_NOMINAL_RATIO
     t_num = statistics.mean(numeric_ms) / 1e3
     achieved = flops / t_num / 1e12
+    if prec != bsm.BSM_FP64:  # split mode: BF16 digit-pair flops against the bf16 peak
+        achieved = flops * 28 / t_num / 1e12
+        fp64_peak = peaks["bf16_tflops_sustained"]
     roofline = {"bound": "tensor", "kernel": "k_numeric_fp64 (DMMA f64)",
                 "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp64_peak,
@@ -282,6 +285,11 @@ def run_gpu(args):
                                f"FP64/bf16 ratio 1.25/2250",
                 "traffic": recorded_traffic("k_numeric_fp64",
                                             "paper_1501_07800_gb300/csrc/bsm_numeric_fp64.cu")}
+
+    # split-precision mode on the same inputs, same timing protocol
+    split = None
+    if not args.no_split and args.mode == "fp64":
+        split = run_split(bsm, torch, ga, gb, args, stream, flops, triples, A, B, rank)
 
     line = None
     if rank == 0:
@@ -293,6 +301,8 @@ def run_gpu(args):
                 "triples": triples, "c_blocks": nblk_c, "c_blocks_symbolic": nc_sym,
                 "phase_ms_last": [float(x) for x in bsm.bsm_last_phase_ms()[0]],
                 "roofline": roofline, "gpu_launches": launches, "clocks": clk}
+        if split is not None:
+            line["split_bf16"] = split
 
     # end to end through the public API with host buffers (pinned)
     if not args.no_e2e:
@@ -310,6 +320,64 @@ def run_gpu(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def run_split(bsm, torch, ga, gb, args, stream, flops, triples, A, B, rank, slices=7):
+    """Split-precision products: time, roofline of the split kernel, and relative
+    Frobenius error against the FP64 product (all C blocks) and against the
+    oracle's definition on sampled C blocks."""
+    prec = bsm.BSM_SPLIT_BF16
+    for _ in range(args.warmup):
+        C = bsm.bsm_multiply(ga, gb, prec=prec, slices=slices)
+        del C
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    num_ms = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        C = bsm.bsm_multiply(ga, gb, prec=prec, slices=slices)
+        ev[i][1].record(stream)
+        num_ms.append(bsm.bsm_last_phase_ms()[0][1])
+        if i < args.steps - 1:
+            del C
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    # errors
+    r1, c1, v1 = bsm.bsm_to_blocks(C, device=True)
+    Cd = bsm.bsm_multiply(ga, gb)
+    r2, c2, v2 = bsm.bsm_to_blocks(Cd, device=True)
+    same = bool(torch.equal(r1, r2) and torch.equal(c1, c2))
+    err_fp64 = float(torch.linalg.vector_norm(v1 - v2) / torch.linalg.vector_norm(v2)) if same else None
+    err_oracle = None
+    if rank == 0:
+        import oracle
+        L = oracle.common_depth(A, B)
+        ta, tb = oracle.tree(A, L), oracle.tree(B, L)
+        rng = np.random.default_rng(synth.BASE_SEED)
+        pick = rng.choice(int(r1.shape[0]), size=min(200, int(r1.shape[0])), replace=False)
+        rr, cc = r1[pick].cpu().numpy(), c1[pick].cpu().numpy()
+        got = v1[torch.from_numpy(pick).to(v1.device)].cpu().numpy()
+        ref = np.stack([oracle.block_product(ta, tb, i, j)[1] for i, j in zip(rr, cc)])
+        err_oracle = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    del C, Cd
+    t_num = statistics.mean(num_ms) / 1e3
+    peaks, which = measured_peaks()
+    pair_flops = flops * slices * (slices + 1) / 2  # BF16 digit-pair products needed
+    achieved = pair_flops / t_num / 1e12
+    return {"value": flops / (sum(step_ms) / len(step_ms) / 1e3) / 1e9, "unit": "GFLOP/s",
+            "ms_per_step": statistics.mean(step_ms), "slices": slices,
+            "rel_err_vs_fp64": err_fp64, "rel_err_vs_oracle_200_blocks": err_oracle,
+            "numeric_ms": 1e3 * t_num,
+            "roofline": {"bound": "tensor", "kernel": "k_numeric_split (tcgen05 kind::f16)",
+                         "achieved": achieved, "peak": peaks["bf16_tflops_sustained"],
+                         "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops_sustained"],
+                         "work": "BF16 digit-pair flops: s(s+1)/2 x 2 bs^3 per block product",
+                         "peak_source": f"{which} bf16 sustained"},
+            "clocks": clk}
 
 
 def run_e2e(bsm, torch, A, B, prec, steps):
@@ -355,6 +423,7 @@ def main():
     ap.add_argument("--mode", default="fp64", choices=["fp64", "split"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="matrix side (profiling runs only)")
     ap.add_argument("--p", type=float, default=None, help="block density (profiling runs only)")
     args = ap.parse_args()

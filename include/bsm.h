@@ -83,13 +83,15 @@ typedef struct {
  *                 0 <= bcol < ceil(ncols/bs); any order; duplicates rejected
  *   vals          float64[nblk][bs][bs], block t row-major at vals + t*bs*bs
  *   on_device     0: the three arrays are host memory (copied in this call);
- *                 1: they are device memory of the current device
+ *                 1: they are device memory of the current device (vals
+ *                 16-byte aligned, brow/bcol 4-byte aligned)
  *   stream        cudaStream_t or NULL
  *   out           receives the new handle (NULL on error)
  *
  * Exactly-zero blocks are dropped.  The library copies the inputs; the caller
  * may reuse its buffers when the call returns.
- * Errors: INVALID_ARG, BLOCKSIZE, OUT_OF_RANGE, DUPLICATE, OOM, CUDA.
+ * Errors: INVALID_ARG (also: misaligned device arrays), BLOCKSIZE,
+ * OUT_OF_RANGE, DUPLICATE, OOM, CUDA.
  */
 bsm_status bsm_build(int64_t nrows, int64_t ncols, int bs, int64_t nblk, const int32_t *brow,
                      const int32_t *bcol, const double *vals, int on_device, void *stream,
@@ -134,7 +136,8 @@ bsm_status bsm_multiply_batched(int n, const bsm_matrix *A, const bsm_matrix *B,
  *   brow, bcol  int32[capacity] or NULL
  *   vals        float64[capacity][bs][bs] or NULL
  *   on_device   0: host buffers (the call synchronises `stream`);
- *               1: device buffers of the handle's device
+ *               1: device buffers of the handle's device (vals 16-byte
+ *               aligned, brow/bcol 4-byte aligned)
  * With all three buffers NULL the call only reports the block count.
  * Errors: INVALID_ARG, BUFFER_TOO_SMALL (count still reported), OOM, CUDA.
  */
@@ -200,6 +203,7 @@ bsm_status bsm_last_phase_ms(double *ms, int cap, int *nphase, int64_t *launches
  *   ta, tb        device int32[seg[nc]]: A and B block index of each product
  *   a_vals, na    device float64[na][bs][bs], row-major blocks of A
  *   b_vals, nb    device float64[nb][bs][bs], row-major blocks of B
+ *                 (a_vals, b_vals and c_vals 16-byte aligned)
  *   c_vals        device float64[nc][bs][bs], output: C block c = sum over its
  *                 products of A[ta] * B[tb], summed in list order
  *   nnz_out       device int64, output: number of C blocks with an entry

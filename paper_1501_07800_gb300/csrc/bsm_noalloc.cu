@@ -205,6 +205,8 @@ extern "C" bsm_status bsm_block_products_fp64_noalloc(int bs, int64_t nc, const 
   if (nc < 0 || na < 0 || nb < 0 || !nnz_out) return BSM_ERR_INVALID_ARG;
   if (nc > BSM_NOALLOC_MAX_CBLOCKS) return BSM_ERR_UNSUPPORTED;  // beyond the scratch array
   if (nc > 0 && (!seg || !ta || !tb || !a_vals || !b_vals || !c_vals)) return BSM_ERR_INVALID_ARG;
+  // blocks are staged by bulk copies and stored with 16-byte vector stores
+  if (((uintptr_t)a_vals | (uintptr_t)b_vals | (uintptr_t)c_vals) & 15) return BSM_ERR_INVALID_ARG;
   int32_t *scratch = nullptr;
   int dev = 0;
   BSM_TRY(scratch_for_current_device(&scratch, &dev));

@@ -30,15 +30,21 @@
 // (g*128/bs + L - t) because consecutive lane blocks are one slice apart.
 // D_d then lands in TMEM lane block L of group g's accumulator.
 //
-// Roles (192 threads, one CTA per SM, persistent over C blocks):
-//   warp 4 lane 0: producer -- 1-D bulk copies of the A and B slices of each
-//                  k-product into a ring of stages (mbarrier complete_tx);
-//   warp 5 lane 0: issues the MMAs of each k-product, commits the stage back
+// Roles (576 threads, one CTA per SM, persistent over C blocks):
+//   warp 16:       producer -- all lanes prefetch work descriptors and block
+//                  indices; lane 0 issues the 1-D bulk copies of the A and B
+//                  slices of each k-product into a ring of stages (mbarrier
+//                  complete_tx) and hands per-C-block descriptors to the other
+//                  roles through a shared-memory ring;
+//   warp 17 lane 0: issues the MMAs of each k-product, commits the stage back
 //                  to the producer and each finished flush to the epilogue;
-//   warps 0-3:     epilogue -- drain TMEM (double-buffered) into integer
-//                  accumulators, combine and round, store C, raise the
-//                  nonzero flag.
+//   warps 0-15:    epilogue, two teams of eight warps taking alternate C
+//                  blocks, each with its own TMEM accumulator buffer -- drain
+//                  TMEM (two warps per lane quadrant) into exact integer
+//                  diagonal sums in shared memory, combine and round, store
+//                  C, raise the nonzero flag.
 #include <climits>
+#include <cstddef>
 
 #include "bsm_ptx.cuh"
 
@@ -49,18 +55,23 @@ constexpr int kMaxSlices = 8;  // 56-bit fixed point at most
 constexpr uint32_t kMagic = 0x4B400000u;  // bits of 1.5 * 2^23
 constexpr float kMagicF = 12582912.0f;
 
-template <int BS>
+template <int BS, int S>
 struct Cfg {
   static constexpr int DPG = 128 / BS;                       // diagonals per group
+  static constexpr int G = (S + DPG - 1) / DPG;              // diagonal groups
   static constexpr int SLICE = BS * BS * 2;                  // bytes of one BF16 slice
-  static constexpr int GMAX = (kMaxSlices + DPG - 1) / DPG;  // groups at most
-  static constexpr int ASLOTS = (DPG - 1) + GMAX * DPG;      // zero pad + slices + pad
-  static constexpr int BSLOTS = kMaxSlices;
+  static constexpr int ASLOTS = (DPG - 1) + G * DPG;         // zero pad + slices + pad
+  static constexpr int BSLOTS = S;
   static constexpr int STAGE = (ASLOTS + BSLOTS) * SLICE;
-  static constexpr int NST = BS == 32 ? 4 : 8;               // ring depth
   static constexpr int CROW = BS + 4;                        // padded int32 row (combine)
-  static constexpr int COMB = kMaxSlices * BS * CROW * 4;    // combine buffer bytes
-  static constexpr int SMEM = NST * STAGE + COMB + 1024;
+  static constexpr int COMB = S * BS * CROW * 4;             // combine buffer bytes (per team)
+  // ring depth: up to 4 (bs 32) / 8 (bs 16) stages within 227 KiB of shared
+  // memory, 8 KiB of it left for the static barriers and descriptor ring
+  static constexpr int BUDGET = 227 * 1024 - 8 * 1024 - 2 * COMB;
+  static constexpr int NSTMAX = BS == 32 ? 4 : 8;
+  static constexpr int NST = BUDGET / STAGE < NSTMAX ? BUDGET / STAGE : NSTMAX;
+  static constexpr int SMEM = NST * STAGE + 2 * COMB;
+  static_assert(NST >= 2, "shared memory too small for two stages");
   static constexpr uint32_t SBO = BS * 16;                   // 8-row group stride
   static constexpr uint32_t LBO = 128;                       // K core-matrix stride
 };
@@ -109,8 +120,9 @@ __global__ void k_col_exp(const double *__restrict__ vals, const uint64_t *__res
   if (m != INT_MIN) atomicMax(colexp + J * bs + c, m);
 }
 
-// Balanced base-2^7 digits of round(x * 2^(7s - E)), most significant first.
-__device__ __forceinline__ void digits(double x, int E, int s, int (&d)[kMaxSlices]) {
+// Balanced base-2^7 digits of round(x * 2^(7S - E)), most significant first.
+template <int S>
+__device__ __forceinline__ void digits(double x, int E, int (&d)[S]) {
   uint64_t b = (uint64_t)__double_as_longlong(x);
   int e = (int)((b >> 52) & 0x7FF);
   uint64_t m = b & ((1ull << 52) - 1);
@@ -119,10 +131,10 @@ __device__ __forceinline__ void digits(double x, int E, int s, int (&d)[kMaxSlic
   else
     m |= 1ull << 52;
   int64_t X = 0;
-  if (m != 0 && E != INT_MIN) {
-    int sh = e - 1075 - E + kBeta * s;  // x = m 2^(e-1075), |x| < 2^E
+  if (m != 0) {
+    int sh = e - 1075 - E + kBeta * S;  // x = m 2^(e-1075), |x| < 2^E
     if (sh >= 0) {
-      X = (int64_t)(m << sh);  // < 2^(7s) <= 2^56
+      X = (int64_t)(m << sh);  // < 2^(7S) <= 2^56
     } else if (sh > -64) {
       uint64_t q = m >> (-sh);
       uint64_t half = (m >> (-sh - 1)) & 1ull;  // round half away from zero
@@ -130,7 +142,8 @@ __device__ __forceinline__ void digits(double x, int E, int s, int (&d)[kMaxSlic
     }
     if (b >> 63) X = -X;
   }
-  for (int i = s - 1; i >= 1; i--) {
+#pragma unroll
+  for (int i = S - 1; i >= 1; i--) {
     int64_t dig = ((X + (1 << (kBeta - 1))) & ((1 << kBeta) - 1)) - (1 << (kBeta - 1));
     d[i] = (int)dig;
     X = (X - dig) >> kBeta;
@@ -138,44 +151,83 @@ __device__ __forceinline__ void digits(double x, int E, int s, int (&d)[kMaxSlic
   d[0] = (int)X;
 }
 
-__device__ __forceinline__ uint16_t small_int_to_bf16(int v) {
+__device__ __forceinline__ uint32_t small_int_to_bf16(int v) {
   // |v| <= 128: the float is exact (magic-number conversion, |v| < 2^22) and
   // has at most 8 significant bits, so its upper 16 bits are the BF16 value
   float f = __int_as_float((int)kMagic + v) - kMagicF;
-  return (uint16_t)(__float_as_uint(f) >> 16);
+  return __float_as_uint(f) >> 16;
 }
 
-// Writes the s slices of every block in the MMA operand layout (K-major,
+// Writes the S slices of every block in the MMA operand layout (K-major,
 // 8x8 BF16 core matrices of 128 bytes, K core matrices 128 B apart, 8-row
 // groups BS*16 B apart).  TRANS = 0: A block, operand rows = block rows,
 // K = block columns, row scales.  TRANS = 1: B block, operand rows = block
-// columns, K = block rows, column scales.
-template <int BS, int TRANS>
-__global__ void k_slice(const double *__restrict__ vals, const uint64_t *__restrict__ keys,
-                        int64_t n, const int *__restrict__ exps, int s,
-                        uint16_t *__restrict__ out) {
-  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= n * BS * BS) return;
-  int64_t t = g / (BS * BS);
-  int e = (int)(g % (BS * BS));
-  int r = e / BS, c = e % BS;  // block row, block column
-  double x = vals[g];
-  int mrow, kcol;
-  int E;
-  if (TRANS == 0) {
-    mrow = r;
-    kcol = c;
-    E = exps[(int64_t)morton_compact(keys[t] >> 1) * BS + r];
-  } else {
-    mrow = c;
-    kcol = r;
-    E = exps[(int64_t)morton_compact(keys[t]) * BS + c];
+// columns, K = block rows, column scales.  A CTA stages one block in shared
+// memory; each thread makes one 8-element core-matrix row (16 bytes per slice)
+// so that a warp writes 512 contiguous bytes per slice.
+template <int BS, int S, int TRANS>
+__global__ void __launch_bounds__(128) k_slice(const double *__restrict__ vals,
+                                               const uint64_t *__restrict__ keys, int64_t n,
+                                               const int *__restrict__ exps,
+                                               uint16_t *__restrict__ out) {
+  __shared__ double blk[BS * (BS + 1)];
+  constexpr int KG = BS / 8;
+  for (int64_t t = blockIdx.x; t < n; t += gridDim.x) {
+    const double *src = vals + t * (int64_t)BS * BS;
+    for (int e = threadIdx.x; e < BS * BS; e += blockDim.x)
+      blk[(e / BS) * (BS + 1) + e % BS] = src[e];
+    __syncthreads();
+    const uint64_t key = keys[t];
+    const int64_t rc = TRANS == 0 ? (int64_t)morton_compact(key >> 1) : (int64_t)morton_compact(key);
+    for (int task = threadIdx.x; task < BS * KG; task += blockDim.x) {
+      const int kg = task % KG, mrow = task / KG;
+      const int E = exps[rc * BS + mrow];
+      uint32_t w[S][4];
+#pragma unroll
+      for (int x = 0; x < 8; x += 2) {
+        const int k0 = kg * 8 + x;
+        double v0 = TRANS == 0 ? blk[mrow * (BS + 1) + k0] : blk[k0 * (BS + 1) + mrow];
+        double v1 = TRANS == 0 ? blk[mrow * (BS + 1) + k0 + 1] : blk[(k0 + 1) * (BS + 1) + mrow];
+        int d0[S], d1[S];
+        digits<S>(v0, E, d0);
+        digits<S>(v1, E, d1);
+#pragma unroll
+        for (int i = 0; i < S; i++)
+          w[i][x / 2] = small_int_to_bf16(d0[i]) | (small_int_to_bf16(d1[i]) << 16);
+      }
+      const uint32_t off = (mrow >> 3) * (BS * 16) + kg * 128 + (mrow & 7) * 16;  // bytes
+      uint8_t *base = reinterpret_cast<uint8_t *>(out + t * (int64_t)S * BS * BS);
+#pragma unroll
+      for (int i = 0; i < S; i++)
+        *reinterpret_cast<uint4 *>(base + (size_t)i * BS * BS * 2 + off) =
+            make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+    }
+    __syncthreads();
   }
-  int d[kMaxSlices];
-  digits(x, E, s, d);
-  uint32_t off = (mrow >> 3) * (BS * 16) + (kcol >> 3) * 128 + (mrow & 7) * 16 + (kcol & 7) * 2;
-  uint16_t *base = out + t * (int64_t)s * BS * BS;
-  for (int i = 0; i < s; i++) base[(int64_t)i * BS * BS + off / 2] = small_int_to_bf16(d[i]);
+}
+
+template <int BS, int S>
+void launch_slices(bsm_matrix A, bsm_matrix B, const int *rowexp, const int *colexp,
+                   uint16_t *asl, uint16_t *bsl, cudaStream_t s) {
+  auto grid = [](int64_t n) { return (unsigned)(n < 152 * 16 ? n : 152 * 16); };
+  count_launch(2);
+  if (A->nblk) k_slice<BS, S, 0><<<grid(A->nblk), 128, 0, s>>>(A->vals, A->keys, A->nblk, rowexp, asl);
+  if (B->nblk) k_slice<BS, S, 1><<<grid(B->nblk), 128, 0, s>>>(B->vals, B->keys, B->nblk, colexp, bsl);
+}
+
+template <int BS>
+void launch_slices_s(bsm_matrix A, bsm_matrix B, const int *rowexp, const int *colexp,
+                     uint16_t *asl, uint16_t *bsl, int slices, cudaStream_t s) {
+  switch (slices) {
+    case 1: launch_slices<BS, 1>(A, B, rowexp, colexp, asl, bsl, s); break;
+    case 2: launch_slices<BS, 2>(A, B, rowexp, colexp, asl, bsl, s); break;
+    case 3: launch_slices<BS, 3>(A, B, rowexp, colexp, asl, bsl, s); break;
+    case 4: launch_slices<BS, 4>(A, B, rowexp, colexp, asl, bsl, s); break;
+    case 5: launch_slices<BS, 5>(A, B, rowexp, colexp, asl, bsl, s); break;
+    case 6: launch_slices<BS, 6>(A, B, rowexp, colexp, asl, bsl, s); break;
+    case 7: launch_slices<BS, 7>(A, B, rowexp, colexp, asl, bsl, s); break;
+    default: launch_slices<BS, 8>(A, B, rowexp, colexp, asl, bsl, s); break;
+  }
 }
 
 __global__ void k_max_seg(const int32_t *__restrict__ seg, int64_t nc, int *__restrict__ out) {
@@ -224,34 +276,103 @@ __device__ __forceinline__ double fixed_to_double(__int128 v, int X) {
 struct SplitArgs {
   const int32_t *seg, *ta, *tb;
   const uint64_t *ckeys;
-  int64_t nc, na, nb;
+  int64_t nc, nt, na, nb;  // C blocks, block products, A / B blocks
   const uint16_t *asl, *bsl;
   const int *rowexp, *colexp;
-  int s, flushk;
+  int flushk;
   double *cv;
   int32_t *nz;
   unsigned *err;
+  unsigned long long *work;  // chunk counter, zero at launch
 };
+constexpr int kChunk = 32;   // C blocks claimed per atomic
 
-template <int BS, int G>
-__global__ void __launch_bounds__(192, 1) k_numeric_split(SplitArgs P) {
-  using C = Cfg<BS>;
+// Per-C-block work descriptor handed from the producer warp to the MMA thread
+// and the epilogue through a shared-memory ring.
+// The exponent arrays are read with 16-byte vector loads: keep them first in
+// a 16-byte aligned struct whose size is a multiple of 16.
+struct __align__(16) Meta {
+  int32_t erow[64];  // row scale exponents of the C block (A rows)
+  int32_t ecol[64];  // column scale exponents (B columns)
+  int64_t c;
+  uint64_t key;
+  int32_t nk;
+  int32_t pad[3];
+};
+static_assert(offsetof(Meta, ecol) % 16 == 0 && sizeof(Meta) % 16 == 0, "Meta alignment");
+constexpr int kMeta = 8;
+
+// sum_d acc_d 2^(7(S-1-d)) for 32-bit acc_d, returned as hi * 2^35 + lo: the
+// terms with shift < 35 are summed in lo (< 2^59.1), the rest in hi.
+template <int S>
+__device__ __forceinline__ void combine_digits(const int32_t (&a)[S], int64_t &hi, int64_t &lo) {
+  lo = 0;
+  hi = 0;
+#pragma unroll
+  for (int d = 0; d < S; d++) {
+    constexpr int T = 35;
+    const int sh = kBeta * (S - 1 - d);
+    if (sh < T)
+      lo += (int64_t)a[d] << sh;
+    else
+      hi += (int64_t)a[d] << (sh - T);
+  }
+}
+
+// Correctly rounded (hi 2^35 + lo) 2^X as FP64; 64-bit path (branch-free
+// rounding) when the value fits in an int64, 128-bit path otherwise.
+__device__ __forceinline__ double split_to_double(int64_t hi, int64_t lo, int X) {
+  if (hi > -(1ll << 27) && hi < (1ll << 27)) {
+    const int64_t v = (int64_t)((uint64_t)hi << 35) + lo;  // |v| < 2^62 + 2^59.1
+    if (v == 0) return 0.0;
+    const uint64_t sign = (uint64_t)v & (1ull << 63);
+    const uint64_t u = v < 0 ? (uint64_t)(-v) : (uint64_t)v;
+    int top = 63 - __clzll((long long)u);
+    const int sh = max(top - 52, 0);
+    uint64_t mant = (u << max(52 - top, 0)) >> sh;
+    const uint64_t rem = sh ? (u & ((1ull << sh) - 1)) : 0, half = sh ? (1ull << (sh - 1)) : 1;
+    mant += (uint64_t)((rem > half) | ((rem == half) & (mant & 1ull)));
+    const int carry = (int)(mant >> 53);  // rounding overflowed to 2^53
+    mant >>= carry;
+    top += carry;
+    const int be = top + X + 1023;
+    if (be >= 1 && be <= 2046)
+      return __longlong_as_double(
+          (long long)(sign | ((uint64_t)be << 52) | (mant & ((1ull << 52) - 1))));
+    const double r = scalbn((double)mant, top - 52 + X);
+    return sign ? -r : r;
+  }
+  return fixed_to_double(((__int128)hi << 35) + (__int128)lo, X);
+}
+
+constexpr int kTeamWarps = 8;                // warps per epilogue team (2 per lane quadrant)
+constexpr int kTeam = kTeamWarps * 32;       // threads per epilogue team
+constexpr int kEpiWarps = 2 * kTeamWarps;    // two teams
+constexpr int kProdWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
+constexpr int kThreads = (kEpiWarps + 2) * 32;
+
+template <int BS, int S>
+__global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
+  using C = Cfg<BS, S>;
   constexpr int DPG = C::DPG;
+  constexpr int G = C::G;
   constexpr uint32_t IDESC = idesc_bf16_f32(128, BS);
-  constexpr int NCOLS = 2 * G * BS < 32 ? 32 : (2 * G * BS <= 64 ? 64 : (2 * G * BS <= 128 ? 128 : 256));
+  constexpr int NCOLS = 2 * G * BS <= 32 ? 32 : (2 * G * BS <= 64 ? 64 : (2 * G * BS <= 128 ? 128 : 256));
+  constexpr uint32_t BYTES = (uint32_t)S * C::SLICE;  // one operand's slices
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[C::NST], empty[C::NST], tfull[2], tempty[2], done;
+  __shared__ __align__(8) uint64_t meta_full[kMeta], meta_empty[kMeta];
+  __shared__ Meta meta[kMeta];
   __shared__ uint32_t tmem_base_sh;
-  __shared__ int warp_any[4];
+  __shared__ int warp_any[2][kTeamWarps];
   __shared__ volatile int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int s = P.s;
   uint8_t *stages = smem;
   int32_t *comb = reinterpret_cast<int32_t *>(smem + C::NST * C::STAGE);
 
   // zero the slice ring once: the pad slots stay zero (copies fill only the
-  // s slice slots of each stage)
+  // S slice slots of each stage)
   for (int i = tid; i < C::NST * C::STAGE / 16; i += blockDim.x)
     reinterpret_cast<uint4 *>(stages)[i] = make_uint4(0, 0, 0, 0);
   fence_proxy_async_smem();
@@ -262,7 +383,11 @@ __global__ void __launch_bounds__(192, 1) k_numeric_split(SplitArgs P) {
     }
     for (int i = 0; i < 2; i++) {
       mbar_init(&tfull[i], 1);
-      mbar_init(&tempty[i], 128);
+      mbar_init(&tempty[i], kTeam);  // buffer i belongs to team i
+    }
+    for (int i = 0; i < kMeta; i++) {
+      mbar_init(&meta_full[i], 1);
+      mbar_init(&meta_empty[i], kTeam + 1);  // MMA thread + the owning team
     }
     mbar_init(&done, 1);
     abort_flag = 0;
@@ -277,52 +402,161 @@ __global__ void __launch_bounds__(192, 1) k_numeric_split(SplitArgs P) {
   tc_fence_after();
   const uint32_t tbase = tmem_base_sh;
 
-  if (warp == 4) {
-    // ------------------------------------------------------------ producer
-    if (lane == 0) {
-      uint32_t it = 0;
-      const uint32_t bytes = (uint32_t)s * C::SLICE;
-      bool pend[C::NST] = {};
-      uint32_t ppar[C::NST] = {};
-      for (int64_t c = blockIdx.x; c < P.nc && !abort_flag; c += gridDim.x) {
-        int32_t k0 = P.seg[c], nk = P.seg[c + 1] - k0;
-        for (int j = 0; j < nk; j++, it++) {
-          int st = it % C::NST;
-          if (!mbar_wait(&empty[st], ((it / C::NST) & 1u) ^ 1u)) {
-            set_err(P.err, DERR_TIMEOUT);
-            abort_flag = 1;
-            break;
-          }
-          int32_t a = P.ta[k0 + j], b = P.tb[k0 + j];
-          uint8_t *sa = stages + (size_t)st * C::STAGE;
-          uint8_t *sb = sa + C::ASLOTS * C::SLICE;
-          pend[st] = true;
-          ppar[st] = (it / C::NST) & 1u;
-          if (a < 0 || a >= P.na || b < 0 || b >= P.nb) {
-            set_err(P.err, DERR_BOUNDS);  // complete the stage without data
-            mbar_arrive(&full[st]);
-            continue;
-          }
-          mbar_expect_tx(&full[st], 2 * bytes);
-          bulk_g2s(sa + (DPG - 1) * C::SLICE, P.asl + (int64_t)a * s * BS * BS, bytes, &full[st]);
-          bulk_g2s(sb, P.bsl + (int64_t)b * s * BS * BS, bytes, &full[st]);
+  if (warp == kProdWarp) {
+    // --------------------------------------------------------- producer warp
+    // Claims chunks of kChunk consecutive C blocks (Morton order) from a
+    // global counter; the chunk's descriptors and its contiguous range of
+    // block products are loaded 32 at a time by the whole warp, the scale
+    // exponents of the next C block one step ahead.  Lane 0 does the barrier
+    // work and issues the copies.  Two sentinel descriptors (nk = -1) end the
+    // consumers.
+    uint32_t it = 0, q = 0;
+    bool pend[C::NST] = {};
+    uint32_t ppar[C::NST] = {};
+    bool stop = false;
+    auto put_meta = [&](int64_t c, uint64_t key, int nk, const int (&er)[BS / 16],
+                        const int (&ec)[BS / 16]) -> bool {
+      const int m = q % kMeta;
+      int okw = 1;
+      if (lane == 0) {
+        okw = mbar_wait(&meta_empty[m], ((q / kMeta) & 1u) ^ 1u) && !abort_flag;
+        if (!okw) {
+          set_err(P.err, DERR_TIMEOUT);
+          abort_flag = 1;
         }
       }
-      // copies still in flight must land before the CTA exits
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (okw) {
+#pragma unroll
+        for (int x = 0; x < BS / 16; x++) {
+          const int idx = lane + 32 * x;  // lanes 0..BS-1 hold row / column values
+          if (idx < BS) {
+            meta[m].erow[idx] = er[x];
+            meta[m].ecol[idx] = ec[x];
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          meta[m].c = c;
+          meta[m].key = key;
+          meta[m].nk = nk;
+          mbar_arrive(&meta_full[m]);  // release: the descriptor is visible
+        }
+      }
+      q++;
+      return okw != 0;
+    };
+    auto load_exps = [&](uint64_t key, int (&er)[BS / 16], int (&ec)[BS / 16]) {
+      const int64_t I = morton_compact(key >> 1), J = morton_compact(key);
+#pragma unroll
+      for (int x = 0; x < BS / 16; x++) {
+        const int idx = lane + 32 * x;
+        er[x] = idx < BS ? P.rowexp[I * BS + idx] : 0;
+        ec[x] = idx < BS ? P.colexp[J * BS + idx] : 0;
+      }
+    };
+    while (!stop) {
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(P.work, (unsigned long long)kChunk);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if ((int64_t)base >= P.nc) break;
+      const int n = (int)min((int64_t)kChunk, P.nc - (int64_t)base);
+      const bool valid = lane < n;
+      const int32_t s0 = valid ? P.seg[base + lane] : 0;
+      const int32_t s1 = valid ? P.seg[base + lane + 1] : 0;
+      const uint64_t key = valid ? P.ckeys[base + lane] : 0;
+      const int32_t t0 = __shfl_sync(0xffffffffu, s0, 0);
+      // products of the chunk [t0, t_end) are contiguous: 32 at a time
+      int32_t tw = t0;  // first product held in (ta_w, tb_w); loads stay below nt
+      int32_t ta_w = t0 + lane < P.nt ? P.ta[t0 + lane] : 0;
+      int32_t tb_w = t0 + lane < P.nt ? P.tb[t0 + lane] : 0;
+      int er[BS / 16], ec[BS / 16], ern[BS / 16], ecn[BS / 16];
+      load_exps(__shfl_sync(0xffffffffu, key, 0), er, ec);
+      for (int i = 0; i < n && !stop; i++) {
+        const uint64_t kk = __shfl_sync(0xffffffffu, key, i);
+        const int32_t k0 = __shfl_sync(0xffffffffu, s0, i);
+        const int32_t nk = __shfl_sync(0xffffffffu, s1, i) - k0;
+        if (i + 1 < n) load_exps(__shfl_sync(0xffffffffu, key, i + 1), ern, ecn);
+        if (!put_meta((int64_t)base + i, kk, nk, er, ec)) {
+          stop = true;
+          break;
+        }
+        for (int j = 0; j < nk; j++, it++) {
+          const int32_t t = k0 + j;
+          if (t >= tw + 32) {  // next window of 32 products
+            tw = t;
+            ta_w = tw + lane < P.nt ? P.ta[tw + lane] : 0;
+            tb_w = tw + lane < P.nt ? P.tb[tw + lane] : 0;
+          }
+          const int32_t aa = __shfl_sync(0xffffffffu, ta_w, t - tw);
+          const int32_t bb = __shfl_sync(0xffffffffu, tb_w, t - tw);
+          int okc = 1;
+          if (lane == 0) {
+            const int st = it % C::NST;
+            if (!mbar_wait(&empty[st], ((it / C::NST) & 1u) ^ 1u) || abort_flag) {
+              set_err(P.err, DERR_TIMEOUT);
+              abort_flag = 1;
+              okc = 0;
+            } else {
+              uint8_t *sa = stages + (size_t)st * C::STAGE;
+              uint8_t *sb = sa + C::ASLOTS * C::SLICE;
+              pend[st] = true;
+              ppar[st] = (it / C::NST) & 1u;
+              if (aa < 0 || aa >= P.na || bb < 0 || bb >= P.nb) {
+                set_err(P.err, DERR_BOUNDS);  // complete the stage without data
+                mbar_arrive(&full[st]);
+              } else {
+                mbar_expect_tx(&full[st], 2 * BYTES);
+                bulk_g2s(sa + (DPG - 1) * C::SLICE, P.asl + (int64_t)aa * S * BS * BS, BYTES,
+                         &full[st]);
+                bulk_g2s(sb, P.bsl + (int64_t)bb * S * BS * BS, BYTES, &full[st]);
+              }
+            }
+          }
+          if (!__shfl_sync(0xffffffffu, okc, 0)) {
+            stop = true;
+            break;
+          }
+        }
+#pragma unroll
+        for (int x = 0; x < BS / 16; x++) {
+          er[x] = ern[x];
+          ec[x] = ecn[x];
+        }
+      }
+    }
+    // two end markers: one for the MMA thread and each epilogue team
+    if (!stop) {
+      int z[BS / 16] = {};
+      put_meta(-1, 0, -1, z, z);
+      put_meta(-1, 0, -1, z, z);
+    }
+    // copies still in flight must land before the CTA exits
+    if (lane == 0)
       for (int st = 0; st < C::NST; st++)
         if (pend[st]) mbar_wait(&full[st], ppar[st]);
-    }
-  } else if (warp == 5) {
+  } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      uint32_t it = 0, fc = 0;
+      uint32_t it = 0, q = 0;
+      uint32_t fcb0 = 0, fcb1 = 0;  // flushes issued into TMEM buffer 0 / 1
       const uint32_t sbase = smem_u32(stages);
-      for (int64_t c = blockIdx.x; c < P.nc && !abort_flag; c += gridDim.x) {
-        int32_t k0 = P.seg[c], nk = P.seg[c + 1] - k0;
+      for (;; q++) {
+        int m = q % kMeta;
+        if (!mbar_wait(&meta_full[m], (q / kMeta) & 1u)) {
+          set_err(P.err, DERR_TIMEOUT);
+          abort_flag = 1;
+          break;
+        }
+        const int nk = meta[m].nk;
+        mbar_arrive(&meta_empty[m]);
+        if (nk < 0 || abort_flag) break;  // end marker
         int nfl = (nk + P.flushk - 1) / P.flushk;
-        for (int f = 0; f < nfl && !abort_flag; f++, fc++) {
-          int b = fc & 1;
-          if (!mbar_wait(&tempty[b], ((fc >> 1) & 1u) ^ 1u)) {
+        const int b = q & 1;  // C blocks alternate between the two teams / buffers
+        for (int f = 0; f < nfl && !abort_flag; f++) {
+          const uint32_t fb = b ? fcb1 : fcb0;
+          if (b) fcb1++; else fcb0++;
+          if (!mbar_wait(&tempty[b], (fb & 1u) ^ 1u)) {
             set_err(P.err, DERR_TIMEOUT);
             abort_flag = 1;
             break;
@@ -337,21 +571,25 @@ __global__ void __launch_bounds__(192, 1) k_numeric_split(SplitArgs P) {
               break;
             }
             tc_fence_after();
-            uint32_t sa = sbase + st * C::STAGE;
-            uint32_t sb = sa + C::ASLOTS * C::SLICE;
+            // descriptors differ only in the start-address field (16-byte
+            // units, < 2^14 inside shared memory): build them once per stage
+            const uint32_t sa = sbase + st * C::STAGE;
+            const uint64_t ad0 = smem_desc(sa, C::LBO, C::SBO);
+            const uint64_t bd0 = smem_desc(sa + C::ASLOTS * C::SLICE, C::LBO, C::SBO);
+            const uint32_t first = (j == f * P.flushk) ? 0u : 1u;
 #pragma unroll
             for (int g = 0; g < G; g++) {
-              uint32_t dt = tbase + (uint32_t)((b * G + g) * BS);
-              int nt = min(s, (g + 1) * DPG);  // K-blocks: slices t = 0 .. nt-1
-              for (int t = 0; t < nt; t++)
+              const uint32_t dt = tbase + (uint32_t)((b * G + g) * BS);
+#pragma unroll
+              for (int t = 0; t < S; t++) {
+                if (t >= (g + 1) * DPG) break;  // K-blocks of group g: t < min(S, (g+1) DPG)
 #pragma unroll
                 for (int h = 0; h < BS / 16; h++) {
-                  uint32_t aaddr = sa + (uint32_t)((DPG - 1 + g * DPG - t) * C::SLICE + h * 256);
-                  uint32_t baddr = sb + (uint32_t)(t * C::SLICE + h * 256);
-                  uint32_t acc = (j > f * P.flushk || t > 0 || h > 0) ? 1u : 0u;
-                  tc_mma_bf16(dt, smem_desc(aaddr, C::LBO, C::SBO), smem_desc(baddr, C::LBO, C::SBO),
-                              IDESC, acc);
+                  const uint64_t aoff = (uint64_t)(((DPG - 1 + g * DPG - t) * C::SLICE + h * 256) >> 4);
+                  const uint64_t boff = (uint64_t)((t * C::SLICE + h * 256) >> 4);
+                  tc_mma_bf16(dt, ad0 + aoff, bd0 + boff, IDESC, (t | h) ? 1u : first);
                 }
+              }
             }
             tc_commit(&empty[st]);  // stage reusable once these MMAs are done
           }
@@ -364,25 +602,53 @@ __global__ void __launch_bounds__(192, 1) k_numeric_split(SplitArgs P) {
     }
   } else {
     // ----------------------------------------------------------- epilogue
-    const int row = warp * 32 + lane;  // TMEM lane = operand row
+    // Two teams of eight warps take alternate C blocks (team t: local C-block
+    // index q with q % 2 == t) and TMEM buffer t.  Warp w of a team drains
+    // lane quadrant w % 4, columns [(w / 4) BS/2, +BS/2), and accumulates the
+    // exact diagonal sums straight into the team's shared-memory buffer
+    // [d][r][c]; the team then combines the diagonals of each output element.
+    // One team's recombination overlaps the other team's drain and the MMAs.
+    constexpr int HC = BS / 2;
+    constexpr int NG4 = BS * BS / 4;                // 4-column groups per C block
+    constexpr int GRP = (NG4 + kTeam - 1) / kTeam;  // combine: groups per thread
+    const int team = warp / kTeamWarps, tw = warp % kTeamWarps, ttid = tid % kTeam;
+    const int wq = tw & 3;
+    const int row = wq * 32 + lane;       // TMEM lane = operand row
     const int L = row / BS, r = row % BS;
-    const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
-    uint32_t fc = 0;
-    for (int64_t c = blockIdx.x; c < P.nc; c += gridDim.x) {
-      int32_t k0 = P.seg[c], nk = P.seg[c + 1] - k0;
-      int nfl = (nk + P.flushk - 1) / P.flushk;
-      uint32_t acc[G][BS];
-#pragma unroll
-      for (int g = 0; g < G; g++)
-#pragma unroll
-        for (int q = 0; q < BS; q++) acc[g][q] = 0;
+    const int c0 = (tw >> 2) * HC;
+    const uint32_t lane_addr = (uint32_t)(wq * 32) << 16;
+    int32_t *tcomb = comb + team * (C::COMB / 4);
+    const int bar_id = 1 + team;
+    uint32_t fct = 0;                     // flushes drained by this team
+    for (uint32_t q = team;; q += 2) {
+      int m = q % kMeta;
+      bool okm = mbar_wait(&meta_full[m], (q / kMeta) & 1u);
       // every decision below is uniform across the warp (tcgen05.ld is
-      // .sync.aligned) and, at the barriers, across the 128 epilogue threads
-      bool ok = __all_sync(0xffffffffu, abort_flag == 0);
-      for (int f = 0; f < nfl && ok; f++, fc++) {
-        int b = fc & 1;
-        bool w = mbar_wait(&tfull[b], (fc >> 1) & 1u);
-        if (!__all_sync(0xffffffffu, w)) {
+      // .sync.aligned) and, at the named barriers, across the team
+      if (named_bar_or(bar_id, kTeam, !okm || abort_flag != 0)) {
+        set_err(P.err, DERR_TIMEOUT);
+        abort_flag = 1;
+        break;
+      }
+      const int nk = meta[m].nk;
+      const int64_t c = meta[m].c;
+      if (nk < 0) break;  // end marker
+      // scale exponents of this thread's output elements (thread handles
+      // columns 4*(g4 % (BS/4)) .. +3 of row g4 / (BS/4), g4 = ttid + i kTeam)
+      int erow[GRP];
+      int4 fcol[GRP];
+#pragma unroll
+      for (int i = 0; i < GRP; i++) {
+        const int g4 = min(ttid + i * kTeam, NG4 - 1);
+        erow[i] = meta[m].erow[g4 / (BS / 4)];
+        fcol[i] = *reinterpret_cast<const int4 *>(&meta[m].ecol[(g4 % (BS / 4)) * 4]);
+      }
+      mbar_arrive(&meta_empty[m]);
+      const int nfl = (nk + P.flushk - 1) / P.flushk;
+      bool ok = true;
+      for (int f = 0; f < nfl && ok; f++, fct++) {
+        bool w = mbar_wait(&tfull[team], fct & 1u);
+        if (!__all_sync(0xffffffffu, w && abort_flag == 0)) {
           set_err(P.err, DERR_TIMEOUT);
           abort_flag = 1;
           ok = false;
@@ -391,57 +657,75 @@ __global__ void __launch_bounds__(192, 1) k_numeric_split(SplitArgs P) {
         tc_fence_after();
 #pragma unroll
         for (int g = 0; g < G; g++) {
-          uint32_t v[BS];
-          if constexpr (BS == 32)
-            tmem_ld32(tbase + lane_addr + (uint32_t)((b * G + g) * BS), v);
+          uint32_t v[HC];
+          if constexpr (HC == 16)
+            tmem_ld16(tbase + lane_addr + (uint32_t)((team * G + g) * BS + c0), v);
           else
-            tmem_ld16(tbase + lane_addr + (uint32_t)((b * G + g) * BS), v);
+            tmem_ld8(tbase + lane_addr + (uint32_t)((team * G + g) * BS + c0), v);
           tmem_ld_wait();
+          const int d = g * DPG + L;
+          if (d < S) {
+            // exact integer value of each FP32 sum (|D| < 2^22)
+            int32_t *dst = tcomb + (d * BS + r) * C::CROW + c0;
 #pragma unroll
-          for (int q = 0; q < BS; q++) acc[g][q] += __float_as_uint(__uint_as_float(v[q]) + kMagicF);
+            for (int x = 0; x < HC; x += 4) {
+              int4 val = make_int4(
+                  (int32_t)(__float_as_uint(__uint_as_float(v[x]) + kMagicF) - kMagic),
+                  (int32_t)(__float_as_uint(__uint_as_float(v[x + 1]) + kMagicF) - kMagic),
+                  (int32_t)(__float_as_uint(__uint_as_float(v[x + 2]) + kMagicF) - kMagic),
+                  (int32_t)(__float_as_uint(__uint_as_float(v[x + 3]) + kMagicF) - kMagic));
+              if (f > 0) {
+                const int4 old = *reinterpret_cast<const int4 *>(dst + x);
+                val.x += old.x;
+                val.y += old.y;
+                val.z += old.z;
+                val.w += old.w;
+              }
+              *reinterpret_cast<int4 *>(dst + x) = val;
+            }
+          }
         }
         tc_fence_before();
-        mbar_arrive(&tempty[b]);
+        mbar_arrive(&tempty[team]);
       }
-      // all 128 epilogue threads agree on whether to continue
-      if (named_bar_or(1, 128, !ok || abort_flag != 0)) break;
-      // diagonals -> shared memory, [d][r][c] with padded rows
-#pragma unroll
-      for (int g = 0; g < G; g++) {
-        int d = g * DPG + L;
-        if (d < s) {
-          int32_t *dst = comb + (d * BS + r) * C::CROW;
-#pragma unroll
-          for (int q = 0; q < BS; q += 4)
-            *reinterpret_cast<int4 *>(dst + q) =
-                make_int4((int32_t)(acc[g][q] - (uint32_t)nfl * kMagic),
-                          (int32_t)(acc[g][q + 1] - (uint32_t)nfl * kMagic),
-                          (int32_t)(acc[g][q + 2] - (uint32_t)nfl * kMagic),
-                          (int32_t)(acc[g][q + 3] - (uint32_t)nfl * kMagic));
-        }
-      }
-      named_bar(1, 128);
-      uint64_t key = P.ckeys[c];
-      int64_t I = morton_compact(key >> 1), J = morton_compact(key);
+      if (named_bar_or(bar_id, kTeam, !ok || abort_flag != 0)) break;
       double *cb = P.cv + c * (int64_t)BS * BS;
       bool any = false;
-      for (int e = tid; e < BS * BS; e += 128) {
-        int rr = e / BS, cc = e % BS;
-        __int128 V = 0;
-        for (int d = 0; d < s; d++)
-          V += (__int128)comb[(d * BS + rr) * C::CROW + cc] << (kBeta * (s - 1 - d));
-        double out = 0.0;
-        if (V != 0) {
-          int X = P.rowexp[I * BS + rr] + P.colexp[J * BS + cc] - kBeta * (s + 1);
-          out = fixed_to_double(V, X);
-          any = true;
+      constexpr int XS = kBeta * (S + 1);
+#pragma unroll
+      for (int i = 0; i < GRP; i++) {
+        const int g4 = ttid + i * kTeam;
+        if (NG4 % kTeam != 0 && g4 >= NG4) break;  // bs 16: part of the team idles here
+        const int rr = g4 / (BS / 4), c4 = (g4 % (BS / 4)) * 4;
+        int4 dv[S];
+#pragma unroll
+        for (int d = 0; d < S; d++)
+          dv[d] = *reinterpret_cast<const int4 *>(tcomb + (d * BS + rr) * C::CROW + c4);
+        double out[4];
+#pragma unroll
+        for (int x = 0; x < 4; x++) {
+          int32_t dg[S];
+#pragma unroll
+          for (int d = 0; d < S; d++) dg[d] = x == 0 ? dv[d].x : x == 1 ? dv[d].y : x == 2 ? dv[d].z : dv[d].w;
+          int64_t hi, lo;
+          combine_digits<S>(dg, hi, lo);
+          const int fx = x == 0 ? fcol[i].x : x == 1 ? fcol[i].y : x == 2 ? fcol[i].z : fcol[i].w;
+          out[x] = split_to_double(hi, lo, erow[i] + fx - XS);
+          any |= (hi | lo) != 0;
         }
-        cb[e] = out;
+        double2 *dst = reinterpret_cast<double2 *>(cb + rr * BS + c4);
+        dst[0] = make_double2(out[0], out[1]);
+        dst[1] = make_double2(out[2], out[3]);
       }
       any = __any_sync(0xffffffffu, any);
-      if (lane == 0) warp_any[warp] = any;
-      named_bar(1, 128);
-      if (tid == 0) P.nz[c] = warp_any[0] | warp_any[1] | warp_any[2] | warp_any[3];
+      if (lane == 0) warp_any[team][tw] = any;
+      named_bar(bar_id, kTeam);  // warp_any complete; shared buffer free for the next block
+      if (ttid == 0) {
+        int nzv = 0;
+#pragma unroll
+        for (int w = 0; w < kTeamWarps; w++) nzv |= warp_any[team][w];
+        P.nz[c] = nzv;
+      }
     }
   }
   __syncthreads();
@@ -453,13 +737,13 @@ __global__ void __launch_bounds__(192, 1) k_numeric_split(SplitArgs P) {
 
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-template <int BS, int G>
+template <int BS, int S>
 bsm_status launch_split(const SplitArgs &a, cudaStream_t s) {
-  using C = Cfg<BS>;
+  using C = Cfg<BS, S>;
   static bool attr = false;
   if (!attr) {
-    BSM_CUDA(cudaFuncSetAttribute(k_numeric_split<BS, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  C::SMEM));
+    BSM_CUDA(cudaFuncSetAttribute(k_numeric_split<BS, S>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     attr = true;
   }
   int dev = 0, sms = 0;
@@ -467,8 +751,23 @@ bsm_status launch_split(const SplitArgs &a, cudaStream_t s) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int64_t grid = a.nc < sms ? a.nc : sms;
   count_launch();
-  k_numeric_split<BS, G><<<(unsigned)grid, 192, C::SMEM, s>>>(a);
+  k_numeric_split<BS, S><<<(unsigned)grid, kThreads, C::SMEM, s>>>(a);
   return cuda_status(cudaGetLastError());
+}
+
+template <int BS>
+bsm_status launch_split_s(const SplitArgs &a, int slices, cudaStream_t s) {
+  switch (slices) {
+    case 1: return launch_split<BS, 1>(a, s);
+    case 2: return launch_split<BS, 2>(a, s);
+    case 3: return launch_split<BS, 3>(a, s);
+    case 4: return launch_split<BS, 4>(a, s);
+    case 5: return launch_split<BS, 5>(a, s);
+    case 6: return launch_split<BS, 6>(a, s);
+    case 7: return launch_split<BS, 7>(a, s);
+    case 8: return launch_split<BS, 8>(a, s);
+  }
+  return BSM_ERR_INVALID_ARG;
 }
 
 }  // namespace
@@ -502,7 +801,7 @@ bsm_status numeric_split(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, 
     dev_free(asl, s);
     dev_free(bsl, s);
   };
-  if ((st = dev_alloc((void **)&dmax, 4, s)) ||
+  if ((st = dev_alloc((void **)&dmax, 16, s)) ||
       (st = dev_alloc((void **)&rowexp, 4 * A->mb * bs, s)) ||
       (st = dev_alloc((void **)&colexp, 4 * B->nb * bs, s)) ||
       (st = dev_alloc((void **)&asl, (size_t)2 * slices * bs * bs * A->nblk, s)) ||
@@ -510,25 +809,18 @@ bsm_status numeric_split(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, 
     cleanup();
     return st;
   }
-  cudaMemsetAsync(dmax, 0, 4, s);
+  cudaMemsetAsync(dmax, 0, 16, s);  // [0]: longest product list; [2..3]: chunk counter
   cudaMemsetAsync(rowexp, 0x80, 4 * A->mb * bs, s);  // 0x80808080: below any exponent
   cudaMemsetAsync(colexp, 0x80, 4 * B->nb * bs, s);
-  count_launch(5);
+  count_launch(3);
   k_max_seg<<<grid_for(sym.nc, 256), 256, 0, s>>>(sym.seg, sym.nc, dmax);
   k_row_exp<<<grid_for(A->nblk, 8), 256, 0, s>>>(A->vals, A->keys, A->nblk, bs, rowexp, errword);
   k_col_exp<<<grid_for(B->nblk * bs, 256), 256, 0, s>>>(B->vals, B->keys, B->nblk, bs, colexp,
                                                        errword);
-  if (bs == 16) {
-    k_slice<16, 0><<<grid_for(A->nblk * 256, 256), 256, 0, s>>>(A->vals, A->keys, A->nblk, rowexp,
-                                                                slices, asl);
-    k_slice<16, 1><<<grid_for(B->nblk * 256, 256), 256, 0, s>>>(B->vals, B->keys, B->nblk, colexp,
-                                                                slices, bsl);
-  } else {
-    k_slice<32, 0><<<grid_for(A->nblk * 1024, 256), 256, 0, s>>>(A->vals, A->keys, A->nblk,
-                                                                 rowexp, slices, asl);
-    k_slice<32, 1><<<grid_for(B->nblk * 1024, 256), 256, 0, s>>>(B->vals, B->keys, B->nblk,
-                                                                 colexp, slices, bsl);
-  }
+  if (bs == 16)
+    launch_slices_s<16>(A, B, rowexp, colexp, asl, bsl, slices, s);
+  else
+    launch_slices_s<32>(A, B, rowexp, colexp, asl, bsl, slices, s);
   int *h = (int *)host_scratch().get(16);
   if (!h) {
     cleanup();
@@ -551,23 +843,19 @@ bsm_status numeric_split(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, 
   a.tb = sym.tb;
   a.ckeys = sym.ckeys;
   a.nc = sym.nc;
+  a.nt = sym.nt;
+  a.work = reinterpret_cast<unsigned long long *>(dmax + 2);
   a.na = A->nblk;
   a.nb = B->nblk;
   a.asl = asl;
   a.bsl = bsl;
   a.rowexp = rowexp;
   a.colexp = colexp;
-  a.s = slices;
   a.flushk = flushk;
   a.cv = cvals;
   a.nz = nzflag;
   a.err = errword;
-  if (bs == 16)
-    st = launch_split<16, 1>(a, s);
-  else if (slices <= 4)
-    st = launch_split<32, 1>(a, s);
-  else
-    st = launch_split<32, 2>(a, s);
+  st = bs == 16 ? launch_split_s<16>(a, slices, s) : launch_split_s<32>(a, slices, s);
   cleanup();  // stream-ordered: freed after the kernel
   return st;
 }

@@ -308,6 +308,10 @@ extern "C" bsm_status bsm_build(int64_t nrows, int64_t ncols, int bs, int64_t nb
   if (!bs_supported(bs)) return BSM_ERR_BLOCKSIZE;
   if (nblk > 0 && (!brow || !bcol || !vals)) return BSM_ERR_INVALID_ARG;
   if (nblk > INT32_MAX) return BSM_ERR_UNSUPPORTED;
+  // device payloads are read with 16-byte vector loads
+  if (on_device && nblk > 0 &&
+      (((uintptr_t)vals & 15) || ((uintptr_t)brow & 3) || ((uintptr_t)bcol & 3)))
+    return BSM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (on_device || nblk == 0)
     return build_from_device(nrows, ncols, bs, nblk, brow, bcol, vals, s, out);
@@ -342,6 +346,9 @@ extern "C" bsm_status bsm_to_blocks(bsm_matrix M, int64_t *nblk_inout, int32_t *
   if (!brow && !bcol && !vals) return BSM_OK;
   if (cap < M->nblk) return BSM_ERR_BUFFER_TOO_SMALL;
   if (M->nblk == 0) return BSM_OK;
+  // device outputs are written with 16-byte vector stores
+  if (on_device && (((uintptr_t)vals & 15) || ((uintptr_t)brow & 3) || ((uintptr_t)bcol & 3)))
+    return BSM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   int64_t n = M->nblk;
   int bs = M->bs;

@@ -67,3 +67,16 @@ def test_argument_checks_before_any_device_work(lib):
     assert lib.bsm_to_blocks(None, ctypes.byref(n), None, None, None, 0, None) == -1
     assert lib.bsm_info(None, None, None, None, None) == -1
     assert lib.bsm_destroy(None) == 0
+
+
+def test_misaligned_device_pointers_rejected_before_any_work(lib):
+    """Device payloads are staged with 16-byte vector loads / bulk copies: a
+    misaligned caller pointer is refused with INVALID_ARG (never dereferenced)."""
+    out = ctypes.c_void_p(1)
+    # vals at an address that is 8 (not 16) byte aligned; never touched
+    assert lib.bsm_build(64, 64, 32, 1, 256, 512, 4104, 1, None, ctypes.byref(out)) == -1
+    assert out.value is None
+    assert lib.bsm_build(64, 64, 32, 1, 258, 512, 4096, 1, None, ctypes.byref(out)) == -1
+    n = ctypes.c_int64(0)
+    assert lib.bsm_block_products_fp64_noalloc(32, 1, 256, 256, 256, 4104, 1, 4096, 1, 4096,
+                                               ctypes.byref(n), None) == -1
