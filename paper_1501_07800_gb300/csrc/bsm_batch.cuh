@@ -1,0 +1,27 @@
+// Batched products: per-product descriptors and the global work-list encoding.
+#pragma once
+
+#include <stdint.h>
+
+// Everything one product's numeric phase needs, in device memory (a table of
+// these is indexed by the work items).
+struct ProdDesc {
+  const int32_t *seg, *ta, *tb;  // task list: C block c sums products seg[c]..seg[c+1]-1
+  const uint64_t *ckeys;         // C block Morton keys
+  const double *av, *bv;         // A / B leaf blocks
+  double *cv;                    // C blocks (output)
+  int32_t *nz;                   // nonzero flag per C block (output)
+  int64_t na, nb, nc, nt;        // A blocks, B blocks, C blocks, products
+  // split mode only
+  const uint16_t *asl, *bsl;     // digit slices of A / B
+  const int *rowexp, *colexp;    // power-of-two scale exponents
+};
+
+// Work item = (product index << 40) | C block index.
+__host__ __device__ inline uint64_t make_item(uint32_t p, uint64_t c) {
+  return ((uint64_t)p << 40) | c;
+}
+__host__ __device__ inline uint32_t item_product(uint64_t it) { return (uint32_t)(it >> 40); }
+__host__ __device__ inline int64_t item_cblock(uint64_t it) {
+  return (int64_t)(it & ((1ull << 40) - 1));
+}

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/bsm.h"
+#include "bsm_batch.cuh"
 
 #define BSM_MAXH 31  // tree heights 0..31: up to 2^31 blocks per side
 
@@ -93,6 +94,8 @@ bsm_status scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaSt
 bsm_status scan_exclusive_int4(const int4 *in, int4 *out, int64_t n, cudaStream_t s);
 bsm_status sort_keys_u64(const uint64_t *kin, uint64_t *kout, const int32_t *vin, int32_t *vout,
                          int64_t n, int end_bit, cudaStream_t s);
+bsm_status sort_pairs_u32_u64(const uint32_t *kin, uint32_t *kout, const uint64_t *vin,
+                              uint64_t *vout, int64_t n, cudaStream_t s);
 
 // Builds the level arrays of a handle whose keys are set (bsm_tree.cu).
 bsm_status build_levels(bsm_matrix M, cudaStream_t s);
@@ -126,6 +129,21 @@ bsm_status numeric_fp64(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, d
 // accumulation, integer recombination).
 bsm_status numeric_split(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, int slices,
                          double *cvals, int32_t *nzflag, unsigned *errword, cudaStream_t s);
+
+// Batched numeric phases over a global (product, C block) work list.
+ProdDesc make_desc(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, double *cvals,
+                   int32_t *nz);
+bsm_status numeric_fp64_batched(int bs, const ProdDesc *prods, const uint64_t *items,
+                                int64_t nitems, unsigned long long *counter, unsigned *errword,
+                                int ctas_per_sm, cudaStream_t s);
+bsm_status split_supported(int bs, int slices);
+int split_flush_group(int bs, int slices);
+bsm_status split_prepare(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, int slices,
+                         int *dmax_dev, unsigned *errword, ProdDesc &d, std::vector<void *> &owned,
+                         cudaStream_t s);
+bsm_status split_launch(int bs, int slices, const ProdDesc *prods_dev, const uint64_t *items,
+                        int64_t nitems, unsigned long long *work, unsigned *errword,
+                        cudaStream_t s);
 
 // Handle shells for results (bsm_tree.cu).
 bsm_matrix new_matrix_shell(int64_t nrows, int64_t ncols, int bs, int L);

@@ -1,5 +1,6 @@
 // C = A*B: symbolic phase, numeric phase, exact-zero block removal, C levels.
 #include <cstring>
+#include <vector>
 
 #include "bsm_internal.cuh"
 
@@ -226,6 +227,144 @@ extern "C" bsm_status bsm_last_stats(int64_t *tasks, int cap, int *nlev, int64_t
   return BSM_OK;
 }
 
+// LPT order: key = -(product-list length) so an ascending sort puts the
+// longest C blocks first.
+__global__ void k_batch_items(const int32_t *__restrict__ seg, int64_t nc, uint32_t p,
+                              uint32_t *__restrict__ keys, uint64_t *__restrict__ items) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  keys[c] = 0xFFFFFFFFu - (uint32_t)(seg[c + 1] - seg[c]);
+  items[c] = make_item(p, (uint64_t)c);
+}
+
+// Products of one block size: symbolic phases one by one, then one persistent
+// numeric launch over all their C blocks in longest-first order, then zero
+// removal and level build per product.
+static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A,
+                                const bsm_matrix *B, bsm_matrix *C, int prec, int slices,
+                                cudaStream_t s) {
+  const int n = (int)idx.size();
+  const int bs = A[idx[0]]->bs;
+  LastStats &ls = last_stats();
+  PhaseTimer timer(timing_enabled());
+  timer.mark(s);
+  std::vector<SymbolicResult> sym(n);
+  std::vector<bsm_matrix> shells(n, nullptr);
+  std::vector<double *> cv(n, nullptr);
+  std::vector<int32_t *> nz(n, nullptr);
+  std::vector<void *> owned;
+  unsigned *err = nullptr;
+  bsm_status st = BSM_OK;
+  auto cleanup = [&](bool keep_results) {
+    for (int i = 0; i < n; i++) {
+      free_symbolic(&sym[i], s);
+      if (!keep_results) {
+        if (shells[i]) free_matrix_shell(shells[i], s);
+        dev_free(cv[i], s);
+      }
+      dev_free(nz[i], s);
+    }
+    for (void *p : owned) dev_free(p, s);
+    dev_free(err, s);
+  };
+  for (int i = 0; i < n && st == BSM_OK; i++) {
+    bsm_matrix a = A[idx[i]], b = B[idx[i]];
+    st = symbolic_multiply(a, b, &sym[i], s);
+    if (st != BSM_OK) break;
+    if (sym[i].nc > 0xFFFFFFFFFFll) st = BSM_ERR_UNSUPPORTED;
+    int64_t side = a->mb > b->nb ? a->mb : b->nb;
+    shells[i] = new_matrix_shell(a->nrows, b->ncols, bs, ceil_log2_i64(side < 1 ? 1 : side));
+    ls.triples += sym[i].nt;
+    ls.nc_sym += sym[i].nc;
+  }
+  int64_t total = 0;
+  for (int i = 0; i < n; i++) total += sym[i].nc;
+  if (st == BSM_OK) st = dev_alloc((void **)&err, sizeof(unsigned), s);
+  if (st == BSM_OK) cudaMemsetAsync(err, 0, sizeof(unsigned), s);
+  for (int i = 0; i < n && st == BSM_OK; i++) {
+    if (sym[i].nc == 0) continue;
+    if ((st = dev_alloc((void **)&cv[i], sizeof(double) * bs * bs * sym[i].nc, s)) != BSM_OK) break;
+    st = dev_alloc((void **)&nz[i], 4 * sym[i].nc, s);
+  }
+  // global work list, longest product lists first
+  uint32_t *k0 = nullptr, *k1 = nullptr;
+  uint64_t *v0 = nullptr, *v1 = nullptr;
+  ProdDesc *table = nullptr;
+  int *scr = nullptr;  // [0] longest list, [2..3] work counter
+  if (st == BSM_OK && total > 0) {
+    if ((st = dev_alloc((void **)&k0, 4 * total, s)) == BSM_OK) owned.push_back(k0);
+    if (st == BSM_OK && (st = dev_alloc((void **)&k1, 4 * total, s)) == BSM_OK) owned.push_back(k1);
+    if (st == BSM_OK && (st = dev_alloc((void **)&v0, 8 * total, s)) == BSM_OK) owned.push_back(v0);
+    if (st == BSM_OK && (st = dev_alloc((void **)&v1, 8 * total, s)) == BSM_OK) owned.push_back(v1);
+    if (st == BSM_OK &&
+        (st = dev_alloc((void **)&table, sizeof(ProdDesc) * n, s)) == BSM_OK)
+      owned.push_back(table);
+    if (st == BSM_OK && (st = dev_alloc((void **)&scr, 16, s)) == BSM_OK) owned.push_back(scr);
+  }
+  timer.mark(s);
+  if (st == BSM_OK && total > 0) {
+    cudaMemsetAsync(scr, 0, 16, s);
+    int64_t off = 0;
+    for (int i = 0; i < n; i++) {
+      if (sym[i].nc == 0) continue;
+      count_launch();
+      k_batch_items<<<grid_for(sym[i].nc, 256), 256, 0, s>>>(sym[i].seg, sym[i].nc, (uint32_t)i,
+                                                             k0 + off, v0 + off);
+      off += sym[i].nc;
+    }
+    st = sort_pairs_u32_u64(k0, k1, v0, v1, total, s);
+    std::vector<ProdDesc> h(n);
+    for (int i = 0; i < n && st == BSM_OK; i++) {
+      h[i] = make_desc(A[idx[i]], B[idx[i]], sym[i], cv[i], nz[i]);
+      if (prec != BSM_FP64 && sym[i].nc > 0)
+        st = split_prepare(A[idx[i]], B[idx[i]], sym[i], slices, scr, err, h[i], owned, s);
+    }
+    if (st == BSM_OK) {
+      void *hp = host_scratch().get(sizeof(ProdDesc) * n + 16);
+      if (!hp) st = BSM_ERR_OOM;
+      if (st == BSM_OK) {
+        memcpy(hp, h.data(), sizeof(ProdDesc) * n);
+        cudaMemcpyAsync(table, hp, sizeof(ProdDesc) * n, cudaMemcpyHostToDevice, s);
+        if (prec != BSM_FP64) {
+          // the 32-bit diagonal accumulators hold at most 511 flushes
+          int *hm = (int *)((char *)hp + sizeof(ProdDesc) * n);
+          cudaMemcpyAsync(hm, scr, 4, cudaMemcpyDeviceToHost, s);
+          st = cuda_status(cudaStreamSynchronize(s));
+          const int flushk = split_flush_group(bs, slices);
+          if (st == BSM_OK && (hm[0] + flushk - 1) / flushk > 511) st = BSM_ERR_UNSUPPORTED;
+        } else {
+          st = cuda_status(cudaStreamSynchronize(s));  // host table reused below
+        }
+      }
+    }
+    unsigned long long *counter = reinterpret_cast<unsigned long long *>(scr + 2);
+    if (st == BSM_OK) {
+      if (prec == BSM_FP64)
+        st = numeric_fp64_batched(bs, table, v1, total, counter, err, 0, s);
+      else
+        st = split_launch(bs, slices, table, v1, total, counter, err, s);
+    }
+  }
+  timer.mark(s);
+  for (int i = 0; i < n && st == BSM_OK; i++) {
+    if (sym[i].nc == 0) {
+      st = build_levels(shells[i], s);
+    } else {
+      st = finish_product(shells[i], &sym[i], cv[i], nz[i], err, s);  // owns cv[i]
+      cv[i] = nullptr;
+    }
+  }
+  timer.mark(s);
+  if (st != BSM_OK) {
+    cleanup(false);
+    return st;
+  }
+  for (int i = 0; i < n; i++) C[idx[i]] = shells[i];
+  cleanup(true);
+  timer.collect(ls.phase_ms);
+  return BSM_OK;
+}
+
 extern "C" bsm_status bsm_multiply_batched(int n, const bsm_matrix *A, const bsm_matrix *B,
                                            bsm_matrix *C, const bsm_mult_opts *opts,
                                            void *stream) {
@@ -234,16 +373,26 @@ extern "C" bsm_status bsm_multiply_batched(int n, const bsm_matrix *A, const bsm
   for (int i = 0; i < n; i++) BSM_TRY(check_pair(A[i], B[i]));
   int prec, slices;
   BSM_TRY(check_opts(opts, &prec, &slices));
+  if (prec != BSM_FP64)
+    for (int i = 0; i < n; i++) BSM_TRY(split_supported(A[i]->bs, slices));
   cudaStream_t s = (cudaStream_t)stream;
-  for (int i = 0; i < n; i++) {
-    bsm_status st = multiply_one(A[i], B[i], prec, slices, s, &C[i]);
-    if (st != BSM_OK) {
-      for (int j = 0; j < i; j++) {
-        bsm_destroy(C[j]);
-        C[j] = nullptr;
-      }
-      return st;
+  LastStats &ls = last_stats();
+  ls = LastStats();
+  int64_t l0 = launch_counter();
+  bsm_status st = BSM_OK;
+  for (int bs : {16, 32, 64}) {
+    std::vector<int> idx;
+    for (int i = 0; i < n; i++)
+      if (A[i]->bs == bs) idx.push_back(i);
+    if (idx.empty()) continue;
+    if ((st = batched_group(idx, A, B, C, prec, slices, s)) != BSM_OK) break;
+  }
+  ls.launches = launch_counter() - l0;
+  if (st != BSM_OK) {
+    for (int i = 0; i < n; i++) {
+      bsm_destroy(C[i]);
+      C[i] = nullptr;
     }
   }
-  return BSM_OK;
+  return st;
 }

@@ -13,6 +13,12 @@
 // FP64 rate of DMMA and DFMA is the same ~1 TFLOP/s, far below what the copies
 // can feed, so the kernel only has to keep the FP64 pipe busy.  The epilogue
 // also raises the C block's nonzero flag (exact-zero detection).
+//
+// Two launch forms share the per-C-block body: one CTA per C block of a single
+// product, and a persistent form that walks a global work list of
+// (product, C block) items of many independent products (batched products),
+// claiming items from an atomic counter in the list's order.
+#include "bsm_batch.cuh"
 #include "bsm_ptx.cuh"
 
 namespace {
@@ -25,22 +31,22 @@ __device__ __forceinline__ void dmma_8x8x4(double (&c)[2], double a, double b) {
                : "d"(a), "d"(b));
 }
 
+// Sums the products seg[c] .. seg[c+1]-1 into C block c (all 128 threads of
+// the CTA).  use0 / use1 count the completed phases of the two stage barriers
+// across calls.  Returns false (after recording the error) on a bad index or a
+// timed-out wait; every thread returns the same value.
 template <int BS>
-__global__ void __launch_bounds__(128) k_numeric_fp64(
-    const int32_t *__restrict__ seg, const int32_t *__restrict__ ta, const int32_t *__restrict__ tb,
-    int64_t nc, int64_t na, int64_t nb, const double *__restrict__ Av,
-    const double *__restrict__ Bv, double *__restrict__ Cv, int32_t *__restrict__ nzflag,
-    unsigned *__restrict__ err) {
+__device__ bool cblock_fp64(const int32_t *__restrict__ seg, const int32_t *__restrict__ ta,
+                            const int32_t *__restrict__ tb, int64_t c, int64_t na, int64_t nb,
+                            const double *__restrict__ Av, const double *__restrict__ Bv,
+                            double *__restrict__ Cv, int32_t *__restrict__ nzflag,
+                            unsigned *__restrict__ err, double *smem, uint64_t *full,
+                            uint32_t &use0, uint32_t &use1) {
   constexpr int BB = BS * BS;
   constexpr int WT = BS / 2;   // warp tile side (2 x 2 warps)
   constexpr int TW = WT / 8;   // 8x8 DMMA tiles per warp tile side
-  extern __shared__ __align__(128) double smem[];  // [kStages][2][BB]
-  __shared__ __align__(8) uint64_t full[kStages];
-
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wr = warp >> 1, wc = warp & 1;
-  const int64_t c = blockIdx.x;
-  if (c >= nc) return;
   const int32_t k0 = seg[c], nk = seg[c + 1] - k0;
   // every block index is checked before any copy is issued
   bool bad = nk < 0;
@@ -48,15 +54,8 @@ __global__ void __launch_bounds__(128) k_numeric_fp64(
     bad |= ta[k0 + j] < 0 || ta[k0 + j] >= na || tb[k0 + j] < 0 || tb[k0 + j] >= nb;
   if (__syncthreads_or(bad)) {
     if (tid == 0) set_err(err, DERR_BOUNDS);
-    return;
+    return false;
   }
-
-  if (tid == 0) {
-    for (int s = 0; s < kStages; s++) mbar_init(&full[s], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-
   auto issue = [&](int j) {
     int s = j % kStages;
     double *sa = smem + (size_t)s * 2 * BB;
@@ -77,17 +76,19 @@ __global__ void __launch_bounds__(128) k_numeric_fp64(
   bool ok = true;
   int jfail = 0;
   for (int j = 0; j < nk; j++) {
-    int s = j % kStages;
-    uint32_t par = (uint32_t)(j / kStages) & 1u;
-    if (!mbar_wait(&full[s], par)) {
-      ok = false;
-    }
+    const int s = j % kStages;
+    const uint32_t par = (s == 0 ? use0 : use1) & 1u;
+    if (!mbar_wait(&full[s], par)) ok = false;
     // every thread takes the same path: a failed wait aborts the whole CTA
     if (__syncthreads_or(!ok)) {
       ok = false;
       jfail = j;
       break;
     }
+    if (s == 0)
+      use0++;
+    else
+      use1++;
     const double *sa = smem + (size_t)s * 2 * BB;
     const double *sb = sa + BB;
 #pragma unroll 2
@@ -108,11 +109,13 @@ __global__ void __launch_bounds__(128) k_numeric_fp64(
   if (!ok) {
     if (tid == 0) {
       set_err(err, DERR_TIMEOUT);
-      // let copies still in flight land before shared memory is released
-      for (int j = jfail; j < jfail + kStages && j < nk; j++)
-        mbar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u);
+      // let copies still in flight land before shared memory is reused
+      for (int j = jfail; j < jfail + kStages && j < nk; j++) {
+        const int s = j % kStages;
+        mbar_wait(&full[s], (s == 0 ? use0 : use1) & 1u);
+      }
     }
-    return;
+    return false;
   }
   bool any = false;
   double *cb = Cv + c * BB;
@@ -126,6 +129,56 @@ __global__ void __launch_bounds__(128) k_numeric_fp64(
     }
   int nzb = __syncthreads_or(any);
   if (tid == 0) nzflag[c] = nzb;
+  return true;
+}
+
+template <int BS>
+__global__ void __launch_bounds__(128) k_numeric_fp64(
+    const int32_t *__restrict__ seg, const int32_t *__restrict__ ta, const int32_t *__restrict__ tb,
+    int64_t nc, int64_t na, int64_t nb, const double *__restrict__ Av,
+    const double *__restrict__ Bv, double *__restrict__ Cv, int32_t *__restrict__ nzflag,
+    unsigned *__restrict__ err) {
+  extern __shared__ __align__(128) double smem[];  // [kStages][2][BS*BS]
+  __shared__ __align__(8) uint64_t full[kStages];
+  const int64_t c = blockIdx.x;
+  if (c >= nc) return;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; s++) mbar_init(&full[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t use0 = 0, use1 = 0;
+  cblock_fp64<BS>(seg, ta, tb, c, na, nb, Av, Bv, Cv, nzflag, err, smem, full, use0, use1);
+}
+
+// Persistent form over a global work list of (product, C block) items.
+template <int BS>
+__global__ void __launch_bounds__(128) k_numeric_fp64_batched(const ProdDesc *__restrict__ prods,
+                                                              const uint64_t *__restrict__ items,
+                                                              int64_t nitems,
+                                                              unsigned long long *counter,
+                                                              unsigned *__restrict__ err) {
+  extern __shared__ __align__(128) double smem[];
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ unsigned long long next_item;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; s++) mbar_init(&full[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t use0 = 0, use1 = 0;
+  for (;;) {
+    if (threadIdx.x == 0) next_item = atomicAdd(counter, 1ull);
+    __syncthreads();
+    const unsigned long long w = next_item;
+    __syncthreads();
+    if ((int64_t)w >= nitems) break;
+    const uint64_t it = items[w];
+    const ProdDesc &p = prods[item_product(it)];
+    if (!cblock_fp64<BS>(p.seg, p.ta, p.tb, item_cblock(it), p.na, p.nb, p.av, p.bv, p.cv, p.nz,
+                         err, smem, full, use0, use1))
+      break;
+  }
 }
 
 template <int BS>
@@ -145,6 +198,32 @@ bsm_status launch(const SymbolicResult &sym, bsm_matrix A, bsm_matrix B, double 
   return cuda_status(cudaGetLastError());
 }
 
+template <int BS>
+bsm_status launch_batched(const ProdDesc *prods, const uint64_t *items, int64_t nitems,
+                          unsigned long long *counter, unsigned *err, int ctas_per_sm,
+                          cudaStream_t s) {
+  size_t smem = (size_t)kStages * 2 * BS * BS * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    BSM_CUDA(cudaFuncSetAttribute(k_numeric_fp64_batched<BS>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  BSM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_numeric_fp64_batched<BS>, 128,
+                                                         smem));
+  if (occ < 1) occ = 1;
+  if (ctas_per_sm <= 0 || ctas_per_sm > occ) ctas_per_sm = occ;
+  int64_t grid = (int64_t)sms * ctas_per_sm;
+  if (grid > nitems) grid = nitems;
+  if (grid < 1) return BSM_OK;
+  count_launch();
+  k_numeric_fp64_batched<BS><<<(unsigned)grid, 128, smem, s>>>(prods, items, nitems, counter, err);
+  return cuda_status(cudaGetLastError());
+}
+
 }  // namespace
 
 bsm_status numeric_fp64(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, double *cvals,
@@ -155,6 +234,18 @@ bsm_status numeric_fp64(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, d
     case 16: return launch<16>(sym, A, B, cvals, nzflag, errword, s);
     case 32: return launch<32>(sym, A, B, cvals, nzflag, errword, s);
     case 64: return launch<64>(sym, A, B, cvals, nzflag, errword, s);
+  }
+  return BSM_ERR_BLOCKSIZE;
+}
+
+bsm_status numeric_fp64_batched(int bs, const ProdDesc *prods, const uint64_t *items,
+                                int64_t nitems, unsigned long long *counter, unsigned *errword,
+                                int ctas_per_sm, cudaStream_t s) {
+  if (nitems == 0) return BSM_OK;
+  switch (bs) {
+    case 16: return launch_batched<16>(prods, items, nitems, counter, errword, ctas_per_sm, s);
+    case 32: return launch_batched<32>(prods, items, nitems, counter, errword, ctas_per_sm, s);
+    case 64: return launch_batched<64>(prods, items, nitems, counter, errword, ctas_per_sm, s);
   }
   return BSM_ERR_BLOCKSIZE;
 }

@@ -45,7 +45,10 @@
 //                  C, raise the nonzero flag.
 #include <climits>
 #include <cstddef>
+#include <cstring>
+#include <vector>
 
+#include "bsm_batch.cuh"
 #include "bsm_ptx.cuh"
 
 namespace {
@@ -274,14 +277,10 @@ __device__ __forceinline__ double fixed_to_double(__int128 v, int X) {
 
 // -------------------------------------------------------- the MMA kernel
 struct SplitArgs {
-  const int32_t *seg, *ta, *tb;
-  const uint64_t *ckeys;
-  int64_t nc, nt, na, nb;  // C blocks, block products, A / B blocks
-  const uint16_t *asl, *bsl;
-  const int *rowexp, *colexp;
+  const ProdDesc *prods;     // product table (device)
+  const uint64_t *items;     // work list of (product, C block); NULL: product 0, C blocks 0..
+  int64_t nitems;
   int flushk;
-  double *cv;
-  int32_t *nz;
   unsigned *err;
   unsigned long long *work;  // chunk counter, zero at launch
 };
@@ -294,8 +293,10 @@ constexpr int kChunk = 32;   // C blocks claimed per atomic
 struct __align__(16) Meta {
   int32_t erow[64];  // row scale exponents of the C block (A rows)
   int32_t ecol[64];  // column scale exponents (B columns)
-  int64_t c;
+  int64_t c;         // C block index within its product
   uint64_t key;
+  double *cv;        // the product's C blocks
+  int32_t *nz;       // the product's nonzero flags
   int32_t nk;
   int32_t pad[3];
 };
@@ -414,8 +415,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
     bool pend[C::NST] = {};
     uint32_t ppar[C::NST] = {};
     bool stop = false;
-    auto put_meta = [&](int64_t c, uint64_t key, int nk, const int (&er)[BS / 16],
-                        const int (&ec)[BS / 16]) -> bool {
+    auto put_meta = [&](int64_t c, uint64_t key, int nk, double *cv, int32_t *nz,
+                        const int (&er)[BS / 16], const int (&ec)[BS / 16]) -> bool {
       const int m = q % kMeta;
       int okw = 1;
       if (lane == 0) {
@@ -439,6 +440,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         if (lane == 0) {
           meta[m].c = c;
           meta[m].key = key;
+          meta[m].cv = cv;
+          meta[m].nz = nz;
           meta[m].nk = nk;
           mbar_arrive(&meta_full[m]);  // release: the descriptor is visible
         }
@@ -446,47 +449,68 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
       q++;
       return okw != 0;
     };
-    auto load_exps = [&](uint64_t key, int (&er)[BS / 16], int (&ec)[BS / 16]) {
+    auto load_exps = [&](const ProdDesc *pd, uint64_t key, int (&er)[BS / 16],
+                         int (&ec)[BS / 16]) {
       const int64_t I = morton_compact(key >> 1), J = morton_compact(key);
 #pragma unroll
       for (int x = 0; x < BS / 16; x++) {
         const int idx = lane + 32 * x;
-        er[x] = idx < BS ? P.rowexp[I * BS + idx] : 0;
-        ec[x] = idx < BS ? P.colexp[J * BS + idx] : 0;
+        er[x] = idx < BS ? pd->rowexp[I * BS + idx] : 0;
+        ec[x] = idx < BS ? pd->colexp[J * BS + idx] : 0;
       }
     };
+    // window of 32 consecutive products (ta, tb) of one product table entry
+    int wp = -1;
+    int32_t tw = 0, ta_w = 0, tb_w = 0;
     while (!stop) {
       unsigned long long base = 0;
       if (lane == 0) base = atomicAdd(P.work, (unsigned long long)kChunk);
       base = __shfl_sync(0xffffffffu, base, 0);
-      if ((int64_t)base >= P.nc) break;
-      const int n = (int)min((int64_t)kChunk, P.nc - (int64_t)base);
-      const bool valid = lane < n;
-      const int32_t s0 = valid ? P.seg[base + lane] : 0;
-      const int32_t s1 = valid ? P.seg[base + lane + 1] : 0;
-      const uint64_t key = valid ? P.ckeys[base + lane] : 0;
-      const int32_t t0 = __shfl_sync(0xffffffffu, s0, 0);
-      // products of the chunk [t0, t_end) are contiguous: 32 at a time
-      int32_t tw = t0;  // first product held in (ta_w, tb_w); loads stay below nt
-      int32_t ta_w = t0 + lane < P.nt ? P.ta[t0 + lane] : 0;
-      int32_t tb_w = t0 + lane < P.nt ? P.tb[t0 + lane] : 0;
+      if ((int64_t)base >= P.nitems) break;
+      const int n = (int)min((int64_t)kChunk, P.nitems - (int64_t)base);
+      // lane i: descriptor of work item base + i
+      int pi = 0;
+      int64_t ci = 0;
+      int32_t s0 = 0, s1 = 0;
+      uint64_t key = 0;
+      if (lane < n) {
+        if (P.items) {
+          const uint64_t it = P.items[base + lane];
+          pi = (int)item_product(it);
+          ci = item_cblock(it);
+        } else {
+          ci = (int64_t)base + lane;
+        }
+        const ProdDesc *pd = &P.prods[pi];
+        s0 = pd->seg[ci];
+        s1 = pd->seg[ci + 1];
+        key = pd->ckeys[ci];
+      }
       int er[BS / 16], ec[BS / 16], ern[BS / 16], ecn[BS / 16];
-      load_exps(__shfl_sync(0xffffffffu, key, 0), er, ec);
+      load_exps(&P.prods[__shfl_sync(0xffffffffu, pi, 0)], __shfl_sync(0xffffffffu, key, 0), er, ec);
       for (int i = 0; i < n && !stop; i++) {
+        const int p = __shfl_sync(0xffffffffu, pi, i);
+        const ProdDesc *pd = &P.prods[p];
+        const int64_t c = __shfl_sync(0xffffffffu, ci, i);
         const uint64_t kk = __shfl_sync(0xffffffffu, key, i);
         const int32_t k0 = __shfl_sync(0xffffffffu, s0, i);
         const int32_t nk = __shfl_sync(0xffffffffu, s1, i) - k0;
-        if (i + 1 < n) load_exps(__shfl_sync(0xffffffffu, key, i + 1), ern, ecn);
-        if (!put_meta((int64_t)base + i, kk, nk, er, ec)) {
+        if (i + 1 < n)
+          load_exps(&P.prods[__shfl_sync(0xffffffffu, pi, i + 1)],
+                    __shfl_sync(0xffffffffu, key, i + 1), ern, ecn);
+        if (!put_meta(c, kk, nk, pd->cv, pd->nz, er, ec)) {
           stop = true;
           break;
         }
+        const uint16_t *asl = pd->asl, *bsl = pd->bsl;
+        const int64_t na = pd->na, nb = pd->nb, nt = pd->nt;
         for (int j = 0; j < nk; j++, it++) {
           const int32_t t = k0 + j;
-          if (t >= tw + 32) {  // next window of 32 products
+          if (p != wp || t < tw || t >= tw + 32) {  // refill the window (loads stay below nt)
+            wp = p;
             tw = t;
-            ta_w = tw + lane < P.nt ? P.ta[tw + lane] : 0;
-            tb_w = tw + lane < P.nt ? P.tb[tw + lane] : 0;
+            ta_w = tw + lane < nt ? pd->ta[tw + lane] : 0;
+            tb_w = tw + lane < nt ? pd->tb[tw + lane] : 0;
           }
           const int32_t aa = __shfl_sync(0xffffffffu, ta_w, t - tw);
           const int32_t bb = __shfl_sync(0xffffffffu, tb_w, t - tw);
@@ -502,14 +526,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
               uint8_t *sb = sa + C::ASLOTS * C::SLICE;
               pend[st] = true;
               ppar[st] = (it / C::NST) & 1u;
-              if (aa < 0 || aa >= P.na || bb < 0 || bb >= P.nb) {
+              if (aa < 0 || aa >= na || bb < 0 || bb >= nb) {
                 set_err(P.err, DERR_BOUNDS);  // complete the stage without data
                 mbar_arrive(&full[st]);
               } else {
                 mbar_expect_tx(&full[st], 2 * BYTES);
-                bulk_g2s(sa + (DPG - 1) * C::SLICE, P.asl + (int64_t)aa * S * BS * BS, BYTES,
+                bulk_g2s(sa + (DPG - 1) * C::SLICE, asl + (int64_t)aa * S * BS * BS, BYTES,
                          &full[st]);
-                bulk_g2s(sb, P.bsl + (int64_t)bb * S * BS * BS, BYTES, &full[st]);
+                bulk_g2s(sb, bsl + (int64_t)bb * S * BS * BS, BYTES, &full[st]);
               }
             }
           }
@@ -528,8 +552,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
     // two end markers: one for the MMA thread and each epilogue team
     if (!stop) {
       int z[BS / 16] = {};
-      put_meta(-1, 0, -1, z, z);
-      put_meta(-1, 0, -1, z, z);
+      put_meta(-1, 0, -1, nullptr, nullptr, z, z);
+      put_meta(-1, 0, -1, nullptr, nullptr, z, z);
     }
     // copies still in flight must land before the CTA exits
     if (lane == 0)
@@ -632,6 +656,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
       }
       const int nk = meta[m].nk;
       const int64_t c = meta[m].c;
+      double *const cvp = meta[m].cv;
+      int32_t *const nzp = meta[m].nz;
       if (nk < 0) break;  // end marker
       // scale exponents of this thread's output elements (thread handles
       // columns 4*(g4 % (BS/4)) .. +3 of row g4 / (BS/4), g4 = ttid + i kTeam)
@@ -689,7 +715,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         mbar_arrive(&tempty[team]);
       }
       if (named_bar_or(bar_id, kTeam, !ok || abort_flag != 0)) break;
-      double *cb = P.cv + c * (int64_t)BS * BS;
+      double *cb = cvp + c * (int64_t)BS * BS;
       bool any = false;
       constexpr int XS = kBeta * (S + 1);
 #pragma unroll
@@ -724,7 +750,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         int nzv = 0;
 #pragma unroll
         for (int w = 0; w < kTeamWarps; w++) nzv |= warp_any[team][w];
-        P.nz[c] = nzv;
+        nzp[c] = nzv;
       }
     }
   }
@@ -749,7 +775,9 @@ bsm_status launch_split(const SplitArgs &a, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t grid = a.nc < sms ? a.nc : sms;
+  const int64_t chunks = (a.nitems + kChunk - 1) / kChunk;
+  int64_t grid = chunks < sms ? chunks : sms;
+  if (grid < 1) return BSM_OK;
   count_launch();
   k_numeric_split<BS, S><<<(unsigned)grid, kThreads, C::SMEM, s>>>(a);
   return cuda_status(cudaGetLastError());
@@ -775,7 +803,7 @@ bsm_status launch_split_s(const SplitArgs &a, int slices, cudaStream_t s) {
 // Largest group of k-products whose diagonal sums stay exact (< 2^22) in the
 // FP32 accumulator: d = 0 sums terms up to 2^14; d >= 1 at most (d + 3) 2^12
 // per inner element.
-static int flush_group(int bs, int s) {
+int split_flush_group(int bs, int s) {
   int maxel = (1 << 22) >> (2 * kBeta);                  // d = 0
   int m2 = ((1 << 22) >> (2 * kBeta - 2)) / (s + 2);     // d = s - 1
   if (m2 < maxel) maxel = m2;
@@ -783,79 +811,119 @@ static int flush_group(int bs, int s) {
   return g < 1 ? 1 : g;
 }
 
-bsm_status numeric_split(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, int slices,
-                         double *cvals, int32_t *nzflag, unsigned *errword, cudaStream_t s) {
-  int bs = A->bs;
+bsm_status split_supported(int bs, int slices) {
   if (bs != 16 && bs != 32) return BSM_ERR_UNSUPPORTED;
   if (slices < 1 || slices > kMaxSlices) return BSM_ERR_INVALID_ARG;
-  if (sym.nc == 0) return BSM_OK;
-  int flushk = flush_group(bs, slices);
-  // the 32-bit diagonal accumulators hold at most 511 flushes of < 2^22
-  int *dmax = nullptr, *rowexp = nullptr, *colexp = nullptr;
+  return BSM_OK;
+}
+
+// Scale exponents and digit slices of A (row scales) and B (column scales) of
+// one product, and the longest product list of its C blocks (written to
+// *dmax_dev).  Fills the split fields of `d`; the allocations are appended to
+// `owned` for the caller to release after the numeric kernel.
+bsm_status split_prepare(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, int slices,
+                         int *dmax_dev, unsigned *errword, ProdDesc &d, std::vector<void *> &owned,
+                         cudaStream_t s) {
+  const int bs = A->bs;
+  int *rowexp = nullptr, *colexp = nullptr;
   uint16_t *asl = nullptr, *bsl = nullptr;
-  bsm_status st = BSM_OK;
-  auto cleanup = [&]() {
-    dev_free(dmax, s);
-    dev_free(rowexp, s);
-    dev_free(colexp, s);
-    dev_free(asl, s);
-    dev_free(bsl, s);
-  };
-  if ((st = dev_alloc((void **)&dmax, 16, s)) ||
-      (st = dev_alloc((void **)&rowexp, 4 * A->mb * bs, s)) ||
-      (st = dev_alloc((void **)&colexp, 4 * B->nb * bs, s)) ||
-      (st = dev_alloc((void **)&asl, (size_t)2 * slices * bs * bs * A->nblk, s)) ||
-      (st = dev_alloc((void **)&bsl, (size_t)2 * slices * bs * bs * B->nblk, s))) {
-    cleanup();
+  bsm_status st;
+  if ((st = dev_alloc((void **)&rowexp, 4 * A->mb * bs, s)) != BSM_OK) return st;
+  owned.push_back(rowexp);
+  if ((st = dev_alloc((void **)&colexp, 4 * B->nb * bs, s)) != BSM_OK) return st;
+  owned.push_back(colexp);
+  if ((st = dev_alloc((void **)&asl, (size_t)2 * slices * bs * bs * A->nblk, s)) != BSM_OK)
     return st;
-  }
-  cudaMemsetAsync(dmax, 0, 16, s);  // [0]: longest product list; [2..3]: chunk counter
+  owned.push_back(asl);
+  if ((st = dev_alloc((void **)&bsl, (size_t)2 * slices * bs * bs * B->nblk, s)) != BSM_OK)
+    return st;
+  owned.push_back(bsl);
   cudaMemsetAsync(rowexp, 0x80, 4 * A->mb * bs, s);  // 0x80808080: below any exponent
   cudaMemsetAsync(colexp, 0x80, 4 * B->nb * bs, s);
-  count_launch(3);
-  k_max_seg<<<grid_for(sym.nc, 256), 256, 0, s>>>(sym.seg, sym.nc, dmax);
-  k_row_exp<<<grid_for(A->nblk, 8), 256, 0, s>>>(A->vals, A->keys, A->nblk, bs, rowexp, errword);
-  k_col_exp<<<grid_for(B->nblk * bs, 256), 256, 0, s>>>(B->vals, B->keys, B->nblk, bs, colexp,
-                                                       errword);
+  count_launch(1);
+  if (sym.nc > 0) k_max_seg<<<grid_for(sym.nc, 256), 256, 0, s>>>(sym.seg, sym.nc, dmax_dev);
+  if (A->nblk) {
+    count_launch(1);
+    k_row_exp<<<grid_for(A->nblk, 8), 256, 0, s>>>(A->vals, A->keys, A->nblk, bs, rowexp, errword);
+  }
+  if (B->nblk) {
+    count_launch(1);
+    k_col_exp<<<grid_for(B->nblk * bs, 256), 256, 0, s>>>(B->vals, B->keys, B->nblk, bs, colexp,
+                                                         errword);
+  }
   if (bs == 16)
     launch_slices_s<16>(A, B, rowexp, colexp, asl, bsl, slices, s);
   else
     launch_slices_s<32>(A, B, rowexp, colexp, asl, bsl, slices, s);
-  int *h = (int *)host_scratch().get(16);
-  if (!h) {
-    cleanup();
-    return BSM_ERR_OOM;
-  }
-  cudaMemcpyAsync(h, dmax, 4, cudaMemcpyDeviceToHost, s);
-  cudaError_t e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) {
-    cleanup();
-    return cuda_status(e);
-  }
-  int nflmax = (h[0] + flushk - 1) / flushk;
-  if (nflmax > 511) {
-    cleanup();
-    return BSM_ERR_UNSUPPORTED;  // a C block with too many products for 32-bit diagonals
-  }
+  d.asl = asl;
+  d.bsl = bsl;
+  d.rowexp = rowexp;
+  d.colexp = colexp;
+  return cuda_status(cudaGetLastError());
+}
+
+bsm_status split_launch(int bs, int slices, const ProdDesc *prods_dev, const uint64_t *items,
+                        int64_t nitems, unsigned long long *work, unsigned *errword,
+                        cudaStream_t s) {
   SplitArgs a;
-  a.seg = sym.seg;
-  a.ta = sym.ta;
-  a.tb = sym.tb;
-  a.ckeys = sym.ckeys;
-  a.nc = sym.nc;
-  a.nt = sym.nt;
-  a.work = reinterpret_cast<unsigned long long *>(dmax + 2);
-  a.na = A->nblk;
-  a.nb = B->nblk;
-  a.asl = asl;
-  a.bsl = bsl;
-  a.rowexp = rowexp;
-  a.colexp = colexp;
-  a.flushk = flushk;
-  a.cv = cvals;
-  a.nz = nzflag;
+  a.prods = prods_dev;
+  a.items = items;
+  a.nitems = nitems;
+  a.flushk = split_flush_group(bs, slices);
   a.err = errword;
-  st = bs == 16 ? launch_split_s<16>(a, slices, s) : launch_split_s<32>(a, slices, s);
-  cleanup();  // stream-ordered: freed after the kernel
+  a.work = work;
+  return bs == 16 ? launch_split_s<16>(a, slices, s) : launch_split_s<32>(a, slices, s);
+}
+
+ProdDesc make_desc(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, double *cvals,
+                   int32_t *nz) {
+  ProdDesc d = {};
+  d.seg = sym.seg;
+  d.ta = sym.ta;
+  d.tb = sym.tb;
+  d.ckeys = sym.ckeys;
+  d.av = A->vals;
+  d.bv = B->vals;
+  d.cv = cvals;
+  d.nz = nz;
+  d.na = A->nblk;
+  d.nb = B->nblk;
+  d.nc = sym.nc;
+  d.nt = sym.nt;
+  return d;
+}
+
+bsm_status numeric_split(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, int slices,
+                         double *cvals, int32_t *nzflag, unsigned *errword, cudaStream_t s) {
+  const int bs = A->bs;
+  BSM_TRY(split_supported(bs, slices));
+  if (sym.nc == 0) return BSM_OK;
+  std::vector<void *> owned;
+  auto cleanup = [&]() {
+    for (void *p : owned) dev_free(p, s);  // stream-ordered: after the kernel
+  };
+  // scratch: [0] longest product list, [2..3] chunk counter, then the product table
+  int *scr = nullptr;
+  bsm_status st = dev_alloc((void **)&scr, 16 + sizeof(ProdDesc), s);
+  if (st != BSM_OK) return st;
+  owned.push_back(scr);
+  cudaMemsetAsync(scr, 0, 16, s);
+  ProdDesc d = make_desc(A, B, sym, cvals, nzflag);
+  st = split_prepare(A, B, sym, slices, scr, errword, d, owned, s);
+  int *h = (int *)host_scratch().get(16 + sizeof(ProdDesc));
+  if (st == BSM_OK && !h) st = BSM_ERR_OOM;
+  if (st == BSM_OK) {
+    memcpy(h + 4, &d, sizeof(ProdDesc));
+    cudaMemcpyAsync(scr + 4, h + 4, sizeof(ProdDesc), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h, scr, 4, cudaMemcpyDeviceToHost, s);
+    st = cuda_status(cudaStreamSynchronize(s));
+  }
+  // the 32-bit diagonal accumulators hold at most 511 flushes of < 2^22
+  const int flushk = split_flush_group(bs, slices);
+  if (st == BSM_OK && (h[0] + flushk - 1) / flushk > 511) st = BSM_ERR_UNSUPPORTED;
+  if (st == BSM_OK)
+    st = split_launch(bs, slices, reinterpret_cast<const ProdDesc *>(scr + 4), nullptr, sym.nc,
+                      reinterpret_cast<unsigned long long *>(scr + 2), errword, s);
+  cleanup();
   return st;
 }

@@ -160,6 +160,15 @@ bsm_status sort_keys_u64(const uint64_t *kin, uint64_t *kout, const int32_t *vin
   }, s);
 }
 
+bsm_status sort_pairs_u32_u64(const uint32_t *kin, uint32_t *kout, const uint64_t *vin,
+                              uint64_t *vout, int64_t n, cudaStream_t s) {
+  if (n <= 0) return BSM_OK;
+  count_launch(2 + 4);
+  return run_cub([&](void *t, size_t &b) {
+    return cub::DeviceRadixSort::SortPairs(t, b, kin, kout, vin, vout, n, 0, 32, s);
+  }, s);
+}
+
 extern "C" const char *bsm_status_string(bsm_status s) {
   switch (s) {
     case BSM_OK: return "ok";
