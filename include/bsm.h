@@ -41,6 +41,7 @@ extern "C" {
 #endif
 
 typedef struct bsm_matrix_s *bsm_matrix;
+typedef struct bsm_plan_s *bsm_plan;
 
 typedef enum {
   BSM_OK = 0,
@@ -64,9 +65,13 @@ typedef enum {
 /* Options of one product (NULL = all defaults: FP64). */
 typedef struct {
   int prec;   /* bsm_precision */
-  int slices; /* split modes: number of slices per operand, 0 = default (6) */
-  int flags;  /* reserved, must be 0 */
+  int slices; /* split modes: number of 7-bit slices per operand, 1..8, 0 = default (7) */
+  int flags;  /* 0, or BSM_FLAG_AUTOTUNE (bsm_plan_create only) */
 } bsm_mult_opts;
+
+/* bsm_plan_create: measure candidate launch configurations and keep the
+ * fastest (cached per product class for the process). */
+#define BSM_FLAG_AUTOTUNE 1
 
 /* Supported leaf block sides. */
 #define BSM_BS_MIN 16
@@ -185,6 +190,66 @@ bsm_status bsm_set_timing(int on);
  * Errors: BUFFER_TOO_SMALL if cap < 3 with ms != NULL.
  */
 bsm_status bsm_last_phase_ms(double *ms, int cap, int *nphase, int64_t *launches);
+
+/*
+ * bsm_update_values -- replace the block values of a handle, keeping its
+ * structure.  The COO list must name exactly the handle's stored blocks (any
+ * order; same count, same coordinates); blocks may become all-zero and stay
+ * stored.  Arguments as in bsm_build.  The caller may reuse its buffers when
+ * the call returns.
+ * Errors: INVALID_ARG (also: a different block set, misaligned device
+ * arrays), OUT_OF_RANGE, OOM, CUDA.
+ */
+bsm_status bsm_update_values(bsm_matrix M, int64_t nblk, const int32_t *brow, const int32_t *bcol,
+                             const double *vals, int on_device, void *stream);
+
+/*
+ * bsm_plan_create -- prepare repeated products C[i] = A[i]*B[i], i < n, whose
+ * operand structures stay fixed.  The symbolic phases (Algorithm 1), the C
+ * structures, a longest-first work list over all (product, C block) items and
+ * all buffers are set up once; the numeric phase (with, in split mode, the
+ * scaling and slicing of the current operand values) is captured into a CUDA
+ * graph that bsm_plan_execute replays as one persistent launch.  With
+ * BSM_FLAG_AUTOTUNE in opts->flags the plan times candidate launch
+ * configurations (work order, work items per claim, CTAs per SM) and keeps
+ * the fastest.  All operands must share one block size.  The plan reads A[i],
+ * B[i] at every execution: they must outlive it (use bsm_update_values to
+ * change their values).  One eager run of the numeric phase is part of the
+ * creation.
+ * Errors: INVALID_ARG, DIM_MISMATCH, BLOCKSIZE, OOM, CUDA, UNSUPPORTED.
+ */
+bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matrix *B,
+                           const bsm_mult_opts *opts, void *stream, bsm_plan *plan);
+
+/* bsm_plan_execute -- replay the plan's numeric phase, ordered after earlier
+ * work on `stream` and before later work on it (asynchronous).  Errors:
+ * INVALID_ARG, CUDA. */
+bsm_status bsm_plan_execute(bsm_plan plan, void *stream);
+
+/* bsm_plan_results -- new handles C[0..n-1] holding the products of the last
+ * execution (exactly-zero blocks removed).  Synchronises `stream`.  Errors:
+ * INVALID_ARG, OOM, CUDA, TIMEOUT (a bounded device wait gave up during the
+ * execution). */
+bsm_status bsm_plan_results(bsm_plan plan, bsm_matrix *C, void *stream);
+
+/* bsm_plan_info -- the launch configuration in use: order (0 longest product
+ * list first, 1 product by product in Morton order), work items per claim of
+ * the split kernel, CTAs per SM of the FP64 kernel (0 = as many as fit), and
+ * the number of (product, C block) work items.  Outputs may be NULL. */
+bsm_status bsm_plan_info(bsm_plan plan, int *order, int *chunk, int *ctas_per_sm,
+                         int64_t *nitems);
+
+/* bsm_plan_destroy -- free a plan (NULL accepted). */
+bsm_status bsm_plan_destroy(bsm_plan plan);
+
+/*
+ * bsm_selftest_wait_timeout -- failure-path check: runs one CTA that waits on
+ * a device barrier that nothing completes, bounded by limit_ms (1..5000), the
+ * same bounded-wait mechanism every kernel of this library uses.  Expected
+ * result: BSM_ERR_TIMEOUT after about limit_ms, with the CUDA context intact.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+bsm_status bsm_selftest_wait_timeout(int limit_ms, void *stream);
 
 /*
  * bsm_block_products_fp64_noalloc -- the FP64 numeric phase for a task list the

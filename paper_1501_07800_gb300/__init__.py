@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libbsm.so")
 
 BSM_FP64 = 0
 BSM_SPLIT_BF16 = 1
+BSM_FLAG_AUTOTUNE = 1
 
 STATUS = {
     0: "BSM_OK", -1: "BSM_ERR_INVALID_ARG", -2: "BSM_ERR_DIM_MISMATCH", -3: "BSM_ERR_BLOCKSIZE",
@@ -39,6 +40,13 @@ _PROTOS = {
     "bsm_last_phase_ms": (_I32, [_P, _I32, _P, _P]),
     "bsm_block_products_fp64_noalloc": (_I32, [_I32, _I64, _P, _P, _P, _P, _I64, _P, _I64, _P,
                                                 _P, _P]),
+    "bsm_selftest_wait_timeout": (_I32, [_I32, _P]),
+    "bsm_update_values": (_I32, [_P, _I64, _P, _P, _P, _I32, _P]),
+    "bsm_plan_create": (_I32, [_I32, _P, _P, _P, _P, _P]),
+    "bsm_plan_execute": (_I32, [_P, _P]),
+    "bsm_plan_results": (_I32, [_P, _P, _P]),
+    "bsm_plan_info": (_I32, [_P, _P, _P, _P, _P]),
+    "bsm_plan_destroy": (_I32, [_P]),
     "bsm_destroy": (_I32, [_P]),
     "bsm_status_string": (ctypes.c_char_p, [_I32]),
 }
@@ -271,6 +279,83 @@ def bsm_block_products_fp64_noalloc(bs: int, seg, ta, tb, a_vals, b_vals, c_vals
         int(a_vals.shape[0]), b_vals.data_ptr(), int(b_vals.shape[0]), c_vals.data_ptr(),
         nnz_out.data_ptr(), _stream_ptr(stream))
     _check(code, "bsm_block_products_fp64_noalloc")
+
+
+def bsm_selftest_wait_timeout(limit_ms: int, stream=None) -> str:
+    """Status name the bounded-wait self test returns (expected BSM_ERR_TIMEOUT)."""
+    return STATUS.get(load().bsm_selftest_wait_timeout(limit_ms, _stream_ptr(stream)), "?")
+
+
+def bsm_update_values(M: Matrix, brow, bcol, vals, stream=None):
+    """New values for exactly the blocks M stores (numpy host or torch CUDA arrays)."""
+    lib = load()
+    if _is_torch_cuda(vals):
+        import torch
+        brow = brow.to(torch.int32).contiguous()
+        bcol = bcol.to(torch.int32).contiguous()
+        vals = vals.to(torch.float64).contiguous()
+        code = lib.bsm_update_values(M.handle, int(brow.numel()), brow.data_ptr(),
+                                     bcol.data_ptr(), vals.data_ptr(), 1, _stream_ptr(stream))
+    else:
+        brow = np.ascontiguousarray(brow, np.int32)
+        bcol = np.ascontiguousarray(bcol, np.int32)
+        vals = np.ascontiguousarray(vals, np.float64)
+        code = lib.bsm_update_values(M.handle, int(brow.shape[0]), brow.ctypes.data,
+                                     bcol.ctypes.data, vals.ctypes.data, 0, _stream_ptr(stream))
+    _check(code, "bsm_update_values")
+
+
+class Plan:
+    """Owning wrapper of a bsm_plan (freed with bsm_plan_destroy).  Keeps the
+    operand handles alive as long as the plan."""
+
+    def __init__(self, handle: int, As, Bs):
+        self.handle = handle
+        self._operands = (list(As), list(Bs))
+        self.n = len(As)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.bsm_plan_destroy(h)
+            self.handle = None
+
+
+def bsm_plan_create(As, Bs, prec: int = BSM_FP64, slices: int = 0, autotune: bool = False,
+                    stream=None) -> Plan:
+    lib = load()
+    n = len(As)
+    ha = (ctypes.c_void_p * max(n, 1))(*[a.handle for a in As])
+    hb = (ctypes.c_void_p * max(n, 1))(*[b.handle for b in Bs])
+    opts = bsm_mult_opts(prec, slices, BSM_FLAG_AUTOTUNE if autotune else 0)
+    out = ctypes.c_void_p()
+    code = lib.bsm_plan_create(n, ha, hb, ctypes.byref(opts), _stream_ptr(stream),
+                               ctypes.byref(out))
+    _check(code, "bsm_plan_create")
+    return Plan(out.value, As, Bs)
+
+
+def bsm_plan_execute(plan: Plan, stream=None):
+    _check(load().bsm_plan_execute(plan.handle, _stream_ptr(stream)), "bsm_plan_execute")
+
+
+def bsm_plan_results(plan: Plan, stream=None):
+    hc = (ctypes.c_void_p * max(plan.n, 1))()
+    _check(load().bsm_plan_results(plan.handle, hc, _stream_ptr(stream)), "bsm_plan_results")
+    return [Matrix(hc[i]) for i in range(plan.n)]
+
+
+def bsm_plan_info(plan: Plan):
+    """(order, chunk, ctas_per_sm, work items)."""
+    o, c, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    n = ctypes.c_int64()
+    _check(load().bsm_plan_info(plan.handle, ctypes.byref(o), ctypes.byref(c), ctypes.byref(k),
+                                ctypes.byref(n)), "bsm_plan_info")
+    return o.value, c.value, k.value, n.value
+
+
+def bsm_plan_destroy(plan: Plan):
+    plan.__del__()
 
 
 def bsm_destroy(M: Matrix):

@@ -143,7 +143,22 @@ bsm_status split_prepare(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, 
                          cudaStream_t s);
 bsm_status split_launch(int bs, int slices, const ProdDesc *prods_dev, const uint64_t *items,
                         int64_t nitems, unsigned long long *work, unsigned *errword,
-                        cudaStream_t s);
+                        cudaStream_t s, int chunk = 32);
+bsm_status split_alloc(bsm_matrix A, bsm_matrix B, int slices, ProdDesc &d,
+                       std::vector<void *> &owned, cudaStream_t s);
+bsm_status split_compute(bsm_matrix A, bsm_matrix B, int slices, const ProdDesc &d,
+                         unsigned *errword, cudaStream_t s);
+void launch_max_seg(const SymbolicResult &sym, int *dmax_dev, cudaStream_t s);
+
+// C assembly from a numeric result: zero removal and level build.
+// finish_product takes ownership of sym->ckeys and cvals; finish_product_copy
+// leaves both untouched and copies what it keeps.
+bsm_status finish_product(bsm_matrix C, SymbolicResult *sym, double *cvals, int32_t *nz,
+                          unsigned *err, cudaStream_t s);
+bsm_status finish_product_copy(bsm_matrix C, const SymbolicResult &sym, const double *cvals,
+                               const int32_t *nz, unsigned *err, cudaStream_t s);
+bsm_status check_pair(bsm_matrix A, bsm_matrix B);
+bsm_status check_opts(const bsm_mult_opts *o, int *prec, int *slices);
 
 // Handle shells for results (bsm_tree.cu).
 bsm_matrix new_matrix_shell(int64_t nrows, int64_t ncols, int bs, int L);

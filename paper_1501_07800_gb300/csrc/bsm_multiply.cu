@@ -17,6 +17,8 @@ __global__ void k_compact_c(const int32_t *__restrict__ nz, const int32_t *__res
 
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+}  // namespace
+
 bsm_status check_pair(bsm_matrix A, bsm_matrix B) {
   if (!A || !B) return BSM_ERR_INVALID_ARG;
   if (A->ncols != B->nrows) return BSM_ERR_DIM_MISMATCH;
@@ -37,12 +39,10 @@ bsm_status check_opts(const bsm_mult_opts *o, int *prec, int *slices) {
   return BSM_OK;
 }
 
-}  // namespace
-
 // Assembles C from the numeric result: drops exactly-zero blocks and builds
 // the level arrays.  Takes ownership of sym->ckeys and cvals.
-static bsm_status finish_product(bsm_matrix C, SymbolicResult *sym, double *cvals, int32_t *nz,
-                                 unsigned *err, cudaStream_t s) {
+bsm_status finish_product(bsm_matrix C, SymbolicResult *sym, double *cvals, int32_t *nz,
+                          unsigned *err, cudaStream_t s) {
   int64_t nc = sym->nc;
   int bs = C->bs;
   int32_t *pos = nullptr;
@@ -95,6 +95,54 @@ static bsm_status finish_product(bsm_matrix C, SymbolicResult *sym, double *cval
   }
   dev_free(pos, s);
   C->nblk = nkeep;
+  return build_levels(C, s);
+}
+
+bsm_status finish_product_copy(bsm_matrix C, const SymbolicResult &sym, const double *cvals,
+                               const int32_t *nz, unsigned *err, cudaStream_t s) {
+  const int64_t nc = sym.nc;
+  const int bs = C->bs;
+  if (nc == 0) return build_levels(C, s);
+  int32_t *pos = nullptr;
+  bsm_status st = dev_alloc((void **)&pos, 4 * (nc + 1), s);
+  if (st != BSM_OK) return st;
+  st = scan_exclusive_i32(nz, pos, nc, s);
+  int32_t *h = (int32_t *)host_scratch().get(16);
+  if (st == BSM_OK && !h) st = BSM_ERR_OOM;
+  if (st == BSM_OK) {
+    cudaMemcpyAsync(h, pos + nc - 1, 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h + 1, nz + nc - 1, 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h + 2, err, 4, cudaMemcpyDeviceToHost, s);
+    st = cuda_status(cudaStreamSynchronize(s));
+  }
+  if (st == BSM_OK && h[2] == DERR_TIMEOUT) st = BSM_ERR_TIMEOUT;
+  if (st == BSM_OK && h[2] != DERR_NONE) st = BSM_ERR_CUDA;
+  const int64_t nkeep = st == BSM_OK ? (int64_t)h[0] + h[1] : 0;
+  uint64_t *okeys = nullptr;
+  double *ovals = nullptr;
+  int32_t *idx = nullptr;
+  if (st == BSM_OK && ((st = dev_alloc((void **)&okeys, 8 * (nkeep > 0 ? nkeep : 1), s)) ||
+                       (st = dev_alloc((void **)&ovals,
+                                       sizeof(double) * bs * bs * (nkeep > 0 ? nkeep : 1), s)) ||
+                       (st = dev_alloc((void **)&idx, 4 * (nkeep > 0 ? nkeep : 1), s)))) {
+    dev_free(okeys, s);
+    dev_free(ovals, s);
+    okeys = nullptr;
+    ovals = nullptr;
+  }
+  if (st == BSM_OK) {
+    count_launch();
+    k_compact_c<<<grid_for(nc, 256), 256, 0, s>>>(nz, pos, nc, sym.ckeys, okeys, idx);
+    launch_gather_blocks(cvals, idx, ovals, nkeep, bs, s);
+    C->keys = okeys;
+    C->vals = ovals;
+    C->owned.push_back(okeys);
+    C->owned.push_back(ovals);
+    C->nblk = nkeep;
+  }
+  dev_free(idx, s);
+  dev_free(pos, s);
+  if (st != BSM_OK) return st;
   return build_levels(C, s);
 }
 
@@ -342,7 +390,7 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
       if (prec == BSM_FP64)
         st = numeric_fp64_batched(bs, table, v1, total, counter, err, 0, s);
       else
-        st = split_launch(bs, slices, table, v1, total, counter, err, s);
+        st = split_launch(bs, slices, table, v1, total, counter, err, s, 32);
     }
   }
   timer.mark(s);

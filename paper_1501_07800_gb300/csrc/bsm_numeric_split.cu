@@ -283,8 +283,9 @@ struct SplitArgs {
   int flushk;
   unsigned *err;
   unsigned long long *work;  // chunk counter, zero at launch
+  int chunk;                 // work items claimed per atomic (1..32)
 };
-constexpr int kChunk = 32;   // C blocks claimed per atomic
+constexpr int kChunk = 32;   // most work items claimed per atomic
 
 // Per-C-block work descriptor handed from the producer warp to the MMA thread
 // and the epilogue through a shared-memory ring.
@@ -464,10 +465,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
     int32_t tw = 0, ta_w = 0, tb_w = 0;
     while (!stop) {
       unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(P.work, (unsigned long long)kChunk);
+      if (lane == 0) base = atomicAdd(P.work, (unsigned long long)P.chunk);
       base = __shfl_sync(0xffffffffu, base, 0);
       if ((int64_t)base >= P.nitems) break;
-      const int n = (int)min((int64_t)kChunk, P.nitems - (int64_t)base);
+      const int n = (int)min((int64_t)P.chunk, P.nitems - (int64_t)base);
       // lane i: descriptor of work item base + i
       int pi = 0;
       int64_t ci = 0;
@@ -775,7 +776,7 @@ bsm_status launch_split(const SplitArgs &a, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t chunks = (a.nitems + kChunk - 1) / kChunk;
+  const int64_t chunks = (a.nitems + a.chunk - 1) / a.chunk;
   int64_t grid = chunks < sms ? chunks : sms;
   if (grid < 1) return BSM_OK;
   count_launch();
@@ -817,13 +818,11 @@ bsm_status split_supported(int bs, int slices) {
   return BSM_OK;
 }
 
-// Scale exponents and digit slices of A (row scales) and B (column scales) of
-// one product, and the longest product list of its C blocks (written to
-// *dmax_dev).  Fills the split fields of `d`; the allocations are appended to
-// `owned` for the caller to release after the numeric kernel.
-bsm_status split_prepare(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, int slices,
-                         int *dmax_dev, unsigned *errword, ProdDesc &d, std::vector<void *> &owned,
-                         cudaStream_t s) {
+// Buffers of the split form of one product: scale exponents of A's rows and
+// B's columns and the digit slices of A and B.  Fills the split fields of `d`;
+// the allocations are appended to `owned` for the caller to release.
+bsm_status split_alloc(bsm_matrix A, bsm_matrix B, int slices, ProdDesc &d,
+                       std::vector<void *> &owned, cudaStream_t s) {
   const int bs = A->bs;
   int *rowexp = nullptr, *colexp = nullptr;
   uint16_t *asl = nullptr, *bsl = nullptr;
@@ -838,10 +837,21 @@ bsm_status split_prepare(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, 
   if ((st = dev_alloc((void **)&bsl, (size_t)2 * slices * bs * bs * B->nblk, s)) != BSM_OK)
     return st;
   owned.push_back(bsl);
+  d.asl = asl;
+  d.bsl = bsl;
+  d.rowexp = rowexp;
+  d.colexp = colexp;
+  return BSM_OK;
+}
+
+// Computes the exponents and slices into the buffers of `d` (no allocation;
+// may be captured in a CUDA graph).
+bsm_status split_compute(bsm_matrix A, bsm_matrix B, int slices, const ProdDesc &d,
+                         unsigned *errword, cudaStream_t s) {
+  const int bs = A->bs;
+  int *rowexp = const_cast<int *>(d.rowexp), *colexp = const_cast<int *>(d.colexp);
   cudaMemsetAsync(rowexp, 0x80, 4 * A->mb * bs, s);  // 0x80808080: below any exponent
   cudaMemsetAsync(colexp, 0x80, 4 * B->nb * bs, s);
-  count_launch(1);
-  if (sym.nc > 0) k_max_seg<<<grid_for(sym.nc, 256), 256, 0, s>>>(sym.seg, sym.nc, dmax_dev);
   if (A->nblk) {
     count_launch(1);
     k_row_exp<<<grid_for(A->nblk, 8), 256, 0, s>>>(A->vals, A->keys, A->nblk, bs, rowexp, errword);
@@ -851,21 +861,34 @@ bsm_status split_prepare(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, 
     k_col_exp<<<grid_for(B->nblk * bs, 256), 256, 0, s>>>(B->vals, B->keys, B->nblk, bs, colexp,
                                                          errword);
   }
+  uint16_t *asl = const_cast<uint16_t *>(d.asl), *bsl = const_cast<uint16_t *>(d.bsl);
   if (bs == 16)
     launch_slices_s<16>(A, B, rowexp, colexp, asl, bsl, slices, s);
   else
     launch_slices_s<32>(A, B, rowexp, colexp, asl, bsl, slices, s);
-  d.asl = asl;
-  d.bsl = bsl;
-  d.rowexp = rowexp;
-  d.colexp = colexp;
   return cuda_status(cudaGetLastError());
+}
+
+// Longest product list of a task list, atomically maxed into *dmax_dev.
+void launch_max_seg(const SymbolicResult &sym, int *dmax_dev, cudaStream_t s) {
+  if (sym.nc == 0) return;
+  count_launch(1);
+  k_max_seg<<<grid_for(sym.nc, 256), 256, 0, s>>>(sym.seg, sym.nc, dmax_dev);
+}
+
+bsm_status split_prepare(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, int slices,
+                         int *dmax_dev, unsigned *errword, ProdDesc &d, std::vector<void *> &owned,
+                         cudaStream_t s) {
+  BSM_TRY(split_alloc(A, B, slices, d, owned, s));
+  launch_max_seg(sym, dmax_dev, s);
+  return split_compute(A, B, slices, d, errword, s);
 }
 
 bsm_status split_launch(int bs, int slices, const ProdDesc *prods_dev, const uint64_t *items,
                         int64_t nitems, unsigned long long *work, unsigned *errword,
-                        cudaStream_t s) {
+                        cudaStream_t s, int chunk) {
   SplitArgs a;
+  a.chunk = chunk < 1 ? 1 : (chunk > kChunk ? kChunk : chunk);
   a.prods = prods_dev;
   a.items = items;
   a.nitems = nitems;

@@ -1,0 +1,363 @@
+// Plans: repeated batched products with fixed operand structures, replayed
+// from a CUDA graph, with launch parameters picked by a measuring autotuner.
+//
+// bsm_plan_create does everything that depends only on the structures of the
+// operands once: the symbolic phase of every product (Algorithm 1 over the
+// quadtrees), C's structures, the global work list and every buffer.  It then
+// captures the numeric phase -- for split precision the scaling and slicing
+// kernels too, because they depend on the values -- into a CUDA graph.
+// bsm_plan_execute replays the graph; after bsm_update_values changed the
+// values of an operand (same blocks), a replay recomputes C from the new values
+// with no symbolic work and no host round trips.
+//
+// Autotuning: for a product class (precision, block size, slice count, number
+// of products, and the magnitudes of the C-block count and of the mean and
+// largest product-list length) the tuner times each candidate launch
+// configuration -- work order (longest product list first, or product by
+// product in Morton order), work items claimed per atomic (split kernel) and
+// CTAs per SM (FP64 kernel) -- and caches the fastest for the process.
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "bsm_internal.cuh"
+
+struct bsm_plan_s {
+  int n = 0, prec = BSM_FP64, slices = 0, bs = 0, device = 0;
+  std::vector<bsm_matrix> A, B;  // not owned; must outlive the plan
+  std::vector<SymbolicResult> sym;
+  std::vector<double *> cv;
+  std::vector<int32_t *> nz;
+  std::vector<ProdDesc> desc;
+  int64_t nitems = 0;
+  uint64_t *items_lpt = nullptr, *items_morton = nullptr;
+  ProdDesc *table = nullptr;
+  int *scr = nullptr;  // [0] longest product list, [2..3] work counter
+  unsigned *err = nullptr;
+  std::vector<void *> owned;
+  // chosen configuration
+  int order = 0;  // 0: longest first, 1: product-major Morton
+  int chunk = 32, ctas_per_sm = 0;
+  bool tuned = false;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+__global__ void k_plan_items(const int32_t *__restrict__ seg, int64_t nc, uint32_t p,
+                             uint32_t *__restrict__ keys, uint64_t *__restrict__ items) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  keys[c] = 0xFFFFFFFFu - (uint32_t)(seg[c + 1] - seg[c]);
+  items[c] = make_item(p, (uint64_t)c);
+}
+
+inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+struct TuneKey {
+  int prec, bs, slices, n, lg_nc, lg_mean, lg_max;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(prec, bs, slices, n, lg_nc, lg_mean, lg_max) <
+           std::tie(o.prec, o.bs, o.slices, o.n, o.lg_nc, o.lg_mean, o.lg_max);
+  }
+};
+struct TuneVal {
+  int order, chunk, ctas;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+int ilog2(int64_t x) {
+  int l = 0;
+  while (x > 1) {
+    x >>= 1;
+    l++;
+  }
+  return l;
+}
+
+// The numeric phase of the plan with a given configuration (no allocation:
+// it may be captured).
+bsm_status enqueue_numeric(bsm_plan P, int order, int chunk, int ctas, cudaStream_t s) {
+  cudaMemsetAsync(P->scr + 2, 0, 8, s);  // work counter
+  cudaMemsetAsync(P->err, 0, sizeof(unsigned), s);
+  const uint64_t *items = order == 0 ? P->items_lpt : P->items_morton;
+  unsigned long long *counter = reinterpret_cast<unsigned long long *>(P->scr + 2);
+  if (P->prec == BSM_FP64)
+    return numeric_fp64_batched(P->bs, P->table, items, P->nitems, counter, P->err, ctas, s);
+  for (int i = 0; i < P->n; i++)
+    if (P->sym[i].nc > 0) BSM_TRY(split_compute(P->A[i], P->B[i], P->slices, P->desc[i], P->err, s));
+  return split_launch(P->bs, P->slices, P->table, items, P->nitems, counter, P->err, s, chunk);
+}
+
+void destroy_plan(bsm_plan P) {
+  if (!P) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != P->device) cudaSetDevice(P->device);
+  cudaStream_t s = P->stream;
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  for (auto &sy : P->sym) free_symbolic(&sy, s);
+  for (double *p : P->cv) dev_free(p, s);
+  for (int32_t *p : P->nz) dev_free(p, s);
+  for (void *p : P->owned) dev_free(p, s);
+  dev_free(P->err, s);
+  if (s) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  if (P->ev_in) cudaEventDestroy(P->ev_in);
+  if (P->ev_out) cudaEventDestroy(P->ev_out);
+  if (cur != P->device) cudaSetDevice(cur);
+  delete P;
+}
+
+// Times one configuration (median of 3 runs after one warm-up), in ms.
+float time_config(bsm_plan P, int order, int chunk, int ctas) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best = 1e30f;
+  enqueue_numeric(P, order, chunk, ctas, P->stream);
+  for (int r = 0; r < 3; r++) {
+    cudaEventRecord(a, P->stream);
+    if (enqueue_numeric(P, order, chunk, ctas, P->stream) != BSM_OK) break;
+    cudaEventRecord(b, P->stream);
+    if (cudaEventSynchronize(b) != cudaSuccess) break;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best) best = ms;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
+bsm_status autotune(bsm_plan P) {
+  int64_t tot_nt = 0, max_nk = 0;
+  for (int i = 0; i < P->n; i++) tot_nt += P->sym[i].nt;
+  int *h = (int *)host_scratch().get(16);
+  if (!h) return BSM_ERR_OOM;
+  cudaMemsetAsync(P->scr, 0, 4, P->stream);
+  for (int i = 0; i < P->n; i++) launch_max_seg(P->sym[i], P->scr, P->stream);
+  cudaMemcpyAsync(h, P->scr, 4, cudaMemcpyDeviceToHost, P->stream);
+  BSM_CUDA(cudaStreamSynchronize(P->stream));
+  max_nk = h[0];
+  TuneKey key{P->prec, P->bs, P->slices, P->n, ilog2(P->nitems),
+              ilog2(P->nitems ? tot_nt / P->nitems : 0), ilog2(max_nk)};
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      P->order = it->second.order;
+      P->chunk = it->second.chunk;
+      P->ctas_per_sm = it->second.ctas;
+      P->tuned = true;
+      return BSM_OK;
+    }
+  }
+  std::vector<TuneVal> cands;
+  for (int order : {0, 1}) {
+    if (P->prec == BSM_FP64)
+      for (int ctas : {0, 4, 2, 1}) cands.push_back({order, 32, ctas});
+    else
+      for (int chunk : {32, 8}) cands.push_back({order, chunk, 0});
+  }
+  float best = 1e30f;
+  TuneVal pick = cands[0];
+  for (const TuneVal &c : cands) {
+    float ms = time_config(P, c.order, c.chunk, c.ctas);
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  P->order = pick.order;
+  P->chunk = pick.chunk;
+  P->ctas_per_sm = pick.ctas;
+  P->tuned = true;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune_cache[key] = pick;
+  return BSM_OK;
+}
+
+}  // namespace
+
+extern "C" bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matrix *B,
+                                      const bsm_mult_opts *opts, void *stream, bsm_plan *out) {
+  if (!out) return BSM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 1 || !A || !B) return BSM_ERR_INVALID_ARG;
+  for (int i = 0; i < n; i++) BSM_TRY(check_pair(A[i], B[i]));
+  int tune = opts ? (opts->flags & BSM_FLAG_AUTOTUNE) : 0;
+  bsm_mult_opts o = opts ? *opts : bsm_mult_opts{BSM_FP64, 0, 0};
+  o.flags &= ~BSM_FLAG_AUTOTUNE;
+  int prec, slices;
+  BSM_TRY(check_opts(&o, &prec, &slices));
+  const int bs = A[0]->bs;
+  for (int i = 0; i < n; i++)
+    if (A[i]->bs != bs) return BSM_ERR_BLOCKSIZE;  // one block size per plan
+  if (prec != BSM_FP64) BSM_TRY(split_supported(bs, slices));
+
+  bsm_plan P = new bsm_plan_s();
+  cudaGetDevice(&P->device);
+  P->n = n;
+  P->prec = prec;
+  P->slices = slices;
+  P->bs = bs;
+  P->A.assign(A, A + n);
+  P->B.assign(B, B + n);
+  P->sym.resize(n);
+  P->cv.assign(n, nullptr);
+  P->nz.assign(n, nullptr);
+  P->desc.resize(n);
+  bsm_status st = cuda_status(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+  if (st == BSM_OK) st = cuda_status(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
+  if (st == BSM_OK) st = cuda_status(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));
+  cudaStream_t s = P->stream;
+  // order the plan's stream after the caller's work on the operands
+  if (st == BSM_OK) {
+    cudaEventRecord(P->ev_in, (cudaStream_t)stream);
+    cudaStreamWaitEvent(s, P->ev_in, 0);
+  }
+  for (int i = 0; i < n && st == BSM_OK; i++) {
+    st = symbolic_multiply(A[i], B[i], &P->sym[i], s);
+    P->nitems += P->sym[i].nc;
+  }
+  if (st == BSM_OK && P->nitems > 0xFFFFFFFFFFll) st = BSM_ERR_UNSUPPORTED;
+  if (st == BSM_OK) st = dev_alloc((void **)&P->err, sizeof(unsigned), s);
+  for (int i = 0; i < n && st == BSM_OK; i++) {
+    const int64_t nc = P->sym[i].nc;
+    if (nc == 0) continue;
+    if ((st = dev_alloc((void **)&P->cv[i], sizeof(double) * bs * bs * nc, s)) != BSM_OK) break;
+    st = dev_alloc((void **)&P->nz[i], 4 * nc, s);
+  }
+  uint32_t *k0 = nullptr, *k1 = nullptr;
+  const int64_t tot = P->nitems > 0 ? P->nitems : 1;
+  auto grab = [&](void **p, size_t bytes) {
+    if (st != BSM_OK) return;
+    st = dev_alloc(p, bytes, s);
+    if (st == BSM_OK) P->owned.push_back(*p);
+  };
+  grab((void **)&k0, 4 * tot);
+  grab((void **)&k1, 4 * tot);
+  grab((void **)&P->items_morton, 8 * tot);
+  grab((void **)&P->items_lpt, 8 * tot);
+  grab((void **)&P->table, sizeof(ProdDesc) * n);
+  grab((void **)&P->scr, 16);
+  if (st == BSM_OK) {
+    cudaMemsetAsync(P->scr, 0, 16, s);
+    int64_t off = 0;
+    for (int i = 0; i < n; i++) {
+      if (P->sym[i].nc == 0) continue;
+      count_launch();
+      k_plan_items<<<grid_for(P->sym[i].nc, 256), 256, 0, s>>>(P->sym[i].seg, P->sym[i].nc,
+                                                               (uint32_t)i, k0 + off,
+                                                               P->items_morton + off);
+      off += P->sym[i].nc;
+    }
+    st = sort_pairs_u32_u64(k0, k1, P->items_morton, P->items_lpt, P->nitems, s);
+  }
+  for (int i = 0; i < n && st == BSM_OK; i++) {
+    P->desc[i] = make_desc(A[i], B[i], P->sym[i], P->cv[i], P->nz[i]);
+    if (prec != BSM_FP64 && P->sym[i].nc > 0) {
+      st = split_alloc(A[i], B[i], slices, P->desc[i], P->owned, s);
+      launch_max_seg(P->sym[i], P->scr, s);
+    }
+  }
+  if (st == BSM_OK) {
+    void *hp = host_scratch().get(sizeof(ProdDesc) * n + 16);
+    if (!hp) st = BSM_ERR_OOM;
+    if (st == BSM_OK) {
+      memcpy(hp, P->desc.data(), sizeof(ProdDesc) * n);
+      cudaMemcpyAsync(P->table, hp, sizeof(ProdDesc) * n, cudaMemcpyHostToDevice, s);
+      int *hm = (int *)((char *)hp + sizeof(ProdDesc) * n);
+      cudaMemcpyAsync(hm, P->scr, 4, cudaMemcpyDeviceToHost, s);
+      st = cuda_status(cudaStreamSynchronize(s));
+      if (st == BSM_OK && prec != BSM_FP64) {
+        const int flushk = split_flush_group(bs, slices);
+        if ((hm[0] + flushk - 1) / flushk > 511) st = BSM_ERR_UNSUPPORTED;
+      }
+    }
+  }
+  if (st == BSM_OK && tune && P->nitems > 0) st = autotune(P);
+  // one eager run: kernel attributes are set up outside the capture, and the
+  // chosen configuration is known to launch
+  if (st == BSM_OK && P->nitems > 0) {
+    st = enqueue_numeric(P, P->order, P->chunk, P->ctas_per_sm, s);
+    if (st == BSM_OK) st = cuda_status(cudaStreamSynchronize(s));
+  }
+  // capture the numeric phase
+  if (st == BSM_OK) {
+    st = cuda_status(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    if (st == BSM_OK) {
+      bsm_status st2 = P->nitems > 0 ? enqueue_numeric(P, P->order, P->chunk, P->ctas_per_sm, s)
+                                     : cuda_status(cudaMemsetAsync(P->err, 0, 4, s));
+      cudaError_t e = cudaStreamEndCapture(s, &P->graph);
+      st = st2 != BSM_OK ? st2 : cuda_status(e);
+    }
+    if (st == BSM_OK) st = cuda_status(cudaGraphInstantiate(&P->exec, P->graph, 0));
+  }
+  if (st != BSM_OK) {
+    destroy_plan(P);
+    return st;
+  }
+  *out = P;
+  return BSM_OK;
+}
+
+extern "C" bsm_status bsm_plan_execute(bsm_plan P, void *stream) {
+  if (!P) return BSM_ERR_INVALID_ARG;
+  cudaStream_t cs = (cudaStream_t)stream;
+  BSM_CUDA(cudaEventRecord(P->ev_in, cs));
+  BSM_CUDA(cudaStreamWaitEvent(P->stream, P->ev_in, 0));
+  BSM_CUDA(cudaGraphLaunch(P->exec, P->stream));
+  BSM_CUDA(cudaEventRecord(P->ev_out, P->stream));
+  BSM_CUDA(cudaStreamWaitEvent(cs, P->ev_out, 0));
+  return BSM_OK;
+}
+
+extern "C" bsm_status bsm_plan_results(bsm_plan P, bsm_matrix *C, void *stream) {
+  if (!P || !C) return BSM_ERR_INVALID_ARG;
+  for (int i = 0; i < P->n; i++) C[i] = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  bsm_status st = BSM_OK;
+  for (int i = 0; i < P->n && st == BSM_OK; i++) {
+    bsm_matrix a = P->A[i], b = P->B[i];
+    int64_t side = a->mb > b->nb ? a->mb : b->nb;
+    bsm_matrix Ci = new_matrix_shell(a->nrows, b->ncols, P->bs, ceil_log2_i64(side < 1 ? 1 : side));
+    st = finish_product_copy(Ci, P->sym[i], P->cv[i], P->nz[i], P->err, s);
+    if (st != BSM_OK) {
+      free_matrix_shell(Ci, s);
+      break;
+    }
+    C[i] = Ci;
+  }
+  if (st != BSM_OK)
+    for (int i = 0; i < P->n; i++) {
+      bsm_destroy(C[i]);
+      C[i] = nullptr;
+    }
+  return st;
+}
+
+extern "C" bsm_status bsm_plan_info(bsm_plan P, int *order, int *chunk, int *ctas_per_sm,
+                                    int64_t *nitems) {
+  if (!P) return BSM_ERR_INVALID_ARG;
+  if (order) *order = P->order;
+  if (chunk) *chunk = P->chunk;
+  if (ctas_per_sm) *ctas_per_sm = P->ctas_per_sm;
+  if (nitems) *nitems = P->nitems;
+  return BSM_OK;
+}
+
+extern "C" bsm_status bsm_plan_destroy(bsm_plan P) {
+  destroy_plan(P);
+  return BSM_OK;
+}

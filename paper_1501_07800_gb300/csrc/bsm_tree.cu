@@ -130,6 +130,29 @@ __global__ void k_rowmajor_coords(const uint64_t *__restrict__ rm, int64_t off, 
 
 static inline unsigned nblocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Keys of a COO list in (I, J) -> Morton form, with range checks.
+__global__ void k_coo_keys(const int32_t *__restrict__ brow, const int32_t *__restrict__ bcol,
+                           int64_t n, int64_t mb, int64_t nb, uint64_t *__restrict__ keys,
+                           int32_t *__restrict__ idx, unsigned *__restrict__ err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t I = brow[i], J = bcol[i];
+  if (I < 0 || I >= mb || J < 0 || J >= nb) {
+    atomicCAS(err, DERR_NONE, DERR_OUT_OF_RANGE);
+    I = 0;
+    J = 0;
+  }
+  keys[i] = morton_key((uint64_t)I, (uint64_t)J);
+  idx[i] = (int32_t)i;
+}
+
+// Sorted update keys must equal the handle's keys one for one.
+__global__ void k_keys_equal(const uint64_t *__restrict__ a, const uint64_t *__restrict__ b,
+                             int64_t n, unsigned *__restrict__ err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && a[i] != b[i]) atomicCAS(err, DERR_NONE, DERR_BOUNDS);
+}
+
 // --------------------------------------------------------------- host side
 bsm_status build_levels(bsm_matrix M, cudaStream_t s) {
   for (int h = 0; h <= BSM_MAXH; h++) M->nlev[h] = 0;
@@ -409,6 +432,79 @@ extern "C" bsm_status bsm_to_blocks(bsm_matrix M, int64_t *nblk_inout, int32_t *
   dev_free(crd, s);
   cleanup();
   return cuda_status(e == cudaSuccess ? cudaGetLastError() : e);
+}
+
+extern "C" bsm_status bsm_update_values(bsm_matrix M, int64_t nblk, const int32_t *brow,
+                                        const int32_t *bcol, const double *vals, int on_device,
+                                        void *stream) {
+  if (!M || nblk < 0 || (on_device != 0 && on_device != 1)) return BSM_ERR_INVALID_ARG;
+  if (nblk != M->nblk) return BSM_ERR_INVALID_ARG;  // the block set must be the same
+  if (nblk == 0) return BSM_OK;
+  if (!brow || !bcol || !vals) return BSM_ERR_INVALID_ARG;
+  if (on_device && (((uintptr_t)vals & 15) || ((uintptr_t)brow & 3) || ((uintptr_t)bcol & 3)))
+    return BSM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int bs = M->bs;
+  const size_t vb = sizeof(double) * bs * bs * nblk;
+  int32_t *dr = nullptr, *dc = nullptr, *idx = nullptr, *sidx = nullptr;
+  double *dv = nullptr;
+  uint64_t *keys = nullptr, *skeys = nullptr;
+  unsigned *err = nullptr;
+  bsm_status st;
+  auto cleanup = [&]() {
+    if (!on_device) {
+      dev_free(dr, s);
+      dev_free(dc, s);
+      dev_free(dv, s);
+    }
+    dev_free(idx, s);
+    dev_free(sidx, s);
+    dev_free(keys, s);
+    dev_free(skeys, s);
+    dev_free(err, s);
+  };
+  if (on_device) {
+    dr = const_cast<int32_t *>(brow);
+    dc = const_cast<int32_t *>(bcol);
+    dv = const_cast<double *>(vals);
+  } else if ((st = dev_alloc((void **)&dr, 4 * nblk, s)) ||
+             (st = dev_alloc((void **)&dc, 4 * nblk, s)) || (st = dev_alloc((void **)&dv, vb, s))) {
+    cleanup();
+    return st;
+  } else {
+    cudaMemcpyAsync(dr, brow, 4 * nblk, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dc, bcol, 4 * nblk, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dv, vals, vb, cudaMemcpyHostToDevice, s);
+  }
+  if ((st = dev_alloc((void **)&idx, 4 * nblk, s)) || (st = dev_alloc((void **)&sidx, 4 * nblk, s)) ||
+      (st = dev_alloc((void **)&keys, 8 * nblk, s)) ||
+      (st = dev_alloc((void **)&skeys, 8 * nblk, s)) ||
+      (st = dev_alloc((void **)&err, sizeof(unsigned), s))) {
+    cleanup();
+    return st;
+  }
+  cudaMemsetAsync(err, 0, sizeof(unsigned), s);
+  count_launch();
+  k_coo_keys<<<nblocks_for(nblk, 256), 256, 0, s>>>(dr, dc, nblk, M->mb, M->nb, keys, idx, err);
+  st = sort_keys_u64(keys, skeys, idx, sidx, nblk, 2 * M->L, s);
+  if (st == BSM_OK) {
+    count_launch();
+    k_keys_equal<<<nblocks_for(nblk, 256), 256, 0, s>>>(skeys, M->keys, nblk, err);
+    unsigned *h = (unsigned *)host_scratch().get(16);
+    if (!h) st = BSM_ERR_OOM;
+    if (st == BSM_OK) {
+      cudaMemcpyAsync(h, err, 4, cudaMemcpyDeviceToHost, s);
+      st = cuda_status(cudaStreamSynchronize(s));
+    }
+    if (st == BSM_OK && h[0] == DERR_OUT_OF_RANGE) st = BSM_ERR_OUT_OF_RANGE;
+    if (st == BSM_OK && h[0] != DERR_NONE) st = BSM_ERR_INVALID_ARG;  // different block set
+  }
+  if (st == BSM_OK) {
+    launch_gather_blocks(dv, sidx, M->vals, nblk, bs, s);
+    st = cuda_status(cudaGetLastError());
+  }
+  cleanup();
+  return st;
 }
 
 extern "C" bsm_status bsm_info(bsm_matrix M, int64_t *nrows, int64_t *ncols, int *bs,

@@ -1,0 +1,86 @@
+"""Plans: symbolic work once, numeric phase replayed from a CUDA graph, with
+an optional measuring autotuner; bsm_update_values changes operand values under
+a fixed structure."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1501_07800_gb300 as bsm
+import synth
+from helpers import assert_same_structure, from_bsm, relerr, to_bsm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    torch.cuda.init()
+    bsm.load()
+
+
+def batch(nprod=8, seed=31):
+    return synth.batched(nprod, seed, nmin=256, nmax=2500, dmin=0.02, dmax=0.2)
+
+
+@pytest.mark.parametrize("prec", [bsm.BSM_FP64, bsm.BSM_SPLIT_BF16])
+@pytest.mark.parametrize("autotune", [False, True])
+def test_plan_equals_batched_and_replays(prec, autotune):
+    pairs = batch()
+    As = [to_bsm(a) for a, _ in pairs]
+    Bs = [to_bsm(b) for _, b in pairs]
+    ref = [from_bsm(c) for c in bsm.bsm_multiply_batched(As, Bs, prec=prec)]
+    plan = bsm.bsm_plan_create(As, Bs, prec=prec, autotune=autotune)
+    order, chunk, ctas, nitems = bsm.bsm_plan_info(plan)
+    assert order in (0, 1) and 1 <= chunk <= 32 and ctas >= 0
+    assert nitems == sum(r.nblk for r in ref)   # generic data: nothing cancels
+    for _ in range(2):                           # graph replays are idempotent
+        bsm.bsm_plan_execute(plan)
+        got = [from_bsm(c) for c in bsm.bsm_plan_results(plan)]
+        for g, r in zip(got, ref):
+            assert_same_structure(g, r)
+            assert np.array_equal(g.vals, r.vals)
+
+
+@pytest.mark.parametrize("prec,tol", [(bsm.BSM_FP64, 1e-12), (bsm.BSM_SPLIT_BF16, 1e-11)])
+def test_plan_after_value_update(prec, tol):
+    pairs = batch(nprod=5, seed=41)
+    As = [to_bsm(a) for a, _ in pairs]
+    Bs = [to_bsm(b) for _, b in pairs]
+    plan = bsm.bsm_plan_create(As, Bs, prec=prec)
+    # new values on the same blocks (shuffled COO order), then replay
+    rng = np.random.default_rng(7)
+    new_pairs = []
+    for (a, b), ga in zip(pairs, As):
+        perm = rng.permutation(a.nblk)
+        vals = a.vals * -1.5 + 0.25
+        vals[a.vals == 0.0] = 0.0  # padding outside the matrix stays zero
+        bsm.bsm_update_values(ga, a.brow[perm], a.bcol[perm], vals[perm])
+        new_pairs.append((synth.BlockCOO(a.nrows, a.ncols, a.bs, a.brow, a.bcol, vals), b))
+    bsm.bsm_plan_execute(plan)
+    got = [from_bsm(c) for c in bsm.bsm_plan_results(plan)]
+    for (a, b), g in zip(new_pairs, got):
+        fresh = from_bsm(bsm.bsm_multiply(to_bsm(a), to_bsm(b), prec=prec))
+        assert_same_structure(g, fresh)
+        assert np.array_equal(g.vals, fresh.vals)
+        E = oracle.multiply(a, b).C
+        assert_same_structure(g, E)
+        assert relerr(g.vals, E.vals) < tol
+
+
+def test_update_values_rejects_other_block_sets():
+    a = synth.random_blocks(512, 32, 0.2, 3)
+    M = to_bsm(a)
+    with pytest.raises(bsm.BsmError) as e:
+        bsm.bsm_update_values(M, a.brow[1:], a.bcol[1:], a.vals[1:])
+    assert e.value.name == "BSM_ERR_INVALID_ARG"
+    bcol = a.bcol.copy()
+    free = next(j for j in range(16) if not np.any((a.brow == a.brow[0]) & (a.bcol == j)))
+    bcol[0] = free
+    with pytest.raises(bsm.BsmError) as e:
+        bsm.bsm_update_values(M, a.brow, bcol, a.vals)
+    assert e.value.name == "BSM_ERR_INVALID_ARG"
+    # the handle is unchanged
+    r = from_bsm(M)
+    assert np.array_equal(r.vals, a.sorted().vals)
