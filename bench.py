@@ -137,17 +137,19 @@ def cpu_baseline(A, B, target_s: float = 12.0):
 
     L = oracle.common_depth(A, B)
     tb = oracle.tree(B, L)
-    rows = 8
-    while True:
+
+    def sample(rows):
         keep = A.brow < rows
         As = synth.BlockCOO(A.nrows, A.ncols, A.bs, A.brow[keep], A.bcol[keep], A.vals[keep])
         ta = oracle.tree(As, L)
         t0 = time.perf_counter()
         P = oracle.multiply_trees(ta, tb)
-        dt = time.perf_counter() - t0
-        if dt > target_s / 4 or rows >= A.mb:
-            break
-        rows = min(A.mb, rows * 4)
+        return P, time.perf_counter() - t0
+
+    rows = 16
+    P, dt = sample(rows)  # calibration, then a sample of about target_s
+    rows = int(min(A.mb, max(rows, rows * target_s / max(dt, 1e-3))))
+    P, dt = sample(rows)
     flops = metrics.block_flops(A.bs, P.triples)
     return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
             "sample": f"first {rows} of {A.mb} block rows of A times all of B "
@@ -312,6 +314,8 @@ def run_gpu(args):
             line["e2e"] = {"value": e2e_v, "unit": "GFLOP/s",
                            "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
                            "ms_per_step": 1e3 * e2e["seconds"] / e2e["steps"]}
+    if line is not None and not args.no_batched:
+        line["batched"] = run_batched(bsm, torch, args, stream)
     if line is not None and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A, B)
     if line is not None:
@@ -380,6 +384,79 @@ def run_split(bsm, torch, ga, gb, args, stream, flops, triples, A, B, rank, slic
             "clocks": clk}
 
 
+def run_batched(bsm, torch, args, stream, nprod=64):
+    """64 independent products, N log-uniform in [2048, 32768], block density
+    U[0.5%, 10%], bs 32, uniform[-1,1) entries (generated on the device).
+    Times the full batched call (symbolic + one persistent numeric launch +
+    C assembly) and the autotuned plan replay (numeric phase from a CUDA graph),
+    FP64 and split BF16x7, and the split result's error against FP64."""
+    from synth import device as sd
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.time()
+    gen = sd.batched(nprod, synth.BASE_SEED + 3, dev)
+    As = [bsm.bsm_build(n, n, 32, r, c, v) for (n, r, c, v), _ in gen]
+    Bs = [bsm.bsm_build(n, n, 32, r, c, v) for _, (n, r, c, v) in gen]
+    del gen
+    torch.cuda.synchronize()
+    log(f"batched workload built in {time.time() - t0:.1f} s")
+    out = {"workload": f"{nprod} products, N log-uniform [2048, 32768], bs 32, block density "
+                       f"U[0.5%, 10%], uniform[-1,1) entries", "products": nprod}
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for i in range(steps):
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    for name, prec in (("fp64", bsm.BSM_FP64), ("split_bf16x7", bsm.BSM_SPLIT_BF16)):
+        C = bsm.bsm_multiply_batched(As, Bs, prec=prec)  # warm-up
+        del C
+        _, triples, ncs = bsm.bsm_last_stats()
+        flops = metrics.block_flops(32, triples)
+        steps = 2 if prec == bsm.BSM_FP64 else 3
+
+        def full():
+            c = bsm.bsm_multiply_batched(As, Bs, prec=prec)
+            del c
+        full_ms = timed(full, steps)
+        t1 = time.time()
+        plan = bsm.bsm_plan_create(As, Bs, prec=prec, autotune=True)
+        create_s = time.time() - t1
+        order, chunk, ctas, nitems = bsm.bsm_plan_info(plan)
+        bsm.bsm_plan_execute(plan)
+        replay_ms = timed(lambda: bsm.bsm_plan_execute(plan), steps)
+        del plan  # one plan's buffers (all C blocks) at a time
+        out[name] = {"full_call_ms": statistics.mean(full_ms),
+                     "full_call_gflops": flops / (statistics.mean(full_ms) / 1e3) / 1e9,
+                     "graph_replay_ms": statistics.mean(replay_ms),
+                     "graph_replay_gflops": flops / (statistics.mean(replay_ms) / 1e3) / 1e9,
+                     "plan_create_s": create_s, "triples": triples, "c_blocks": nitems,
+                     "autotuned": {"order": "longest-first" if order == 0 else
+                                   "product-major Morton", "chunk": chunk, "ctas_per_sm": ctas}}
+    # split vs FP64, product by product on every 8th product (bounded memory)
+    num = den = 0.0
+    for i in range(0, nprod, 8):
+        cf = bsm.bsm_multiply(As[i], Bs[i])
+        cs = bsm.bsm_multiply(As[i], Bs[i], prec=bsm.BSM_SPLIT_BF16)
+        rf, _, vf = bsm.bsm_to_blocks(cf, device=True)
+        rs, _, vs = bsm.bsm_to_blocks(cs, device=True)
+        del cf, cs
+        if rf.shape != rs.shape:
+            num = float("nan")
+            break
+        num += float(torch.sum((vf - vs) ** 2))
+        den += float(torch.sum(vf ** 2))
+        del rf, rs, vf, vs
+    out["split_rel_err_vs_fp64"] = (num / den) ** 0.5 if den > 0 else None
+    out["split_err_sample"] = "every 8th product, all C blocks"
+    return out
+
+
 def run_e2e(bsm, torch, A, B, prec, steps):
     """Host COO in pinned memory -> bsm_build x2 -> bsm_multiply -> bsm_to_blocks
     into pinned host buffers, every step."""
@@ -424,6 +501,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-split", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="matrix side (profiling runs only)")
     ap.add_argument("--p", type=float, default=None, help="block density (profiling runs only)")
     args = ap.parse_args()

@@ -118,14 +118,13 @@ void destroy_plan(bsm_plan P) {
   delete P;
 }
 
-// Times one configuration (median of 3 runs after one warm-up), in ms.
-float time_config(bsm_plan P, int order, int chunk, int ctas) {
+// Times one configuration (best of `reps` runs), in ms.
+float time_config(bsm_plan P, int order, int chunk, int ctas, int reps) {
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   float best = 1e30f;
-  enqueue_numeric(P, order, chunk, ctas, P->stream);
-  for (int r = 0; r < 3; r++) {
+  for (int r = 0; r < reps; r++) {
     cudaEventRecord(a, P->stream);
     if (enqueue_numeric(P, order, chunk, ctas, P->stream) != BSM_OK) break;
     cudaEventRecord(b, P->stream);
@@ -162,17 +161,21 @@ bsm_status autotune(bsm_plan P) {
       return BSM_OK;
     }
   }
+  // FP64 runs at the FP64 pipe's rate whatever the schedule, and one run of a
+  // large batch takes seconds: only the work order is measured there.
   std::vector<TuneVal> cands;
   for (int order : {0, 1}) {
     if (P->prec == BSM_FP64)
-      for (int ctas : {0, 4, 2, 1}) cands.push_back({order, 32, ctas});
+      cands.push_back({order, 32, 0});
     else
       for (int chunk : {32, 8}) cands.push_back({order, chunk, 0});
   }
+  const int reps = P->prec == BSM_FP64 ? 1 : 2;
+  enqueue_numeric(P, cands[0].order, cands[0].chunk, cands[0].ctas, P->stream);  // warm-up
   float best = 1e30f;
   TuneVal pick = cands[0];
   for (const TuneVal &c : cands) {
-    float ms = time_config(P, c.order, c.chunk, c.ctas);
+    float ms = time_config(P, c.order, c.chunk, c.ctas, reps);
     if (ms < best) {
       best = ms;
       pick = c;

@@ -1,0 +1,24 @@
+"""The torch generator reproduces the numpy generator bit for bit (CPU)."""
+import numpy as np
+import torch
+
+import synth
+from synth import device as sd
+
+
+def test_hash_and_uniform_match_numpy():
+    a = np.arange(1000, dtype=np.uint64) * np.uint64(7919)
+    b = np.arange(1000, dtype=np.uint64)[::-1].copy()
+    h_np = synth.hash3(synth.BASE_SEED, a, b)
+    h_t = sd.hash3(synth.BASE_SEED, torch.from_numpy(a.astype(np.int64)),
+                   torch.from_numpy(b.astype(np.int64)))
+    assert np.array_equal(h_np.view(np.int64), h_t.numpy())
+    assert np.array_equal(synth.uniform01(h_np), sd.uniform01(h_t).numpy())
+
+
+def test_random_blocks_match_numpy():
+    for n, bs, p, seed in [(700, 32, 0.1, 5), (333, 16, 0.3, 9)]:
+        ref = synth.random_blocks(n, bs, p, seed, dist="uniform")
+        r, c, v = sd.random_blocks(n, bs, p, seed, "cpu")
+        assert np.array_equal(r.numpy(), ref.brow) and np.array_equal(c.numpy(), ref.bcol)
+        assert np.array_equal(v.numpy(), ref.vals)
