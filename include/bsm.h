@@ -115,7 +115,12 @@ bsm_status bsm_build(int64_t nrows, int64_t ncols, int bs, int64_t nblk, const i
  *   C      receives the new handle (NULL on error); C.nrows = A.nrows,
  *          C.ncols = B.ncols, C.bs = A.bs
  *   opts   NULL or options (precision mode, slice count)
- * Errors: INVALID_ARG, DIM_MISMATCH, BLOCKSIZE, OOM, CUDA, TIMEOUT, UNSUPPORTED.
+ * Products too large for one pass of the symbolic phase are expanded and
+ * computed in consecutive Morton ranges of C (see bsm_last_chunks).
+ * Errors: INVALID_ARG, DIM_MISMATCH, BLOCKSIZE, OOM, CUDA, TIMEOUT,
+ * UNSUPPORTED (one quadrant of one C node with more than 2^31 block pairs on
+ * a level; split mode with bs 64, or with more than 511 accumulation groups
+ * in one C block).
  */
 bsm_status bsm_multiply(bsm_matrix A, bsm_matrix B, bsm_matrix *C, const bsm_mult_opts *opts,
                         void *stream);
@@ -170,6 +175,15 @@ bsm_status bsm_level_counts(bsm_matrix M, int64_t *counts, int cap, int *nlev);
  *   nc_sym   receives the number of C blocks before zero-block removal
  */
 bsm_status bsm_last_stats(int64_t *tasks, int cap, int *nlev, int64_t *triples, int64_t *nc_sym);
+
+/*
+ * bsm_last_chunks -- number of Morton-range chunks the symbolic phase of the
+ * last bsm_multiply on this thread delivered its task list in.  A product
+ * whose expansion exceeds the per-level pair budget (2^30 pairs by default;
+ * the environment variable BSM_SYM_BUDGET overrides it) is computed chunk by
+ * chunk: halves of a level's C-node list, or the four quadrants of one node.
+ */
+bsm_status bsm_last_chunks(int *nchunks);
 
 /*
  * bsm_set_timing -- per-phase CUDA-event timing of bsm_multiply on the calling

@@ -36,6 +36,7 @@ _PROTOS = {
     "bsm_info": (_I32, [_P, _P, _P, _P, _P]),
     "bsm_level_counts": (_I32, [_P, _P, _I32, _P]),
     "bsm_last_stats": (_I32, [_P, _I32, _P, _P, _P]),
+    "bsm_last_chunks": (_I32, [_P]),
     "bsm_set_timing": (_I32, [_I32]),
     "bsm_last_phase_ms": (_I32, [_P, _I32, _P, _P]),
     "bsm_block_products_fp64_noalloc": (_I32, [_I32, _I64, _P, _P, _P, _P, _I64, _P, _I64, _P,
@@ -251,6 +252,12 @@ def bsm_last_stats():
     _check(lib.bsm_last_stats(t.ctypes.data, 64, ctypes.byref(nlev), ctypes.byref(trip),
                               ctypes.byref(ncs)), "bsm_last_stats")
     return t[: nlev.value].copy(), trip.value, ncs.value
+
+
+def bsm_last_chunks() -> int:
+    n = ctypes.c_int()
+    _check(load().bsm_last_chunks(ctypes.byref(n)), "bsm_last_chunks")
+    return n.value
 
 
 def bsm_set_timing(on: bool):

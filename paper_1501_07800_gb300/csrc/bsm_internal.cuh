@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <vector>
 
 #include "../../include/bsm.h"
@@ -117,6 +118,14 @@ struct SymbolicResult {
   int64_t tasks[BSM_MAXH + 1] = {};  // pairs per height (index = height)
 };
 bsm_status symbolic_multiply(bsm_matrix A, bsm_matrix B, SymbolicResult *out, cudaStream_t s);
+
+// Chunked symbolic phase: the leaf task list arrives as consecutive Morton
+// ranges of C, each handed to `sink` (which may take ownership of the arrays
+// by clearing the pointers).  budget: pairs per level part (0 = default, or
+// the BSM_SYM_BUDGET environment variable).  tasks[h]: pairs per height.
+using LeafSink = std::function<bsm_status(SymbolicResult &)>;
+bsm_status symbolic_chunks(bsm_matrix A, bsm_matrix B, const LeafSink &sink, int64_t *tasks,
+                           int *H, int *nchunks, cudaStream_t s, int64_t budget);
 void free_symbolic(SymbolicResult *r, cudaStream_t s);
 
 // ----------------------------------------------------------- numeric phase
@@ -171,6 +180,7 @@ struct LastStats {
   int64_t triples = 0, nc_sym = 0;
   double phase_ms[3] = {0, 0, 0};
   int64_t launches = 0;
+  int chunks = 0;  // symbolic chunks (Morton ranges of C) of the last product
 };
 LastStats &last_stats();
 

@@ -173,83 +173,191 @@ struct PhaseTimer {
   }
 };
 
-// One product with an explicit numeric routine (shared by single and batched
-// entry points).
+// Compacts the nonzero C blocks of one chunk into new arrays (or takes the
+// chunk's arrays when nothing was dropped).
+static bsm_status compact_chunk(SymbolicResult &r, double *&cvals, const int32_t *nz,
+                                unsigned *err, int bs, uint64_t **okeys_out, double **ovals_out,
+                                int64_t *n_out, cudaStream_t s) {
+  const int64_t nc = r.nc;
+  int32_t *pos = nullptr;
+  bsm_status st = dev_alloc((void **)&pos, 4 * (nc + 1), s);
+  if (st != BSM_OK) return st;
+  st = scan_exclusive_i32(nz, pos, nc, s);
+  int32_t *h = (int32_t *)host_scratch().get(16);
+  if (st == BSM_OK && !h) st = BSM_ERR_OOM;
+  if (st == BSM_OK) {
+    cudaMemcpyAsync(h, pos + nc - 1, 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h + 1, nz + nc - 1, 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h + 2, err, 4, cudaMemcpyDeviceToHost, s);
+    st = cuda_status(cudaStreamSynchronize(s));
+  }
+  if (st == BSM_OK && h[2] == DERR_TIMEOUT) st = BSM_ERR_TIMEOUT;
+  if (st == BSM_OK && h[2] != DERR_NONE) st = BSM_ERR_CUDA;
+  if (st != BSM_OK) {
+    dev_free(pos, s);
+    return st;
+  }
+  const int64_t nkeep = (int64_t)h[0] + h[1];
+  if (nkeep == nc) {
+    *okeys_out = r.ckeys;
+    *ovals_out = cvals;
+    r.ckeys = nullptr;
+    cvals = nullptr;
+  } else {
+    uint64_t *okeys = nullptr;
+    double *ovals = nullptr;
+    int32_t *idx = nullptr;
+    const int64_t m = nkeep > 0 ? nkeep : 1;
+    if ((st = dev_alloc((void **)&okeys, 8 * m, s)) ||
+        (st = dev_alloc((void **)&ovals, sizeof(double) * bs * bs * m, s)) ||
+        (st = dev_alloc((void **)&idx, 4 * m, s))) {
+      dev_free(okeys, s);
+      dev_free(ovals, s);
+      dev_free(idx, s);
+      dev_free(pos, s);
+      return st;
+    }
+    count_launch();
+    k_compact_c<<<grid_for(nc, 256), 256, 0, s>>>(nz, pos, nc, r.ckeys, okeys, idx);
+    launch_gather_blocks(cvals, idx, ovals, nkeep, bs, s);
+    dev_free(idx, s);
+    *okeys_out = okeys;
+    *ovals_out = ovals;
+  }
+  dev_free(pos, s);
+  *n_out = nkeep;
+  return BSM_OK;
+}
+
+// One product: the symbolic phase delivers the task list in Morton-range
+// chunks (one chunk unless a level exceeds the pair budget); each chunk is
+// computed and compacted as it arrives, and C is assembled from the chunks.
 static bsm_status multiply_one(bsm_matrix A, bsm_matrix B, int prec, int slices, cudaStream_t s,
                                bsm_matrix *out) {
   *out = nullptr;
   LastStats &ls = last_stats();
   ls = LastStats();
-  int64_t l0 = launch_counter();
-  PhaseTimer timer(timing_enabled());
-  timer.mark(s);
-  SymbolicResult sym;
-  bsm_status st = symbolic_multiply(A, B, &sym, s);
-  if (st != BSM_OK) {
-    free_symbolic(&sym, s);
-    return st;
+  const int64_t l0 = launch_counter();
+  const bool timed = timing_enabled();
+  cudaEvent_t e0 = nullptr, e1 = nullptr, ea = nullptr, eb = nullptr, ec = nullptr;
+  if (timed) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&ea);
+    cudaEventCreate(&eb);
+    cudaEventCreate(&ec);
+    cudaEventRecord(e0, s);
   }
-  ls.nlev = sym.H + 1;
-  for (int l = 0; l <= sym.H; l++) ls.tasks[l] = sym.tasks[sym.H - l];
-  ls.triples = sym.nt;
-  ls.nc_sym = sym.nc;
-  int64_t mb = A->mb, nb = B->nb;
-  int64_t side = mb > nb ? mb : nb;
-  bsm_matrix C = new_matrix_shell(A->nrows, B->ncols, A->bs, ceil_log2_i64(side < 1 ? 1 : side));
-  if (sym.nc == 0) {
-    free_symbolic(&sym, s);
-    st = build_levels(C, s);
-    if (st != BSM_OK) {
-      free_matrix_shell(C, s);
-      return st;
-    }
-    ls.launches = launch_counter() - l0;
-    *out = C;
-    return BSM_OK;
-  }
-  if (sym.nc > 0x7FFFFFFF) {
-    free_symbolic(&sym, s);
-    free_matrix_shell(C, s);
-    return BSM_ERR_UNSUPPORTED;
-  }
-  double *cvals = nullptr;
-  int32_t *nz = nullptr;
+  double numeric_ms = 0, finish_ms = 0;
+  const int bs = A->bs;
+  struct Chunk {
+    uint64_t *keys;
+    double *vals;
+    int64_t n;
+  };
+  std::vector<Chunk> chunks;
   unsigned *err = nullptr;
-  int bs = A->bs;
-  if ((st = dev_alloc((void **)&cvals, sizeof(double) * bs * bs * sym.nc, s)) ||
-      (st = dev_alloc((void **)&nz, 4 * sym.nc, s)) ||
-      (st = dev_alloc((void **)&err, sizeof(unsigned), s))) {
+  bsm_status st = dev_alloc((void **)&err, sizeof(unsigned), s);
+  if (st == BSM_OK) cudaMemsetAsync(err, 0, sizeof(unsigned), s);
+  LeafSink sink = [&](SymbolicResult &r) -> bsm_status {
+    ls.triples += r.nt;
+    ls.nc_sym += r.nc;
+    if (r.nc == 0) return BSM_OK;
+    if (r.nc > 0x7FFFFFFF) return BSM_ERR_UNSUPPORTED;
+    double *cvals = nullptr;
+    int32_t *nz = nullptr;
+    bsm_status e;
+    if ((e = dev_alloc((void **)&cvals, sizeof(double) * bs * bs * r.nc, s)) ||
+        (e = dev_alloc((void **)&nz, 4 * r.nc, s))) {
+      dev_free(cvals, s);
+      dev_free(nz, s);
+      return e;
+    }
+    if (timed) cudaEventRecord(ea, s);
+    e = prec == BSM_FP64 ? numeric_fp64(A, B, r, cvals, nz, err, s)
+                         : numeric_split(A, B, r, slices, cvals, nz, err, s);
+    if (timed) cudaEventRecord(eb, s);
+    Chunk c{nullptr, nullptr, 0};
+    if (e == BSM_OK) e = compact_chunk(r, cvals, nz, err, bs, &c.keys, &c.vals, &c.n, s);
+    if (timed) {
+      cudaEventRecord(ec, s);
+      if (cudaEventSynchronize(ec) == cudaSuccess) {
+        float t1 = 0, t2 = 0;
+        cudaEventElapsedTime(&t1, ea, eb);
+        cudaEventElapsedTime(&t2, eb, ec);
+        numeric_ms += t1;
+        finish_ms += t2;
+      }
+    }
     dev_free(cvals, s);
     dev_free(nz, s);
-    dev_free(err, s);
-    free_symbolic(&sym, s);
-    free_matrix_shell(C, s);
-    return st;
-  }
-  cudaMemsetAsync(err, 0, sizeof(unsigned), s);
-  timer.mark(s);
-  if (prec == BSM_FP64)
-    st = numeric_fp64(A, B, sym, cvals, nz, err, s);
-  else
-    st = numeric_split(A, B, sym, slices, cvals, nz, err, s);
-  timer.mark(s);
+    if (e == BSM_OK) {
+      if (c.n > 0) {
+        chunks.push_back(c);
+      } else {
+        dev_free(c.keys, s);
+        dev_free(c.vals, s);
+      }
+    }
+    return e;
+  };
+  int H = 0, nch = 0;
+  int64_t tasks[BSM_MAXH + 1];
+  if (st == BSM_OK) st = symbolic_chunks(A, B, sink, tasks, &H, &nch, s, 0);
+  int64_t mb = A->mb, nb = B->nb;
+  int64_t side = mb > nb ? mb : nb;
+  bsm_matrix C = new_matrix_shell(A->nrows, B->ncols, bs, ceil_log2_i64(side < 1 ? 1 : side));
+  // assemble C: chunks are consecutive Morton ranges
   if (st == BSM_OK) {
-    st = finish_product(C, &sym, cvals, nz, err, s);  // owns cvals from here
-    cvals = nullptr;
+    int64_t total = 0;
+    for (auto &c : chunks) total += c.n;
+    if (chunks.size() == 1) {
+      C->keys = chunks[0].keys;
+      C->vals = chunks[0].vals;
+      chunks.clear();
+    } else if (total > 0) {
+      if ((st = dev_alloc((void **)&C->keys, 8 * total, s)) == BSM_OK &&
+          (st = dev_alloc((void **)&C->vals, sizeof(double) * bs * bs * total, s)) == BSM_OK) {
+        int64_t off = 0;
+        for (auto &c : chunks) {
+          cudaMemcpyAsync(C->keys + off, c.keys, 8 * c.n, cudaMemcpyDeviceToDevice, s);
+          cudaMemcpyAsync(C->vals + off * bs * bs, c.vals, sizeof(double) * bs * bs * c.n,
+                          cudaMemcpyDeviceToDevice, s);
+          off += c.n;
+        }
+      }
+    }
+    if (C->keys) C->owned.push_back(C->keys);
+    if (C->vals) C->owned.push_back(C->vals);
+    C->nblk = total;
   }
-  timer.mark(s);
-  dev_free(cvals, s);
-  dev_free(nz, s);
+  for (auto &c : chunks) {
+    dev_free(c.keys, s);
+    dev_free(c.vals, s);
+  }
   dev_free(err, s);
-  free_symbolic(&sym, s);
+  if (st == BSM_OK) st = build_levels(C, s);
   if (st != BSM_OK) {
     free_matrix_shell(C, s);
-    return st;
+  } else {
+    *out = C;
   }
-  timer.collect(ls.phase_ms);
+  ls.nlev = H + 1;
+  for (int l = 0; l <= H; l++) ls.tasks[l] = tasks[H - l];
+  ls.chunks = nch;
+  if (timed) {
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) == cudaSuccess) {
+      float tot = 0;
+      cudaEventElapsedTime(&tot, e0, e1);
+      ls.phase_ms[1] = numeric_ms;
+      ls.phase_ms[2] = finish_ms;
+      ls.phase_ms[0] = tot - numeric_ms - finish_ms;
+    }
+    for (cudaEvent_t e : {e0, e1, ea, eb, ec}) cudaEventDestroy(e);
+  }
   ls.launches = launch_counter() - l0;
-  *out = C;
-  return BSM_OK;
+  return st;
 }
 
 extern "C" bsm_status bsm_multiply(bsm_matrix A, bsm_matrix B, bsm_matrix *C,
@@ -260,6 +368,12 @@ extern "C" bsm_status bsm_multiply(bsm_matrix A, bsm_matrix B, bsm_matrix *C,
   int prec, slices;
   BSM_TRY(check_opts(opts, &prec, &slices));
   return multiply_one(A, B, prec, slices, (cudaStream_t)stream, C);
+}
+
+extern "C" bsm_status bsm_last_chunks(int *nchunks) {
+  if (!nchunks) return BSM_ERR_INVALID_ARG;
+  *nchunks = last_stats().chunks;
+  return BSM_OK;
 }
 
 extern "C" bsm_status bsm_last_stats(int64_t *tasks, int cap, int *nlev, int64_t *triples,

@@ -16,8 +16,18 @@
 // of the recursion without a sort.  The sums of Algorithm 2 (C_mn = Y1 + Y2)
 // become the concatenation of the children of a segment's pairs.
 //
-// Per level: count (per pair, four quadrant counts) -> exclusive scan of the
-// 4-vectors -> segment pass (quadrant totals, new segments) -> scan -> fill.
+// Per level: count (per pair, four quadrant counts; exact 64-bit level total)
+// -> exclusive scan of the 4-vectors -> segment pass (quadrant totals, new
+// segments) -> scan -> fill.
+//
+// Large products: when a level would exceed a pair budget, the expansion
+// continues depth first on parts of it -- the two halves of its segment list
+// (contiguous Morton ranges of C), or, for a single C node, its four C
+// quadrants one at a time -- so the leaf task list arrives in chunks that are
+// contiguous, consecutive ranges of C in Morton order.
+#include <cstdlib>
+#include <vector>
+
 #include "bsm_internal.cuh"
 
 namespace {
@@ -47,28 +57,38 @@ __device__ __forceinline__ int quad_count(unsigned ma, unsigned mb, int m, int n
                ((ma >> (2 * m + 1)) & (mb >> (2 + n)) & 1u));
 }
 
+// Per pair: child counts of the quadrants in qmask; the level's exact total
+// is accumulated in 64 bits (one atomic per warp).
 __global__ void k_sym_count(const int32_t *__restrict__ pa, const int32_t *__restrict__ pb,
-                            int64_t np, LevelView va, LevelView vb, int4 *__restrict__ cnt) {
+                            int64_t np, LevelView va, LevelView vb, unsigned qmask,
+                            int4 *__restrict__ cnt, unsigned long long *__restrict__ total) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p > np) return;
-  if (p == np) {  // sentinel so that the exclusive scan also yields the total
-    cnt[p] = make_int4(0, 0, 0, 0);
-    return;
+  int t = 0;
+  if (p < np) {
+    unsigned ma, mb;
+    int32_t ca, cb;
+    node_info(va, pa[p], ma, ca);
+    node_info(vb, pb[p], mb, cb);
+    int4 c = make_int4((qmask & 1u) ? quad_count(ma, mb, 0, 0) : 0,
+                       (qmask & 2u) ? quad_count(ma, mb, 0, 1) : 0,
+                       (qmask & 4u) ? quad_count(ma, mb, 1, 0) : 0,
+                       (qmask & 8u) ? quad_count(ma, mb, 1, 1) : 0);
+    cnt[p] = c;
+    t = c.x + c.y + c.z + c.w;
+  } else if (p == np) {
+    cnt[p] = make_int4(0, 0, 0, 0);  // sentinel: the exclusive scan then ends with the total
   }
-  unsigned ma, mb;
-  int32_t ca, cb;
-  node_info(va, pa[p], ma, ca);
-  node_info(vb, pb[p], mb, cb);
-  cnt[p] = make_int4(quad_count(ma, mb, 0, 0), quad_count(ma, mb, 0, 1), quad_count(ma, mb, 1, 0),
-                     quad_count(ma, mb, 1, 1));
+  unsigned long long w = __reduce_add_sync(0xffffffffu, (unsigned)t);
+  if ((threadIdx.x & 31) == 0 && w) atomicAdd(total, w);
 }
 
 __device__ __forceinline__ int q_of(const int4 &v, int q) {
   return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
 }
 
-// Per segment: quadrant totals and the number of non-empty quadrants.
-__global__ void k_sym_seg_count(const int32_t *__restrict__ sst, int64_t ns,
+// Segment starts sst[] are stored offset by poff (pair index of the first
+// pair of this part of the level); P is indexed from that first pair.
+__global__ void k_sym_seg_count(const int32_t *__restrict__ sst, int32_t poff, int64_t ns,
                                 const int4 *__restrict__ P, int32_t *__restrict__ nnz) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s > ns) return;
@@ -76,18 +96,18 @@ __global__ void k_sym_seg_count(const int32_t *__restrict__ sst, int64_t ns,
     nnz[s] = 0;
     return;
   }
-  int4 a = P[sst[s]], b = P[sst[s + 1]];
+  int4 a = P[sst[s] - poff], b = P[sst[s + 1] - poff];
   nnz[s] = (b.x > a.x) + (b.y > a.y) + (b.z > a.z) + (b.w > a.w);
 }
 
 // New segments: key 4*ckey + q and start offset for each non-empty quadrant.
 __global__ void k_sym_seg_write(const uint64_t *__restrict__ sck, const int32_t *__restrict__ sst,
-                                int64_t ns, const int4 *__restrict__ P,
+                                int32_t poff, int64_t ns, const int4 *__restrict__ P,
                                 const int32_t *__restrict__ nbase, uint64_t *__restrict__ nck,
                                 int32_t *__restrict__ nst) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= ns) return;
-  int4 a = P[sst[s]], b = P[sst[s + 1]];
+  int4 a = P[sst[s] - poff], b = P[sst[s + 1] - poff];
   int32_t off = a.x + a.y + a.z + a.w;  // children of all earlier segments
   int32_t j = nbase[s];
   for (int q = 0; q < 4; q++) {
@@ -99,22 +119,21 @@ __global__ void k_sym_seg_write(const uint64_t *__restrict__ sck, const int32_t 
     }
     off += t;
   }
-  if (s == ns - 1) {
-    nst[j] = off;  // end sentinel = total child pairs
-  }
+  if (s == ns - 1) nst[j] = off;  // end sentinel = total child pairs
 }
 
-// Child pairs in (segment, quadrant, parent pair, k) order.
+// Child pairs in (segment, quadrant, parent pair, k) order.  Segment ids in
+// pseg are offset by soff.
 __global__ void k_sym_fill(const int32_t *__restrict__ pa, const int32_t *__restrict__ pb,
-                           const int32_t *__restrict__ pseg, int64_t np,
-                           const int32_t *__restrict__ sst, const int4 *__restrict__ P,
-                           const int32_t *__restrict__ nbase, LevelView va, LevelView vb,
-                           int32_t *__restrict__ npa, int32_t *__restrict__ npb,
-                           int32_t *__restrict__ npseg) {
+                           const int32_t *__restrict__ pseg, int32_t soff, int64_t np,
+                           const int32_t *__restrict__ sst, int32_t poff,
+                           const int4 *__restrict__ P, const int32_t *__restrict__ nbase,
+                           LevelView va, LevelView vb, unsigned qmask, int32_t *__restrict__ npa,
+                           int32_t *__restrict__ npb, int32_t *__restrict__ npseg) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
-  int32_t s = pseg[p];
-  int4 a = P[sst[s]], b = P[sst[s + 1]], me = P[p];
+  int32_t s = pseg[p] - soff;
+  int4 a = P[sst[s] - poff], b = P[sst[s + 1] - poff], me = P[p];
   unsigned ma, mb;
   int32_t ca, cb;
   node_info(va, pa[p], ma, ca);
@@ -123,7 +142,7 @@ __global__ void k_sym_fill(const int32_t *__restrict__ pa, const int32_t *__rest
   int32_t segid = nbase[s];
   for (int q = 0; q < 4; q++) {
     int32_t t = q_of(b, q) - q_of(a, q);
-    if (t == 0) continue;
+    if (t == 0 || !((qmask >> q) & 1u)) continue;
     int m = q >> 1, n = q & 1;
     int32_t pos = off + (q_of(me, q) - q_of(a, q));
     for (int k = 0; k < 2; k++) {
@@ -165,6 +184,194 @@ LevelView view_of(bsm_matrix M, int h) {
   return v;
 }
 
+// One part of one level of the expansion.  Arrays may point into a larger
+// level (then `owns` is false and the offsets are nonzero).
+struct Level {
+  int32_t *pa = nullptr, *pb = nullptr, *pseg = nullptr, *sst = nullptr;
+  uint64_t *sck = nullptr;
+  int64_t np = 0, ns = 0;
+  int h = 0;
+  int32_t soff = 0, poff = 0;
+  bool owns = false;
+};
+
+void free_level(Level &L, cudaStream_t s) {
+  if (!L.owns) return;
+  dev_free(L.pa, s);
+  dev_free(L.pb, s);
+  dev_free(L.pseg, s);
+  dev_free(L.sst, s);
+  dev_free(L.sck, s);
+  L = Level();
+}
+
+int64_t pair_budget() {
+  const char *e = getenv("BSM_SYM_BUDGET");
+  if (e) {
+    long long v = atoll(e);
+    if (v >= 1) return v;
+  }
+  return (int64_t)1 << 30;
+}
+
+struct Expander {
+  bsm_matrix A, B;
+  cudaStream_t s;
+  int64_t budget;
+  int64_t *tasks;  // per height
+  const LeafSink &sink;
+  int chunks = 0;
+
+  // segment starts [0] and [idx] of a level part, read back
+  bsm_status read_sst(const Level &L, int64_t idx, int32_t *out) {
+    int32_t *h = (int32_t *)host_scratch().get(16);
+    if (!h) return BSM_ERR_OOM;
+    cudaMemcpyAsync(h, L.sst + idx, 4, cudaMemcpyDeviceToHost, s);
+    BSM_CUDA(cudaStreamSynchronize(s));
+    *out = h[0];
+    return BSM_OK;
+  }
+
+  Level sub(const Level &L, int64_t s0, int64_t s1, int32_t p0abs, int32_t p1abs) {
+    Level S;
+    const int32_t p0 = p0abs - L.poff;
+    S.pa = L.pa + p0;
+    S.pb = L.pb + p0;
+    S.pseg = L.pseg + p0;
+    S.sst = L.sst + s0;
+    S.sck = L.sck + s0;
+    S.np = p1abs - p0abs;
+    S.ns = s1 - s0;
+    S.h = L.h;
+    S.soff = L.soff + (int32_t)s0;
+    S.poff = p0abs;
+    S.owns = false;
+    return S;
+  }
+
+  bsm_status leaf(Level &L) {
+    SymbolicResult r;
+    r.nc = L.ns;
+    r.nt = L.np;
+    r.ckeys = L.sck;
+    r.seg = L.sst;
+    r.ta = L.pa;
+    r.tb = L.pb;
+    chunks++;
+    // the sink may take ownership of the arrays (then it clears the pointers)
+    bsm_status st = sink(r);
+    if (L.owns) {
+      if (r.ckeys == nullptr) L.sck = nullptr;
+      if (r.seg == nullptr) L.sst = nullptr;
+      if (r.ta == nullptr) L.pa = nullptr;
+      if (r.tb == nullptr) L.pb = nullptr;
+    }
+    return st;
+  }
+
+  bsm_status process(Level &L, unsigned qmask) {
+    if (L.h == 0) return leaf(L);
+    LevelView va = view_of(A, L.h), vb = view_of(B, L.h);
+    int4 *P = nullptr;
+    unsigned long long *tot = nullptr;
+    bsm_status st;
+    if ((st = dev_alloc((void **)&P, sizeof(int4) * (L.np + 1), s)) != BSM_OK) return st;
+    if ((st = dev_alloc((void **)&tot, 8, s)) != BSM_OK) {
+      dev_free(P, s);
+      return st;
+    }
+    cudaMemsetAsync(tot, 0, 8, s);
+    count_launch();
+    k_sym_count<<<grid_for(L.np + 1, 256), 256, 0, s>>>(L.pa, L.pb, L.np, va, vb, qmask, P, tot);
+    unsigned long long *ht = (unsigned long long *)host_scratch().get(16);
+    if (!ht) st = BSM_ERR_OOM;
+    if (st == BSM_OK) {
+      cudaMemcpyAsync(ht, tot, 8, cudaMemcpyDeviceToHost, s);
+      st = cuda_status(cudaStreamSynchronize(s));
+    }
+    const int64_t total = st == BSM_OK ? (int64_t)ht[0] : 0;
+    dev_free(tot, s);
+    if (st != BSM_OK || total == 0) {
+      dev_free(P, s);
+      return st;
+    }
+    const int64_t hard = (int64_t)INT32_MAX - 1;
+    if (total > budget) {
+      // split: halves of the segment list, or the quadrants of a single node
+      if (L.ns > 1) {
+        dev_free(P, s);
+        const int64_t mid = L.ns / 2;
+        int32_t p0, pm, p1;
+        BSM_TRY(read_sst(L, 0, &p0));
+        BSM_TRY(read_sst(L, mid, &pm));
+        BSM_TRY(read_sst(L, L.ns, &p1));
+        Level lo = sub(L, 0, mid, p0, pm), hi = sub(L, mid, L.ns, pm, p1);
+        BSM_TRY(process(lo, qmask));
+        return process(hi, qmask);
+      }
+      if (__builtin_popcount(qmask) > 1) {
+        dev_free(P, s);
+        for (int q = 0; q < 4; q++)
+          if ((qmask >> q) & 1u) BSM_TRY(process(L, 1u << q));
+        return BSM_OK;
+      }
+      if (total > hard) {
+        dev_free(P, s);
+        return BSM_ERR_UNSUPPORTED;  // one quadrant of one node exceeds 2^31 pairs
+      }
+    }
+    if (total > hard) {
+      dev_free(P, s);
+      return BSM_ERR_UNSUPPORTED;
+    }
+    tasks[L.h - 1] += total;
+    // scan, segments, fill
+    int32_t *nnz = nullptr, *nbase = nullptr;
+    Level N;
+    N.h = L.h - 1;
+    N.np = total;
+    N.owns = true;
+    auto fail = [&](bsm_status e) {
+      dev_free(P, s);
+      dev_free(nnz, s);
+      dev_free(nbase, s);
+      free_level(N, s);
+      return e;
+    };
+    if ((st = scan_exclusive_int4(P, P, L.np + 1, s)) != BSM_OK) return fail(st);
+    if ((st = dev_alloc((void **)&nnz, 4 * (L.ns + 1), s)) ||
+        (st = dev_alloc((void **)&nbase, 4 * (L.ns + 1), s)))
+      return fail(st);
+    count_launch();
+    k_sym_seg_count<<<grid_for(L.ns + 1, 256), 256, 0, s>>>(L.sst, L.poff, L.ns, P, nnz);
+    if ((st = scan_exclusive_i32(nnz, nbase, L.ns + 1, s)) != BSM_OK) return fail(st);
+    int32_t *hn = (int32_t *)host_scratch().get(16);
+    if (!hn) return fail(BSM_ERR_OOM);
+    cudaMemcpyAsync(hn, nbase + L.ns, 4, cudaMemcpyDeviceToHost, s);
+    if ((st = cuda_status(cudaStreamSynchronize(s))) != BSM_OK) return fail(st);
+    N.ns = hn[0];
+    const bool last = (N.h == 0);
+    if ((st = dev_alloc((void **)&N.pa, 4 * N.np, s)) ||
+        (st = dev_alloc((void **)&N.pb, 4 * N.np, s)) ||
+        (!last && (st = dev_alloc((void **)&N.pseg, 4 * N.np, s))) ||
+        (st = dev_alloc((void **)&N.sck, 8 * N.ns, s)) ||
+        (st = dev_alloc((void **)&N.sst, 4 * (N.ns + 1), s)))
+      return fail(st);
+    count_launch(2);
+    k_sym_seg_write<<<grid_for(L.ns, 256), 256, 0, s>>>(L.sck, L.sst, L.poff, L.ns, P, nbase,
+                                                        N.sck, N.sst);
+    k_sym_fill<<<grid_for(L.np, 256), 256, 0, s>>>(L.pa, L.pb, L.pseg, L.soff, L.np, L.sst, L.poff,
+                                                   P, nbase, va, vb, qmask, N.pa, N.pb, N.pseg);
+    st = cuda_status(cudaGetLastError());
+    dev_free(P, s);
+    dev_free(nnz, s);
+    dev_free(nbase, s);
+    if (st == BSM_OK) st = process(N, 0xFu);
+    free_level(N, s);
+    return st;
+  }
+};
+
 }  // namespace
 
 void free_symbolic(SymbolicResult *r, cudaStream_t s) {
@@ -177,135 +384,53 @@ void free_symbolic(SymbolicResult *r, cudaStream_t s) {
   r->ta = r->tb = nullptr;
 }
 
-bsm_status symbolic_multiply(bsm_matrix A, bsm_matrix B, SymbolicResult *out, cudaStream_t s) {
-  *out = SymbolicResult();
-  int H = A->L > B->L ? A->L : B->L;
-  out->H = H;
+bsm_status symbolic_chunks(bsm_matrix A, bsm_matrix B, const LeafSink &sink, int64_t *tasks,
+                           int *H, int *nchunks, cudaStream_t s, int64_t budget) {
+  const int h0 = A->L > B->L ? A->L : B->L;
+  *H = h0;
+  *nchunks = 0;
+  for (int h = 0; h <= BSM_MAXH; h++) tasks[h] = 0;
   if (A->nblk == 0 || B->nblk == 0) return BSM_OK;
-  bsm_status st = BSM_OK;
-  // current level
-  int32_t *pa = nullptr, *pb = nullptr, *pseg = nullptr, *sst = nullptr;
-  uint64_t *sck = nullptr;
-  int64_t np = 1, ns = 1;
-  auto free_level = [&]() {
-    dev_free(pa, s);
-    dev_free(pb, s);
-    dev_free(pseg, s);
-    dev_free(sst, s);
-    dev_free(sck, s);
-    pa = pb = pseg = sst = nullptr;
-    sck = nullptr;
-  };
-  if ((st = dev_alloc((void **)&pa, 4, s)) || (st = dev_alloc((void **)&pb, 4, s)) ||
-      (st = dev_alloc((void **)&pseg, 4, s)) || (st = dev_alloc((void **)&sst, 8, s)) ||
-      (st = dev_alloc((void **)&sck, 8, s))) {
-    free_level();
+  Level R;
+  R.np = 1;
+  R.ns = 1;
+  R.h = h0;
+  R.owns = true;
+  bsm_status st;
+  if ((st = dev_alloc((void **)&R.pa, 4, s)) || (st = dev_alloc((void **)&R.pb, 4, s)) ||
+      (st = dev_alloc((void **)&R.pseg, 4, s)) || (st = dev_alloc((void **)&R.sst, 8, s)) ||
+      (st = dev_alloc((void **)&R.sck, 8, s))) {
+    free_level(R, s);
     return st;
   }
   count_launch();
-  k_sym_root<<<1, 1, 0, s>>>(pa, pb, pseg, sck, sst);
-  out->tasks[H] = 1;
-  int32_t *hbuf = (int32_t *)host_scratch().get(64);
-  if (!hbuf) {
-    free_level();
-    return BSM_ERR_OOM;
-  }
-  for (int h = H; h >= 1; h--) {
-    LevelView va = view_of(A, h), vb = view_of(B, h);
-    int4 *P = nullptr;
-    int32_t *nnz = nullptr, *nbase = nullptr;
-    int32_t *npa = nullptr, *npb = nullptr, *npseg = nullptr, *nst = nullptr;
-    uint64_t *nck = nullptr;
-    auto free_tmp = [&]() {
-      dev_free(P, s);
-      dev_free(nnz, s);
-      dev_free(nbase, s);
-    };
-    if ((st = dev_alloc((void **)&P, sizeof(int4) * (np + 1), s)) ||
-        (st = dev_alloc((void **)&nnz, 4 * (ns + 1), s)) ||
-        (st = dev_alloc((void **)&nbase, 4 * (ns + 1), s))) {
-      free_tmp();
-      free_level();
-      return st;
-    }
-    count_launch();
-    k_sym_count<<<grid_for(np + 1, 256), 256, 0, s>>>(pa, pb, np, va, vb, P);
-    if ((st = scan_exclusive_int4(P, P, np + 1, s)) != BSM_OK) {
-      free_tmp();
-      free_level();
-      return st;
-    }
-    count_launch();
-    k_sym_seg_count<<<grid_for(ns + 1, 256), 256, 0, s>>>(sst, ns, P, nnz);
-    if ((st = scan_exclusive_i32(nnz, nbase, ns + 1, s)) != BSM_OK) {
-      free_tmp();
-      free_level();
-      return st;
-    }
-    // sizes of the next level
-    cudaMemcpyAsync(hbuf, P + np, sizeof(int4), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(hbuf + 4, nbase + ns, 4, cudaMemcpyDeviceToHost, s);
-    cudaError_t e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-      free_tmp();
-      free_level();
-      return cuda_status(e);
-    }
-    int64_t tot = (int64_t)hbuf[0] + hbuf[1] + hbuf[2] + hbuf[3];
-    int64_t nns = hbuf[4];
-    if (tot > INT32_MAX - 1 || hbuf[0] < 0 || hbuf[1] < 0 || hbuf[2] < 0 || hbuf[3] < 0) {
-      free_tmp();
-      free_level();
-      return BSM_ERR_UNSUPPORTED;  // more than 2^31 pairs in one level
-    }
-    out->tasks[h - 1] = tot;
-    if (tot == 0) {
-      free_tmp();
-      free_level();
-      for (int g = h - 2; g >= 0; g--) out->tasks[g] = 0;
-      return BSM_OK;  // empty product
-    }
-    bool last = (h == 1);
-    if ((st = dev_alloc((void **)&npa, 4 * tot, s)) || (st = dev_alloc((void **)&npb, 4 * tot, s)) ||
-        (!last && (st = dev_alloc((void **)&npseg, 4 * tot, s))) ||
-        (st = dev_alloc((void **)&nck, 8 * nns, s)) ||
-        (st = dev_alloc((void **)&nst, 4 * (nns + 1), s))) {
-      dev_free(npa, s);
-      dev_free(npb, s);
-      dev_free(npseg, s);
-      dev_free(nck, s);
-      dev_free(nst, s);
-      free_tmp();
-      free_level();
-      return st;
-    }
-    count_launch();
-    k_sym_seg_write<<<grid_for(ns, 256), 256, 0, s>>>(sck, sst, ns, P, nbase, nck, nst);
-    count_launch();
-    k_sym_fill<<<grid_for(np, 256), 256, 0, s>>>(pa, pb, pseg, np, sst, P, nbase, va, vb, npa, npb,
-                                                 npseg);
-    e = cudaGetLastError();
-    free_tmp();
-    free_level();
-    pa = npa;
-    pb = npb;
-    pseg = npseg;
-    sck = nck;
-    sst = nst;
-    np = tot;
-    ns = nns;
-    if (e != cudaSuccess) {
-      free_level();
-      return cuda_status(e);
-    }
-  }
-  // leaf level: segments are the C blocks
-  dev_free(pseg, s);
-  out->nc = ns;
-  out->nt = np;
-  out->ckeys = sck;
-  out->seg = sst;
-  out->ta = pa;
-  out->tb = pb;
-  return BSM_OK;
+  k_sym_root<<<1, 1, 0, s>>>(R.pa, R.pb, R.pseg, R.sck, R.sst);
+  tasks[h0] = 1;
+  Expander ex{A, B, s, budget > 0 ? budget : pair_budget(), tasks, sink};
+  st = ex.process(R, 0xFu);
+  free_level(R, s);
+  *nchunks = ex.chunks;
+  return st;
+}
+
+bsm_status symbolic_multiply(bsm_matrix A, bsm_matrix B, SymbolicResult *out, cudaStream_t s) {
+  *out = SymbolicResult();
+  int nch = 0, H = 0;
+  int64_t tasks[BSM_MAXH + 1];
+  bool got = false;
+  // one task list for the whole product (no budget split): the sink keeps it
+  LeafSink keep = [&](SymbolicResult &r) -> bsm_status {
+    if (got) return BSM_ERR_UNSUPPORTED;
+    got = true;
+    *out = r;
+    r.ckeys = nullptr;
+    r.seg = nullptr;
+    r.ta = r.tb = nullptr;
+    return BSM_OK;
+  };
+  bsm_status st = symbolic_chunks(A, B, keep, tasks, &H, &nch, s, (int64_t)INT32_MAX - 1);
+  out->H = H;
+  for (int h = 0; h <= BSM_MAXH; h++) out->tasks[h] = tasks[h];
+  if (st != BSM_OK) free_symbolic(out, s);
+  return st;
 }
