@@ -457,6 +457,117 @@ def run_batched(bsm, torch, args, stream, nprod=64):
     return out
 
 
+def run_decay(args):
+    """Decay-type product A*A: points uniform in a cube at 0.1 per cubic Angstrom,
+    recursive-bisection order, 5 functions per point, A_ij = s_ij exp(-0.5 r_ij)
+    dropped below 1e-6, bs 32 (20,000 points: N = 100,000).  FP64 and split
+    BF16x7; C's structure against the block-pattern product (the definition of
+    S_C, no exact cancellation in this data), values against the oracle's
+    definition on 1000 uniformly sampled C blocks."""
+    import torch
+
+    import oracle
+    import paper_1501_07800_gb300 as bsm
+    from synth import device as sd
+
+    torch.cuda.set_device(0)
+    bsm.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    npts, bs = args.points, 32
+    t0 = time.time()
+    n, r, c, v = sd.decay(npts, bs, synth.BASE_SEED + 2, dev)
+    nbk = -(-n // bs)
+    A = bsm.bsm_build(n, n, bs, r, c, v)
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    nblk = A.nblk
+    # structure of C by definition: block pattern product
+    Pm = torch.zeros((nbk, nbk), dtype=torch.float32, device=dev)
+    Pm[r.long(), c.long()] = 1.0
+    pat = (Pm @ Pm) > 0.5
+    del Pm
+    ci, cj = torch.nonzero(pat, as_tuple=True)
+    del pat
+    nc_def = int(ci.numel())
+    g = torch.Generator(device="cpu").manual_seed(synth.BASE_SEED)
+    pick = torch.randperm(nc_def, generator=g)[:1000]
+    si, sj = ci.cpu()[pick].numpy(), cj.cpu()[pick].numpy()
+    # oracle operands restricted to the sampled rows (left) and columns (right)
+    rows_keep = torch.isin(r, torch.from_numpy(si).to(dev).to(torch.int32))
+    cols_keep = torch.isin(c, torch.from_numpy(sj).to(dev).to(torch.int32))
+    left = synth.BlockCOO(n, n, bs, r[rows_keep].cpu().numpy(), c[rows_keep].cpu().numpy(),
+                          v[rows_keep].cpu().numpy())
+    right = synth.BlockCOO(n, n, bs, r[cols_keep].cpu().numpy(), c[cols_keep].cpu().numpy(),
+                           v[cols_keep].cpu().numpy())
+    del r, c, v, rows_keep, cols_keep
+    torch.cuda.empty_cache()
+    t1 = time.time()
+    L = oracle.common_depth(left, right)
+    tl, tr = oracle.tree(left, L), oracle.tree(right, L)
+    ref = np.stack([oracle.block_product(tl, tr, i, j)[1] for i, j in zip(si, sj)])
+    oracle_s = time.time() - t1
+    del tl, tr, left, right
+    log(f"decay: n={n} blocks={nblk} C(def)={nc_def}; generation {gen_s:.1f} s, "
+        f"oracle on 1000 blocks {oracle_s:.1f} s")
+    bsm.bsm_set_timing(True)
+    out = {"workload": f"decay A*A, {npts} points (N={n}), bs {bs}", "a_blocks": nblk,
+           "c_blocks_definition": nc_def}
+    peaks, which = measured_peaks()
+    fp64_peak = peaks["bf16_tflops"] * FP64_NOMINAL_RATIO
+    for name, prec, reps in (("split_bf16x7", bsm.BSM_SPLIT_BF16, args.steps),
+                             ("fp64", bsm.BSM_FP64, 1)):
+        times = []
+        C = None
+        for k in range(reps + (1 if prec != bsm.BSM_FP64 else 0)):
+            C = None
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            C = bsm.bsm_multiply(A, A, prec=prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if prec == bsm.BSM_FP64 or k > 0:  # split: first run is a warm-up
+                times.append(e0.elapsed_time(e1))
+        ms, _ = bsm.bsm_last_phase_ms()
+        _, triples, ncs = bsm.bsm_last_stats()
+        flops = metrics.block_flops(bs, triples)
+        # structure: compare coordinates (no values) with the definition
+        nr, ncol, _, ncb = bsm.bsm_info(C)
+        cr = torch.empty(ncb, dtype=torch.int32, device=dev)
+        cc = torch.empty(ncb, dtype=torch.int32, device=dev)
+        import ctypes
+        cnt = ctypes.c_int64(ncb)
+        code = bsm.load().bsm_to_blocks(C.handle, ctypes.byref(cnt), cr.data_ptr(), cc.data_ptr(),
+                                        None, 1, stream.cuda_stream)
+        assert code == 0
+        key_gpu = cr.long() * nbk + cc.long()
+        key_def = ci.long() * nbk + cj.long()
+        same_structure = bool(key_gpu.numel() == key_def.numel() and
+                              torch.equal(torch.sort(key_gpu).values, torch.sort(key_def).values))
+        # sampled values
+        pos = torch.searchsorted(key_gpu, torch.from_numpy(si * nbk + sj).to(dev))
+        _, _, cv = bsm.bsm_to_blocks(C, device=True)
+        got = cv[pos].cpu().numpy()
+        del cv, cr, cc, key_gpu, key_def
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        t_num = ms[1] / 1e3
+        res = {"ms_per_product": statistics.mean(times), "gflops": flops / (statistics.mean(times) / 1e3) / 1e9,
+               "phase_ms": [float(x) for x in ms], "chunks": bsm.bsm_last_chunks(),
+               "triples": triples, "c_blocks": ncb, "structure_matches_definition": same_structure,
+               "rel_err_vs_oracle_1000_blocks": err}
+        if prec == bsm.BSM_FP64:
+            res["numeric_tflops"] = flops / t_num / 1e12
+            res["frac_of_fp64_peak"] = flops / t_num / 1e12 / fp64_peak
+            res["peak"] = f"{fp64_peak:.4f} TFLOP/s ({which} bf16 x 1.25/2250)"
+        out[name] = res
+        del C
+        torch.cuda.empty_cache()
+        log(f"{name}: {res}")
+    out["split_speedup_vs_fp64"] = out["fp64"]["ms_per_product"] / out["split_bf16x7"]["ms_per_product"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_e2e(bsm, torch, A, B, prec, steps):
     """Host COO in pinned memory -> bsm_build x2 -> bsm_multiply -> bsm_to_blocks
     into pinned host buffers, every step."""
@@ -502,6 +613,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--workload", default="random", choices=["random", "decay"],
+                    help="decay: the decay-type A*A product (separate JSON line)")
+    ap.add_argument("--points", type=int, default=20000, help="decay workload: number of points")
     ap.add_argument("--n", type=int, default=None, help="matrix side (profiling runs only)")
     ap.add_argument("--p", type=float, default=None, help="block density (profiling runs only)")
     args = ap.parse_args()
@@ -515,6 +629,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "decay":
+        return run_decay(args)
     return run_gpu(args)
 
 

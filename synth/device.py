@@ -76,3 +76,56 @@ def batched(nprod: int, seed: int, device, bs: int = 32, **kw):
 
 def to_host(n: int, bs: int, brow, bcol, vals) -> BlockCOO:
     return BlockCOO(n, n, bs, brow.cpu().numpy(), bcol.cpu().numpy(), vals.cpu().numpy())
+
+
+def decay(npoints: int, bs: int, seed: int, device, nfun: int = 5, alpha: float = 0.5,
+          cutoff: float = 1e-6, density: float = 0.1, chunk_blocks: int = 1 << 17):
+    """Device tensors (n, brow, bcol, vals) of the decay-type matrix of
+    synth.decay: points from synth.decay_points (host, recursive bisection
+    order), blocks whose bounding boxes come within the cutoff radius, entries
+    s_ij exp(-alpha r_ij) below `cutoff` set to zero.  Entries may differ from
+    the numpy generator in the last bit (exp on the device)."""
+    import math
+
+    from . import decay_points
+
+    pts_np = decay_points(npoints, seed, density)
+    pts = torch.from_numpy(pts_np).to(device)
+    n = npoints * nfun
+    nbk = -(-n // bs)
+    rcut = -math.log(cutoff) / alpha
+    ptidx = torch.clamp(torch.arange(nbk * bs, device=device) // nfun, max=npoints - 1).view(nbk, bs)
+    bp = pts[ptidx]                      # [nbk, bs, 3]
+    lo, hi = bp.min(1).values, bp.max(1).values
+    rows, cols = [], []
+    step = max(1, (1 << 24) // nbk)
+    for r0 in range(0, nbk, step):
+        r1 = min(nbk, r0 + step)
+        gap = torch.clamp(torch.maximum(lo[r0:r1, None, :] - hi[None, :, :],
+                                        lo[None, :, :] - hi[r0:r1, None, :]), min=0.0)
+        near = (gap * gap).sum(-1).sqrt() <= rcut
+        bi, bj = torch.nonzero(near, as_tuple=True)
+        rows.append(bi + r0)
+        cols.append(bj)
+    brow = torch.cat(rows).to(torch.int64)
+    bcol = torch.cat(cols).to(torch.int64)
+    nb_ = brow.numel()
+    vals = torch.empty((nb_, bs, bs), dtype=torch.float64, device=device)
+    r = torch.arange(bs, dtype=torch.int64, device=device)
+    sseed = seed ^ 0x2545F491
+    for t0 in range(0, nb_, chunk_blocks):
+        t1 = min(nb_, t0 + chunk_blocks)
+        gi = brow[t0:t1, None, None] * bs + r[None, :, None]
+        gj = bcol[t0:t1, None, None] * bs + r[None, None, :]
+        pi = torch.clamp(gi // nfun, max=npoints - 1)
+        pj = torch.clamp(gj // nfun, max=npoints - 1)
+        d = pts[pi] - pts[pj]
+        rr = (d * d).sum(-1).sqrt()
+        lo_i, hi_i = torch.minimum(gi, gj), torch.maximum(gi, gj)
+        sgn = torch.where((hash3(sseed, lo_i, hi_i) & 1) == 1, -1.0, 1.0).to(torch.float64)
+        sgn = torch.where(gi == gj, torch.ones_like(sgn), sgn)
+        v = sgn * torch.exp(-alpha * rr)
+        v = torch.where(v.abs() < cutoff, torch.zeros_like(v), v)
+        v = torch.where((gi < n) & (gj < n), v, torch.zeros_like(v))
+        vals[t0:t1] = v
+    return n, brow.to(torch.int32), bcol.to(torch.int32), vals

@@ -22,3 +22,15 @@ def test_random_blocks_match_numpy():
         r, c, v = sd.random_blocks(n, bs, p, seed, "cpu")
         assert np.array_equal(r.numpy(), ref.brow) and np.array_equal(c.numpy(), ref.bcol)
         assert np.array_equal(v.numpy(), ref.vals)
+
+
+def test_decay_matches_numpy_structure_and_values():
+    ref = synth.decay(120, 16, 7)
+    n, r, c, v = sd.decay(120, 16, 7, "cpu")
+    nz = (v != 0).flatten(1).any(1)
+    r, c, v = r[nz].numpy(), c[nz].numpy(), v[nz].numpy()
+    o = np.lexsort((c, r))
+    E = ref.sorted()
+    assert n == ref.nrows
+    assert np.array_equal(r[o], E.brow) and np.array_equal(c[o], E.bcol)
+    assert np.allclose(v[o], E.vals, rtol=1e-15, atol=0)
