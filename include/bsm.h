@@ -66,12 +66,17 @@ typedef enum {
 typedef struct {
   int prec;   /* bsm_precision */
   int slices; /* split modes: number of 7-bit slices per operand, 1..8, 0 = default (7) */
-  int flags;  /* 0, or BSM_FLAG_AUTOTUNE (bsm_plan_create only) */
+  int flags;  /* 0, BSM_FLAG_AUTOTUNE (bsm_plan_create only), or
+                 BSM_FLAG_TRANS_A / BSM_FLAG_TRANS_B (bsm_multiply only) */
 } bsm_mult_opts;
 
 /* bsm_plan_create: measure candidate launch configurations and keep the
  * fastest (cached per product class for the process). */
 #define BSM_FLAG_AUTOTUNE 1
+/* bsm_multiply: use A^T (resp. B^T) in place of A (resp. B), the transposed
+ * multiplication task types C = A^T B, A B^T, A^T B^T of Sec. 3.2. */
+#define BSM_FLAG_TRANS_A 2
+#define BSM_FLAG_TRANS_B 4
 
 /* Supported leaf block sides. */
 #define BSM_BS_MIN 16
@@ -111,19 +116,78 @@ bsm_status bsm_build(int64_t nrows, int64_t ncols, int bs, int64_t nblk, const i
  * by one owner.  C blocks whose entries are all exactly zero are removed.
  * The depth of the product is the larger depth of A and B.
  *
- *   A, B   operands, A.ncols == B.nrows, same bs
- *   C      receives the new handle (NULL on error); C.nrows = A.nrows,
- *          C.ncols = B.ncols, C.bs = A.bs
- *   opts   NULL or options (precision mode, slice count)
+ *   A, B   operands, op(A).ncols == op(B).nrows, same bs, where op(X) is X,
+ *          or X^T when opts->flags holds BSM_FLAG_TRANS_A / _B
+ *   C      receives the new handle (NULL on error); C.nrows = op(A).nrows,
+ *          C.ncols = op(B).ncols, C.bs = A.bs
+ *   opts   NULL or options (precision mode, slice count, transposition)
+ * A transposed operand is materialised (bsm_transpose) for the duration of
+ * the call.
  * Products too large for one pass of the symbolic phase are expanded and
  * computed in consecutive Morton ranges of C (see bsm_last_chunks).
  * Errors: INVALID_ARG, DIM_MISMATCH, BLOCKSIZE, OOM, CUDA, TIMEOUT,
  * UNSUPPORTED (one quadrant of one C node with more than 2^31 block pairs on
- * a level; split mode with bs 64, or with more than 511 accumulation groups
- * in one C block).
+ * a level; split mode with bs 64).
  */
 bsm_status bsm_multiply(bsm_matrix A, bsm_matrix B, bsm_matrix *C, const bsm_mult_opts *opts,
                         void *stream);
+
+/*
+ * bsm_transpose -- T = A^T as a new handle (keys with row and column swapped,
+ * every block transposed; Sec. 3.2 transposed task types).
+ *   A    input handle (unchanged)
+ *   out  receives the new handle (NULL on error); out.nrows = A.ncols,
+ *        out.ncols = A.nrows, same bs and depth
+ * Stream-ordered; the caller owns the result (bsm_destroy).
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+bsm_status bsm_transpose(bsm_matrix A, bsm_matrix *out, void *stream);
+
+/*
+ * bsm_add -- C = A + B (Algorithm 2 with the leaf add): a block present in
+ * both operands is the sum of the two, a block present in one is copied, and
+ * a block present in neither is NIL.  Sums that are exactly zero in every
+ * entry are removed, as for products.
+ *   A, B  operands of equal dimensions and block size (unchanged)
+ *   out   receives the new handle (NULL on error); depth = max of the two
+ * Stream-ordered; the caller owns the result (bsm_destroy).
+ * Errors: INVALID_ARG, DIM_MISMATCH, BLOCKSIZE, OOM, CUDA, UNSUPPORTED
+ * (more than 2^31 - 1 blocks in A and B together).
+ */
+bsm_status bsm_add(bsm_matrix A, bsm_matrix B, bsm_matrix *out, void *stream);
+
+/*
+ * Symmetric matrices (Sec. 3.2, additional task types for the symmetric
+ * matrix square) are stored as their upper triangle of blocks: only blocks
+ * with I <= J, diagonal blocks in full.  Symmetric results are returned the
+ * same way.  Operands in this storage must be square and hold no block below
+ * the diagonal (else BSM_ERR_DIM_MISMATCH / BSM_ERR_OUT_OF_RANGE).  The
+ * symmetric results are computed from the ordinary symbolic recursion with
+ * the C nodes below the diagonal skipped, so roughly half of the block
+ * products of the full product are formed.  All are stream-ordered and
+ * return a new handle the caller owns; opts as for bsm_multiply (no flags).
+ * Errors: as bsm_multiply, plus OUT_OF_RANGE as above.
+ */
+#define BSM_SYM_LEFT 0  /* bsm_sym_multiply: A is the symmetric operand */
+#define BSM_SYM_RIGHT 1 /* bsm_sym_multiply: B is the symmetric operand */
+
+/* bsm_sym_square -- C = A^2, A symmetric: upper triangle of A*A. */
+bsm_status bsm_sym_square(bsm_matrix A, bsm_matrix *C, const bsm_mult_opts *opts, void *stream);
+
+/* bsm_syrk -- symmetric rank-k product, upper triangle of C = A A^T
+ * (trans = 0) or C = A^T A (trans = 1); A is a general matrix. */
+bsm_status bsm_syrk(bsm_matrix A, int trans, bsm_matrix *C, const bsm_mult_opts *opts,
+                    void *stream);
+
+/* bsm_sym_multiply -- C = A B (general result) where A (side = BSM_SYM_LEFT)
+ * or B (side = BSM_SYM_RIGHT) is symmetric in upper-triangle storage. */
+bsm_status bsm_sym_multiply(bsm_matrix A, bsm_matrix B, int side, bsm_matrix *C,
+                            const bsm_mult_opts *opts, void *stream);
+
+/* bsm_sym_to_full -- the full matrix (both triangles) of a symmetric matrix
+ * in upper-triangle storage: each strictly-upper block also appears,
+ * transposed, at its mirror position. */
+bsm_status bsm_sym_to_full(bsm_matrix A, bsm_matrix *out, void *stream);
 
 /*
  * bsm_multiply_batched -- C[i] = A[i]*B[i] for n independent products.

@@ -53,6 +53,18 @@ def _load():
     lib.orc_build.argtypes = [I64, I64, I32, I32, I32, I64, P, P, P, ctypes.POINTER(I32)]
     lib.orc_multiply.restype = P
     lib.orc_multiply.argtypes = [P, P, P, P, ctypes.POINTER(I32)]
+    lib.orc_multiply_t.restype = P
+    lib.orc_multiply_t.argtypes = [P, I32, P, I32, P, P, ctypes.POINTER(I32)]
+    lib.orc_add.restype = P
+    lib.orc_add.argtypes = [P, P, ctypes.POINTER(I32)]
+    lib.orc_sym_full.restype = P
+    lib.orc_sym_full.argtypes = [P, ctypes.POINTER(I32)]
+    lib.orc_sym_square.restype = P
+    lib.orc_sym_square.argtypes = [P, ctypes.POINTER(I32)]
+    lib.orc_syrk.restype = P
+    lib.orc_syrk.argtypes = [P, I32, ctypes.POINTER(I32)]
+    lib.orc_symm.restype = P
+    lib.orc_symm.argtypes = [P, P, I32, ctypes.POINTER(I32)]
     lib.orc_nblocks.restype = I64
     lib.orc_nblocks.argtypes = [P]
     lib.orc_depth.restype = I32
@@ -132,24 +144,41 @@ class Product:
     triples: int       # leaf block products (nonzero A_IK, B_KJ pairs)
 
 
-def multiply(A: BlockCOO, B: BlockCOO, leaf_dim: int = 4096) -> Product:
-    """C = A*B by the quadtree recursion (Algorithm 1/2), zero blocks dropped."""
-    lib = _load()
+def multiply(A: BlockCOO, B: BlockCOO, leaf_dim: int = 4096, trans_a: bool = False,
+             trans_b: bool = False) -> Product:
+    """C = op(A)*op(B) by the quadtree recursion (Algorithm 1/2, and the
+    transposed task types of Sec. 3.2), zero blocks dropped."""
     L = common_depth(A, B)
     ta, tb = tree(A, L, leaf_dim), tree(B, L, leaf_dim)
-    return multiply_trees(ta, tb)
+    return multiply_trees(ta, tb, trans_a, trans_b)
 
 
-def multiply_trees(ta: Tree, tb: Tree) -> Product:
+def multiply_trees(ta: Tree, tb: Tree, trans_a: bool = False, trans_b: bool = False) -> Product:
     lib = _load()
     tasks = np.zeros(ta.depth + 1, np.int64)
     trip = ctypes.c_int64(0)
     st = ctypes.c_int(0)
-    p = lib.orc_multiply(ta._p, tb._p, tasks.ctypes.data, ctypes.byref(trip), ctypes.byref(st))
+    p = lib.orc_multiply_t(ta._p, int(trans_a), tb._p, int(trans_b), tasks.ctypes.data,
+                           ctypes.byref(trip), ctypes.byref(st))
     if st.value:
         raise OracleError(st.value)
-    tc = Tree(p, ta.nrows, tb.ncols, ta.bs, ta.L, ta.leaf_nb)
+    nrows = ta.ncols if trans_a else ta.nrows
+    ncols = tb.nrows if trans_b else tb.ncols
+    tc = Tree(p, nrows, ncols, ta.bs, ta.L, ta.leaf_nb)
     return Product(tc.to_coo(), tasks, int(trip.value))
+
+
+def add(A: BlockCOO, B: BlockCOO, leaf_dim: int = 4096) -> BlockCOO:
+    """C = A + B by Algorithm 2 (leaf add where both have a block), exactly
+    zero sums dropped."""
+    lib = _load()
+    L = common_depth(A, B)
+    ta, tb = tree(A, L, leaf_dim), tree(B, L, leaf_dim)
+    st = ctypes.c_int(0)
+    p = lib.orc_add(ta._p, tb._p, ctypes.byref(st))
+    if st.value:
+        raise OracleError(st.value)
+    return Tree(p, ta.nrows, ta.ncols, ta.bs, ta.L, ta.leaf_nb).to_coo()
 
 
 def task_counts(A: BlockCOO, B: BlockCOO) -> np.ndarray:
@@ -163,3 +192,44 @@ def block_product(ta: Tree, tb: Tree, I: int, J: int) -> tuple[bool, np.ndarray]
     out = np.zeros((ta.bs, ta.bs), np.float64)
     any_ = _load().orc_block_product(ta._p, tb._p, int(I), int(J), out.ctypes.data)
     return bool(any_), out
+
+
+# ------------------------------------------------------- symmetric storage
+# A symmetric matrix is passed as its upper triangle of blocks (I <= J), the
+# diagonal blocks in full; symmetric results come back the same way.
+def _call(fn, *args):
+    st = ctypes.c_int(0)
+    p = fn(*args, ctypes.byref(st))
+    if st.value:
+        raise OracleError(st.value)
+    return p
+
+
+def sym_full(U: BlockCOO, leaf_dim: int = 4096) -> BlockCOO:
+    """The full matrix of an upper-triangle-stored symmetric matrix."""
+    t = tree(U, None, leaf_dim)
+    p = _call(_load().orc_sym_full, t._p)
+    return Tree(p, U.nrows, U.ncols, U.bs, t.L, t.leaf_nb).to_coo()
+
+
+def sym_square(U: BlockCOO, leaf_dim: int = 4096) -> BlockCOO:
+    """Upper triangle of S*S, S the symmetric matrix U stores."""
+    t = tree(U, None, leaf_dim)
+    p = _call(_load().orc_sym_square, t._p)
+    return Tree(p, U.nrows, U.ncols, U.bs, t.L, t.leaf_nb).to_coo()
+
+
+def syrk(A: BlockCOO, trans: bool = False, leaf_dim: int = 4096) -> BlockCOO:
+    """Upper triangle of A A^T (trans False) or A^T A (trans True)."""
+    t = tree(A, None, leaf_dim)
+    p = _call(_load().orc_syrk, t._p, int(bool(trans)))
+    n = A.ncols if trans else A.nrows
+    return Tree(p, n, n, A.bs, t.L, t.leaf_nb).to_coo()
+
+
+def sym_multiply(A: BlockCOO, B: BlockCOO, side: int = 0, leaf_dim: int = 4096) -> BlockCOO:
+    """S B (side 0, A stores S) or A S (side 1, B stores S)."""
+    L = common_depth(A, B)
+    ta, tb = tree(A, L, leaf_dim), tree(B, L, leaf_dim)
+    p = _call(_load().orc_symm, ta._p, tb._p, int(side))
+    return Tree(p, A.nrows, B.ncols, A.bs, L, ta.leaf_nb).to_coo()

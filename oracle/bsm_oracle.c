@@ -18,7 +18,11 @@
  *     m, n in {1, 2} and the four results assembled into a new node
  *     (createFromIds, Sec. 3.2).
  *   - add() is Algorithm 2: recurse (or leaf add) when both inputs are
- *     non-NIL, otherwise the non-NIL input or NIL.
+ *     non-NIL, otherwise the non-NIL input or NIL.  orc_add() exposes it as
+ *     the C = A + B task type (Sec. 3.2).
+ *   - The transposed task types C = A^T B, A B^T, A^T B^T (Sec. 3.2) run the
+ *     same recursion with the children of a transposed operand taken in
+ *     transposed position and its leaf blocks read transposed.
  *   - The leaf multiply is a sum of outer products over the inner block index
  *     (Sec. 4.1, Fig. 3), each block product a naive triple loop.
  *   - Blocks whose entries are all exactly 0.0 are not stored: input blocks
@@ -62,6 +66,7 @@ typedef struct {
   int64_t *tasks; /* per level, or NULL */
   int64_t triples;
   int oom;
+  int ta, tb; /* operands enter transposed (Sec. 3.2 transposed task types) */
 } orc_ctx;
 
 /* ------------------------------------------------------------ node helpers */
@@ -230,12 +235,14 @@ static orc_node *leaf_multiply(const orc_matrix *m, const orc_node *a, const orc
     cx->oom = 1;
     return NULL;
   }
+  /* op(A)_ik is A_ik, or A_ki read transposed; likewise op(B)_kj. */
+  const int ta = cx->ta, tb = cx->tb;
   for (int k = 0; k < nb; k++)
     for (int i = 0; i < nb; i++) {
-      const double *aik = a->blk[i * nb + k];
+      const double *aik = ta ? a->blk[k * nb + i] : a->blk[i * nb + k];
       if (!aik) continue;
       for (int j = 0; j < nb; j++) {
-        const double *bkj = b->blk[k * nb + j];
+        const double *bkj = tb ? b->blk[j * nb + k] : b->blk[k * nb + j];
         if (!bkj) continue;
         double **xij = &x->blk[i * nb + j];
         if (!*xij) {
@@ -249,8 +256,9 @@ static orc_node *leaf_multiply(const orc_matrix *m, const orc_node *a, const orc
         double *c = *xij;
         for (int r = 0; r < bs; r++)
           for (int kk = 0; kk < bs; kk++) {
-            double av = aik[r * bs + kk];
-            for (int q = 0; q < bs; q++) c[r * bs + q] += av * bkj[kk * bs + q];
+            double av = ta ? aik[kk * bs + r] : aik[r * bs + kk];
+            for (int q = 0; q < bs; q++)
+              c[r * bs + q] += av * (tb ? bkj[q * bs + kk] : bkj[kk * bs + q]);
           }
       }
     }
@@ -301,14 +309,20 @@ static orc_node *multiply(const orc_matrix *m, const orc_node *a, const orc_node
     cx->oom = 1;
     return NULL;
   }
+  /* child (r, c) of op(X) is child (r, c) of X, or child (c, r) if X enters
+   * transposed */
+#define OPA(r, c) a->child[cx->ta ? 2 * (c) + (r) : 2 * (r) + (c)]
+#define OPB(r, c) b->child[cx->tb ? 2 * (c) + (r) : 2 * (r) + (c)]
   int any = 0;
   for (int mm = 0; mm < 2; mm++)
     for (int n = 0; n < 2; n++) {
-      orc_node *y1 = multiply(m, a->child[2 * mm + 0], b->child[2 * 0 + n], level + 1, cx);
-      orc_node *y2 = multiply(m, a->child[2 * mm + 1], b->child[2 * 1 + n], level + 1, cx);
+      orc_node *y1 = multiply(m, OPA(mm, 0), OPB(0, n), level + 1, cx);
+      orc_node *y2 = multiply(m, OPA(mm, 1), OPB(1, n), level + 1, cx);
       c->child[2 * mm + n] = add(m, y1, y2, level + 1);
       any |= c->child[2 * mm + n] != NULL;
     }
+#undef OPA
+#undef OPB
   if (!any) {
     free_node(m, c);
     return NULL;
@@ -343,16 +357,19 @@ static orc_node *drop_zero(const orc_matrix *m, orc_node *n, int level) {
   return n;
 }
 
-/* C = A*B.  tasks (optional) receives the multiply-task count of each level
- * 0..depth; triples receives the number of leaf block products. */
-orc_matrix *orc_multiply(const orc_matrix *A, const orc_matrix *B, int64_t *tasks,
-                         int64_t *triples, int *status) {
+/* C = op(A)*op(B), op(X) = X or X^T (ta, tb).  tasks (optional) receives the
+ * multiply-task count of each level 0..depth; triples receives the number of
+ * leaf block products. */
+orc_matrix *orc_multiply_t(const orc_matrix *A, int ta, const orc_matrix *B, int tb,
+                           int64_t *tasks, int64_t *triples, int *status) {
   *status = ORC_OK;
   if (!A || !B) {
     *status = ORC_ERR_INVALID_ARG;
     return NULL;
   }
-  if (A->ncols != B->nrows) {
+  int64_t ar = ta ? A->ncols : A->nrows, ac = ta ? A->nrows : A->ncols;
+  int64_t br = tb ? B->ncols : B->nrows, bc = tb ? B->nrows : B->ncols;
+  if (ac != br) {
     *status = ORC_ERR_DIM_MISMATCH;
     return NULL;
   }
@@ -364,12 +381,12 @@ orc_matrix *orc_multiply(const orc_matrix *A, const orc_matrix *B, int64_t *task
     *status = ORC_ERR_INVALID_ARG;
     return NULL;
   }
-  orc_matrix *C = alloc_matrix(A->nrows, B->ncols, A->bs, A->L, A->leaf_nb);
+  orc_matrix *C = alloc_matrix(ar, bc, A->bs, A->L, A->leaf_nb);
   if (!C) {
     *status = ORC_ERR_OOM;
     return NULL;
   }
-  orc_ctx cx = {tasks, 0, 0};
+  orc_ctx cx = {tasks, 0, 0, ta != 0, tb != 0};
   if (tasks) memset(tasks, 0, sizeof(int64_t) * (size_t)(A->depth + 1));
   C->root = multiply(C, A->root, B->root, 0, &cx);
   if (triples) *triples = cx.triples;
@@ -379,6 +396,211 @@ orc_matrix *orc_multiply(const orc_matrix *A, const orc_matrix *B, int64_t *task
     return NULL;
   }
   C->root = drop_zero(C, C->root, 0);
+  return C;
+}
+
+orc_matrix *orc_multiply(const orc_matrix *A, const orc_matrix *B, int64_t *tasks,
+                         int64_t *triples, int *status) {
+  return orc_multiply_t(A, 0, B, 0, tasks, triples, status);
+}
+
+/* Deep copy of a subtree (the add below consumes its inputs). */
+static orc_node *copy_node(const orc_matrix *m, const orc_node *n, int level, int *oom) {
+  if (!n) return NULL;
+  orc_node *x = new_node(m, level == m->depth);
+  if (!x) {
+    *oom = 1;
+    return NULL;
+  }
+  if (level == m->depth) {
+    size_t bb = (size_t)m->bs * m->bs * sizeof(double);
+    for (int64_t t = 0; t < (int64_t)m->leaf_nb * m->leaf_nb; t++) {
+      if (!n->blk[t]) continue;
+      x->blk[t] = (double *)malloc(bb);
+      if (!x->blk[t]) {
+        *oom = 1;
+        return x;
+      }
+      memcpy(x->blk[t], n->blk[t], bb);
+    }
+    return x;
+  }
+  for (int c = 0; c < 4; c++) x->child[c] = copy_node(m, n->child[c], level + 1, oom);
+  return x;
+}
+
+/* C = A + B by Algorithm 2 (on copies of the operands), exactly-zero sums
+ * removed. */
+orc_matrix *orc_add(const orc_matrix *A, const orc_matrix *B, int *status) {
+  *status = ORC_OK;
+  if (!A || !B) {
+    *status = ORC_ERR_INVALID_ARG;
+    return NULL;
+  }
+  if (A->nrows != B->nrows || A->ncols != B->ncols) {
+    *status = ORC_ERR_DIM_MISMATCH;
+    return NULL;
+  }
+  if (A->bs != B->bs) {
+    *status = ORC_ERR_BLOCKSIZE;
+    return NULL;
+  }
+  if (A->L != B->L || A->leaf_nb != B->leaf_nb) {
+    *status = ORC_ERR_INVALID_ARG;
+    return NULL;
+  }
+  orc_matrix *C = alloc_matrix(A->nrows, A->ncols, A->bs, A->L, A->leaf_nb);
+  if (!C) {
+    *status = ORC_ERR_OOM;
+    return NULL;
+  }
+  int oom = 0;
+  orc_node *x = copy_node(C, A->root, 0, &oom);
+  orc_node *y = copy_node(C, B->root, 0, &oom);
+  C->root = add(C, x, y, 0);
+  if (oom) {
+    *status = ORC_ERR_OOM;
+    orc_free(C);
+    return NULL;
+  }
+  C->root = drop_zero(C, C->root, 0);
+  return C;
+}
+
+/* ------------------------------------------------------ symmetric storage */
+/* A symmetric matrix is given by its upper triangle of blocks (I <= J), the
+ * diagonal blocks in full (Sec. 3.2, symmetric task types).  The symmetric
+ * results are defined plainly: the full matrix S (each strictly-upper block
+ * also placed, transposed, at its mirror position), the ordinary product by
+ * Algorithm 1, and the blocks with I <= J of that product. */
+
+/* Slot of leaf block (I, J), creating the path; NULL on OOM. */
+static double **block_slot(orc_matrix *m, int64_t I, int64_t J) {
+  orc_node **slot = &m->root;
+  for (int level = 0; level <= m->depth; level++) {
+    if (!*slot) {
+      *slot = new_node(m, level == m->depth);
+      if (!*slot) return NULL;
+    }
+    if (level == m->depth) break;
+    int shift = m->L - level - 1;
+    slot = &(*slot)->child[2 * ((I >> shift) & 1) + ((J >> shift) & 1)];
+  }
+  int64_t mask = m->leaf_nb - 1;
+  return &(*slot)->blk[(I & mask) * m->leaf_nb + (J & mask)];
+}
+
+static int mirror_into(orc_matrix *F, const orc_matrix *U, const orc_node *n, int level,
+                       int64_t I0, int64_t J0) {
+  if (!n) return ORC_OK;
+  int bs = U->bs;
+  size_t bb = (size_t)bs * bs;
+  if (level == U->depth) {
+    for (int i = 0; i < U->leaf_nb; i++)
+      for (int j = 0; j < U->leaf_nb; j++) {
+        const double *b = n->blk[i * U->leaf_nb + j];
+        if (!b) continue;
+        int64_t I = I0 * U->leaf_nb + i, J = J0 * U->leaf_nb + j;
+        if (I > J) return ORC_ERR_OUT_OF_RANGE; /* not upper-triangle storage */
+        double **d = block_slot(F, I, J);
+        if (!d || !(*d = (double *)malloc(bb * sizeof(double)))) return ORC_ERR_OOM;
+        memcpy(*d, b, bb * sizeof(double));
+        if (I < J) {
+          double **t = block_slot(F, J, I);
+          if (!t || !(*t = (double *)malloc(bb * sizeof(double)))) return ORC_ERR_OOM;
+          for (int r = 0; r < bs; r++)
+            for (int c = 0; c < bs; c++) (*t)[r * bs + c] = b[c * bs + r];
+        }
+      }
+    return ORC_OK;
+  }
+  for (int c = 0; c < 4; c++) {
+    int st = mirror_into(F, U, n->child[c], level + 1, 2 * I0 + (c >> 1), 2 * J0 + (c & 1));
+    if (st) return st;
+  }
+  return ORC_OK;
+}
+
+/* The full symmetric matrix of an upper-triangle-stored one. */
+orc_matrix *orc_sym_full(const orc_matrix *U, int *status) {
+  *status = ORC_OK;
+  if (!U) {
+    *status = ORC_ERR_INVALID_ARG;
+    return NULL;
+  }
+  if (U->nrows != U->ncols) {
+    *status = ORC_ERR_DIM_MISMATCH;
+    return NULL;
+  }
+  orc_matrix *F = alloc_matrix(U->nrows, U->ncols, U->bs, U->L, U->leaf_nb);
+  if (!F) {
+    *status = ORC_ERR_OOM;
+    return NULL;
+  }
+  int st = mirror_into(F, U, U->root, 0, 0, 0);
+  if (st) {
+    *status = st;
+    orc_free(F);
+    return NULL;
+  }
+  return F;
+}
+
+/* Remove blocks with I > J (and nodes left empty). */
+static orc_node *keep_upper(const orc_matrix *m, orc_node *n, int level, int64_t I0, int64_t J0) {
+  if (!n) return NULL;
+  if (level == m->depth) {
+    for (int i = 0; i < m->leaf_nb; i++)
+      for (int j = 0; j < m->leaf_nb; j++) {
+        double **b = &n->blk[i * m->leaf_nb + j];
+        if (*b && I0 * m->leaf_nb + i > J0 * m->leaf_nb + j) {
+          free(*b);
+          *b = NULL;
+        }
+      }
+    if (leaf_is_empty(m, n)) {
+      free_node(m, n);
+      return NULL;
+    }
+    return n;
+  }
+  int any = 0;
+  for (int c = 0; c < 4; c++) {
+    n->child[c] = keep_upper(m, n->child[c], level + 1, 2 * I0 + (c >> 1), 2 * J0 + (c & 1));
+    any |= n->child[c] != NULL;
+  }
+  if (!any) {
+    free_node(m, n);
+    return NULL;
+  }
+  return n;
+}
+
+/* C = A^2 for symmetric A (upper-triangle storage in and out). */
+orc_matrix *orc_sym_square(const orc_matrix *U, int *status) {
+  orc_matrix *F = orc_sym_full(U, status);
+  if (!F) return NULL;
+  orc_matrix *C = orc_multiply_t(F, 0, F, 0, NULL, NULL, status);
+  orc_free(F);
+  if (C) C->root = keep_upper(C, C->root, 0, 0, 0);
+  return C;
+}
+
+/* Symmetric rank-k: C = A A^T (trans = 0) or A^T A (trans = 1), upper
+ * triangle. */
+orc_matrix *orc_syrk(const orc_matrix *A, int trans, int *status) {
+  orc_matrix *C = orc_multiply_t(A, trans != 0, A, trans == 0, NULL, NULL, status);
+  if (C) C->root = keep_upper(C, C->root, 0, 0, 0);
+  return C;
+}
+
+/* C = S B (side 0, S = A symmetric) or C = A S (side 1, S = B symmetric). */
+orc_matrix *orc_symm(const orc_matrix *A, const orc_matrix *B, int side, int *status) {
+  orc_matrix *F = orc_sym_full(side == 0 ? A : B, status);
+  if (!F) return NULL;
+  orc_matrix *C = side == 0 ? orc_multiply_t(F, 0, B, 0, NULL, NULL, status)
+                            : orc_multiply_t(A, 0, F, 0, NULL, NULL, status);
+  orc_free(F);
   return C;
 }
 

@@ -19,6 +19,10 @@ LIB_PATH = os.path.join(_HERE, "libbsm.so")
 BSM_FP64 = 0
 BSM_SPLIT_BF16 = 1
 BSM_FLAG_AUTOTUNE = 1
+BSM_FLAG_TRANS_A = 2
+BSM_FLAG_TRANS_B = 4
+BSM_SYM_LEFT = 0
+BSM_SYM_RIGHT = 1
 
 STATUS = {
     0: "BSM_OK", -1: "BSM_ERR_INVALID_ARG", -2: "BSM_ERR_DIM_MISMATCH", -3: "BSM_ERR_BLOCKSIZE",
@@ -31,6 +35,12 @@ _P, _I64, _I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
 _PROTOS = {
     "bsm_build": (_I32, [_I64, _I64, _I32, _I64, _P, _P, _P, _I32, _P, _P]),
     "bsm_multiply": (_I32, [_P, _P, _P, _P, _P]),
+    "bsm_transpose": (_I32, [_P, _P, _P]),
+    "bsm_add": (_I32, [_P, _P, _P, _P]),
+    "bsm_sym_square": (_I32, [_P, _P, _P, _P]),
+    "bsm_syrk": (_I32, [_P, _I32, _P, _P, _P]),
+    "bsm_sym_multiply": (_I32, [_P, _P, _I32, _P, _P, _P]),
+    "bsm_sym_to_full": (_I32, [_P, _P, _P]),
     "bsm_multiply_batched": (_I32, [_I32, _P, _P, _P, _P, _P]),
     "bsm_to_blocks": (_I32, [_P, _P, _P, _P, _P, _I32, _P]),
     "bsm_info": (_I32, [_P, _P, _P, _P, _P]),
@@ -157,19 +167,68 @@ def bsm_build(nrows: int, ncols: int, bs: int, brow, bcol, vals, stream=None) ->
     return Matrix(out.value)
 
 
-def _opts(prec: int, slices: int):
-    if prec == BSM_FP64 and slices == 0:
+def _opts(prec: int, slices: int, flags: int = 0):
+    if prec == BSM_FP64 and slices == 0 and flags == 0:
         return None
-    return ctypes.byref(bsm_mult_opts(prec, slices, 0))
+    return ctypes.byref(bsm_mult_opts(prec, slices, flags))
 
 
 def bsm_multiply(A: Matrix, B: Matrix, prec: int = BSM_FP64, slices: int = 0,
-                 stream=None) -> Matrix:
+                 stream=None, trans_a: bool = False, trans_b: bool = False) -> Matrix:
+    """C = op(A) op(B); op(X) = X^T when trans_x is set."""
     lib = load()
     out = ctypes.c_void_p()
-    code = lib.bsm_multiply(A.handle, B.handle, ctypes.byref(out), _opts(prec, slices),
+    flags = (BSM_FLAG_TRANS_A if trans_a else 0) | (BSM_FLAG_TRANS_B if trans_b else 0)
+    code = lib.bsm_multiply(A.handle, B.handle, ctypes.byref(out), _opts(prec, slices, flags),
                             _stream_ptr(stream))
     _check(code, "bsm_multiply")
+    return Matrix(out.value)
+
+
+def bsm_transpose(A: Matrix, stream=None) -> Matrix:
+    out = ctypes.c_void_p()
+    _check(load().bsm_transpose(A.handle, ctypes.byref(out), _stream_ptr(stream)),
+           "bsm_transpose")
+    return Matrix(out.value)
+
+
+def bsm_add(A: Matrix, B: Matrix, stream=None) -> Matrix:
+    out = ctypes.c_void_p()
+    _check(load().bsm_add(A.handle, B.handle, ctypes.byref(out), _stream_ptr(stream)), "bsm_add")
+    return Matrix(out.value)
+
+
+def bsm_sym_square(A: Matrix, prec: int = BSM_FP64, slices: int = 0, stream=None) -> Matrix:
+    """Upper triangle of A*A; A symmetric in upper-triangle storage."""
+    out = ctypes.c_void_p()
+    _check(load().bsm_sym_square(A.handle, ctypes.byref(out), _opts(prec, slices),
+                                 _stream_ptr(stream)), "bsm_sym_square")
+    return Matrix(out.value)
+
+
+def bsm_syrk(A: Matrix, trans: bool = False, prec: int = BSM_FP64, slices: int = 0,
+             stream=None) -> Matrix:
+    """Upper triangle of A A^T (trans False) or A^T A (trans True)."""
+    out = ctypes.c_void_p()
+    _check(load().bsm_syrk(A.handle, int(bool(trans)), ctypes.byref(out), _opts(prec, slices),
+                           _stream_ptr(stream)), "bsm_syrk")
+    return Matrix(out.value)
+
+
+def bsm_sym_multiply(A: Matrix, B: Matrix, side: int = BSM_SYM_LEFT, prec: int = BSM_FP64,
+                     slices: int = 0, stream=None) -> Matrix:
+    """A B with A (side BSM_SYM_LEFT) or B (BSM_SYM_RIGHT) symmetric in
+    upper-triangle storage."""
+    out = ctypes.c_void_p()
+    _check(load().bsm_sym_multiply(A.handle, B.handle, int(side), ctypes.byref(out),
+                                   _opts(prec, slices), _stream_ptr(stream)), "bsm_sym_multiply")
+    return Matrix(out.value)
+
+
+def bsm_sym_to_full(A: Matrix, stream=None) -> Matrix:
+    out = ctypes.c_void_p()
+    _check(load().bsm_sym_to_full(A.handle, ctypes.byref(out), _stream_ptr(stream)),
+           "bsm_sym_to_full")
     return Matrix(out.value)
 
 

@@ -123,9 +123,11 @@ bsm_status symbolic_multiply(bsm_matrix A, bsm_matrix B, SymbolicResult *out, cu
 // ranges of C, each handed to `sink` (which may take ownership of the arrays
 // by clearing the pointers).  budget: pairs per level part (0 = default, or
 // the BSM_SYM_BUDGET environment variable).  tasks[h]: pairs per height.
+// upper: only C blocks with I <= J (symmetric square and SYRK results).
 using LeafSink = std::function<bsm_status(SymbolicResult &)>;
 bsm_status symbolic_chunks(bsm_matrix A, bsm_matrix B, const LeafSink &sink, int64_t *tasks,
-                           int *H, int *nchunks, cudaStream_t s, int64_t budget);
+                           int *H, int *nchunks, cudaStream_t s, int64_t budget,
+                           bool upper = false);
 void free_symbolic(SymbolicResult *r, cudaStream_t s);
 
 // ----------------------------------------------------------- numeric phase
@@ -147,17 +149,20 @@ bsm_status numeric_fp64_batched(int bs, const ProdDesc *prods, const uint64_t *i
                                 int ctas_per_sm, cudaStream_t s);
 bsm_status split_supported(int bs, int slices);
 int split_flush_group(int bs, int slices);
-bsm_status split_prepare(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, int slices,
-                         int *dmax_dev, unsigned *errword, ProdDesc &d, std::vector<void *> &owned,
-                         cudaStream_t s);
+bsm_status split_prepare(bsm_matrix A, bsm_matrix B, int slices, unsigned *errword, ProdDesc &d,
+                         std::vector<void *> &owned, cudaStream_t s);
+// fold: device scratch of split_fold_bytes(bs) bytes, private to the launch
+// (C blocks with very long product lists park exact partial sums there).
 bsm_status split_launch(int bs, int slices, const ProdDesc *prods_dev, const uint64_t *items,
                         int64_t nitems, unsigned long long *work, unsigned *errword,
-                        cudaStream_t s, int chunk = 32);
+                        int64_t *fold, cudaStream_t s, int chunk = 32);
+size_t split_fold_bytes(int bs);
+// Longest product list of a task list, atomically maxed into *dmax_dev.
+void launch_max_seg(const SymbolicResult &sym, int *dmax_dev, cudaStream_t s);
 bsm_status split_alloc(bsm_matrix A, bsm_matrix B, int slices, ProdDesc &d,
                        std::vector<void *> &owned, cudaStream_t s);
 bsm_status split_compute(bsm_matrix A, bsm_matrix B, int slices, const ProdDesc &d,
                          unsigned *errword, cudaStream_t s);
-void launch_max_seg(const SymbolicResult &sym, int *dmax_dev, cudaStream_t s);
 
 // C assembly from a numeric result: zero removal and level build.
 // finish_product takes ownership of sym->ckeys and cvals; finish_product_copy
@@ -167,7 +172,15 @@ bsm_status finish_product(bsm_matrix C, SymbolicResult *sym, double *cvals, int3
 bsm_status finish_product_copy(bsm_matrix C, const SymbolicResult &sym, const double *cvals,
                                const int32_t *nz, unsigned *err, cudaStream_t s);
 bsm_status check_pair(bsm_matrix A, bsm_matrix B);
-bsm_status check_opts(const bsm_mult_opts *o, int *prec, int *slices);
+// One product through the chunked symbolic phase and the chosen numeric
+// phase (bsm_multiply.cu); upper: only C blocks with I <= J.
+bsm_status multiply_one(bsm_matrix A, bsm_matrix B, int prec, int slices, cudaStream_t s,
+                        bsm_matrix *out, bool upper = false);
+// dst[t] = src[idx[t] & 0x7FFFFFFF], transposed when bit 31 of idx[t] is set
+// (bsm_ops.cu).
+void launch_gather_blocks_t(const double *src, const int32_t *idx, double *dst, int64_t n, int bs,
+                            cudaStream_t s);
+bsm_status check_opts(const bsm_mult_opts *o, int *prec, int *slices, int allowed_flags);
 
 // Handle shells for results (bsm_tree.cu).
 bsm_matrix new_matrix_shell(int64_t nrows, int64_t ncols, int bs, int L);

@@ -27,11 +27,11 @@ bsm_status check_pair(bsm_matrix A, bsm_matrix B) {
   return BSM_OK;
 }
 
-bsm_status check_opts(const bsm_mult_opts *o, int *prec, int *slices) {
+bsm_status check_opts(const bsm_mult_opts *o, int *prec, int *slices, int allowed_flags) {
   *prec = BSM_FP64;
   *slices = 0;
   if (!o) return BSM_OK;
-  if (o->flags != 0) return BSM_ERR_INVALID_ARG;
+  if (o->flags & ~allowed_flags) return BSM_ERR_INVALID_ARG;
   if (o->prec != BSM_FP64 && o->prec != BSM_SPLIT_BF16) return BSM_ERR_INVALID_ARG;
   if (o->slices < 0 || o->slices > 8) return BSM_ERR_INVALID_ARG;
   *prec = o->prec;
@@ -232,8 +232,8 @@ static bsm_status compact_chunk(SymbolicResult &r, double *&cvals, const int32_t
 // One product: the symbolic phase delivers the task list in Morton-range
 // chunks (one chunk unless a level exceeds the pair budget); each chunk is
 // computed and compacted as it arrives, and C is assembled from the chunks.
-static bsm_status multiply_one(bsm_matrix A, bsm_matrix B, int prec, int slices, cudaStream_t s,
-                               bsm_matrix *out) {
+bsm_status multiply_one(bsm_matrix A, bsm_matrix B, int prec, int slices, cudaStream_t s,
+                        bsm_matrix *out, bool upper) {
   *out = nullptr;
   LastStats &ls = last_stats();
   ls = LastStats();
@@ -303,7 +303,7 @@ static bsm_status multiply_one(bsm_matrix A, bsm_matrix B, int prec, int slices,
   };
   int H = 0, nch = 0;
   int64_t tasks[BSM_MAXH + 1];
-  if (st == BSM_OK) st = symbolic_chunks(A, B, sink, tasks, &H, &nch, s, 0);
+  if (st == BSM_OK) st = symbolic_chunks(A, B, sink, tasks, &H, &nch, s, 0, upper);
   int64_t mb = A->mb, nb = B->nb;
   int64_t side = mb > nb ? mb : nb;
   bsm_matrix C = new_matrix_shell(A->nrows, B->ncols, bs, ceil_log2_i64(side < 1 ? 1 : side));
@@ -364,10 +364,28 @@ extern "C" bsm_status bsm_multiply(bsm_matrix A, bsm_matrix B, bsm_matrix *C,
                                    const bsm_mult_opts *opts, void *stream) {
   if (!C) return BSM_ERR_INVALID_ARG;
   *C = nullptr;
-  BSM_TRY(check_pair(A, B));
+  if (!A || !B) return BSM_ERR_INVALID_ARG;
   int prec, slices;
-  BSM_TRY(check_opts(opts, &prec, &slices));
-  return multiply_one(A, B, prec, slices, (cudaStream_t)stream, C);
+  BSM_TRY(check_opts(opts, &prec, &slices, BSM_FLAG_TRANS_A | BSM_FLAG_TRANS_B));
+  const int flags = opts ? opts->flags : 0;
+  const bool ta = flags & BSM_FLAG_TRANS_A, tb = flags & BSM_FLAG_TRANS_B;
+  // op(A) and op(B) dimensions are checked before any transposition is made.
+  if ((ta ? A->nrows : A->ncols) != (tb ? B->ncols : B->nrows)) return BSM_ERR_DIM_MISMATCH;
+  if (A->bs != B->bs) return BSM_ERR_BLOCKSIZE;
+  if (A->device != B->device) return BSM_ERR_INVALID_ARG;
+  if (prec != BSM_FP64) BSM_TRY(split_supported(A->bs, slices));
+  cudaStream_t s = (cudaStream_t)stream;
+  // The transposed task types (Sec. 3.2) are the plain product of transposed
+  // handles: op(X) is X with its keys' row and column bits swapped and every
+  // block transposed, made once here and released after the product.
+  bsm_matrix At = nullptr, Bt = nullptr;
+  bsm_status st = BSM_OK;
+  if (ta) st = bsm_transpose(A, &At, stream);
+  if (st == BSM_OK && tb) st = (A == B && ta) ? (Bt = At, BSM_OK) : bsm_transpose(B, &Bt, stream);
+  if (st == BSM_OK) st = multiply_one(ta ? At : A, tb ? Bt : B, prec, slices, s, C);
+  if (Bt && Bt != At) bsm_destroy(Bt);
+  if (At) bsm_destroy(At);
+  return st;
 }
 
 extern "C" bsm_status bsm_last_chunks(int *nchunks) {
@@ -479,7 +497,7 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
     for (int i = 0; i < n && st == BSM_OK; i++) {
       h[i] = make_desc(A[idx[i]], B[idx[i]], sym[i], cv[i], nz[i]);
       if (prec != BSM_FP64 && sym[i].nc > 0)
-        st = split_prepare(A[idx[i]], B[idx[i]], sym[i], slices, scr, err, h[i], owned, s);
+        st = split_prepare(A[idx[i]], B[idx[i]], slices, err, h[i], owned, s);
     }
     if (st == BSM_OK) {
       void *hp = host_scratch().get(sizeof(ProdDesc) * n + 16);
@@ -487,24 +505,19 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
       if (st == BSM_OK) {
         memcpy(hp, h.data(), sizeof(ProdDesc) * n);
         cudaMemcpyAsync(table, hp, sizeof(ProdDesc) * n, cudaMemcpyHostToDevice, s);
-        if (prec != BSM_FP64) {
-          // the 32-bit diagonal accumulators hold at most 511 flushes
-          int *hm = (int *)((char *)hp + sizeof(ProdDesc) * n);
-          cudaMemcpyAsync(hm, scr, 4, cudaMemcpyDeviceToHost, s);
-          st = cuda_status(cudaStreamSynchronize(s));
-          const int flushk = split_flush_group(bs, slices);
-          if (st == BSM_OK && (hm[0] + flushk - 1) / flushk > 511) st = BSM_ERR_UNSUPPORTED;
-        } else {
-          st = cuda_status(cudaStreamSynchronize(s));  // host table reused below
-        }
+        st = cuda_status(cudaStreamSynchronize(s));  // host table reused below
       }
     }
+    int64_t *fold = nullptr;
+    if (st == BSM_OK && prec != BSM_FP64 &&
+        (st = dev_alloc((void **)&fold, split_fold_bytes(bs), s)) == BSM_OK)
+      owned.push_back(fold);
     unsigned long long *counter = reinterpret_cast<unsigned long long *>(scr + 2);
     if (st == BSM_OK) {
       if (prec == BSM_FP64)
         st = numeric_fp64_batched(bs, table, v1, total, counter, err, 0, s);
       else
-        st = split_launch(bs, slices, table, v1, total, counter, err, s, 32);
+        st = split_launch(bs, slices, table, v1, total, counter, err, fold, s, 32);
     }
   }
   timer.mark(s);
@@ -534,7 +547,7 @@ extern "C" bsm_status bsm_multiply_batched(int n, const bsm_matrix *A, const bsm
   for (int i = 0; i < n; i++) C[i] = nullptr;
   for (int i = 0; i < n; i++) BSM_TRY(check_pair(A[i], B[i]));
   int prec, slices;
-  BSM_TRY(check_opts(opts, &prec, &slices));
+  BSM_TRY(check_opts(opts, &prec, &slices, 0));
   if (prec != BSM_FP64)
     for (int i = 0; i < n; i++) BSM_TRY(split_supported(A[i]->bs, slices));
   cudaStream_t s = (cudaStream_t)stream;

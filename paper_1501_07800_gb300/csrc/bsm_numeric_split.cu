@@ -284,8 +284,13 @@ struct SplitArgs {
   unsigned *err;
   unsigned long long *work;  // chunk counter, zero at launch
   int chunk;                 // work items claimed per atomic (1..32)
+  int64_t *fold;             // [grid][2 teams][BS*BS][hi, lo]: folded diagonal sums
 };
 constexpr int kChunk = 32;   // most work items claimed per atomic
+// The 32-bit diagonal sums in shared memory take at most kFold flushes of
+// magnitude < 2^22 each; a C block with more flushes folds them every kFold
+// flushes into exact 64-bit (hi, lo) pairs in per-CTA global scratch.
+constexpr int kFold = 511;
 
 // Per-C-block work descriptor handed from the producer warp to the MMA thread
 // and the epilogue through a shared-memory ring.
@@ -672,48 +677,91 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
       }
       mbar_arrive(&meta_empty[m]);
       const int nfl = (nk + P.flushk - 1) / P.flushk;
+      int64_t *const fold = P.fold + ((int64_t)blockIdx.x * 2 + team) * (BS * BS * 2);
       bool ok = true;
-      for (int f = 0; f < nfl && ok; f++, fct++) {
-        bool w = mbar_wait(&tfull[team], fct & 1u);
-        if (!__all_sync(0xffffffffu, w && abort_flag == 0)) {
-          set_err(P.err, DERR_TIMEOUT);
-          abort_flag = 1;
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-#pragma unroll
-        for (int g = 0; g < G; g++) {
-          uint32_t v[HC];
-          if constexpr (HC == 16)
-            tmem_ld16(tbase + lane_addr + (uint32_t)((team * G + g) * BS + c0), v);
-          else
-            tmem_ld8(tbase + lane_addr + (uint32_t)((team * G + g) * BS + c0), v);
-          tmem_ld_wait();
-          const int d = g * DPG + L;
-          if (d < S) {
-            // exact integer value of each FP32 sum (|D| < 2^22)
-            int32_t *dst = tcomb + (d * BS + r) * C::CROW + c0;
-#pragma unroll
-            for (int x = 0; x < HC; x += 4) {
-              int4 val = make_int4(
-                  (int32_t)(__float_as_uint(__uint_as_float(v[x]) + kMagicF) - kMagic),
-                  (int32_t)(__float_as_uint(__uint_as_float(v[x + 1]) + kMagicF) - kMagic),
-                  (int32_t)(__float_as_uint(__uint_as_float(v[x + 2]) + kMagicF) - kMagic),
-                  (int32_t)(__float_as_uint(__uint_as_float(v[x + 3]) + kMagicF) - kMagic));
-              if (f > 0) {
-                const int4 old = *reinterpret_cast<const int4 *>(dst + x);
-                val.x += old.x;
-                val.y += old.y;
-                val.z += old.z;
-                val.w += old.w;
-              }
-              *reinterpret_cast<int4 *>(dst + x) = val;
-            }
+      // Every warp runs all nfl iterations (doing no work once `ok` is false)
+      // so that the team meets the same fold barriers whatever happened.
+      for (int f = 0; f < nfl; f++, fct++) {
+        if (ok) {
+          bool w = mbar_wait(&tfull[team], fct & 1u);
+          if (!__all_sync(0xffffffffu, w && abort_flag == 0)) {
+            set_err(P.err, DERR_TIMEOUT);
+            abort_flag = 1;
+            ok = false;
           }
         }
-        tc_fence_before();
-        mbar_arrive(&tempty[team]);
+        if (ok) {
+          tc_fence_after();
+#pragma unroll
+          for (int g = 0; g < G; g++) {
+            uint32_t v[HC];
+            if constexpr (HC == 16)
+              tmem_ld16(tbase + lane_addr + (uint32_t)((team * G + g) * BS + c0), v);
+            else
+              tmem_ld8(tbase + lane_addr + (uint32_t)((team * G + g) * BS + c0), v);
+            tmem_ld_wait();
+            const int d = g * DPG + L;
+            if (d < S) {
+              // exact integer value of each FP32 sum (|D| < 2^22)
+              int32_t *dst = tcomb + (d * BS + r) * C::CROW + c0;
+#pragma unroll
+              for (int x = 0; x < HC; x += 4) {
+                int4 val = make_int4(
+                    (int32_t)(__float_as_uint(__uint_as_float(v[x]) + kMagicF) - kMagic),
+                    (int32_t)(__float_as_uint(__uint_as_float(v[x + 1]) + kMagicF) - kMagic),
+                    (int32_t)(__float_as_uint(__uint_as_float(v[x + 2]) + kMagicF) - kMagic),
+                    (int32_t)(__float_as_uint(__uint_as_float(v[x + 3]) + kMagicF) - kMagic));
+                if (f % kFold != 0) {
+                  const int4 old = *reinterpret_cast<const int4 *>(dst + x);
+                  val.x += old.x;
+                  val.y += old.y;
+                  val.z += old.z;
+                  val.w += old.w;
+                }
+                *reinterpret_cast<int4 *>(dst + x) = val;
+              }
+            }
+          }
+          tc_fence_before();
+          mbar_arrive(&tempty[team]);
+        }
+        if ((f + 1) % kFold == 0 && f + 1 < nfl) {
+          // the 32-bit sums are full: fold them into this thread's (hi, lo)
+          // pairs.  The barrier's OR makes `ok` uniform across the team.
+          if (named_bar_or(bar_id, kTeam, !ok || abort_flag != 0)) {
+            ok = false;
+          } else {
+#pragma unroll
+            for (int i = 0; i < GRP; i++) {
+              const int g4 = ttid + i * kTeam;
+              if (NG4 % kTeam != 0 && g4 >= NG4) break;
+              const int rr = g4 / (BS / 4), c4 = (g4 % (BS / 4)) * 4;
+              int4 dv[S];
+#pragma unroll
+              for (int d = 0; d < S; d++)
+                dv[d] = *reinterpret_cast<const int4 *>(tcomb + (d * BS + rr) * C::CROW + c4);
+#pragma unroll
+              for (int x = 0; x < 4; x++) {
+                int32_t dg[S];
+#pragma unroll
+                for (int d = 0; d < S; d++)
+                  dg[d] = x == 0 ? dv[d].x : x == 1 ? dv[d].y : x == 2 ? dv[d].z : dv[d].w;
+                int64_t hi, lo;
+                combine_digits<S>(dg, hi, lo);
+                int64_t *fp = fold + (rr * BS + c4 + x) * 2;
+                if (f + 1 > kFold) {
+                  hi += fp[0];
+                  lo += fp[1];
+                }
+                hi += lo >> 35;  // keep lo in [0, 2^35): hi 2^35 + lo unchanged
+                lo &= (1ll << 35) - 1;
+                fp[0] = hi;
+                fp[1] = lo;
+              }
+            }
+            named_bar(bar_id, kTeam);  // folded before the next drain overwrites
+          }
+        }
       }
       if (named_bar_or(bar_id, kTeam, !ok || abort_flag != 0)) break;
       double *cb = cvp + c * (int64_t)BS * BS;
@@ -736,9 +784,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
           for (int d = 0; d < S; d++) dg[d] = x == 0 ? dv[d].x : x == 1 ? dv[d].y : x == 2 ? dv[d].z : dv[d].w;
           int64_t hi, lo;
           combine_digits<S>(dg, hi, lo);
+          if (nfl > kFold) {
+            const int64_t *fp = fold + (rr * BS + c4 + x) * 2;
+            hi += fp[0];
+            lo += fp[1];
+          }
           const int fx = x == 0 ? fcol[i].x : x == 1 ? fcol[i].y : x == 2 ? fcol[i].z : fcol[i].w;
           out[x] = split_to_double(hi, lo, erow[i] + fx - XS);
-          any |= (hi | lo) != 0;
+          any |= out[x] != 0.0;
         }
         double2 *dst = reinterpret_cast<double2 *>(cb + rr * BS + c4);
         dst[0] = make_double2(out[0], out[1]);
@@ -779,6 +832,7 @@ bsm_status launch_split(const SplitArgs &a, cudaStream_t s) {
   const int64_t chunks = (a.nitems + a.chunk - 1) / a.chunk;
   int64_t grid = chunks < sms ? chunks : sms;
   if (grid < 1) return BSM_OK;
+  if (!a.fold) return BSM_ERR_INVALID_ARG;  // sized by split_fold_bytes: grid <= SM count
   count_launch();
   k_numeric_split<BS, S><<<(unsigned)grid, kThreads, C::SMEM, s>>>(a);
   return cuda_status(cudaGetLastError());
@@ -810,6 +864,13 @@ int split_flush_group(int bs, int s) {
   if (m2 < maxel) maxel = m2;
   int g = maxel / bs;
   return g < 1 ? 1 : g;
+}
+
+size_t split_fold_bytes(int bs) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return (size_t)(sms > 0 ? sms : 1) * 2 * bs * bs * 2 * sizeof(int64_t);
 }
 
 bsm_status split_supported(int bs, int slices) {
@@ -876,18 +937,17 @@ void launch_max_seg(const SymbolicResult &sym, int *dmax_dev, cudaStream_t s) {
   k_max_seg<<<grid_for(sym.nc, 256), 256, 0, s>>>(sym.seg, sym.nc, dmax_dev);
 }
 
-bsm_status split_prepare(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, int slices,
-                         int *dmax_dev, unsigned *errword, ProdDesc &d, std::vector<void *> &owned,
-                         cudaStream_t s) {
+bsm_status split_prepare(bsm_matrix A, bsm_matrix B, int slices, unsigned *errword, ProdDesc &d,
+                         std::vector<void *> &owned, cudaStream_t s) {
   BSM_TRY(split_alloc(A, B, slices, d, owned, s));
-  launch_max_seg(sym, dmax_dev, s);
   return split_compute(A, B, slices, d, errword, s);
 }
 
 bsm_status split_launch(int bs, int slices, const ProdDesc *prods_dev, const uint64_t *items,
                         int64_t nitems, unsigned long long *work, unsigned *errword,
-                        cudaStream_t s, int chunk) {
+                        int64_t *fold, cudaStream_t s, int chunk) {
   SplitArgs a;
+  a.fold = fold;
   a.chunk = chunk < 1 ? 1 : (chunk > kChunk ? kChunk : chunk);
   a.prods = prods_dev;
   a.items = items;
@@ -925,28 +985,27 @@ bsm_status numeric_split(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, 
   auto cleanup = [&]() {
     for (void *p : owned) dev_free(p, s);  // stream-ordered: after the kernel
   };
-  // scratch: [0] longest product list, [2..3] chunk counter, then the product table
+  // scratch: [2..3] chunk counter, then the product table
   int *scr = nullptr;
   bsm_status st = dev_alloc((void **)&scr, 16 + sizeof(ProdDesc), s);
   if (st != BSM_OK) return st;
   owned.push_back(scr);
   cudaMemsetAsync(scr, 0, 16, s);
   ProdDesc d = make_desc(A, B, sym, cvals, nzflag);
-  st = split_prepare(A, B, sym, slices, scr, errword, d, owned, s);
+  st = split_prepare(A, B, slices, errword, d, owned, s);
   int *h = (int *)host_scratch().get(16 + sizeof(ProdDesc));
   if (st == BSM_OK && !h) st = BSM_ERR_OOM;
   if (st == BSM_OK) {
     memcpy(h + 4, &d, sizeof(ProdDesc));
     cudaMemcpyAsync(scr + 4, h + 4, sizeof(ProdDesc), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(h, scr, 4, cudaMemcpyDeviceToHost, s);
-    st = cuda_status(cudaStreamSynchronize(s));
+    st = cuda_status(cudaStreamSynchronize(s));  // the host staging buffer is reused
   }
-  // the 32-bit diagonal accumulators hold at most 511 flushes of < 2^22
-  const int flushk = split_flush_group(bs, slices);
-  if (st == BSM_OK && (h[0] + flushk - 1) / flushk > 511) st = BSM_ERR_UNSUPPORTED;
+  int64_t *fold = nullptr;
+  if (st == BSM_OK && (st = dev_alloc((void **)&fold, split_fold_bytes(bs), s)) == BSM_OK)
+    owned.push_back(fold);
   if (st == BSM_OK)
     st = split_launch(bs, slices, reinterpret_cast<const ProdDesc *>(scr + 4), nullptr, sym.nc,
-                      reinterpret_cast<unsigned long long *>(scr + 2), errword, s);
+                      reinterpret_cast<unsigned long long *>(scr + 2), errword, fold, s);
   cleanup();
   return st;
 }

@@ -36,6 +36,7 @@ struct bsm_plan_s {
   ProdDesc *table = nullptr;
   int *scr = nullptr;  // [0] longest product list, [2..3] work counter
   unsigned *err = nullptr;
+  int64_t *fold = nullptr;  // split mode: scratch of the numeric kernel
   std::vector<void *> owned;
   // chosen configuration
   int order = 0;  // 0: longest first, 1: product-major Morton
@@ -92,7 +93,8 @@ bsm_status enqueue_numeric(bsm_plan P, int order, int chunk, int ctas, cudaStrea
     return numeric_fp64_batched(P->bs, P->table, items, P->nitems, counter, P->err, ctas, s);
   for (int i = 0; i < P->n; i++)
     if (P->sym[i].nc > 0) BSM_TRY(split_compute(P->A[i], P->B[i], P->slices, P->desc[i], P->err, s));
-  return split_launch(P->bs, P->slices, P->table, items, P->nitems, counter, P->err, s, chunk);
+  return split_launch(P->bs, P->slices, P->table, items, P->nitems, counter, P->err, P->fold, s,
+                      chunk);
 }
 
 void destroy_plan(bsm_plan P) {
@@ -202,7 +204,7 @@ extern "C" bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matr
   bsm_mult_opts o = opts ? *opts : bsm_mult_opts{BSM_FP64, 0, 0};
   o.flags &= ~BSM_FLAG_AUTOTUNE;
   int prec, slices;
-  BSM_TRY(check_opts(&o, &prec, &slices));
+  BSM_TRY(check_opts(&o, &prec, &slices, 0));
   const int bs = A[0]->bs;
   for (int i = 0; i < n; i++)
     if (A[i]->bs != bs) return BSM_ERR_BLOCKSIZE;  // one block size per plan
@@ -269,24 +271,19 @@ extern "C" bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matr
   }
   for (int i = 0; i < n && st == BSM_OK; i++) {
     P->desc[i] = make_desc(A[i], B[i], P->sym[i], P->cv[i], P->nz[i]);
-    if (prec != BSM_FP64 && P->sym[i].nc > 0) {
+    if (prec != BSM_FP64 && P->sym[i].nc > 0)
       st = split_alloc(A[i], B[i], slices, P->desc[i], P->owned, s);
-      launch_max_seg(P->sym[i], P->scr, s);
-    }
   }
+  if (st == BSM_OK && prec != BSM_FP64 &&
+      (st = dev_alloc((void **)&P->fold, split_fold_bytes(bs), s)) == BSM_OK)
+    P->owned.push_back(P->fold);
   if (st == BSM_OK) {
     void *hp = host_scratch().get(sizeof(ProdDesc) * n + 16);
     if (!hp) st = BSM_ERR_OOM;
     if (st == BSM_OK) {
       memcpy(hp, P->desc.data(), sizeof(ProdDesc) * n);
       cudaMemcpyAsync(P->table, hp, sizeof(ProdDesc) * n, cudaMemcpyHostToDevice, s);
-      int *hm = (int *)((char *)hp + sizeof(ProdDesc) * n);
-      cudaMemcpyAsync(hm, P->scr, 4, cudaMemcpyDeviceToHost, s);
       st = cuda_status(cudaStreamSynchronize(s));
-      if (st == BSM_OK && prec != BSM_FP64) {
-        const int flushk = split_flush_group(bs, slices);
-        if ((hm[0] + flushk - 1) / flushk > 511) st = BSM_ERR_UNSUPPORTED;
-      }
     }
   }
   if (st == BSM_OK && tune && P->nitems > 0) st = autotune(P);

@@ -57,10 +57,26 @@ __device__ __forceinline__ int quad_count(unsigned ma, unsigned mb, int m, int n
                ((ma >> (2 * m + 1)) & (mb >> (2 + n)) & 1u));
 }
 
+// Upper-triangle products (symmetric square, SYRK) keep only C nodes on or
+// above the diagonal.  Children of a node strictly above the diagonal all lie
+// above it; a diagonal node drops its lower-left quadrant q = 2 (m=1, n=0).
+struct UpperView {
+  const uint64_t *sck;  // segment C keys of the level part (NULL: full C)
+  const int32_t *pseg;  // segment id of each pair, offset by soff
+  int32_t soff;
+};
+
+__device__ __forceinline__ unsigned pair_qmask(const UpperView &u, int64_t p, unsigned qmask) {
+  if (!u.sck) return qmask;
+  const uint64_t k = u.sck[u.pseg[p] - u.soff];
+  const bool diag = ((k >> 1) & 0x5555555555555555ull) == (k & 0x5555555555555555ull);
+  return diag ? (qmask & ~4u) : qmask;
+}
+
 // Per pair: child counts of the quadrants in qmask; the level's exact total
 // is accumulated in 64 bits (one atomic per warp).
 __global__ void k_sym_count(const int32_t *__restrict__ pa, const int32_t *__restrict__ pb,
-                            int64_t np, LevelView va, LevelView vb, unsigned qmask,
+                            int64_t np, LevelView va, LevelView vb, unsigned qmask, UpperView up,
                             int4 *__restrict__ cnt, unsigned long long *__restrict__ total) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int t = 0;
@@ -69,6 +85,7 @@ __global__ void k_sym_count(const int32_t *__restrict__ pa, const int32_t *__res
     int32_t ca, cb;
     node_info(va, pa[p], ma, ca);
     node_info(vb, pb[p], mb, cb);
+    qmask = pair_qmask(up, p, qmask);
     int4 c = make_int4((qmask & 1u) ? quad_count(ma, mb, 0, 0) : 0,
                        (qmask & 2u) ? quad_count(ma, mb, 0, 1) : 0,
                        (qmask & 4u) ? quad_count(ma, mb, 1, 0) : 0,
@@ -128,10 +145,12 @@ __global__ void k_sym_fill(const int32_t *__restrict__ pa, const int32_t *__rest
                            const int32_t *__restrict__ pseg, int32_t soff, int64_t np,
                            const int32_t *__restrict__ sst, int32_t poff,
                            const int4 *__restrict__ P, const int32_t *__restrict__ nbase,
-                           LevelView va, LevelView vb, unsigned qmask, int32_t *__restrict__ npa,
-                           int32_t *__restrict__ npb, int32_t *__restrict__ npseg) {
+                           LevelView va, LevelView vb, unsigned qmask, UpperView up,
+                           int32_t *__restrict__ npa, int32_t *__restrict__ npb,
+                           int32_t *__restrict__ npseg) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
+  qmask = pair_qmask(up, p, qmask);
   int32_t s = pseg[p] - soff;
   int4 a = P[sst[s] - poff], b = P[sst[s + 1] - poff], me = P[p];
   unsigned ma, mb;
@@ -220,6 +239,7 @@ struct Expander {
   int64_t budget;
   int64_t *tasks;  // per height
   const LeafSink &sink;
+  bool upper;
   int chunks = 0;
 
   // segment starts [0] and [idx] of a level part, read back
@@ -281,8 +301,10 @@ struct Expander {
       return st;
     }
     cudaMemsetAsync(tot, 0, 8, s);
+    const UpperView up{upper ? L.sck : nullptr, L.pseg, L.soff};
     count_launch();
-    k_sym_count<<<grid_for(L.np + 1, 256), 256, 0, s>>>(L.pa, L.pb, L.np, va, vb, qmask, P, tot);
+    k_sym_count<<<grid_for(L.np + 1, 256), 256, 0, s>>>(L.pa, L.pb, L.np, va, vb, qmask, up, P,
+                                                         tot);
     unsigned long long *ht = (unsigned long long *)host_scratch().get(16);
     if (!ht) st = BSM_ERR_OOM;
     if (st == BSM_OK) {
@@ -361,7 +383,8 @@ struct Expander {
     k_sym_seg_write<<<grid_for(L.ns, 256), 256, 0, s>>>(L.sck, L.sst, L.poff, L.ns, P, nbase,
                                                         N.sck, N.sst);
     k_sym_fill<<<grid_for(L.np, 256), 256, 0, s>>>(L.pa, L.pb, L.pseg, L.soff, L.np, L.sst, L.poff,
-                                                   P, nbase, va, vb, qmask, N.pa, N.pb, N.pseg);
+                                                   P, nbase, va, vb, qmask, up, N.pa, N.pb,
+                                                   N.pseg);
     st = cuda_status(cudaGetLastError());
     dev_free(P, s);
     dev_free(nnz, s);
@@ -385,7 +408,7 @@ void free_symbolic(SymbolicResult *r, cudaStream_t s) {
 }
 
 bsm_status symbolic_chunks(bsm_matrix A, bsm_matrix B, const LeafSink &sink, int64_t *tasks,
-                           int *H, int *nchunks, cudaStream_t s, int64_t budget) {
+                           int *H, int *nchunks, cudaStream_t s, int64_t budget, bool upper) {
   const int h0 = A->L > B->L ? A->L : B->L;
   *H = h0;
   *nchunks = 0;
@@ -406,7 +429,7 @@ bsm_status symbolic_chunks(bsm_matrix A, bsm_matrix B, const LeafSink &sink, int
   count_launch();
   k_sym_root<<<1, 1, 0, s>>>(R.pa, R.pb, R.pseg, R.sck, R.sst);
   tasks[h0] = 1;
-  Expander ex{A, B, s, budget > 0 ? budget : pair_budget(), tasks, sink};
+  Expander ex{A, B, s, budget > 0 ? budget : pair_budget(), tasks, sink, upper};
   st = ex.process(R, 0xFu);
   free_level(R, s);
   *nchunks = ex.chunks;

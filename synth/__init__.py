@@ -96,6 +96,23 @@ def from_dense(d: np.ndarray, bs: int, keep_zero_blocks: bool = False) -> BlockC
 
 
 # ---------------------------------------------------------------- hashing
+def upper_blocks(m: BlockCOO) -> BlockCOO:
+    """The blocks with I <= J: upper-triangle storage of a symmetric matrix."""
+    k = m.brow <= m.bcol
+    return BlockCOO(m.nrows, m.ncols, m.bs, m.brow[k].copy(), m.bcol[k].copy(),
+                    np.ascontiguousarray(m.vals[k]))
+
+
+def random_upper(n: int, bs: int, p: float, seed: int) -> BlockCOO:
+    """Upper-triangle storage of a random symmetric matrix: random blocks with
+    I < J, and diagonal blocks made symmetric (x + x^T) where present."""
+    m = upper_blocks(random_blocks(n, bs, p, seed))
+    d = m.brow == m.bcol
+    v = m.vals.copy()
+    v[d] = v[d] + v[d].transpose(0, 2, 1)
+    return BlockCOO(m.nrows, m.ncols, m.bs, m.brow, m.bcol, v)
+
+
 def splitmix64(x: np.ndarray) -> np.ndarray:
     """SplitMix64 finaliser applied to x + golden gamma (vectorised, uint64)."""
     with np.errstate(over="ignore"):

@@ -66,6 +66,15 @@ def test_argument_checks_before_any_device_work(lib):
     n = ctypes.c_int64(0)
     assert lib.bsm_to_blocks(None, ctypes.byref(n), None, None, None, 0, None) == -1
     assert lib.bsm_info(None, None, None, None, None) == -1
+    assert lib.bsm_transpose(None, ctypes.byref(out), None) == -1
+    assert lib.bsm_transpose(None, None, None) == -1
+    assert lib.bsm_add(None, None, ctypes.byref(out), None) == -1
+    assert lib.bsm_add(None, None, None, None) == -1
+    assert lib.bsm_sym_square(None, ctypes.byref(out), None, None) == -1
+    assert lib.bsm_sym_square(None, None, None, None) == -1
+    assert lib.bsm_syrk(None, 0, ctypes.byref(out), None, None) == -1
+    assert lib.bsm_sym_multiply(None, None, 0, ctypes.byref(out), None, None) == -1
+    assert lib.bsm_sym_to_full(None, ctypes.byref(out), None) == -1
     assert lib.bsm_destroy(None) == 0
 
 

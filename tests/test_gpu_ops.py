@@ -1,0 +1,155 @@
+"""GPU parity of the remaining task types of Sec. 3.2: transposition, the
+transposed products C = A^T B, A B^T, A^T B^T, and C = A + B (Algorithm 2).
+
+Transposition and addition are bit-exact (data movement, and one rounding per
+entry).  Transposed products: structure bit-exact against the oracle's
+transposed recursion; values within 1e-12 relative Frobenius error in FP64 and
+1e-11 in the split mode, as for the plain product.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1501_07800_gb300 as bsm
+import synth
+from helpers import assert_same_structure, from_bsm, relerr, to_bsm
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+TOL_SPLIT = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    torch.cuda.init()
+    bsm.load()
+
+
+@pytest.mark.parametrize("bs", [16, 32, 64])
+def test_transpose_bit_exact(bs):
+    A = synth.random_blocks(40 * bs + 7, bs, 0.2, 300 + bs, ncols=23 * bs + 3)
+    T = from_bsm(bsm.bsm_transpose(to_bsm(A)))
+    E = A.transpose().sorted()
+    assert_same_structure(T, E)
+    assert np.array_equal(T.vals, E.vals)
+
+
+def test_transpose_levels_and_involution():
+    A = synth.random_blocks(3000, 32, 0.05, 311, ncols=1700)
+    M = to_bsm(A)
+    T = bsm.bsm_transpose(M)
+    TT = from_bsm(bsm.bsm_transpose(T))
+    assert_same_structure(TT, A.sorted())
+    assert np.array_equal(TT.vals, A.sorted().vals)
+    # the level arrays of the transposed handle are those of a fresh build
+    F = to_bsm(A.transpose())
+    assert np.array_equal(bsm.bsm_level_counts(T), bsm.bsm_level_counts(F))
+
+
+def test_transpose_empty():
+    Z = synth.BlockCOO(100, 60, 16, np.zeros(0, np.int32), np.zeros(0, np.int32),
+                       np.zeros((0, 16, 16)))
+    T = bsm.bsm_transpose(to_bsm(Z))
+    assert bsm.bsm_info(T) == (60, 100, 16, 0)
+
+
+@pytest.mark.parametrize("ta,tb", [(1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("n,k,m,bs", [(1000, 777, 1234, 32), (520, 300, 410, 16),
+                                      (640, 640, 640, 64)])
+def test_transposed_products_fp64(ta, tb, n, k, m, bs):
+    A = synth.random_blocks(k if ta else n, bs, 0.15, 320 + n, ncols=n if ta else k)
+    B = synth.random_blocks(m if tb else k, bs, 0.15, 321 + m, ncols=k if tb else m)
+    C = from_bsm(bsm.bsm_multiply(to_bsm(A), to_bsm(B), trans_a=bool(ta), trans_b=bool(tb)))
+    E = oracle.multiply(A, B, trans_a=bool(ta), trans_b=bool(tb)).C
+    assert_same_structure(C, E)
+    assert relerr(C.vals, E.vals) < TOL
+
+
+@pytest.mark.parametrize("ta,tb", [(1, 0), (0, 1), (1, 1)])
+def test_transposed_products_split(ta, tb):
+    A = synth.random_blocks(1500, 32, 0.1, 330, ncols=900)
+    B = synth.random_blocks(1500 if not tb else 1100, 32, 0.1, 331,
+                            ncols=1100 if not tb else 1500)
+    if not ta:
+        A = A.transpose()          # op(A) = A must be 900 x 1500
+    C = from_bsm(bsm.bsm_multiply(to_bsm(A), to_bsm(B), prec=bsm.BSM_SPLIT_BF16,
+                                  trans_a=bool(ta), trans_b=bool(tb)))
+    E = oracle.multiply(A, B, trans_a=bool(ta), trans_b=bool(tb)).C
+    assert_same_structure(C, E)
+    assert relerr(C.vals, E.vals) < TOL_SPLIT
+
+
+def test_gram_matrices_same_handle():
+    """A^T A and A A^T with one handle passed twice."""
+    A = synth.random_blocks(1200, 32, 0.1, 340, ncols=800)
+    M = to_bsm(A)
+    for ta, tb in [(1, 0), (0, 1)]:
+        C = from_bsm(bsm.bsm_multiply(M, M, trans_a=bool(ta), trans_b=bool(tb)))
+        E = oracle.multiply(A, A, trans_a=bool(ta), trans_b=bool(tb)).C
+        assert_same_structure(C, E)
+        assert relerr(C.vals, E.vals) < TOL
+
+
+def test_transposed_dimension_check():
+    M = to_bsm(synth.random_blocks(640, 32, 0.2, 350, ncols=320))
+    with pytest.raises(bsm.BsmError) as e:
+        bsm.bsm_multiply(M, M)
+    assert e.value.name == "BSM_ERR_DIM_MISMATCH"
+    with pytest.raises(bsm.BsmError) as e:
+        bsm.bsm_multiply(M, M, trans_a=True, trans_b=True)
+    assert e.value.name == "BSM_ERR_DIM_MISMATCH"
+
+
+@pytest.mark.parametrize("bs", [16, 32, 64])
+def test_add_bit_exact(bs):
+    A = synth.random_blocks(50 * bs + 9, bs, 0.2, 360 + bs, ncols=31 * bs + 5)
+    B = synth.random_blocks(50 * bs + 9, bs, 0.2, 361 + bs, ncols=31 * bs + 5)
+    C = from_bsm(bsm.bsm_add(to_bsm(A), to_bsm(B)))
+    E = oracle.add(A, B)
+    assert_same_structure(C, E)
+    assert np.array_equal(C.vals, E.vals)
+
+
+def test_add_cancellation_and_empty():
+    A = synth.random_blocks(2000, 32, 0.05, 370)
+    S = A.sorted()
+    neg = synth.BlockCOO(A.nrows, A.ncols, A.bs, S.brow.copy(), S.bcol.copy(), -S.vals)
+    assert bsm.bsm_info(bsm.bsm_add(to_bsm(A), to_bsm(neg)))[3] == 0
+    part = synth.BlockCOO(A.nrows, A.ncols, A.bs, S.brow[::3].copy(), S.bcol[::3].copy(),
+                          -S.vals[::3])
+    C = from_bsm(bsm.bsm_add(to_bsm(A), to_bsm(part)))
+    E = oracle.add(A, part)
+    assert_same_structure(C, E)
+    assert np.array_equal(C.vals, E.vals)
+    Z = synth.BlockCOO(2000, 2000, 32, np.zeros(0, np.int32), np.zeros(0, np.int32),
+                       np.zeros((0, 32, 32)))
+    C = from_bsm(bsm.bsm_add(to_bsm(Z), to_bsm(A)))
+    assert_same_structure(C, S)
+    assert np.array_equal(C.vals, S.vals)
+    assert bsm.bsm_info(bsm.bsm_add(to_bsm(Z), to_bsm(Z)))[3] == 0
+
+
+def test_add_then_multiply_levels_valid():
+    """The sum is a complete handle: its product matches the oracle's."""
+    A = synth.random_blocks(1500, 32, 0.05, 380)
+    B = synth.random_blocks(1500, 32, 0.05, 381)
+    S = bsm.bsm_add(to_bsm(A), to_bsm(B))
+    C = from_bsm(bsm.bsm_multiply(S, S))
+    s = oracle.add(A, B)
+    E = oracle.multiply(s, s).C
+    assert_same_structure(C, E)
+    assert relerr(C.vals, E.vals) < TOL
+
+
+def test_add_errors():
+    A = to_bsm(synth.random_blocks(640, 32, 0.2, 390))
+    B = to_bsm(synth.random_blocks(640, 32, 0.2, 391, ncols=320))
+    with pytest.raises(bsm.BsmError) as e:
+        bsm.bsm_add(A, B)
+    assert e.value.name == "BSM_ERR_DIM_MISMATCH"
+    C = to_bsm(synth.random_blocks(640, 16, 0.2, 392))
+    with pytest.raises(bsm.BsmError) as e:
+        bsm.bsm_add(A, C)
+    assert e.value.name == "BSM_ERR_BLOCKSIZE"

@@ -111,6 +111,51 @@ def test_long_k_lists_split():
     assert relerr(C.vals, E.vals) < TOL_SPLIT
 
 
+@pytest.mark.parametrize("bs,nk", [(32, 1600), (32, 5000), (16, 3600), (16, 8000)])
+def test_fold_of_very_long_k_lists_exact(bs, nk):
+    """C blocks whose product lists exceed the 511 flushes that the 32-bit
+    diagonal sums hold: the sums are folded into 64-bit pairs (one to several
+    times) and the integer result stays bit-exact."""
+    A = synth.random_blocks(2 * bs, bs, 1.0, 36, dist="int8", ncols=bs * nk)
+    B = synth.random_blocks(bs * nk, bs, 1.0, 37, dist="int8", ncols=2 * bs)
+    C = split_product(A, B)
+    E = oracle.multiply(A, B).C
+    assert_same_structure(C, E)
+    assert np.array_equal(C.vals, E.vals)
+
+
+@pytest.mark.parametrize("slices", [1, 7])
+def test_fold_prevents_32bit_overflow(slices):
+    """All entries 127: every diagonal-0 product term is 127^2, the 32-bit sum
+    of a C entry would pass 2^31 after ~1330 flushes; with 5000 products
+    (1667 flushes) the exact result 127^2 * 32 * 5000 needs the folds."""
+    bs, nk = 32, 5000
+    ones = np.full((nk, bs, bs), 127.0)
+    A = synth.BlockCOO(bs, bs * nk, bs, np.zeros(nk, np.int32), np.arange(nk, dtype=np.int32),
+                       ones)
+    B = synth.BlockCOO(bs * nk, bs, bs, np.arange(nk, dtype=np.int32), np.zeros(nk, np.int32),
+                       ones.copy())
+    C = split_product(A, B, slices=slices)
+    assert C.nblk == 1
+    assert np.all(C.vals == 127.0 ** 2 * bs * nk)
+
+
+def test_fold_real_values_and_batched_and_plan():
+    bs, nk = 32, 2100
+    A = synth.random_blocks(bs, bs, 1.0, 38, ncols=bs * nk)
+    B = synth.random_blocks(bs * nk, bs, 1.0, 39, ncols=bs)
+    E = oracle.multiply(A, B).C
+    C = split_product(A, B)
+    assert relerr(C.vals, E.vals) < TOL_SPLIT
+    ga, gb = to_bsm(A), to_bsm(B)
+    Cb = from_bsm(bsm.bsm_multiply_batched([ga, ga], [gb, gb], prec=bsm.BSM_SPLIT_BF16)[1])
+    assert np.array_equal(Cb.vals, C.vals)
+    plan = bsm.bsm_plan_create([ga], [gb], prec=bsm.BSM_SPLIT_BF16)
+    bsm.bsm_plan_execute(plan)
+    Cp = from_bsm(bsm.bsm_plan_results(plan)[0])
+    assert np.array_equal(Cp.vals, C.vals)
+
+
 def test_decay_square_split():
     A = synth.decay(300, 16, 33)
     C = split_product(A, A)

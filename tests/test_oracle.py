@@ -147,6 +147,163 @@ def test_associativity_and_transpose():
     assert_same_structure(btat, ab.transpose().sorted())
 
 
+# ------------------------------------- transposed task types and C = A + B
+@pytest.mark.parametrize("ta,tb", [(1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("n,k,m,bs,leaf", [(300, 200, 250, 16, 64), (97, 131, 77, 8, 8),
+                                           (256, 256, 256, 32, 4096)])
+def test_transposed_products_bruteforce(ta, tb, n, k, m, bs, leaf):
+    """op(A) op(B) against the dense product of the transposed dense arrays."""
+    A = synth.random_blocks(k if ta else n, bs, 0.25, 91 + n, ncols=n if ta else k)
+    B = synth.random_blocks(m if tb else k, bs, 0.25, 92 + m, ncols=k if tb else m)
+    P = oracle.multiply(A, B, leaf_dim=leaf, trans_a=bool(ta), trans_b=bool(tb))
+    a = A.to_dense().T if ta else A.to_dense()
+    b = B.to_dense().T if tb else B.to_dense()
+    E = synth.from_dense(a @ b, bs).sorted()
+    assert_same_structure(P.C, E)
+    assert relerr(P.C.vals, E.vals) < 1e-14
+    assert (P.C.nrows, P.C.ncols) == (n, m)
+    # the transposed recursion visits the same products in the same order as
+    # the plain recursion on explicitly transposed operands: identical bits
+    Q = oracle.multiply(A.transpose() if ta else A, B.transpose() if tb else B, leaf_dim=leaf)
+    assert_same_structure(P.C, Q.C)
+    assert np.array_equal(P.C.vals, Q.C.vals)
+    assert np.array_equal(P.tasks, Q.tasks) and P.triples == Q.triples
+
+
+def test_transposed_dimension_check():
+    A = synth.random_blocks(64, 16, 0.5, 1, ncols=48)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.multiply(A, A, trans_a=False, trans_b=False)
+    assert e.value.code == -2
+    assert oracle.multiply(A, A, trans_a=True).C.nrows == 48      # A^T A: 48 x 48
+    assert oracle.multiply(A, A, trans_b=True).C.nrows == 64      # A A^T: 64 x 64
+
+
+@pytest.mark.parametrize("n,m,bs,p,leaf", [(300, 200, 16, 0.3, 64), (97, 131, 8, 0.5, 8),
+                                           (512, 512, 32, 0.05, 4096)])
+def test_add_bruteforce(n, m, bs, p, leaf):
+    A = synth.random_blocks(n, bs, p, 101 + n, ncols=m)
+    B = synth.random_blocks(n, bs, p, 102 + m, ncols=m)
+    C = oracle.add(A, B, leaf_dim=leaf)
+    # one rounding per entry: the sum is bit-exact against the dense sum
+    E = synth.from_dense(A.to_dense() + B.to_dense(), bs).sorted()
+    assert_same_structure(C, E)
+    assert np.array_equal(C.vals, E.vals)
+    keys = set(zip(A.brow.tolist(), A.bcol.tolist())) | set(zip(B.brow.tolist(), B.bcol.tolist()))
+    assert set(zip(C.brow.tolist(), C.bcol.tolist())) == keys   # generic data: no cancellation
+    D = oracle.add(B, A, leaf_dim=leaf)
+    assert np.array_equal(C.vals, D.vals)
+
+
+def test_add_cancellation_and_identity():
+    A = synth.random_blocks(200, 16, 0.3, 111)
+    neg = synth.BlockCOO(A.nrows, A.ncols, A.bs, A.brow.copy(), A.bcol.copy(), -A.vals)
+    assert oracle.add(A, neg).nblk == 0
+    Z = synth.BlockCOO(200, 200, 16, np.zeros(0, np.int32), np.zeros(0, np.int32),
+                       np.zeros((0, 16, 16)))
+    S = oracle.add(A, Z)
+    assert_same_structure(S, A.sorted())
+    assert np.array_equal(S.vals, A.sorted().vals)
+    # partial cancellation: one block of the sum cancels, the others stay
+    half = A.sorted()
+    part = synth.BlockCOO(A.nrows, A.ncols, A.bs, half.brow[:1].copy(), half.bcol[:1].copy(),
+                          -half.vals[:1])
+    T = oracle.add(half, part)
+    assert T.nblk == A.nblk - 1
+    B = synth.random_blocks(200, 16, 0.3, 112, ncols=120)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.add(A, B)
+    assert e.value.code == -2
+
+
+# ------------------------------------------------- symmetric task types
+def dense_sym(U):
+    """Dense symmetric matrix of upper-triangle storage, by numpy: the stored
+    blocks, plus every strictly-upper block transposed into the mirror."""
+    bs, nb = U.bs, -(-U.nrows // U.bs)
+    d = np.zeros((nb * bs, nb * bs))
+    for I, J, v in zip(U.brow, U.bcol, U.vals):
+        d[I * bs:(I + 1) * bs, J * bs:(J + 1) * bs] = v
+        if I < J:
+            d[J * bs:(J + 1) * bs, I * bs:(I + 1) * bs] = v.T
+    return d[:U.nrows, :U.ncols]
+
+
+def upper_of_dense(d, bs):
+    return synth.upper_blocks(synth.from_dense(d, bs)).sorted()
+
+
+@pytest.mark.parametrize("n,bs,p,leaf", [(300, 16, 0.2, 64), (97, 8, 0.4, 8), (512, 32, 0.1, 4096)])
+def test_sym_full_and_square_bruteforce(n, bs, p, leaf):
+    U = synth.random_upper(n, bs, p, 121 + n)
+    S = dense_sym(U)
+    assert np.array_equal(S, S.T)
+    F = oracle.sym_full(U, leaf_dim=leaf)
+    assert np.array_equal(F.to_dense(), S)
+    C = oracle.sym_square(U, leaf_dim=leaf)
+    E = upper_of_dense(S @ S, bs)
+    assert_same_structure(C, E)
+    assert np.all(C.brow <= C.bcol)
+    assert relerr(C.vals, E.vals) < 1e-14
+
+
+def test_sym_square_of_exactly_symmetric_matrix():
+    """For an exactly symmetric A, the upper storage mirrors back to A bit for
+    bit, and A^2 from it equals the upper triangle of the plain product."""
+    A = synth.decay(120, 16, 9)
+    U = synth.upper_blocks(A)
+    F = oracle.sym_full(U)
+    assert_same_structure(F, A.sorted())
+    assert np.array_equal(F.vals, A.sorted().vals)
+    C = oracle.sym_square(U)
+    E = synth.upper_blocks(oracle.multiply(A, A).C)
+    assert_same_structure(C, E)
+    assert np.array_equal(C.vals, E.vals)
+    # the upper triangle holds a little over half of the product's blocks
+    full = oracle.multiply(A, A).C.nblk
+    assert C.nblk == (full + np.sum(oracle.multiply(A, A).C.brow == oracle.multiply(A, A).C.bcol)) // 2
+
+
+@pytest.mark.parametrize("trans", [False, True])
+@pytest.mark.parametrize("n,k,bs", [(300, 170, 16), (97, 131, 8)])
+def test_syrk_bruteforce(trans, n, k, bs):
+    A = synth.random_blocks(k if trans else n, bs, 0.3, 131 + n, ncols=n if trans else k)
+    a = A.to_dense()
+    g = a.T @ a if trans else a @ a.T
+    C = oracle.syrk(A, trans)
+    E = upper_of_dense(g, bs)
+    assert_same_structure(C, E)
+    assert relerr(C.vals, E.vals) < 1e-14
+    assert (C.nrows, C.ncols) == (n, n)
+
+
+@pytest.mark.parametrize("side", [0, 1])
+def test_sym_multiply_bruteforce(side):
+    bs = 16
+    U = synth.random_upper(280, bs, 0.2, 141)
+    G = synth.random_blocks(280, bs, 0.2, 142, ncols=200) if side == 0 else \
+        synth.random_blocks(200, bs, 0.2, 142, ncols=280)
+    S = dense_sym(U)
+    if side == 0:
+        C, d = oracle.sym_multiply(U, G, 0), S @ G.to_dense()
+    else:
+        C, d = oracle.sym_multiply(G, U, 1), G.to_dense() @ S
+    E = synth.from_dense(d, bs).sorted()
+    assert_same_structure(C, E)
+    assert relerr(C.vals, E.vals) < 1e-14
+
+
+def test_sym_storage_errors():
+    A = synth.random_blocks(128, 16, 0.5, 151)          # has blocks below the diagonal
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.sym_square(A)
+    assert e.value.code == -4
+    R = synth.upper_blocks(synth.random_blocks(128, 16, 0.5, 152, ncols=96))
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.sym_square(R)
+    assert e.value.code == -2
+
+
 def test_symmetric_square_structure_symmetric():
     A = synth.decay(60, 16, 7)
     C = oracle.multiply(A, A).C
