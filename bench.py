@@ -460,10 +460,15 @@ def run_batched(bsm, torch, args, stream, nprod=64):
 def run_decay(args):
     """Decay-type product A*A: points uniform in a cube at 0.1 per cubic Angstrom,
     recursive-bisection order, 5 functions per point, A_ij = s_ij exp(-0.5 r_ij)
-    dropped below 1e-6, bs 32 (20,000 points: N = 100,000).  FP64 and split
-    BF16x7; C's structure against the block-pattern product (the definition of
-    S_C, no exact cancellation in this data), values against the oracle's
-    definition on 1000 uniformly sampled C blocks."""
+    dropped below 1e-6 (20,000 points: N = 100,000).  FP64 and split BF16 with
+    the given slice counts; optionally the symmetric square (upper triangle of
+    A*A from the upper triangle of A).  C's symbolic structure is compared with
+    the block-pattern product (the definition of S_C); blocks whose entries all
+    vanish (element-level sparsity inside blocks) are removed by the product,
+    and on 1000 uniformly sampled C blocks the values and the presence of each
+    block are compared with the oracle's definition."""
+    import ctypes
+
     import torch
 
     import oracle
@@ -474,22 +479,35 @@ def run_decay(args):
     bsm.load()
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
-    npts, bs = args.points, 32
+    npts, bs = args.points, args.bs
     t0 = time.time()
     n, r, c, v = sd.decay(npts, bs, synth.BASE_SEED + 2, dev)
     nbk = -(-n // bs)
     A = bsm.bsm_build(n, n, bs, r, c, v)
+    U = None
+    if args.sym:
+        up = r <= c
+        U = bsm.bsm_build(n, n, bs, r[up].contiguous(), c[up].contiguous(), v[up].contiguous())
+        del up
     torch.cuda.synchronize()
     gen_s = time.time() - t0
     nblk = A.nblk
-    # structure of C by definition: block pattern product
+    # structure of C by definition: the block-pattern product of A's stored
+    # blocks (the generator's all-zero blocks are not stored)
+    ar = torch.empty(max(nblk, 1), dtype=torch.int32, device=dev)
+    ac = torch.empty(max(nblk, 1), dtype=torch.int32, device=dev)
+    cnt = ctypes.c_int64(nblk)
+    assert bsm.load().bsm_to_blocks(A.handle, ctypes.byref(cnt), ar.data_ptr(), ac.data_ptr(),
+                                    None, 1, stream.cuda_stream) == 0
     Pm = torch.zeros((nbk, nbk), dtype=torch.float32, device=dev)
-    Pm[r.long(), c.long()] = 1.0
+    Pm[ar[:nblk].long(), ac[:nblk].long()] = 1.0
+    del ar, ac
     pat = (Pm @ Pm) > 0.5
     del Pm
     ci, cj = torch.nonzero(pat, as_tuple=True)
     del pat
     nc_def = int(ci.numel())
+    nc_def_upper = int((ci <= cj).sum())
     g = torch.Generator(device="cpu").manual_seed(synth.BASE_SEED)
     pick = torch.randperm(nc_def, generator=g)[:1000]
     si, sj = ci.cpu()[pick].numpy(), cj.cpu()[pick].numpy()
@@ -505,25 +523,33 @@ def run_decay(args):
     t1 = time.time()
     L = oracle.common_depth(left, right)
     tl, tr = oracle.tree(left, L), oracle.tree(right, L)
-    ref = np.stack([oracle.block_product(tl, tr, i, j)[1] for i, j in zip(si, sj)])
+    refs = [oracle.block_product(tl, tr, i, j) for i, j in zip(si, sj)]
+    ref = np.stack([x[1] for x in refs])
+    ref_nonzero = np.array([bool(np.any(x[1] != 0.0)) for x in refs])
     oracle_s = time.time() - t1
     del tl, tr, left, right
     log(f"decay: n={n} blocks={nblk} C(def)={nc_def}; generation {gen_s:.1f} s, "
         f"oracle on 1000 blocks {oracle_s:.1f} s")
     bsm.bsm_set_timing(True)
     out = {"workload": f"decay A*A, {npts} points (N={n}), bs {bs}", "a_blocks": nblk,
-           "c_blocks_definition": nc_def}
+           "c_blocks_definition": nc_def, "sampled_blocks_exactly_zero": int((~ref_nonzero).sum())}
     peaks, which = measured_peaks()
     fp64_peak = peaks["bf16_tflops"] * FP64_NOMINAL_RATIO
-    for name, prec, reps in (("split_bf16x7", bsm.BSM_SPLIT_BF16, args.steps),
-                             ("fp64", bsm.BSM_FP64, 1)):
+    slices = [int(x) for x in args.slices.split(",") if x]
+    legs = [(f"split_bf16x{k}", False, bsm.BSM_SPLIT_BF16, k, args.steps) for k in slices]
+    legs.append(("fp64", False, bsm.BSM_FP64, 0, 1))
+    if args.sym:
+        legs += [(f"sym_square_split_bf16x{slices[-1]}", True, bsm.BSM_SPLIT_BF16, slices[-1],
+                  args.steps), ("sym_square_fp64", True, bsm.BSM_FP64, 0, 1)]
+    for name, sym, prec, nsl, reps in legs:
         times = []
         C = None
         for k in range(reps + (1 if prec != bsm.BSM_FP64 else 0)):
             C = None
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            C = bsm.bsm_multiply(A, A, prec=prec)
+            C = (bsm.bsm_sym_square(U, prec=prec, slices=nsl) if sym
+                 else bsm.bsm_multiply(A, A, prec=prec, slices=nsl))
             e1.record(stream)
             torch.cuda.synchronize()
             if prec == bsm.BSM_FP64 or k > 0:  # split: first run is a warm-up
@@ -531,29 +557,35 @@ def run_decay(args):
         ms, _ = bsm.bsm_last_phase_ms()
         _, triples, ncs = bsm.bsm_last_stats()
         flops = metrics.block_flops(bs, triples)
-        # structure: compare coordinates (no values) with the definition
         nr, ncol, _, ncb = bsm.bsm_info(C)
-        cr = torch.empty(ncb, dtype=torch.int32, device=dev)
-        cc = torch.empty(ncb, dtype=torch.int32, device=dev)
-        import ctypes
+        cr = torch.empty(max(ncb, 1), dtype=torch.int32, device=dev)
+        cc = torch.empty(max(ncb, 1), dtype=torch.int32, device=dev)
         cnt = ctypes.c_int64(ncb)
         code = bsm.load().bsm_to_blocks(C.handle, ctypes.byref(cnt), cr.data_ptr(), cc.data_ptr(),
                                         None, 1, stream.cuda_stream)
         assert code == 0
-        key_gpu = cr.long() * nbk + cc.long()
-        key_def = ci.long() * nbk + cj.long()
-        same_structure = bool(key_gpu.numel() == key_def.numel() and
-                              torch.equal(torch.sort(key_gpu).values, torch.sort(key_def).values))
-        # sampled values
-        pos = torch.searchsorted(key_gpu, torch.from_numpy(si * nbk + sj).to(dev))
+        key_gpu = cr[:ncb].long() * nbk + cc[:ncb].long()   # row-major: ascending
+        # sampled blocks: a symmetric result holds (min, max); C_ji = C_ij^T
+        lo, hi = (np.minimum(si, sj), np.maximum(si, sj)) if sym else (si, sj)
+        want = torch.from_numpy(lo.astype(np.int64) * nbk + hi).to(dev)
+        pos = torch.searchsorted(key_gpu, want).clamp(max=max(ncb - 1, 0))
+        present = (key_gpu[pos] == want).cpu().numpy() if ncb else np.zeros(len(si), bool)
         _, _, cv = bsm.bsm_to_blocks(C, device=True)
-        got = cv[pos].cpu().numpy()
-        del cv, cr, cc, key_gpu, key_def
+        got = cv[pos].cpu().numpy() if ncb else np.zeros_like(ref)
+        got[~present] = 0.0
+        if sym:
+            flip = si > sj
+            got[flip] = got[flip].transpose(0, 2, 1)
+        del cv, cr, cc, key_gpu
         err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         t_num = ms[1] / 1e3
-        res = {"ms_per_product": statistics.mean(times), "gflops": flops / (statistics.mean(times) / 1e3) / 1e9,
+        res = {"ms_per_product": statistics.mean(times),
+               "gflops": flops / (statistics.mean(times) / 1e3) / 1e9,
                "phase_ms": [float(x) for x in ms], "chunks": bsm.bsm_last_chunks(),
-               "triples": triples, "c_blocks": ncb, "structure_matches_definition": same_structure,
+               "triples": triples, "c_blocks_symbolic": ncs, "c_blocks": ncb,
+               "symbolic_structure_matches_definition":
+                   ncs == (nc_def_upper if sym else nc_def),
+               "sampled_presence_matches_oracle": bool(np.array_equal(present, ref_nonzero)),
                "rel_err_vs_oracle_1000_blocks": err}
         if prec == bsm.BSM_FP64:
             res["numeric_tflops"] = flops / t_num / 1e12
@@ -563,7 +595,12 @@ def run_decay(args):
         del C
         torch.cuda.empty_cache()
         log(f"{name}: {res}")
-    out["split_speedup_vs_fp64"] = out["fp64"]["ms_per_product"] / out["split_bf16x7"]["ms_per_product"]
+    best = f"split_bf16x{max(slices)}" if slices else None
+    if best:
+        out["split_speedup_vs_fp64"] = out["fp64"]["ms_per_product"] / out[best]["ms_per_product"]
+    if args.sym:
+        out["sym_square_speedup_vs_full_fp64"] = (out["fp64"]["ms_per_product"] /
+                                                  out["sym_square_fp64"]["ms_per_product"])
     print(json.dumps(out), flush=True)
     return 0
 
@@ -616,6 +653,10 @@ def main():
     ap.add_argument("--workload", default="random", choices=["random", "decay"],
                     help="decay: the decay-type A*A product (separate JSON line)")
     ap.add_argument("--points", type=int, default=20000, help="decay workload: number of points")
+    ap.add_argument("--bs", type=int, default=32, help="decay workload: leaf block size")
+    ap.add_argument("--slices", default="7", help="decay workload: split slice counts, e.g. 3,5,7")
+    ap.add_argument("--sym", action="store_true",
+                    help="decay workload: also the symmetric square from the upper triangle")
     ap.add_argument("--n", type=int, default=None, help="matrix side (profiling runs only)")
     ap.add_argument("--p", type=float, default=None, help="block density (profiling runs only)")
     args = ap.parse_args()

@@ -73,6 +73,11 @@ typedef struct {
 /* bsm_plan_create: measure candidate launch configurations and keep the
  * fastest (cached per product class for the process). */
 #define BSM_FLAG_AUTOTUNE 1
+/* bsm_plan_create: also choose the leaf block size (16, 32, 64; split modes
+ * 16, 32) by timing the product on re-blocked copies of the operands.  The
+ * plan then copies the operands' current values into its re-blocked copies
+ * at every execution and returns C in the operands' block size. */
+#define BSM_FLAG_AUTOTUNE_BS 8
 /* bsm_multiply: use A^T (resp. B^T) in place of A (resp. B), the transposed
  * multiplication task types C = A^T B, A B^T, A^T B^T of Sec. 3.2. */
 #define BSM_FLAG_TRANS_A 2
@@ -190,6 +195,53 @@ bsm_status bsm_sym_multiply(bsm_matrix A, bsm_matrix B, int side, bsm_matrix *C,
 bsm_status bsm_sym_to_full(bsm_matrix A, bsm_matrix *out, void *stream);
 
 /*
+ * bsm_reblock -- the same matrix cut into leaf blocks of side bs (16, 32 or
+ * 64).  Splitting drops sub-blocks that are exactly zero; merging fills
+ * absent sub-blocks with zeros.  Values are copied bit for bit.
+ *   A    input handle (unchanged)
+ *   out  receives the new handle (NULL on error)
+ * Stream-ordered; the caller owns the result.  Errors: INVALID_ARG,
+ * BLOCKSIZE, OOM, CUDA, UNSUPPORTED (more than 2^31 - 1 sub-blocks).
+ */
+bsm_status bsm_reblock(bsm_matrix A, int bs, bsm_matrix *out, void *stream);
+
+/*
+ * bsm_node_norms2 -- squared Frobenius norms of the quadtree nodes at a
+ * height above the leaf blocks (0 = the blocks themselves; the per-node norms
+ * of Sec. 7), in Morton order of the nodes, with the nodes' coordinates at
+ * that height.  Summation order is fixed (rows ascending, each row's squares
+ * in column order; a node sums its children in child order), each operation
+ * rounded separately, so results are reproducible bit for bit.
+ *   height     0 .. depth of the matrix
+ *   norm2      float64[capacity] or NULL
+ *   I, J       int32[capacity] or NULL: node row / column at that height
+ *   n_inout    in: capacity; out: number of nodes at that height
+ *   on_device  0: host buffers (the call synchronises `stream`); 1: device
+ *              buffers (norm2 8-byte, I/J 4-byte aligned)
+ * With all three buffers NULL only the count is returned.
+ * Errors: INVALID_ARG, OUT_OF_RANGE (height), BUFFER_TOO_SMALL, OOM, CUDA.
+ */
+bsm_status bsm_node_norms2(bsm_matrix M, int height, double *norm2, int32_t *I, int32_t *J,
+                           int64_t *n_inout, int on_device, void *stream);
+
+/*
+ * bsm_truncate -- remove small blocks so that the Frobenius norm of the
+ * removed part is at most tau (the truncation of Sec. 6.2): the longest run
+ * of blocks in ascending order of squared norm (ties: Morton order) whose
+ * squared norms sum to at most tau^2.  The sum is decided exactly in integer
+ * units 2^e = 2^(floor(log2 tau^2) - 63): each squared norm is rounded up to a
+ * whole unit and the run stops before the integer sum passes tau^2, so the
+ * removed squared norm never exceeds tau^2.  tau <= 0 removes nothing; blocks
+ * whose norm is NaN are never removed.
+ *   out      receives the new handle (caller owns it)
+ *   removed  NULL or receives the number of removed blocks
+ *   bound    NULL or receives the rounded-up removed squared norm (<= tau^2)
+ * Errors: INVALID_ARG, OOM, CUDA, UNSUPPORTED (more than 2^31 - 1 blocks).
+ */
+bsm_status bsm_truncate(bsm_matrix M, double tau, bsm_matrix *out, int64_t *removed,
+                        double *bound, void *stream);
+
+/*
  * bsm_multiply_batched -- C[i] = A[i]*B[i] for n independent products.
  * Symbolic phases run per product; the numeric phase of all products runs as
  * one persistent launch over a single work list ordered by decreasing work.
@@ -298,6 +350,9 @@ bsm_status bsm_update_values(bsm_matrix M, int64_t nblk, const int32_t *brow, co
  */
 bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matrix *B,
                            const bsm_mult_opts *opts, void *stream, bsm_plan *plan);
+
+/* bsm_plan_block_size -- the leaf block size the plan computes at. */
+bsm_status bsm_plan_block_size(bsm_plan plan, int *bs);
 
 /* bsm_plan_execute -- replay the plan's numeric phase, ordered after earlier
  * work on `stream` and before later work on it (asynchronous).  Errors:

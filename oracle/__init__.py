@@ -38,7 +38,8 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain -O2, no vectorisation flags)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-ffp-contract=off",
+                               "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -57,6 +58,13 @@ def _load():
     lib.orc_multiply_t.argtypes = [P, I32, P, I32, P, P, ctypes.POINTER(I32)]
     lib.orc_add.restype = P
     lib.orc_add.argtypes = [P, P, ctypes.POINTER(I32)]
+    lib.orc_node_norms2.restype = I64
+    lib.orc_node_norms2.argtypes = [P, I32, P, P, P]
+    lib.orc_truncate.restype = P
+    lib.orc_truncate.argtypes = [P, ctypes.c_double, ctypes.POINTER(I64),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I32)]
+    lib.orc_block_norm2.restype = ctypes.c_double
+    lib.orc_block_norm2.argtypes = [P, I32]
     lib.orc_sym_full.restype = P
     lib.orc_sym_full.argtypes = [P, ctypes.POINTER(I32)]
     lib.orc_sym_square.restype = P
@@ -233,3 +241,34 @@ def sym_multiply(A: BlockCOO, B: BlockCOO, side: int = 0, leaf_dim: int = 4096) 
     ta, tb = tree(A, L, leaf_dim), tree(B, L, leaf_dim)
     p = _call(_load().orc_symm, ta._p, tb._p, int(side))
     return Tree(p, A.nrows, B.ncols, A.bs, L, ta.leaf_nb).to_coo()
+
+
+# ---------------------------------------------------------- Frobenius norms
+def block_norm2(block: np.ndarray) -> float:
+    """Squared Frobenius norm of one block in the fixed summation order (rows
+    ascending, each row's squares summed in ascending column order)."""
+    b = np.ascontiguousarray(block, np.float64)
+    return float(_load().orc_block_norm2(b.ctypes.data, b.shape[0]))
+
+
+def node_norms2(A: BlockCOO, height: int):
+    """(I, J, squared norm) of the quadtree nodes `height` levels above the
+    blocks (0 = the blocks), in depth-first child order."""
+    t = tree(A, None, leaf_dim=A.bs)
+    lib = _load()
+    n = lib.orc_node_norms2(t._p, int(height), None, None, None)
+    if n < 0:
+        raise OracleError(-1)
+    I = np.zeros(n, np.int32)
+    J = np.zeros(n, np.int32)
+    v = np.zeros(n, np.float64)
+    lib.orc_node_norms2(t._p, int(height), I.ctypes.data, J.ctypes.data, v.ctypes.data)
+    return I, J, v
+
+
+def truncate(A: BlockCOO, tau: float, leaf_dim: int = 4096):
+    """(truncated matrix, blocks removed, bound on the removed squared norm)."""
+    t = tree(A, None, leaf_dim)
+    rem, bound = ctypes.c_int64(0), ctypes.c_double(0.0)
+    p = _call(_load().orc_truncate, t._p, float(tau), ctypes.byref(rem), ctypes.byref(bound))
+    return Tree(p, A.nrows, A.ncols, A.bs, t.L, t.leaf_nb).to_coo(), rem.value, bound.value

@@ -34,6 +34,7 @@
  *
  * Single threaded and deliberately unoptimised.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -601,6 +602,174 @@ orc_matrix *orc_symm(const orc_matrix *A, const orc_matrix *B, int side, int *st
   orc_matrix *C = side == 0 ? orc_multiply_t(F, 0, B, 0, NULL, NULL, status)
                             : orc_multiply_t(A, 0, F, 0, NULL, NULL, status);
   orc_free(F);
+  return C;
+}
+
+static const double *find_block(const orc_matrix *m, int64_t I, int64_t J);
+int64_t orc_nblocks(const orc_matrix *m);
+
+/* --------------------------------------------------- Frobenius norms */
+/* Per-node Frobenius norms (Sec. 7 names them as extra quadtree information)
+ * and truncation with a bound on the Frobenius norm of the error (Sec. 6.2
+ * truncates the overlap matrix that way).  Squared norms are summed in one
+ * fixed order so that both implementations round identically: a block's
+ * squared norm is the sum over rows, in ascending order, of the row sums of
+ * squares in ascending column order; a node's is the sum of its children's in
+ * child order 0..3.  (The file is compiled without FMA contraction.) */
+double orc_block_norm2(const double *b, int bs) {
+  double t = 0.0;
+  for (int r = 0; r < bs; r++) {
+    double row = 0.0;
+    for (int c = 0; c < bs; c++) {
+      double sq = b[r * bs + c] * b[r * bs + c];
+      row = row + sq;
+    }
+    t = t + row;
+  }
+  return t;
+}
+
+static double node_norm2(const orc_matrix *m, const orc_node *n, int level, int want_level,
+                         int64_t I0, int64_t J0, int32_t *I, int32_t *J, double *v,
+                         int64_t *pos) {
+  double t;
+  if (level == m->depth) {
+    t = orc_block_norm2(n->blk[0], m->bs); /* leaf_nb == 1: one block per leaf */
+  } else {
+    t = 0.0;
+    for (int c = 0; c < 4; c++)
+      if (n->child[c])
+        t = t + node_norm2(m, n->child[c], level + 1, want_level, 2 * I0 + (c >> 1),
+                           2 * J0 + (c & 1), I, J, v, pos);
+  }
+  if (level == want_level) {
+    if (I) {
+      I[*pos] = (int32_t)I0;
+      J[*pos] = (int32_t)J0;
+      v[*pos] = t;
+    }
+    (*pos)++;
+  }
+  return t;
+}
+
+/* Squared norms of the nodes at `height` above the blocks (0 = the blocks)
+ * of a tree built with one block per leaf, in depth-first child order, with
+ * their coordinates at that height.  Returns the node count (arrays may be
+ * NULL), or -1 if the tree has multi-block leaves or height is out of range. */
+int64_t orc_node_norms2(const orc_matrix *m, int height, int32_t *I, int32_t *J, double *v) {
+  if (m->leaf_nb != 1 || height < 0 || height > m->depth) return -1;
+  int64_t pos = 0;
+  if (m->root) node_norm2(m, m->root, 0, m->depth - height, 0, 0, I, J, v, &pos);
+  return pos;
+}
+
+static uint64_t morton2(uint64_t I, uint64_t J) {
+  uint64_t k = 0;
+  for (int b = 0; b < 32; b++) k |= (((I >> b) & 1) << (2 * b + 1)) | (((J >> b) & 1) << (2 * b));
+  return k;
+}
+
+typedef struct {
+  double n2;
+  uint64_t key;
+  int64_t I, J;
+} orc_nrm;
+
+static int cmp_nrm(const void *a, const void *b) {
+  const orc_nrm *x = (const orc_nrm *)a, *y = (const orc_nrm *)b;
+  /* NaN sorts last */
+  int xn = x->n2 != x->n2, yn = y->n2 != y->n2;
+  if (xn != yn) return xn - yn;
+  if (!xn && x->n2 != y->n2) return x->n2 < y->n2 ? -1 : 1;
+  return (x->key > y->key) - (x->key < y->key);
+}
+
+static void collect_nrm(const orc_matrix *m, const orc_node *n, int level, int64_t I0, int64_t J0,
+                        orc_nrm *out, int64_t *pos) {
+  if (!n) return;
+  if (level == m->depth) {
+    for (int i = 0; i < m->leaf_nb; i++)
+      for (int j = 0; j < m->leaf_nb; j++) {
+        const double *b = n->blk[i * m->leaf_nb + j];
+        if (!b) continue;
+        int64_t I = I0 * m->leaf_nb + i, J = J0 * m->leaf_nb + j;
+        out[*pos].n2 = orc_block_norm2(b, m->bs);
+        out[*pos].key = morton2((uint64_t)I, (uint64_t)J);
+        out[*pos].I = I;
+        out[*pos].J = J;
+        (*pos)++;
+      }
+    return;
+  }
+  for (int c = 0; c < 4; c++)
+    collect_nrm(m, n->child[c], level + 1, 2 * I0 + (c >> 1), 2 * J0 + (c & 1), out, pos);
+}
+
+/* Truncation: remove the longest run of blocks, in ascending order of squared
+ * norm (ties: ascending Morton key), whose squared norms sum to at most tau^2.
+ * The sum is taken in integers so that the decision is exact: with
+ * 2^e = 2^(floor(log2 tau^2) - 63), every squared norm s is rounded up to
+ * Q = ceil(s / 2^e) (saturating at 2^64 - 1) and the run is the longest prefix
+ * whose Q add up to at most T = floor(tau^2 / 2^e) in exact (saturating)
+ * 64-bit arithmetic; so sum(s) <= sum(Q) 2^e <= tau^2 holds rigorously.
+ * tau <= 0 (or tau^2 == 0) removes nothing; NaN norms are never removed.
+ * *removed receives the count and *bound the value sum(Q) 2^e. */
+orc_matrix *orc_truncate(const orc_matrix *A, double tau, int64_t *removed, double *bound,
+                         int *status) {
+  *status = ORC_OK;
+  *removed = 0;
+  *bound = 0.0;
+  int64_t n = orc_nblocks(A), pos = 0;
+  orc_nrm *it = (orc_nrm *)malloc(sizeof(orc_nrm) * (size_t)(n > 0 ? n : 1));
+  if (!it) {
+    *status = ORC_ERR_OOM;
+    return NULL;
+  }
+  collect_nrm(A, A->root, 0, 0, 0, it, &pos);
+  qsort(it, (size_t)n, sizeof(orc_nrm), cmp_nrm);
+  double t2 = tau * tau;
+  int64_t k = 0;
+  if (tau > 0.0 && isinf(t2)) { /* everything but NaN-norm blocks */
+    while (k < n && it[k].n2 == it[k].n2) k++;
+    *bound = t2;
+  } else if (tau > 0.0 && t2 > 0.0) {
+    int ex;
+    frexp(t2, &ex); /* t2 = f 2^ex, f in [0.5, 1): floor(log2 t2) = ex - 1 */
+    const int e = ex - 1 - 63;
+    const uint64_t T = (uint64_t)floor(ldexp(t2, -e)); /* in [2^63, 2^64) */
+    uint64_t acc = 0;
+    for (; k < n; k++) {
+      if (it[k].n2 != it[k].n2) break; /* NaN */
+      const double q = ceil(ldexp(it[k].n2, -e));
+      const uint64_t Q = q >= 18446744073709551616.0 ? UINT64_MAX : (uint64_t)q;
+      const uint64_t nxt = acc + Q < acc ? UINT64_MAX : acc + Q;
+      if (nxt > T) break;
+      acc = nxt;
+    }
+    *bound = ldexp((double)acc, e);
+  }
+  *removed = k;
+  /* rebuild without the removed blocks */
+  orc_matrix *C = alloc_matrix(A->nrows, A->ncols, A->bs, A->L, A->leaf_nb);
+  if (!C) {
+    free(it);
+    *status = ORC_ERR_OOM;
+    return NULL;
+  }
+  size_t bb = (size_t)A->bs * A->bs;
+  for (int64_t t = k; t < n; t++) {
+    const double *src = find_block(A, it[t].I, it[t].J);
+    double **d = block_slot(C, it[t].I, it[t].J);
+    if (!d || !(*d = (double *)malloc(bb * sizeof(double)))) {
+      free(it);
+      orc_free(C);
+      *status = ORC_ERR_OOM;
+      return NULL;
+    }
+    memcpy(*d, src, bb * sizeof(double));
+  }
+  free(it);
   return C;
 }
 

@@ -21,6 +21,7 @@ BSM_SPLIT_BF16 = 1
 BSM_FLAG_AUTOTUNE = 1
 BSM_FLAG_TRANS_A = 2
 BSM_FLAG_TRANS_B = 4
+BSM_FLAG_AUTOTUNE_BS = 8
 BSM_SYM_LEFT = 0
 BSM_SYM_RIGHT = 1
 
@@ -41,6 +42,9 @@ _PROTOS = {
     "bsm_syrk": (_I32, [_P, _I32, _P, _P, _P]),
     "bsm_sym_multiply": (_I32, [_P, _P, _I32, _P, _P, _P]),
     "bsm_sym_to_full": (_I32, [_P, _P, _P]),
+    "bsm_reblock": (_I32, [_P, _I32, _P, _P]),
+    "bsm_node_norms2": (_I32, [_P, _I32, _P, _P, _P, _P, _I32, _P]),
+    "bsm_truncate": (_I32, [_P, ctypes.c_double, _P, _P, _P, _P]),
     "bsm_multiply_batched": (_I32, [_I32, _P, _P, _P, _P, _P]),
     "bsm_to_blocks": (_I32, [_P, _P, _P, _P, _P, _I32, _P]),
     "bsm_info": (_I32, [_P, _P, _P, _P, _P]),
@@ -57,6 +61,7 @@ _PROTOS = {
     "bsm_plan_execute": (_I32, [_P, _P]),
     "bsm_plan_results": (_I32, [_P, _P, _P]),
     "bsm_plan_info": (_I32, [_P, _P, _P, _P, _P]),
+    "bsm_plan_block_size": (_I32, [_P, _P]),
     "bsm_plan_destroy": (_I32, [_P]),
     "bsm_destroy": (_I32, [_P]),
     "bsm_status_string": (ctypes.c_char_p, [_I32]),
@@ -232,6 +237,36 @@ def bsm_sym_to_full(A: Matrix, stream=None) -> Matrix:
     return Matrix(out.value)
 
 
+def bsm_reblock(A: Matrix, bs: int, stream=None) -> Matrix:
+    out = ctypes.c_void_p()
+    _check(load().bsm_reblock(A.handle, int(bs), ctypes.byref(out), _stream_ptr(stream)),
+           "bsm_reblock")
+    return Matrix(out.value)
+
+
+def bsm_node_norms2(M: Matrix, height: int = 0, stream=None):
+    """(I, J, squared norm) of the nodes `height` levels above the blocks."""
+    lib = load()
+    n = ctypes.c_int64(0)
+    _check(lib.bsm_node_norms2(M.handle, int(height), None, None, None, ctypes.byref(n), 0,
+                               _stream_ptr(stream)), "bsm_node_norms2")
+    v = np.zeros(n.value, np.float64)
+    I = np.zeros(n.value, np.int32)
+    J = np.zeros(n.value, np.int32)
+    _check(lib.bsm_node_norms2(M.handle, int(height), v.ctypes.data, I.ctypes.data, J.ctypes.data,
+                               ctypes.byref(n), 0, _stream_ptr(stream)), "bsm_node_norms2")
+    return I, J, v
+
+
+def bsm_truncate(M: Matrix, tau: float, stream=None):
+    """(truncated handle, blocks removed, bound on the removed squared norm)."""
+    out = ctypes.c_void_p()
+    rem, bound = ctypes.c_int64(0), ctypes.c_double(0.0)
+    _check(load().bsm_truncate(M.handle, float(tau), ctypes.byref(out), ctypes.byref(rem),
+                               ctypes.byref(bound), _stream_ptr(stream)), "bsm_truncate")
+    return Matrix(out.value), rem.value, bound.value
+
+
 def bsm_multiply_batched(As, Bs, prec: int = BSM_FP64, slices: int = 0, stream=None):
     lib = load()
     n = len(As)
@@ -388,12 +423,13 @@ class Plan:
 
 
 def bsm_plan_create(As, Bs, prec: int = BSM_FP64, slices: int = 0, autotune: bool = False,
-                    stream=None) -> Plan:
+                    stream=None, autotune_bs: bool = False) -> Plan:
     lib = load()
     n = len(As)
     ha = (ctypes.c_void_p * max(n, 1))(*[a.handle for a in As])
     hb = (ctypes.c_void_p * max(n, 1))(*[b.handle for b in Bs])
-    opts = bsm_mult_opts(prec, slices, BSM_FLAG_AUTOTUNE if autotune else 0)
+    flags = (BSM_FLAG_AUTOTUNE if autotune else 0) | (BSM_FLAG_AUTOTUNE_BS if autotune_bs else 0)
+    opts = bsm_mult_opts(prec, slices, flags)
     out = ctypes.c_void_p()
     code = lib.bsm_plan_create(n, ha, hb, ctypes.byref(opts), _stream_ptr(stream),
                                ctypes.byref(out))
@@ -418,6 +454,12 @@ def bsm_plan_info(plan: Plan):
     _check(load().bsm_plan_info(plan.handle, ctypes.byref(o), ctypes.byref(c), ctypes.byref(k),
                                 ctypes.byref(n)), "bsm_plan_info")
     return o.value, c.value, k.value, n.value
+
+
+def bsm_plan_block_size(plan: Plan) -> int:
+    b = ctypes.c_int()
+    _check(load().bsm_plan_block_size(plan.handle, ctypes.byref(b)), "bsm_plan_block_size")
+    return b.value
 
 
 def bsm_plan_destroy(plan: Plan):

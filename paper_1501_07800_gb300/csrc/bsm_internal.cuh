@@ -93,6 +93,8 @@ HostScratch &host_scratch();
 bsm_status scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
 bsm_status scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
 bsm_status scan_exclusive_int4(const int4 *in, int4 *out, int64_t n, cudaStream_t s);
+// Inclusive prefix sums of uint64 values, saturating at 2^64 - 1.
+bsm_status scan_inclusive_u64_sat(const uint64_t *in, uint64_t *out, int64_t n, cudaStream_t s);
 bsm_status sort_keys_u64(const uint64_t *kin, uint64_t *kout, const int32_t *vin, int32_t *vout,
                          int64_t n, int end_bit, cudaStream_t s);
 bsm_status sort_pairs_u32_u64(const uint32_t *kin, uint32_t *kout, const uint64_t *vin,
@@ -123,11 +125,12 @@ bsm_status symbolic_multiply(bsm_matrix A, bsm_matrix B, SymbolicResult *out, cu
 // ranges of C, each handed to `sink` (which may take ownership of the arrays
 // by clearing the pointers).  budget: pairs per level part (0 = default, or
 // the BSM_SYM_BUDGET environment variable).  tasks[h]: pairs per height.
-// upper: only C blocks with I <= J (symmetric square and SYRK results).
+// upper: 0, or k >= 1 to keep only C nodes on or above the diagonal at
+// heights >= k - 1 (k = 1: C blocks with I <= J, for symmetric results; k = 2:
+// blocks whose parent node is on or above the diagonal).
 using LeafSink = std::function<bsm_status(SymbolicResult &)>;
 bsm_status symbolic_chunks(bsm_matrix A, bsm_matrix B, const LeafSink &sink, int64_t *tasks,
-                           int *H, int *nchunks, cudaStream_t s, int64_t budget,
-                           bool upper = false);
+                           int *H, int *nchunks, cudaStream_t s, int64_t budget, int upper = 0);
 void free_symbolic(SymbolicResult *r, cudaStream_t s);
 
 // ----------------------------------------------------------- numeric phase
@@ -173,13 +176,22 @@ bsm_status finish_product_copy(bsm_matrix C, const SymbolicResult &sym, const do
                                const int32_t *nz, unsigned *err, cudaStream_t s);
 bsm_status check_pair(bsm_matrix A, bsm_matrix B);
 // One product through the chunked symbolic phase and the chosen numeric
-// phase (bsm_multiply.cu); upper: only C blocks with I <= J.
+// phase (bsm_multiply.cu); upper: only C blocks with I <= J.  Split modes
+// at block size 64 run at 32 on re-cut operands (the split result does not
+// depend on the leaf size) and merge C back.
 bsm_status multiply_one(bsm_matrix A, bsm_matrix B, int prec, int slices, cudaStream_t s,
                         bsm_matrix *out, bool upper = false);
 // dst[t] = src[idx[t] & 0x7FFFFFFF], transposed when bit 31 of idx[t] is set
 // (bsm_ops.cu).
 void launch_gather_blocks_t(const double *src, const int32_t *idx, double *dst, int64_t n, int bs,
                             cudaStream_t s);
+// Re-blocking (bsm_ops.cu).  keep_all: splitting keeps every sub-block inside
+// the matrix, so the new structure depends on A's structure only; map_out
+// receives the index map reblock_refresh uses to copy new values of A into
+// the re-blocked handle (caller frees it with dev_free).
+bsm_status reblock_impl(bsm_matrix A, int bs, bool keep_all, bsm_matrix *out, int32_t **map_out,
+                        cudaStream_t s);
+void reblock_refresh(bsm_matrix src, bsm_matrix dst, const int32_t *map, cudaStream_t s);
 bsm_status check_opts(const bsm_mult_opts *o, int *prec, int *slices, int allowed_flags);
 
 // Handle shells for results (bsm_tree.cu).

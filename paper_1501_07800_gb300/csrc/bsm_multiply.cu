@@ -232,8 +232,31 @@ static bsm_status compact_chunk(SymbolicResult &r, double *&cvals, const int32_t
 // One product: the symbolic phase delivers the task list in Morton-range
 // chunks (one chunk unless a level exceeds the pair budget); each chunk is
 // computed and compacted as it arrives, and C is assembled from the chunks.
+static bsm_status multiply_chunked(bsm_matrix A, bsm_matrix B, int prec, int slices,
+                                   cudaStream_t s, bsm_matrix *out, int upper);
+
 bsm_status multiply_one(bsm_matrix A, bsm_matrix B, int prec, int slices, cudaStream_t s,
                         bsm_matrix *out, bool upper) {
+  *out = nullptr;
+  if (prec == BSM_FP64 || A->bs != 64) return multiply_chunked(A, B, prec, slices, s, out, upper);
+  // The split kernel takes 16- and 32-wide blocks.  Its result does not depend
+  // on the leaf size: the scales span whole rows of A and columns of B and the
+  // digit sums are exact, so the bs-64 product is the bs-32 product of the
+  // re-cut operands, merged back (an upper-triangle result keeps the 32-blocks
+  // of every diagonal 64-block).
+  bsm_matrix a = nullptr, b = nullptr, c = nullptr;
+  bsm_status st = reblock_impl(A, 32, false, &a, nullptr, s);
+  if (st == BSM_OK) st = B == A ? (b = a, BSM_OK) : reblock_impl(B, 32, false, &b, nullptr, s);
+  if (st == BSM_OK) st = multiply_chunked(a, b, prec, slices, s, &c, upper ? 2 : 0);
+  if (st == BSM_OK) st = reblock_impl(c, 64, false, out, nullptr, s);
+  bsm_destroy(c);
+  if (b != a) bsm_destroy(b);
+  bsm_destroy(a);
+  return st;
+}
+
+static bsm_status multiply_chunked(bsm_matrix A, bsm_matrix B, int prec, int slices,
+                                   cudaStream_t s, bsm_matrix *out, int upper) {
   *out = nullptr;
   LastStats &ls = last_stats();
   ls = LastStats();
@@ -373,7 +396,7 @@ extern "C" bsm_status bsm_multiply(bsm_matrix A, bsm_matrix B, bsm_matrix *C,
   if ((ta ? A->nrows : A->ncols) != (tb ? B->ncols : B->nrows)) return BSM_ERR_DIM_MISMATCH;
   if (A->bs != B->bs) return BSM_ERR_BLOCKSIZE;
   if (A->device != B->device) return BSM_ERR_INVALID_ARG;
-  if (prec != BSM_FP64) BSM_TRY(split_supported(A->bs, slices));
+  if (prec != BSM_FP64) BSM_TRY(split_supported(A->bs == 64 ? 32 : A->bs, slices));
   cudaStream_t s = (cudaStream_t)stream;
   // The transposed task types (Sec. 3.2) are the plain product of transposed
   // handles: op(X) is X with its keys' row and column bits swapped and every

@@ -250,3 +250,228 @@ extern "C" bsm_status bsm_add(bsm_matrix A, bsm_matrix B, bsm_matrix *out, void 
   *out = C;
   return BSM_OK;
 }
+
+// ------------------------------------------------------------- re-blocking
+// A matrix re-cut into leaf blocks of another side (16, 32 or 64; the ratio is
+// a power of two).  Splitting a block of side bs into f x f blocks of side
+// bs/f: the sub-block (i, j) of block (I, J) is block (I f + i, J f + j), whose
+// Morton key is key(I, J) << 2 log2 f | key(i, j); taking the sub-blocks of
+// each block in Morton order keeps the list sorted, and all-zero sub-blocks
+// are dropped.  Merging f x f blocks into one: block (I, J) goes to
+// (I / f, J / f), key >> 2 log2 f, and the f^2 children of one merged block
+// are contiguous in Morton order; absent children are zero.
+namespace {
+
+// flag[t f^2 + q] = 1 if sub-block q (Morton index) of block t is kept: it
+// has an entry != 0, or (keep_all) it lies inside the matrix.  One warp per
+// sub-block.
+__global__ void k_split_flags(const double *__restrict__ vals, const uint64_t *__restrict__ keys,
+                              int64_t n, int bs, int nbs, int keep_all, int64_t mb, int64_t nb,
+                              int32_t *__restrict__ flag) {
+  const int f = bs / nbs, f2 = f * f;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n * f2) return;
+  const int64_t t = w / f2;
+  const int q = (int)(w % f2);
+  const int i = (int)morton_compact((uint64_t)q >> 1), j = (int)morton_compact((uint64_t)q);
+  if (keep_all) {
+    if (lane == 0) {
+      const int64_t I = (int64_t)morton_compact(keys[t] >> 1) * f + i;
+      const int64_t J = (int64_t)morton_compact(keys[t]) * f + j;
+      flag[w] = I < mb && J < nb;
+    }
+    return;
+  }
+  const double *b = vals + t * bs * bs + (int64_t)(i * nbs) * bs + j * nbs;
+  bool any = false;
+  for (int e = lane; e < nbs * nbs; e += 32) any |= b[(e / nbs) * bs + e % nbs] != 0.0;
+  any = __any_sync(0xffffffffu, any);
+  if (lane == 0) flag[w] = any;
+}
+
+__global__ void k_split_keys(const uint64_t *__restrict__ keys, int64_t n, int f,
+                             const int32_t *__restrict__ flag, const int32_t *__restrict__ pos,
+                             uint64_t *__restrict__ okeys, int32_t *__restrict__ map) {
+  const int f2 = f * f, sh = 2 * (31 - __clz(f));
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n * f2 || !flag[w]) return;
+  okeys[pos[w]] = (keys[w / f2] << sh) | (uint64_t)(w % f2);
+  map[pos[w]] = (int32_t)w;
+}
+
+// dst[o] = sub-block map[o] % f^2 of block map[o] / f^2 (one CTA per block).
+__global__ void k_split_gather(const double *__restrict__ src, const int32_t *__restrict__ map,
+                               int64_t nout, int bs, int nbs, double *__restrict__ dst) {
+  const int f = bs / nbs, f2 = f * f;
+  for (int64_t o = blockIdx.x; o < nout; o += gridDim.x) {
+    const int64_t w = map[o];
+    const int q = (int)(w % f2);
+    const int i = (int)morton_compact((uint64_t)q >> 1), j = (int)morton_compact((uint64_t)q);
+    const double *b = src + (w / f2) * bs * bs + (int64_t)(i * nbs) * bs + j * nbs;
+    double *d = dst + o * nbs * nbs;
+    for (int e = threadIdx.x; e < nbs * nbs; e += blockDim.x) d[e] = b[(e / nbs) * bs + e % nbs];
+  }
+}
+
+__global__ void k_merge_heads(const uint64_t *__restrict__ keys, int64_t n, int sh,
+                              int32_t *__restrict__ head) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  head[t] = t == 0 || (keys[t] >> sh) != (keys[t - 1] >> sh);
+}
+
+__global__ void k_merge_keys(const uint64_t *__restrict__ keys, int64_t n, int sh,
+                             const int32_t *__restrict__ head, const int32_t *__restrict__ hpos,
+                             uint64_t *__restrict__ okeys, int32_t *__restrict__ dst_of) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int32_t o = hpos[t] + head[t] - 1;  // index of this block's merged block
+  dst_of[t] = o;
+  if (head[t]) okeys[o] = keys[t] >> sh;
+}
+
+// Block t goes to sub-position key & (f^2 - 1) of merged block dst_of[t]
+// (zero-filled beforehand).  One CTA per source block.
+__global__ void k_merge_scatter(const double *__restrict__ src, const uint64_t *__restrict__ keys,
+                                const int32_t *__restrict__ dst_of, int64_t n, int bs, int nbs,
+                                double *__restrict__ dst) {
+  const int f = nbs / bs;
+  for (int64_t t = blockIdx.x; t < n; t += gridDim.x) {
+    const uint64_t q = keys[t] & (uint64_t)(f * f - 1);
+    const int i = (int)morton_compact(q >> 1), j = (int)morton_compact(q);
+    double *d = dst + (int64_t)dst_of[t] * nbs * nbs + (int64_t)(i * bs) * nbs + j * bs;
+    const double *b = src + t * bs * bs;
+    for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) d[(e / bs) * nbs + e % bs] = b[e];
+  }
+}
+
+inline unsigned grid_blocks(int64_t n) { return (unsigned)(n < 152 * 16 ? n : 152 * 16); }
+
+}  // namespace
+
+// Core of re-blocking.  keep_all: splitting keeps every sub-block inside the
+// matrix (the structure then depends only on A's structure); map_out, if not
+// NULL, receives the index map that reblock_refresh needs (caller frees).
+bsm_status reblock_impl(bsm_matrix A, int bs, bool keep_all, bsm_matrix *out, int32_t **map_out,
+                        cudaStream_t s) {
+  *out = nullptr;
+  if (map_out) *map_out = nullptr;
+  const int obs = A->bs;
+  const int64_t n = A->nblk;
+  const int64_t mb = (A->nrows + bs - 1) / bs, nb = (A->ncols + bs - 1) / bs;
+  const int64_t side = mb > nb ? mb : nb;
+  bsm_matrix R = new_matrix_shell(A->nrows, A->ncols, bs, ceil_log2_i64(side < 1 ? 1 : side));
+  bsm_status st = BSM_OK;
+  int32_t *flag = nullptr, *pos = nullptr, *map = nullptr;
+  int64_t nout = 0;
+  auto owned_alloc = [&](void **p, size_t bytes) {
+    bsm_status r = dev_alloc(p, bytes, s);
+    if (r == BSM_OK) R->owned.push_back(*p);
+    return r;
+  };
+  int32_t *h = (int32_t *)host_scratch().get(16);
+  if (!h) st = BSM_ERR_OOM;
+  if (st == BSM_OK && n > 0 && bs == obs) {
+    nout = n;
+    if ((st = owned_alloc((void **)&R->keys, 8 * n)) == BSM_OK &&
+        (st = owned_alloc((void **)&R->vals, sizeof(double) * bs * bs * n)) == BSM_OK) {
+      cudaMemcpyAsync(R->keys, A->keys, 8 * n, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(R->vals, A->vals, sizeof(double) * bs * bs * n, cudaMemcpyDeviceToDevice, s);
+    }
+  } else if (st == BSM_OK && n > 0 && bs < obs) {
+    const int f = obs / bs;
+    const int64_t m = n * f * f;
+    if (m > 0x7FFFFFFF) st = BSM_ERR_UNSUPPORTED;
+    if (st == BSM_OK && (st = dev_alloc((void **)&flag, 4 * m, s)) == BSM_OK &&
+        (st = dev_alloc((void **)&pos, 4 * m, s)) == BSM_OK) {
+      count_launch();
+      k_split_flags<<<grid_for(m * 32, 256), 256, 0, s>>>(A->vals, A->keys, n, obs, bs,
+                                                          keep_all ? 1 : 0, mb, nb, flag);
+      st = scan_exclusive_i32(flag, pos, m, s);
+    }
+    if (st == BSM_OK) {
+      cudaMemcpyAsync(h, pos + m - 1, 4, cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(h + 1, flag + m - 1, 4, cudaMemcpyDeviceToHost, s);
+      st = cuda_status(cudaStreamSynchronize(s));
+      nout = (int64_t)h[0] + h[1];
+    }
+    if (st == BSM_OK && nout > 0 && (st = owned_alloc((void **)&R->keys, 8 * nout)) == BSM_OK &&
+        (st = owned_alloc((void **)&R->vals, sizeof(double) * bs * bs * nout)) == BSM_OK &&
+        (st = dev_alloc((void **)&map, 4 * nout, s)) == BSM_OK) {
+      count_launch(2);
+      k_split_keys<<<grid_for(m, 256), 256, 0, s>>>(A->keys, n, f, flag, pos, R->keys, map);
+      k_split_gather<<<grid_blocks(nout), 256, 0, s>>>(A->vals, map, nout, obs, bs, R->vals);
+      st = cuda_status(cudaGetLastError());
+    }
+  } else if (st == BSM_OK && n > 0) {
+    const int f = bs / obs;
+    const int sh = 2 * (f == 2 ? 1 : 2);
+    if ((st = dev_alloc((void **)&flag, 4 * n, s)) == BSM_OK &&
+        (st = dev_alloc((void **)&pos, 4 * n, s)) == BSM_OK &&
+        (st = dev_alloc((void **)&map, 4 * n, s)) == BSM_OK) {
+      count_launch();
+      k_merge_heads<<<grid_for(n, 256), 256, 0, s>>>(A->keys, n, sh, flag);
+      st = scan_exclusive_i32(flag, pos, n, s);
+    }
+    if (st == BSM_OK) {
+      cudaMemcpyAsync(h, pos + n - 1, 4, cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(h + 1, flag + n - 1, 4, cudaMemcpyDeviceToHost, s);
+      st = cuda_status(cudaStreamSynchronize(s));
+      nout = (int64_t)h[0] + h[1];
+    }
+    if (st == BSM_OK && (st = owned_alloc((void **)&R->keys, 8 * nout)) == BSM_OK &&
+        (st = owned_alloc((void **)&R->vals, sizeof(double) * bs * bs * nout)) == BSM_OK) {
+      cudaMemsetAsync(R->vals, 0, sizeof(double) * bs * bs * nout, s);
+      count_launch(2);
+      k_merge_keys<<<grid_for(n, 256), 256, 0, s>>>(A->keys, n, sh, flag, pos, R->keys, map);
+      k_merge_scatter<<<grid_blocks(n), 256, 0, s>>>(A->vals, A->keys, map, n, obs, bs, R->vals);
+      st = cuda_status(cudaGetLastError());
+    }
+  }
+  dev_free(flag, s);
+  dev_free(pos, s);
+  if (st == BSM_OK && map_out) {
+    *map_out = map;
+  } else {
+    dev_free(map, s);
+  }
+  R->nblk = st == BSM_OK ? nout : 0;
+  if (st == BSM_OK) st = build_levels(R, s);
+  if (st != BSM_OK) {
+    if (map_out && *map_out) {
+      dev_free(*map_out, s);
+      *map_out = nullptr;
+    }
+    free_matrix_shell(R, s);
+    return st;
+  }
+  *out = R;
+  return BSM_OK;
+}
+
+void reblock_refresh(bsm_matrix src, bsm_matrix dst, const int32_t *map, cudaStream_t s) {
+  if (src->nblk == 0 || dst->nblk == 0) return;
+  const int obs = src->bs, bs = dst->bs;
+  if (obs == bs) {
+    cudaMemcpyAsync(dst->vals, src->vals, sizeof(double) * bs * bs * src->nblk,
+                    cudaMemcpyDeviceToDevice, s);
+  } else if (bs < obs) {
+    count_launch();
+    k_split_gather<<<grid_blocks(dst->nblk), 256, 0, s>>>(src->vals, map, dst->nblk, obs, bs,
+                                                          dst->vals);
+  } else {
+    cudaMemsetAsync(dst->vals, 0, sizeof(double) * bs * bs * dst->nblk, s);
+    count_launch();
+    k_merge_scatter<<<grid_blocks(src->nblk), 256, 0, s>>>(src->vals, src->keys, map, src->nblk,
+                                                           obs, bs, dst->vals);
+  }
+}
+
+extern "C" bsm_status bsm_reblock(bsm_matrix A, int bs, bsm_matrix *out, void *stream) {
+  if (!out) return BSM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!A) return BSM_ERR_INVALID_ARG;
+  if (bs != 16 && bs != 32 && bs != 64) return BSM_ERR_BLOCKSIZE;
+  return reblock_impl(A, bs, false, out, nullptr, (cudaStream_t)stream);
+}

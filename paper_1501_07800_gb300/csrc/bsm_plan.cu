@@ -10,6 +10,10 @@
 // values of an operand (same blocks), a replay recomputes C from the new values
 // with no symbolic work and no host round trips.
 //
+// Leaf size: with BSM_FLAG_AUTOTUNE_BS the plan also tries the block sides
+// 16, 32 and 64 (split mode: 16 and 32) on re-blocked copies of the operands
+// and keeps the fastest full execution (copy refresh included).
+//
 // Autotuning: for a product class (precision, block size, slice count, number
 // of products, and the magnitudes of the C-block count and of the mean and
 // largest product-list length) the tuner times each candidate launch
@@ -46,6 +50,13 @@ struct bsm_plan_s {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // Leaf-size choice (BSM_FLAG_AUTOTUNE_BS): the plan wraps an inner plan at
+  // block size `bs` over re-blocked copies of the operands, refreshed from the
+  // caller's handles at every execution; results are re-cut to user_bs.
+  bsm_plan inner = nullptr;
+  int user_bs = 0;
+  std::vector<bsm_matrix> rsrc, rops;  // caller handle -> re-blocked copy (owned)
+  std::vector<int32_t *> rmap;         // refresh maps (owned)
 };
 
 namespace {
@@ -102,6 +113,9 @@ void destroy_plan(bsm_plan P) {
   int cur = 0;
   cudaGetDevice(&cur);
   if (cur != P->device) cudaSetDevice(P->device);
+  if (P->inner) destroy_plan(P->inner);
+  for (bsm_matrix M : P->rops) bsm_destroy(M);
+  for (int32_t *m : P->rmap) dev_free(m, nullptr);
   cudaStream_t s = P->stream;
   if (P->exec) cudaGraphExecDestroy(P->exec);
   if (P->graph) cudaGraphDestroy(P->graph);
@@ -192,6 +206,109 @@ bsm_status autotune(bsm_plan P) {
   return BSM_OK;
 }
 
+// Refreshes the re-blocked operands of a wrapper plan from the caller's
+// handles, then runs the inner plan (stream-ordered on `cs`).
+bsm_status execute_wrapped(bsm_plan W, cudaStream_t cs) {
+  for (size_t r = 0; r < W->rops.size(); r++) reblock_refresh(W->rsrc[r], W->rops[r], W->rmap[r], cs);
+  BSM_CUDA(cudaGetLastError());
+  return bsm_plan_execute(W->inner, cs);
+}
+
+// A wrapper plan computing at block size cb (== the operands' own: no copies).
+bsm_status create_at_bs(int n, const bsm_matrix *A, const bsm_matrix *B, const bsm_mult_opts &o,
+                        int cb, cudaStream_t cs, bsm_plan *out) {
+  *out = nullptr;
+  bsm_plan W = new bsm_plan_s();
+  cudaGetDevice(&W->device);
+  W->n = n;
+  W->prec = o.prec;
+  W->bs = cb;
+  W->user_bs = A[0]->bs;
+  W->A.assign(A, A + n);
+  W->B.assign(B, B + n);
+  std::vector<bsm_matrix> ia(n), ib(n);
+  bsm_status st = BSM_OK;
+  auto copy_of = [&](bsm_matrix X, bsm_matrix *R) -> bsm_status {
+    if (X->bs == cb) {
+      *R = X;
+      return BSM_OK;
+    }
+    for (size_t r = 0; r < W->rsrc.size(); r++)
+      if (W->rsrc[r] == X) {
+        *R = W->rops[r];
+        return BSM_OK;
+      }
+    int32_t *map = nullptr;
+    BSM_TRY(reblock_impl(X, cb, true, R, &map, cs));
+    W->rsrc.push_back(X);
+    W->rops.push_back(*R);
+    W->rmap.push_back(map);
+    return BSM_OK;
+  };
+  for (int i = 0; i < n && st == BSM_OK; i++) {
+    st = copy_of(A[i], &ia[i]);
+    if (st == BSM_OK) st = copy_of(B[i], &ib[i]);
+  }
+  if (st == BSM_OK) st = bsm_plan_create(n, ia.data(), ib.data(), &o, cs, &W->inner);
+  if (st != BSM_OK) {
+    destroy_plan(W);
+    return st;
+  }
+  W->nitems = W->inner->nitems;
+  *out = W;
+  return BSM_OK;
+}
+
+// Leaf-size autotuning: a wrapper plan per candidate block size, each timed
+// over full executions (operand refresh included); the fastest is kept.
+bsm_status create_tuned_bs(int n, const bsm_matrix *A, const bsm_matrix *B, bsm_mult_opts o,
+                           cudaStream_t cs, bsm_plan *out) {
+  *out = nullptr;
+  o.flags = BSM_FLAG_AUTOTUNE;  // the inner plans tune their launch parameters
+  std::vector<int> cands = o.prec == BSM_FP64 ? std::vector<int>{16, 32, 64}
+                                              : std::vector<int>{16, 32};
+  bsm_plan best = nullptr;
+  float best_ms = 1e30f;
+  bsm_status first_err = BSM_OK;
+  cudaEvent_t a, b;
+  BSM_CUDA(cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return BSM_ERR_CUDA;
+  }
+  for (int cb : cands) {
+    bsm_plan W = nullptr;
+    bsm_status st = create_at_bs(n, A, B, o, cb, cs, &W);
+    float ms = 1e30f;
+    for (int r = 0; r < 2 && st == BSM_OK; r++) {  // the first run warms up
+      cudaEventRecord(a, cs);
+      st = execute_wrapped(W, cs);
+      cudaEventRecord(b, cs);
+      if (st == BSM_OK) st = cuda_status(cudaEventSynchronize(b));
+      float t = 0;
+      if (st == BSM_OK && r > 0 && cudaEventElapsedTime(&t, a, b) == cudaSuccess) ms = t;
+    }
+    if (st != BSM_OK) {
+      if (first_err == BSM_OK) first_err = st;
+      destroy_plan(W);
+      cudaGetLastError();
+      continue;
+    }
+    if (ms < best_ms) {
+      destroy_plan(best);
+      best = W;
+      best_ms = ms;
+    } else {
+      destroy_plan(W);
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (!best) return first_err != BSM_OK ? first_err : BSM_ERR_CUDA;
+  *out = best;
+  return BSM_OK;
+}
+
 }  // namespace
 
 extern "C" bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matrix *B,
@@ -201,13 +318,15 @@ extern "C" bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matr
   if (n < 1 || !A || !B) return BSM_ERR_INVALID_ARG;
   for (int i = 0; i < n; i++) BSM_TRY(check_pair(A[i], B[i]));
   int tune = opts ? (opts->flags & BSM_FLAG_AUTOTUNE) : 0;
+  const int tune_bs = opts ? (opts->flags & BSM_FLAG_AUTOTUNE_BS) : 0;
   bsm_mult_opts o = opts ? *opts : bsm_mult_opts{BSM_FP64, 0, 0};
-  o.flags &= ~BSM_FLAG_AUTOTUNE;
+  o.flags &= ~(BSM_FLAG_AUTOTUNE | BSM_FLAG_AUTOTUNE_BS);
   int prec, slices;
   BSM_TRY(check_opts(&o, &prec, &slices, 0));
   const int bs = A[0]->bs;
   for (int i = 0; i < n; i++)
-    if (A[i]->bs != bs) return BSM_ERR_BLOCKSIZE;  // one block size per plan
+    if (A[i]->bs != bs || B[i]->bs != bs) return BSM_ERR_BLOCKSIZE;  // one block size per plan
+  if (tune_bs) return create_tuned_bs(n, A, B, o, (cudaStream_t)stream, out);
   if (prec != BSM_FP64) BSM_TRY(split_supported(bs, slices));
 
   bsm_plan P = new bsm_plan_s();
@@ -315,6 +434,7 @@ extern "C" bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matr
 extern "C" bsm_status bsm_plan_execute(bsm_plan P, void *stream) {
   if (!P) return BSM_ERR_INVALID_ARG;
   cudaStream_t cs = (cudaStream_t)stream;
+  if (P->inner) return execute_wrapped(P, cs);
   BSM_CUDA(cudaEventRecord(P->ev_in, cs));
   BSM_CUDA(cudaStreamWaitEvent(P->stream, P->ev_in, 0));
   BSM_CUDA(cudaGraphLaunch(P->exec, P->stream));
@@ -328,6 +448,23 @@ extern "C" bsm_status bsm_plan_results(bsm_plan P, bsm_matrix *C, void *stream) 
   for (int i = 0; i < P->n; i++) C[i] = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
   bsm_status st = BSM_OK;
+  if (P->inner) {
+    BSM_TRY(bsm_plan_results(P->inner, C, stream));
+    if (P->bs == P->user_bs) return BSM_OK;
+    // re-cut to the operands' block size (all-zero blocks dropped)
+    for (int i = 0; i < P->n && st == BSM_OK; i++) {
+      bsm_matrix R = nullptr;
+      st = reblock_impl(C[i], P->user_bs, false, &R, nullptr, s);
+      bsm_destroy(C[i]);
+      C[i] = R;
+    }
+    if (st != BSM_OK)
+      for (int i = 0; i < P->n; i++) {
+        bsm_destroy(C[i]);
+        C[i] = nullptr;
+      }
+    return st;
+  }
   for (int i = 0; i < P->n && st == BSM_OK; i++) {
     bsm_matrix a = P->A[i], b = P->B[i];
     int64_t side = a->mb > b->nb ? a->mb : b->nb;
@@ -347,9 +484,16 @@ extern "C" bsm_status bsm_plan_results(bsm_plan P, bsm_matrix *C, void *stream) 
   return st;
 }
 
+extern "C" bsm_status bsm_plan_block_size(bsm_plan P, int *bs) {
+  if (!P || !bs) return BSM_ERR_INVALID_ARG;
+  *bs = P->bs;
+  return BSM_OK;
+}
+
 extern "C" bsm_status bsm_plan_info(bsm_plan P, int *order, int *chunk, int *ctas_per_sm,
                                     int64_t *nitems) {
   if (!P) return BSM_ERR_INVALID_ARG;
+  if (P->inner) return bsm_plan_info(P->inner, order, chunk, ctas_per_sm, nitems);
   if (order) *order = P->order;
   if (chunk) *chunk = P->chunk;
   if (ctas_per_sm) *ctas_per_sm = P->ctas_per_sm;

@@ -239,7 +239,7 @@ struct Expander {
   int64_t budget;
   int64_t *tasks;  // per height
   const LeafSink &sink;
-  bool upper;
+  int upper;  // 0: all of C; k >= 1: C nodes at height >= k - 1 on or above the diagonal
   int chunks = 0;
 
   // segment starts [0] and [idx] of a level part, read back
@@ -301,7 +301,7 @@ struct Expander {
       return st;
     }
     cudaMemsetAsync(tot, 0, 8, s);
-    const UpperView up{upper ? L.sck : nullptr, L.pseg, L.soff};
+    const UpperView up{(upper && L.h - 1 >= upper - 1) ? L.sck : nullptr, L.pseg, L.soff};
     count_launch();
     k_sym_count<<<grid_for(L.np + 1, 256), 256, 0, s>>>(L.pa, L.pb, L.np, va, vb, qmask, up, P,
                                                          tot);
@@ -408,7 +408,7 @@ void free_symbolic(SymbolicResult *r, cudaStream_t s) {
 }
 
 bsm_status symbolic_chunks(bsm_matrix A, bsm_matrix B, const LeafSink &sink, int64_t *tasks,
-                           int *H, int *nchunks, cudaStream_t s, int64_t budget, bool upper) {
+                           int *H, int *nchunks, cudaStream_t s, int64_t budget, int upper) {
   const int h0 = A->L > B->L ? A->L : B->L;
   *H = h0;
   *nchunks = 0;

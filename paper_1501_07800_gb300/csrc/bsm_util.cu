@@ -150,6 +150,21 @@ bsm_status scan_exclusive_int4(const int4 *in, int4 *out, int64_t n, cudaStream_
   }, s);
 }
 
+struct SatAddU64 {
+  __host__ __device__ uint64_t operator()(uint64_t a, uint64_t b) const {
+    const uint64_t c = a + b;
+    return c < a ? ~0ull : c;
+  }
+};
+
+bsm_status scan_inclusive_u64_sat(const uint64_t *in, uint64_t *out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return BSM_OK;
+  count_launch(2);
+  return run_cub([&](void *t, size_t &b) {
+    return cub::DeviceScan::InclusiveScan(t, b, in, out, SatAddU64(), n, s);
+  }, s);
+}
+
 bsm_status sort_keys_u64(const uint64_t *kin, uint64_t *kout, const int32_t *vin, int32_t *vout,
                          int64_t n, int end_bit, cudaStream_t s) {
   if (n <= 0) return BSM_OK;

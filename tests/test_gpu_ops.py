@@ -153,3 +153,35 @@ def test_add_errors():
     with pytest.raises(bsm.BsmError) as e:
         bsm.bsm_add(A, C)
     assert e.value.name == "BSM_ERR_BLOCKSIZE"
+
+
+def recut(m: synth.BlockCOO, bs: int) -> synth.BlockCOO:
+    """The dense matrix cut into bs x bs blocks, all-zero blocks omitted."""
+    return synth.from_dense(m.to_dense(), bs).sorted()
+
+
+@pytest.mark.parametrize("obs,nbs", [(32, 16), (64, 16), (64, 32), (16, 32), (16, 64), (32, 64),
+                                     (32, 32)])
+def test_reblock_bit_exact(obs, nbs):
+    A = synth.random_blocks(20 * obs + 13, obs, 0.2, 450 + obs + nbs, ncols=17 * obs + 5)
+    # make some sub-blocks exactly zero so that splitting must drop them
+    A.vals[::3, : obs // 2, : obs // 2] = 0.0
+    R = from_bsm(bsm.bsm_reblock(to_bsm(A), nbs))
+    E = recut(A, nbs)
+    assert_same_structure(R, E)
+    assert np.array_equal(R.vals, E.vals)
+
+
+def test_reblock_round_trip_and_product():
+    A = synth.random_blocks(3000, 32, 0.03, 460)
+    B = synth.random_blocks(3000, 32, 0.03, 461)
+    M = to_bsm(A)
+    back = from_bsm(bsm.bsm_reblock(bsm.bsm_reblock(M, 64), 32))
+    assert_same_structure(back, A.sorted())
+    assert np.array_equal(back.vals, A.sorted().vals)
+    # the product at bs 64 is the product at bs 32, re-cut
+    C64 = from_bsm(bsm.bsm_reblock(bsm.bsm_multiply(bsm.bsm_reblock(M, 64),
+                                                     bsm.bsm_reblock(to_bsm(B), 64)), 32))
+    E = oracle.multiply(A, B).C
+    assert_same_structure(C64, E)
+    assert relerr(C64.vals, E.vals) < TOL

@@ -84,3 +84,51 @@ def test_update_values_rejects_other_block_sets():
     # the handle is unchanged
     r = from_bsm(M)
     assert np.array_equal(r.vals, a.sorted().vals)
+
+
+@pytest.mark.parametrize("prec,tol", [(bsm.BSM_FP64, 1e-12), (bsm.BSM_SPLIT_BF16, 1e-11)])
+def test_plan_chooses_leaf_size(prec, tol):
+    """With leaf-size tuning the plan may compute at another block side on
+    re-blocked copies; results come back at the operands' block size with the
+    oracle's structure, also after the operand values change."""
+    pairs = batch(nprod=4, seed=51)
+    As = [to_bsm(a) for a, _ in pairs]
+    Bs = [to_bsm(b) for _, b in pairs]
+    plan = bsm.bsm_plan_create(As, Bs, prec=prec, autotune=True, autotune_bs=True)
+    cb = bsm.bsm_plan_block_size(plan)
+    assert cb in ((16, 32, 64) if prec == bsm.BSM_FP64 else (16, 32))
+    bsm.bsm_plan_execute(plan)
+    got = [from_bsm(c) for c in bsm.bsm_plan_results(plan)]
+    for (a, b), g in zip(pairs, got):
+        E = oracle.multiply(a, b).C
+        assert_same_structure(g, E)
+        assert relerr(g.vals, E.vals) < tol
+    # new values, same blocks: the re-blocked copies are refreshed on execute
+    new_pairs = []
+    for (a, b), ga in zip(pairs, As):
+        vals = a.vals * 0.5 - 0.125
+        vals[a.vals == 0.0] = 0.0
+        bsm.bsm_update_values(ga, a.brow, a.bcol, vals)
+        new_pairs.append((synth.BlockCOO(a.nrows, a.ncols, a.bs, a.brow, a.bcol, vals), b))
+    bsm.bsm_plan_execute(plan)
+    got = [from_bsm(c) for c in bsm.bsm_plan_results(plan)]
+    for (a, b), g in zip(new_pairs, got):
+        E = oracle.multiply(a, b).C
+        assert_same_structure(g, E)
+        assert relerr(g.vals, E.vals) < tol
+
+
+@pytest.mark.parametrize("cb", [16, 64])
+def test_plan_at_forced_leaf_sizes_matches(cb):
+    """Each leaf size the tuner may pick gives the oracle's result (the tuner
+    is bypassed by re-blocking by hand and planning at that size)."""
+    pairs = batch(nprod=3, seed=61)
+    ra = [bsm.bsm_reblock(to_bsm(a), cb) for a, _ in pairs]
+    rb = [bsm.bsm_reblock(to_bsm(b), cb) for _, b in pairs]
+    plan = bsm.bsm_plan_create(ra, rb)
+    bsm.bsm_plan_execute(plan)
+    got = [from_bsm(bsm.bsm_reblock(c, 32)) for c in bsm.bsm_plan_results(plan)]
+    for (a, b), g in zip(pairs, got):
+        E = oracle.multiply(a, b).C
+        assert_same_structure(g, E)
+        assert relerr(g.vals, E.vals) < 1e-12

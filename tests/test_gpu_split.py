@@ -181,8 +181,27 @@ def test_split_is_deterministic():
     assert np.array_equal(C1.vals, C2.vals)
 
 
-def test_split_rejects_bs64():
-    A = to_bsm(synth.random_blocks(128, 64, 1.0, 5))
-    with pytest.raises(bsm.BsmError) as e:
-        bsm.bsm_multiply(A, A, prec=bsm.BSM_SPLIT_BF16)
-    assert e.value.name == "BSM_ERR_UNSUPPORTED"
+def test_split_bs64_equals_bs32_recut():
+    """bs 64 runs as the bs-32 product of the re-cut operands: identical bits
+    to splitting the same matrices cut at 32, and the oracle's structure."""
+    A = synth.random_blocks(40 * 64 + 17, 64, 0.1, 5)
+    B = synth.random_blocks(40 * 64 + 17, 64, 0.1, 6)
+    C = from_bsm(bsm.bsm_multiply(to_bsm(A), to_bsm(B), prec=bsm.BSM_SPLIT_BF16))
+    E = oracle.multiply(A, B).C
+    assert_same_structure(C, E)
+    assert relerr(C.vals, E.vals) < TOL_SPLIT
+    a32 = synth.from_dense(A.to_dense(), 32)
+    b32 = synth.from_dense(B.to_dense(), 32)
+    C32 = from_bsm(bsm.bsm_reblock(bsm.bsm_multiply(to_bsm(a32), to_bsm(b32),
+                                                    prec=bsm.BSM_SPLIT_BF16), 64))
+    assert_same_structure(C, C32)
+    assert np.array_equal(C.vals, C32.vals)
+
+
+def test_split_bs64_symmetric_square():
+    A = synth.decay(300, 64, 19)
+    U = synth.upper_blocks(A)
+    C = from_bsm(bsm.bsm_sym_square(to_bsm(U), prec=bsm.BSM_SPLIT_BF16))
+    E = oracle.sym_square(U)
+    assert_same_structure(C, E)
+    assert relerr(C.vals, E.vals) < TOL_SPLIT
