@@ -605,6 +605,40 @@ def run_decay(args):
     return 0
 
 
+def run_rmat(args):
+    """Locality sweep on R-MAT graph matrices (N = 8192, 5 edge draws per row,
+    b = c = d = (1 - a) / 3): per-level multiply-task counts of A*A (the
+    quantity of Fig. 5, right) and the time of the product, bs 16."""
+    import torch
+
+    import paper_1501_07800_gb300 as bsm
+
+    torch.cuda.set_device(0)
+    bsm.load()
+    stream = torch.cuda.current_stream()
+    out = {"workload": "R-MAT A*A, N = 8192, 5 draws per row, bs 16", "sweep": []}
+    for a in (0.25, 0.4, 0.55, 0.7, 0.85, 0.95):
+        A = synth.rmat(13, a, 16, synth.BASE_SEED + 40)
+        M = bsm.bsm_build(A.nrows, A.ncols, A.bs, A.brow, A.bcol, A.vals)
+        times = []
+        for k in range(args.warmup + args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            C = bsm.bsm_multiply(M, M)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+        tasks, triples, _ = bsm.bsm_last_stats()
+        row = {"a": a, "a_blocks": A.nblk, "c_blocks": bsm.bsm_info(C)[3],
+               "tasks_per_level_root_first": [int(x) for x in tasks], "triples": triples,
+               "ms_per_product": statistics.median(times)}
+        out["sweep"].append(row)
+        log(f"rmat: {row}")
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_e2e(bsm, torch, A, B, prec, steps):
     """Host COO in pinned memory -> bsm_build x2 -> bsm_multiply -> bsm_to_blocks
     into pinned host buffers, every step."""
@@ -650,7 +684,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--workload", default="random", choices=["random", "decay"],
+    ap.add_argument("--workload", default="random", choices=["random", "decay", "rmat"],
                     help="decay: the decay-type A*A product (separate JSON line)")
     ap.add_argument("--points", type=int, default=20000, help="decay workload: number of points")
     ap.add_argument("--bs", type=int, default=32, help="decay workload: leaf block size")
@@ -672,6 +706,8 @@ def main():
         return run_reference(args)
     if args.workload == "decay":
         return run_decay(args)
+    if args.workload == "rmat":
+        return run_rmat(args)
     return run_gpu(args)
 
 

@@ -289,6 +289,40 @@ def decay(npoints: int, bs: int, seed: int, nfun: int = 5, alpha: float = 0.5,
     return _drop_zero_blocks(BlockCOO(n, n, bs, brow, bcol, vals))
 
 
+# ------------------------------------------------------------ R-MAT graphs
+def rmat_edges(scale: int, a: float, nnz_per_row: int, seed: int):
+    """Distinct (row, col) pairs of an R-MAT graph (Chakrabarti, Zhan and
+    Faloutsos, SDM 2004) on 2^scale nodes with nnz_per_row * 2^scale edge
+    draws: each draw picks one quadrant per bit level with probabilities
+    a (top-left), b = c = d = (1 - a) / 3 (top-right, bottom-left,
+    bottom-right); repeated edges collapse to one entry."""
+    n = 1 << scale
+    m = nnz_per_row * n
+    e = np.arange(m, dtype=np.uint64)
+    b = (1.0 - a) / 3.0
+    row = np.zeros(m, np.int64)
+    col = np.zeros(m, np.int64)
+    for lvl in range(scale):
+        u = uniform01(hash3(seed, e, 1000 + lvl))
+        bottom = u >= a + b                              # quadrants c, d
+        right = ((u >= a) & (u < a + b)) | (u >= a + 2 * b)  # quadrants b, d
+        row = 2 * row + bottom
+        col = 2 * col + right
+    key = np.unique(row * n + col)
+    return key // n, key % n
+
+
+def rmat(scale: int, a: float, bs: int, seed: int, nnz_per_row: int = 5) -> BlockCOO:
+    """R-MAT graph matrix (entries 1.0) cut into bs x bs blocks."""
+    n = 1 << scale
+    row, col = rmat_edges(scale, a, nnz_per_row, seed)
+    nb = -(-n // bs)
+    bkey, inv = np.unique((row // bs) * nb + col // bs, return_inverse=True)
+    vals = np.zeros((bkey.size, bs, bs))
+    vals[inv, row % bs, col % bs] = 1.0
+    return BlockCOO(n, n, bs, (bkey // nb).astype(np.int32), (bkey % nb).astype(np.int32), vals)
+
+
 # ------------------------------------------------------ batched workload
 def batched_specs(nprod: int, seed: int, nmin: int = 2048, nmax: int = 32768,
                   dmin: float = 0.005, dmax: float = 0.10, bs: int = 32):
