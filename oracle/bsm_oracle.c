@@ -27,7 +27,7 @@
  *     (Sec. 4.1, Fig. 3), each block product a naive triple loop.
  *   - Blocks whose entries are all exactly 0.0 are not stored: input blocks
  *     are dropped when the matrix is built, product blocks after the multiply
- *     (sparsity "dynamically detected", abstract; only nonzero submatrices
+ *     (sparsity found during the computation, abstract; only nonzero submatrices
  *     stored, Sec. 4.1).  -0.0 counts as zero, NaN does not.
  *   - Multiply-task counts per level (tasks whose inputs are both non-NIL) are
  *     the quantities C_l of Sec. 5.1, Eq. 1 - Eq. 5.
