@@ -59,13 +59,16 @@ typedef enum {
 
 typedef enum {
   BSM_FP64 = 0,       /* FP64 tensor-core (DMMA) products, FP64 accumulation */
-  BSM_SPLIT_BF16 = 1  /* FP64 blocks split into BF16 slices on tcgen05 */
+  BSM_SPLIT_BF16 = 1, /* FP64 blocks split into BF16 slices (7-bit digits) on tcgen05 */
+  BSM_SPLIT_FP8 = 2   /* FP64 blocks split into FP8 E4M3 slices (4-bit digits) on tcgen05 */
 } bsm_precision;
 
 /* Options of one product (NULL = all defaults: FP64). */
 typedef struct {
   int prec;   /* bsm_precision */
-  int slices; /* split modes: number of 7-bit slices per operand, 1..8, 0 = default (7) */
+  int slices; /* split modes: digit slices per operand, 0 = default; BF16: 1..8
+                 (default 7, 49-bit fixed point per row/column), FP8: 2, 3, 4,
+                 6, 8 or 12 (default 6, 24 bits) */
   int flags;  /* 0, BSM_FLAG_AUTOTUNE (bsm_plan_create only), or
                  BSM_FLAG_TRANS_A / BSM_FLAG_TRANS_B (bsm_multiply only) */
 } bsm_mult_opts;

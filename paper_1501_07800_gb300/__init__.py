@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libbsm.so")
 
 BSM_FP64 = 0
 BSM_SPLIT_BF16 = 1
+BSM_SPLIT_FP8 = 2
 BSM_FLAG_AUTOTUNE = 1
 BSM_FLAG_TRANS_A = 2
 BSM_FLAG_TRANS_B = 4

@@ -13,7 +13,7 @@ struct ProdDesc {
   int32_t *nz;                   // nonzero flag per C block (output)
   int64_t na, nb, nc, nt;        // A blocks, B blocks, C blocks, products
   // split mode only
-  const uint16_t *asl, *bsl;     // digit slices of A / B
+  const uint8_t *asl, *bsl;      // digit slices of A / B (BF16 or E4M3 codes)
   const int *rowexp, *colexp;    // power-of-two scale exponents
 };
 

@@ -139,8 +139,18 @@ void free_symbolic(SymbolicResult *r, cudaStream_t s);
 bsm_status numeric_fp64(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, double *cvals,
                         int32_t *nzflag, unsigned *errword, cudaStream_t s);
 
-// Split-precision numeric phase (BF16 slices on tcgen05, exact FP32
-// accumulation, integer recombination).
+// Split-precision numeric phase (BF16 or E4M3 digit slices on tcgen05, exact
+// FP32 accumulation, integer recombination).  The split functions take a
+// "spec": the slice count in the low byte and the digit format (0 BF16,
+// 1 E4M3) above it, as check_opts makes it from the options.
+inline int split_spec(int fmt, int slices) { return slices | (fmt << 8); }
+inline int split_spec_fmt(int spec) { return spec >> 8; }
+inline int split_spec_slices(int spec) { return spec & 0xFF; }
+// Block width the split kernels run a single product at (operands of another
+// width are re-cut exactly): E4M3 32; BF16 the operands' own, 64 as 32.
+inline int split_width(int prec, int bs) {
+  return prec == BSM_SPLIT_FP8 ? 32 : (bs == 64 ? 32 : bs);
+}
 bsm_status numeric_split(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, int slices,
                          double *cvals, int32_t *nzflag, unsigned *errword, cudaStream_t s);
 
@@ -185,11 +195,12 @@ bsm_status multiply_one(bsm_matrix A, bsm_matrix B, int prec, int slices, cudaSt
 // (bsm_ops.cu).
 void launch_gather_blocks_t(const double *src, const int32_t *idx, double *dst, int64_t n, int bs,
                             cudaStream_t s);
-// Re-blocking (bsm_ops.cu).  keep_all: splitting keeps every sub-block inside
-// the matrix, so the new structure depends on A's structure only; map_out
-// receives the index map reblock_refresh uses to copy new values of A into
-// the re-blocked handle (caller frees it with dev_free).
-bsm_status reblock_impl(bsm_matrix A, int bs, bool keep_all, bsm_matrix *out, int32_t **map_out,
+// Re-blocking (bsm_ops.cu).  keep_all, when splitting: 0 drops all-zero
+// sub-blocks, 1 keeps every sub-block inside the matrix (the new structure
+// then depends on A's structure only), 2 drops all-zero sub-blocks and those
+// below the diagonal; map_out receives the index map reblock_refresh uses to
+// copy new values of A into the re-blocked handle (caller frees it).
+bsm_status reblock_impl(bsm_matrix A, int bs, int keep_all, bsm_matrix *out, int32_t **map_out,
                         cudaStream_t s);
 void reblock_refresh(bsm_matrix src, bsm_matrix dst, const int32_t *map, cudaStream_t s);
 bsm_status check_opts(const bsm_mult_opts *o, int *prec, int *slices, int allowed_flags);

@@ -27,15 +27,20 @@ bsm_status check_pair(bsm_matrix A, bsm_matrix B) {
   return BSM_OK;
 }
 
+// For split modes *slices receives the split spec (slice count and digit
+// format, see split_spec).
 bsm_status check_opts(const bsm_mult_opts *o, int *prec, int *slices, int allowed_flags) {
   *prec = BSM_FP64;
   *slices = 0;
   if (!o) return BSM_OK;
   if (o->flags & ~allowed_flags) return BSM_ERR_INVALID_ARG;
-  if (o->prec != BSM_FP64 && o->prec != BSM_SPLIT_BF16) return BSM_ERR_INVALID_ARG;
-  if (o->slices < 0 || o->slices > 8) return BSM_ERR_INVALID_ARG;
+  if (o->prec != BSM_FP64 && o->prec != BSM_SPLIT_BF16 && o->prec != BSM_SPLIT_FP8)
+    return BSM_ERR_INVALID_ARG;
+  const int maxs = o->prec == BSM_SPLIT_FP8 ? 12 : 8;
+  if (o->slices < 0 || o->slices > maxs) return BSM_ERR_INVALID_ARG;
   *prec = o->prec;
-  *slices = o->slices == 0 ? 7 : o->slices;
+  if (o->prec == BSM_SPLIT_BF16) *slices = split_spec(0, o->slices == 0 ? 7 : o->slices);
+  if (o->prec == BSM_SPLIT_FP8) *slices = split_spec(1, o->slices == 0 ? 6 : o->slices);
   return BSM_OK;
 }
 
@@ -238,17 +243,20 @@ static bsm_status multiply_chunked(bsm_matrix A, bsm_matrix B, int prec, int sli
 bsm_status multiply_one(bsm_matrix A, bsm_matrix B, int prec, int slices, cudaStream_t s,
                         bsm_matrix *out, bool upper) {
   *out = nullptr;
-  if (prec == BSM_FP64 || A->bs != 64) return multiply_chunked(A, B, prec, slices, s, out, upper);
-  // The split kernel takes 16- and 32-wide blocks.  Its result does not depend
-  // on the leaf size: the scales span whole rows of A and columns of B and the
-  // digit sums are exact, so the bs-64 product is the bs-32 product of the
-  // re-cut operands, merged back (an upper-triangle result keeps the 32-blocks
-  // of every diagonal 64-block).
+  const int wb = prec == BSM_SPLIT_FP8 ? 32 : (A->bs == 64 ? 32 : A->bs);  // kernel's width
+  if (prec == BSM_FP64 || A->bs == wb) return multiply_chunked(A, B, prec, slices, s, out, upper);
+  // The split kernels take 16- and 32-wide blocks (E4M3: 32 only).  Their
+  // result does not depend on the leaf size: the scales span whole rows of A
+  // and columns of B and the digit sums are exact, so the product at another
+  // width is the product of the re-cut operands, cut back.  For an
+  // upper-triangle result the pruning applies at the coarser of the two
+  // widths, and blocks below the diagonal are dropped when cutting finer.
+  const bool coarser = wb < A->bs;  // computing on finer blocks than the operands'
   bsm_matrix a = nullptr, b = nullptr, c = nullptr;
-  bsm_status st = reblock_impl(A, 32, false, &a, nullptr, s);
-  if (st == BSM_OK) st = B == A ? (b = a, BSM_OK) : reblock_impl(B, 32, false, &b, nullptr, s);
-  if (st == BSM_OK) st = multiply_chunked(a, b, prec, slices, s, &c, upper ? 2 : 0);
-  if (st == BSM_OK) st = reblock_impl(c, 64, false, out, nullptr, s);
+  bsm_status st = reblock_impl(A, wb, 0, &a, nullptr, s);
+  if (st == BSM_OK) st = B == A ? (b = a, BSM_OK) : reblock_impl(B, wb, 0, &b, nullptr, s);
+  if (st == BSM_OK) st = multiply_chunked(a, b, prec, slices, s, &c, upper ? (coarser ? 2 : 1) : 0);
+  if (st == BSM_OK) st = reblock_impl(c, A->bs, upper && !coarser ? 2 : 0, out, nullptr, s);
   bsm_destroy(c);
   if (b != a) bsm_destroy(b);
   bsm_destroy(a);
@@ -396,7 +404,7 @@ extern "C" bsm_status bsm_multiply(bsm_matrix A, bsm_matrix B, bsm_matrix *C,
   if ((ta ? A->nrows : A->ncols) != (tb ? B->ncols : B->nrows)) return BSM_ERR_DIM_MISMATCH;
   if (A->bs != B->bs) return BSM_ERR_BLOCKSIZE;
   if (A->device != B->device) return BSM_ERR_INVALID_ARG;
-  if (prec != BSM_FP64) BSM_TRY(split_supported(A->bs == 64 ? 32 : A->bs, slices));
+  if (prec != BSM_FP64) BSM_TRY(split_supported(split_width(prec, A->bs), slices));
   cudaStream_t s = (cudaStream_t)stream;
   // The transposed task types (Sec. 3.2) are the plain product of transposed
   // handles: op(X) is X with its keys' row and column bits swapped and every

@@ -48,21 +48,38 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_fp8.h>
+
 #include "bsm_batch.cuh"
 #include "bsm_ptx.cuh"
 
 namespace {
 
-constexpr int kBeta = 7;       // digit width in bits
-constexpr int kMaxSlices = 8;  // 56-bit fixed point at most
+// Digit formats.  F = 0: BF16 operands, base-2^7 digits (|a_0| <= 128, the
+// others <= 64, exact in BF16's 8-bit significand), MMA kind::f16, K = 16 per
+// instruction.  F = 1: FP8 E4M3 operands, base-2^4 digits (|a_0| <= 16, the
+// others <= 8, exact in E4M3), MMA kind::f8f6f4, K = 32 per instruction.
+// TSPLIT: the combination keeps the digit terms with shift < TSPLIT in `lo`
+// and the rest in `hi` (value = hi 2^TSPLIT + lo), chosen so that neither
+// part can overflow 64 bits.
+template <int F>
+struct Fmt;
+template <>
+struct Fmt<0> {
+  static constexpr int BETA = 7, EB = 2, KPI = 16, TSPLIT = 35, MAXS = 8;
+};
+template <>
+struct Fmt<1> {
+  static constexpr int BETA = 4, EB = 1, KPI = 32, TSPLIT = 32, MAXS = 12;
+};
 constexpr uint32_t kMagic = 0x4B400000u;  // bits of 1.5 * 2^23
 constexpr float kMagicF = 12582912.0f;
 
-template <int BS, int S>
+template <int BS, int S, int F>
 struct Cfg {
   static constexpr int DPG = 128 / BS;                       // diagonals per group
   static constexpr int G = (S + DPG - 1) / DPG;              // diagonal groups
-  static constexpr int SLICE = BS * BS * 2;                  // bytes of one BF16 slice
+  static constexpr int SLICE = BS * BS * Fmt<F>::EB;         // bytes of one slice
   static constexpr int ASLOTS = (DPG - 1) + G * DPG;         // zero pad + slices + pad
   static constexpr int BSLOTS = S;
   static constexpr int STAGE = (ASLOTS + BSLOTS) * SLICE;
@@ -71,11 +88,11 @@ struct Cfg {
   // ring depth: up to 4 (bs 32) / 8 (bs 16) stages within 227 KiB of shared
   // memory, 8 KiB of it left for the static barriers and descriptor ring
   static constexpr int BUDGET = 227 * 1024 - 8 * 1024 - 2 * COMB;
-  static constexpr int NSTMAX = BS == 32 ? 4 : 8;
+  static constexpr int NSTMAX = BS == 32 ? (F ? 6 : 4) : 8;
   static constexpr int NST = BUDGET / STAGE < NSTMAX ? BUDGET / STAGE : NSTMAX;
   static constexpr int SMEM = NST * STAGE + 2 * COMB;
   static_assert(NST >= 2, "shared memory too small for two stages");
-  static constexpr uint32_t SBO = BS * 16;                   // 8-row group stride
+  static constexpr uint32_t SBO = BS * 8 * Fmt<F>::EB;       // 8-row group stride
   static constexpr uint32_t LBO = 128;                       // K core-matrix stride
 };
 
@@ -123,8 +140,8 @@ __global__ void k_col_exp(const double *__restrict__ vals, const uint64_t *__res
   if (m != INT_MIN) atomicMax(colexp + J * bs + c, m);
 }
 
-// Balanced base-2^7 digits of round(x * 2^(7S - E)), most significant first.
-template <int S>
+// Balanced base-2^B digits of round(x * 2^(B S - E)), most significant first.
+template <int S, int B>
 __device__ __forceinline__ void digits(double x, int E, int (&d)[S]) {
   uint64_t b = (uint64_t)__double_as_longlong(x);
   int e = (int)((b >> 52) & 0x7FF);
@@ -135,9 +152,9 @@ __device__ __forceinline__ void digits(double x, int E, int (&d)[S]) {
     m |= 1ull << 52;
   int64_t X = 0;
   if (m != 0) {
-    int sh = e - 1075 - E + kBeta * S;  // x = m 2^(e-1075), |x| < 2^E
+    int sh = e - 1075 - E + B * S;  // x = m 2^(e-1075), |x| < 2^E
     if (sh >= 0) {
-      X = (int64_t)(m << sh);  // < 2^(7S) <= 2^56
+      X = (int64_t)(m << sh);  // < 2^(B S) <= 2^56
     } else if (sh > -64) {
       uint64_t q = m >> (-sh);
       uint64_t half = (m >> (-sh - 1)) & 1ull;  // round half away from zero
@@ -147,9 +164,9 @@ __device__ __forceinline__ void digits(double x, int E, int (&d)[S]) {
   }
 #pragma unroll
   for (int i = S - 1; i >= 1; i--) {
-    int64_t dig = ((X + (1 << (kBeta - 1))) & ((1 << kBeta) - 1)) - (1 << (kBeta - 1));
+    int64_t dig = ((X + (1 << (B - 1))) & ((1 << B) - 1)) - (1 << (B - 1));
     d[i] = (int)dig;
-    X = (X - dig) >> kBeta;
+    X = (X - dig) >> B;
   }
   d[0] = (int)X;
 }
@@ -161,20 +178,29 @@ __device__ __forceinline__ uint32_t small_int_to_bf16(int v) {
   return __float_as_uint(f) >> 16;
 }
 
-// Writes the S slices of every block in the MMA operand layout (K-major,
-// 8x8 BF16 core matrices of 128 bytes, K core matrices 128 B apart, 8-row
-// groups BS*16 B apart).  TRANS = 0: A block, operand rows = block rows,
-// K = block columns, row scales.  TRANS = 1: B block, operand rows = block
-// columns, K = block rows, column scales.  A CTA stages one block in shared
-// memory; each thread makes one 8-element core-matrix row (16 bytes per slice)
-// so that a warp writes 512 contiguous bytes per slice.
-template <int BS, int S, int TRANS>
+__device__ __forceinline__ uint32_t small_int_to_e4m3(int v) {
+  // |v| <= 16 has at most 4 significant bits and an exponent within E4M3's
+  // range: the conversion is exact
+  return (uint32_t)__nv_cvt_float_to_fp8((float)v, __NV_SATFINITE, __NV_E4M3);
+}
+
+// Writes the S slices of every block in the MMA operand layout (K-major
+// core matrices of 8 rows x 16 bytes -- 8 BF16 or 16 E4M3 elements -- K core
+// matrices 128 B apart, 8-row groups SBO apart).  TRANS = 0: A block, operand
+// rows = block rows, K = block columns, row scales.  TRANS = 1: B block,
+// operand rows = block columns, K = block rows, column scales.  A CTA stages
+// one block in shared memory; each thread makes one core-matrix row (16 bytes
+// per slice), so a warp writes 512 contiguous bytes per slice.
+template <int BS, int S, int TRANS, int F>
 __global__ void __launch_bounds__(128) k_slice(const double *__restrict__ vals,
                                                const uint64_t *__restrict__ keys, int64_t n,
                                                const int *__restrict__ exps,
-                                               uint16_t *__restrict__ out) {
+                                               uint8_t *__restrict__ out) {
+  using C = Cfg<BS, S, F>;
+  constexpr int B = Fmt<F>::BETA;
+  constexpr int EPR = 16 / Fmt<F>::EB;  // elements per core-matrix row
+  constexpr int KG = BS / EPR;
   __shared__ double blk[BS * (BS + 1)];
-  constexpr int KG = BS / 8;
   for (int64_t t = blockIdx.x; t < n; t += gridDim.x) {
     const double *src = vals + t * (int64_t)BS * BS;
     for (int e = threadIdx.x; e < BS * BS; e += blockDim.x)
@@ -185,52 +211,63 @@ __global__ void __launch_bounds__(128) k_slice(const double *__restrict__ vals,
     for (int task = threadIdx.x; task < BS * KG; task += blockDim.x) {
       const int kg = task % KG, mrow = task / KG;
       const int E = exps[rc * BS + mrow];
-      uint32_t w[S][4];
+      uint32_t w[S][4] = {};
 #pragma unroll
-      for (int x = 0; x < 8; x += 2) {
-        const int k0 = kg * 8 + x;
-        double v0 = TRANS == 0 ? blk[mrow * (BS + 1) + k0] : blk[k0 * (BS + 1) + mrow];
-        double v1 = TRANS == 0 ? blk[mrow * (BS + 1) + k0 + 1] : blk[(k0 + 1) * (BS + 1) + mrow];
-        int d0[S], d1[S];
-        digits<S>(v0, E, d0);
-        digits<S>(v1, E, d1);
+      for (int x = 0; x < EPR; x++) {
+        const int k = kg * EPR + x;
+        const double v = TRANS == 0 ? blk[mrow * (BS + 1) + k] : blk[k * (BS + 1) + mrow];
+        int dg[S];
+        digits<S, B>(v, E, dg);
 #pragma unroll
-        for (int i = 0; i < S; i++)
-          w[i][x / 2] = small_int_to_bf16(d0[i]) | (small_int_to_bf16(d1[i]) << 16);
+        for (int i = 0; i < S; i++) {
+          if (F == 0)
+            w[i][x / 2] |= small_int_to_bf16(dg[i]) << (16 * (x & 1));
+          else
+            w[i][x / 4] |= small_int_to_e4m3(dg[i]) << (8 * (x & 3));
+        }
       }
-      const uint32_t off = (mrow >> 3) * (BS * 16) + kg * 128 + (mrow & 7) * 16;  // bytes
-      uint8_t *base = reinterpret_cast<uint8_t *>(out + t * (int64_t)S * BS * BS);
+      const uint32_t off = (mrow >> 3) * C::SBO + kg * 128 + (mrow & 7) * 16;  // bytes
+      uint8_t *base = out + t * (int64_t)S * C::SLICE;
 #pragma unroll
       for (int i = 0; i < S; i++)
-        *reinterpret_cast<uint4 *>(base + (size_t)i * BS * BS * 2 + off) =
+        *reinterpret_cast<uint4 *>(base + (size_t)i * C::SLICE + off) =
             make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
     }
     __syncthreads();
   }
 }
 
-template <int BS, int S>
+template <int BS, int S, int F>
 void launch_slices(bsm_matrix A, bsm_matrix B, const int *rowexp, const int *colexp,
-                   uint16_t *asl, uint16_t *bsl, cudaStream_t s) {
+                   uint8_t *asl, uint8_t *bsl, cudaStream_t s) {
   auto grid = [](int64_t n) { return (unsigned)(n < 152 * 16 ? n : 152 * 16); };
   count_launch(2);
-  if (A->nblk) k_slice<BS, S, 0><<<grid(A->nblk), 128, 0, s>>>(A->vals, A->keys, A->nblk, rowexp, asl);
-  if (B->nblk) k_slice<BS, S, 1><<<grid(B->nblk), 128, 0, s>>>(B->vals, B->keys, B->nblk, colexp, bsl);
+  if (A->nblk)
+    k_slice<BS, S, 0, F><<<grid(A->nblk), 128, 0, s>>>(A->vals, A->keys, A->nblk, rowexp, asl);
+  if (B->nblk)
+    k_slice<BS, S, 1, F><<<grid(B->nblk), 128, 0, s>>>(B->vals, B->keys, B->nblk, colexp, bsl);
+}
+
+// Slice counts with a compiled kernel: 1..8 for BF16, {2,3,4,6,8,12} for E4M3.
+inline bool spec_compiled(int fmt, int slices) {
+  if (fmt == 0) return slices >= 1 && slices <= 8;
+  return slices == 2 || slices == 3 || slices == 4 || slices == 6 || slices == 8 || slices == 12;
 }
 
 template <int BS>
 void launch_slices_s(bsm_matrix A, bsm_matrix B, const int *rowexp, const int *colexp,
-                     uint16_t *asl, uint16_t *bsl, int slices, cudaStream_t s) {
-  switch (slices) {
-    case 1: launch_slices<BS, 1>(A, B, rowexp, colexp, asl, bsl, s); break;
-    case 2: launch_slices<BS, 2>(A, B, rowexp, colexp, asl, bsl, s); break;
-    case 3: launch_slices<BS, 3>(A, B, rowexp, colexp, asl, bsl, s); break;
-    case 4: launch_slices<BS, 4>(A, B, rowexp, colexp, asl, bsl, s); break;
-    case 5: launch_slices<BS, 5>(A, B, rowexp, colexp, asl, bsl, s); break;
-    case 6: launch_slices<BS, 6>(A, B, rowexp, colexp, asl, bsl, s); break;
-    case 7: launch_slices<BS, 7>(A, B, rowexp, colexp, asl, bsl, s); break;
-    default: launch_slices<BS, 8>(A, B, rowexp, colexp, asl, bsl, s); break;
+                     uint8_t *asl, uint8_t *bsl, int fmt, int slices, cudaStream_t s) {
+#define BSM_SL(F, S)                                             \
+  if (fmt == F && slices == S) {                                 \
+    launch_slices<BS, S, F>(A, B, rowexp, colexp, asl, bsl, s); \
+    return;                                                      \
   }
+  BSM_SL(0, 1) BSM_SL(0, 2) BSM_SL(0, 3) BSM_SL(0, 4) BSM_SL(0, 5) BSM_SL(0, 6) BSM_SL(0, 7)
+  BSM_SL(0, 8)
+  if constexpr (BS == 32) {  // E4M3 needs K = 32 per instruction: one 32-wide block
+    BSM_SL(1, 2) BSM_SL(1, 3) BSM_SL(1, 4) BSM_SL(1, 6) BSM_SL(1, 8) BSM_SL(1, 12)
+  }
+#undef BSM_SL
 }
 
 __global__ void k_max_seg(const int32_t *__restrict__ seg, int64_t nc, int *__restrict__ out) {
@@ -309,16 +346,15 @@ struct __align__(16) Meta {
 static_assert(offsetof(Meta, ecol) % 16 == 0 && sizeof(Meta) % 16 == 0, "Meta alignment");
 constexpr int kMeta = 8;
 
-// sum_d acc_d 2^(7(S-1-d)) for 32-bit acc_d, returned as hi * 2^35 + lo: the
-// terms with shift < 35 are summed in lo (< 2^59.1), the rest in hi.
-template <int S>
+// sum_d acc_d 2^(B(S-1-d)) for 32-bit acc_d, returned as hi * 2^T + lo: the
+// terms with shift < T are summed in lo (< 2^59.1), the rest in hi.
+template <int S, int B, int T>
 __device__ __forceinline__ void combine_digits(const int32_t (&a)[S], int64_t &hi, int64_t &lo) {
   lo = 0;
   hi = 0;
 #pragma unroll
   for (int d = 0; d < S; d++) {
-    constexpr int T = 35;
-    const int sh = kBeta * (S - 1 - d);
+    const int sh = B * (S - 1 - d);
     if (sh < T)
       lo += (int64_t)a[d] << sh;
     else
@@ -326,11 +362,12 @@ __device__ __forceinline__ void combine_digits(const int32_t (&a)[S], int64_t &h
   }
 }
 
-// Correctly rounded (hi 2^35 + lo) 2^X as FP64; 64-bit path (branch-free
+// Correctly rounded (hi 2^T + lo) 2^X as FP64; 64-bit path (branch-free
 // rounding) when the value fits in an int64, 128-bit path otherwise.
+template <int T>
 __device__ __forceinline__ double split_to_double(int64_t hi, int64_t lo, int X) {
   if (hi > -(1ll << 27) && hi < (1ll << 27)) {
-    const int64_t v = (int64_t)((uint64_t)hi << 35) + lo;  // |v| < 2^62 + 2^59.1
+    const int64_t v = (int64_t)((uint64_t)hi << T) + lo;  // |v| < 2^(27+T) + 2^59.1
     if (v == 0) return 0.0;
     const uint64_t sign = (uint64_t)v & (1ull << 63);
     const uint64_t u = v < 0 ? (uint64_t)(-v) : (uint64_t)v;
@@ -349,7 +386,7 @@ __device__ __forceinline__ double split_to_double(int64_t hi, int64_t lo, int X)
     const double r = scalbn((double)mant, top - 52 + X);
     return sign ? -r : r;
   }
-  return fixed_to_double(((__int128)hi << 35) + (__int128)lo, X);
+  return fixed_to_double(((__int128)hi << T) + (__int128)lo, X);
 }
 
 constexpr int kTeamWarps = 8;                // warps per epilogue team (2 per lane quadrant)
@@ -358,12 +395,13 @@ constexpr int kEpiWarps = 2 * kTeamWarps;    // two teams
 constexpr int kProdWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
 constexpr int kThreads = (kEpiWarps + 2) * 32;
 
-template <int BS, int S>
+template <int BS, int S, int F>
 __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
-  using C = Cfg<BS, S>;
+  using C = Cfg<BS, S, F>;
   constexpr int DPG = C::DPG;
   constexpr int G = C::G;
-  constexpr uint32_t IDESC = idesc_bf16_f32(128, BS);
+  constexpr int BETA = Fmt<F>::BETA, TS = Fmt<F>::TSPLIT;
+  constexpr uint32_t IDESC = F == 0 ? idesc_bf16_f32(128, BS) : idesc_e4m3_f32(128, BS);
   constexpr int NCOLS = 2 * G * BS <= 32 ? 32 : (2 * G * BS <= 64 ? 64 : (2 * G * BS <= 128 ? 128 : 256));
   constexpr uint32_t BYTES = (uint32_t)S * C::SLICE;  // one operand's slices
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -508,7 +546,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
           stop = true;
           break;
         }
-        const uint16_t *asl = pd->asl, *bsl = pd->bsl;
+        const uint8_t *asl = pd->asl, *bsl = pd->bsl;
         const int64_t na = pd->na, nb = pd->nb, nt = pd->nt;
         for (int j = 0; j < nk; j++, it++) {
           const int32_t t = k0 + j;
@@ -537,9 +575,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
                 mbar_arrive(&full[st]);
               } else {
                 mbar_expect_tx(&full[st], 2 * BYTES);
-                bulk_g2s(sa + (DPG - 1) * C::SLICE, asl + (int64_t)aa * S * BS * BS, BYTES,
-                         &full[st]);
-                bulk_g2s(sb, bsl + (int64_t)bb * S * BS * BS, BYTES, &full[st]);
+                bulk_g2s(sa + (DPG - 1) * C::SLICE, asl + (int64_t)aa * BYTES, BYTES, &full[st]);
+                bulk_g2s(sb, bsl + (int64_t)bb * BYTES, BYTES, &full[st]);
               }
             }
           }
@@ -614,10 +651,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
               for (int t = 0; t < S; t++) {
                 if (t >= (g + 1) * DPG) break;  // K-blocks of group g: t < min(S, (g+1) DPG)
 #pragma unroll
-                for (int h = 0; h < BS / 16; h++) {
+                for (int h = 0; h < BS / Fmt<F>::KPI; h++) {
+                  // one instruction's K = two core matrices = 256 bytes
                   const uint64_t aoff = (uint64_t)(((DPG - 1 + g * DPG - t) * C::SLICE + h * 256) >> 4);
                   const uint64_t boff = (uint64_t)((t * C::SLICE + h * 256) >> 4);
-                  tc_mma_bf16(dt, ad0 + aoff, bd0 + boff, IDESC, (t | h) ? 1u : first);
+                  if (F == 0)
+                    tc_mma_bf16(dt, ad0 + aoff, bd0 + boff, IDESC, (t | h) ? 1u : first);
+                  else
+                    tc_mma_f8(dt, ad0 + aoff, bd0 + boff, IDESC, (t | h) ? 1u : first);
                 }
               }
             }
@@ -747,14 +788,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
                 for (int d = 0; d < S; d++)
                   dg[d] = x == 0 ? dv[d].x : x == 1 ? dv[d].y : x == 2 ? dv[d].z : dv[d].w;
                 int64_t hi, lo;
-                combine_digits<S>(dg, hi, lo);
+                combine_digits<S, BETA, TS>(dg, hi, lo);
                 int64_t *fp = fold + (rr * BS + c4 + x) * 2;
                 if (f + 1 > kFold) {
                   hi += fp[0];
                   lo += fp[1];
                 }
-                hi += lo >> 35;  // keep lo in [0, 2^35): hi 2^35 + lo unchanged
-                lo &= (1ll << 35) - 1;
+                hi += lo >> TS;  // keep lo in [0, 2^TS): hi 2^TS + lo unchanged
+                lo &= (1ll << TS) - 1;
                 fp[0] = hi;
                 fp[1] = lo;
               }
@@ -766,7 +807,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
       if (named_bar_or(bar_id, kTeam, !ok || abort_flag != 0)) break;
       double *cb = cvp + c * (int64_t)BS * BS;
       bool any = false;
-      constexpr int XS = kBeta * (S + 1);
+      constexpr int XS = BETA * (S + 1);
 #pragma unroll
       for (int i = 0; i < GRP; i++) {
         const int g4 = ttid + i * kTeam;
@@ -783,14 +824,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
 #pragma unroll
           for (int d = 0; d < S; d++) dg[d] = x == 0 ? dv[d].x : x == 1 ? dv[d].y : x == 2 ? dv[d].z : dv[d].w;
           int64_t hi, lo;
-          combine_digits<S>(dg, hi, lo);
+          combine_digits<S, BETA, TS>(dg, hi, lo);
           if (nfl > kFold) {
             const int64_t *fp = fold + (rr * BS + c4 + x) * 2;
             hi += fp[0];
             lo += fp[1];
           }
           const int fx = x == 0 ? fcol[i].x : x == 1 ? fcol[i].y : x == 2 ? fcol[i].z : fcol[i].w;
-          out[x] = split_to_double(hi, lo, erow[i] + fx - XS);
+          out[x] = split_to_double<TS>(hi, lo, erow[i] + fx - XS);
           any |= out[x] != 0.0;
         }
         double2 *dst = reinterpret_cast<double2 *>(cb + rr * BS + c4);
@@ -817,12 +858,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
 
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-template <int BS, int S>
+template <int BS, int S, int F>
 bsm_status launch_split(const SplitArgs &a, cudaStream_t s) {
-  using C = Cfg<BS, S>;
+  using C = Cfg<BS, S, F>;
   static bool attr = false;
   if (!attr) {
-    BSM_CUDA(cudaFuncSetAttribute(k_numeric_split<BS, S>,
+    BSM_CUDA(cudaFuncSetAttribute(k_numeric_split<BS, S, F>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     attr = true;
   }
@@ -834,33 +875,33 @@ bsm_status launch_split(const SplitArgs &a, cudaStream_t s) {
   if (grid < 1) return BSM_OK;
   if (!a.fold) return BSM_ERR_INVALID_ARG;  // sized by split_fold_bytes: grid <= SM count
   count_launch();
-  k_numeric_split<BS, S><<<(unsigned)grid, kThreads, C::SMEM, s>>>(a);
+  k_numeric_split<BS, S, F><<<(unsigned)grid, kThreads, C::SMEM, s>>>(a);
   return cuda_status(cudaGetLastError());
 }
 
 template <int BS>
-bsm_status launch_split_s(const SplitArgs &a, int slices, cudaStream_t s) {
-  switch (slices) {
-    case 1: return launch_split<BS, 1>(a, s);
-    case 2: return launch_split<BS, 2>(a, s);
-    case 3: return launch_split<BS, 3>(a, s);
-    case 4: return launch_split<BS, 4>(a, s);
-    case 5: return launch_split<BS, 5>(a, s);
-    case 6: return launch_split<BS, 6>(a, s);
-    case 7: return launch_split<BS, 7>(a, s);
-    case 8: return launch_split<BS, 8>(a, s);
+bsm_status launch_split_s(const SplitArgs &a, int fmt, int slices, cudaStream_t s) {
+#define BSM_LS(F, S) \
+  if (fmt == F && slices == S) return launch_split<BS, S, F>(a, s);
+  BSM_LS(0, 1) BSM_LS(0, 2) BSM_LS(0, 3) BSM_LS(0, 4) BSM_LS(0, 5) BSM_LS(0, 6) BSM_LS(0, 7)
+  BSM_LS(0, 8)
+  if constexpr (BS == 32) {
+    BSM_LS(1, 2) BSM_LS(1, 3) BSM_LS(1, 4) BSM_LS(1, 6) BSM_LS(1, 8) BSM_LS(1, 12)
   }
+#undef BSM_LS
   return BSM_ERR_INVALID_ARG;
 }
 
 }  // namespace
 
 // Largest group of k-products whose diagonal sums stay exact (< 2^22) in the
-// FP32 accumulator: d = 0 sums terms up to 2^14; d >= 1 at most (d + 3) 2^12
-// per inner element.
-int split_flush_group(int bs, int s) {
-  int maxel = (1 << 22) >> (2 * kBeta);                  // d = 0
-  int m2 = ((1 << 22) >> (2 * kBeta - 2)) / (s + 2);     // d = s - 1
+// FP32 accumulator: with digit base 2^B, d = 0 sums terms up to 2^(2B); d >= 1
+// at most (d + 3) 2^(2B-2) per inner element.
+int split_flush_group(int bs, int spec) {
+  const int beta = split_spec_fmt(spec) == 0 ? Fmt<0>::BETA : Fmt<1>::BETA;
+  const int s = split_spec_slices(spec);
+  int maxel = (1 << 22) >> (2 * beta);                  // d = 0
+  int m2 = ((1 << 22) >> (2 * beta - 2)) / (s + 2);     // d = s - 1
   if (m2 < maxel) maxel = m2;
   int g = maxel / bs;
   return g < 1 ? 1 : g;
@@ -873,29 +914,34 @@ size_t split_fold_bytes(int bs) {
   return (size_t)(sms > 0 ? sms : 1) * 2 * bs * bs * 2 * sizeof(int64_t);
 }
 
-bsm_status split_supported(int bs, int slices) {
+bsm_status split_supported(int bs, int spec) {
   if (bs != 16 && bs != 32) return BSM_ERR_UNSUPPORTED;
-  if (slices < 1 || slices > kMaxSlices) return BSM_ERR_INVALID_ARG;
+  const int fmt = split_spec_fmt(spec), slices = split_spec_slices(spec);
+  if (fmt == 1 && bs != 32) return BSM_ERR_UNSUPPORTED;  // one E4M3 instruction spans K = 32
+  if (fmt < 0 || fmt > 1) return BSM_ERR_INVALID_ARG;
+  if (slices < 1 || slices > (fmt ? Fmt<1>::MAXS : Fmt<0>::MAXS)) return BSM_ERR_INVALID_ARG;
+  if (!spec_compiled(fmt, slices)) return BSM_ERR_UNSUPPORTED;
   return BSM_OK;
 }
 
 // Buffers of the split form of one product: scale exponents of A's rows and
 // B's columns and the digit slices of A and B.  Fills the split fields of `d`;
 // the allocations are appended to `owned` for the caller to release.
-bsm_status split_alloc(bsm_matrix A, bsm_matrix B, int slices, ProdDesc &d,
+bsm_status split_alloc(bsm_matrix A, bsm_matrix B, int spec, ProdDesc &d,
                        std::vector<void *> &owned, cudaStream_t s) {
   const int bs = A->bs;
+  const size_t eb = split_spec_fmt(spec) == 0 ? 2 : 1, slices = split_spec_slices(spec);
   int *rowexp = nullptr, *colexp = nullptr;
-  uint16_t *asl = nullptr, *bsl = nullptr;
+  uint8_t *asl = nullptr, *bsl = nullptr;
   bsm_status st;
   if ((st = dev_alloc((void **)&rowexp, 4 * A->mb * bs, s)) != BSM_OK) return st;
   owned.push_back(rowexp);
   if ((st = dev_alloc((void **)&colexp, 4 * B->nb * bs, s)) != BSM_OK) return st;
   owned.push_back(colexp);
-  if ((st = dev_alloc((void **)&asl, (size_t)2 * slices * bs * bs * A->nblk, s)) != BSM_OK)
+  if ((st = dev_alloc((void **)&asl, eb * slices * bs * bs * A->nblk, s)) != BSM_OK)
     return st;
   owned.push_back(asl);
-  if ((st = dev_alloc((void **)&bsl, (size_t)2 * slices * bs * bs * B->nblk, s)) != BSM_OK)
+  if ((st = dev_alloc((void **)&bsl, eb * slices * bs * bs * B->nblk, s)) != BSM_OK)
     return st;
   owned.push_back(bsl);
   d.asl = asl;
@@ -907,8 +953,9 @@ bsm_status split_alloc(bsm_matrix A, bsm_matrix B, int slices, ProdDesc &d,
 
 // Computes the exponents and slices into the buffers of `d` (no allocation;
 // may be captured in a CUDA graph).
-bsm_status split_compute(bsm_matrix A, bsm_matrix B, int slices, const ProdDesc &d,
+bsm_status split_compute(bsm_matrix A, bsm_matrix B, int spec, const ProdDesc &d,
                          unsigned *errword, cudaStream_t s) {
+  const int fmt = split_spec_fmt(spec), slices = split_spec_slices(spec);
   const int bs = A->bs;
   int *rowexp = const_cast<int *>(d.rowexp), *colexp = const_cast<int *>(d.colexp);
   cudaMemsetAsync(rowexp, 0x80, 4 * A->mb * bs, s);  // 0x80808080: below any exponent
@@ -922,11 +969,11 @@ bsm_status split_compute(bsm_matrix A, bsm_matrix B, int slices, const ProdDesc 
     k_col_exp<<<grid_for(B->nblk * bs, 256), 256, 0, s>>>(B->vals, B->keys, B->nblk, bs, colexp,
                                                          errword);
   }
-  uint16_t *asl = const_cast<uint16_t *>(d.asl), *bsl = const_cast<uint16_t *>(d.bsl);
+  uint8_t *asl = const_cast<uint8_t *>(d.asl), *bsl = const_cast<uint8_t *>(d.bsl);
   if (bs == 16)
-    launch_slices_s<16>(A, B, rowexp, colexp, asl, bsl, slices, s);
+    launch_slices_s<16>(A, B, rowexp, colexp, asl, bsl, fmt, slices, s);
   else
-    launch_slices_s<32>(A, B, rowexp, colexp, asl, bsl, slices, s);
+    launch_slices_s<32>(A, B, rowexp, colexp, asl, bsl, fmt, slices, s);
   return cuda_status(cudaGetLastError());
 }
 
@@ -943,19 +990,20 @@ bsm_status split_prepare(bsm_matrix A, bsm_matrix B, int slices, unsigned *errwo
   return split_compute(A, B, slices, d, errword, s);
 }
 
-bsm_status split_launch(int bs, int slices, const ProdDesc *prods_dev, const uint64_t *items,
+bsm_status split_launch(int bs, int spec, const ProdDesc *prods_dev, const uint64_t *items,
                         int64_t nitems, unsigned long long *work, unsigned *errword,
                         int64_t *fold, cudaStream_t s, int chunk) {
+  const int fmt = split_spec_fmt(spec), slices = split_spec_slices(spec);
   SplitArgs a;
   a.fold = fold;
   a.chunk = chunk < 1 ? 1 : (chunk > kChunk ? kChunk : chunk);
   a.prods = prods_dev;
   a.items = items;
   a.nitems = nitems;
-  a.flushk = split_flush_group(bs, slices);
+  a.flushk = split_flush_group(bs, spec);
   a.err = errword;
   a.work = work;
-  return bs == 16 ? launch_split_s<16>(a, slices, s) : launch_split_s<32>(a, slices, s);
+  return bs == 16 ? launch_split_s<16>(a, fmt, slices, s) : launch_split_s<32>(a, fmt, slices, s);
 }
 
 ProdDesc make_desc(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, double *cvals,

@@ -263,7 +263,8 @@ extern "C" bsm_status bsm_add(bsm_matrix A, bsm_matrix B, bsm_matrix *out, void 
 namespace {
 
 // flag[t f^2 + q] = 1 if sub-block q (Morton index) of block t is kept: it
-// has an entry != 0, or (keep_all) it lies inside the matrix.  One warp per
+// has an entry != 0 (mode 0), it lies inside the matrix (mode 1), or it has an
+// entry != 0 and lies on or above the diagonal (mode 2).  One warp per
 // sub-block.
 __global__ void k_split_flags(const double *__restrict__ vals, const uint64_t *__restrict__ keys,
                               int64_t n, int bs, int nbs, int keep_all, int64_t mb, int64_t nb,
@@ -275,19 +276,17 @@ __global__ void k_split_flags(const double *__restrict__ vals, const uint64_t *_
   const int64_t t = w / f2;
   const int q = (int)(w % f2);
   const int i = (int)morton_compact((uint64_t)q >> 1), j = (int)morton_compact((uint64_t)q);
-  if (keep_all) {
-    if (lane == 0) {
-      const int64_t I = (int64_t)morton_compact(keys[t] >> 1) * f + i;
-      const int64_t J = (int64_t)morton_compact(keys[t]) * f + j;
-      flag[w] = I < mb && J < nb;
-    }
+  const int64_t I = (int64_t)morton_compact(keys[t] >> 1) * f + i;
+  const int64_t J = (int64_t)morton_compact(keys[t]) * f + j;
+  if (keep_all == 1) {
+    if (lane == 0) flag[w] = I < mb && J < nb;
     return;
   }
   const double *b = vals + t * bs * bs + (int64_t)(i * nbs) * bs + j * nbs;
   bool any = false;
   for (int e = lane; e < nbs * nbs; e += 32) any |= b[(e / nbs) * bs + e % nbs] != 0.0;
   any = __any_sync(0xffffffffu, any);
-  if (lane == 0) flag[w] = any;
+  if (lane == 0) flag[w] = any && (keep_all != 2 || I <= J);
 }
 
 __global__ void k_split_keys(const uint64_t *__restrict__ keys, int64_t n, int f,
@@ -350,10 +349,12 @@ inline unsigned grid_blocks(int64_t n) { return (unsigned)(n < 152 * 16 ? n : 15
 
 }  // namespace
 
-// Core of re-blocking.  keep_all: splitting keeps every sub-block inside the
-// matrix (the structure then depends only on A's structure); map_out, if not
-// NULL, receives the index map that reblock_refresh needs (caller frees).
-bsm_status reblock_impl(bsm_matrix A, int bs, bool keep_all, bsm_matrix *out, int32_t **map_out,
+// Core of re-blocking.  keep_all (splitting only): 0 drops all-zero
+// sub-blocks; 1 keeps every sub-block inside the matrix (the structure then
+// depends only on A's structure); 2 also drops sub-blocks below the diagonal.
+// map_out, if not NULL, receives the index map that reblock_refresh needs
+// (caller frees).
+bsm_status reblock_impl(bsm_matrix A, int bs, int keep_all, bsm_matrix *out, int32_t **map_out,
                         cudaStream_t s) {
   *out = nullptr;
   if (map_out) *map_out = nullptr;
@@ -386,8 +387,8 @@ bsm_status reblock_impl(bsm_matrix A, int bs, bool keep_all, bsm_matrix *out, in
     if (st == BSM_OK && (st = dev_alloc((void **)&flag, 4 * m, s)) == BSM_OK &&
         (st = dev_alloc((void **)&pos, 4 * m, s)) == BSM_OK) {
       count_launch();
-      k_split_flags<<<grid_for(m * 32, 256), 256, 0, s>>>(A->vals, A->keys, n, obs, bs,
-                                                          keep_all ? 1 : 0, mb, nb, flag);
+      k_split_flags<<<grid_for(m * 32, 256), 256, 0, s>>>(A->vals, A->keys, n, obs, bs, keep_all,
+                                                          mb, nb, flag);
       st = scan_exclusive_i32(flag, pos, m, s);
     }
     if (st == BSM_OK) {
@@ -473,5 +474,5 @@ extern "C" bsm_status bsm_reblock(bsm_matrix A, int bs, bsm_matrix *out, void *s
   *out = nullptr;
   if (!A) return BSM_ERR_INVALID_ARG;
   if (bs != 16 && bs != 32 && bs != 64) return BSM_ERR_BLOCKSIZE;
-  return reblock_impl(A, bs, false, out, nullptr, (cudaStream_t)stream);
+  return reblock_impl(A, bs, 0, out, nullptr, (cudaStream_t)stream);
 }

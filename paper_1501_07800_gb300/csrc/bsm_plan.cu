@@ -239,7 +239,7 @@ bsm_status create_at_bs(int n, const bsm_matrix *A, const bsm_matrix *B, const b
         return BSM_OK;
       }
     int32_t *map = nullptr;
-    BSM_TRY(reblock_impl(X, cb, true, R, &map, cs));
+    BSM_TRY(reblock_impl(X, cb, 1, R, &map, cs));
     W->rsrc.push_back(X);
     W->rops.push_back(*R);
     W->rmap.push_back(map);
@@ -454,7 +454,7 @@ extern "C" bsm_status bsm_plan_results(bsm_plan P, bsm_matrix *C, void *stream) 
     // re-cut to the operands' block size (all-zero blocks dropped)
     for (int i = 0; i < P->n && st == BSM_OK; i++) {
       bsm_matrix R = nullptr;
-      st = reblock_impl(C[i], P->user_bs, false, &R, nullptr, s);
+      st = reblock_impl(C[i], P->user_bs, 0, &R, nullptr, s);
       bsm_destroy(C[i]);
       C[i] = R;
     }

@@ -116,7 +116,7 @@ static bsm_status sym_full(bsm_matrix U, bsm_matrix *out, cudaStream_t s) {
 
 static bsm_status sym_opts(const bsm_mult_opts *opts, int bs, int *prec, int *slices) {
   BSM_TRY(check_opts(opts, prec, slices, 0));
-  if (*prec != BSM_FP64) BSM_TRY(split_supported(bs == 64 ? 32 : bs, *slices));
+  if (*prec != BSM_FP64) BSM_TRY(split_supported(split_width(*prec, bs), *slices));
   return BSM_OK;
 }
 

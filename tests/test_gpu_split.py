@@ -205,3 +205,86 @@ def test_split_bs64_symmetric_square():
     E = oracle.sym_square(U)
     assert_same_structure(C, E)
     assert relerr(C.vals, E.vals) < TOL_SPLIT
+
+
+# ------------------------------------------------------------ E4M3 digits
+FP8_SLICES = [2, 3, 4, 6, 8, 12]
+
+
+def fp8_product(A, B, slices=0):
+    return from_bsm(bsm.bsm_multiply(to_bsm(A), to_bsm(B), prec=bsm.BSM_SPLIT_FP8, slices=slices))
+
+
+@pytest.mark.parametrize("slices", FP8_SLICES)
+def test_fp8_integers_exact(slices):
+    """|entries| <= 8 need one base-16 digit: every product and sum is exact."""
+    A = synth.random_blocks(40 * 32 + 5, 32, 0.3, 600, dist="int8")
+    B = synth.random_blocks(40 * 32 + 5, 32, 0.3, 601, dist="int8")
+    C = fp8_product(A, B, slices)
+    E = oracle.multiply(A, B).C
+    assert_same_structure(C, E)
+    assert np.array_equal(C.vals, E.vals)
+
+
+def test_fp8_error_decreases_with_slices():
+    A = synth.random_blocks(1024, 32, 0.1, 602)
+    B = synth.random_blocks(1024, 32, 0.1, 603)
+    E = oracle.multiply(A, B).C
+    errs = []
+    for s in FP8_SLICES:
+        C = fp8_product(A, B, s)
+        assert_same_structure(C, E)
+        errs.append(relerr(C.vals, E.vals))
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[FP8_SLICES.index(6)] < 1e-5     # 24-bit fixed point per row / column
+    assert errs[-1] < TOL_SPLIT                # 48 bits
+
+
+@pytest.mark.parametrize("bs", [16, 64])
+def test_fp8_other_widths_equal_bs32_recut(bs):
+    """E4M3 runs on 32-wide blocks; other widths are re-cut exactly, so the
+    result equals the bs-32 product of the same matrices, re-cut."""
+    A = synth.random_blocks(37 * bs + 9, bs, 0.1, 610 + bs)
+    B = synth.random_blocks(37 * bs + 9, bs, 0.1, 611 + bs)
+    C = fp8_product(A, B, 12)
+    a32 = synth.from_dense(A.to_dense(), 32)
+    b32 = synth.from_dense(B.to_dense(), 32)
+    R = from_bsm(bsm.bsm_reblock(bsm.bsm_multiply(to_bsm(a32), to_bsm(b32),
+                                                  prec=bsm.BSM_SPLIT_FP8, slices=12), bs))
+    assert_same_structure(C, R)
+    assert np.array_equal(C.vals, R.vals)
+    E = oracle.multiply(A, B).C
+    assert_same_structure(C, E)
+    assert relerr(C.vals, E.vals) < TOL_SPLIT
+
+
+@pytest.mark.parametrize("bs", [16, 32])
+def test_fp8_symmetric_square(bs):
+    A = synth.decay(240, bs, 620 + bs)
+    U = synth.upper_blocks(A)
+    C = from_bsm(bsm.bsm_sym_square(to_bsm(U), prec=bsm.BSM_SPLIT_FP8, slices=12))
+    E = oracle.sym_square(U)
+    assert_same_structure(C, E)
+    assert relerr(C.vals, E.vals) < TOL_SPLIT
+
+
+def test_fp8_batched_equals_single():
+    pairs = synth.batched(5, 630, nmin=256, nmax=2000, dmin=0.02, dmax=0.2)
+    As = [to_bsm(a) for a, _ in pairs]
+    Bs = [to_bsm(b) for _, b in pairs]
+    got = bsm.bsm_multiply_batched(As, Bs, prec=bsm.BSM_SPLIT_FP8, slices=8)
+    for ga, gb, c in zip(As, Bs, got):
+        one = from_bsm(bsm.bsm_multiply(ga, gb, prec=bsm.BSM_SPLIT_FP8, slices=8))
+        g = from_bsm(c)
+        assert_same_structure(g, one)
+        assert np.array_equal(g.vals, one.vals)
+
+
+def test_fp8_rejects_uncompiled_slice_counts():
+    A = to_bsm(synth.random_blocks(256, 32, 0.3, 640))
+    with pytest.raises(bsm.BsmError) as e:
+        bsm.bsm_multiply(A, A, prec=bsm.BSM_SPLIT_FP8, slices=5)
+    assert e.value.name == "BSM_ERR_UNSUPPORTED"
+    with pytest.raises(bsm.BsmError) as e:
+        bsm.bsm_multiply(A, A, prec=bsm.BSM_SPLIT_FP8, slices=13)
+    assert e.value.name == "BSM_ERR_INVALID_ARG"
