@@ -537,6 +537,8 @@ def run_decay(args):
     fp64_peak = peaks["bf16_tflops"] * FP64_NOMINAL_RATIO
     slices = [int(x) for x in args.slices.split(",") if x]
     legs = [(f"split_bf16x{k}", False, bsm.BSM_SPLIT_BF16, k, args.steps) for k in slices]
+    legs += [(f"split_fp8x{k}", False, bsm.BSM_SPLIT_FP8, int(k), args.steps)
+             for k in args.fp8_slices.split(",") if k]
     legs.append(("fp64", False, bsm.BSM_FP64, 0, 1))
     if args.sym:
         legs += [(f"sym_square_split_bf16x{slices[-1]}", True, bsm.BSM_SPLIT_BF16, slices[-1],
@@ -693,6 +695,7 @@ def main():
     ap.add_argument("--points", type=int, default=20000, help="decay workload: number of points")
     ap.add_argument("--bs", type=int, default=32, help="decay workload: leaf block size")
     ap.add_argument("--slices", default="7", help="decay workload: split slice counts, e.g. 3,5,7")
+    ap.add_argument("--fp8-slices", default="", help="decay workload: FP8 split slice counts")
     ap.add_argument("--sym", action="store_true",
                     help="decay workload: also the symmetric square from the upper triangle")
     ap.add_argument("--n", type=int, default=None, help="matrix side (profiling runs only)")

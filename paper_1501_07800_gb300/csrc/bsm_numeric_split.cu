@@ -1,4 +1,7 @@
-// Split-precision numeric phase: FP64 block products on BF16 tensor cores.
+// Split-precision numeric phase: FP64 block products on BF16 or FP8 (E4M3)
+// tensor cores.  Written below for the BF16 form (digit base 2^7); the E4M3
+// form is the same with base 2^4 (|a_0| <= 16, |a_i>0| <= 8), kind::f8f6f4
+// MMAs with K = 32 per instruction, and 32-wide blocks only.
 //
 // Each FP64 entry is written exactly as a sum of s BF16-representable digits
 // (an error-free splitting in the manner of Ozaki, Ogita, Oishi and Rump,
@@ -14,7 +17,8 @@
 // accumulator as long as it stays below 2^22 in magnitude (and below 2^24 for
 // every partial sum); the k-products of a C block are therefore accumulated in
 // groups ("flushes") of at most `flushk` leaf blocks, each flush moved out of
-// TMEM into 32-bit integer registers.  After the last flush the diagonals are
+// TMEM into 32-bit integer sums (folded into 64-bit pairs every 511 flushes
+// for very long product lists).  After the last flush the diagonals are
 // combined in 128-bit integer arithmetic and rounded once to FP64.  No FP64
 // arithmetic is done per k-product: on GB300 the FP64 pipe is ~1 TFLOP/s,
 // three orders of magnitude below the BF16 tensor rate.
@@ -334,16 +338,16 @@ constexpr int kFold = 511;
 // The exponent arrays are read with 16-byte vector loads: keep them first in
 // a 16-byte aligned struct whose size is a multiple of 16.
 struct __align__(16) Meta {
-  int32_t erow[64];  // row scale exponents of the C block (A rows)
-  int32_t ecol[64];  // column scale exponents (B columns)
-  int64_t c;         // C block index within its product
+  int64_t c;            // C block index within its product
   uint64_t key;
-  double *cv;        // the product's C blocks
-  int32_t *nz;       // the product's nonzero flags
+  double *cv;           // the product's C blocks
+  int32_t *nz;          // the product's nonzero flags
+  const int *rowexp;    // the product's row / column scale exponents
+  const int *colexp;
   int32_t nk;
   int32_t pad[3];
 };
-static_assert(offsetof(Meta, ecol) % 16 == 0 && sizeof(Meta) % 16 == 0, "Meta alignment");
+static_assert(sizeof(Meta) % 16 == 0, "Meta alignment");
 constexpr int kMeta = 8;
 
 // sum_d acc_d 2^(B(S-1-d)) for 32-bit acc_d, returned as hi * 2^T + lo: the
@@ -451,16 +455,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
     // --------------------------------------------------------- producer warp
     // Claims chunks of kChunk consecutive C blocks (Morton order) from a
     // global counter; the chunk's descriptors and its contiguous range of
-    // block products are loaded 32 at a time by the whole warp, the scale
-    // exponents of the next C block one step ahead.  Lane 0 does the barrier
-    // work and issues the copies.  Two sentinel descriptors (nk = -1) end the
-    // consumers.
+    // block products are loaded 32 at a time by the whole warp.  Lane 0 does
+    // the barrier work and issues the copies.  Two sentinel descriptors
+    // (nk = -1) end the consumers.  The epilogue loads the scale exponents
+    // itself.
     uint32_t it = 0, q = 0;
     bool pend[C::NST] = {};
     uint32_t ppar[C::NST] = {};
     bool stop = false;
-    auto put_meta = [&](int64_t c, uint64_t key, int nk, double *cv, int32_t *nz,
-                        const int (&er)[BS / 16], const int (&ec)[BS / 16]) -> bool {
+    auto put_meta = [&](int64_t c, uint64_t key, int nk, const ProdDesc *pd) -> bool {
       const int m = q % kMeta;
       int okw = 1;
       if (lane == 0) {
@@ -468,40 +471,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         if (!okw) {
           set_err(P.err, DERR_TIMEOUT);
           abort_flag = 1;
-        }
-      }
-      okw = __shfl_sync(0xffffffffu, okw, 0);
-      if (okw) {
-#pragma unroll
-        for (int x = 0; x < BS / 16; x++) {
-          const int idx = lane + 32 * x;  // lanes 0..BS-1 hold row / column values
-          if (idx < BS) {
-            meta[m].erow[idx] = er[x];
-            meta[m].ecol[idx] = ec[x];
-          }
-        }
-        __syncwarp();
-        if (lane == 0) {
+        } else {
           meta[m].c = c;
           meta[m].key = key;
-          meta[m].cv = cv;
-          meta[m].nz = nz;
+          meta[m].cv = pd ? pd->cv : nullptr;
+          meta[m].nz = pd ? pd->nz : nullptr;
+          meta[m].rowexp = pd ? pd->rowexp : nullptr;
+          meta[m].colexp = pd ? pd->colexp : nullptr;
           meta[m].nk = nk;
           mbar_arrive(&meta_full[m]);  // release: the descriptor is visible
         }
       }
+      okw = __shfl_sync(0xffffffffu, okw, 0);
       q++;
       return okw != 0;
-    };
-    auto load_exps = [&](const ProdDesc *pd, uint64_t key, int (&er)[BS / 16],
-                         int (&ec)[BS / 16]) {
-      const int64_t I = morton_compact(key >> 1), J = morton_compact(key);
-#pragma unroll
-      for (int x = 0; x < BS / 16; x++) {
-        const int idx = lane + 32 * x;
-        er[x] = idx < BS ? pd->rowexp[I * BS + idx] : 0;
-        ec[x] = idx < BS ? pd->colexp[J * BS + idx] : 0;
-      }
     };
     // window of 32 consecutive products (ta, tb) of one product table entry
     int wp = -1;
@@ -530,8 +513,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         s1 = pd->seg[ci + 1];
         key = pd->ckeys[ci];
       }
-      int er[BS / 16], ec[BS / 16], ern[BS / 16], ecn[BS / 16];
-      load_exps(&P.prods[__shfl_sync(0xffffffffu, pi, 0)], __shfl_sync(0xffffffffu, key, 0), er, ec);
       for (int i = 0; i < n && !stop; i++) {
         const int p = __shfl_sync(0xffffffffu, pi, i);
         const ProdDesc *pd = &P.prods[p];
@@ -539,10 +520,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         const uint64_t kk = __shfl_sync(0xffffffffu, key, i);
         const int32_t k0 = __shfl_sync(0xffffffffu, s0, i);
         const int32_t nk = __shfl_sync(0xffffffffu, s1, i) - k0;
-        if (i + 1 < n)
-          load_exps(&P.prods[__shfl_sync(0xffffffffu, pi, i + 1)],
-                    __shfl_sync(0xffffffffu, key, i + 1), ern, ecn);
-        if (!put_meta(c, kk, nk, pd->cv, pd->nz, er, ec)) {
+        if (!put_meta(c, kk, nk, pd)) {
           stop = true;
           break;
         }
@@ -585,18 +563,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
             break;
           }
         }
-#pragma unroll
-        for (int x = 0; x < BS / 16; x++) {
-          er[x] = ern[x];
-          ec[x] = ecn[x];
-        }
       }
     }
     // two end markers: one for the MMA thread and each epilogue team
     if (!stop) {
-      int z[BS / 16] = {};
-      put_meta(-1, 0, -1, nullptr, nullptr, z, z);
-      put_meta(-1, 0, -1, nullptr, nullptr, z, z);
+      put_meta(-1, 0, -1, nullptr);
+      put_meta(-1, 0, -1, nullptr);
     }
     // copies still in flight must land before the CTA exits
     if (lane == 0)
@@ -705,18 +677,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
       const int64_t c = meta[m].c;
       double *const cvp = meta[m].cv;
       int32_t *const nzp = meta[m].nz;
+      const uint64_t ckey = meta[m].key;
+      const int *const rowexp = meta[m].rowexp, *const colexp = meta[m].colexp;
+      mbar_arrive(&meta_empty[m]);
       if (nk < 0) break;  // end marker
       // scale exponents of this thread's output elements (thread handles
-      // columns 4*(g4 % (BS/4)) .. +3 of row g4 / (BS/4), g4 = ttid + i kTeam)
+      // columns 4*(g4 % (BS/4)) .. +3 of row g4 / (BS/4), g4 = ttid + i kTeam),
+      // loaded here so that their latency hides behind the first flush
+      const int64_t crow = (int64_t)morton_compact(ckey >> 1) * BS;
+      const int64_t ccol = (int64_t)morton_compact(ckey) * BS;
       int erow[GRP];
       int4 fcol[GRP];
 #pragma unroll
       for (int i = 0; i < GRP; i++) {
         const int g4 = min(ttid + i * kTeam, NG4 - 1);
-        erow[i] = meta[m].erow[g4 / (BS / 4)];
-        fcol[i] = *reinterpret_cast<const int4 *>(&meta[m].ecol[(g4 % (BS / 4)) * 4]);
+        erow[i] = rowexp[crow + g4 / (BS / 4)];
+        fcol[i] = *reinterpret_cast<const int4 *>(colexp + ccol + (g4 % (BS / 4)) * 4);
       }
-      mbar_arrive(&meta_empty[m]);
       const int nfl = (nk + P.flushk - 1) / P.flushk;
       int64_t *const fold = P.fold + ((int64_t)blockIdx.x * 2 + team) * (BS * BS * 2);
       bool ok = true;
