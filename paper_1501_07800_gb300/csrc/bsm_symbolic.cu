@@ -74,29 +74,39 @@ __device__ __forceinline__ unsigned pair_qmask(const UpperView &u, int64_t p, un
 }
 
 // Per pair: child counts of the quadrants in qmask; the level's exact total
-// is accumulated in 64 bits (one atomic per warp).
+// is accumulated in 64 bits: per thread over a grid-stride loop, per block in
+// shared memory, one atomic per block.
 __global__ void k_sym_count(const int32_t *__restrict__ pa, const int32_t *__restrict__ pb,
                             int64_t np, LevelView va, LevelView vb, unsigned qmask, UpperView up,
                             int4 *__restrict__ cnt, unsigned long long *__restrict__ total) {
-  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int t = 0;
-  if (p < np) {
+  __shared__ unsigned long long wsum[32];
+  unsigned long long mine = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= np; p += stride) {
+    if (p == np) {
+      cnt[p] = make_int4(0, 0, 0, 0);  // sentinel: the exclusive scan then ends with the total
+      continue;
+    }
     unsigned ma, mb;
     int32_t ca, cb;
     node_info(va, pa[p], ma, ca);
     node_info(vb, pb[p], mb, cb);
-    qmask = pair_qmask(up, p, qmask);
-    int4 c = make_int4((qmask & 1u) ? quad_count(ma, mb, 0, 0) : 0,
-                       (qmask & 2u) ? quad_count(ma, mb, 0, 1) : 0,
-                       (qmask & 4u) ? quad_count(ma, mb, 1, 0) : 0,
-                       (qmask & 8u) ? quad_count(ma, mb, 1, 1) : 0);
+    const unsigned qm = pair_qmask(up, p, qmask);
+    int4 c = make_int4((qm & 1u) ? quad_count(ma, mb, 0, 0) : 0,
+                       (qm & 2u) ? quad_count(ma, mb, 0, 1) : 0,
+                       (qm & 4u) ? quad_count(ma, mb, 1, 0) : 0,
+                       (qm & 8u) ? quad_count(ma, mb, 1, 1) : 0);
     cnt[p] = c;
-    t = c.x + c.y + c.z + c.w;
-  } else if (p == np) {
-    cnt[p] = make_int4(0, 0, 0, 0);  // sentinel: the exclusive scan then ends with the total
+    mine += (unsigned)(c.x + c.y + c.z + c.w);
   }
-  unsigned long long w = __reduce_add_sync(0xffffffffu, (unsigned)t);
-  if ((threadIdx.x & 31) == 0 && w) atomicAdd(total, w);
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) b += wsum[w];
+    if (b) atomicAdd(total, b);
+  }
 }
 
 __device__ __forceinline__ int q_of(const int4 &v, int q) {
@@ -303,8 +313,14 @@ struct Expander {
     cudaMemsetAsync(tot, 0, 8, s);
     const UpperView up{(upper && L.h - 1 >= upper - 1) ? L.sck : nullptr, L.pseg, L.soff};
     count_launch();
-    k_sym_count<<<grid_for(L.np + 1, 256), 256, 0, s>>>(L.pa, L.pb, L.np, va, vb, qmask, up, P,
-                                                         tot);
+    {
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const int64_t want = (L.np + 1 + 255) / 256, cap = (int64_t)(sms > 0 ? sms : 1) * 16;
+      k_sym_count<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(L.pa, L.pb, L.np, va, vb,
+                                                                        qmask, up, P, tot);
+    }
     unsigned long long *ht = (unsigned long long *)host_scratch().get(16);
     if (!ht) st = BSM_ERR_OOM;
     if (st == BSM_OK) {
