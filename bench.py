@@ -234,7 +234,18 @@ def run_gpu(args):
 
     n, bs, p = WORKLOAD["n"], WORKLOAD["bs"], WORKLOAD["p"]
     t0 = time.time()
-    A, B = workload(rank, n, bs, p)
+    # replicas: one product per rank (weak scaling); --shard: one product
+    # split by Morton ranges of C over the ranks (strong scaling)
+    A, B = workload(0 if args.shard else rank, n, bs, p)
+    key_range = None
+    if args.shard:
+        from paper_1501_07800_gb300 import shard as sh
+        L = sh.depth(-(-n // bs))
+        key_range = sh.balanced_ranges(A.brow, A.bcol, B.brow, B.bcol, world, L)[rank]
+        am, bm = sh.shard_operands(A.brow, A.bcol, B.brow, B.bcol, *key_range, L)
+        A = synth.BlockCOO(n, n, bs, A.brow[am], A.bcol[am], A.vals[am])
+        B = synth.BlockCOO(n, n, bs, B.brow[bm], B.bcol[bm], B.vals[bm])
+        args.no_split = args.no_e2e = args.no_batched = True
     log(f"[rank {rank}] generated A {A.nblk} blocks, B {B.nblk} blocks in {time.time() - t0:.1f} s")
     ga = bsm.bsm_build(n, n, bs, torch.from_numpy(A.brow).to(dev), torch.from_numpy(A.bcol).to(dev),
                        torch.from_numpy(A.vals).to(dev))
@@ -244,8 +255,14 @@ def run_gpu(args):
 
     bsm.bsm_set_timing(True)
     prec = bsm.BSM_SPLIT_BF16 if args.mode == "split" else bsm.BSM_FP64
+
+    def product():
+        if key_range is None:
+            return bsm.bsm_multiply(ga, gb, prec=prec)
+        return bsm.bsm_multiply_range(ga, gb, key_range[0], key_range[1], prec=prec)
+
     for _ in range(args.warmup):
-        C = bsm.bsm_multiply(ga, gb, prec=prec)
+        C = product()
         del C
     torch.cuda.synchronize()
     _, triples, nc_sym = bsm.bsm_last_stats()
@@ -259,7 +276,7 @@ def run_gpu(args):
     numeric_ms, launches = [], 0
     for i in range(args.steps):
         ev[i][0].record(stream)
-        C = bsm.bsm_multiply(ga, gb, prec=prec)
+        C = product()
         ev[i][1].record(stream)
         ms, nl = bsm.bsm_last_phase_ms()
         numeric_ms.append(ms[1])
@@ -298,8 +315,10 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "bf16x-split",
-                "data": "synthetic", "config": dict(WORKLOAD, parallelism=f"replicas{world}"),
+                "scaling": "strong" if args.shard else "weak", "vs_baseline": None,
+                "dtype": "f64" if prec == 0 else "bf16x-split", "data": "synthetic",
+                "config": dict(WORKLOAD, parallelism=(f"C Morton-range shards x{world}"
+                                                      if args.shard else f"replicas{world}")),
                 "triples": triples, "c_blocks": nblk_c, "c_blocks_symbolic": nc_sym,
                 "phase_ms_last": [float(x) for x in bsm.bsm_last_phase_ms()[0]],
                 "roofline": roofline, "gpu_launches": launches, "clocks": clk}
@@ -698,6 +717,8 @@ def main():
     ap.add_argument("--fp8-slices", default="", help="decay workload: FP8 split slice counts")
     ap.add_argument("--sym", action="store_true",
                     help="decay workload: also the symmetric square from the upper triangle")
+    ap.add_argument("--shard", action="store_true",
+                    help="split one product over the ranks by Morton ranges of C")
     ap.add_argument("--n", type=int, default=None, help="matrix side (profiling runs only)")
     ap.add_argument("--p", type=float, default=None, help="block density (profiling runs only)")
     args = ap.parse_args()

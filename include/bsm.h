@@ -141,6 +141,20 @@ bsm_status bsm_multiply(bsm_matrix A, bsm_matrix B, bsm_matrix *C, const bsm_mul
                         void *stream);
 
 /*
+ * bsm_multiply_range -- the C blocks of C = A*B whose Morton keys lie in
+ * [key_lo, key_hi) (key of block (I, J): bit 2b+1 = bit b of I, bit 2b = bit
+ * b of J).  Contiguous key ranges are quadtree subtrees and unions of them, so
+ * disjoint ranges partition C with no block computed twice: the shards of a
+ * product split over several GPUs.  The symbolic phase prunes every C node
+ * outside the range.  Blocks are computed exactly as by bsm_multiply (same
+ * values bit for bit); C has the full product's dimensions.
+ * Errors: as bsm_multiply; INVALID_ARG if key_hi <= key_lo; UNSUPPORTED for a
+ * split mode that re-cuts to wider blocks (E4M3 with bs 16).
+ */
+bsm_status bsm_multiply_range(bsm_matrix A, bsm_matrix B, uint64_t key_lo, uint64_t key_hi,
+                              bsm_matrix *C, const bsm_mult_opts *opts, void *stream);
+
+/*
  * bsm_transpose -- T = A^T as a new handle (keys with row and column swapped,
  * every block transposed; Sec. 3.2 transposed task types).
  *   A    input handle (unchanged)

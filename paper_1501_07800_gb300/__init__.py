@@ -38,6 +38,7 @@ _PROTOS = {
     "bsm_build": (_I32, [_I64, _I64, _I32, _I64, _P, _P, _P, _I32, _P, _P]),
     "bsm_multiply": (_I32, [_P, _P, _P, _P, _P]),
     "bsm_transpose": (_I32, [_P, _P, _P]),
+    "bsm_multiply_range": (_I32, [_P, _P, ctypes.c_uint64, ctypes.c_uint64, _P, _P, _P]),
     "bsm_add": (_I32, [_P, _P, _P, _P]),
     "bsm_sym_square": (_I32, [_P, _P, _P, _P]),
     "bsm_syrk": (_I32, [_P, _I32, _P, _P, _P]),
@@ -188,6 +189,16 @@ def bsm_multiply(A: Matrix, B: Matrix, prec: int = BSM_FP64, slices: int = 0,
     code = lib.bsm_multiply(A.handle, B.handle, ctypes.byref(out), _opts(prec, slices, flags),
                             _stream_ptr(stream))
     _check(code, "bsm_multiply")
+    return Matrix(out.value)
+
+
+def bsm_multiply_range(A: Matrix, B: Matrix, key_lo: int, key_hi: int, prec: int = BSM_FP64,
+                       slices: int = 0, stream=None) -> Matrix:
+    """The C blocks of A*B with Morton keys in [key_lo, key_hi)."""
+    out = ctypes.c_void_p()
+    _check(load().bsm_multiply_range(A.handle, B.handle, int(key_lo), int(key_hi),
+                                     ctypes.byref(out), _opts(prec, slices), _stream_ptr(stream)),
+           "bsm_multiply_range")
     return Matrix(out.value)
 
 

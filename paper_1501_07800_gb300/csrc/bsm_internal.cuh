@@ -129,8 +129,10 @@ bsm_status symbolic_multiply(bsm_matrix A, bsm_matrix B, SymbolicResult *out, cu
 // heights >= k - 1 (k = 1: C blocks with I <= J, for symmetric results; k = 2:
 // blocks whose parent node is on or above the diagonal).
 using LeafSink = std::function<bsm_status(SymbolicResult &)>;
+// [key_lo, key_hi): only C blocks whose Morton keys lie in it (key_hi == 0: all).
 bsm_status symbolic_chunks(bsm_matrix A, bsm_matrix B, const LeafSink &sink, int64_t *tasks,
-                           int *H, int *nchunks, cudaStream_t s, int64_t budget, int upper = 0);
+                           int *H, int *nchunks, cudaStream_t s, int64_t budget, int upper = 0,
+                           uint64_t key_lo = 0, uint64_t key_hi = 0);
 void free_symbolic(SymbolicResult *r, cudaStream_t s);
 
 // ----------------------------------------------------------- numeric phase
@@ -190,7 +192,8 @@ bsm_status check_pair(bsm_matrix A, bsm_matrix B);
 // at block size 64 run at 32 on re-cut operands (the split result does not
 // depend on the leaf size) and merge C back.
 bsm_status multiply_one(bsm_matrix A, bsm_matrix B, int prec, int slices, cudaStream_t s,
-                        bsm_matrix *out, bool upper = false);
+                        bsm_matrix *out, bool upper = false, uint64_t key_lo = 0,
+                        uint64_t key_hi = 0);
 // dst[t] = src[idx[t] & 0x7FFFFFFF], transposed when bit 31 of idx[t] is set
 // (bsm_ops.cu).
 void launch_gather_blocks_t(const double *src, const int32_t *idx, double *dst, int64_t n, int bs,

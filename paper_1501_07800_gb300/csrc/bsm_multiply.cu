@@ -238,24 +238,30 @@ static bsm_status compact_chunk(SymbolicResult &r, double *&cvals, const int32_t
 // chunks (one chunk unless a level exceeds the pair budget); each chunk is
 // computed and compacted as it arrives, and C is assembled from the chunks.
 static bsm_status multiply_chunked(bsm_matrix A, bsm_matrix B, int prec, int slices,
-                                   cudaStream_t s, bsm_matrix *out, int upper);
+                                   cudaStream_t s, bsm_matrix *out, int upper, uint64_t key_lo,
+                                   uint64_t key_hi);
 
 bsm_status multiply_one(bsm_matrix A, bsm_matrix B, int prec, int slices, cudaStream_t s,
-                        bsm_matrix *out, bool upper) {
+                        bsm_matrix *out, bool upper, uint64_t key_lo, uint64_t key_hi) {
   *out = nullptr;
   const int wb = prec == BSM_SPLIT_FP8 ? 32 : (A->bs == 64 ? 32 : A->bs);  // kernel's width
-  if (prec == BSM_FP64 || A->bs == wb) return multiply_chunked(A, B, prec, slices, s, out, upper);
+  if (prec == BSM_FP64 || A->bs == wb)
+    return multiply_chunked(A, B, prec, slices, s, out, upper, key_lo, key_hi);
   // The split kernels take 16- and 32-wide blocks (E4M3: 32 only).  Their
   // result does not depend on the leaf size: the scales span whole rows of A
   // and columns of B and the digit sums are exact, so the product at another
   // width is the product of the re-cut operands, cut back.  For an
   // upper-triangle result the pruning applies at the coarser of the two
-  // widths, and blocks below the diagonal are dropped when cutting finer.
+  // widths, and blocks below the diagonal are dropped when cutting finer.  A
+  // key range maps exactly onto finer blocks (each key becomes four).
   const bool coarser = wb < A->bs;  // computing on finer blocks than the operands'
+  if (key_hi && !coarser) return BSM_ERR_UNSUPPORTED;
   bsm_matrix a = nullptr, b = nullptr, c = nullptr;
   bsm_status st = reblock_impl(A, wb, 0, &a, nullptr, s);
   if (st == BSM_OK) st = B == A ? (b = a, BSM_OK) : reblock_impl(B, wb, 0, &b, nullptr, s);
-  if (st == BSM_OK) st = multiply_chunked(a, b, prec, slices, s, &c, upper ? (coarser ? 2 : 1) : 0);
+  if (st == BSM_OK)
+    st = multiply_chunked(a, b, prec, slices, s, &c, upper ? (coarser ? 2 : 1) : 0, key_lo << 2,
+                          key_hi << 2);
   if (st == BSM_OK) st = reblock_impl(c, A->bs, upper && !coarser ? 2 : 0, out, nullptr, s);
   bsm_destroy(c);
   if (b != a) bsm_destroy(b);
@@ -264,7 +270,8 @@ bsm_status multiply_one(bsm_matrix A, bsm_matrix B, int prec, int slices, cudaSt
 }
 
 static bsm_status multiply_chunked(bsm_matrix A, bsm_matrix B, int prec, int slices,
-                                   cudaStream_t s, bsm_matrix *out, int upper) {
+                                   cudaStream_t s, bsm_matrix *out, int upper, uint64_t key_lo,
+                                   uint64_t key_hi) {
   *out = nullptr;
   LastStats &ls = last_stats();
   ls = LastStats();
@@ -334,7 +341,8 @@ static bsm_status multiply_chunked(bsm_matrix A, bsm_matrix B, int prec, int sli
   };
   int H = 0, nch = 0;
   int64_t tasks[BSM_MAXH + 1];
-  if (st == BSM_OK) st = symbolic_chunks(A, B, sink, tasks, &H, &nch, s, 0, upper);
+  if (st == BSM_OK)
+    st = symbolic_chunks(A, B, sink, tasks, &H, &nch, s, 0, upper, key_lo, key_hi);
   int64_t mb = A->mb, nb = B->nb;
   int64_t side = mb > nb ? mb : nb;
   bsm_matrix C = new_matrix_shell(A->nrows, B->ncols, bs, ceil_log2_i64(side < 1 ? 1 : side));
@@ -417,6 +425,19 @@ extern "C" bsm_status bsm_multiply(bsm_matrix A, bsm_matrix B, bsm_matrix *C,
   if (Bt && Bt != At) bsm_destroy(Bt);
   if (At) bsm_destroy(At);
   return st;
+}
+
+extern "C" bsm_status bsm_multiply_range(bsm_matrix A, bsm_matrix B, uint64_t key_lo,
+                                         uint64_t key_hi, bsm_matrix *C,
+                                         const bsm_mult_opts *opts, void *stream) {
+  if (!C) return BSM_ERR_INVALID_ARG;
+  *C = nullptr;
+  BSM_TRY(check_pair(A, B));
+  if (key_hi <= key_lo) return BSM_ERR_INVALID_ARG;
+  int prec, slices;
+  BSM_TRY(check_opts(opts, &prec, &slices, 0));
+  if (prec != BSM_FP64) BSM_TRY(split_supported(split_width(prec, A->bs), slices));
+  return multiply_one(A, B, prec, slices, (cudaStream_t)stream, C, false, key_lo, key_hi);
 }
 
 extern "C" bsm_status bsm_last_chunks(int *nchunks) {

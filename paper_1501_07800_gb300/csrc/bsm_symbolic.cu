@@ -57,27 +57,44 @@ __device__ __forceinline__ int quad_count(unsigned ma, unsigned mb, int m, int n
                ((ma >> (2 * m + 1)) & (mb >> (2 + n)) & 1u));
 }
 
-// Upper-triangle products (symmetric square, SYRK) keep only C nodes on or
-// above the diagonal.  Children of a node strictly above the diagonal all lie
-// above it; a diagonal node drops its lower-left quadrant q = 2 (m=1, n=0).
-struct UpperView {
-  const uint64_t *sck;  // segment C keys of the level part (NULL: full C)
+// Restrictions of C.  Upper-triangle products (symmetric square, SYRK) keep
+// only C nodes on or above the diagonal: children of a node strictly above the
+// diagonal all lie above it; a diagonal node drops its lower-left quadrant
+// q = 2 (m=1, n=0).  A Morton range [lo, hi) of C's block keys keeps a child
+// whose key range [k 4^h, (k+1) 4^h) at child height h meets it.
+struct CView {
+  const uint64_t *sck;  // segment C keys of the level part (NULL: no restriction)
   const int32_t *pseg;  // segment id of each pair, offset by soff
   int32_t soff;
+  int upper;            // prune below the diagonal
+  int ch;               // height of the children (for the range test)
+  uint64_t lo, hi;      // block-key range; hi == 0: none
 };
 
-__device__ __forceinline__ unsigned pair_qmask(const UpperView &u, int64_t p, unsigned qmask) {
+__device__ __forceinline__ unsigned pair_qmask(const CView &u, int64_t p, unsigned qmask) {
   if (!u.sck) return qmask;
   const uint64_t k = u.sck[u.pseg[p] - u.soff];
-  const bool diag = ((k >> 1) & 0x5555555555555555ull) == (k & 0x5555555555555555ull);
-  return diag ? (qmask & ~4u) : qmask;
+  if (u.upper) {
+    const bool diag = ((k >> 1) & 0x5555555555555555ull) == (k & 0x5555555555555555ull);
+    if (diag) qmask &= ~4u;
+  }
+  if (u.hi) {
+    const int sh = 2 * u.ch;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const uint64_t first = (4 * k + q) << sh;
+      const uint64_t last = first + ((1ull << sh) - 1);  // inclusive
+      if (first >= u.hi || last < u.lo) qmask &= ~(1u << q);
+    }
+  }
+  return qmask;
 }
 
 // Per pair: child counts of the quadrants in qmask; the level's exact total
 // is accumulated in 64 bits: per thread over a grid-stride loop, per block in
 // shared memory, one atomic per block.
 __global__ void k_sym_count(const int32_t *__restrict__ pa, const int32_t *__restrict__ pb,
-                            int64_t np, LevelView va, LevelView vb, unsigned qmask, UpperView up,
+                            int64_t np, LevelView va, LevelView vb, unsigned qmask, CView up,
                             int4 *__restrict__ cnt, unsigned long long *__restrict__ total) {
   __shared__ unsigned long long wsum[32];
   unsigned long long mine = 0;
@@ -155,7 +172,7 @@ __global__ void k_sym_fill(const int32_t *__restrict__ pa, const int32_t *__rest
                            const int32_t *__restrict__ pseg, int32_t soff, int64_t np,
                            const int32_t *__restrict__ sst, int32_t poff,
                            const int4 *__restrict__ P, const int32_t *__restrict__ nbase,
-                           LevelView va, LevelView vb, unsigned qmask, UpperView up,
+                           LevelView va, LevelView vb, unsigned qmask, CView up,
                            int32_t *__restrict__ npa, int32_t *__restrict__ npb,
                            int32_t *__restrict__ npseg) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -250,6 +267,7 @@ struct Expander {
   int64_t *tasks;  // per height
   const LeafSink &sink;
   int upper;  // 0: all of C; k >= 1: C nodes at height >= k - 1 on or above the diagonal
+  uint64_t lo = 0, hi = 0;  // C block-key range [lo, hi); hi == 0: all
   int chunks = 0;
 
   // segment starts [0] and [idx] of a level part, read back
@@ -311,7 +329,9 @@ struct Expander {
       return st;
     }
     cudaMemsetAsync(tot, 0, 8, s);
-    const UpperView up{(upper && L.h - 1 >= upper - 1) ? L.sck : nullptr, L.pseg, L.soff};
+    const bool up_on = upper && L.h - 1 >= upper - 1;
+    const CView up{(up_on || hi) ? L.sck : nullptr, L.pseg, L.soff, up_on ? 1 : 0, L.h - 1, lo,
+                   hi};
     count_launch();
     {
       int dev = 0, sms = 0;
@@ -424,7 +444,8 @@ void free_symbolic(SymbolicResult *r, cudaStream_t s) {
 }
 
 bsm_status symbolic_chunks(bsm_matrix A, bsm_matrix B, const LeafSink &sink, int64_t *tasks,
-                           int *H, int *nchunks, cudaStream_t s, int64_t budget, int upper) {
+                           int *H, int *nchunks, cudaStream_t s, int64_t budget, int upper,
+                           uint64_t key_lo, uint64_t key_hi) {
   const int h0 = A->L > B->L ? A->L : B->L;
   *H = h0;
   *nchunks = 0;
@@ -446,6 +467,8 @@ bsm_status symbolic_chunks(bsm_matrix A, bsm_matrix B, const LeafSink &sink, int
   k_sym_root<<<1, 1, 0, s>>>(R.pa, R.pb, R.pseg, R.sck, R.sst);
   tasks[h0] = 1;
   Expander ex{A, B, s, budget > 0 ? budget : pair_budget(), tasks, sink, upper};
+  ex.lo = key_lo;
+  ex.hi = key_hi;
   st = ex.process(R, 0xFu);
   free_level(R, s);
   *nchunks = ex.chunks;

@@ -76,6 +76,7 @@ def test_argument_checks_before_any_device_work(lib):
     assert lib.bsm_sym_multiply(None, None, 0, ctypes.byref(out), None, None) == -1
     assert lib.bsm_sym_to_full(None, ctypes.byref(out), None) == -1
     assert lib.bsm_reblock(None, 32, ctypes.byref(out), None) == -1
+    assert lib.bsm_multiply_range(None, None, 0, 1, ctypes.byref(out), None, None) == -1
     b = ctypes.c_int()
     assert lib.bsm_plan_block_size(None, ctypes.byref(b)) == -1
     assert lib.bsm_node_norms2(None, 0, None, None, None, ctypes.byref(n), 0, None) == -1
