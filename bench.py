@@ -558,10 +558,13 @@ def run_decay(args):
     legs = [(f"split_bf16x{k}", False, bsm.BSM_SPLIT_BF16, k, args.steps) for k in slices]
     legs += [(f"split_fp8x{k}", False, bsm.BSM_SPLIT_FP8, int(k), args.steps)
              for k in args.fp8_slices.split(",") if k]
-    legs.append(("fp64", False, bsm.BSM_FP64, 0, 1))
+    if not args.no_fp64:
+        legs.append(("fp64", False, bsm.BSM_FP64, 0, 1))
     if args.sym:
         legs += [(f"sym_square_split_bf16x{slices[-1]}", True, bsm.BSM_SPLIT_BF16, slices[-1],
-                  args.steps), ("sym_square_fp64", True, bsm.BSM_FP64, 0, 1)]
+                  args.steps)]
+        if not args.no_fp64:
+            legs.append(("sym_square_fp64", True, bsm.BSM_FP64, 0, 1))
     # FP64 first: its statistics are the product's own at this block size (a
     # split product at a width its kernel does not take runs on re-cut blocks,
     # and its statistics are those of the re-cut product)
@@ -628,9 +631,9 @@ def run_decay(args):
         torch.cuda.empty_cache()
         log(f"{name}: {res}")
     best = f"split_bf16x{max(slices)}" if slices else None
-    if best:
+    if best and "fp64" in out:
         out["split_speedup_vs_fp64"] = out["fp64"]["ms_per_product"] / out[best]["ms_per_product"]
-    if args.sym:
+    if args.sym and "sym_square_fp64" in out:
         out["sym_square_speedup_vs_full_fp64"] = (out["fp64"]["ms_per_product"] /
                                                   out["sym_square_fp64"]["ms_per_product"])
     print(json.dumps(out), flush=True)
@@ -726,6 +729,7 @@ def main():
     ap.add_argument("--bs", type=int, default=32, help="decay workload: leaf block size")
     ap.add_argument("--slices", default="7", help="decay workload: split slice counts, e.g. 3,5,7")
     ap.add_argument("--fp8-slices", default="", help="decay workload: FP8 split slice counts")
+    ap.add_argument("--no-fp64", action="store_true", help="decay workload: skip the FP64 legs")
     ap.add_argument("--sym", action="store_true",
                     help="decay workload: also the symmetric square from the upper triangle")
     ap.add_argument("--shard", action="store_true",

@@ -406,10 +406,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
   constexpr int G = C::G;
   constexpr int BETA = Fmt<F>::BETA, TS = Fmt<F>::TSPLIT;
   constexpr uint32_t IDESC = F == 0 ? idesc_bf16_f32(128, BS) : idesc_e4m3_f32(128, BS);
-  constexpr int NCOLS = 2 * G * BS <= 32 ? 32 : (2 * G * BS <= 64 ? 64 : (2 * G * BS <= 128 ? 128 : 256));
+  // TMEM accumulators: each team owns NBUF buffers of G*BS columns, two when
+  // they fit in the 256 columns we allocate, so that the MMAs of a C block's
+  // next flush run while the team drains the previous one
+  constexpr int NBUF = 4 * G * BS <= 256 ? 2 : 1;
+  constexpr int TCOLS = 2 * NBUF * G * BS;
+  constexpr int NCOLS = TCOLS <= 32 ? 32 : (TCOLS <= 64 ? 64 : (TCOLS <= 128 ? 128 : 256));
   constexpr uint32_t BYTES = (uint32_t)S * C::SLICE;  // one operand's slices
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t full[C::NST], empty[C::NST], tfull[2], tempty[2], done;
+  // tfull / tempty: per (team, buffer), index 2 * team + buffer
+  __shared__ __align__(8) uint64_t full[C::NST], empty[C::NST], tfull[4], tempty[4], done;
   __shared__ __align__(8) uint64_t meta_full[kMeta], meta_empty[kMeta];
   __shared__ Meta meta[kMeta];
   __shared__ uint32_t tmem_base_sh;
@@ -430,9 +436,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
-    for (int i = 0; i < 2; i++) {
+    for (int i = 0; i < 4; i++) {
       mbar_init(&tfull[i], 1);
-      mbar_init(&tempty[i], kTeam);  // buffer i belongs to team i
+      mbar_init(&tempty[i], kTeam);  // buffers 2t, 2t+1 belong to team t
     }
     for (int i = 0; i < kMeta; i++) {
       mbar_init(&meta_full[i], 1);
@@ -595,7 +601,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         for (int f = 0; f < nfl && !abort_flag; f++) {
           const uint32_t fb = b ? fcb1 : fcb0;
           if (b) fcb1++; else fcb0++;
-          if (!mbar_wait(&tempty[b], (fb & 1u) ^ 1u)) {
+          const uint32_t u = fb % NBUF, use = fb / NBUF;  // buffer and its use count
+          if (!mbar_wait(&tempty[2 * b + u], (use & 1u) ^ 1u)) {
             set_err(P.err, DERR_TIMEOUT);
             abort_flag = 1;
             break;
@@ -618,7 +625,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
             const uint32_t first = (j == f * P.flushk) ? 0u : 1u;
 #pragma unroll
             for (int g = 0; g < G; g++) {
-              const uint32_t dt = tbase + (uint32_t)((b * G + g) * BS);
+              const uint32_t dt = tbase + (uint32_t)(((b * NBUF + u) * G + g) * BS);
 #pragma unroll
               for (int t = 0; t < S; t++) {
                 if (t >= (g + 1) * DPG) break;  // K-blocks of group g: t < min(S, (g+1) DPG)
@@ -636,7 +643,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
             }
             tc_commit(&empty[st]);  // stage reusable once these MMAs are done
           }
-          tc_commit(&tfull[b]);  // flush ready for the epilogue
+          tc_commit(&tfull[2 * b + u]);  // flush ready for the epilogue
         }
       }
       // no MMA may still be running when TMEM is released
@@ -701,7 +708,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
       // so that the team meets the same fold barriers whatever happened.
       for (int f = 0; f < nfl; f++, fct++) {
         if (ok) {
-          bool w = mbar_wait(&tfull[team], fct & 1u);
+          bool w = mbar_wait(&tfull[2 * team + fct % NBUF], (fct / NBUF) & 1u);
           if (!__all_sync(0xffffffffu, w && abort_flag == 0)) {
             set_err(P.err, DERR_TIMEOUT);
             abort_flag = 1;
@@ -714,9 +721,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
           for (int g = 0; g < G; g++) {
             uint32_t v[HC];
             if constexpr (HC == 16)
-              tmem_ld16(tbase + lane_addr + (uint32_t)((team * G + g) * BS + c0), v);
+              tmem_ld16(tbase + lane_addr + (uint32_t)(((team * NBUF + fct % NBUF) * G + g) * BS + c0), v);
             else
-              tmem_ld8(tbase + lane_addr + (uint32_t)((team * G + g) * BS + c0), v);
+              tmem_ld8(tbase + lane_addr + (uint32_t)(((team * NBUF + fct % NBUF) * G + g) * BS + c0), v);
             tmem_ld_wait();
             const int d = g * DPG + L;
             if (d < S) {
@@ -741,7 +748,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
             }
           }
           tc_fence_before();
-          mbar_arrive(&tempty[team]);
+          mbar_arrive(&tempty[2 * team + fct % NBUF]);
         }
         if ((f + 1) % kFold == 0 && f + 1 < nfl) {
           // the 32-bit sums are full: fold them into this thread's (hi, lo)
