@@ -163,7 +163,7 @@ bsm_status numeric_fp64_batched(int bs, const ProdDesc *prods, const uint64_t *i
                                 int64_t nitems, unsigned long long *counter, unsigned *errword,
                                 int ctas_per_sm, cudaStream_t s);
 bsm_status split_supported(int bs, int slices);
-int split_flush_group(int bs, int slices);
+int split_flush_group(int bs, int spec, int bound_log2);
 bsm_status split_prepare(bsm_matrix A, bsm_matrix B, int slices, unsigned *errword, ProdDesc &d,
                          std::vector<void *> &owned, cudaStream_t s);
 // fold: device scratch of split_fold_bytes(bs) bytes, private to the launch

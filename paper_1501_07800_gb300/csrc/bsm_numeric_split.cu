@@ -321,7 +321,8 @@ struct SplitArgs {
   const ProdDesc *prods;     // product table (device)
   const uint64_t *items;     // work list of (product, C block); NULL: product 0, C blocks 0..
   int64_t nitems;
-  int flushk;
+  int flushk;                // block products per flush: sums < 2^22 (magic conversion)
+  int flushk_wide;           // the same for sums <= 2^24 (bitwise conversion), long lists
   unsigned *err;
   unsigned long long *work;  // chunk counter, zero at launch
   int chunk;                 // work items claimed per atomic (1..32)
@@ -329,9 +330,33 @@ struct SplitArgs {
 };
 constexpr int kChunk = 32;   // most work items claimed per atomic
 // The 32-bit diagonal sums in shared memory take at most kFold flushes of
-// magnitude < 2^22 each; a C block with more flushes folds them every kFold
-// flushes into exact 64-bit (hi, lo) pairs in per-CTA global scratch.
-constexpr int kFold = 511;
+// magnitude < 2^22 each (kFoldWide of <= 2^24); a C block with more flushes
+// folds them every kFold flushes into exact 64-bit (hi, lo) pairs in per-CTA
+// global scratch.
+constexpr int kFold = 511, kFoldWide = 127;
+
+// Flush mode of a C block with nk block products: a list longer than one
+// narrow flush uses wide flushes (4x longer, converted bit by bit).
+struct FlushPlan {
+  bool wide;
+  int fk, nfl, kf;
+};
+__device__ __forceinline__ FlushPlan flush_plan(int nk, int flushk, int flushk_wide) {
+  FlushPlan p;
+  p.wide = nk > flushk;
+  p.fk = p.wide ? flushk_wide : flushk;
+  p.nfl = (nk + p.fk - 1) / p.fk;
+  p.kf = p.wide ? kFoldWide : kFold;
+  return p;
+}
+
+// Exact value of an integer-valued FP32 with |v| <= 2^24, from its bits.
+__device__ __forceinline__ int32_t f32_int_exact(uint32_t b) {
+  const int e = (int)((b >> 23) & 0xFFu);
+  const uint32_t m = (b & 0x7FFFFFu) | 0x800000u;
+  const int32_t mag = e < 127 ? 0 : (e > 150 ? (int32_t)(m << (e - 150)) : (int32_t)(m >> (150 - e)));
+  return (b >> 31) ? -mag : mag;
+}
 
 // Per-C-block work descriptor handed from the producer warp to the MMA thread
 // and the epilogue through a shared-memory ring.
@@ -596,7 +621,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         const int nk = meta[m].nk;
         mbar_arrive(&meta_empty[m]);
         if (nk < 0 || abort_flag) break;  // end marker
-        int nfl = (nk + P.flushk - 1) / P.flushk;
+        const FlushPlan fp = flush_plan(nk, P.flushk, P.flushk_wide);
+        const int nfl = fp.nfl;
         const int b = q & 1;  // C blocks alternate between the two teams / buffers
         for (int f = 0; f < nfl && !abort_flag; f++) {
           const uint32_t fb = b ? fcb1 : fcb0;
@@ -608,8 +634,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
             break;
           }
           tc_fence_after();
-          int jend = min(nk, (f + 1) * P.flushk);
-          for (int j = f * P.flushk; j < jend; j++, it++) {
+          int jend = min(nk, (f + 1) * fp.fk);
+          for (int j = f * fp.fk; j < jend; j++, it++) {
             int st = it % C::NST;
             if (!mbar_wait(&full[st], (it / C::NST) & 1u)) {
               set_err(P.err, DERR_TIMEOUT);
@@ -622,7 +648,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
             const uint32_t sa = sbase + st * C::STAGE;
             const uint64_t ad0 = smem_desc(sa, C::LBO, C::SBO);
             const uint64_t bd0 = smem_desc(sa + C::ASLOTS * C::SLICE, C::LBO, C::SBO);
-            const uint32_t first = (j == f * P.flushk) ? 0u : 1u;
+            const uint32_t first = (j == f * fp.fk) ? 0u : 1u;
 #pragma unroll
             for (int g = 0; g < G; g++) {
               const uint32_t dt = tbase + (uint32_t)(((b * NBUF + u) * G + g) * BS);
@@ -701,7 +727,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         erow[i] = rowexp[crow + g4 / (BS / 4)];
         fcol[i] = *reinterpret_cast<const int4 *>(colexp + ccol + (g4 % (BS / 4)) * 4);
       }
-      const int nfl = (nk + P.flushk - 1) / P.flushk;
+      const FlushPlan fplan = flush_plan(nk, P.flushk, P.flushk_wide);
+      const int nfl = fplan.nfl, kf = fplan.kf;
+      const bool wide = fplan.wide;
       int64_t *const fold = P.fold + ((int64_t)blockIdx.x * 2 + team) * (BS * BS * 2);
       bool ok = true;
       // Every warp runs all nfl iterations (doing no work once `ok` is false)
@@ -727,16 +755,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
             tmem_ld_wait();
             const int d = g * DPG + L;
             if (d < S) {
-              // exact integer value of each FP32 sum (|D| < 2^22)
+              // exact integer value of each FP32 sum (|D| < 2^22: magic add;
+              // wide flushes, |D| <= 2^24: from the bits)
               int32_t *dst = tcomb + (d * BS + r) * C::CROW + c0;
 #pragma unroll
               for (int x = 0; x < HC; x += 4) {
-                int4 val = make_int4(
-                    (int32_t)(__float_as_uint(__uint_as_float(v[x]) + kMagicF) - kMagic),
-                    (int32_t)(__float_as_uint(__uint_as_float(v[x + 1]) + kMagicF) - kMagic),
-                    (int32_t)(__float_as_uint(__uint_as_float(v[x + 2]) + kMagicF) - kMagic),
-                    (int32_t)(__float_as_uint(__uint_as_float(v[x + 3]) + kMagicF) - kMagic));
-                if (f % kFold != 0) {
+                int4 val;
+                if (!wide) {
+                  val = make_int4(
+                      (int32_t)(__float_as_uint(__uint_as_float(v[x]) + kMagicF) - kMagic),
+                      (int32_t)(__float_as_uint(__uint_as_float(v[x + 1]) + kMagicF) - kMagic),
+                      (int32_t)(__float_as_uint(__uint_as_float(v[x + 2]) + kMagicF) - kMagic),
+                      (int32_t)(__float_as_uint(__uint_as_float(v[x + 3]) + kMagicF) - kMagic));
+                } else {
+                  val = make_int4(f32_int_exact(v[x]), f32_int_exact(v[x + 1]),
+                                  f32_int_exact(v[x + 2]), f32_int_exact(v[x + 3]));
+                }
+                if (f % kf != 0) {
                   const int4 old = *reinterpret_cast<const int4 *>(dst + x);
                   val.x += old.x;
                   val.y += old.y;
@@ -750,7 +785,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
           tc_fence_before();
           mbar_arrive(&tempty[2 * team + fct % NBUF]);
         }
-        if ((f + 1) % kFold == 0 && f + 1 < nfl) {
+        if ((f + 1) % kf == 0 && f + 1 < nfl) {
           // the 32-bit sums are full: fold them into this thread's (hi, lo)
           // pairs.  The barrier's OR makes `ok` uniform across the team.
           if (named_bar_or(bar_id, kTeam, !ok || abort_flag != 0)) {
@@ -774,7 +809,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
                 int64_t hi, lo;
                 combine_digits<S, BETA, TS>(dg, hi, lo);
                 int64_t *fp = fold + (rr * BS + c4 + x) * 2;
-                if (f + 1 > kFold) {
+                if (f + 1 > kf) {
                   hi += fp[0];
                   lo += fp[1];
                 }
@@ -809,7 +844,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
           for (int d = 0; d < S; d++) dg[d] = x == 0 ? dv[d].x : x == 1 ? dv[d].y : x == 2 ? dv[d].z : dv[d].w;
           int64_t hi, lo;
           combine_digits<S, BETA, TS>(dg, hi, lo);
-          if (nfl > kFold) {
+          if (nfl > kf) {
             const int64_t *fp = fold + (rr * BS + c4 + x) * 2;
             hi += fp[0];
             lo += fp[1];
@@ -878,14 +913,15 @@ bsm_status launch_split_s(const SplitArgs &a, int fmt, int slices, cudaStream_t 
 
 }  // namespace
 
-// Largest group of k-products whose diagonal sums stay exact (< 2^22) in the
-// FP32 accumulator: with digit base 2^B, d = 0 sums terms up to 2^(2B); d >= 1
-// at most (d + 3) 2^(2B-2) per inner element.
-int split_flush_group(int bs, int spec) {
+// Largest group of k-products whose diagonal sums stay within 2^bound_log2
+// (22: below the magic-number conversion's limit; 24: the largest integers
+// FP32 holds exactly) in the FP32 accumulator: with digit base 2^B, d = 0
+// sums terms up to 2^(2B); d >= 1 at most (d + 3) 2^(2B-2) per inner element.
+int split_flush_group(int bs, int spec, int bound_log2) {
   const int beta = split_spec_fmt(spec) == 0 ? Fmt<0>::BETA : Fmt<1>::BETA;
   const int s = split_spec_slices(spec);
-  int maxel = (1 << 22) >> (2 * beta);                  // d = 0
-  int m2 = ((1 << 22) >> (2 * beta - 2)) / (s + 2);     // d = s - 1
+  int maxel = (1 << bound_log2) >> (2 * beta);                  // d = 0
+  int m2 = ((1 << bound_log2) >> (2 * beta - 2)) / (s + 2);     // d = s - 1
   if (m2 < maxel) maxel = m2;
   int g = maxel / bs;
   return g < 1 ? 1 : g;
@@ -984,7 +1020,8 @@ bsm_status split_launch(int bs, int spec, const ProdDesc *prods_dev, const uint6
   a.prods = prods_dev;
   a.items = items;
   a.nitems = nitems;
-  a.flushk = split_flush_group(bs, spec);
+  a.flushk = split_flush_group(bs, spec, 22);
+  a.flushk_wide = split_flush_group(bs, spec, 24);
   a.err = errword;
   a.work = work;
   return bs == 16 ? launch_split_s<16>(a, fmt, slices, s) : launch_split_s<32>(a, fmt, slices, s);

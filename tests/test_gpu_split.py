@@ -288,3 +288,20 @@ def test_fp8_rejects_uncompiled_slice_counts():
     with pytest.raises(bsm.BsmError) as e:
         bsm.bsm_multiply(A, A, prec=bsm.BSM_SPLIT_FP8, slices=13)
     assert e.value.name == "BSM_ERR_INVALID_ARG"
+
+
+@pytest.mark.parametrize("prec,x,slices", [(bsm.BSM_SPLIT_FP8, 15 / 16, 2),
+                                           (bsm.BSM_SPLIT_BF16, 127 / 128, 2)])
+def test_accumulator_exact_near_its_bound(prec, x, slices):
+    """Every entry x has one large top digit (15 in base 16, 127 in base 128)
+    and zero below it, so each flush sums digit products of one sign up to
+    just under 2^22: the tensor-core accumulation must be exact there."""
+    bs, nk = 32, 2000
+    vals = np.full((nk, bs, bs), x)
+    A = synth.BlockCOO(bs, bs * nk, bs, np.zeros(nk, np.int32), np.arange(nk, dtype=np.int32),
+                       vals)
+    B = synth.BlockCOO(bs * nk, bs, bs, np.arange(nk, dtype=np.int32), np.zeros(nk, np.int32),
+                       vals.copy())
+    C = from_bsm(bsm.bsm_multiply(to_bsm(A), to_bsm(B), prec=prec, slices=slices))
+    assert C.nblk == 1
+    assert np.all(C.vals == x * x * bs * nk)   # exactly representable
