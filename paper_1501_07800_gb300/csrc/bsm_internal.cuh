@@ -172,6 +172,8 @@ bsm_status split_launch(int bs, int slices, const ProdDesc *prods_dev, const uin
                         int64_t nitems, unsigned long long *work, unsigned *errword,
                         int64_t *fold, cudaStream_t s, int chunk = 32);
 size_t split_fold_bytes(int bs);
+// Work items per claim for a list of nt block products over nc C blocks.
+int split_chunk_for(int64_t nt, int64_t nc);
 // Longest product list of a task list, atomically maxed into *dmax_dev.
 void launch_max_seg(const SymbolicResult &sym, int *dmax_dev, cudaStream_t s);
 bsm_status split_alloc(bsm_matrix A, bsm_matrix B, int slices, ProdDesc &d,

@@ -509,8 +509,11 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
     ls.triples += sym[i].nt;
     ls.nc_sym += sym[i].nc;
   }
-  int64_t total = 0;
-  for (int i = 0; i < n; i++) total += sym[i].nc;
+  int64_t total = 0, total_nt = 0;
+  for (int i = 0; i < n; i++) {
+    total += sym[i].nc;
+    total_nt += sym[i].nt;
+  }
   if (st == BSM_OK) st = dev_alloc((void **)&err, sizeof(unsigned), s);
   if (st == BSM_OK) cudaMemsetAsync(err, 0, sizeof(unsigned), s);
   for (int i = 0; i < n && st == BSM_OK; i++) {
@@ -569,7 +572,8 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
       if (prec == BSM_FP64)
         st = numeric_fp64_batched(bs, table, v1, total, counter, err, 0, s);
       else
-        st = split_launch(bs, slices, table, v1, total, counter, err, fold, s, 32);
+        st = split_launch(bs, slices, table, v1, total, counter, err, fold, s,
+                          split_chunk_for(total_nt, total));
     }
   }
   timer.mark(s);

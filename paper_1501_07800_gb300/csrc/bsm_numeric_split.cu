@@ -927,6 +927,16 @@ int split_flush_group(int bs, int spec, int bound_log2) {
   return g < 1 ? 1 : g;
 }
 
+// Work items per claim.  Short product lists: 32 consecutive C blocks per
+// atomic keep the claiming cheap.  Long lists: one C block per claim, so that
+// the CTAs work on neighbouring C blocks (in Morton order) at the same time and
+// share the slices of their A rows and B columns in L2 instead of each
+// streaming its own region from HBM.
+int split_chunk_for(int64_t nt, int64_t nc) {
+  const int64_t avg = nc > 0 ? nt / nc : 0;
+  return avg >= 16 ? 1 : (avg >= 4 ? 8 : 32);
+}
+
 size_t split_fold_bytes(int bs) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -1074,7 +1084,8 @@ bsm_status numeric_split(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, 
     owned.push_back(fold);
   if (st == BSM_OK)
     st = split_launch(bs, slices, reinterpret_cast<const ProdDesc *>(scr + 4), nullptr, sym.nc,
-                      reinterpret_cast<unsigned long long *>(scr + 2), errword, fold, s);
+                      reinterpret_cast<unsigned long long *>(scr + 2), errword, fold, s,
+                      split_chunk_for(sym.nt, sym.nc));
   cleanup();
   return st;
 }

@@ -184,7 +184,7 @@ bsm_status autotune(bsm_plan P) {
     if (P->prec == BSM_FP64)
       cands.push_back({order, 32, 0});
     else
-      for (int chunk : {32, 8}) cands.push_back({order, chunk, 0});
+      for (int chunk : {32, 8, 1}) cands.push_back({order, chunk, 0});
   }
   const int reps = P->prec == BSM_FP64 ? 1 : 2;
   enqueue_numeric(P, cands[0].order, cands[0].chunk, cands[0].ctas, P->stream);  // warm-up
