@@ -25,10 +25,11 @@
  *   - Block payloads are row-major bs x bs float64.  Matrix sides need not be
  *     multiples of bs: edge blocks are stored full size and their entries
  *     outside the matrix must be zero (the quadtree pads the matrix to 2^L
- *     blocks per side, Sec. 3.1 "uniform blocksize ... as far as possible").
+ *     blocks per side: the uniform power-of-two blocking of Sec. 3.1).
  *   - A block is "zero" when every entry compares equal to 0.0 (so -0.0 is
  *     zero and NaN is not).  Zero blocks are never stored (Sec. 4.1).
- *   - Handles are immutable after creation, owned by the caller, freed with
+ *   - A handle's block structure is fixed at creation (its values change only
+ *     through bsm_update_values); handles are owned by the caller, freed with
  *     bsm_destroy, and bound to the device that was current at creation.
  */
 #ifndef BSM_H
