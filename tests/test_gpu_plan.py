@@ -132,3 +132,19 @@ def test_plan_at_forced_leaf_sizes_matches(cb):
         E = oracle.multiply(a, b).C
         assert_same_structure(g, E)
         assert relerr(g.vals, E.vals) < 1e-12
+
+
+def test_plan_fp8_equals_batched():
+    pairs = batch(nprod=4, seed=71)
+    As = [to_bsm(a) for a, _ in pairs]
+    Bs = [to_bsm(b) for _, b in pairs]
+    ref = [from_bsm(c) for c in bsm.bsm_multiply_batched(As, Bs, prec=bsm.BSM_SPLIT_FP8,
+                                                         slices=12)]
+    plan = bsm.bsm_plan_create(As, Bs, prec=bsm.BSM_SPLIT_FP8, slices=12, autotune=True)
+    bsm.bsm_plan_execute(plan)
+    for g, r, (a, b) in zip(bsm.bsm_plan_results(plan), ref, pairs):
+        g = from_bsm(g)
+        assert_same_structure(g, r)
+        assert np.array_equal(g.vals, r.vals)
+        E = oracle.multiply(a, b).C
+        assert relerr(g.vals, E.vals) < 1e-11
