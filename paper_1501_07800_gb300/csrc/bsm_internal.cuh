@@ -44,6 +44,16 @@ struct bsm_matrix_s {
   std::vector<void *> owned;
 };
 
+// v != 0.0 (so -0.0 is zero and NaN is not), from the bits: on GB300 a double
+// compare would take the FP64 pipe, the scarcest unit of the chip.
+__host__ __device__ inline bool nonzero_f64(double v) {
+#ifdef __CUDA_ARCH__
+  return ((uint64_t)__double_as_longlong(v) << 1) != 0;
+#else
+  return v != 0.0;
+#endif
+}
+
 // Morton key: bit 2b+1 = bit b of the block row, bit 2b = bit b of the block
 // column, so the two low bits of a key are the child index 2*rowbit + colbit.
 __host__ __device__ inline uint64_t morton_spread(uint64_t x) {

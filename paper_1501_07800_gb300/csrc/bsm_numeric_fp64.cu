@@ -123,7 +123,7 @@ __device__ bool cblock_fp64(const int32_t *__restrict__ seg, const int32_t *__re
   for (int i = 0; i < TW; i++)
 #pragma unroll
     for (int q = 0; q < TW; q++) {
-      any |= (acc[i][q][0] != 0.0) | (acc[i][q][1] != 0.0);
+      any |= nonzero_f64(acc[i][q][0]) | nonzero_f64(acc[i][q][1]);
       int row = wr * WT + i * 8 + ar, col = wc * WT + q * 8 + 2 * ak;
       *reinterpret_cast<double2 *>(cb + row * BS + col) = make_double2(acc[i][q][0], acc[i][q][1]);
     }

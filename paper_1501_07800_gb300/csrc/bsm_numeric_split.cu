@@ -851,7 +851,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
           }
           const int fx = x == 0 ? fcol[i].x : x == 1 ? fcol[i].y : x == 2 ? fcol[i].z : fcol[i].w;
           out[x] = split_to_double<TS>(hi, lo, erow[i] + fx - XS);
-          any |= out[x] != 0.0;
+          any |= nonzero_f64(out[x]);
         }
         double2 *dst = reinterpret_cast<double2 *>(cb + rr * BS + c4);
         dst[0] = make_double2(out[0], out[1]);

@@ -90,7 +90,7 @@ __global__ void k_add_blocks(const uint64_t *__restrict__ keys, const uint32_t *
   for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
     double v = two ? x[e] + y[e] : x[e];
     d[e] = v;
-    any |= v != 0.0;
+    any |= nonzero_f64(v);
   }
   any = __syncthreads_or(any);
   if (threadIdx.x == 0) {
@@ -284,7 +284,7 @@ __global__ void k_split_flags(const double *__restrict__ vals, const uint64_t *_
   }
   const double *b = vals + t * bs * bs + (int64_t)(i * nbs) * bs + j * nbs;
   bool any = false;
-  for (int e = lane; e < nbs * nbs; e += 32) any |= b[(e / nbs) * bs + e % nbs] != 0.0;
+  for (int e = lane; e < nbs * nbs; e += 32) any |= nonzero_f64(b[(e / nbs) * bs + e % nbs]);
   any = __any_sync(0xffffffffu, any);
   if (lane == 0) flag[w] = any && (keep_all != 2 || I <= J);
 }

@@ -26,7 +26,7 @@ __global__ void k_make_keys(const int32_t *__restrict__ brow, const int32_t *__r
   bool any = false;
   for (int t = lane; t < n2; t += 32) {
     double2 v = b[t];
-    any |= (v.x != 0.0) | (v.y != 0.0);
+    any |= nonzero_f64(v.x) | nonzero_f64(v.y);
   }
   any = __any_sync(0xffffffffu, any);
   if (lane == 0) {
