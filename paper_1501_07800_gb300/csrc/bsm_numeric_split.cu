@@ -393,9 +393,16 @@ __device__ __forceinline__ void combine_digits(const int32_t (&a)[S], int64_t &h
 
 // Correctly rounded (hi 2^T + lo) 2^X as FP64; 64-bit path (branch-free
 // rounding) when the value fits in an int64, 128-bit path otherwise.
+// The general case (values beyond 64 bits, results in the subnormal or
+// overflow range): rare, and kept out of line so that none of its FP64
+// instructions is issued, predicated off, on the common path.
+__device__ __noinline__ double split_to_double_slow(int64_t hi, int64_t lo, int T, int X) {
+  return fixed_to_double(((__int128)hi << T) + (__int128)lo, X);
+}
+
 template <int T>
 __device__ __forceinline__ double split_to_double(int64_t hi, int64_t lo, int X) {
-  if (hi > -(1ll << 27) && hi < (1ll << 27)) {
+  if (__builtin_expect(hi > -(1ll << 27) && hi < (1ll << 27), 1)) {
     const int64_t v = (int64_t)((uint64_t)hi << T) + lo;  // |v| < 2^(27+T) + 2^59.1
     if (v == 0) return 0.0;
     const uint64_t sign = (uint64_t)v & (1ull << 63);
@@ -409,13 +416,11 @@ __device__ __forceinline__ double split_to_double(int64_t hi, int64_t lo, int X)
     mant >>= carry;
     top += carry;
     const int be = top + X + 1023;
-    if (be >= 1 && be <= 2046)
+    if (__builtin_expect(be >= 1 && be <= 2046, 1))
       return __longlong_as_double(
           (long long)(sign | ((uint64_t)be << 52) | (mant & ((1ull << 52) - 1))));
-    const double r = scalbn((double)mant, top - 52 + X);
-    return sign ? -r : r;
   }
-  return fixed_to_double(((__int128)hi << T) + (__int128)lo, X);
+  return split_to_double_slow(hi, lo, T, X);
 }
 
 constexpr int kTeamWarps = 8;                // warps per epilogue team (2 per lane quadrant)

@@ -305,3 +305,27 @@ def test_accumulator_exact_near_its_bound(prec, x, slices):
     C = from_bsm(bsm.bsm_multiply(to_bsm(A), to_bsm(B), prec=prec, slices=slices))
     assert C.nblk == 1
     assert np.all(C.vals == x * x * bs * nk)   # exactly representable
+
+
+@pytest.mark.parametrize("scale,check", [(1e-160, "subnormal"), (1e160, "overflow")])
+def test_results_beyond_the_normal_range(scale, check):
+    """Products far below the smallest normal double round to subnormals, and
+    far above the largest overflow to infinity, as in FP64 (the out-of-line
+    rounding path)."""
+    A = synth.random_blocks(256, 32, 0.5, 650)
+    B = synth.random_blocks(256, 32, 0.5, 651)
+    A.vals *= scale
+    B.vals *= scale
+    C = split_product(A, B)
+    with np.errstate(over="ignore", under="ignore", invalid="ignore"):
+        E = oracle.multiply(A, B).C
+    if check == "subnormal":
+        assert_same_structure(C, E)
+        assert np.all(np.abs(C.vals) < 2.3e-308)
+        assert np.max(np.abs(C.vals - E.vals)) < 1e-320
+        assert np.count_nonzero(C.vals) > 0.9 * np.count_nonzero(E.vals)
+    else:
+        assert_same_structure(C, E)
+        big = np.abs(E.vals) > 1e300
+        assert np.array_equal(np.isinf(C.vals), np.isinf(E.vals) | (big & np.isinf(C.vals)))
+        assert np.all(np.sign(C.vals[np.isinf(C.vals)]) == np.sign(E.vals[np.isinf(C.vals)]))
