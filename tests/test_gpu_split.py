@@ -332,4 +332,5 @@ def test_results_beyond_the_normal_range(e):
         both = inf & np.isinf(want)
         assert np.array_equal(np.sign(C.vals[both]), np.sign(want[both]))
         fin = ~inf & np.isfinite(want)
-        assert relerr(C.vals[fin], want[fin]) < TOL_SPLIT
+        # compare scaled back down (norms of values near 1e308 overflow)
+        assert relerr(np.ldexp(C.vals[fin], -2 * e), np.ldexp(want[fin], -2 * e)) < TOL_SPLIT
