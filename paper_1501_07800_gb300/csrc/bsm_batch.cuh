@@ -15,6 +15,11 @@ struct ProdDesc {
   // split mode only
   const uint8_t *asl, *bsl;      // digit slices of A / B (BF16 or E4M3 codes)
   const int *rowexp, *colexp;    // power-of-two scale exponents
+  // pair items (split kernel with two C blocks per item): items are sibling
+  // pairs (I, 2y), (I, 2y+1); seg / ta / tb / ckeys describe the pairs (merged
+  // product lists, tb = B pair slot, key of the even sibling), pairc[2p],
+  // pairc[2p+1] are the pair's C blocks (-1: absent), nb counts B pair slots
+  const int32_t *pairc;
 };
 
 // Work item = (product index << 40) | C block index.

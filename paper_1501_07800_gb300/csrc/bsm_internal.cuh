@@ -178,9 +178,11 @@ bsm_status split_prepare(bsm_matrix A, bsm_matrix B, int slices, unsigned *errwo
                          std::vector<void *> &owned, cudaStream_t s);
 // fold: device scratch of split_fold_bytes(bs) bytes, private to the launch
 // (C blocks with very long product lists park exact partial sums there).
+// np = 2: items are pairs of sibling C blocks (ProdDesc.pairc, B slices in
+// pair slots).
 bsm_status split_launch(int bs, int slices, const ProdDesc *prods_dev, const uint64_t *items,
                         int64_t nitems, unsigned long long *work, unsigned *errword,
-                        int64_t *fold, cudaStream_t s, int chunk = 32);
+                        int64_t *fold, cudaStream_t s, int chunk = 32, int np = 1);
 size_t split_fold_bytes(int bs);
 // Work items per claim for a list of nt block products over nc C blocks.
 int split_chunk_for(int64_t nt, int64_t nc);
@@ -188,8 +190,9 @@ int split_chunk_for(int64_t nt, int64_t nc);
 void launch_max_seg(const SymbolicResult &sym, int *dmax_dev, cudaStream_t s);
 bsm_status split_alloc(bsm_matrix A, bsm_matrix B, int slices, ProdDesc &d,
                        std::vector<void *> &owned, cudaStream_t s);
+// bslot (pair items only): B pair slot of every B block, NULL otherwise.
 bsm_status split_compute(bsm_matrix A, bsm_matrix B, int slices, const ProdDesc &d,
-                         unsigned *errword, cudaStream_t s);
+                         unsigned *errword, cudaStream_t s, const int32_t *bslot = nullptr);
 
 // C assembly from a numeric result: zero removal and level build.
 // finish_product takes ownership of sym->ckeys and cvals; finish_product_copy

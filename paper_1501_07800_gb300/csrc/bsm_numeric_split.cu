@@ -79,22 +79,26 @@ struct Fmt<1> {
 constexpr uint32_t kMagic = 0x4B400000u;  // bits of 1.5 * 2^23
 constexpr float kMagicF = 12582912.0f;
 
-template <int BS, int S, int F>
+// NP: C blocks per work item.  1: one C block (N = bs per MMA), two epilogue
+// teams.  2: a pair of sibling C blocks (I, 2y), (I, 2y+1) sharing every A
+// tile (N = 2 bs per MMA, half the A-operand traffic per output), one team.
+template <int BS, int S, int F, int NP = 1>
 struct Cfg {
   static constexpr int DPG = 128 / BS;                       // diagonals per group
   static constexpr int G = (S + DPG - 1) / DPG;              // diagonal groups
   static constexpr int SLICE = BS * BS * Fmt<F>::EB;         // bytes of one slice
   static constexpr int ASLOTS = (DPG - 1) + G * DPG;         // zero pad + slices + pad
-  static constexpr int BSLOTS = S;
+  static constexpr int BSLOTS = NP * S;                      // B slices (a pair interleaved)
   static constexpr int STAGE = (ASLOTS + BSLOTS) * SLICE;
-  static constexpr int CROW = BS + 4;                        // padded int32 row (combine)
+  static constexpr int NTEAM = NP == 2 ? 1 : 2;              // epilogue teams
+  static constexpr int CROW = NP * BS + 4;                   // padded int32 row (combine)
   static constexpr int COMB = S * BS * CROW * 4;             // combine buffer bytes (per team)
   // ring depth: up to 4 (bs 32) / 8 (bs 16) stages within 227 KiB of shared
   // memory, 8 KiB of it left for the static barriers and descriptor ring
-  static constexpr int BUDGET = 227 * 1024 - 8 * 1024 - 2 * COMB;
+  static constexpr int BUDGET = 227 * 1024 - 8 * 1024 - NTEAM * COMB;
   static constexpr int NSTMAX = BS == 32 ? (F ? 6 : 4) : 8;
   static constexpr int NST = BUDGET / STAGE < NSTMAX ? BUDGET / STAGE : NSTMAX;
-  static constexpr int SMEM = NST * STAGE + 2 * COMB;
+  static constexpr int SMEM = NST * STAGE + NTEAM * COMB;
   static_assert(NST >= 2, "shared memory too small for two stages");
   static constexpr uint32_t SBO = BS * 8 * Fmt<F>::EB;       // 8-row group stride
   static constexpr uint32_t LBO = 128;                       // K core-matrix stride
@@ -195,10 +199,14 @@ __device__ __forceinline__ uint32_t small_int_to_e4m3(int v) {
 // operand rows = block columns, K = block rows, column scales.  A CTA stages
 // one block in shared memory; each thread makes one core-matrix row (16 bytes
 // per slice), so a warp writes 512 contiguous bytes per slice.
+// pslot (B only, NULL otherwise): the pair slot of each block; the slices of
+// the two sibling blocks (I, 2y), (I, 2y+1) of a slot are then interleaved,
+// slice i of the even sibling at 2i, of the odd one at 2i+1.
 template <int BS, int S, int TRANS, int F>
 __global__ void __launch_bounds__(128) k_slice(const double *__restrict__ vals,
                                                const uint64_t *__restrict__ keys, int64_t n,
                                                const int *__restrict__ exps,
+                                               const int32_t *__restrict__ pslot,
                                                uint8_t *__restrict__ out) {
   using C = Cfg<BS, S, F>;
   constexpr int B = Fmt<F>::BETA;
@@ -231,10 +239,12 @@ __global__ void __launch_bounds__(128) k_slice(const double *__restrict__ vals,
         }
       }
       const uint32_t off = (mrow >> 3) * C::SBO + kg * 128 + (mrow & 7) * 16;  // bytes
-      uint8_t *base = out + t * (int64_t)S * C::SLICE;
+      uint8_t *base = pslot ? out + ((int64_t)pslot[t] * 2 * S + (key & 1)) * C::SLICE
+                            : out + t * (int64_t)S * C::SLICE;
+      const int64_t step = pslot ? 2 * C::SLICE : C::SLICE;
 #pragma unroll
       for (int i = 0; i < S; i++)
-        *reinterpret_cast<uint4 *>(base + (size_t)i * C::SLICE + off) =
+        *reinterpret_cast<uint4 *>(base + i * step + off) =
             make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
     }
     __syncthreads();
@@ -243,13 +253,20 @@ __global__ void __launch_bounds__(128) k_slice(const double *__restrict__ vals,
 
 template <int BS, int S, int F>
 void launch_slices(bsm_matrix A, bsm_matrix B, const int *rowexp, const int *colexp,
-                   uint8_t *asl, uint8_t *bsl, cudaStream_t s) {
+                   uint8_t *asl, uint8_t *bsl, const int32_t *bslot, cudaStream_t s) {
   auto grid = [](int64_t n) { return (unsigned)(n < 152 * 16 ? n : 152 * 16); };
   count_launch(2);
   if (A->nblk)
-    k_slice<BS, S, 0, F><<<grid(A->nblk), 128, 0, s>>>(A->vals, A->keys, A->nblk, rowexp, asl);
+    k_slice<BS, S, 0, F><<<grid(A->nblk), 128, 0, s>>>(A->vals, A->keys, A->nblk, rowexp,
+                                                        nullptr, asl);
   if (B->nblk)
-    k_slice<BS, S, 1, F><<<grid(B->nblk), 128, 0, s>>>(B->vals, B->keys, B->nblk, colexp, bsl);
+    k_slice<BS, S, 1, F><<<grid(B->nblk), 128, 0, s>>>(B->vals, B->keys, B->nblk, colexp,
+                                                        bslot, bsl);
+}
+
+// Slice counts with a compiled pair kernel (32-wide blocks): BF16 6..8, E4M3 8, 12.
+inline bool pair_compiled(int fmt, int slices) {
+  return fmt == 0 ? (slices >= 6 && slices <= 8) : (slices == 8 || slices == 12);
 }
 
 // Slice counts with a compiled kernel: 1..8 for BF16, {2,3,4,6,8,12} for E4M3.
@@ -260,11 +277,12 @@ inline bool spec_compiled(int fmt, int slices) {
 
 template <int BS>
 void launch_slices_s(bsm_matrix A, bsm_matrix B, const int *rowexp, const int *colexp,
-                     uint8_t *asl, uint8_t *bsl, int fmt, int slices, cudaStream_t s) {
-#define BSM_SL(F, S)                                             \
-  if (fmt == F && slices == S) {                                 \
-    launch_slices<BS, S, F>(A, B, rowexp, colexp, asl, bsl, s); \
-    return;                                                      \
+                     uint8_t *asl, uint8_t *bsl, const int32_t *bslot, int fmt, int slices,
+                     cudaStream_t s) {
+#define BSM_SL(F, S)                                                    \
+  if (fmt == F && slices == S) {                                        \
+    launch_slices<BS, S, F>(A, B, rowexp, colexp, asl, bsl, bslot, s); \
+    return;                                                             \
   }
   BSM_SL(0, 1) BSM_SL(0, 2) BSM_SL(0, 3) BSM_SL(0, 4) BSM_SL(0, 5) BSM_SL(0, 6) BSM_SL(0, 7)
   BSM_SL(0, 8)
@@ -363,14 +381,15 @@ __device__ __forceinline__ int32_t f32_int_exact(uint32_t b) {
 // The exponent arrays are read with 16-byte vector loads: keep them first in
 // a 16-byte aligned struct whose size is a multiple of 16.
 struct __align__(16) Meta {
-  int64_t c;            // C block index within its product
+  int64_t c;            // C block index within its product (pairs: the even sibling, or -1)
+  int64_t c1;           // pairs: the odd sibling, or -1
   uint64_t key;
   double *cv;           // the product's C blocks
   int32_t *nz;          // the product's nonzero flags
   const int *rowexp;    // the product's row / column scale exponents
   const int *colexp;
   int32_t nk;
-  int32_t pad[3];
+  int32_t pad[1];
 };
 static_assert(sizeof(Meta) % 16 == 0, "Meta alignment");
 constexpr int kMeta = 8;
@@ -423,33 +442,37 @@ __device__ __forceinline__ double split_to_double(int64_t hi, int64_t lo, int X)
   return split_to_double_slow(hi, lo, T, X);
 }
 
-constexpr int kTeamWarps = 8;                // warps per epilogue team (2 per lane quadrant)
-constexpr int kTeam = kTeamWarps * 32;       // threads per epilogue team
-constexpr int kEpiWarps = 2 * kTeamWarps;    // two teams
+constexpr int kEpiWarps = 16;                // epilogue warps (4 per lane quadrant)
 constexpr int kProdWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
 constexpr int kThreads = (kEpiWarps + 2) * 32;
 
-template <int BS, int S, int F>
+template <int BS, int S, int F, int NP>
 __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
-  using C = Cfg<BS, S, F>;
+  using C = Cfg<BS, S, F, NP>;
   constexpr int DPG = C::DPG;
   constexpr int G = C::G;
+  constexpr int NTEAM = C::NTEAM;
+  constexpr int kTeamWarps = kEpiWarps / NTEAM;  // 8 (two teams) or 16 (one)
+  constexpr int kTeam = kTeamWarps * 32;         // threads per epilogue team
+  constexpr int NB = NP * BS;                    // MMA N: output columns per item
   constexpr int BETA = Fmt<F>::BETA, TS = Fmt<F>::TSPLIT;
-  constexpr uint32_t IDESC = F == 0 ? idesc_bf16_f32(128, BS) : idesc_e4m3_f32(128, BS);
-  // TMEM accumulators: each team owns NBUF buffers of G*BS columns, two when
-  // they fit in the 256 columns we allocate, so that the MMAs of a C block's
+  constexpr uint32_t IDESC = F == 0 ? idesc_bf16_f32(128, NB) : idesc_e4m3_f32(128, NB);
+  // TMEM accumulators: each team owns NBUF buffers of G*NB columns, two when
+  // they fit in the 256 columns we allocate, so that the MMAs of an item's
   // next flush run while the team drains the previous one
-  constexpr int NBUF = 4 * G * BS <= 256 ? 2 : 1;
-  constexpr int TCOLS = 2 * NBUF * G * BS;
+  constexpr int NBUF = NTEAM * 2 * G * NB <= 256 ? 2 : 1;
+  constexpr int TCOLS = NTEAM * NBUF * G * NB;
+  static_assert(TCOLS <= 256, "TMEM columns");
   constexpr int NCOLS = TCOLS <= 32 ? 32 : (TCOLS <= 64 ? 64 : (TCOLS <= 128 ? 128 : 256));
-  constexpr uint32_t BYTES = (uint32_t)S * C::SLICE;  // one operand's slices
+  constexpr uint32_t BYTES = (uint32_t)S * C::SLICE;          // one A block's slices
+  constexpr uint32_t BYTES_B = (uint32_t)NP * S * C::SLICE;   // B block (pair) slices
   extern __shared__ __align__(1024) uint8_t smem[];
   // tfull / tempty: per (team, buffer), index 2 * team + buffer
   __shared__ __align__(8) uint64_t full[C::NST], empty[C::NST], tfull[4], tempty[4], done;
   __shared__ __align__(8) uint64_t meta_full[kMeta], meta_empty[kMeta];
   __shared__ Meta meta[kMeta];
   __shared__ uint32_t tmem_base_sh;
-  __shared__ int warp_any[2][kTeamWarps];
+  __shared__ int warp_any[2][2][16];  // [team][block of the item][warp]
   __shared__ volatile int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -499,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
     bool pend[C::NST] = {};
     uint32_t ppar[C::NST] = {};
     bool stop = false;
-    auto put_meta = [&](int64_t c, uint64_t key, int nk, const ProdDesc *pd) -> bool {
+    auto put_meta = [&](int64_t c, int64_t c1, uint64_t key, int nk, const ProdDesc *pd) -> bool {
       const int m = q % kMeta;
       int okw = 1;
       if (lane == 0) {
@@ -509,6 +532,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
           abort_flag = 1;
         } else {
           meta[m].c = c;
+          meta[m].c1 = c1;
           meta[m].key = key;
           meta[m].cv = pd ? pd->cv : nullptr;
           meta[m].nz = pd ? pd->nz : nullptr;
@@ -535,6 +559,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
       int pi = 0;
       int64_t ci = 0;
       int32_t s0 = 0, s1 = 0;
+      int64_t e0 = 0, e1 = -1;  // the item's C blocks (e1: a pair's odd sibling)
       uint64_t key = 0;
       if (lane < n) {
         if (P.items) {
@@ -548,15 +573,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         s0 = pd->seg[ci];
         s1 = pd->seg[ci + 1];
         key = pd->ckeys[ci];
+        if (NP == 2) {
+          e0 = pd->pairc[2 * ci];
+          e1 = pd->pairc[2 * ci + 1];
+        } else {
+          e0 = ci;
+        }
       }
       for (int i = 0; i < n && !stop; i++) {
         const int p = __shfl_sync(0xffffffffu, pi, i);
         const ProdDesc *pd = &P.prods[p];
-        const int64_t c = __shfl_sync(0xffffffffu, ci, i);
+        const int64_t c = __shfl_sync(0xffffffffu, e0, i);
+        const int64_t c1 = __shfl_sync(0xffffffffu, e1, i);
         const uint64_t kk = __shfl_sync(0xffffffffu, key, i);
         const int32_t k0 = __shfl_sync(0xffffffffu, s0, i);
         const int32_t nk = __shfl_sync(0xffffffffu, s1, i) - k0;
-        if (!put_meta(c, kk, nk, pd)) {
+        if (!put_meta(c, c1, kk, nk, pd)) {
           stop = true;
           break;
         }
@@ -588,9 +620,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
                 set_err(P.err, DERR_BOUNDS);  // complete the stage without data
                 mbar_arrive(&full[st]);
               } else {
-                mbar_expect_tx(&full[st], 2 * BYTES);
+                mbar_expect_tx(&full[st], BYTES + BYTES_B);
                 bulk_g2s(sa + (DPG - 1) * C::SLICE, asl + (int64_t)aa * BYTES, BYTES, &full[st]);
-                bulk_g2s(sb, bsl + (int64_t)bb * BYTES, BYTES, &full[st]);
+                bulk_g2s(sb, bsl + (int64_t)bb * BYTES_B, BYTES_B, &full[st]);
               }
             }
           }
@@ -601,11 +633,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         }
       }
     }
-    // two end markers: one for the MMA thread and each epilogue team
-    if (!stop) {
-      put_meta(-1, 0, -1, nullptr);
-      put_meta(-1, 0, -1, nullptr);
-    }
+    // end markers: one for the MMA thread and each epilogue team (the MMA
+    // thread stops at the first)
+    if (!stop)
+      for (int t = 0; t < NTEAM; t++) put_meta(-1, -1, 0, -1, nullptr);
     // copies still in flight must land before the CTA exits
     if (lane == 0)
       for (int st = 0; st < C::NST; st++)
@@ -614,7 +645,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
     // ---------------------------------------------------------- MMA issuer
     if (lane == 0) {
       uint32_t it = 0, q = 0;
-      uint32_t fcb0 = 0, fcb1 = 0;  // flushes issued into TMEM buffer 0 / 1
+      uint32_t fcb0 = 0, fcb1 = 0;  // flushes issued for team 0 / 1
       const uint32_t sbase = smem_u32(stages);
       for (;; q++) {
         int m = q % kMeta;
@@ -628,7 +659,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         if (nk < 0 || abort_flag) break;  // end marker
         const FlushPlan fp = flush_plan(nk, P.flushk, P.flushk_wide);
         const int nfl = fp.nfl;
-        const int b = q & 1;  // C blocks alternate between the two teams / buffers
+        const int b = q % NTEAM;  // items alternate between the teams
         for (int f = 0; f < nfl && !abort_flag; f++) {
           const uint32_t fb = b ? fcb1 : fcb0;
           if (b) fcb1++; else fcb0++;
@@ -656,7 +687,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
             const uint32_t first = (j == f * fp.fk) ? 0u : 1u;
 #pragma unroll
             for (int g = 0; g < G; g++) {
-              const uint32_t dt = tbase + (uint32_t)(((b * NBUF + u) * G + g) * BS);
+              const uint32_t dt = tbase + (uint32_t)(((b * NBUF + u) * G + g) * NB);
 #pragma unroll
               for (int t = 0; t < S; t++) {
                 if (t >= (g + 1) * DPG) break;  // K-blocks of group g: t < min(S, (g+1) DPG)
@@ -664,7 +695,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
                 for (int h = 0; h < BS / Fmt<F>::KPI; h++) {
                   // one instruction's K = two core matrices = 256 bytes
                   const uint64_t aoff = (uint64_t)(((DPG - 1 + g * DPG - t) * C::SLICE + h * 256) >> 4);
-                  const uint64_t boff = (uint64_t)((t * C::SLICE + h * 256) >> 4);
+                  // B K-block t: slice t of one block, or of both blocks of a
+                  // pair side by side (N rows 0..bs-1 and bs..2bs-1)
+                  const uint64_t boff = (uint64_t)((NP * t * C::SLICE + h * 256) >> 4);
                   if (F == 0)
                     tc_mma_bf16(dt, ad0 + aoff, bd0 + boff, IDESC, (t | h) ? 1u : first);
                   else
@@ -683,14 +716,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
     }
   } else {
     // ----------------------------------------------------------- epilogue
-    // Two teams of eight warps take alternate C blocks (team t: local C-block
-    // index q with q % 2 == t) and TMEM buffer t.  Warp w of a team drains
-    // lane quadrant w % 4, columns [(w / 4) BS/2, +BS/2), and accumulates the
-    // exact diagonal sums straight into the team's shared-memory buffer
-    // [d][r][c]; the team then combines the diagonals of each output element.
-    // One team's recombination overlaps the other team's drain and the MMAs.
-    constexpr int HC = BS / 2;
-    constexpr int NG4 = BS * BS / 4;                // 4-column groups per C block
+    // Single C blocks: two teams of eight warps take alternate items (team t:
+    // local item index q with q % 2 == t) and their own TMEM buffers; pairs:
+    // one team of sixteen warps.  Warp w of a team drains lane quadrant w % 4,
+    // a slice of HC columns, and accumulates the exact diagonal sums straight
+    // into the team's shared-memory buffer [d][r][c]; the team then combines
+    // the diagonals of each output element.  With two teams one team's
+    // recombination overlaps the other team's drain and the MMAs.
+    constexpr int HC = NB / (kTeamWarps / 4);       // 16 columns per warp at bs 32
+    constexpr int NG4 = NB * BS / 4;                // 4-column groups per item
     constexpr int GRP = (NG4 + kTeam - 1) / kTeam;  // combine: groups per thread
     const int team = warp / kTeamWarps, tw = warp % kTeamWarps, ttid = tid % kTeam;
     const int wq = tw & 3;
@@ -701,7 +735,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
     int32_t *tcomb = comb + team * (C::COMB / 4);
     const int bar_id = 1 + team;
     uint32_t fct = 0;                     // flushes drained by this team
-    for (uint32_t q = team;; q += 2) {
+    for (uint32_t q = team;; q += NTEAM) {
       int m = q % kMeta;
       bool okm = mbar_wait(&meta_full[m], (q / kMeta) & 1u);
       // every decision below is uniform across the warp (tcgen05.ld is
@@ -712,7 +746,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         break;
       }
       const int nk = meta[m].nk;
-      const int64_t c = meta[m].c;
+      const int64_t cblk[2] = {meta[m].c, meta[m].c1};
       double *const cvp = meta[m].cv;
       int32_t *const nzp = meta[m].nz;
       const uint64_t ckey = meta[m].key;
@@ -720,8 +754,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
       mbar_arrive(&meta_empty[m]);
       if (nk < 0) break;  // end marker
       // scale exponents of this thread's output elements (thread handles
-      // columns 4*(g4 % (BS/4)) .. +3 of row g4 / (BS/4), g4 = ttid + i kTeam),
-      // loaded here so that their latency hides behind the first flush
+      // item columns 4*(g4 % (NB/4)) .. +3 of row g4 / (NB/4), g4 = ttid + i
+      // kTeam; for a pair the columns continue into the odd sibling, whose
+      // block column follows), loaded here so that their latency hides behind
+      // the first flush
       const int64_t crow = (int64_t)morton_compact(ckey >> 1) * BS;
       const int64_t ccol = (int64_t)morton_compact(ckey) * BS;
       int erow[GRP];
@@ -729,13 +765,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
 #pragma unroll
       for (int i = 0; i < GRP; i++) {
         const int g4 = min(ttid + i * kTeam, NG4 - 1);
-        erow[i] = rowexp[crow + g4 / (BS / 4)];
-        fcol[i] = *reinterpret_cast<const int4 *>(colexp + ccol + (g4 % (BS / 4)) * 4);
+        erow[i] = rowexp[crow + g4 / (NB / 4)];
+        fcol[i] = *reinterpret_cast<const int4 *>(colexp + ccol + (g4 % (NB / 4)) * 4);
       }
       const FlushPlan fplan = flush_plan(nk, P.flushk, P.flushk_wide);
       const int nfl = fplan.nfl, kf = fplan.kf;
       const bool wide = fplan.wide;
-      int64_t *const fold = P.fold + ((int64_t)blockIdx.x * 2 + team) * (BS * BS * 2);
+      int64_t *const fold = P.fold + ((int64_t)blockIdx.x * 2 + team) * (NB * BS * 2);
       bool ok = true;
       // Every warp runs all nfl iterations (doing no work once `ok` is false)
       // so that the team meets the same fold barriers whatever happened.
@@ -754,9 +790,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
           for (int g = 0; g < G; g++) {
             uint32_t v[HC];
             if constexpr (HC == 16)
-              tmem_ld16(tbase + lane_addr + (uint32_t)(((team * NBUF + fct % NBUF) * G + g) * BS + c0), v);
+              tmem_ld16(tbase + lane_addr + (uint32_t)(((team * NBUF + fct % NBUF) * G + g) * NB + c0), v);
             else
-              tmem_ld8(tbase + lane_addr + (uint32_t)(((team * NBUF + fct % NBUF) * G + g) * BS + c0), v);
+              tmem_ld8(tbase + lane_addr + (uint32_t)(((team * NBUF + fct % NBUF) * G + g) * NB + c0), v);
             tmem_ld_wait();
             const int d = g * DPG + L;
             if (d < S) {
@@ -800,7 +836,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
             for (int i = 0; i < GRP; i++) {
               const int g4 = ttid + i * kTeam;
               if (NG4 % kTeam != 0 && g4 >= NG4) break;
-              const int rr = g4 / (BS / 4), c4 = (g4 % (BS / 4)) * 4;
+              const int rr = g4 / (NB / 4), c4 = (g4 % (NB / 4)) * 4;
               int4 dv[S];
 #pragma unroll
               for (int d = 0; d < S; d++)
@@ -813,7 +849,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
                   dg[d] = x == 0 ? dv[d].x : x == 1 ? dv[d].y : x == 2 ? dv[d].z : dv[d].w;
                 int64_t hi, lo;
                 combine_digits<S, BETA, TS>(dg, hi, lo);
-                int64_t *fp = fold + (rr * BS + c4 + x) * 2;
+                int64_t *fp = fold + (rr * NB + c4 + x) * 2;
                 if (f + 1 > kf) {
                   hi += fp[0];
                   lo += fp[1];
@@ -829,14 +865,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         }
       }
       if (named_bar_or(bar_id, kTeam, !ok || abort_flag != 0)) break;
-      double *cb = cvp + c * (int64_t)BS * BS;
-      bool any = false;
+      bool any[2] = {false, false};
       constexpr int XS = BETA * (S + 1);
 #pragma unroll
       for (int i = 0; i < GRP; i++) {
         const int g4 = ttid + i * kTeam;
         if (NG4 % kTeam != 0 && g4 >= NG4) break;  // bs 16: part of the team idles here
-        const int rr = g4 / (BS / 4), c4 = (g4 % (BS / 4)) * 4;
+        const int rr = g4 / (NB / 4), c4 = (g4 % (NB / 4)) * 4;
+        const int blk = c4 / BS, cc = c4 % BS;     // C block of the item, its column
         int4 dv[S];
 #pragma unroll
         for (int d = 0; d < S; d++)
@@ -850,26 +886,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
           int64_t hi, lo;
           combine_digits<S, BETA, TS>(dg, hi, lo);
           if (nfl > kf) {
-            const int64_t *fp = fold + (rr * BS + c4 + x) * 2;
+            const int64_t *fp = fold + (rr * NB + c4 + x) * 2;
             hi += fp[0];
             lo += fp[1];
           }
           const int fx = x == 0 ? fcol[i].x : x == 1 ? fcol[i].y : x == 2 ? fcol[i].z : fcol[i].w;
           out[x] = split_to_double<TS>(hi, lo, erow[i] + fx - XS);
-          any |= nonzero_f64(out[x]);
+          any[blk] |= nonzero_f64(out[x]);
         }
-        double2 *dst = reinterpret_cast<double2 *>(cb + rr * BS + c4);
-        dst[0] = make_double2(out[0], out[1]);
-        dst[1] = make_double2(out[2], out[3]);
+        if (cblk[blk] >= 0) {  // a pair's absent sibling is computed as zero and dropped
+          double2 *dst = reinterpret_cast<double2 *>(cvp + cblk[blk] * (int64_t)BS * BS + rr * BS + cc);
+          dst[0] = make_double2(out[0], out[1]);
+          dst[1] = make_double2(out[2], out[3]);
+        }
       }
-      any = __any_sync(0xffffffffu, any);
-      if (lane == 0) warp_any[team][tw] = any;
-      named_bar(bar_id, kTeam);  // warp_any complete; shared buffer free for the next block
-      if (ttid == 0) {
-        int nzv = 0;
 #pragma unroll
-        for (int w = 0; w < kTeamWarps; w++) nzv |= warp_any[team][w];
-        nzp[c] = nzv;
+      for (int b = 0; b < NP; b++) {
+        const bool a = __any_sync(0xffffffffu, any[b]);
+        if (lane == 0) warp_any[team][b][tw] = a;
+      }
+      named_bar(bar_id, kTeam);  // warp_any complete; shared buffer free for the next item
+      if (ttid == 0) {
+#pragma unroll
+        for (int b = 0; b < NP; b++) {
+          int nzv = 0;
+          for (int w = 0; w < kTeamWarps; w++) nzv |= warp_any[team][b][w];
+          if (cblk[b] >= 0) nzp[cblk[b]] = nzv;
+        }
       }
     }
   }
@@ -882,12 +925,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
 
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-template <int BS, int S, int F>
+template <int BS, int S, int F, int NP>
 bsm_status launch_split(const SplitArgs &a, cudaStream_t s) {
-  using C = Cfg<BS, S, F>;
+  using C = Cfg<BS, S, F, NP>;
   static bool attr = false;
   if (!attr) {
-    BSM_CUDA(cudaFuncSetAttribute(k_numeric_split<BS, S, F>,
+    BSM_CUDA(cudaFuncSetAttribute(k_numeric_split<BS, S, F, NP>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     attr = true;
   }
@@ -899,21 +942,95 @@ bsm_status launch_split(const SplitArgs &a, cudaStream_t s) {
   if (grid < 1) return BSM_OK;
   if (!a.fold) return BSM_ERR_INVALID_ARG;  // sized by split_fold_bytes: grid <= SM count
   count_launch();
-  k_numeric_split<BS, S, F><<<(unsigned)grid, kThreads, C::SMEM, s>>>(a);
+  k_numeric_split<BS, S, F, NP><<<(unsigned)grid, kThreads, C::SMEM, s>>>(a);
   return cuda_status(cudaGetLastError());
 }
 
 template <int BS>
-bsm_status launch_split_s(const SplitArgs &a, int fmt, int slices, cudaStream_t s) {
+bsm_status launch_split_s(const SplitArgs &a, int fmt, int slices, int np, cudaStream_t s) {
 #define BSM_LS(F, S) \
-  if (fmt == F && slices == S) return launch_split<BS, S, F>(a, s);
+  if (np == 1 && fmt == F && slices == S) return launch_split<BS, S, F, 1>(a, s);
+#define BSM_LP(F, S) \
+  if (np == 2 && fmt == F && slices == S) return launch_split<BS, S, F, 2>(a, s);
   BSM_LS(0, 1) BSM_LS(0, 2) BSM_LS(0, 3) BSM_LS(0, 4) BSM_LS(0, 5) BSM_LS(0, 6) BSM_LS(0, 7)
   BSM_LS(0, 8)
   if constexpr (BS == 32) {
     BSM_LS(1, 2) BSM_LS(1, 3) BSM_LS(1, 4) BSM_LS(1, 6) BSM_LS(1, 8) BSM_LS(1, 12)
+    BSM_LP(0, 6) BSM_LP(0, 7) BSM_LP(0, 8) BSM_LP(1, 8) BSM_LP(1, 12)
   }
 #undef BSM_LS
+#undef BSM_LP
   return BSM_ERR_INVALID_ARG;
+}
+
+// ----------------------------------------------------------- pair items
+// Siblings: keys that differ only in bit 0 (the block column's lowest bit).
+__global__ void k_pair_heads(const uint64_t *__restrict__ keys, int64_t n,
+                             int32_t *__restrict__ head) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  head[i] = i == 0 || (keys[i] >> 1) != (keys[i - 1] >> 1);
+}
+
+// Pair index of every key; optionally pairc[2 p + (key & 1)] = i and the
+// pair's even key.
+__global__ void k_pair_assign(const uint64_t *__restrict__ keys, int64_t n,
+                              const int32_t *__restrict__ head, const int32_t *__restrict__ hpos,
+                              int32_t *__restrict__ slot, int32_t *__restrict__ pairc,
+                              uint64_t *__restrict__ pkeys) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t p = hpos[i] + head[i] - 1;
+  if (slot) slot[i] = p;
+  if (pairc) pairc[2 * (int64_t)p + (keys[i] & 1)] = (int32_t)i;
+  if (pkeys && head[i]) pkeys[p] = keys[i] & ~1ull;
+}
+
+__device__ __forceinline__ uint32_t row_of(const uint64_t *bkeys, int32_t b) {
+  return morton_compact(bkeys[b] >> 1);
+}
+
+// Merged product list of each C pair: the union over K of the two siblings'
+// lists (both sorted by K); an entry is (A block, B pair slot).  write = 0:
+// count only.
+__global__ void k_pair_merge(const int32_t *__restrict__ pairc, int64_t npairs,
+                             const int32_t *__restrict__ seg, const int32_t *__restrict__ ta,
+                             const int32_t *__restrict__ tb, const uint64_t *__restrict__ bkeys,
+                             const int32_t *__restrict__ bslot, int32_t *__restrict__ cnt,
+                             const int32_t *__restrict__ mseg, int32_t *__restrict__ mta,
+                             int32_t *__restrict__ mtb, int write) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  const int32_t c0 = pairc[2 * p], c1 = pairc[2 * p + 1];
+  int32_t i0 = c0 >= 0 ? seg[c0] : 0, e0 = c0 >= 0 ? seg[c0 + 1] : 0;
+  int32_t i1 = c1 >= 0 ? seg[c1] : 0, e1 = c1 >= 0 ? seg[c1 + 1] : 0;
+  int32_t o = write ? mseg[p] : 0, n = 0;
+  while (i0 < e0 || i1 < e1) {
+    int32_t a, b;
+    if (i1 >= e1) {
+      a = ta[i0];
+      b = tb[i0++];
+    } else if (i0 >= e0) {
+      a = ta[i1];
+      b = tb[i1++];
+    } else {
+      const uint32_t k0 = row_of(bkeys, tb[i0]), k1 = row_of(bkeys, tb[i1]);
+      if (k0 <= k1) {
+        a = ta[i0];
+        b = tb[i0++];
+        if (k0 == k1) i1++;  // same A block, sibling B block of the same slot
+      } else {
+        a = ta[i1];
+        b = tb[i1++];
+      }
+    }
+    if (write) {
+      mta[o + n] = a;
+      mtb[o + n] = bslot[b];
+    }
+    n++;
+  }
+  if (!write) cnt[p] = n;
 }
 
 }  // namespace
@@ -946,7 +1063,8 @@ size_t split_fold_bytes(int bs) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return (size_t)(sms > 0 ? sms : 1) * 2 * bs * bs * 2 * sizeof(int64_t);
+  // per CTA and team: (hi, lo) for every output of an item (a pair: 2 bs^2)
+  return (size_t)(sms > 0 ? sms : 1) * 2 * bs * (2 * bs) * 2 * sizeof(int64_t);
 }
 
 bsm_status split_supported(int bs, int spec) {
@@ -989,7 +1107,7 @@ bsm_status split_alloc(bsm_matrix A, bsm_matrix B, int spec, ProdDesc &d,
 // Computes the exponents and slices into the buffers of `d` (no allocation;
 // may be captured in a CUDA graph).
 bsm_status split_compute(bsm_matrix A, bsm_matrix B, int spec, const ProdDesc &d,
-                         unsigned *errword, cudaStream_t s) {
+                         unsigned *errword, cudaStream_t s, const int32_t *bslot) {
   const int fmt = split_spec_fmt(spec), slices = split_spec_slices(spec);
   const int bs = A->bs;
   int *rowexp = const_cast<int *>(d.rowexp), *colexp = const_cast<int *>(d.colexp);
@@ -1006,9 +1124,9 @@ bsm_status split_compute(bsm_matrix A, bsm_matrix B, int spec, const ProdDesc &d
   }
   uint8_t *asl = const_cast<uint8_t *>(d.asl), *bsl = const_cast<uint8_t *>(d.bsl);
   if (bs == 16)
-    launch_slices_s<16>(A, B, rowexp, colexp, asl, bsl, fmt, slices, s);
+    launch_slices_s<16>(A, B, rowexp, colexp, asl, bsl, bslot, fmt, slices, s);
   else
-    launch_slices_s<32>(A, B, rowexp, colexp, asl, bsl, fmt, slices, s);
+    launch_slices_s<32>(A, B, rowexp, colexp, asl, bsl, bslot, fmt, slices, s);
   return cuda_status(cudaGetLastError());
 }
 
@@ -1027,7 +1145,7 @@ bsm_status split_prepare(bsm_matrix A, bsm_matrix B, int slices, unsigned *errwo
 
 bsm_status split_launch(int bs, int spec, const ProdDesc *prods_dev, const uint64_t *items,
                         int64_t nitems, unsigned long long *work, unsigned *errword,
-                        int64_t *fold, cudaStream_t s, int chunk) {
+                        int64_t *fold, cudaStream_t s, int chunk, int np) {
   const int fmt = split_spec_fmt(spec), slices = split_spec_slices(spec);
   SplitArgs a;
   a.fold = fold;
@@ -1039,7 +1157,8 @@ bsm_status split_launch(int bs, int spec, const ProdDesc *prods_dev, const uint6
   a.flushk_wide = split_flush_group(bs, spec, 24);
   a.err = errword;
   a.work = work;
-  return bs == 16 ? launch_split_s<16>(a, fmt, slices, s) : launch_split_s<32>(a, fmt, slices, s);
+  return bs == 16 ? launch_split_s<16>(a, fmt, slices, np, s)
+                  : launch_split_s<32>(a, fmt, slices, np, s);
 }
 
 ProdDesc make_desc(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, double *cvals,
@@ -1060,11 +1179,154 @@ ProdDesc make_desc(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, double
   return d;
 }
 
+// Pair items (two sibling C blocks per MMA, N = 2 bs) for long product lists:
+// each A tile then serves twice the outputs.  BSM_SPLIT_PAIRS=0 / 1 in the
+// environment turns them off / on regardless of the list length.
+static bool use_pairs(int bs, int spec, const SymbolicResult &sym) {
+  if (bs != 32 || !pair_compiled(split_spec_fmt(spec), split_spec_slices(spec))) return false;
+  const char *e = getenv("BSM_SPLIT_PAIRS");
+  if (e && e[0] == '0') return false;
+  if (e && e[0] == '1') return true;
+  return sym.nc > 0 && sym.nt >= 16 * sym.nc;
+}
+
+// The numeric phase over pairs of sibling C blocks: B pair slots, merged
+// product lists per C pair, B slices in pair slots, one launch.
+static bsm_status numeric_split_pairs(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym,
+                                      int spec, double *cvals, int32_t *nzflag, unsigned *errword,
+                                      cudaStream_t s) {
+  const int bs = A->bs, fmt = split_spec_fmt(spec);
+  const int64_t slices = split_spec_slices(spec), eb = fmt == 0 ? 2 : 1;
+  const int64_t nb = B->nblk, nc = sym.nc;
+  std::vector<void *> owned;
+  auto cleanup = [&]() {
+    for (void *p : owned) dev_free(p, s);  // stream-ordered: after the kernel
+  };
+  auto grab = [&](void **p, size_t bytes) -> bsm_status {
+    bsm_status r = dev_alloc(p, bytes > 0 ? bytes : 16, s);
+    if (r == BSM_OK) owned.push_back(*p);
+    return r;
+  };
+  int64_t *h = (int64_t *)host_scratch().get(sizeof(ProdDesc) + 64);
+  if (!h) return BSM_ERR_OOM;
+  int32_t *bhead, *bpos, *bslot, *chead, *cpos, *pairc, *cnt, *mseg, *mta, *mtb;
+  uint64_t *pkeys;
+  bsm_status st;
+  // B pair slots
+  if ((st = grab((void **)&bhead, 4 * nb)) || (st = grab((void **)&bpos, 4 * nb)) ||
+      (st = grab((void **)&bslot, 4 * nb)) || (st = grab((void **)&chead, 4 * nc)) ||
+      (st = grab((void **)&cpos, 4 * nc))) {
+    cleanup();
+    return st;
+  }
+  count_launch(4);
+  k_pair_heads<<<grid_for(nb, 256), 256, 0, s>>>(B->keys, nb, bhead);
+  k_pair_heads<<<grid_for(nc, 256), 256, 0, s>>>(sym.ckeys, nc, chead);
+  if ((st = scan_exclusive_i32(bhead, bpos, nb, s)) || (st = scan_exclusive_i32(chead, cpos, nc, s))) {
+    cleanup();
+    return st;
+  }
+  int32_t *h32 = (int32_t *)h;
+  cudaMemcpyAsync(h32 + 0, bpos + nb - 1, 4, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(h32 + 1, bhead + nb - 1, 4, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(h32 + 2, cpos + nc - 1, 4, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(h32 + 3, chead + nc - 1, 4, cudaMemcpyDeviceToHost, s);
+  if ((st = cuda_status(cudaStreamSynchronize(s))) != BSM_OK) {
+    cleanup();
+    return st;
+  }
+  const int64_t npb = (int64_t)h32[0] + h32[1], npc = (int64_t)h32[2] + h32[3];
+  if ((st = grab((void **)&pairc, 8 * npc)) || (st = grab((void **)&pkeys, 8 * npc)) ||
+      (st = grab((void **)&cnt, 4 * (npc + 1))) || (st = grab((void **)&mseg, 4 * (npc + 1)))) {
+    cleanup();
+    return st;
+  }
+  cudaMemsetAsync(pairc, 0xFF, 8 * npc, s);  // -1: absent sibling
+  cudaMemsetAsync(cnt + npc, 0, 4, s);
+  k_pair_assign<<<grid_for(nb, 256), 256, 0, s>>>(B->keys, nb, bhead, bpos, bslot, nullptr,
+                                                  nullptr);
+  k_pair_assign<<<grid_for(nc, 256), 256, 0, s>>>(sym.ckeys, nc, chead, cpos, nullptr, pairc,
+                                                  pkeys);
+  k_pair_merge<<<grid_for(npc, 128), 128, 0, s>>>(pairc, npc, sym.seg, sym.ta, sym.tb, B->keys,
+                                                  bslot, cnt, nullptr, nullptr, nullptr, 0);
+  if ((st = scan_exclusive_i32(cnt, mseg, npc + 1, s)) != BSM_OK) {
+    cleanup();
+    return st;
+  }
+  cudaMemcpyAsync(h32, mseg + npc, 4, cudaMemcpyDeviceToHost, s);
+  if ((st = cuda_status(cudaStreamSynchronize(s))) != BSM_OK) {
+    cleanup();
+    return st;
+  }
+  const int64_t mt = h32[0];
+  if ((st = grab((void **)&mta, 4 * mt)) || (st = grab((void **)&mtb, 4 * mt))) {
+    cleanup();
+    return st;
+  }
+  count_launch(3);
+  k_pair_merge<<<grid_for(npc, 128), 128, 0, s>>>(pairc, npc, sym.seg, sym.ta, sym.tb, B->keys,
+                                                  bslot, nullptr, mseg, mta, mtb, 1);
+  // exponents and slices (B in pair slots; absent siblings stay zero)
+  ProdDesc d = {};
+  int *rowexp, *colexp;
+  uint8_t *asl, *bsl;
+  const size_t slice_bytes = (size_t)eb * bs * bs;
+  // colexp has one spare block column: the odd sibling of a pair in the last
+  // block column reads its (unused) exponents there
+  if ((st = grab((void **)&rowexp, 4 * A->mb * bs)) ||
+      (st = grab((void **)&colexp, 4 * (B->nb + 1) * bs)) ||
+      (st = grab((void **)&asl, slice_bytes * slices * A->nblk)) ||
+      (st = grab((void **)&bsl, slice_bytes * 2 * slices * npb))) {
+    cleanup();
+    return st;
+  }
+  cudaMemsetAsync(bsl, 0, slice_bytes * 2 * slices * npb, s);
+  d.asl = asl;
+  d.bsl = bsl;
+  d.rowexp = rowexp;
+  d.colexp = colexp;
+  if ((st = split_compute(A, B, spec, d, errword, s, bslot)) != BSM_OK) {
+    cleanup();
+    return st;
+  }
+  d.seg = mseg;
+  d.ta = mta;
+  d.tb = mtb;
+  d.ckeys = pkeys;
+  d.cv = cvals;
+  d.nz = nzflag;
+  d.na = A->nblk;
+  d.nb = npb;
+  d.nc = npc;
+  d.nt = mt;
+  d.pairc = pairc;
+  // the product table and the work counter
+  int *scr = nullptr;
+  int64_t *fold = nullptr;
+  if ((st = grab((void **)&scr, 16 + sizeof(ProdDesc))) ||
+      (st = grab((void **)&fold, split_fold_bytes(bs)))) {
+    cleanup();
+    return st;
+  }
+  cudaMemsetAsync(scr, 0, 16, s);
+  memcpy(h, &d, sizeof(ProdDesc));
+  cudaMemcpyAsync(scr + 4, h, sizeof(ProdDesc), cudaMemcpyHostToDevice, s);
+  st = cuda_status(cudaStreamSynchronize(s));  // the host staging buffer is reused
+  if (st == BSM_OK)
+    st = split_launch(bs, spec, reinterpret_cast<const ProdDesc *>(scr + 4), nullptr, npc,
+                      reinterpret_cast<unsigned long long *>(scr + 2), errword, fold, s,
+                      split_chunk_for(mt, npc), 2);
+  cleanup();
+  return st;
+}
+
 bsm_status numeric_split(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, int slices,
                          double *cvals, int32_t *nzflag, unsigned *errword, cudaStream_t s) {
   const int bs = A->bs;
   BSM_TRY(split_supported(bs, slices));
   if (sym.nc == 0) return BSM_OK;
+  if (use_pairs(bs, slices, sym))
+    return numeric_split_pairs(A, B, sym, slices, cvals, nzflag, errword, s);
   std::vector<void *> owned;
   auto cleanup = [&]() {
     for (void *p : owned) dev_free(p, s);  // stream-ordered: after the kernel

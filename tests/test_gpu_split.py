@@ -334,3 +334,74 @@ def test_results_beyond_the_normal_range(e):
         fin = ~inf & np.isfinite(want)
         # compare scaled back down (norms of values near 1e308 overflow)
         assert relerr(np.ldexp(C.vals[fin], -2 * e), np.ldexp(want[fin], -2 * e)) < TOL_SPLIT
+
+
+# ------------------------------------------------- pairs of sibling C blocks
+def with_pairs(flag, fn):
+    import os
+    old = os.environ.get("BSM_SPLIT_PAIRS")
+    os.environ["BSM_SPLIT_PAIRS"] = flag
+    try:
+        return fn()
+    finally:
+        if old is None:
+            os.environ.pop("BSM_SPLIT_PAIRS", None)
+        else:
+            os.environ["BSM_SPLIT_PAIRS"] = old
+
+
+PAIR_MODES = [(bsm.BSM_SPLIT_BF16, 6), (bsm.BSM_SPLIT_BF16, 7), (bsm.BSM_SPLIT_BF16, 8),
+              (bsm.BSM_SPLIT_FP8, 8), (bsm.BSM_SPLIT_FP8, 12)]
+
+
+@pytest.mark.parametrize("prec,slices", PAIR_MODES)
+def test_pairs_equal_single_blocks(prec, slices):
+    """Two sibling C blocks per MMA (N = 64) give the same bits as one block
+    per MMA: the same exact digit sums, rounded once."""
+    A = synth.decay(260, 32, 660)
+    B = synth.random_blocks(A.ncols, 32, 0.3, 661, ncols=A.ncols + 70)  # odd block columns
+    ga, gb = to_bsm(A), to_bsm(B)
+    run = lambda: from_bsm(bsm.bsm_multiply(ga, gb, prec=prec, slices=slices))
+    one = with_pairs("0", run)
+    two = with_pairs("1", run)
+    assert_same_structure(two, one)
+    assert np.array_equal(two.vals, one.vals)
+    E = oracle.multiply(A, B).C
+    assert_same_structure(two, E)
+    bits = slices * (7 if prec == bsm.BSM_SPLIT_BF16 else 4)
+    assert relerr(two.vals, E.vals) < max(TOL_SPLIT, 2.0 ** -(bits - 8))
+
+
+def test_pairs_long_lists_fold_and_chunks():
+    """Pairs with folded accumulations (2000 products per C block) and with the
+    symbolic phase cut into many Morton chunks (siblings in different chunks)."""
+    import os
+    bs, nk = 32, 2000
+    A = synth.random_blocks(bs, bs, 1.0, 670, dist="int8", ncols=bs * nk)
+    B = synth.random_blocks(bs * nk, bs, 1.0, 671, dist="int8", ncols=3 * bs)
+    E = oracle.multiply(A, B).C
+    C = with_pairs("1", lambda: from_bsm(bsm.bsm_multiply(to_bsm(A), to_bsm(B),
+                                                          prec=bsm.BSM_SPLIT_BF16)))
+    assert_same_structure(C, E)
+    assert np.array_equal(C.vals, E.vals)
+    A2 = synth.random_blocks(2000, 32, 0.2, 672)
+    B2 = synth.random_blocks(2000, 32, 0.2, 673)
+    ga, gb = to_bsm(A2), to_bsm(B2)
+    base = with_pairs("0", lambda: from_bsm(bsm.bsm_multiply(ga, gb, prec=bsm.BSM_SPLIT_BF16)))
+    os.environ["BSM_SYM_BUDGET"] = "500"
+    try:
+        got = with_pairs("1", lambda: from_bsm(bsm.bsm_multiply(ga, gb, prec=bsm.BSM_SPLIT_BF16)))
+        assert bsm.bsm_last_chunks() > 1
+    finally:
+        os.environ.pop("BSM_SYM_BUDGET", None)
+    assert_same_structure(got, base)
+    assert np.array_equal(got.vals, base.vals)
+
+
+def test_pairs_symmetric_square():
+    A = synth.decay(300, 32, 680)
+    U = to_bsm(synth.upper_blocks(A))
+    one = with_pairs("0", lambda: from_bsm(bsm.bsm_sym_square(U, prec=bsm.BSM_SPLIT_BF16)))
+    two = with_pairs("1", lambda: from_bsm(bsm.bsm_sym_square(U, prec=bsm.BSM_SPLIT_BF16)))
+    assert_same_structure(two, one)
+    assert np.array_equal(two.vals, one.vals)
