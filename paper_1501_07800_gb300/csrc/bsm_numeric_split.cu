@@ -34,7 +34,12 @@
 // (g*128/bs + L - t) because consecutive lane blocks are one slice apart.
 // D_d then lands in TMEM lane block L of group g's accumulator.
 //
-// Roles (576 threads, one CTA per SM, persistent over C blocks):
+// Items: one C block, or (long product lists) a pair of sibling C blocks
+// (I, 2y), (I, 2y+1) whose merged product list runs as 128 x 2bs MMAs: the B
+// slices of the two sibling B blocks sit side by side (a pair slot), so each
+// A tile feeds both C blocks.
+//
+// Roles (576 threads, one CTA per SM, persistent over items):
 //   warp 16:       producer -- all lanes prefetch work descriptors and block
 //                  indices; lane 0 issues the 1-D bulk copies of the A and B
 //                  slices of each k-product into a ring of stages (mbarrier
