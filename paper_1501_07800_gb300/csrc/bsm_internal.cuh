@@ -184,6 +184,13 @@ bsm_status split_launch(int bs, int slices, const ProdDesc *prods_dev, const uin
                         int64_t nitems, unsigned long long *work, unsigned *errword,
                         int64_t *fold, cudaStream_t s, int chunk = 32, int np = 1);
 size_t split_fold_bytes(int bs);
+// Pair items (two sibling C blocks per item) for nt products over nc C blocks?
+bool split_use_pairs(int bs, int spec, int64_t nt, int64_t nc);
+// Pair-item structures of one product (task-list fields of d, A slices, B
+// slices in pair slots, padded exponents); *bslot: B pair slot per B block.
+bsm_status split_pairs_prepare(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, int spec,
+                               ProdDesc &d, int32_t **bslot, std::vector<void *> &owned,
+                               cudaStream_t s);
 // Work items per claim for a list of nt block products over nc C blocks.
 int split_chunk_for(int64_t nt, int64_t nc);
 // Longest product list of a task list, atomically maxed into *dmax_dev.

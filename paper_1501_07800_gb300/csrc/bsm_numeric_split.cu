@@ -1187,140 +1187,141 @@ ProdDesc make_desc(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, double
 // Pair items (two sibling C blocks per MMA, N = 2 bs) for long product lists:
 // each A tile then serves twice the outputs.  BSM_SPLIT_PAIRS=0 / 1 in the
 // environment turns them off / on regardless of the list length.
-static bool use_pairs(int bs, int spec, const SymbolicResult &sym) {
+bool split_use_pairs(int bs, int spec, int64_t nt, int64_t nc) {
   if (bs != 32 || !pair_compiled(split_spec_fmt(spec), split_spec_slices(spec))) return false;
   const char *e = getenv("BSM_SPLIT_PAIRS");
   if (e && e[0] == '0') return false;
   if (e && e[0] == '1') return true;
-  return sym.nc > 0 && sym.nt >= 16 * sym.nc;
+  return nc > 0 && nt >= 16 * nc;
 }
 
-// The numeric phase over pairs of sibling C blocks: B pair slots, merged
-// product lists per C pair, B slices in pair slots, one launch.
-static bsm_status numeric_split_pairs(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym,
-                                      int spec, double *cvals, int32_t *nzflag, unsigned *errword,
-                                      cudaStream_t s) {
+// Pair items of one product: B pair slots, C sibling pairs and their merged
+// product lists (structure only; no values).  Fills the task-list fields of
+// `d` (seg, ta, tb, ckeys, nc, nt, nb, pairc), allocates the A slices, the B
+// slices in pair slots (zeroed: absent siblings stay zero) and the exponents
+// (one spare block column), and returns the B pair slot of every B block for
+// split_compute.  Allocations are appended to `owned`.
+bsm_status split_pairs_prepare(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, int spec,
+                               ProdDesc &d, int32_t **bslot_out, std::vector<void *> &owned,
+                               cudaStream_t s) {
   const int bs = A->bs, fmt = split_spec_fmt(spec);
   const int64_t slices = split_spec_slices(spec), eb = fmt == 0 ? 2 : 1;
   const int64_t nb = B->nblk, nc = sym.nc;
-  std::vector<void *> owned;
-  auto cleanup = [&]() {
-    for (void *p : owned) dev_free(p, s);  // stream-ordered: after the kernel
-  };
+  *bslot_out = nullptr;
   auto grab = [&](void **p, size_t bytes) -> bsm_status {
     bsm_status r = dev_alloc(p, bytes > 0 ? bytes : 16, s);
     if (r == BSM_OK) owned.push_back(*p);
     return r;
   };
-  int64_t *h = (int64_t *)host_scratch().get(sizeof(ProdDesc) + 64);
-  if (!h) return BSM_ERR_OOM;
+  int32_t *h32 = (int32_t *)host_scratch().get(64);
+  if (!h32) return BSM_ERR_OOM;
   int32_t *bhead, *bpos, *bslot, *chead, *cpos, *pairc, *cnt, *mseg, *mta, *mtb;
   uint64_t *pkeys;
-  bsm_status st;
-  // B pair slots
-  if ((st = grab((void **)&bhead, 4 * nb)) || (st = grab((void **)&bpos, 4 * nb)) ||
-      (st = grab((void **)&bslot, 4 * nb)) || (st = grab((void **)&chead, 4 * nc)) ||
-      (st = grab((void **)&cpos, 4 * nc))) {
-    cleanup();
-    return st;
+  BSM_TRY(grab((void **)&bhead, 4 * nb));
+  BSM_TRY(grab((void **)&bpos, 4 * nb));
+  BSM_TRY(grab((void **)&bslot, 4 * nb));
+  BSM_TRY(grab((void **)&chead, 4 * nc));
+  BSM_TRY(grab((void **)&cpos, 4 * nc));
+  count_launch(2);
+  if (nb) k_pair_heads<<<grid_for(nb, 256), 256, 0, s>>>(B->keys, nb, bhead);
+  if (nc) k_pair_heads<<<grid_for(nc, 256), 256, 0, s>>>(sym.ckeys, nc, chead);
+  BSM_TRY(scan_exclusive_i32(bhead, bpos, nb, s));
+  BSM_TRY(scan_exclusive_i32(chead, cpos, nc, s));
+  h32[0] = h32[1] = h32[2] = h32[3] = 0;
+  if (nb) {
+    cudaMemcpyAsync(h32 + 0, bpos + nb - 1, 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h32 + 1, bhead + nb - 1, 4, cudaMemcpyDeviceToHost, s);
   }
-  count_launch(4);
-  k_pair_heads<<<grid_for(nb, 256), 256, 0, s>>>(B->keys, nb, bhead);
-  k_pair_heads<<<grid_for(nc, 256), 256, 0, s>>>(sym.ckeys, nc, chead);
-  if ((st = scan_exclusive_i32(bhead, bpos, nb, s)) || (st = scan_exclusive_i32(chead, cpos, nc, s))) {
-    cleanup();
-    return st;
+  if (nc) {
+    cudaMemcpyAsync(h32 + 2, cpos + nc - 1, 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h32 + 3, chead + nc - 1, 4, cudaMemcpyDeviceToHost, s);
   }
-  int32_t *h32 = (int32_t *)h;
-  cudaMemcpyAsync(h32 + 0, bpos + nb - 1, 4, cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(h32 + 1, bhead + nb - 1, 4, cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(h32 + 2, cpos + nc - 1, 4, cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(h32 + 3, chead + nc - 1, 4, cudaMemcpyDeviceToHost, s);
-  if ((st = cuda_status(cudaStreamSynchronize(s))) != BSM_OK) {
-    cleanup();
-    return st;
-  }
+  BSM_CUDA(cudaStreamSynchronize(s));
   const int64_t npb = (int64_t)h32[0] + h32[1], npc = (int64_t)h32[2] + h32[3];
-  if ((st = grab((void **)&pairc, 8 * npc)) || (st = grab((void **)&pkeys, 8 * npc)) ||
-      (st = grab((void **)&cnt, 4 * (npc + 1))) || (st = grab((void **)&mseg, 4 * (npc + 1)))) {
-    cleanup();
-    return st;
-  }
+  BSM_TRY(grab((void **)&pairc, 8 * npc));
+  BSM_TRY(grab((void **)&pkeys, 8 * npc));
+  BSM_TRY(grab((void **)&cnt, 4 * (npc + 1)));
+  BSM_TRY(grab((void **)&mseg, 4 * (npc + 1)));
   cudaMemsetAsync(pairc, 0xFF, 8 * npc, s);  // -1: absent sibling
   cudaMemsetAsync(cnt + npc, 0, 4, s);
-  k_pair_assign<<<grid_for(nb, 256), 256, 0, s>>>(B->keys, nb, bhead, bpos, bslot, nullptr,
-                                                  nullptr);
-  k_pair_assign<<<grid_for(nc, 256), 256, 0, s>>>(sym.ckeys, nc, chead, cpos, nullptr, pairc,
-                                                  pkeys);
-  k_pair_merge<<<grid_for(npc, 128), 128, 0, s>>>(pairc, npc, sym.seg, sym.ta, sym.tb, B->keys,
-                                                  bslot, cnt, nullptr, nullptr, nullptr, 0);
-  if ((st = scan_exclusive_i32(cnt, mseg, npc + 1, s)) != BSM_OK) {
-    cleanup();
-    return st;
-  }
-  cudaMemcpyAsync(h32, mseg + npc, 4, cudaMemcpyDeviceToHost, s);
-  if ((st = cuda_status(cudaStreamSynchronize(s))) != BSM_OK) {
-    cleanup();
-    return st;
-  }
-  const int64_t mt = h32[0];
-  if ((st = grab((void **)&mta, 4 * mt)) || (st = grab((void **)&mtb, 4 * mt))) {
-    cleanup();
-    return st;
-  }
   count_launch(3);
-  k_pair_merge<<<grid_for(npc, 128), 128, 0, s>>>(pairc, npc, sym.seg, sym.ta, sym.tb, B->keys,
-                                                  bslot, nullptr, mseg, mta, mtb, 1);
-  // exponents and slices (B in pair slots; absent siblings stay zero)
-  ProdDesc d = {};
+  if (nb)
+    k_pair_assign<<<grid_for(nb, 256), 256, 0, s>>>(B->keys, nb, bhead, bpos, bslot, nullptr,
+                                                    nullptr);
+  if (nc) {
+    k_pair_assign<<<grid_for(nc, 256), 256, 0, s>>>(sym.ckeys, nc, chead, cpos, nullptr, pairc,
+                                                    pkeys);
+    k_pair_merge<<<grid_for(npc, 128), 128, 0, s>>>(pairc, npc, sym.seg, sym.ta, sym.tb, B->keys,
+                                                    bslot, cnt, nullptr, nullptr, nullptr, 0);
+  }
+  BSM_TRY(scan_exclusive_i32(cnt, mseg, npc + 1, s));
+  cudaMemcpyAsync(h32, mseg + npc, 4, cudaMemcpyDeviceToHost, s);
+  BSM_CUDA(cudaStreamSynchronize(s));
+  const int64_t mt = h32[0];
+  BSM_TRY(grab((void **)&mta, 4 * mt));
+  BSM_TRY(grab((void **)&mtb, 4 * mt));
+  if (npc) {
+    count_launch();
+    k_pair_merge<<<grid_for(npc, 128), 128, 0, s>>>(pairc, npc, sym.seg, sym.ta, sym.tb, B->keys,
+                                                    bslot, nullptr, mseg, mta, mtb, 1);
+  }
   int *rowexp, *colexp;
   uint8_t *asl, *bsl;
   const size_t slice_bytes = (size_t)eb * bs * bs;
   // colexp has one spare block column: the odd sibling of a pair in the last
   // block column reads its (unused) exponents there
-  if ((st = grab((void **)&rowexp, 4 * A->mb * bs)) ||
-      (st = grab((void **)&colexp, 4 * (B->nb + 1) * bs)) ||
-      (st = grab((void **)&asl, slice_bytes * slices * A->nblk)) ||
-      (st = grab((void **)&bsl, slice_bytes * 2 * slices * npb))) {
-    cleanup();
-    return st;
-  }
+  BSM_TRY(grab((void **)&rowexp, 4 * A->mb * bs));
+  BSM_TRY(grab((void **)&colexp, 4 * (B->nb + 1) * bs));
+  BSM_TRY(grab((void **)&asl, slice_bytes * slices * A->nblk));
+  BSM_TRY(grab((void **)&bsl, slice_bytes * 2 * slices * npb));
   cudaMemsetAsync(bsl, 0, slice_bytes * 2 * slices * npb, s);
   d.asl = asl;
   d.bsl = bsl;
   d.rowexp = rowexp;
   d.colexp = colexp;
-  if ((st = split_compute(A, B, spec, d, errword, s, bslot)) != BSM_OK) {
-    cleanup();
-    return st;
-  }
   d.seg = mseg;
   d.ta = mta;
   d.tb = mtb;
   d.ckeys = pkeys;
-  d.cv = cvals;
-  d.nz = nzflag;
-  d.na = A->nblk;
   d.nb = npb;
   d.nc = npc;
   d.nt = mt;
   d.pairc = pairc;
-  // the product table and the work counter
+  *bslot_out = bslot;
+  return cuda_status(cudaGetLastError());
+}
+
+// The numeric phase of one product over pairs of sibling C blocks.
+static bsm_status numeric_split_pairs(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym,
+                                      int spec, double *cvals, int32_t *nzflag, unsigned *errword,
+                                      cudaStream_t s) {
+  const int bs = A->bs;
+  std::vector<void *> owned;
+  auto cleanup = [&]() {
+    for (void *p : owned) dev_free(p, s);  // stream-ordered: after the kernel
+  };
+  ProdDesc d = make_desc(A, B, sym, cvals, nzflag);
+  int32_t *bslot = nullptr;
+  bsm_status st = split_pairs_prepare(A, B, sym, spec, d, &bslot, owned, s);
+  if (st == BSM_OK) st = split_compute(A, B, spec, d, errword, s, bslot);
   int *scr = nullptr;
   int64_t *fold = nullptr;
-  if ((st = grab((void **)&scr, 16 + sizeof(ProdDesc))) ||
-      (st = grab((void **)&fold, split_fold_bytes(bs)))) {
-    cleanup();
-    return st;
+  if (st == BSM_OK && (st = dev_alloc((void **)&scr, 16 + sizeof(ProdDesc), s)) == BSM_OK)
+    owned.push_back(scr);
+  if (st == BSM_OK && (st = dev_alloc((void **)&fold, split_fold_bytes(bs), s)) == BSM_OK)
+    owned.push_back(fold);
+  void *h = host_scratch().get(sizeof(ProdDesc) + 64);
+  if (st == BSM_OK && !h) st = BSM_ERR_OOM;
+  if (st == BSM_OK) {
+    cudaMemsetAsync(scr, 0, 16, s);
+    memcpy(h, &d, sizeof(ProdDesc));
+    cudaMemcpyAsync(scr + 4, h, sizeof(ProdDesc), cudaMemcpyHostToDevice, s);
+    st = cuda_status(cudaStreamSynchronize(s));  // the host staging buffer is reused
   }
-  cudaMemsetAsync(scr, 0, 16, s);
-  memcpy(h, &d, sizeof(ProdDesc));
-  cudaMemcpyAsync(scr + 4, h, sizeof(ProdDesc), cudaMemcpyHostToDevice, s);
-  st = cuda_status(cudaStreamSynchronize(s));  // the host staging buffer is reused
   if (st == BSM_OK)
-    st = split_launch(bs, spec, reinterpret_cast<const ProdDesc *>(scr + 4), nullptr, npc,
+    st = split_launch(bs, spec, reinterpret_cast<const ProdDesc *>(scr + 4), nullptr, d.nc,
                       reinterpret_cast<unsigned long long *>(scr + 2), errword, fold, s,
-                      split_chunk_for(mt, npc), 2);
+                      split_chunk_for(d.nt, d.nc), 2);
   cleanup();
   return st;
 }
@@ -1330,7 +1331,7 @@ bsm_status numeric_split(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, 
   const int bs = A->bs;
   BSM_TRY(split_supported(bs, slices));
   if (sym.nc == 0) return BSM_OK;
-  if (use_pairs(bs, slices, sym))
+  if (split_use_pairs(bs, slices, sym.nt, sym.nc))
     return numeric_split_pairs(A, B, sym, slices, cvals, nzflag, errword, s);
   std::vector<void *> owned;
   auto cleanup = [&]() {

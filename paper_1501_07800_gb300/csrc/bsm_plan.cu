@@ -41,6 +41,8 @@ struct bsm_plan_s {
   int *scr = nullptr;  // [0] longest product list, [2..3] work counter
   unsigned *err = nullptr;
   int64_t *fold = nullptr;  // split mode: scratch of the numeric kernel
+  int np = 1;               // split mode: C blocks per item (2: sibling pairs)
+  std::vector<int32_t *> bslot;  // pairs: B pair slot of every B block, per product
   std::vector<void *> owned;
   // chosen configuration
   int order = 0;  // 0: longest first, 1: product-major Morton
@@ -72,10 +74,10 @@ __global__ void k_plan_items(const int32_t *__restrict__ seg, int64_t nc, uint32
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 struct TuneKey {
-  int prec, bs, slices, n, lg_nc, lg_mean, lg_max;
+  int prec, bs, slices, np, n, lg_nc, lg_mean, lg_max;
   bool operator<(const TuneKey &o) const {
-    return std::tie(prec, bs, slices, n, lg_nc, lg_mean, lg_max) <
-           std::tie(o.prec, o.bs, o.slices, o.n, o.lg_nc, o.lg_mean, o.lg_max);
+    return std::tie(prec, bs, slices, np, n, lg_nc, lg_mean, lg_max) <
+           std::tie(o.prec, o.bs, o.slices, o.np, o.n, o.lg_nc, o.lg_mean, o.lg_max);
   }
 };
 struct TuneVal {
@@ -103,9 +105,11 @@ bsm_status enqueue_numeric(bsm_plan P, int order, int chunk, int ctas, cudaStrea
   if (P->prec == BSM_FP64)
     return numeric_fp64_batched(P->bs, P->table, items, P->nitems, counter, P->err, ctas, s);
   for (int i = 0; i < P->n; i++)
-    if (P->sym[i].nc > 0) BSM_TRY(split_compute(P->A[i], P->B[i], P->slices, P->desc[i], P->err, s));
+    if (P->sym[i].nc > 0)
+      BSM_TRY(split_compute(P->A[i], P->B[i], P->slices, P->desc[i], P->err, s,
+                            P->np == 2 ? P->bslot[i] : nullptr));
   return split_launch(P->bs, P->slices, P->table, items, P->nitems, counter, P->err, P->fold, s,
-                      chunk);
+                      chunk, P->np);
 }
 
 void destroy_plan(bsm_plan P) {
@@ -164,7 +168,7 @@ bsm_status autotune(bsm_plan P) {
   cudaMemcpyAsync(h, P->scr, 4, cudaMemcpyDeviceToHost, P->stream);
   BSM_CUDA(cudaStreamSynchronize(P->stream));
   max_nk = h[0];
-  TuneKey key{P->prec, P->bs, P->slices, P->n, ilog2(P->nitems),
+  TuneKey key{P->prec, P->bs, P->slices, P->np, P->n, ilog2(P->nitems),
               ilog2(P->nitems ? tot_nt / P->nitems : 0), ilog2(max_nk)};
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
@@ -350,11 +354,12 @@ extern "C" bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matr
     cudaEventRecord(P->ev_in, (cudaStream_t)stream);
     cudaStreamWaitEvent(s, P->ev_in, 0);
   }
+  int64_t all_nc = 0, all_nt = 0;
   for (int i = 0; i < n && st == BSM_OK; i++) {
     st = symbolic_multiply(A[i], B[i], &P->sym[i], s);
-    P->nitems += P->sym[i].nc;
+    all_nc += P->sym[i].nc;
+    all_nt += P->sym[i].nt;
   }
-  if (st == BSM_OK && P->nitems > 0xFFFFFFFFFFll) st = BSM_ERR_UNSUPPORTED;
   if (st == BSM_OK) st = dev_alloc((void **)&P->err, sizeof(unsigned), s);
   for (int i = 0; i < n && st == BSM_OK; i++) {
     const int64_t nc = P->sym[i].nc;
@@ -362,6 +367,20 @@ extern "C" bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matr
     if ((st = dev_alloc((void **)&P->cv[i], sizeof(double) * bs * bs * nc, s)) != BSM_OK) break;
     st = dev_alloc((void **)&P->nz[i], 4 * nc, s);
   }
+  // per-product descriptors; split mode: slices and exponents, and for long
+  // lists the sibling-pair items (merged lists, B pair slots)
+  P->np = prec != BSM_FP64 && split_use_pairs(bs, slices, all_nt, all_nc) ? 2 : 1;
+  P->bslot.assign(n, nullptr);
+  for (int i = 0; i < n && st == BSM_OK; i++) {
+    P->desc[i] = make_desc(A[i], B[i], P->sym[i], P->cv[i], P->nz[i]);
+    if (prec == BSM_FP64 || P->sym[i].nc == 0) continue;
+    if (P->np == 2)
+      st = split_pairs_prepare(A[i], B[i], P->sym[i], slices, P->desc[i], &P->bslot[i], P->owned, s);
+    else
+      st = split_alloc(A[i], B[i], slices, P->desc[i], P->owned, s);
+  }
+  for (int i = 0; i < n && st == BSM_OK; i++) P->nitems += P->sym[i].nc ? P->desc[i].nc : 0;
+  if (st == BSM_OK && P->nitems > 0xFFFFFFFFFFll) st = BSM_ERR_UNSUPPORTED;
   uint32_t *k0 = nullptr, *k1 = nullptr;
   const int64_t tot = P->nitems > 0 ? P->nitems : 1;
   auto grab = [&](void **p, size_t bytes) {
@@ -378,20 +397,15 @@ extern "C" bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matr
   if (st == BSM_OK) {
     cudaMemsetAsync(P->scr, 0, 16, s);
     int64_t off = 0;
-    for (int i = 0; i < n; i++) {
-      if (P->sym[i].nc == 0) continue;
+    for (int i = 0; i < n; i++) {  // items: C blocks, or pairs of them
+      if (P->sym[i].nc == 0 || P->desc[i].nc == 0) continue;
       count_launch();
-      k_plan_items<<<grid_for(P->sym[i].nc, 256), 256, 0, s>>>(P->sym[i].seg, P->sym[i].nc,
-                                                               (uint32_t)i, k0 + off,
-                                                               P->items_morton + off);
-      off += P->sym[i].nc;
+      k_plan_items<<<grid_for(P->desc[i].nc, 256), 256, 0, s>>>(P->desc[i].seg, P->desc[i].nc,
+                                                                (uint32_t)i, k0 + off,
+                                                                P->items_morton + off);
+      off += P->desc[i].nc;
     }
     st = sort_pairs_u32_u64(k0, k1, P->items_morton, P->items_lpt, P->nitems, s);
-  }
-  for (int i = 0; i < n && st == BSM_OK; i++) {
-    P->desc[i] = make_desc(A[i], B[i], P->sym[i], P->cv[i], P->nz[i]);
-    if (prec != BSM_FP64 && P->sym[i].nc > 0)
-      st = split_alloc(A[i], B[i], slices, P->desc[i], P->owned, s);
   }
   if (st == BSM_OK && prec != BSM_FP64 &&
       (st = dev_alloc((void **)&P->fold, split_fold_bytes(bs), s)) == BSM_OK)

@@ -148,3 +148,44 @@ def test_plan_fp8_equals_batched():
         assert np.array_equal(g.vals, r.vals)
         E = oracle.multiply(a, b).C
         assert relerr(g.vals, E.vals) < 1e-11
+
+
+def test_plan_with_sibling_pairs():
+    """Plans whose split numeric phase runs on pairs of sibling C blocks give
+    the bits of single-block items, also after a value update (the pair-slot
+    slices are recomputed in the replayed graph)."""
+    import os
+    pairs = [(synth.decay(200, 32, 90 + k), None) for k in range(3)]
+    pairs = [(a, synth.random_blocks(a.ncols, 32, 0.4, 95 + k, ncols=a.ncols - 40))
+             for k, (a, _) in enumerate(pairs)]
+    As = [to_bsm(a) for a, _ in pairs]
+    Bs = [to_bsm(b) for _, b in pairs]
+
+    def run(flag):
+        os.environ["BSM_SPLIT_PAIRS"] = flag
+        try:
+            plan = bsm.bsm_plan_create(As, Bs, prec=bsm.BSM_SPLIT_BF16, autotune=True)
+            bsm.bsm_plan_execute(plan)
+            return plan, [from_bsm(c) for c in bsm.bsm_plan_results(plan)]
+        finally:
+            os.environ.pop("BSM_SPLIT_PAIRS", None)
+
+    plan1, one = run("0")
+    plan2, two = run("1")
+    assert bsm.bsm_plan_info(plan2)[3] < bsm.bsm_plan_info(plan1)[3]   # fewer items: pairs
+    for a, b in zip(one, two):
+        assert_same_structure(b, a)
+        assert np.array_equal(b.vals, a.vals)
+    # new values of A, same blocks: replay both plans
+    for (a, b), ga in zip(pairs, As):
+        bsm.bsm_update_values(ga, a.brow, a.bcol, a.vals * 0.75)
+    for plan in (plan1, plan2):
+        bsm.bsm_plan_execute(plan)
+    one = [from_bsm(c) for c in bsm.bsm_plan_results(plan1)]
+    two = [from_bsm(c) for c in bsm.bsm_plan_results(plan2)]
+    for (a, b), x, y in zip(pairs, one, two):
+        assert np.array_equal(x.vals, y.vals)
+        E = oracle.multiply(synth.BlockCOO(a.nrows, a.ncols, a.bs, a.brow, a.bcol, a.vals * 0.75),
+                            b).C
+        assert_same_structure(y, E)
+        assert relerr(y.vals, E.vals) < 1e-11
