@@ -521,16 +521,44 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
     if ((st = dev_alloc((void **)&cv[i], sizeof(double) * bs * bs * sym[i].nc, s)) != BSM_OK) break;
     st = dev_alloc((void **)&nz[i], 4 * sym[i].nc, s);
   }
+  // per-product descriptors; split mode: slices and exponents, and for long
+  // lists sibling-pair items (merged lists, B pair slots)
+  const int np = prec != BSM_FP64 && split_use_pairs(bs, slices, total_nt, total) ? 2 : 1;
+  std::vector<ProdDesc> h(n);
+  std::vector<int32_t *> bslot(n, nullptr);
+  for (int i = 0; i < n && st == BSM_OK; i++) {
+    h[i] = make_desc(A[idx[i]], B[idx[i]], sym[i], cv[i], nz[i]);
+    if (prec == BSM_FP64 || sym[i].nc == 0) continue;
+    if (np == 2) {
+      st = split_pairs_prepare(A[idx[i]], B[idx[i]], sym[i], slices, h[i], &bslot[i], owned, s);
+      if (st == BSM_OK) st = split_compute(A[idx[i]], B[idx[i]], slices, h[i], err, s, bslot[i]);
+    } else {
+      st = split_prepare(A[idx[i]], B[idx[i]], slices, err, h[i], owned, s);
+    }
+  }
+  const int64_t total_items = [&] {
+    int64_t t = 0;
+    for (int i = 0; i < n; i++) t += sym[i].nc ? h[i].nc : 0;
+    return t;
+  }();
+  const int64_t total_item_nt = np == 2 ? [&] {
+    int64_t t = 0;
+    for (int i = 0; i < n; i++) t += sym[i].nc ? h[i].nt : 0;
+    return t;
+  }() : total_nt;
   // global work list, longest product lists first
   uint32_t *k0 = nullptr, *k1 = nullptr;
   uint64_t *v0 = nullptr, *v1 = nullptr;
   ProdDesc *table = nullptr;
   int *scr = nullptr;  // [0] longest list, [2..3] work counter
   if (st == BSM_OK && total > 0) {
-    if ((st = dev_alloc((void **)&k0, 4 * total, s)) == BSM_OK) owned.push_back(k0);
-    if (st == BSM_OK && (st = dev_alloc((void **)&k1, 4 * total, s)) == BSM_OK) owned.push_back(k1);
-    if (st == BSM_OK && (st = dev_alloc((void **)&v0, 8 * total, s)) == BSM_OK) owned.push_back(v0);
-    if (st == BSM_OK && (st = dev_alloc((void **)&v1, 8 * total, s)) == BSM_OK) owned.push_back(v1);
+    if ((st = dev_alloc((void **)&k0, 4 * total_items, s)) == BSM_OK) owned.push_back(k0);
+    if (st == BSM_OK && (st = dev_alloc((void **)&k1, 4 * total_items, s)) == BSM_OK)
+      owned.push_back(k1);
+    if (st == BSM_OK && (st = dev_alloc((void **)&v0, 8 * total_items, s)) == BSM_OK)
+      owned.push_back(v0);
+    if (st == BSM_OK && (st = dev_alloc((void **)&v1, 8 * total_items, s)) == BSM_OK)
+      owned.push_back(v1);
     if (st == BSM_OK &&
         (st = dev_alloc((void **)&table, sizeof(ProdDesc) * n, s)) == BSM_OK)
       owned.push_back(table);
@@ -540,20 +568,14 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
   if (st == BSM_OK && total > 0) {
     cudaMemsetAsync(scr, 0, 16, s);
     int64_t off = 0;
-    for (int i = 0; i < n; i++) {
-      if (sym[i].nc == 0) continue;
+    for (int i = 0; i < n; i++) {  // items: C blocks, or pairs of them
+      if (sym[i].nc == 0 || h[i].nc == 0) continue;
       count_launch();
-      k_batch_items<<<grid_for(sym[i].nc, 256), 256, 0, s>>>(sym[i].seg, sym[i].nc, (uint32_t)i,
-                                                             k0 + off, v0 + off);
-      off += sym[i].nc;
+      k_batch_items<<<grid_for(h[i].nc, 256), 256, 0, s>>>(h[i].seg, h[i].nc, (uint32_t)i,
+                                                           k0 + off, v0 + off);
+      off += h[i].nc;
     }
-    st = sort_pairs_u32_u64(k0, k1, v0, v1, total, s);
-    std::vector<ProdDesc> h(n);
-    for (int i = 0; i < n && st == BSM_OK; i++) {
-      h[i] = make_desc(A[idx[i]], B[idx[i]], sym[i], cv[i], nz[i]);
-      if (prec != BSM_FP64 && sym[i].nc > 0)
-        st = split_prepare(A[idx[i]], B[idx[i]], slices, err, h[i], owned, s);
-    }
+    st = sort_pairs_u32_u64(k0, k1, v0, v1, total_items, s);
     if (st == BSM_OK) {
       void *hp = host_scratch().get(sizeof(ProdDesc) * n + 16);
       if (!hp) st = BSM_ERR_OOM;
@@ -572,8 +594,8 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
       if (prec == BSM_FP64)
         st = numeric_fp64_batched(bs, table, v1, total, counter, err, 0, s);
       else
-        st = split_launch(bs, slices, table, v1, total, counter, err, fold, s,
-                          split_chunk_for(total_nt, total));
+        st = split_launch(bs, slices, table, v1, total_items, counter, err, fold, s,
+                          split_chunk_for(total_item_nt, total_items), np);
     }
   }
   timer.mark(s);

@@ -405,3 +405,20 @@ def test_pairs_symmetric_square():
     two = with_pairs("1", lambda: from_bsm(bsm.bsm_sym_square(U, prec=bsm.BSM_SPLIT_BF16)))
     assert_same_structure(two, one)
     assert np.array_equal(two.vals, one.vals)
+
+
+def test_batched_with_sibling_pairs():
+    prods = [(synth.decay(180 + 20 * k, 32, 690 + k), synth.decay(180 + 20 * k, 32, 690 + k))
+             for k in range(3)]
+    As = [to_bsm(a) for a, _ in prods]
+    Bs = [to_bsm(b) for _, b in prods]
+    one = with_pairs("0", lambda: [from_bsm(c) for c in
+                                   bsm.bsm_multiply_batched(As, Bs, prec=bsm.BSM_SPLIT_BF16)])
+    two = with_pairs("1", lambda: [from_bsm(c) for c in
+                                   bsm.bsm_multiply_batched(As, Bs, prec=bsm.BSM_SPLIT_BF16)])
+    for (a, b), x, y in zip(prods, one, two):
+        assert_same_structure(y, x)
+        assert np.array_equal(y.vals, x.vals)
+        E = oracle.multiply(a, b).C
+        assert_same_structure(y, E)
+        assert relerr(y.vals, E.vals) < TOL_SPLIT
