@@ -405,7 +405,32 @@ extern "C" bsm_status bsm_to_blocks(bsm_matrix M, int64_t *nblk_inout, int32_t *
     cleanup();
     return st;
   }
-  // host output: gather through a bounded device staging buffer
+  // host output into pinned (page-locked, device-mapped) buffers: the gather
+  // and coordinate kernels write straight into them over the host link, with
+  // no staging copy
+  auto mapped = [](void *p, uintptr_t align) -> void * {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return (uintptr_t)a.devicePointer % align ? nullptr : a.devicePointer;
+  };
+  double *mv = (double *)mapped(vals, 16);
+  int32_t *mr = (int32_t *)mapped(brow, 4), *mc = (int32_t *)mapped(bcol, 4);
+  if ((!vals || mv) && (!brow || mr) && (!bcol || mc)) {
+    if (brow || bcol) {
+      count_launch();
+      k_rowmajor_coords<<<nblocks_for(n, 256), 256, 0, s>>>(rms, 0, n, mr, mc);
+    }
+    if (vals) launch_gather_blocks(M->vals, sidx, mv, n, bs, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    cleanup();
+    return cuda_status(e == cudaSuccess ? cudaGetLastError() : e);
+  }
+  // other host output: gather through a bounded device staging buffer
   size_t bblk = sizeof(double) * bs * bs;
   int64_t chunk = (int64_t)((size_t)1 << 30) / (int64_t)bblk;
   if (chunk > n) chunk = n;

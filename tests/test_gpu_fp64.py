@@ -42,6 +42,27 @@ def test_build_roundtrip(device):
     assert np.array_equal(R.vals, E.vals)
 
 
+def test_to_blocks_into_pinned_host_buffers():
+    """Pinned host buffers are written directly by the gather kernels; the
+    result equals the staged copy into pageable buffers."""
+    import torch
+    A = synth.random_blocks(3000, 32, 0.05, 8)
+    M = to_bsm(A)
+    n = M.nblk
+    pinned = (torch.empty(n, dtype=torch.int32, pin_memory=True).numpy(),
+              torch.empty(n, dtype=torch.int32, pin_memory=True).numpy(),
+              torch.empty((n, 32, 32), dtype=torch.float64, pin_memory=True).numpy())
+    r, c, v = bsm.bsm_to_blocks(M, out=pinned)
+    E = A.sorted()
+    assert np.array_equal(r, E.brow) and np.array_equal(c, E.bcol)
+    assert np.array_equal(v, E.vals)
+    # values only, into a pinned buffer; coordinates into pageable ones
+    mixed = (np.empty(n, np.int32), np.empty(n, np.int32), pinned[2])
+    mixed[2][...] = 0
+    r2, c2, v2 = bsm.bsm_to_blocks(M, out=mixed)
+    assert np.array_equal(r2, E.brow) and np.array_equal(v2, E.vals)
+
+
 def test_build_drops_zero_blocks_and_rejects_bad_input():
     bs = 16
     A = synth.random_blocks(200, bs, 0.3, 6)
