@@ -604,6 +604,7 @@ def run_decay(args):
         want = torch.from_numpy(lo.astype(np.int64) * nbk + hi).to(dev)
         pos = torch.searchsorted(key_gpu, want).clamp(max=max(ncb - 1, 0))
         present = (key_gpu[pos] == want).cpu().numpy() if ncb else np.zeros(len(si), bool)
+        bsm.bsm_release_memory()  # cached pool memory is not PyTorch's to use
         _, _, cv = bsm.bsm_to_blocks(C, device=True)
         got = cv[pos].cpu().numpy() if ncb else np.zeros_like(ref)
         got[~present] = 0.0

@@ -328,6 +328,18 @@ bsm_status bsm_last_chunks(int *nchunks);
 bsm_status bsm_set_timing(int on);
 
 /*
+ * bsm_release_memory -- return the device memory the library keeps cached to
+ * the driver.  The library allocates stream-ordered from the current device's
+ * default memory pool and keeps freed memory in the pool, so that repeated
+ * products reuse it without new driver allocations; memory cached there is
+ * not available to other allocators (cudaMalloc, PyTorch's allocator).  This
+ * call synchronises the current device, then releases every cached byte not
+ * backing a live allocation (handles, plans and their buffers stay valid).
+ * Errors: CUDA if the synchronisation or the release fails.
+ */
+bsm_status bsm_release_memory(void);
+
+/*
  * bsm_last_phase_ms -- results of the last timed bsm_multiply on this thread.
  *   ms        double[cap]: ms[0] symbolic phase, ms[1] numeric phase (the
  *             numeric kernel plus, in split modes, the slicing kernels),

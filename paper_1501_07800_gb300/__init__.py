@@ -54,6 +54,7 @@ _PROTOS = {
     "bsm_last_stats": (_I32, [_P, _I32, _P, _P, _P]),
     "bsm_last_chunks": (_I32, [_P]),
     "bsm_set_timing": (_I32, [_I32]),
+    "bsm_release_memory": (_I32, []),
     "bsm_last_phase_ms": (_I32, [_P, _I32, _P, _P]),
     "bsm_block_products_fp64_noalloc": (_I32, [_I32, _I64, _P, _P, _P, _P, _I64, _P, _I64, _P,
                                                 _P, _P]),
@@ -368,6 +369,12 @@ def bsm_last_chunks() -> int:
 
 def bsm_set_timing(on: bool):
     _check(load().bsm_set_timing(1 if on else 0), "bsm_set_timing")
+
+
+def bsm_release_memory():
+    """Give the library's cached device memory back to the driver (after a
+    device synchronisation), e.g. before a large PyTorch allocation."""
+    _check(load().bsm_release_memory(), "bsm_release_memory")
 
 
 def bsm_last_phase_ms():

@@ -98,6 +98,16 @@ extern "C" bsm_status bsm_set_timing(int on) {
   return BSM_OK;
 }
 
+extern "C" bsm_status bsm_release_memory(void) {
+  int dev = 0;
+  BSM_CUDA(cudaGetDevice(&dev));
+  BSM_CUDA(cudaDeviceSynchronize());
+  cudaMemPool_t pool;
+  BSM_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  BSM_CUDA(cudaMemPoolTrimTo(pool, 0));
+  return BSM_OK;
+}
+
 extern "C" bsm_status bsm_last_phase_ms(double *ms, int cap, int *nphase, int64_t *launches) {
   LastStats &ls = last_stats();
   if (nphase) *nphase = 3;
