@@ -109,6 +109,25 @@ struct Cfg {
   static constexpr uint32_t LBO = 128;                       // K core-matrix stride
 };
 
+// Order of the B slices in the operand.  Slice j = t + DPG k (t < DPG) sits
+// at position b_off(t) + k: the slices sharing a residue t are adjacent, so
+// one MMA with the Toeplitz A tile of group g and offset t (rows L carry
+// a_(g DPG + L - t)) multiplies it by [b_t | b_(t+DPG) | ...] at once and adds
+// into the accumulators of groups g, g+1, ... (column block k lands in group
+// g + k, whose diagonal g DPG + k DPG + L is exactly (g DPG + L - t) + (t + k
+// DPG)).  b_count(t): slices with residue t.
+__host__ __device__ constexpr int b_count(int S, int DPG, int t) {
+  return t < S ? (S - t + DPG - 1) / DPG : 0;
+}
+__host__ __device__ constexpr int b_off(int S, int DPG, int t) {
+  int o = 0;
+  for (int u = 0; u < t; u++) o += b_count(S, DPG, u);
+  return o;
+}
+__host__ __device__ constexpr int b_pos(int S, int DPG, int j) {
+  return b_off(S, DPG, j % DPG) + j / DPG;
+}
+
 // ------------------------------------------------------------ slicing
 __device__ __forceinline__ int exp_bound(double x) {
   // smallest E with |x| < 2^E (x != 0); 1025 flags Inf/NaN
@@ -204,9 +223,10 @@ __device__ __forceinline__ uint32_t small_int_to_e4m3(int v) {
 // operand rows = block columns, K = block rows, column scales.  A CTA stages
 // one block in shared memory; each thread makes one core-matrix row (16 bytes
 // per slice), so a warp writes 512 contiguous bytes per slice.
-// pslot (B only, NULL otherwise): the pair slot of each block; the slices of
-// the two sibling blocks (I, 2y), (I, 2y+1) of a slot are then interleaved,
-// slice i of the even sibling at 2i, of the odd one at 2i+1.
+// B slices are stored in the operand order of b_pos.  pslot (B only, NULL
+// otherwise): the pair slot of each block; the slices of the two sibling
+// blocks (I, 2y), (I, 2y+1) of a slot are then interleaved, position p of the
+// even sibling at 2p, of the odd one at 2p+1.
 template <int BS, int S, int TRANS, int F>
 __global__ void __launch_bounds__(128) k_slice(const double *__restrict__ vals,
                                                const uint64_t *__restrict__ keys, int64_t n,
@@ -248,9 +268,11 @@ __global__ void __launch_bounds__(128) k_slice(const double *__restrict__ vals,
                             : out + t * (int64_t)S * C::SLICE;
       const int64_t step = pslot ? 2 * C::SLICE : C::SLICE;
 #pragma unroll
-      for (int i = 0; i < S; i++)
-        *reinterpret_cast<uint4 *>(base + i * step + off) =
+      for (int i = 0; i < S; i++) {
+        const int pos = TRANS == 0 ? i : b_pos(S, C::DPG, i);  // B: operand order
+        *reinterpret_cast<uint4 *>(base + pos * step + off) =
             make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+      }
     }
     __syncthreads();
   }
@@ -461,7 +483,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
   constexpr int kTeam = kTeamWarps * 32;         // threads per epilogue team
   constexpr int NB = NP * BS;                    // MMA N: output columns per item
   constexpr int BETA = Fmt<F>::BETA, TS = Fmt<F>::TSPLIT;
-  constexpr uint32_t IDESC = F == 0 ? idesc_bf16_f32(128, NB) : idesc_e4m3_f32(128, NB);
+  // instruction descriptors for N = NB, 2 NB, 3 NB (one to three diagonal groups)
+  constexpr uint32_t IDESC1 = F == 0 ? idesc_bf16_f32(128, NB) : idesc_e4m3_f32(128, NB);
+  constexpr uint32_t IDESC2 = F == 0 ? idesc_bf16_f32(128, 2 * NB) : idesc_e4m3_f32(128, 2 * NB);
+  constexpr uint32_t IDESC3 = F == 0 ? idesc_bf16_f32(128, 3 * NB) : idesc_e4m3_f32(128, 3 * NB);
+  static_assert(G <= 3 && G * NB <= 256, "one MMA spans at most three groups, N <= 256");
   // TMEM accumulators: each team owns NBUF buffers of G*NB columns, two when
   // they fit in the 256 columns we allocate, so that the MMAs of an item's
   // next flush run while the team drains the previous one
@@ -690,23 +716,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
             const uint64_t ad0 = smem_desc(sa, C::LBO, C::SBO);
             const uint64_t bd0 = smem_desc(sa + C::ASLOTS * C::SLICE, C::LBO, C::SBO);
             const uint32_t first = (j == f * fp.fk) ? 0u : 1u;
+            // (g, t): Toeplitz A tile of group g at offset t times the nbk B
+            // slices of residue t, into groups g .. g + nbk - 1.  The first
+            // instruction (g = t = h = 0) spans every group and starts the
+            // accumulation of a flush.
 #pragma unroll
             for (int g = 0; g < G; g++) {
               const uint32_t dt = tbase + (uint32_t)(((b * NBUF + u) * G + g) * NB);
 #pragma unroll
-              for (int t = 0; t < S; t++) {
-                if (t >= (g + 1) * DPG) break;  // K-blocks of group g: t < min(S, (g+1) DPG)
+              for (int t = 0; t < DPG; t++) {
+                const int nbk = b_count(S, DPG, t) < G - g ? b_count(S, DPG, t) : G - g;
+                if (nbk <= 0 || g * DPG - t >= S) continue;  // B slices or A rows all zero
+                const uint32_t idesc = nbk == 1 ? IDESC1 : (nbk == 2 ? IDESC2 : IDESC3);
 #pragma unroll
                 for (int h = 0; h < BS / Fmt<F>::KPI; h++) {
                   // one instruction's K = two core matrices = 256 bytes
                   const uint64_t aoff = (uint64_t)(((DPG - 1 + g * DPG - t) * C::SLICE + h * 256) >> 4);
-                  // B K-block t: slice t of one block, or of both blocks of a
-                  // pair side by side (N rows 0..bs-1 and bs..2bs-1)
-                  const uint64_t boff = (uint64_t)((NP * t * C::SLICE + h * 256) >> 4);
+                  // B: positions b_off(t) .. + nbk - 1, each one block's slice
+                  // or a pair's two slices side by side (N rows 0..bs-1 and
+                  // bs..2bs-1 of each position)
+                  const uint64_t boff =
+                      (uint64_t)((NP * b_off(S, DPG, t) * C::SLICE + h * 256) >> 4);
+                  const uint32_t acc = (g | t | h) ? 1u : first;
                   if (F == 0)
-                    tc_mma_bf16(dt, ad0 + aoff, bd0 + boff, IDESC, (t | h) ? 1u : first);
+                    tc_mma_bf16(dt, ad0 + aoff, bd0 + boff, idesc, acc);
                   else
-                    tc_mma_f8(dt, ad0 + aoff, bd0 + boff, IDESC, (t | h) ? 1u : first);
+                    tc_mma_f8(dt, ad0 + aoff, bd0 + boff, idesc, acc);
                 }
               }
             }
