@@ -41,6 +41,12 @@ def _cuda():
     assert torch.cuda.is_available(), "GPU tests need CUDA"
     torch.cuda.init()
     bsm.load()
+    yield
+    # hand the large products' memory back for the tests that follow
+    import gc
+    gc.collect()
+    bsm.bsm_release_memory()
+    torch.cuda.empty_cache()
 
 
 def host(x) -> np.ndarray:
