@@ -437,8 +437,12 @@ __device__ __forceinline__ void combine_digits(const int32_t (&a)[S], int64_t &h
   }
 }
 
-// Correctly rounded (hi 2^T + lo) 2^X as FP64; 64-bit path (branch-free
-// rounding) when the value fits in an int64, 128-bit path otherwise.
+// Correctly rounded (hi 2^T + lo) 2^X as FP64; 64-bit path when the value
+// fits in an int64, 128-bit path otherwise.  The 64-bit path rounds to nearest
+// even by adding 2^(sh-1) - 1 plus the kept part's lowest bit before the
+// shift, and adds the 53-bit significand (hidden bit included) to the
+// exponent field minus one, so that a rounding carry to 2^53 raises the
+// exponent by itself.
 // The general case (values beyond 64 bits, results in the subnormal or
 // overflow range): rare, and kept out of line so that none of its FP64
 // instructions is issued, predicated off, on the common path.
@@ -453,18 +457,17 @@ __device__ __forceinline__ double split_to_double(int64_t hi, int64_t lo, int X)
     if (v == 0) return 0.0;
     const uint64_t sign = (uint64_t)v & (1ull << 63);
     const uint64_t u = v < 0 ? (uint64_t)(-v) : (uint64_t)v;
-    int top = 63 - __clzll((long long)u);
-    const int sh = max(top - 52, 0);
-    uint64_t mant = (u << max(52 - top, 0)) >> sh;
-    const uint64_t rem = sh ? (u & ((1ull << sh) - 1)) : 0, half = sh ? (1ull << (sh - 1)) : 1;
-    mant += (uint64_t)((rem > half) | ((rem == half) & (mant & 1ull)));
-    const int carry = (int)(mant >> 53);  // rounding overflowed to 2^53
-    mant >>= carry;
-    top += carry;
+    const int top = 63 - __clzll((long long)u);
+    uint64_t q;
+    if (top <= 52) {
+      q = u << (52 - top);
+    } else {
+      const int sh = top - 52;
+      q = (u + ((1ull << (sh - 1)) - 1) + ((u >> sh) & 1ull)) >> sh;
+    }
     const int be = top + X + 1023;
-    if (__builtin_expect(be >= 1 && be <= 2046, 1))
-      return __longlong_as_double(
-          (long long)(sign | ((uint64_t)be << 52) | (mant & ((1ull << 52) - 1))));
+    if (__builtin_expect(be >= 1 && be <= 2045, 1))
+      return __longlong_as_double((long long)(sign | (((uint64_t)(be - 1) << 52) + q)));
   }
   return split_to_double_slow(hi, lo, T, X);
 }
@@ -775,16 +778,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
     int32_t *tcomb = comb + team * (C::COMB / 4);
     const int bar_id = 1 + team;
     uint32_t fct = 0;                     // flushes drained by this team
+    // nonzero flags of the team's previous item, written by thread 0 of the
+    // team once the next item's first barrier shows every warp's flag
+    int32_t *prev_nz = nullptr;
+    int64_t prev_c[2] = {-1, -1};
     for (uint32_t q = team;; q += NTEAM) {
       int m = q % kMeta;
       bool okm = mbar_wait(&meta_full[m], (q / kMeta) & 1u);
       // every decision below is uniform across the warp (tcgen05.ld is
-      // .sync.aligned) and, at the named barriers, across the team
+      // .sync.aligned) and, at the named barriers, across the team.  This
+      // barrier also ends the previous item: its warp flags are complete and
+      // its shared-memory diagonal buffer is free.
       if (named_bar_or(bar_id, kTeam, !okm || abort_flag != 0)) {
         set_err(P.err, DERR_TIMEOUT);
         abort_flag = 1;
         break;
       }
+      if (ttid == 0 && prev_nz) {
+#pragma unroll
+        for (int b = 0; b < NP; b++) {
+          int nzv = 0;
+          for (int w = 0; w < kTeamWarps; w++) nzv |= warp_any[team][b][w];
+          if (prev_c[b] >= 0) prev_nz[prev_c[b]] = nzv;
+        }
+      }
+      // (the flags are rewritten only after the next barrier, which thread 0
+      // reaches after reading them)
       const int nk = meta[m].nk;
       const int64_t cblk[2] = {meta[m].c, meta[m].c1};
       double *const cvp = meta[m].cv;
@@ -945,15 +964,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         const bool a = __any_sync(0xffffffffu, any[b]);
         if (lane == 0) warp_any[team][b][tw] = a;
       }
-      named_bar(bar_id, kTeam);  // warp_any complete; shared buffer free for the next item
-      if (ttid == 0) {
-#pragma unroll
-        for (int b = 0; b < NP; b++) {
-          int nzv = 0;
-          for (int w = 0; w < kTeamWarps; w++) nzv |= warp_any[team][b][w];
-          if (cblk[b] >= 0) nzp[cblk[b]] = nzv;
-        }
-      }
+      prev_nz = nzp;
+      prev_c[0] = cblk[0];
+      prev_c[1] = cblk[1];
     }
   }
   __syncthreads();
