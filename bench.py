@@ -727,7 +727,8 @@ def main():
     ap.add_argument("--workload", default="random", choices=["random", "decay", "rmat"],
                     help="decay: the decay-type A*A product (separate JSON line)")
     ap.add_argument("--points", type=int, default=20000, help="decay workload: number of points")
-    ap.add_argument("--bs", type=int, default=32, help="decay workload: leaf block size")
+    ap.add_argument("--bs", type=int, default=32, choices=[16, 32, 64],
+                    help="leaf block size (random and decay workloads)")
     ap.add_argument("--slices", default="7", help="decay workload: split slice counts, e.g. 3,5,7")
     ap.add_argument("--fp8-slices", default="", help="decay workload: FP8 split slice counts")
     ap.add_argument("--no-fp64", action="store_true", help="decay workload: skip the FP64 legs")
@@ -738,11 +739,18 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="matrix side (profiling runs only)")
     ap.add_argument("--p", type=float, default=None, help="block density (profiling runs only)")
     args = ap.parse_args()
-    if args.n is not None or args.p is not None:
+    if args.n is not None or args.p is not None or args.bs != 32:
+        # the random workload at another leaf size (each block position
+        # nonzero with the same p at that size), or a reduced profiling case
         WORKLOAD["n"] = args.n or WORKLOAD["n"]
         WORKLOAD["p"] = args.p or WORKLOAD["p"]
-        WORKLOAD["workload"] = (f"random block-sparse N={WORKLOAD['n']}, bs=32, block density "
-                                f"{WORKLOAD['p']}, N(0,1) (reduced profiling case)")
+        WORKLOAD["bs"] = args.bs
+        reduced = args.n is not None or args.p is not None
+        WORKLOAD["workload"] = (f"random block-sparse N={WORKLOAD['n']}, bs={args.bs}, block "
+                                f"density {WORKLOAD['p']}, N(0,1)"
+                                + (" (reduced profiling case)" if reduced else ""))
+        if args.bs != 32:
+            WORKLOAD["l2"] = "inputs larger than L2 (A+B about 1.4 GB, C over 10 GB)"
     if args.warmup < 3:
         log("warm-up raised to 3 steps")
         args.warmup = 3
