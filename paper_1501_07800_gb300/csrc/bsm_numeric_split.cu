@@ -291,9 +291,11 @@ void launch_slices(bsm_matrix A, bsm_matrix B, const int *rowexp, const int *col
                                                         bslot, bsl);
 }
 
-// Slice counts with a compiled pair kernel (32-wide blocks): BF16 6..8, E4M3 8, 12.
+// Slice counts with a compiled pair kernel (32-wide blocks): BF16 3..8, E4M3
+// 4, 6, 8, 12.
 inline bool pair_compiled(int fmt, int slices) {
-  return fmt == 0 ? (slices >= 6 && slices <= 8) : (slices == 8 || slices == 12);
+  return fmt == 0 ? (slices >= 3 && slices <= 8)
+                  : (slices == 4 || slices == 6 || slices == 8 || slices == 12);
 }
 
 // Slice counts with a compiled kernel: 1..8 for BF16, {2,3,4,6,8,12} for E4M3.
@@ -1009,7 +1011,8 @@ bsm_status launch_split_s(const SplitArgs &a, int fmt, int slices, int np, cudaS
   BSM_LS(0, 8)
   if constexpr (BS == 32) {
     BSM_LS(1, 2) BSM_LS(1, 3) BSM_LS(1, 4) BSM_LS(1, 6) BSM_LS(1, 8) BSM_LS(1, 12)
-    BSM_LP(0, 6) BSM_LP(0, 7) BSM_LP(0, 8) BSM_LP(1, 8) BSM_LP(1, 12)
+    BSM_LP(0, 3) BSM_LP(0, 4) BSM_LP(0, 5) BSM_LP(0, 6) BSM_LP(0, 7) BSM_LP(0, 8)
+    BSM_LP(1, 4) BSM_LP(1, 6) BSM_LP(1, 8) BSM_LP(1, 12)
   }
 #undef BSM_LS
 #undef BSM_LP
