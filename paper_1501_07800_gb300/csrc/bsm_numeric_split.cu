@@ -291,11 +291,11 @@ void launch_slices(bsm_matrix A, bsm_matrix B, const int *rowexp, const int *col
                                                         bslot, bsl);
 }
 
-// Slice counts with a compiled pair kernel (32-wide blocks): BF16 3..8, E4M3
-// 4, 6, 8, 12.
-inline bool pair_compiled(int fmt, int slices) {
-  return fmt == 0 ? (slices >= 3 && slices <= 8)
-                  : (slices == 4 || slices == 6 || slices == 8 || slices == 12);
+// Slice counts with a compiled pair kernel: BF16 3..8 (16- and 32-wide
+// blocks), E4M3 4, 6, 8, 12 (32-wide).
+inline bool pair_compiled(int bs, int fmt, int slices) {
+  if (fmt == 0) return (bs == 16 || bs == 32) && slices >= 3 && slices <= 8;
+  return bs == 32 && (slices == 4 || slices == 6 || slices == 8 || slices == 12);
 }
 
 // Slice counts with a compiled kernel: 1..8 for BF16, {2,3,4,6,8,12} for E4M3.
@@ -1014,6 +1014,9 @@ bsm_status launch_split_s(const SplitArgs &a, int fmt, int slices, int np, cudaS
     BSM_LP(0, 3) BSM_LP(0, 4) BSM_LP(0, 5) BSM_LP(0, 6) BSM_LP(0, 7) BSM_LP(0, 8)
     BSM_LP(1, 4) BSM_LP(1, 6) BSM_LP(1, 8) BSM_LP(1, 12)
   }
+  if constexpr (BS == 16) {
+    BSM_LP(0, 3) BSM_LP(0, 4) BSM_LP(0, 5) BSM_LP(0, 6) BSM_LP(0, 7) BSM_LP(0, 8)
+  }
 #undef BSM_LS
 #undef BSM_LP
   return BSM_ERR_INVALID_ARG;
@@ -1239,7 +1242,7 @@ ProdDesc make_desc(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, double
 // each A tile then serves twice the outputs.  BSM_SPLIT_PAIRS=0 / 1 in the
 // environment turns them off / on regardless of the list length.
 bool split_use_pairs(int bs, int spec, int64_t nt, int64_t nc) {
-  if (bs != 32 || !pair_compiled(split_spec_fmt(spec), split_spec_slices(spec))) return false;
+  if (!pair_compiled(bs, split_spec_fmt(spec), split_spec_slices(spec))) return false;
   const char *e = getenv("BSM_SPLIT_PAIRS");
   if (e && e[0] == '0') return false;
   if (e && e[0] == '1') return true;

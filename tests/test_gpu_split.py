@@ -354,12 +354,13 @@ PAIR_MODES = [(bsm.BSM_SPLIT_BF16, s) for s in (3, 4, 5, 6, 7, 8)] + \
              [(bsm.BSM_SPLIT_FP8, s) for s in (4, 6, 8, 12)]
 
 
-@pytest.mark.parametrize("prec,slices", PAIR_MODES)
-def test_pairs_equal_single_blocks(prec, slices):
-    """Two sibling C blocks per MMA (N = 64) give the same bits as one block
+@pytest.mark.parametrize("prec,slices,bs", [m + (32,) for m in PAIR_MODES] +
+                         [(bsm.BSM_SPLIT_BF16, s, 16) for s in (3, 7, 8)])
+def test_pairs_equal_single_blocks(prec, slices, bs):
+    """Two sibling C blocks per MMA (N = 2 bs) give the same bits as one block
     per MMA: the same exact digit sums, rounded once."""
-    A = synth.decay(260, 32, 660)
-    B = synth.random_blocks(A.ncols, 32, 0.3, 661, ncols=A.ncols + 70)  # odd block columns
+    A = synth.decay(260, bs, 660)
+    B = synth.random_blocks(A.ncols, bs, 0.3, 661, ncols=A.ncols + 70)  # odd block columns
     ga, gb = to_bsm(A), to_bsm(B)
     run = lambda: from_bsm(bsm.bsm_multiply(ga, gb, prec=prec, slices=slices))
     one = with_pairs("0", run)
