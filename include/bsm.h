@@ -263,7 +263,9 @@ bsm_status bsm_truncate(bsm_matrix M, double tau, bsm_matrix *out, int64_t *remo
  * bsm_multiply_batched -- C[i] = A[i]*B[i] for n independent products.
  * Symbolic phases run per product; the numeric phase of all products runs as
  * one persistent launch over a single work list ordered by decreasing work.
- * Results are identical to n calls of bsm_multiply with the same options.
+ * Results are identical to n calls of bsm_multiply with the same options
+ * (split products at a leaf size their kernels do not take -- 64, or 16 with
+ * E4M3 digits -- run on operands re-cut to 32 and are cut back, as there).
  *   n          number of products (>= 0)
  *   A, B       arrays of n handles
  *   C          array of n handle slots, filled on success (all NULL on error)
@@ -372,7 +374,10 @@ bsm_status bsm_update_values(bsm_matrix M, int64_t nblk, const int32_t *brow, co
  * graph that bsm_plan_execute replays as one persistent launch.  With
  * BSM_FLAG_AUTOTUNE in opts->flags the plan times candidate launch
  * configurations (work order, work items per claim, CTAs per SM) and keeps
- * the fastest.  All operands must share one block size.  The plan reads A[i],
+ * the fastest.  All operands must share one block size; split plans at a
+ * leaf size their kernels do not take (64, or 16 with E4M3 digits) compute on
+ * re-cut copies of the operands, refreshed at every execution, and return
+ * results at the operands' size.  The plan reads A[i],
  * B[i] at every execution: they must outlive it (use bsm_update_values to
  * change their values).  One eager run of the numeric phase is part of the
  * creation.

@@ -627,19 +627,55 @@ extern "C" bsm_status bsm_multiply_batched(int n, const bsm_matrix *A, const bsm
   int prec, slices;
   BSM_TRY(check_opts(opts, &prec, &slices, 0));
   if (prec != BSM_FP64)
-    for (int i = 0; i < n; i++) BSM_TRY(split_supported(A[i]->bs, slices));
+    for (int i = 0; i < n; i++) BSM_TRY(split_supported(split_width(prec, A[i]->bs), slices));
   cudaStream_t s = (cudaStream_t)stream;
   LastStats &ls = last_stats();
   ls = LastStats();
   int64_t l0 = launch_counter();
   bsm_status st = BSM_OK;
+  // Split products at a width their kernels do not take run on operands
+  // re-cut to the kernel's width (each distinct handle once); their results
+  // are cut back, exactly as bsm_multiply does (the split result does not
+  // depend on the leaf size).
+  std::vector<bsm_matrix> wa(A, A + n), wb(B, B + n), wc(n, nullptr), own;
+  auto recut = [&](bsm_matrix X, bsm_matrix *R) -> bsm_status {
+    const int w = split_width(prec, X->bs);
+    if (prec == BSM_FP64 || w == X->bs) {
+      *R = X;
+      return BSM_OK;
+    }
+    for (size_t k = 0; k < own.size(); k += 2)
+      if (own[k] == X) {
+        *R = own[k + 1];
+        return BSM_OK;
+      }
+    BSM_TRY(reblock_impl(X, w, 0, R, nullptr, s));
+    own.push_back(X);
+    own.push_back(*R);
+    return BSM_OK;
+  };
+  for (int i = 0; i < n && st == BSM_OK; i++) {
+    st = recut(A[i], &wa[i]);
+    if (st == BSM_OK) st = recut(B[i], &wb[i]);
+  }
   for (int bs : {16, 32, 64}) {
+    if (st != BSM_OK) break;
     std::vector<int> idx;
     for (int i = 0; i < n; i++)
-      if (A[i]->bs == bs) idx.push_back(i);
+      if (wa[i]->bs == bs) idx.push_back(i);
     if (idx.empty()) continue;
-    if ((st = batched_group(idx, A, B, C, prec, slices, s)) != BSM_OK) break;
+    st = batched_group(idx, wa.data(), wb.data(), wc.data(), prec, slices, s);
   }
+  for (int i = 0; i < n; i++) {
+    if (st == BSM_OK && wc[i] && wa[i] != A[i]) {
+      st = reblock_impl(wc[i], A[i]->bs, 0, &C[i], nullptr, s);
+      bsm_destroy(wc[i]);
+    } else {
+      C[i] = wc[i];
+    }
+    wc[i] = nullptr;
+  }
+  for (size_t k = 1; k < own.size(); k += 2) bsm_destroy(own[k]);
   ls.launches = launch_counter() - l0;
   if (st != BSM_OK) {
     for (int i = 0; i < n; i++) {

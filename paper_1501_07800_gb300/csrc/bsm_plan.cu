@@ -331,6 +331,13 @@ extern "C" bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matr
   for (int i = 0; i < n; i++)
     if (A[i]->bs != bs || B[i]->bs != bs) return BSM_ERR_BLOCKSIZE;  // one block size per plan
   if (tune_bs) return create_tuned_bs(n, A, B, o, (cudaStream_t)stream, out);
+  if (prec != BSM_FP64 && split_width(prec, bs) != bs) {
+    // split kernels of another width: a wrapper plan on re-cut operands,
+    // results cut back (the split result does not depend on the leaf size)
+    bsm_mult_opts oi = o;
+    oi.flags |= tune;
+    return create_at_bs(n, A, B, oi, split_width(prec, bs), (cudaStream_t)stream, out);
+  }
   if (prec != BSM_FP64) BSM_TRY(split_supported(bs, slices));
 
   bsm_plan P = new bsm_plan_s();

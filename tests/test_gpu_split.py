@@ -424,3 +424,31 @@ def test_batched_with_sibling_pairs():
         E = oracle.multiply(a, b).C
         assert_same_structure(y, E)
         assert relerr(y.vals, E.vals) < TOL_SPLIT
+
+
+@pytest.mark.parametrize("prec,slices,bs", [(bsm.BSM_SPLIT_BF16, 7, 64), (bsm.BSM_SPLIT_FP8, 12, 64),
+                                            (bsm.BSM_SPLIT_FP8, 12, 16)])
+def test_recut_batched_and_plan_equal_single(prec, slices, bs):
+    """Batched products and plans at a leaf size the split kernels do not take
+    run on re-cut operands and give the bits of single products (which are
+    tested against the bs-32 product of the same matrices above)."""
+    pairs = synth.batched(4, 650 + bs, bs=bs, nmin=8 * bs, nmax=40 * bs, dmin=0.05, dmax=0.3)
+    As = [to_bsm(a) for a, _ in pairs]
+    Bs = [to_bsm(b) for _, b in pairs]
+    As.append(As[0])  # a handle used twice, and a square
+    Bs.append(As[0])
+    single = [from_bsm(bsm.bsm_multiply(a, b, prec=prec, slices=slices)) for a, b in zip(As, Bs)]
+    batched = [from_bsm(c) for c in bsm.bsm_multiply_batched(As, Bs, prec=prec, slices=slices)]
+    plan = bsm.bsm_plan_create(As, Bs, prec=prec, slices=slices)
+    assert bsm.bsm_plan_block_size(plan) == 32
+    bsm.bsm_plan_execute(plan)
+    planned = [from_bsm(c) for c in bsm.bsm_plan_results(plan)]
+    for one, b, p in zip(single, batched, planned):
+        assert one.bs == b.bs == p.bs == bs
+        assert_same_structure(b, one)
+        assert np.array_equal(b.vals, one.vals)
+        assert_same_structure(p, one)
+        assert np.array_equal(p.vals, one.vals)
+    E = oracle.multiply(*pairs[0]).C
+    assert_same_structure(single[0], E)
+    assert relerr(single[0].vals, E.vals) < TOL_SPLIT
