@@ -342,6 +342,20 @@ bsm_status bsm_set_timing(int on);
 bsm_status bsm_release_memory(void);
 
 /*
+ * bsm_set_memory_limit -- cap the device memory the library's allocations
+ * may hold in the current device's default pool: an allocation that would
+ * take the pool's in-use bytes above `bytes` fails with OOM, and the call
+ * that needed it returns OOM after freeing what it had allocated.  0 removes
+ * the cap (the default).  Process-wide.  Meant for callers that share the
+ * device and for fault injection in tests.
+ * bsm_memory_in_use -- the pool's bytes in use by live allocations (handles,
+ * plans, work in flight); synchronises the current device first.
+ * Errors: INVALID_ARG (NULL bytes), CUDA.
+ */
+bsm_status bsm_set_memory_limit(uint64_t bytes);
+bsm_status bsm_memory_in_use(uint64_t *bytes);
+
+/*
  * bsm_last_phase_ms -- results of the last timed bsm_multiply on this thread.
  *   ms        double[cap]: ms[0] symbolic phase, ms[1] numeric phase (the
  *             numeric kernel plus, in split modes, the slicing kernels),

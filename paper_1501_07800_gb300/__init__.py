@@ -55,6 +55,8 @@ _PROTOS = {
     "bsm_last_chunks": (_I32, [_P]),
     "bsm_set_timing": (_I32, [_I32]),
     "bsm_release_memory": (_I32, []),
+    "bsm_set_memory_limit": (_I32, [ctypes.c_uint64]),
+    "bsm_memory_in_use": (_I32, [_P]),
     "bsm_last_phase_ms": (_I32, [_P, _I32, _P, _P]),
     "bsm_block_products_fp64_noalloc": (_I32, [_I32, _I64, _P, _P, _P, _P, _I64, _P, _I64, _P,
                                                 _P, _P]),
@@ -369,6 +371,19 @@ def bsm_last_chunks() -> int:
 
 def bsm_set_timing(on: bool):
     _check(load().bsm_set_timing(1 if on else 0), "bsm_set_timing")
+
+
+def bsm_set_memory_limit(nbytes: int):
+    """Cap the library's device pool usage (0: no cap); allocations beyond it
+    make the call return BSM_ERR_OOM."""
+    _check(load().bsm_set_memory_limit(int(nbytes)), "bsm_set_memory_limit")
+
+
+def bsm_memory_in_use() -> int:
+    """Bytes of the library's device pool held by live allocations."""
+    v = ctypes.c_uint64()
+    _check(load().bsm_memory_in_use(ctypes.byref(v)), "bsm_memory_in_use")
+    return v.value
 
 
 def bsm_release_memory():

@@ -7,8 +7,19 @@
 #include <functional>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/bsm.h"
 #include "bsm_batch.cuh"
+
+// NVTX range for the duration of a scope (visible to profilers; a no-op
+// without one attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 #define BSM_MAXH 31  // tree heights 0..31: up to 2^31 blocks per side
 

@@ -45,14 +45,17 @@ bsm_status check_opts(const bsm_mult_opts *o, int *prec, int *slices, int allowe
 }
 
 // Assembles C from the numeric result: drops exactly-zero blocks and builds
-// the level arrays.  Takes ownership of sym->ckeys and cvals.
+// the level arrays.  Takes ownership of sym->ckeys and cvals (freed on error).
 bsm_status finish_product(bsm_matrix C, SymbolicResult *sym, double *cvals, int32_t *nz,
                           unsigned *err, cudaStream_t s) {
   int64_t nc = sym->nc;
   int bs = C->bs;
   int32_t *pos = nullptr;
   bsm_status st = dev_alloc((void **)&pos, 4 * (nc + 1), s);
-  if (st != BSM_OK) return st;
+  if (st != BSM_OK) {
+    dev_free(cvals, s);
+    return st;
+  }
   st = scan_exclusive_i32(nz, pos, nc, s);
   int32_t *h = (int32_t *)host_scratch().get(16);
   if (st == BSM_OK && !h) st = BSM_ERR_OOM;
@@ -66,6 +69,7 @@ bsm_status finish_product(bsm_matrix C, SymbolicResult *sym, double *cvals, int3
   if (st == BSM_OK && h[2] != DERR_NONE) st = BSM_ERR_CUDA;
   if (st != BSM_OK) {
     dev_free(pos, s);
+    dev_free(cvals, s);
     return st;
   }
   int64_t nkeep = (int64_t)h[0] + h[1];
@@ -86,6 +90,7 @@ bsm_status finish_product(bsm_matrix C, SymbolicResult *sym, double *cvals, int3
       dev_free(ovals, s);
       dev_free(idx, s);
       dev_free(pos, s);
+      dev_free(cvals, s);
       return st;
     }
     count_launch();
@@ -312,8 +317,11 @@ static bsm_status multiply_chunked(bsm_matrix A, bsm_matrix B, int prec, int sli
       return e;
     }
     if (timed) cudaEventRecord(ea, s);
-    e = prec == BSM_FP64 ? numeric_fp64(A, B, r, cvals, nz, err, s)
-                         : numeric_split(A, B, r, slices, cvals, nz, err, s);
+    {
+      NvtxRange numeric(prec == BSM_FP64 ? "numeric fp64" : "numeric split");
+      e = prec == BSM_FP64 ? numeric_fp64(A, B, r, cvals, nz, err, s)
+                           : numeric_split(A, B, r, slices, cvals, nz, err, s);
+    }
     if (timed) cudaEventRecord(eb, s);
     Chunk c{nullptr, nullptr, 0};
     if (e == BSM_OK) e = compact_chunk(r, cvals, nz, err, bs, &c.keys, &c.vals, &c.n, s);
@@ -401,6 +409,7 @@ static bsm_status multiply_chunked(bsm_matrix A, bsm_matrix B, int prec, int sli
 
 extern "C" bsm_status bsm_multiply(bsm_matrix A, bsm_matrix B, bsm_matrix *C,
                                    const bsm_mult_opts *opts, void *stream) {
+  NvtxRange range("bsm_multiply");
   if (!C) return BSM_ERR_INVALID_ARG;
   *C = nullptr;
   if (!A || !B) return BSM_ERR_INVALID_ARG;
@@ -621,6 +630,7 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
 extern "C" bsm_status bsm_multiply_batched(int n, const bsm_matrix *A, const bsm_matrix *B,
                                            bsm_matrix *C, const bsm_mult_opts *opts,
                                            void *stream) {
+  NvtxRange range("bsm_multiply_batched");
   if (n < 0 || (n > 0 && (!A || !B || !C))) return BSM_ERR_INVALID_ARG;
   for (int i = 0; i < n; i++) C[i] = nullptr;
   for (int i = 0; i < n; i++) BSM_TRY(check_pair(A[i], B[i]));

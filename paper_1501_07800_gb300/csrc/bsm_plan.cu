@@ -317,6 +317,7 @@ bsm_status create_tuned_bs(int n, const bsm_matrix *A, const bsm_matrix *B, bsm_
 
 extern "C" bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matrix *B,
                                       const bsm_mult_opts *opts, void *stream, bsm_plan *out) {
+  NvtxRange range("bsm_plan_create");
   if (!out) return BSM_ERR_INVALID_ARG;
   *out = nullptr;
   if (n < 1 || !A || !B) return BSM_ERR_INVALID_ARG;
@@ -454,6 +455,7 @@ extern "C" bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matr
 
 extern "C" bsm_status bsm_plan_execute(bsm_plan P, void *stream) {
   if (!P) return BSM_ERR_INVALID_ARG;
+  NvtxRange range("bsm_plan_execute");
   cudaStream_t cs = (cudaStream_t)stream;
   if (P->inner) return execute_wrapped(P, cs);
   BSM_CUDA(cudaEventRecord(P->ev_in, cs));

@@ -324,6 +324,7 @@ static bsm_status build_from_device(int64_t nrows, int64_t ncols, int bs, int64_
 extern "C" bsm_status bsm_build(int64_t nrows, int64_t ncols, int bs, int64_t nblk,
                                 const int32_t *brow, const int32_t *bcol, const double *vals,
                                 int on_device, void *stream, bsm_matrix *out) {
+  NvtxRange range("bsm_build");
   if (!out) return BSM_ERR_INVALID_ARG;
   *out = nullptr;
   if (nrows < 0 || ncols < 0 || nblk < 0 || (on_device != 0 && on_device != 1))
@@ -363,6 +364,7 @@ extern "C" bsm_status bsm_build(int64_t nrows, int64_t ncols, int bs, int64_t nb
 
 extern "C" bsm_status bsm_to_blocks(bsm_matrix M, int64_t *nblk_inout, int32_t *brow,
                                     int32_t *bcol, double *vals, int on_device, void *stream) {
+  NvtxRange range("bsm_to_blocks");
   if (!M || !nblk_inout || (on_device != 0 && on_device != 1)) return BSM_ERR_INVALID_ARG;
   int64_t cap = *nblk_inout;
   *nblk_inout = M->nblk;

@@ -2,6 +2,7 @@
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
+#include <atomic>
 #include <cstdlib>
 #include <mutex>
 
@@ -31,12 +32,25 @@ static void configure_pool_once(int dev) {
   done[dev] = true;
 }
 
+// Cap on the pool's in-use bytes (bsm_set_memory_limit); 0 = none.
+static std::atomic<uint64_t> g_mem_limit{0};
+
 bsm_status dev_alloc(void **p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
   int dev = 0;
   cudaGetDevice(&dev);
   configure_pool_once(dev);
+  if (const uint64_t cap = g_mem_limit.load(std::memory_order_relaxed)) {
+    cudaMemPool_t pool;
+    uint64_t used = 0;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) {
+      cudaGetLastError();
+      return BSM_ERR_CUDA;
+    }
+    if (used + bytes > cap) return BSM_ERR_OOM;
+  }
   cudaError_t e = cudaMallocAsync(p, bytes, s);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -105,6 +119,24 @@ extern "C" bsm_status bsm_release_memory(void) {
   cudaMemPool_t pool;
   BSM_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
   BSM_CUDA(cudaMemPoolTrimTo(pool, 0));
+  return BSM_OK;
+}
+
+extern "C" bsm_status bsm_set_memory_limit(uint64_t bytes) {
+  g_mem_limit.store(bytes, std::memory_order_relaxed);
+  return BSM_OK;
+}
+
+extern "C" bsm_status bsm_memory_in_use(uint64_t *bytes) {
+  if (!bytes) return BSM_ERR_INVALID_ARG;
+  int dev = 0;
+  BSM_CUDA(cudaGetDevice(&dev));
+  BSM_CUDA(cudaDeviceSynchronize());
+  cudaMemPool_t pool;
+  BSM_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t used = 0;
+  BSM_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+  *bytes = used;
   return BSM_OK;
 }
 

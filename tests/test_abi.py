@@ -82,6 +82,8 @@ def test_argument_checks_before_any_device_work(lib):
     assert lib.bsm_node_norms2(None, 0, None, None, None, ctypes.byref(n), 0, None) == -1
     assert lib.bsm_truncate(None, ctypes.c_double(1.0), ctypes.byref(out), None, None, None) == -1
     assert lib.bsm_destroy(None) == 0
+    assert lib.bsm_memory_in_use(None) == -1
+    assert lib.bsm_set_memory_limit(ctypes.c_uint64(0)) == 0
 
 
 def test_misaligned_device_pointers_rejected_before_any_work(lib):
