@@ -72,6 +72,11 @@ typedef struct {
                  6, 8 or 12 (default 6, 24 bits) */
   int flags;  /* 0, BSM_FLAG_AUTOTUNE (bsm_plan_create only), or
                  BSM_FLAG_TRANS_A / BSM_FLAG_TRANS_B (bsm_multiply only) */
+  int bs;     /* leaf size to compute at (bsm_multiply, bsm_multiply_batched,
+                 bsm_plan_create): 0 = the operands' own, which must then be
+                 equal; 16, 32 or 64 = operands of another size are re-cut to
+                 it exactly (bsm_reblock; plans refresh their re-cut copies
+                 at every execution) and C has this size */
 } bsm_mult_opts;
 
 /* bsm_plan_create: measure candidate launch configurations and keep the

@@ -84,7 +84,8 @@ class BsmError(RuntimeError):
 
 
 class bsm_mult_opts(ctypes.Structure):
-    _fields_ = [("prec", ctypes.c_int), ("slices", ctypes.c_int), ("flags", ctypes.c_int)]
+    _fields_ = [("prec", ctypes.c_int), ("slices", ctypes.c_int), ("flags", ctypes.c_int),
+                ("bs", ctypes.c_int)]
 
 
 def load(path: str | None = None):
@@ -177,20 +178,22 @@ def bsm_build(nrows: int, ncols: int, bs: int, brow, bcol, vals, stream=None) ->
     return Matrix(out.value)
 
 
-def _opts(prec: int, slices: int, flags: int = 0):
-    if prec == BSM_FP64 and slices == 0 and flags == 0:
+def _opts(prec: int, slices: int, flags: int = 0, bs: int = 0):
+    if prec == BSM_FP64 and slices == 0 and flags == 0 and bs == 0:
         return None
-    return ctypes.byref(bsm_mult_opts(prec, slices, flags))
+    return ctypes.byref(bsm_mult_opts(prec, slices, flags, bs))
 
 
 def bsm_multiply(A: Matrix, B: Matrix, prec: int = BSM_FP64, slices: int = 0,
-                 stream=None, trans_a: bool = False, trans_b: bool = False) -> Matrix:
-    """C = op(A) op(B); op(X) = X^T when trans_x is set."""
+                 stream=None, trans_a: bool = False, trans_b: bool = False,
+                 bs: int = 0) -> Matrix:
+    """C = op(A) op(B); op(X) = X^T when trans_x is set.  bs: leaf size to
+    compute at (operands re-cut to it; 0 = theirs)."""
     lib = load()
     out = ctypes.c_void_p()
     flags = (BSM_FLAG_TRANS_A if trans_a else 0) | (BSM_FLAG_TRANS_B if trans_b else 0)
-    code = lib.bsm_multiply(A.handle, B.handle, ctypes.byref(out), _opts(prec, slices, flags),
-                            _stream_ptr(stream))
+    code = lib.bsm_multiply(A.handle, B.handle, ctypes.byref(out),
+                            _opts(prec, slices, flags, bs), _stream_ptr(stream))
     _check(code, "bsm_multiply")
     return Matrix(out.value)
 
@@ -282,7 +285,8 @@ def bsm_truncate(M: Matrix, tau: float, stream=None):
     return Matrix(out.value), rem.value, bound.value
 
 
-def bsm_multiply_batched(As, Bs, prec: int = BSM_FP64, slices: int = 0, stream=None):
+def bsm_multiply_batched(As, Bs, prec: int = BSM_FP64, slices: int = 0, stream=None,
+                         bs: int = 0):
     lib = load()
     n = len(As)
     if len(Bs) != n:
@@ -290,7 +294,8 @@ def bsm_multiply_batched(As, Bs, prec: int = BSM_FP64, slices: int = 0, stream=N
     ha = (ctypes.c_void_p * max(n, 1))(*[a.handle for a in As])
     hb = (ctypes.c_void_p * max(n, 1))(*[b.handle for b in Bs])
     hc = (ctypes.c_void_p * max(n, 1))()
-    code = lib.bsm_multiply_batched(n, ha, hb, hc, _opts(prec, slices), _stream_ptr(stream))
+    code = lib.bsm_multiply_batched(n, ha, hb, hc, _opts(prec, slices, 0, bs),
+                                    _stream_ptr(stream))
     _check(code, "bsm_multiply_batched")
     return [Matrix(hc[i]) for i in range(n)]
 
@@ -457,13 +462,13 @@ class Plan:
 
 
 def bsm_plan_create(As, Bs, prec: int = BSM_FP64, slices: int = 0, autotune: bool = False,
-                    stream=None, autotune_bs: bool = False) -> Plan:
+                    stream=None, autotune_bs: bool = False, bs: int = 0) -> Plan:
     lib = load()
     n = len(As)
     ha = (ctypes.c_void_p * max(n, 1))(*[a.handle for a in As])
     hb = (ctypes.c_void_p * max(n, 1))(*[b.handle for b in Bs])
     flags = (BSM_FLAG_AUTOTUNE if autotune else 0) | (BSM_FLAG_AUTOTUNE_BS if autotune_bs else 0)
-    opts = bsm_mult_opts(prec, slices, flags)
+    opts = bsm_mult_opts(prec, slices, flags, bs)
     out = ctypes.c_void_p()
     code = lib.bsm_plan_create(n, ha, hb, ctypes.byref(opts), _stream_ptr(stream),
                                ctypes.byref(out))

@@ -38,6 +38,7 @@ bsm_status check_opts(const bsm_mult_opts *o, int *prec, int *slices, int allowe
     return BSM_ERR_INVALID_ARG;
   const int maxs = o->prec == BSM_SPLIT_FP8 ? 12 : 8;
   if (o->slices < 0 || o->slices > maxs) return BSM_ERR_INVALID_ARG;
+  if (o->bs != 0 && o->bs != 16 && o->bs != 32 && o->bs != 64) return BSM_ERR_BLOCKSIZE;
   *prec = o->prec;
   if (o->prec == BSM_SPLIT_BF16) *slices = split_spec(0, o->slices == 0 ? 7 : o->slices);
   if (o->prec == BSM_SPLIT_FP8) *slices = split_spec(1, o->slices == 0 ? 6 : o->slices);
@@ -416,23 +417,33 @@ extern "C" bsm_status bsm_multiply(bsm_matrix A, bsm_matrix B, bsm_matrix *C,
   int prec, slices;
   BSM_TRY(check_opts(opts, &prec, &slices, BSM_FLAG_TRANS_A | BSM_FLAG_TRANS_B));
   const int flags = opts ? opts->flags : 0;
+  const int obs = opts ? opts->bs : 0;
   const bool ta = flags & BSM_FLAG_TRANS_A, tb = flags & BSM_FLAG_TRANS_B;
   // op(A) and op(B) dimensions are checked before any transposition is made.
   if ((ta ? A->nrows : A->ncols) != (tb ? B->ncols : B->nrows)) return BSM_ERR_DIM_MISMATCH;
-  if (A->bs != B->bs) return BSM_ERR_BLOCKSIZE;
+  if (!obs && A->bs != B->bs) return BSM_ERR_BLOCKSIZE;
   if (A->device != B->device) return BSM_ERR_INVALID_ARG;
-  if (prec != BSM_FP64) BSM_TRY(split_supported(split_width(prec, A->bs), slices));
+  const int cbs = obs ? obs : A->bs;  // the leaf size the product is computed at
+  if (prec != BSM_FP64) BSM_TRY(split_supported(split_width(prec, cbs), slices));
   cudaStream_t s = (cudaStream_t)stream;
+  // Operands of another leaf size are re-cut exactly (same entries, zero
+  // blocks dropped), once per distinct handle.
+  bsm_matrix Ar = nullptr, Br = nullptr;
+  bsm_status st = BSM_OK;
+  if (A->bs != cbs) st = reblock_impl(A, cbs, 0, &Ar, nullptr, s);
+  if (st == BSM_OK && B->bs != cbs) st = B == A ? (Br = Ar, BSM_OK) : reblock_impl(B, cbs, 0, &Br, nullptr, s);
+  bsm_matrix a = Ar ? Ar : A, b = Br ? Br : B;
   // The transposed task types (Sec. 3.2) are the plain product of transposed
   // handles: op(X) is X with its keys' row and column bits swapped and every
   // block transposed, made once here and released after the product.
   bsm_matrix At = nullptr, Bt = nullptr;
-  bsm_status st = BSM_OK;
-  if (ta) st = bsm_transpose(A, &At, stream);
-  if (st == BSM_OK && tb) st = (A == B && ta) ? (Bt = At, BSM_OK) : bsm_transpose(B, &Bt, stream);
-  if (st == BSM_OK) st = multiply_one(ta ? At : A, tb ? Bt : B, prec, slices, s, C);
+  if (st == BSM_OK && ta) st = bsm_transpose(a, &At, stream);
+  if (st == BSM_OK && tb) st = (a == b && ta) ? (Bt = At, BSM_OK) : bsm_transpose(b, &Bt, stream);
+  if (st == BSM_OK) st = multiply_one(ta ? At : a, tb ? Bt : b, prec, slices, s, C);
   if (Bt && Bt != At) bsm_destroy(Bt);
   if (At) bsm_destroy(At);
+  if (Br && Br != Ar) bsm_destroy(Br);
+  if (Ar) bsm_destroy(Ar);
   return st;
 }
 
@@ -633,24 +644,36 @@ extern "C" bsm_status bsm_multiply_batched(int n, const bsm_matrix *A, const bsm
   NvtxRange range("bsm_multiply_batched");
   if (n < 0 || (n > 0 && (!A || !B || !C))) return BSM_ERR_INVALID_ARG;
   for (int i = 0; i < n; i++) C[i] = nullptr;
-  for (int i = 0; i < n; i++) BSM_TRY(check_pair(A[i], B[i]));
   int prec, slices;
   BSM_TRY(check_opts(opts, &prec, &slices, 0));
+  const int obs = opts ? opts->bs : 0;  // leaf size override (0: the operands')
+  for (int i = 0; i < n; i++) {
+    if (!A[i] || !B[i]) return BSM_ERR_INVALID_ARG;
+    if (A[i]->ncols != B[i]->nrows) return BSM_ERR_DIM_MISMATCH;
+    if (!obs && A[i]->bs != B[i]->bs) return BSM_ERR_BLOCKSIZE;
+    if (A[i]->device != B[i]->device) return BSM_ERR_INVALID_ARG;
+  }
   if (prec != BSM_FP64)
-    for (int i = 0; i < n; i++) BSM_TRY(split_supported(split_width(prec, A[i]->bs), slices));
+    for (int i = 0; i < n; i++)
+      BSM_TRY(split_supported(split_width(prec, obs ? obs : A[i]->bs), slices));
   cudaStream_t s = (cudaStream_t)stream;
   LastStats &ls = last_stats();
   ls = LastStats();
   int64_t l0 = launch_counter();
   bsm_status st = BSM_OK;
-  // Split products at a width their kernels do not take run on operands
-  // re-cut to the kernel's width (each distinct handle once); their results
-  // are cut back, exactly as bsm_multiply does (the split result does not
-  // depend on the leaf size).
+  // Operands are re-cut (each distinct handle once) to the override size, and
+  // split products at a width their kernels do not take to the kernel's
+  // width; results are cut back to the override size or the operands' own,
+  // exactly as bsm_multiply does (the split result does not depend on the
+  // leaf size).
   std::vector<bsm_matrix> wa(A, A + n), wb(B, B + n), wc(n, nullptr), own;
+  auto target = [&](bsm_matrix X) {
+    const int b = obs ? obs : X->bs;
+    return prec == BSM_FP64 ? b : split_width(prec, b);
+  };
   auto recut = [&](bsm_matrix X, bsm_matrix *R) -> bsm_status {
-    const int w = split_width(prec, X->bs);
-    if (prec == BSM_FP64 || w == X->bs) {
+    const int w = target(X);
+    if (w == X->bs) {
       *R = X;
       return BSM_OK;
     }
@@ -677,8 +700,9 @@ extern "C" bsm_status bsm_multiply_batched(int n, const bsm_matrix *A, const bsm
     st = batched_group(idx, wa.data(), wb.data(), wc.data(), prec, slices, s);
   }
   for (int i = 0; i < n; i++) {
-    if (st == BSM_OK && wc[i] && wa[i] != A[i]) {
-      st = reblock_impl(wc[i], A[i]->bs, 0, &C[i], nullptr, s);
+    const int rbs = obs ? obs : A[i]->bs;  // the result's leaf size
+    if (st == BSM_OK && wc[i] && wc[i]->bs != rbs) {
+      st = reblock_impl(wc[i], rbs, 0, &C[i], nullptr, s);
       bsm_destroy(wc[i]);
     } else {
       C[i] = wc[i];

@@ -218,16 +218,17 @@ bsm_status execute_wrapped(bsm_plan W, cudaStream_t cs) {
   return bsm_plan_execute(W->inner, cs);
 }
 
-// A wrapper plan computing at block size cb (== the operands' own: no copies).
+// A wrapper plan computing at block size cb on re-cut copies of the operands
+// (operands already of size cb are used as they are); results at user_bs.
 bsm_status create_at_bs(int n, const bsm_matrix *A, const bsm_matrix *B, const bsm_mult_opts &o,
-                        int cb, cudaStream_t cs, bsm_plan *out) {
+                        int cb, int user_bs, cudaStream_t cs, bsm_plan *out) {
   *out = nullptr;
   bsm_plan W = new bsm_plan_s();
   cudaGetDevice(&W->device);
   W->n = n;
   W->prec = o.prec;
   W->bs = cb;
-  W->user_bs = A[0]->bs;
+  W->user_bs = user_bs;
   W->A.assign(A, A + n);
   W->B.assign(B, B + n);
   std::vector<bsm_matrix> ia(n), ib(n);
@@ -282,7 +283,7 @@ bsm_status create_tuned_bs(int n, const bsm_matrix *A, const bsm_matrix *B, bsm_
   }
   for (int cb : cands) {
     bsm_plan W = nullptr;
-    bsm_status st = create_at_bs(n, A, B, o, cb, cs, &W);
+    bsm_status st = create_at_bs(n, A, B, o, cb, A[0]->bs, cs, &W);
     float ms = 1e30f;
     for (int r = 0; r < 2 && st == BSM_OK; r++) {  // the first run warms up
       cudaEventRecord(a, cs);
@@ -321,14 +322,26 @@ extern "C" bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matr
   if (!out) return BSM_ERR_INVALID_ARG;
   *out = nullptr;
   if (n < 1 || !A || !B) return BSM_ERR_INVALID_ARG;
-  for (int i = 0; i < n; i++) BSM_TRY(check_pair(A[i], B[i]));
   int tune = opts ? (opts->flags & BSM_FLAG_AUTOTUNE) : 0;
   const int tune_bs = opts ? (opts->flags & BSM_FLAG_AUTOTUNE_BS) : 0;
-  bsm_mult_opts o = opts ? *opts : bsm_mult_opts{BSM_FP64, 0, 0};
+  bsm_mult_opts o = opts ? *opts : bsm_mult_opts{BSM_FP64, 0, 0, 0};
   o.flags &= ~(BSM_FLAG_AUTOTUNE | BSM_FLAG_AUTOTUNE_BS);
   int prec, slices;
   BSM_TRY(check_opts(&o, &prec, &slices, 0));
+  const int obs = o.bs;  // leaf size override: operands re-cut to it, results at it
+  o.bs = 0;
+  if (obs && tune_bs) return BSM_ERR_INVALID_ARG;
+  for (int i = 0; i < n; i++) {
+    if (!A[i] || !B[i]) return BSM_ERR_INVALID_ARG;
+    if (A[i]->ncols != B[i]->nrows) return BSM_ERR_DIM_MISMATCH;
+    if (A[i]->device != B[i]->device) return BSM_ERR_INVALID_ARG;
+  }
   const int bs = A[0]->bs;
+  if (obs) {
+    bsm_mult_opts oi = o;
+    oi.flags |= tune;
+    return create_at_bs(n, A, B, oi, obs, obs, (cudaStream_t)stream, out);
+  }
   for (int i = 0; i < n; i++)
     if (A[i]->bs != bs || B[i]->bs != bs) return BSM_ERR_BLOCKSIZE;  // one block size per plan
   if (tune_bs) return create_tuned_bs(n, A, B, o, (cudaStream_t)stream, out);
@@ -337,7 +350,7 @@ extern "C" bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matr
     // results cut back (the split result does not depend on the leaf size)
     bsm_mult_opts oi = o;
     oi.flags |= tune;
-    return create_at_bs(n, A, B, oi, split_width(prec, bs), (cudaStream_t)stream, out);
+    return create_at_bs(n, A, B, oi, split_width(prec, bs), bs, (cudaStream_t)stream, out);
   }
   if (prec != BSM_FP64) BSM_TRY(split_supported(bs, slices));
 

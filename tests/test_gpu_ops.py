@@ -185,3 +185,62 @@ def test_reblock_round_trip_and_product():
     E = oracle.multiply(A, B).C
     assert_same_structure(C64, E)
     assert relerr(C64.vals, E.vals) < TOL
+
+
+# ---------------------------------------------------- leaf-size override
+def _recut(m: synth.BlockCOO, bs: int) -> synth.BlockCOO:
+    return synth.from_dense(m.to_dense(), bs)
+
+
+@pytest.mark.parametrize("abs_,bbs,cbs", [(32, 16, 32), (16, 16, 64), (64, 32, 16)])
+def test_bs_override_equals_product_of_recut_operands(abs_, bbs, cbs):
+    """opts.bs: operands of any sizes are re-cut exactly to the requested
+    size; the product equals, bit for bit, the product of operands built at
+    that size, and C has that size."""
+    n = 23 * 16 + 5
+    A = synth.random_blocks(n, abs_, 0.25, 700 + abs_)
+    B = synth.random_blocks(n, bbs, 0.25, 701 + bbs)
+    ga, gb = to_bsm(A), to_bsm(B)
+    want = from_bsm(bsm.bsm_multiply(to_bsm(_recut(A, cbs)), to_bsm(_recut(B, cbs))))
+    got = from_bsm(bsm.bsm_multiply(ga, gb, bs=cbs))
+    assert got.bs == cbs
+    assert_same_structure(got, want)
+    assert np.array_equal(got.vals, want.vals)
+    E = oracle.multiply(_recut(A, cbs), _recut(B, cbs)).C
+    assert_same_structure(got, E)
+    assert relerr(got.vals, E.vals) < 1e-12
+    # transposed, split, batched and planned forms take the same override
+    gt = from_bsm(bsm.bsm_multiply(gb, ga, trans_a=True, trans_b=True, bs=cbs))
+    wt = from_bsm(bsm.bsm_multiply(to_bsm(_recut(B, cbs)), to_bsm(_recut(A, cbs)),
+                                   trans_a=True, trans_b=True))
+    assert_same_structure(gt, wt)
+    assert np.array_equal(gt.vals, wt.vals)
+    ws = from_bsm(bsm.bsm_multiply(to_bsm(_recut(A, cbs)), to_bsm(_recut(B, cbs)),
+                                   prec=bsm.BSM_SPLIT_BF16))
+    gs = from_bsm(bsm.bsm_multiply(ga, gb, prec=bsm.BSM_SPLIT_BF16, bs=cbs))
+    assert_same_structure(gs, ws)
+    assert np.array_equal(gs.vals, ws.vals)
+    for prec, w in ((bsm.BSM_FP64, want), (bsm.BSM_SPLIT_BF16, ws)):
+        gbt = [from_bsm(c) for c in bsm.bsm_multiply_batched([ga, ga], [gb, gb], prec=prec,
+                                                             bs=cbs)]
+        plan = bsm.bsm_plan_create([ga], [gb], prec=prec, bs=cbs)
+        bsm.bsm_plan_execute(plan)
+        gp = from_bsm(bsm.bsm_plan_results(plan)[0])
+        for g in gbt + [gp]:
+            assert g.bs == cbs
+            assert_same_structure(g, w)
+            assert np.array_equal(g.vals, w.vals)
+
+
+def test_different_block_sizes_need_the_override():
+    A = to_bsm(synth.random_blocks(256, 32, 0.3, 710))
+    B = to_bsm(synth.random_blocks(256, 16, 0.3, 711))
+    with pytest.raises(bsm.BsmError) as e:
+        bsm.bsm_multiply(A, B)
+    assert e.value.name == "BSM_ERR_BLOCKSIZE"
+    with pytest.raises(bsm.BsmError) as e:
+        bsm.bsm_multiply(A, A, bs=24)
+    assert e.value.name == "BSM_ERR_BLOCKSIZE"
+    with pytest.raises(bsm.BsmError) as e:
+        bsm.bsm_multiply_batched([A], [B])
+    assert e.value.name == "BSM_ERR_BLOCKSIZE"
