@@ -485,7 +485,9 @@ def run_decay(args):
     the block-pattern product (the definition of S_C); blocks whose entries all
     vanish (element-level sparsity inside blocks) are removed by the product,
     and on 1000 uniformly sampled C blocks the values and the presence of each
-    block are compared with the oracle's definition."""
+    block are compared with the oracle's definition.  With --node-side only the
+    C blocks of one diagonal quadtree node are computed (from the operand
+    blocks in its rows and columns) and checked on a 32 x 32 grid of them."""
     import ctypes
 
     import torch
@@ -500,7 +502,20 @@ def run_decay(args):
     stream = torch.cuda.current_stream()
     npts, bs = args.points, args.bs
     t0 = time.time()
-    n, r, c, v = sd.decay(npts, bs, synth.BASE_SEED + 2, dev)
+    # --node-side S: only the C blocks of one diagonal quadtree node
+    # [lo, lo + S)^2 (S a power of two, lo a multiple of S) are computed, from
+    # the operand blocks with a row or a column in [lo, lo + S): the products
+    # whose full C would not fit on one GPU, one node at a time
+    node = None
+    if args.node_side:
+        S = args.node_side
+        nbk_full = -(-(npts * 5) // bs)
+        lo_b = args.node_at if args.node_at is not None else (nbk_full // 2) // S * S
+        if S & (S - 1) or lo_b % S or lo_b >= nbk_full:
+            raise SystemExit("--node-side must be a power of two and --node-at a multiple of it")
+        node = (lo_b, min(lo_b + S, nbk_full))
+        args.sym = False
+    n, r, c, v = sd.decay(npts, bs, synth.BASE_SEED + 2, dev, cross=node)
     nbk = -(-n // bs)
     A = bsm.bsm_build(n, n, bs, r, c, v)
     U = None
@@ -521,14 +536,28 @@ def run_decay(args):
     Pm = torch.zeros((nbk, nbk), dtype=torch.float32, device=dev)
     Pm[ar[:nblk].long(), ac[:nblk].long()] = 1.0
     del ar, ac
-    pat = (Pm @ Pm) > 0.5
-    del Pm
-    ci, cj = torch.nonzero(pat, as_tuple=True)
-    del pat
+    if node is None:
+        pat = (Pm @ Pm) > 0.5
+        ci, cj = torch.nonzero(pat, as_tuple=True)
+    else:  # the node's rows and columns need all of K: present in the cross
+        a0, a1 = node
+        pat = (Pm[a0:a1] @ Pm[:, a0:a1]) > 0.5
+        ci, cj = torch.nonzero(pat, as_tuple=True)
+        ci, cj = ci + a0, cj + a0
+    del Pm, pat
     nc_def = int(ci.numel())
     nc_def_upper = int((ci <= cj).sum())
     g = torch.Generator(device="cpu").manual_seed(synth.BASE_SEED)
-    pick = torch.randperm(nc_def, generator=g)[:1000]
+    if node is None:
+        pick = torch.randperm(nc_def, generator=g)[:1000]
+    else:
+        # a grid of 32 block rows x 32 block columns of the node (about 1000
+        # blocks) keeps the oracle's restricted operands small
+        side = node[1] - node[0]
+        gr = node[0] + torch.randperm(side, generator=g)[:32]
+        gc = node[0] + torch.randperm(side, generator=g)[:32]
+        cic, cjc = ci.cpu(), cj.cpu()
+        pick = torch.nonzero(torch.isin(cic, gr) & torch.isin(cjc, gc)).flatten()
     si, sj = ci.cpu()[pick].numpy(), cj.cpu()[pick].numpy()
     # oracle operands restricted to the sampled rows (left) and columns (right)
     rows_keep = torch.isin(r, torch.from_numpy(si).to(dev).to(torch.int32))
@@ -548,10 +577,18 @@ def run_decay(args):
     oracle_s = time.time() - t1
     del tl, tr, left, right
     log(f"decay: n={n} blocks={nblk} C(def)={nc_def}; generation {gen_s:.1f} s, "
-        f"oracle on 1000 blocks {oracle_s:.1f} s")
+        f"oracle on {len(si)} blocks {oracle_s:.1f} s")
     bsm.bsm_set_timing(True)
     out = {"workload": f"decay A*A, {npts} points (N={n}), bs {bs}", "a_blocks": nblk,
            "c_blocks_definition": nc_def, "sampled_blocks_exactly_zero": int((~ref_nonzero).sum())}
+    key_range = None
+    if node is not None:
+        from paper_1501_07800_gb300 import shard as sh
+        klo = int(sh.morton(node[0], node[0]))
+        key_range = (klo, klo + args.node_side * args.node_side)
+        out["workload"] += (f": the C blocks of the diagonal quadtree node [{node[0]}, {node[1]})^2 "
+                            f"of {nbk}^2 block positions, operands restricted to its rows and "
+                            f"columns (bsm_multiply_range)")
     peaks, which = measured_peaks()
     fp64_peak = peaks["bf16_tflops"] * FP64_NOMINAL_RATIO
     slices = [int(x) for x in args.slices.split(",") if x]
@@ -578,7 +615,8 @@ def run_decay(args):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             C = (bsm.bsm_sym_square(U, prec=prec, slices=nsl) if sym
-                 else bsm.bsm_multiply(A, A, prec=prec, slices=nsl))
+                 else bsm.bsm_multiply_range(A, A, *key_range, prec=prec, slices=nsl)
+                 if key_range else bsm.bsm_multiply(A, A, prec=prec, slices=nsl))
             e1.record(stream)
             torch.cuda.synchronize()
             if prec == bsm.BSM_FP64 or k > 0:  # split: first run is a warm-up
@@ -622,7 +660,7 @@ def run_decay(args):
                "symbolic_structure_matches_definition":
                    None if recut else ncs == (nc_def_upper if sym else nc_def),
                "sampled_presence_matches_oracle": bool(np.array_equal(present, ref_nonzero)),
-               "rel_err_vs_oracle_1000_blocks": err}
+               "rel_err_vs_oracle_sampled_blocks": err, "sampled_blocks": int(len(si))}
         if prec == bsm.BSM_FP64:
             res["numeric_tflops"] = flops / t_num / 1e12
             res["frac_of_fp64_peak"] = flops / t_num / 1e12 / fp64_peak
@@ -732,6 +770,11 @@ def main():
     ap.add_argument("--slices", default="7", help="decay workload: split slice counts, e.g. 3,5,7")
     ap.add_argument("--fp8-slices", default="", help="decay workload: FP8 split slice counts")
     ap.add_argument("--no-fp64", action="store_true", help="decay workload: skip the FP64 legs")
+    ap.add_argument("--node-side", type=int, default=0,
+                    help="decay workload: compute only the C blocks of one diagonal quadtree "
+                         "node of this side (blocks, a power of two)")
+    ap.add_argument("--node-at", type=int, default=None,
+                    help="decay workload: first block row/column of that node")
     ap.add_argument("--sym", action="store_true",
                     help="decay workload: also the symmetric square from the upper triangle")
     ap.add_argument("--shard", action="store_true",

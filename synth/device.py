@@ -79,12 +79,15 @@ def to_host(n: int, bs: int, brow, bcol, vals) -> BlockCOO:
 
 
 def decay(npoints: int, bs: int, seed: int, device, nfun: int = 5, alpha: float = 0.5,
-          cutoff: float = 1e-6, density: float = 0.1, chunk_blocks: int = 1 << 17):
+          cutoff: float = 1e-6, density: float = 0.1, chunk_blocks: int | None = None,
+          cross: tuple[int, int] | None = None):
     """Device tensors (n, brow, bcol, vals) of the decay-type matrix of
     synth.decay: points from synth.decay_points (host, recursive bisection
     order), blocks whose bounding boxes come within the cutoff radius, entries
     s_ij exp(-alpha r_ij) below `cutoff` set to zero.  Entries may differ from
-    the numpy generator in the last bit (exp on the device)."""
+    the numpy generator in the last bit (exp on the device).  cross=(lo, hi):
+    only the blocks whose block row or block column lies in [lo, hi) (the
+    operands of the C blocks [lo, hi)^2 of A*A)."""
     import math
 
     from . import decay_points
@@ -99,11 +102,18 @@ def decay(npoints: int, bs: int, seed: int, device, nfun: int = 5, alpha: float 
     lo, hi = bp.min(1).values, bp.max(1).values
     rows, cols = [], []
     step = max(1, (1 << 24) // nbk)
+    if chunk_blocks is None:
+        chunk_blocks = max(1, (1 << 27) // (bs * bs))  # 2^27 entries per chunk
+    if cross is not None:
+        incross = torch.zeros(nbk, dtype=torch.bool, device=device)
+        incross[cross[0]:cross[1]] = True
     for r0 in range(0, nbk, step):
         r1 = min(nbk, r0 + step)
         gap = torch.clamp(torch.maximum(lo[r0:r1, None, :] - hi[None, :, :],
                                         lo[None, :, :] - hi[r0:r1, None, :]), min=0.0)
         near = (gap * gap).sum(-1).sqrt() <= rcut
+        if cross is not None:
+            near &= incross[r0:r1, None] | incross[None, :]
         bi, bj = torch.nonzero(near, as_tuple=True)
         rows.append(bi + r0)
         cols.append(bj)

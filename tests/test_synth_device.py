@@ -34,3 +34,13 @@ def test_decay_matches_numpy_structure_and_values():
     assert n == ref.nrows
     assert np.array_equal(r[o], E.brow) and np.array_equal(c[o], E.bcol)
     assert np.allclose(v[o], E.vals, rtol=1e-15, atol=0)
+
+
+def test_decay_cross_is_the_filtered_matrix():
+    """cross=(lo, hi) keeps exactly the blocks with a row or a column in
+    [lo, hi): the operands of the C blocks [lo, hi)^2 of A*A."""
+    n, r, c, v = sd.decay(400, 32, 5, "cpu")
+    n2, r2, c2, v2 = sd.decay(400, 32, 5, "cpu", cross=(10, 20), chunk_blocks=97)
+    keep = ((r >= 10) & (r < 20)) | ((c >= 10) & (c < 20))
+    assert n2 == n and 0 < int(keep.sum()) < len(r)
+    assert torch.equal(r[keep], r2) and torch.equal(c[keep], c2) and torch.equal(v[keep], v2)
