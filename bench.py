@@ -407,8 +407,9 @@ def run_batched(bsm, torch, args, stream, nprod=64):
     """64 independent products, N log-uniform in [2048, 32768], block density
     U[0.5%, 10%], bs 32, uniform[-1,1) entries (generated on the device).
     Times the full batched call (symbolic + one persistent numeric launch +
-    C assembly) and the autotuned plan replay (numeric phase from a CUDA graph),
-    FP64 and split BF16x7, and the split result's error against FP64."""
+    C assembly) and the autotuned plan replay (numeric phase from a CUDA graph;
+    leaf size and launch schedule chosen by measurement), FP64 and split
+    BF16x7, and the split result's error against FP64."""
     from synth import device as sd
 
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -444,9 +445,12 @@ def run_batched(bsm, torch, args, stream, nprod=64):
             del c
         full_ms = timed(full, steps)
         t1 = time.time()
-        plan = bsm.bsm_plan_create(As, Bs, prec=prec, autotune=True)
+        # the autotuner picks the leaf size (re-blocked copies of the
+        # operands, refreshed at every replay) and the launch schedule
+        plan = bsm.bsm_plan_create(As, Bs, prec=prec, autotune=True, autotune_bs=True)
         create_s = time.time() - t1
         order, chunk, ctas, nitems = bsm.bsm_plan_info(plan)
+        leaf = bsm.bsm_plan_block_size(plan)
         bsm.bsm_plan_execute(plan)
         replay_ms = timed(lambda: bsm.bsm_plan_execute(plan), steps)
         del plan  # one plan's buffers (all C blocks) at a time
@@ -454,8 +458,9 @@ def run_batched(bsm, torch, args, stream, nprod=64):
                      "full_call_gflops": flops / (statistics.mean(full_ms) / 1e3) / 1e9,
                      "graph_replay_ms": statistics.mean(replay_ms),
                      "graph_replay_gflops": flops / (statistics.mean(replay_ms) / 1e3) / 1e9,
-                     "plan_create_s": create_s, "triples": triples, "c_blocks": nitems,
-                     "autotuned": {"order": "longest-first" if order == 0 else
+                     "plan_create_s": create_s, "triples": triples, "work_items": nitems,
+                     "autotuned": {"leaf_size": leaf,
+                                   "order": "longest-first" if order == 0 else
                                    "product-major Morton", "chunk": chunk, "ctas_per_sm": ctas}}
     # split vs FP64, product by product on every 8th product (bounded memory)
     num = den = 0.0
