@@ -264,12 +264,14 @@ bsm_status create_at_bs(int n, const bsm_matrix *A, const bsm_matrix *B, const b
   return BSM_OK;
 }
 
-// Leaf-size autotuning: a wrapper plan per candidate block size, each timed
-// over full executions (operand refresh included); the fastest is kept.
+// Leaf-size autotuning: a wrapper plan per candidate block size with the
+// default launch schedule, each timed over a full execution (operand refresh
+// included) after a warm-up; the fastest size is then planned again with the
+// launch-schedule autotuner, which thus runs at one size only.
 bsm_status create_tuned_bs(int n, const bsm_matrix *A, const bsm_matrix *B, bsm_mult_opts o,
                            cudaStream_t cs, bsm_plan *out) {
   *out = nullptr;
-  o.flags = BSM_FLAG_AUTOTUNE;  // the inner plans tune their launch parameters
+  o.flags = 0;
   std::vector<int> cands = o.prec == BSM_FP64 ? std::vector<int>{16, 32, 64}
                                               : std::vector<int>{16, 32};
   bsm_plan best = nullptr;
@@ -310,8 +312,10 @@ bsm_status create_tuned_bs(int n, const bsm_matrix *A, const bsm_matrix *B, bsm_
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (!best) return first_err != BSM_OK ? first_err : BSM_ERR_CUDA;
-  *out = best;
-  return BSM_OK;
+  const int cb = best->bs;
+  destroy_plan(best);
+  o.flags = BSM_FLAG_AUTOTUNE;  // the chosen size's plan tunes its launch schedule
+  return create_at_bs(n, A, B, o, cb, A[0]->bs, cs, out);
 }
 
 }  // namespace
