@@ -82,10 +82,12 @@ typedef struct {
 /* bsm_plan_create: measure candidate launch configurations and keep the
  * fastest (cached per product class for the process). */
 #define BSM_FLAG_AUTOTUNE 1
-/* bsm_plan_create: also choose the leaf block size (16, 32, 64; split modes
- * 16, 32) by timing the product on re-blocked copies of the operands.  The
- * plan then copies the operands' current values into its re-blocked copies
- * at every execution and returns C in the operands' block size. */
+/* bsm_plan_create: also choose the leaf block size by timing the product on
+ * re-blocked copies of the operands (FP64: the operands' size and the finer
+ * ones -- coarser blocks only add zero-fill flops at the FP64 rate; split
+ * modes: 16 and 32).  The plan then copies the operands' current values into
+ * its re-blocked copies at every execution and returns C in the operands'
+ * block size. */
 #define BSM_FLAG_AUTOTUNE_BS 8
 /* bsm_multiply: use A^T (resp. B^T) in place of A (resp. B), the transposed
  * multiplication task types C = A^T B, A B^T, A^T B^T of Sec. 3.2. */

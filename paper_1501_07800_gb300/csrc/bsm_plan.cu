@@ -265,15 +265,20 @@ bsm_status create_at_bs(int n, const bsm_matrix *A, const bsm_matrix *B, const b
 }
 
 // Leaf-size autotuning: a wrapper plan per candidate block size with the
-// default launch schedule, each timed over a full execution (operand refresh
-// included) after a warm-up; the fastest size is then planned again with the
-// launch-schedule autotuner, which thus runs at one size only.
+// default launch schedule, each timed over one full execution (operand
+// refresh included; the plan's creation ran it once already); the fastest
+// size is then planned again with the launch-schedule autotuner, which thus
+// runs at one size only.  FP64 products run at the FP64 pipe's rate at every
+// leaf size, so a coarser size only adds the flops of the zero fill of its
+// larger blocks: FP64 candidates are the operands' size and the finer ones.
+// The split kernels take 16 and 32 (wider operands are re-cut to 32).
 bsm_status create_tuned_bs(int n, const bsm_matrix *A, const bsm_matrix *B, bsm_mult_opts o,
                            cudaStream_t cs, bsm_plan *out) {
   *out = nullptr;
   o.flags = 0;
-  std::vector<int> cands = o.prec == BSM_FP64 ? std::vector<int>{16, 32, 64}
-                                              : std::vector<int>{16, 32};
+  std::vector<int> cands;
+  for (int cb : {16, 32, 64})
+    if (o.prec == BSM_FP64 ? cb <= A[0]->bs : cb <= 32) cands.push_back(cb);
   bsm_plan best = nullptr;
   float best_ms = 1e30f;
   bsm_status first_err = BSM_OK;
@@ -287,13 +292,13 @@ bsm_status create_tuned_bs(int n, const bsm_matrix *A, const bsm_matrix *B, bsm_
     bsm_plan W = nullptr;
     bsm_status st = create_at_bs(n, A, B, o, cb, A[0]->bs, cs, &W);
     float ms = 1e30f;
-    for (int r = 0; r < 2 && st == BSM_OK; r++) {  // the first run warms up
+    if (st == BSM_OK && cands.size() > 1) {
       cudaEventRecord(a, cs);
       st = execute_wrapped(W, cs);
       cudaEventRecord(b, cs);
       if (st == BSM_OK) st = cuda_status(cudaEventSynchronize(b));
       float t = 0;
-      if (st == BSM_OK && r > 0 && cudaEventElapsedTime(&t, a, b) == cudaSuccess) ms = t;
+      if (st == BSM_OK && cudaEventElapsedTime(&t, a, b) == cudaSuccess) ms = t;
     }
     if (st != BSM_OK) {
       if (first_err == BSM_OK) first_err = st;
