@@ -95,8 +95,7 @@ struct Cfg {
   static constexpr int ASLOTS = (DPG - 1) + G * DPG;         // zero pad + slices + pad
   static constexpr int BSLOTS = NP * S;                      // B slices (a pair interleaved)
   static constexpr int STAGE = (ASLOTS + BSLOTS) * SLICE;
-  // epilogue teams: short items at bs 16 (256 outputs) need more in flight
-  static constexpr int NTEAM = NP == 2 ? 1 : (BS == 16 ? 4 : 2);
+  static constexpr int NTEAM = NP == 2 ? 1 : 2;              // epilogue teams
   static constexpr int CROW = NP * BS + 4;                   // padded int32 row (combine)
   static constexpr int COMB = S * BS * CROW * 4;             // combine buffer bytes (per team)
   // ring depth: up to 4 (bs 32) / 8 (bs 16) stages within 227 KiB of shared
@@ -485,8 +484,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
   constexpr int DPG = C::DPG;
   constexpr int G = C::G;
   constexpr int NTEAM = C::NTEAM;
-  constexpr int kTeamWarps = kEpiWarps / NTEAM;  // 4, 8 or 16 warps per team
-  static_assert(NTEAM <= 4 && kTeamWarps % 4 == 0, "teams cover whole lane quadrants");
+  constexpr int kTeamWarps = kEpiWarps / NTEAM;  // 8 (two teams) or 16 (one)
   constexpr int kTeam = kTeamWarps * 32;         // threads per epilogue team
   constexpr int NB = NP * BS;                    // MMA N: output columns per item
   constexpr int BETA = Fmt<F>::BETA, TS = Fmt<F>::TSPLIT;
@@ -506,11 +504,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
   constexpr uint32_t BYTES_B = (uint32_t)NP * S * C::SLICE;   // B block (pair) slices
   extern __shared__ __align__(1024) uint8_t smem[];
   // tfull / tempty: per (team, buffer), index 2 * team + buffer
-  __shared__ __align__(8) uint64_t full[C::NST], empty[C::NST], tfull[8], tempty[8], done;
+  __shared__ __align__(8) uint64_t full[C::NST], empty[C::NST], tfull[4], tempty[4], done;
   __shared__ __align__(8) uint64_t meta_full[kMeta], meta_empty[kMeta];
   __shared__ Meta meta[kMeta];
   __shared__ uint32_t tmem_base_sh;
-  __shared__ int warp_any[4][2][16];  // [team][block of the item][warp]
+  __shared__ int warp_any[2][2][16];  // [team][block of the item][warp]
   __shared__ volatile int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -527,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
-    for (int i = 0; i < 2 * NTEAM; i++) {
+    for (int i = 0; i < 4; i++) {
       mbar_init(&tfull[i], 1);
       mbar_init(&tempty[i], kTeam);  // buffers 2t, 2t+1 belong to team t
     }
@@ -683,7 +681,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
     // ---------------------------------------------------------- MMA issuer
     if (lane == 0) {
       uint32_t it = 0, q = 0;
-      uint32_t fcb[NTEAM] = {};  // flushes issued per team
+      uint32_t fcb0 = 0, fcb1 = 0;  // flushes issued for team 0 / 1
       const uint32_t sbase = smem_u32(stages);
       for (;; q++) {
         int m = q % kMeta;
@@ -699,7 +697,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         const int nfl = fp.nfl;
         const int b = q % NTEAM;  // items alternate between the teams
         for (int f = 0; f < nfl && !abort_flag; f++) {
-          const uint32_t fb = fcb[b]++;
+          const uint32_t fb = b ? fcb1 : fcb0;
+          if (b) fcb1++; else fcb0++;
           const uint32_t u = fb % NBUF, use = fb / NBUF;  // buffer and its use count
           if (!mbar_wait(&tempty[2 * b + u], (use & 1u) ^ 1u)) {
             set_err(P.err, DERR_TIMEOUT);
@@ -762,9 +761,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
     }
   } else {
     // ----------------------------------------------------------- epilogue
-    // Single C blocks: two teams of eight warps (bs 16: four teams of four)
-    // take turns on items (team t: item index q with q % NTEAM == t), each with
-    // its own TMEM buffers; pairs: one team of sixteen warps.  Warp w of a team drains lane quadrant w % 4,
+    // Single C blocks: two teams of eight warps take alternate items (team t:
+    // local item index q with q % 2 == t) and their own TMEM buffers; pairs:
+    // one team of sixteen warps.  Warp w of a team drains lane quadrant w % 4,
     // a slice of HC columns, and accumulates the exact diagonal sums straight
     // into the team's shared-memory buffer [d][r][c]; the team then combines
     // the diagonals of each output element.  With two teams one team's
@@ -833,7 +832,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
       const FlushPlan fplan = flush_plan(nk, P.flushk, P.flushk_wide);
       const int nfl = fplan.nfl, kf = fplan.kf;
       const bool wide = fplan.wide;
-      int64_t *const fold = P.fold + ((int64_t)blockIdx.x * NTEAM + team) * (NB * BS * 2);
+      int64_t *const fold = P.fold + ((int64_t)blockIdx.x * 2 + team) * (NB * BS * 2);
       bool ok = true;
       // Every warp runs all nfl iterations (doing no work once `ok` is false)
       // so that the team meets the same fold barriers whatever happened.
@@ -1123,9 +1122,8 @@ size_t split_fold_bytes(int bs) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // per CTA: (hi, lo) for every output of each team's item -- the most of
-  // 2 teams x bs^2 (bs 32), 4 teams x bs^2 (bs 16) and 1 team x 2 bs^2 (pairs)
-  return (size_t)(sms > 0 ? sms : 1) * 4 * bs * bs * 2 * sizeof(int64_t);
+  // per CTA and team: (hi, lo) for every output of an item (a pair: 2 bs^2)
+  return (size_t)(sms > 0 ? sms : 1) * 2 * bs * (2 * bs) * 2 * sizeof(int64_t);
 }
 
 bsm_status split_supported(int bs, int spec) {
