@@ -76,7 +76,8 @@ typedef struct {
                  bsm_plan_create): 0 = the operands' own, which must then be
                  equal; 16, 32 or 64 = operands of another size are re-cut to
                  it exactly (bsm_reblock; plans refresh their re-cut copies
-                 at every execution) and C has this size */
+                 at every execution) and C has this size; the other calls
+                 taking options require 0 (INVALID_ARG otherwise) */
 } bsm_mult_opts;
 
 /* bsm_plan_create: measure candidate launch configurations and keep the

@@ -456,6 +456,7 @@ extern "C" bsm_status bsm_multiply_range(bsm_matrix A, bsm_matrix B, uint64_t ke
   if (key_hi <= key_lo) return BSM_ERR_INVALID_ARG;
   int prec, slices;
   BSM_TRY(check_opts(opts, &prec, &slices, 0));
+  if (opts && opts->bs) return BSM_ERR_INVALID_ARG;  // keys are those of the operands' size
   if (prec != BSM_FP64) BSM_TRY(split_supported(split_width(prec, A->bs), slices));
   return multiply_one(A, B, prec, slices, (cudaStream_t)stream, C, false, key_lo, key_hi);
 }

@@ -116,6 +116,7 @@ static bsm_status sym_full(bsm_matrix U, bsm_matrix *out, cudaStream_t s) {
 
 static bsm_status sym_opts(const bsm_mult_opts *opts, int bs, int *prec, int *slices) {
   BSM_TRY(check_opts(opts, prec, slices, 0));
+  if (opts && opts->bs) return BSM_ERR_INVALID_ARG;  // computed at the operand's size
   if (*prec != BSM_FP64) BSM_TRY(split_supported(split_width(*prec, bs), *slices));
   return BSM_OK;
 }
