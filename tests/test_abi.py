@@ -97,3 +97,33 @@ def test_misaligned_device_pointers_rejected_before_any_work(lib):
     n = ctypes.c_int64(0)
     assert lib.bsm_block_products_fp64_noalloc(32, 1, 256, 256, 256, 4104, 1, 4096, 1, 4096,
                                                ctypes.byref(n), None) == -1
+
+
+def test_header_is_plain_c_and_links_from_c(lib, tmp_path):
+    """include/bsm.h compiles as strict C99 and a C program links against
+    libbsm.so and calls it (calls that need no GPU)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_bsm.c"
+    src.write_text(
+        '#include "bsm.h"\n#include <stdio.h>\n#include <string.h>\n'
+        "int main(void) {\n"
+        "  bsm_mult_opts o = {BSM_SPLIT_BF16, 7, 0, 32};\n"
+        "  bsm_matrix m = NULL;\n"
+        "  if (strcmp(bsm_status_string(BSM_OK), \"ok\") != 0) return 3;\n"
+        "  if (o.bs != 32 || bsm_destroy(m) != BSM_OK) return 2;\n"
+        "  return bsm_multiply(m, m, &m, &o, NULL) == BSM_ERR_INVALID_ARG ? 0 : 1;\n"
+        "}\n")
+    libdir = os.path.join(ROOT, "paper_1501_07800_gb300")
+    inc = os.path.join(ROOT, "include")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                        "-fsyntax-only", "-I", inc, str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    exe = tmp_path / "use_bsm"
+    r = subprocess.run([gcc, "-std=c99", "-I", inc, str(src), "-L", libdir, "-lbsm",
+                        f"-Wl,-rpath,{libdir}", "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert subprocess.run([str(exe)]).returncode == 0
