@@ -244,3 +244,15 @@ def test_different_block_sizes_need_the_override():
     with pytest.raises(bsm.BsmError) as e:
         bsm.bsm_multiply_batched([A], [B])
     assert e.value.name == "BSM_ERR_BLOCKSIZE"
+
+
+def test_calls_without_the_override_reject_it():
+    import ctypes
+    A = to_bsm(synth.random_blocks(256, 32, 0.3, 712))
+    lib = bsm.load()
+    out = ctypes.c_void_p()
+    opts = bsm.bsm_mult_opts(bsm.BSM_FP64, 0, 0, 16)
+    assert lib.bsm_multiply_range(A.handle, A.handle, 0, 1 << 20, ctypes.byref(out),
+                                  ctypes.byref(opts), None) == -1
+    assert lib.bsm_sym_square(A.handle, ctypes.byref(out), ctypes.byref(opts), None) == -1
+    assert out.value is None
