@@ -387,6 +387,35 @@ def test_block_product_by_definition():
         assert found and relerr(blk, E.vals[t]) < 1e-14
 
 
+def test_block_product_from_restricted_operands():
+    """The sampled checks compute C_IJ from A restricted to the sampled block
+    rows and B to the sampled block columns: the same bits as from the whole
+    operands, since C_IJ only reads row I of A and column J of B."""
+    A = synth.random_blocks(700, 32, 0.15, 83)
+    B = synth.random_blocks(700, 32, 0.15, 84)
+    L = oracle.common_depth(A, B)
+    ta, tb = oracle.tree(A, L), oracle.tree(B, L)
+    rows, cols = np.array([1, 5, 9, 12, 16, 20]), np.array([0, 3, 5, 11, 17, 21])
+    ka, kb = np.isin(A.brow, rows), np.isin(B.bcol, cols)
+    left = synth.BlockCOO(A.nrows, A.ncols, 32, A.brow[ka], A.bcol[ka], A.vals[ka])
+    right = synth.BlockCOO(B.nrows, B.ncols, 32, B.brow[kb], B.bcol[kb], B.vals[kb])
+    tl, tr = oracle.tree(left, L), oracle.tree(right, L)
+    E = dense_product_blocks(A, B)
+    n = 0
+    for i in rows:
+        for j in cols:
+            f1, b1 = oracle.block_product(ta, tb, i, j)
+            f2, b2 = oracle.block_product(tl, tr, i, j)
+            assert f1 == f2 and np.array_equal(b1, b2)
+            hit = (E.brow == i) & (E.bcol == j)
+            if hit.any():
+                n += 1
+                assert relerr(b1, E.vals[hit][0]) < 1e-14
+            else:
+                assert not np.any(b1)
+    assert n > 5
+
+
 # ------------------------------------------------- task counts (Sec. 5.1)
 def brute_force_level_counts(A, B, L):
     """Count (A node (I,K), B node (K,J)) pairs at every level of a block quadtree."""
