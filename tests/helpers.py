@@ -28,3 +28,18 @@ def assert_same_structure(C: synth.BlockCOO, E: synth.BlockCOO):
     assert (C.nrows, C.ncols, C.bs) == (E.nrows, E.ncols, E.bs)
     assert C.nblk == E.nblk, (C.nblk, E.nblk)
     assert np.array_equal(C.brow, E.brow) and np.array_equal(C.bcol, E.bcol)
+
+
+def pattern_product(ar, ac, br, bc, mb, kb, nb):
+    """(I, J) of C's structure by definition, row-major: some K has A_IK and
+    B_KJ stored (SciPy sparse product of the block patterns, on the host)."""
+    import scipy.sparse as sp
+
+    def host(x):
+        return x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+    PA = sp.csr_matrix((np.ones(len(ar), np.int32), (host(ar), host(ac))), shape=(mb, kb))
+    PB = sp.csr_matrix((np.ones(len(br), np.int32), (host(br), host(bc))), shape=(kb, nb))
+    C = (PA @ PB).tocsr()
+    C.sort_indices()
+    rows = np.repeat(np.arange(mb, dtype=np.int64), np.diff(C.indptr))
+    return rows, C.indices.astype(np.int64)

@@ -23,12 +23,11 @@ log-uniform in [2048, 32768] and block density U[0.5%, 10%].
 """
 import numpy as np
 import pytest
-import scipy.sparse as sp
 
 import oracle
 import paper_1501_07800_gb300 as bsm
 import synth
-from helpers import relerr
+from helpers import pattern_product, relerr
 from paper_1501_07800_gb300 import shard
 
 pytestmark = pytest.mark.gpu
@@ -51,17 +50,6 @@ def _cuda():
 
 def host(x) -> np.ndarray:
     return x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
-
-
-def pattern_product(ar, ac, br, bc, mb, kb, nb):
-    """(I, J) of the definition's structure, row-major: some K has A_IK and
-    B_KJ stored."""
-    PA = sp.csr_matrix((np.ones(len(ar), np.int32), (host(ar), host(ac))), shape=(mb, kb))
-    PB = sp.csr_matrix((np.ones(len(br), np.int32), (host(br), host(bc))), shape=(kb, nb))
-    C = (PA @ PB).tocsr()
-    C.sort_indices()
-    rows = np.repeat(np.arange(mb, dtype=np.int64), np.diff(C.indptr))
-    return rows, C.indices.astype(np.int64)
 
 
 def stored_pattern(M):

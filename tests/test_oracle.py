@@ -416,6 +416,19 @@ def test_block_product_from_restricted_operands():
     assert n > 5
 
 
+def test_pattern_product_helper_is_the_oracle_structure():
+    """The block-pattern product the full-size GPU tests use as C's
+    definition equals the oracle's structure (no exact cancellation with
+    N(0,1) entries), rectangular and ragged included."""
+    from helpers import pattern_product
+    for (m, k, n, bs, p, seed) in [(900, 700, 500, 32, 0.05, 91), (333, 333, 333, 16, 0.2, 92)]:
+        A = synth.random_blocks(m, bs, p, seed, ncols=k)
+        B = synth.random_blocks(k, bs, p, seed + 1, ncols=n)
+        E = oracle.multiply(A, B).C
+        r, c = pattern_product(A.brow, A.bcol, B.brow, B.bcol, A.mb, A.nb, B.nb)
+        assert np.array_equal(r, E.brow) and np.array_equal(c, E.bcol)
+
+
 # ------------------------------------------------- task counts (Sec. 5.1)
 def brute_force_level_counts(A, B, L):
     """Count (A node (I,K), B node (K,J)) pairs at every level of a block quadtree."""
