@@ -7,6 +7,8 @@ block-sparse leaf multiply of Sec. 4.1 / Fig. 3 of Rubensson & Rudberg -- and
 shares no code with the CUDA library.
 
 Functions here are argument marshalling only; all arithmetic is in the C file.
+``oracle/split.py`` (exact Python integers) defines the split-precision modes'
+result, which the paper does not cover.
 """
 from __future__ import annotations
 
