@@ -96,3 +96,31 @@ def test_power_of_two_row_scaling_is_exact():
     want = C.to_dense()
     want[16:32] *= 2.0 ** 40
     assert np.array_equal(Cs.to_dense(), want)
+
+
+def test_one_slice_is_the_rounded_product_of_the_rounded_operands():
+    """With one slice nothing is dropped: C_rc is the correctly rounded exact
+    sum of products of the operands rounded to B bits against their row /
+    column scales, a_rk = round(A_rk 2^(B-E_r)) 2^(E_r-B) -- an independent
+    check of the scales, the fixed point and the final exponent."""
+    from fractions import Fraction
+    Bb = 7
+    A = synth.random_blocks(2 * 16 + 3, 16, 0.8, 71)
+    B = synth.random_blocks(2 * 16 + 3, 16, 0.8, 72)
+    C = osplit.multiply(A, B, "bf16", 1)
+    Ad, Bd = A.to_dense(), B.to_dense()
+    n = Ad.shape[0]
+    er = [max((osplit.scale_exponent(v) for v in Ad[r] if v != 0), default=0) for r in range(n)]
+    fc = [max((osplit.scale_exponent(v) for v in Bd[:, c] if v != 0), default=0) for c in range(n)]
+
+    def rnd(x, E):  # x rounded to B bits below 2^E, ties away from zero
+        v = Fraction(float(x)) * Fraction(2) ** (Bb - E)
+        q = int(abs(v) + Fraction(1, 2))
+        return Fraction(-q if v < 0 else q) * Fraction(2) ** (E - Bb)
+    Ar = [[rnd(Ad[r, k], er[r]) for k in range(n)] for r in range(n)]
+    Br = [[rnd(Bd[k, c], fc[c]) for c in range(n)] for k in range(n)]
+    Cd = C.to_dense()
+    rng = np.random.default_rng(73)
+    for r, c in zip(rng.integers(0, n, 60), rng.integers(0, n, 60)):
+        exact = sum((Ar[r][k] * Br[k][c] for k in range(n)), Fraction(0))
+        assert Cd[r, c] == float(exact)
