@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <functional>
 #include <vector>
 
@@ -11,6 +12,20 @@
 
 #include "../../include/bsm.h"
 #include "bsm_batch.cuh"
+
+// Runs `set` (a kernel attribute setting, which is per device) the first
+// time it is needed on the current device; thread-safe (setting an attribute
+// twice is harmless).  `done` holds one bit per device ordinal below 64.
+template <typename F>
+bsm_status once_per_device(std::atomic<uint64_t> &done, F set) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return set();
+  const uint64_t bit = 1ull << dev;
+  if (done.load(std::memory_order_acquire) & bit) return BSM_OK;
+  const bsm_status st = set();
+  if (st == BSM_OK) done.fetch_or(bit, std::memory_order_release);
+  return st;
+}
 
 // NVTX range for the duration of a scope (visible to profilers; a no-op
 // without one attached).

@@ -185,12 +185,11 @@ template <int BS>
 bsm_status launch(const SymbolicResult &sym, bsm_matrix A, bsm_matrix B, double *Cv, int32_t *nz,
                   unsigned *err, cudaStream_t s) {
   size_t smem = (size_t)kStages * 2 * BS * BS * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    BSM_CUDA(cudaFuncSetAttribute(k_numeric_fp64<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  BSM_TRY(once_per_device(attr, [&] {
+    return cuda_status(cudaFuncSetAttribute(
+        k_numeric_fp64<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }));
   // one CTA per C block (nc < 2^31 is checked by the caller)
   count_launch();
   k_numeric_fp64<BS><<<(unsigned)sym.nc, 128, smem, s>>>(sym.seg, sym.ta, sym.tb, sym.nc, A->nblk,
@@ -203,12 +202,11 @@ bsm_status launch_batched(const ProdDesc *prods, const uint64_t *items, int64_t 
                           unsigned long long *counter, unsigned *err, int ctas_per_sm,
                           cudaStream_t s) {
   size_t smem = (size_t)kStages * 2 * BS * BS * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    BSM_CUDA(cudaFuncSetAttribute(k_numeric_fp64_batched<BS>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  BSM_TRY(once_per_device(attr, [&] {
+    return cuda_status(cudaFuncSetAttribute(
+        k_numeric_fp64_batched<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }));
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -983,12 +983,11 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t);
 template <int BS, int S, int F, int NP>
 bsm_status launch_split(const SplitArgs &a, cudaStream_t s) {
   using C = Cfg<BS, S, F, NP>;
-  static bool attr = false;
-  if (!attr) {
-    BSM_CUDA(cudaFuncSetAttribute(k_numeric_split<BS, S, F, NP>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  BSM_TRY(once_per_device(attr, [&] {
+    return cuda_status(cudaFuncSetAttribute(
+        k_numeric_split<BS, S, F, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+  }));
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
