@@ -188,7 +188,7 @@ bsm_status bsm_transpose(bsm_matrix A, bsm_matrix *out, void *stream);
 bsm_status bsm_add(bsm_matrix A, bsm_matrix B, bsm_matrix *out, void *stream);
 
 /*
- * Symmetric matrices (Sec. 3.2, additional task types for the symmetric
+ * Symmetric matrices (Sec. 3.3, additional task types for the symmetric
  * matrix square) are stored as their upper triangle of blocks: only blocks
  * with I <= J, diagonal blocks in full.  Symmetric results are returned the
  * same way.  Operands in this storage must be square and hold no block below

@@ -470,7 +470,7 @@ orc_matrix *orc_add(const orc_matrix *A, const orc_matrix *B, int *status) {
 
 /* ------------------------------------------------------ symmetric storage */
 /* A symmetric matrix is given by its upper triangle of blocks (I <= J), the
- * diagonal blocks in full (Sec. 3.2, symmetric task types).  The symmetric
+ * diagonal blocks in full (Sec. 3.3, symmetric task types).  The symmetric
  * results are defined plainly: the full matrix S (each strictly-upper block
  * also placed, transposed, at its mirror position), the ordinary product by
  * Algorithm 1, and the blocks with I <= J of that product. */

@@ -1,4 +1,4 @@
-// Symmetric task types (Sec. 3.2, additional task types for the symmetric
+// Symmetric task types (Sec. 3.3, additional task types for the symmetric
 // matrix square): C = A^2 with A symmetric, C = A B with A or B symmetric,
 // and the symmetric rank-k products C = A A^T and C = A^T A.
 //
