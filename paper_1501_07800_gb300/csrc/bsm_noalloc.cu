@@ -9,8 +9,9 @@
 // caller passes every input and output buffer; the only other memory used is
 // the file-scope scratch array below.
 //
-// The scratch array is a static device array: every GPU that loads this
-// library holds it (about 4 MiB) until the process exits.  All calls share it
+// The scratch array is a static device array: every GPU on which a call was
+// made holds it (about 4 MiB) from that first call -- which loads the module
+// and may therefore allocate -- until the process exits.  All calls share it
 // and it keeps the last call's contents, so calls whose work overlaps on the
 // GPU (different streams, or different host threads on one device) race on it
 // and must be serialised by the caller.  The error word is cleared on the
@@ -18,120 +19,39 @@
 // blocks of each call.
 #include <mutex>
 
+#include "bsm_fp64_body.cuh"
 #include "bsm_ptx.cuh"
 
 namespace {
 
-constexpr int kStages = 2;
 constexpr int kErrWords = 64;  // word 0: device error code; the rest pads to 256 B
 
 // [flags of up to BSM_NOALLOC_MAX_CBLOCKS C blocks | error word + padding]
 static __device__ __align__(256) int32_t g_scratch[BSM_NOALLOC_MAX_CBLOCKS + kErrWords];
 
-__device__ __forceinline__ void dmma_8x8x4(double (&c)[2], double a, double b) {
-  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
-               : "+d"(c[0]), "+d"(c[1])
-               : "d"(a), "d"(b));
-}
-
-// Same work as the library's FP64 numeric kernel: one CTA sums the products of
-// one C block on DMMA from bulk-copied blocks.  Its nonzero flag goes to the
-// scratch array instead of a caller or pool buffer.
+// The library's FP64 per-C-block body (one CTA per C block, bulk-copy ring,
+// DMMA, bounds check and bounded waits); the nonzero flag goes to the
+// scratch array, and a C block whose CTA gave up (bad index or timed-out
+// wait) has its flag cleared, so that only the error word reports it.
 template <int BS>
 __global__ void __launch_bounds__(128) k_products_fp64_noalloc(
     const int32_t *__restrict__ seg, const int32_t *__restrict__ ta, const int32_t *__restrict__ tb,
     int64_t nc, int64_t na, int64_t nb, const double *__restrict__ Av,
     const double *__restrict__ Bv, double *__restrict__ Cv, int32_t *__restrict__ flags,
     unsigned *__restrict__ err) {
-  constexpr int BB = BS * BS;
-  constexpr int WT = BS / 2;
-  constexpr int TW = WT / 8;
   extern __shared__ __align__(128) double smem[];
-  __shared__ __align__(8) uint64_t full[kStages];
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wr = warp >> 1, wc = warp & 1;
+  __shared__ __align__(8) uint64_t full[kFp64Stages];
   const int64_t c = blockIdx.x;
   if (c >= nc) return;
-  const int32_t k0 = seg[c], nk = seg[c + 1] - k0;
-  bool bad = nk < 0;
-  for (int j = tid; j < nk; j += blockDim.x)
-    bad |= ta[k0 + j] < 0 || ta[k0 + j] >= na || tb[k0 + j] < 0 || tb[k0 + j] >= nb;
-  if (__syncthreads_or(bad)) {
-    if (tid == 0) {
-      set_err(err, DERR_BOUNDS);
-      flags[c] = 0;
-    }
-    return;
-  }
-  if (tid == 0) {
-    for (int s = 0; s < kStages; s++) mbar_init(&full[s], 1);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kFp64Stages; s++) mbar_init(&full[s], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  auto issue = [&](int j) {
-    int s = j % kStages;
-    double *sa = smem + (size_t)s * 2 * BB;
-    mbar_expect_tx(&full[s], 2u * BB * 8u);
-    bulk_g2s(sa, Av + (int64_t)ta[k0 + j] * BB, BB * 8u, &full[s]);
-    bulk_g2s(sa + BB, Bv + (int64_t)tb[k0 + j] * BB, BB * 8u, &full[s]);
-  };
-  if (tid == 0)
-    for (int j = 0; j < kStages && j < nk; j++) issue(j);
-  double acc[TW][TW][2];
-#pragma unroll
-  for (int i = 0; i < TW; i++)
-#pragma unroll
-    for (int j = 0; j < TW; j++) acc[i][j][0] = acc[i][j][1] = 0.0;
-  const int ar = lane >> 2, ak = lane & 3;
-  bool ok = true;
-  int jfail = 0;
-  for (int j = 0; j < nk; j++) {
-    int s = j % kStages;
-    if (!mbar_wait(&full[s], (uint32_t)(j / kStages) & 1u)) ok = false;
-    if (__syncthreads_or(!ok)) {
-      ok = false;
-      jfail = j;
-      break;
-    }
-    const double *sa = smem + (size_t)s * 2 * BB;
-    const double *sb = sa + BB;
-#pragma unroll 2
-    for (int kk = 0; kk < BS; kk += 4) {
-      double a[TW], b[TW];
-#pragma unroll
-      for (int i = 0; i < TW; i++) a[i] = sa[(wr * WT + i * 8 + ar) * BS + kk + ak];
-#pragma unroll
-      for (int i = 0; i < TW; i++) b[i] = sb[(kk + ak) * BS + wc * WT + i * 8 + ar];
-#pragma unroll
-      for (int i = 0; i < TW; i++)
-#pragma unroll
-        for (int q = 0; q < TW; q++) dmma_8x8x4(acc[i][q], a[i], b[q]);
-    }
-    __syncthreads();
-    if (tid == 0 && j + kStages < nk) issue(j + kStages);
-  }
-  if (!ok) {
-    if (tid == 0) {
-      set_err(err, DERR_TIMEOUT);
-      flags[c] = 0;
-      for (int j = jfail; j < jfail + kStages && j < nk; j++)
-        mbar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u);
-    }
-    return;
-  }
-  bool any = false;
-  double *cb = Cv + c * BB;
-#pragma unroll
-  for (int i = 0; i < TW; i++)
-#pragma unroll
-    for (int q = 0; q < TW; q++) {
-      any |= nonzero_f64(acc[i][q][0]) | nonzero_f64(acc[i][q][1]);
-      int row = wr * WT + i * 8 + ar, col = wc * WT + q * 8 + 2 * ak;
-      *reinterpret_cast<double2 *>(cb + row * BS + col) = make_double2(acc[i][q][0], acc[i][q][1]);
-    }
-  int nzb = __syncthreads_or(any);
-  if (tid == 0) flags[c] = nzb;
+  uint32_t use0 = 0, use1 = 0;
+  if (!cblock_fp64<BS>(seg, ta, tb, c, na, nb, Av, Bv, Cv, flags, err, smem, full, use0, use1) &&
+      threadIdx.x == 0)
+    flags[c] = 0;
 }
 
 // One CTA: counts the nonzero flags; writes -1 if any CTA recorded an error.
@@ -151,13 +71,23 @@ __global__ void k_count_flags_noalloc(const int32_t *__restrict__ flags, int64_t
   }
 }
 
-// Device address of g_scratch, looked up once per device with that device
-// current (a host-side use of the symbol itself would not be a device address).
+template <int BS>
+constexpr size_t smem_bytes() {
+  return (size_t)kFp64Stages * 2 * BS * BS * sizeof(double);
+}
+
+// Per-device set-up, done once per device by the first call made with that
+// device current: the device address of g_scratch (in host code the symbol
+// itself is only a host-side stand-in, not a device address) and the
+// kernels' shared-memory attributes.  Under lazy module loading this is also
+// when the module -- the scratch array and the kernels of every block size --
+// is loaded onto the device, which may allocate device memory: the first call
+// on each device must therefore come before the caller reserves all device
+// memory and before any stream capture.
 std::mutex g_mu;
 int32_t *g_ptr[64] = {};
-bool g_attr[64][3] = {};
 
-bsm_status scratch_for_current_device(int32_t **out, int *dev_out) {
+bsm_status setup_current_device(int32_t **out) {
   int dev = 0;
   BSM_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return BSM_ERR_UNSUPPORTED;
@@ -166,30 +96,30 @@ bsm_status scratch_for_current_device(int32_t **out, int *dev_out) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess || !p) return cuda_status(e == cudaSuccess ? cudaErrorUnknown : e);
+    BSM_CUDA(cudaFuncSetAttribute(k_products_fp64_noalloc<16>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_bytes<16>()));
+    BSM_CUDA(cudaFuncSetAttribute(k_products_fp64_noalloc<32>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_bytes<32>()));
+    BSM_CUDA(cudaFuncSetAttribute(k_products_fp64_noalloc<64>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_bytes<64>()));
+    cudaFuncAttributes fa;
+    BSM_CUDA(cudaFuncGetAttributes(&fa, k_count_flags_noalloc));
     g_ptr[dev] = (int32_t *)p;
   }
   *out = g_ptr[dev];
-  *dev_out = dev;
   return BSM_OK;
 }
 
 template <int BS>
-bsm_status launch(int dev, int64_t nc, const int32_t *seg, const int32_t *ta, const int32_t *tb,
+bsm_status launch(int64_t nc, const int32_t *seg, const int32_t *ta, const int32_t *tb,
                   const double *a, int64_t na, const double *b, int64_t nb, double *c,
                   int32_t *flags, unsigned *err, cudaStream_t s) {
-  size_t smem = (size_t)kStages * 2 * BS * BS * sizeof(double);
-  {
-    std::lock_guard<std::mutex> g(g_mu);
-    int slot = BS == 16 ? 0 : BS == 32 ? 1 : 2;
-    if (!g_attr[dev][slot]) {
-      BSM_CUDA(cudaFuncSetAttribute(k_products_fp64_noalloc<BS>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      g_attr[dev][slot] = true;
-    }
-  }
   if (nc > 0)
-    k_products_fp64_noalloc<BS><<<(unsigned)nc, 128, smem, s>>>(seg, ta, tb, nc, na, nb, a, b, c,
-                                                               flags, err);
+    k_products_fp64_noalloc<BS><<<(unsigned)nc, 128, smem_bytes<BS>(), s>>>(
+        seg, ta, tb, nc, na, nb, a, b, c, flags, err);
   return cuda_status(cudaGetLastError());
 }
 
@@ -208,17 +138,16 @@ extern "C" bsm_status bsm_block_products_fp64_noalloc(int bs, int64_t nc, const 
   // blocks are staged by bulk copies and stored with 16-byte vector stores
   if (((uintptr_t)a_vals | (uintptr_t)b_vals | (uintptr_t)c_vals) & 15) return BSM_ERR_INVALID_ARG;
   int32_t *scratch = nullptr;
-  int dev = 0;
-  BSM_TRY(scratch_for_current_device(&scratch, &dev));
+  BSM_TRY(setup_current_device(&scratch));
   int32_t *flags = scratch;
   unsigned *err = (unsigned *)(scratch + BSM_NOALLOC_MAX_CBLOCKS);
   cudaStream_t s = (cudaStream_t)stream;
   BSM_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), s));  // must start at zero every call
   bsm_status st = BSM_OK;
   switch (bs) {
-    case 16: st = launch<16>(dev, nc, seg, ta, tb, a_vals, na, b_vals, nb, c_vals, flags, err, s); break;
-    case 32: st = launch<32>(dev, nc, seg, ta, tb, a_vals, na, b_vals, nb, c_vals, flags, err, s); break;
-    default: st = launch<64>(dev, nc, seg, ta, tb, a_vals, na, b_vals, nb, c_vals, flags, err, s); break;
+    case 16: st = launch<16>(nc, seg, ta, tb, a_vals, na, b_vals, nb, c_vals, flags, err, s); break;
+    case 32: st = launch<32>(nc, seg, ta, tb, a_vals, na, b_vals, nb, c_vals, flags, err, s); break;
+    default: st = launch<64>(nc, seg, ta, tb, a_vals, na, b_vals, nb, c_vals, flags, err, s); break;
   }
   if (st != BSM_OK) return st;
   k_count_flags_noalloc<<<1, 1024, 0, s>>>(flags, nc, err, nnz_out);
