@@ -332,8 +332,10 @@ bsm_status bsm_last_chunks(int *nchunks);
 /*
  * bsm_set_timing -- per-phase CUDA-event timing of bsm_multiply on the calling
  * thread: 1 = on, 0 = off (default off; the environment variable
- * BSM_TIMING=1 turns it on for every thread).  Timing adds events on the
- * product's stream and one event synchronisation per product.
+ * BSM_TIMING=1 turns it on for every thread).  Timing records CUDA events on
+ * the product's stream and never waits for them, so a timed product runs as
+ * an untimed one does; bsm_last_phase_ms waits for the last product's events
+ * when it is called.
  */
 bsm_status bsm_set_timing(int on);
 
@@ -364,7 +366,8 @@ bsm_status bsm_set_memory_limit(uint64_t bytes);
 bsm_status bsm_memory_in_use(uint64_t *bytes);
 
 /*
- * bsm_last_phase_ms -- results of the last timed bsm_multiply on this thread.
+ * bsm_last_phase_ms -- results of the last timed bsm_multiply (or
+ * bsm_multiply_batched) on this thread; waits for that product's events.
  *   ms        double[cap]: ms[0] symbolic phase, ms[1] numeric phase (the
  *             numeric kernel plus, in split modes, the slicing kernels),
  *             ms[2] zero-block removal and level build of C; may be NULL
@@ -467,9 +470,14 @@ bsm_status bsm_selftest_wait_timeout(int limit_ms, void *stream);
  *   stream        cudaStream_t or NULL; the call is asynchronous on it
  *
  * Scratch: a static device array of BSM_NOALLOC_MAX_CBLOCKS + 64 int32 (about
- * 4 MiB) compiled into the library; every GPU that loads the library holds it
- * until the process exits.  The first call on a device looks up its address
- * with that device current; make that first call before any stream capture.
+ * 4 MiB) compiled into the library.  The first call on a device (any bs; a
+ * call with nc = 0 is enough) sets the device up with that device current:
+ * it looks up the array's device address and loads the module that holds
+ * the array and these kernels, which under CUDA's lazy module loading is the
+ * moment the array and the kernels' code take device memory.  Make that
+ * first call on each device before the process reserves all device memory
+ * and before any stream capture; from then on no call allocates, and the
+ * device holds the array until the process exits.
  * All calls share the array and it keeps the last call's contents, so calls
  * whose work overlaps on the GPU race on it: serialise them (one stream, or
  * events between streams).

@@ -61,6 +61,9 @@ _PROTOS = {
     "bsm_block_products_fp64_noalloc": (_I32, [_I32, _I64, _P, _P, _P, _P, _I64, _P, _I64, _P,
                                                 _P, _P]),
     "bsm_selftest_wait_timeout": (_I32, [_I32, _P]),
+    "bsm_probe_fp64": (_I32, [_I32, _I64, _P, _P, _P]),
+    "bsm_probe_tcgen05": (_I32, [_I32, _I32, _I64, _P, _P, _P]),
+    "bsm_probe_bulk_copy": (_I32, [_I64, _I32, _I32, _P, _P, _P]),
     "bsm_update_values": (_I32, [_P, _I64, _P, _P, _P, _I32, _P]),
     "bsm_plan_create": (_I32, [_I32, _P, _P, _P, _P, _P]),
     "bsm_plan_execute": (_I32, [_P, _P]),
@@ -412,13 +415,73 @@ BSM_NOALLOC_MAX_CBLOCKS = 1 << 20
 def bsm_block_products_fp64_noalloc(bs: int, seg, ta, tb, a_vals, b_vals, c_vals, nnz_out,
                                     stream=None):
     """FP64 block products of a caller-supplied task list into caller buffers,
-    with no allocation (all arguments are torch CUDA tensors; see bsm.h)."""
+    with no allocation (all arguments are torch CUDA tensors; see bsm.h).
+
+    The tensors are checked, not converted (a conversion would allocate):
+    seg, ta, tb int32; a_vals, b_vals, c_vals float64 [n, bs, bs]; nnz_out
+    int64 with one element; all contiguous and on the current CUDA device.
+    """
+    import torch
+    dev = torch.cuda.current_device()
+    want = (("seg", seg, torch.int32), ("ta", ta, torch.int32), ("tb", tb, torch.int32),
+            ("a_vals", a_vals, torch.float64), ("b_vals", b_vals, torch.float64),
+            ("c_vals", c_vals, torch.float64), ("nnz_out", nnz_out, torch.int64))
+    for name, t, dt in want:
+        if not _is_torch_cuda(t) or t.device.index != dev:
+            raise ValueError(f"{name} must be a CUDA tensor on the current device (cuda:{dev})")
+        if t.dtype != dt:
+            raise ValueError(f"{name} has dtype {t.dtype}, expected {dt}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    for name, t in (("a_vals", a_vals), ("b_vals", b_vals), ("c_vals", c_vals)):
+        if t.dim() != 3 or tuple(t.shape[1:]) != (bs, bs):
+            raise ValueError(f"{name} must have shape [n, {bs}, {bs}]")
+    if seg.dim() != 1 or seg.numel() < 1:
+        raise ValueError("seg must be a 1-D tensor of nc + 1 offsets")
+    if ta.shape != tb.shape or ta.dim() != 1:
+        raise ValueError("ta and tb must be 1-D tensors of the same length")
+    if nnz_out.numel() != 1:
+        raise ValueError("nnz_out must hold one element")
     nc = int(seg.numel()) - 1
+    if int(c_vals.shape[0]) != nc:
+        raise ValueError(f"c_vals holds {int(c_vals.shape[0])} blocks, seg describes {nc}")
     code = load().bsm_block_products_fp64_noalloc(
         bs, nc, seg.data_ptr(), ta.data_ptr(), tb.data_ptr(), a_vals.data_ptr(),
         int(a_vals.shape[0]), b_vals.data_ptr(), int(b_vals.shape[0]), c_vals.data_ptr(),
         nnz_out.data_ptr(), _stream_ptr(stream))
     _check(code, "bsm_block_products_fp64_noalloc")
+
+
+BSM_PROBE_DMMA_M8N8K4 = 0
+BSM_PROBE_DMMA_M16N8K4 = 1
+BSM_PROBE_DMMA_M16N8K8 = 2
+BSM_PROBE_DMMA_M16N8K16 = 3
+BSM_PROBE_DFMA = 4
+
+
+def bsm_probe_fp64(kind: int, iters: int, stream=None):
+    """(flops, ms) of one FP64 probe launch (include/bsm_probe.h)."""
+    f, ms = ctypes.c_double(), ctypes.c_float()
+    _check(load().bsm_probe_fp64(int(kind), int(iters), ctypes.byref(f), ctypes.byref(ms),
+                                 _stream_ptr(stream)), "bsm_probe_fp64")
+    return f.value, ms.value
+
+
+def bsm_probe_tcgen05(fmt: int, n: int, iters: int, stream=None):
+    """(flops, ms) of one tcgen05.mma probe launch: fmt 0 BF16, 1 E4M3; M = 128."""
+    f, ms = ctypes.c_double(), ctypes.c_float()
+    _check(load().bsm_probe_tcgen05(int(fmt), int(n), int(iters), ctypes.byref(f),
+                                    ctypes.byref(ms), _stream_ptr(stream)), "bsm_probe_tcgen05")
+    return f.value, ms.value
+
+
+def bsm_probe_bulk_copy(nbytes: int, stage_bytes: int = 32768, stages: int = 4, stream=None):
+    """(bytes, ms) of one bulk-copy streaming launch."""
+    f, ms = ctypes.c_double(), ctypes.c_float()
+    _check(load().bsm_probe_bulk_copy(int(nbytes), int(stage_bytes), int(stages),
+                                      ctypes.byref(f), ctypes.byref(ms), _stream_ptr(stream)),
+           "bsm_probe_bulk_copy")
+    return f.value, ms.value
 
 
 def bsm_selftest_wait_timeout(limit_ms: int, stream=None) -> str:
