@@ -275,6 +275,13 @@ LastStats &last_stats();
 int64_t &launch_counter();
 inline void count_launch(int n = 1) { launch_counter() += n; }
 bool timing_enabled();
+// Deferred per-phase timing of the last product on the calling thread (when
+// timing is enabled): a product records CUDA events on its stream and never
+// waits for them; bsm_last_phase_ms resolves them when it is called.
+void timing_begin();                          // drops the previous product's events
+int timing_mark(cudaStream_t s);              // records an event: its index, -1 if off
+void timing_span(int phase, int e0, int e1);  // phase += elapsed(e0, e1)
+void timing_rest(int phase, int e0, int e1);  // phase = elapsed(e0, e1) - the other phases
 
 #define BSM_TRY(x)                       \
   do {                                   \

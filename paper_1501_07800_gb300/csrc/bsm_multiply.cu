@@ -157,33 +157,6 @@ bsm_status finish_product_copy(bsm_matrix C, const SymbolicResult &sym, const do
   return build_levels(C, s);
 }
 
-// Per-phase CUDA events of one product (only when timing is enabled).
-struct PhaseTimer {
-  bool on;
-  cudaEvent_t ev[4] = {};
-  int n = 0;
-  explicit PhaseTimer(bool enabled) : on(enabled) {
-    if (on)
-      for (auto &e : ev) cudaEventCreate(&e);
-  }
-  void mark(cudaStream_t s) {
-    if (on && n < 4) cudaEventRecord(ev[n++], s);
-  }
-  void collect(double *ms) {
-    if (!on) return;
-    if (n == 4 && cudaEventSynchronize(ev[3]) == cudaSuccess)
-      for (int i = 0; i < 3; i++) {
-        float t = 0;
-        cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
-        ms[i] = t;
-      }
-  }
-  ~PhaseTimer() {
-    if (on)
-      for (auto &e : ev) cudaEventDestroy(e);
-  }
-};
-
 // Compacts the nonzero C blocks of one chunk into new arrays (or takes the
 // chunk's arrays when nothing was dropped).
 static bsm_status compact_chunk(SymbolicResult &r, double *&cvals, const int32_t *nz,
@@ -282,17 +255,10 @@ static bsm_status multiply_chunked(bsm_matrix A, bsm_matrix B, int prec, int sli
   LastStats &ls = last_stats();
   ls = LastStats();
   const int64_t l0 = launch_counter();
-  const bool timed = timing_enabled();
-  cudaEvent_t e0 = nullptr, e1 = nullptr, ea = nullptr, eb = nullptr, ec = nullptr;
-  if (timed) {
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventCreate(&ea);
-    cudaEventCreate(&eb);
-    cudaEventCreate(&ec);
-    cudaEventRecord(e0, s);
-  }
-  double numeric_ms = 0, finish_ms = 0;
+  // timing (when enabled): events only, resolved by bsm_last_phase_ms, so
+  // that the product never waits for them
+  timing_begin();
+  const int t_begin = timing_mark(s);
   const int bs = A->bs;
   struct Chunk {
     uint64_t *keys;
@@ -317,25 +283,18 @@ static bsm_status multiply_chunked(bsm_matrix A, bsm_matrix B, int prec, int sli
       dev_free(nz, s);
       return e;
     }
-    if (timed) cudaEventRecord(ea, s);
+    const int t_a = timing_mark(s);
     {
       NvtxRange numeric(prec == BSM_FP64 ? "numeric fp64" : "numeric split");
       e = prec == BSM_FP64 ? numeric_fp64(A, B, r, cvals, nz, err, s)
                            : numeric_split(A, B, r, slices, cvals, nz, err, s);
     }
-    if (timed) cudaEventRecord(eb, s);
+    const int t_b = timing_mark(s);
     Chunk c{nullptr, nullptr, 0};
     if (e == BSM_OK) e = compact_chunk(r, cvals, nz, err, bs, &c.keys, &c.vals, &c.n, s);
-    if (timed) {
-      cudaEventRecord(ec, s);
-      if (cudaEventSynchronize(ec) == cudaSuccess) {
-        float t1 = 0, t2 = 0;
-        cudaEventElapsedTime(&t1, ea, eb);
-        cudaEventElapsedTime(&t2, eb, ec);
-        numeric_ms += t1;
-        finish_ms += t2;
-      }
-    }
+    const int t_c = timing_mark(s);
+    timing_span(1, t_a, t_b);
+    timing_span(2, t_b, t_c);
     dev_free(cvals, s);
     dev_free(nz, s);
     if (e == BSM_OK) {
@@ -393,17 +352,7 @@ static bsm_status multiply_chunked(bsm_matrix A, bsm_matrix B, int prec, int sli
   ls.nlev = H + 1;
   for (int l = 0; l <= H; l++) ls.tasks[l] = tasks[H - l];
   ls.chunks = nch;
-  if (timed) {
-    cudaEventRecord(e1, s);
-    if (cudaEventSynchronize(e1) == cudaSuccess) {
-      float tot = 0;
-      cudaEventElapsedTime(&tot, e0, e1);
-      ls.phase_ms[1] = numeric_ms;
-      ls.phase_ms[2] = finish_ms;
-      ls.phase_ms[0] = tot - numeric_ms - finish_ms;
-    }
-    for (cudaEvent_t e : {e0, e1, ea, eb, ec}) cudaEventDestroy(e);
-  }
+  timing_rest(0, t_begin, timing_mark(s));  // symbolic phase: the rest of the product
   ls.launches = launch_counter() - l0;
   return st;
 }
@@ -499,8 +448,7 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
   const int n = (int)idx.size();
   const int bs = A[idx[0]]->bs;
   LastStats &ls = last_stats();
-  PhaseTimer timer(timing_enabled());
-  timer.mark(s);
+  const int t0 = timing_mark(s);  // timing: events only, resolved by bsm_last_phase_ms
   std::vector<SymbolicResult> sym(n);
   std::vector<bsm_matrix> shells(n, nullptr);
   std::vector<double *> cv(n, nullptr);
@@ -585,7 +533,7 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
       owned.push_back(table);
     if (st == BSM_OK && (st = dev_alloc((void **)&scr, 16, s)) == BSM_OK) owned.push_back(scr);
   }
-  timer.mark(s);
+  const int t1 = timing_mark(s);
   if (st == BSM_OK && total > 0) {
     cudaMemsetAsync(scr, 0, 16, s);
     int64_t off = 0;
@@ -619,7 +567,7 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
                           split_chunk_for(total_item_nt, total_items), np);
     }
   }
-  timer.mark(s);
+  const int t2 = timing_mark(s);
   for (int i = 0; i < n && st == BSM_OK; i++) {
     if (sym[i].nc == 0) {
       st = build_levels(shells[i], s);
@@ -628,14 +576,16 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
       cv[i] = nullptr;
     }
   }
-  timer.mark(s);
+  const int t3 = timing_mark(s);
   if (st != BSM_OK) {
     cleanup(false);
     return st;
   }
   for (int i = 0; i < n; i++) C[idx[i]] = shells[i];
   cleanup(true);
-  timer.collect(ls.phase_ms);
+  timing_span(0, t0, t1);  // symbolic phases and the work list
+  timing_span(1, t1, t2);  // the numeric launch
+  timing_span(2, t2, t3);  // zero removal and C's levels
   return BSM_OK;
 }
 
@@ -660,6 +610,7 @@ extern "C" bsm_status bsm_multiply_batched(int n, const bsm_matrix *A, const bsm
   cudaStream_t s = (cudaStream_t)stream;
   LastStats &ls = last_stats();
   ls = LastStats();
+  timing_begin();
   int64_t l0 = launch_counter();
   bsm_status st = BSM_OK;
   // Operands are re-cut (each distinct handle once) to the override size, and

@@ -2,9 +2,11 @@
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
+#include <array>
 #include <atomic>
 #include <cstdlib>
 #include <mutex>
+#include <vector>
 
 #include "bsm_internal.cuh"
 
@@ -140,8 +142,69 @@ extern "C" bsm_status bsm_memory_in_use(uint64_t *bytes) {
   return BSM_OK;
 }
 
+namespace {
+struct PendingTiming {
+  std::vector<cudaEvent_t> ev;
+  std::vector<std::array<int, 3>> spans;  // (phase, first event, last event)
+  int rest[3] = {-1, -1, -1};             // (phase, first event, last event)
+  void clear() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    ev.clear();
+    spans.clear();
+    rest[0] = -1;
+  }
+};
+thread_local PendingTiming t_pending;
+
+// Waits for the last recorded event and turns the spans into phase times.
+void timing_resolve(LastStats &ls) {
+  PendingTiming &p = t_pending;
+  if (p.ev.empty()) return;
+  if (cudaEventSynchronize(p.ev.back()) == cudaSuccess) {
+    double ms[3] = {0, 0, 0};
+    auto el = [&](int a, int b) {
+      float t = 0;
+      if (a >= 0 && b >= 0) cudaEventElapsedTime(&t, p.ev[a], p.ev[b]);
+      return (double)t;
+    };
+    for (auto &sp : p.spans) ms[sp[0]] += el(sp[1], sp[2]);
+    if (p.rest[0] >= 0) {
+      double other = 0;
+      for (int i = 0; i < 3; i++)
+        if (i != p.rest[0]) other += ms[i];
+      ms[p.rest[0]] = el(p.rest[1], p.rest[2]) - other;
+    }
+    for (int i = 0; i < 3; i++) ls.phase_ms[i] = ms[i];
+  }
+  p.clear();
+}
+}  // namespace
+
+void timing_begin() { t_pending.clear(); }
+
+int timing_mark(cudaStream_t s) {
+  if (!timing_enabled()) return -1;
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return -1;
+  cudaEventRecord(e, s);
+  t_pending.ev.push_back(e);
+  return (int)t_pending.ev.size() - 1;
+}
+
+void timing_span(int phase, int e0, int e1) {
+  if (e0 >= 0 && e1 >= 0) t_pending.spans.push_back({phase, e0, e1});
+}
+
+void timing_rest(int phase, int e0, int e1) {
+  if (e0 < 0 || e1 < 0) return;
+  t_pending.rest[0] = phase;
+  t_pending.rest[1] = e0;
+  t_pending.rest[2] = e1;
+}
+
 extern "C" bsm_status bsm_last_phase_ms(double *ms, int cap, int *nphase, int64_t *launches) {
   LastStats &ls = last_stats();
+  timing_resolve(ls);
   if (nphase) *nphase = 3;
   if (launches) *launches = ls.launches;
   if (ms) {
