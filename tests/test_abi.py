@@ -1,5 +1,6 @@
-"""The C ABI library loads and exports every symbol include/bsm.h declares; the
-host-side argument checks run without a GPU (they return before any CUDA call)."""
+"""The C ABI library loads and exports every symbol the headers in include/
+declare; the host-side argument checks run without a GPU (they return before
+any CUDA call)."""
 import ctypes
 import os
 import re
@@ -10,9 +11,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "bsm.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(bsm_[a-z_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(bsm_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -84,6 +90,16 @@ def test_argument_checks_before_any_device_work(lib):
     assert lib.bsm_destroy(None) == 0
     assert lib.bsm_memory_in_use(None) == -1
     assert lib.bsm_set_memory_limit(ctypes.c_uint64(0)) == 0
+    # peak probes
+    f, ms = ctypes.c_double(), ctypes.c_float()
+    assert lib.bsm_probe_fp64(99, 1, ctypes.byref(f), ctypes.byref(ms), None) == -1
+    assert lib.bsm_probe_fp64(0, 0, ctypes.byref(f), ctypes.byref(ms), None) == -1
+    assert lib.bsm_probe_tcgen05(2, 64, 1, ctypes.byref(f), ctypes.byref(ms), None) == -1
+    assert lib.bsm_probe_tcgen05(0, 40, 1, ctypes.byref(f), ctypes.byref(ms), None) == -1
+    assert lib.bsm_probe_bulk_copy(1 << 20, 100, 4, ctypes.byref(f), ctypes.byref(ms),
+                                   None) == -1
+    assert lib.bsm_probe_bulk_copy(1 << 30, 65536, 8, ctypes.byref(f), ctypes.byref(ms),
+                                   None) == -1
 
 
 def test_misaligned_device_pointers_rejected_before_any_work(lib):
@@ -109,7 +125,7 @@ def test_header_is_plain_c_and_links_from_c(lib, tmp_path):
         pytest.skip("no C compiler")
     src = tmp_path / "use_bsm.c"
     src.write_text(
-        '#include "bsm.h"\n#include <stdio.h>\n#include <string.h>\n'
+        '#include "bsm.h"\n#include "bsm_probe.h"\n#include <stdio.h>\n#include <string.h>\n'
         "int main(void) {\n"
         "  bsm_mult_opts o = {BSM_SPLIT_BF16, 7, 0, 32};\n"
         "  bsm_matrix m = NULL;\n"
