@@ -7,6 +7,14 @@ exact-zero removal and C's level build, inputs resident in HBM):
   nonzero with probability 0.02 (uniform placement), entries N(0,1), C = A*B.
 Useful flops = 2 * bs^3 per nonzero (A_IK, B_KJ) block pair.
 
+The default run also times, on the same GPU: the split-precision product of
+the same operands, the product end to end with host buffers, 64 batched
+products, the 20,000-point decay-type product (split BF16x7 and FP8x12 whole,
+FP64 on one diagonal quadtree node of C, errors against the oracle on
+sampled blocks), and the CPU oracle on bounded samples (one core and every
+available core).  The FP64 roofline denominator is measured in the same run
+by the library's probe (bsm_probe_fp64).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun every rank runs an independent product of the same size
 (weak scaling, no data-path collective); rank 0 prints one JSON line.
@@ -18,9 +26,7 @@ import hashlib
 import json
 import os
 import statistics
-import subprocess
 import sys
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -35,9 +41,6 @@ METRIC = "useful GFLOP/s of C=A*B (2*bs^3 per nonzero block pair), FP64"
 WORKLOAD = {"workload": "random block-sparse N=65536, bs=32, block density 0.02, N(0,1)",
             "n": 65536, "bs": 32, "p": 0.02, "global_batch": 1,
             "l2": "inputs larger than L2 (A+B 1.4 GB, C 19 GB)"}
-# FP64 tensor peak: no FP64 entry in the measured peaks, so the bf16 measured
-# burst peak is scaled by the nominal FP64 / bf16 dense ratio (1.25 / 2250).
-FP64_NOMINAL_RATIO = 1.25 / 2250.0
 
 
 def log(*a):
@@ -52,67 +55,38 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
 
 
-def workload(rank: int, n: int, bs: int, p: float):
+def workload_seeds(rank: int):
     sa = synth.BASE_SEED + 1 + 1000 * rank
+    return sa, sa + 7919
+
+
+WORKLOAD_SEEDS = workload_seeds(0)
+
+
+def workload(rank: int, n: int, bs: int, p: float):
+    sa, sb = workload_seeds(rank)
     A = synth.random_blocks(n, bs, p, sa)
-    B = synth.random_blocks(n, bs, p, sa + 7919)
+    B = synth.random_blocks(n, bs, p, sb)
     return A, B
 
 
-# ------------------------------------------------------------- clock probe
-class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+# ------------------------------------------------------------- peaks, clocks
+def ClockSampler(dev: int):
+    from paper_1501_07800_gb300.probe import ClockSampler as CS
+    return CS(dev)
 
-    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, dev: int):
-        self.dev = dev
-        self.proc = None
-        self.lines = []
-
-    def start(self):
-        try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except (FileNotFoundError, OSError):
-            self.proc = None
-
-    def _read(self):
-        for ln in self.proc.stdout:
-            self.lines.append(ln.strip())
-
-    def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        self.t.join(timeout=2)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 7:
-                continue
-            try:
-                sm.append(float(f[0]))
-                smax.append(float(f[1]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[3:7]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+def fp64_peak_measured(bsm, seconds: float = 1.0) -> dict:
+    """The FP64 tensor-pipe peak measured now by the library's probe
+    (bsm_probe_fp64, mma.sync m8n8k4 -- the FP64 kernel's instruction -- on
+    every SM, best of two launches of about a second), with its clock."""
+    from paper_1501_07800_gb300 import probe
+    p = probe.fp64_peak(seconds)
+    clk = p["clocks"]
+    return {"tflops": p["tflops"], "clocks": clk, "runs": p["runs"],
+            "source": (f"measured in this run by bsm_probe_fp64 (DMMA m8n8k4, every SM; "
+                       f"paper_1501_07800_gb300/csrc/bsm_probe.cu): {p['tflops']:.4f} TFLOP/s "
+                       f"at median SM clock {clk.get('sm_mhz')} MHz")}
 
 
 # ------------------------------------------------------------ traffic table
@@ -130,9 +104,63 @@ def recorded_traffic(kernel: str, src: str):
 
 
 # ------------------------------------------------------------ CPU baseline
-def cpu_baseline(A, B, target_s: float = 12.0):
-    """The oracle, as it stands, on a bounded sample: the first R block rows of A
-    times the whole of B (same workload, fewer C rows)."""
+def _oracle_rows_worker(n, bs, p, seed_a, seed_b, r0, r1, bar, q):
+    """One process of the all-core oracle timing: regenerates the workload from
+    its seeds, builds the oracle's trees for A's block rows [r0, r1) and all of
+    B, waits for the other processes, and times the product (the unmodified
+    oracle; CLOCK_MONOTONIC times, comparable across processes)."""
+    import oracle
+    A = synth.random_blocks(n, bs, p, seed_a)
+    B = synth.random_blocks(n, bs, p, seed_b)
+    keep = (A.brow >= r0) & (A.brow < r1)
+    As = synth.BlockCOO(A.nrows, A.ncols, A.bs, A.brow[keep], A.bcol[keep], A.vals[keep])
+    L = oracle.common_depth(A, B)
+    ta, tb = oracle.tree(As, L), oracle.tree(B, L)
+    del A
+    bar.wait(timeout=900)
+    t0 = time.perf_counter()
+    P = oracle.multiply_trees(ta, tb)
+    q.put((r0, t0, time.perf_counter(), P.triples))
+
+
+def oracle_all_cores(n, bs, p, seed_a, seed_b, rows_per_proc: int, nproc: int) -> dict:
+    """The oracle in `nproc` processes over disjoint ranges of A's block rows
+    (the same arithmetic; spawned processes, no GPU): wall time from the first
+    start to the last end."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    bar, q = ctx.Barrier(nproc), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_rows_worker,
+                         args=(n, bs, p, seed_a, seed_b, k * rows_per_proc,
+                               (k + 1) * rows_per_proc, bar, q)) for k in range(nproc)]
+    for pr in procs:
+        pr.start()
+    import queue
+    res, t_end = [], time.time() + 1800
+    try:
+        while len(res) < nproc:
+            try:
+                res.append(q.get(timeout=2))
+            except queue.Empty:
+                if any(pr.exitcode not in (None, 0) for pr in procs) or time.time() > t_end:
+                    raise RuntimeError("an oracle process failed")
+    finally:
+        for pr in procs:
+            pr.join(timeout=30 if len(res) == nproc else 0.1)
+            if pr.is_alive():
+                pr.terminate()
+    t0 = min(x[1] for x in res)
+    t1 = max(x[2] for x in res)
+    triples = sum(x[3] for x in res)
+    return {"seconds": t1 - t0, "triples": triples,
+            "gflops": metrics.block_flops(bs, triples) / (t1 - t0) / 1e9}
+
+
+def cpu_baseline(A, B, decay=None, target_s: float = 12.0):
+    """The oracle, as it stands, on bounded samples of the same workload: the
+    first R block rows of A times the whole of B on one core, then disjoint
+    row ranges in one process per available host core.  With the decay
+    product's sampled-block timing, its extrapolated full-product times."""
     import oracle
 
     L = oracle.common_depth(A, B)
@@ -150,10 +178,38 @@ def cpu_baseline(A, B, target_s: float = 12.0):
     P, dt = sample(rows)  # calibration, then a sample of about target_s
     rows = int(min(A.mb, max(rows, rows * target_s / max(dt, 1e-3))))
     P, dt = sample(rows)
-    flops = metrics.block_flops(A.bs, P.triples)
-    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {rows} of {A.mb} block rows of A times all of B "
-                      f"({P.triples} block products, {dt:.2f} s single-threaded)"}
+    del tb
+    single = metrics.block_flops(A.bs, P.triples) / dt / 1e9
+    cores = len(os.sched_getaffinity(0))
+    out = {"value": single, "unit": "GFLOP/s", "cores": 1, "cores_available": cores,
+           "kind": "oracle",
+           "sample": f"first {rows} of {A.mb} block rows of A times all of B "
+                     f"({P.triples} block products, {dt:.2f} s single-threaded)",
+           "single_thread": {"value": single, "rows": rows, "seconds": dt}}
+    if cores > 1:
+        # about target_s of wall time in all processes, disjoint row ranges
+        per = int(max(1, min(A.mb // cores, rows * target_s / max(dt, 1e-3))))
+        sa, sb = WORKLOAD_SEEDS
+        allc = oracle_all_cores(A.nrows, A.bs, WORKLOAD["p"], sa, sb, per, cores)
+        out.update({"value": allc["gflops"], "cores": cores,
+                    "sample": f"{cores} processes, each {per} consecutive block rows of A "
+                              f"(rows 0..{cores * per - 1} of {A.mb}) times all of B "
+                              f"({allc['triples']} block products, {allc['seconds']:.2f} s wall)",
+                    "all_cores": {"value": allc["gflops"], "processes": cores,
+                                  "rows_per_process": per, "seconds": allc["seconds"],
+                                  "speedup_vs_single": allc["gflops"] / single}})
+    if decay is not None and "oracle" in decay:
+        o = decay["oracle"]
+        scale = out["value"] / single
+        out["decay_c2_extrapolated"] = {
+            "single_thread_s": o["full_product_s_extrapolated"],
+            "all_cores_s": o["full_product_s_extrapolated"] / scale,
+            "how": f"oracle time on {o['sampled_blocks']} sampled C blocks of the 20,000-point "
+                   f"decay product ({o['gflops']:.2f} GFLOP/s, one thread), extrapolated to "
+                   f"its {decay['block_products']} block products by the flop ratio; all cores: "
+                   f"divided by the all-core speedup measured on the random product",
+            "label": "extrapolated"}
+    return out
 
 
 def run_reference(args):
@@ -253,7 +309,6 @@ def run_gpu(args):
                        torch.from_numpy(B.vals).to(dev))
     torch.cuda.synchronize()
 
-    bsm.bsm_set_timing(True)
     prec = bsm.BSM_SPLIT_BF16 if args.mode == "split" else bsm.BSM_FP64
 
     def product():
@@ -261,6 +316,8 @@ def run_gpu(args):
             return bsm.bsm_multiply(ga, gb, prec=prec)
         return bsm.bsm_multiply_range(ga, gb, key_range[0], key_range[1], prec=prec)
 
+    # the FP64 roofline denominator, measured now on this GPU
+    peak = fp64_peak_measured(bsm) if prec == bsm.BSM_FP64 else None
     for _ in range(args.warmup):
         C = product()
         del C
@@ -268,42 +325,57 @@ def run_gpu(args):
     _, triples, nc_sym = bsm.bsm_last_stats()
     flops = metrics.block_flops(bs, triples)
 
+    def timed_steps(k: int, instrumented: bool):
+        """k products between events on the stream.  instrumented: per-phase
+        timing on -- CUDA events the product records and never waits for,
+        read back after each step's end event (outside the step's interval)."""
+        bsm.bsm_set_timing(instrumented)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(k)]
+        num, nlaunch, nblk = [], 0, 0
+        for i in range(k):
+            ev[i][0].record(stream)
+            C = product()
+            ev[i][1].record(stream)
+            ms, nl = bsm.bsm_last_phase_ms()
+            num.append(ms[1])
+            nlaunch += nl
+            nblk = C.nblk
+            del C
+        torch.cuda.synchronize()
+        return [x.elapsed_time(y) for x, y in ev], num, nlaunch, nblk
+
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    numeric_ms, launches = [], 0
-    for i in range(args.steps):
-        ev[i][0].record(stream)
-        C = product()
-        ev[i][1].record(stream)
-        ms, nl = bsm.bsm_last_phase_ms()
-        numeric_ms.append(ms[1])
-        launches += nl
-        nblk_c = C.nblk
-        del C
+    step_ms, numeric_ms, launches, nblk_c = timed_steps(args.steps, True)
     barrier()
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    phase_last = [float(x) for x in bsm.bsm_last_phase_ms()[0]]
+    # the same steps without any instrumentation: the timing events cost nothing
+    plain_ms, _, _, _ = timed_steps(min(args.steps, 3), False)
+    bsm.bsm_set_timing(True)
     tot_s = allmax(sum(step_ms) / 1e3)
     total_flops = allsum(flops * args.steps)
     value = total_flops / tot_s / 1e9
 
     peaks, which = measured_peaks()
-    fp64_peak = peaks["bf16_tflops"] * FP64_NOMINAL_RATIO
     t_num = statistics.mean(numeric_ms) / 1e3
-    achieved = flops / t_num / 1e12
-    if prec != bsm.BSM_FP64:  # split mode: BF16 digit-pair flops against the bf16 peak
-        achieved = flops * 28 / t_num / 1e12
-        fp64_peak = peaks["bf16_tflops_sustained"]
-    roofline = {"bound": "tensor", "kernel": "k_numeric_fp64 (DMMA f64)",
-                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak,
-                "peak_source": f"{which} bf16 burst {peaks['bf16_tflops']} TFLOP/s x nominal "
-                               f"FP64/bf16 ratio 1.25/2250",
-                "traffic": recorded_traffic("k_numeric_fp64",
-                                            "paper_1501_07800_gb300/csrc/bsm_numeric_fp64.cu")}
+    if prec == bsm.BSM_FP64:
+        roofline = {"bound": "tensor", "kernel": "k_numeric_fp64 (DMMA f64)",
+                    "achieved": flops / t_num / 1e12, "peak": peak["tflops"],
+                    "unit": "TFLOP/s", "frac": flops / t_num / 1e12 / peak["tflops"],
+                    "peak_source": peak["source"], "peak_runs_tflops": peak["runs"],
+                    "achieved_from": "useful flops / mean duration of the numeric phase "
+                                     "(CUDA events on the product's stream) over the timed steps"}
+    else:  # split mode: BF16 digit-pair flops against the bf16 peak
+        roofline = {"bound": "tensor", "kernel": "k_numeric_split (tcgen05 kind::f16)",
+                    "achieved": flops * 28 / t_num / 1e12, "peak": peaks["bf16_tflops_sustained"],
+                    "unit": "TFLOP/s",
+                    "frac": flops * 28 / t_num / 1e12 / peaks["bf16_tflops_sustained"],
+                    "peak_source": f"{which} bf16 sustained"}
+    roofline["traffic"] = recorded_traffic("k_numeric_fp64",
+                                           "paper_1501_07800_gb300/csrc/bsm_numeric_fp64.cu")
 
     # split-precision mode on the same inputs, same timing protocol
     split = None
@@ -320,7 +392,8 @@ def run_gpu(args):
                 "config": dict(WORKLOAD, parallelism=(f"C Morton-range shards x{world}"
                                                       if args.shard else f"replicas{world}")),
                 "triples": triples, "c_blocks": nblk_c, "c_blocks_symbolic": nc_sym,
-                "phase_ms_last": [float(x) for x in bsm.bsm_last_phase_ms()[0]],
+                "phase_ms_last": phase_last, "ms_per_step_uninstrumented":
+                    statistics.mean(plain_ms),
                 "roofline": roofline, "gpu_launches": launches, "clocks": clk}
         if split is not None:
             line["split_bf16"] = split
@@ -335,14 +408,45 @@ def run_gpu(args):
                            "ms_per_step": 1e3 * e2e["seconds"] / e2e["steps"]}
     if line is not None and not args.no_batched:
         line["batched"] = run_batched(bsm, torch, args, stream)
+    if line is not None and world == 1 and not args.no_decay:
+        # the decay-type product with 20,000 points (N = 100,000): full split
+        # products, FP64 on one diagonal quadtree node of C
+        del ga, gb
+        bsm.bsm_release_memory()
+        torch.cuda.empty_cache()
+        line["decay_c2"] = decay_c2(bsm, torch, peak, args)
     if line is not None and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(A, B)
+        line["cpu_baseline"] = cpu_baseline(A, B, line.get("decay_c2"))
     if line is not None:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def decay_c2(bsm, torch, peak, args) -> dict:
+    """The electronic-structure-like product A*A with 20,000 points (N =
+    100,000, bs 32): split BF16x7 and FP8x12 over the whole product (two timed
+    products each after a warm-up), FP64 on the C blocks of the diagonal
+    quadtree node [1024, 1536)^2 (its block products' flops against the FP64
+    peak), errors against the oracle on 1000 C blocks sampled over all of C
+    (plus 200 inside the node), with the clock record."""
+    if peak is None:
+        peak = fp64_peak_measured(bsm)
+    legs = [dict(name="split_bf16x7", prec=bsm.BSM_SPLIT_BF16, slices=7, sym=False),
+            dict(name="split_fp8x12", prec=bsm.BSM_SPLIT_FP8, slices=12, sym=False),
+            dict(name="fp64_node", prec=bsm.BSM_FP64, slices=0, sym=False, range=(1024, 512),
+                 steps=1)]
+    clk = ClockSampler(torch.cuda.current_device()).start()
+    out = decay_product(bsm, torch, 20000, 32, legs, 2, peak=peak)
+    out["clocks"] = clk.stop()
+    f = out["fp64_node"]
+    for k in ("split_bf16x7", "split_fp8x12"):
+        # the FP64 time of the whole product at the node's measured rate
+        fp64_full_ms = out["block_products"] / f["block_products"] * f["ms_per_product"]
+        out[k]["speedup_vs_fp64_at_node_rate"] = fp64_full_ms / out[k]["ms_per_product"]
+    return out
 
 
 def run_split(bsm, torch, ga, gb, args, stream, flops, triples, A, B, rank, slices=7):
@@ -481,58 +585,55 @@ def run_batched(bsm, torch, args, stream, nprod=64):
     return out
 
 
-def run_decay(args):
-    """Decay-type product A*A: points uniform in a cube at 0.1 per cubic Angstrom,
-    recursive-bisection order, 5 functions per point, A_ij = s_ij exp(-0.5 r_ij)
-    dropped below 1e-6 (20,000 points: N = 100,000).  FP64 and split BF16 with
-    the given slice counts; optionally the symmetric square (upper triangle of
-    A*A from the upper triangle of A).  C's symbolic structure is compared with
-    the block-pattern product (the definition of S_C); blocks whose entries all
-    vanish (element-level sparsity inside blocks) are removed by the product,
-    and on 1000 uniformly sampled C blocks the values and the presence of each
-    block are compared with the oracle's definition.  With --node-side only the
-    C blocks of one diagonal quadtree node are computed (from the operand
-    blocks in its rows and columns) and checked on a 32 x 32 grid of them."""
+def _morton(i: int, j: int) -> int:
+    from paper_1501_07800_gb300 import shard as sh
+    return int(sh.morton(i, j))
+
+
+def decay_product(bsm, torch, npts: int, bs: int, legs, steps: int, node=None,
+                  nsample: int = 1000, range_sample: int = 200, peak=None) -> dict:
+    """Decay-type product A*A: points uniform in a cube at 0.1 per cubic
+    Angstrom, recursive-bisection order, 5 functions per point, A_ij = s_ij
+    exp(-0.5 r_ij) dropped below 1e-6 (20,000 points: N = 100,000), generated
+    on the device.
+
+    legs: dicts {name, prec, slices, sym, range}; range = (first block, side)
+    of a diagonal quadtree node of C (a Morton range, bsm_multiply_range) or
+    None for the whole product; sym: the symmetric square (upper triangle of
+    A*A from the upper triangle of A).  Each leg is timed over `steps`
+    products (split legs after one warm-up product).  C's symbolic structure
+    is compared with the block-pattern product (the definition of S_C);
+    blocks whose entries all vanish are removed by the product, and on
+    `nsample` C blocks sampled uniformly over C (plus `range_sample` inside
+    every node range) the values and the presence of each block are compared
+    with the oracle's definition, computed from the operand blocks in the
+    sampled rows and columns.  The oracle's time on the sampled blocks
+    (single-threaded) gives its extrapolated time for the whole product.
+    node = (lo, hi): only the operand blocks with a row or a column in
+    [lo, hi) are generated (products whose full C would not fit on one GPU);
+    every leg then covers the node and the sample is a 32 x 32 grid of it."""
     import ctypes
 
-    import torch
-
     import oracle
-    import paper_1501_07800_gb300 as bsm
     from synth import device as sd
 
-    torch.cuda.set_device(0)
-    bsm.load()
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    npts, bs = args.points, args.bs
     t0 = time.time()
-    # --node-side S: only the C blocks of one diagonal quadtree node
-    # [lo, lo + S)^2 (S a power of two, lo a multiple of S) are computed, from
-    # the operand blocks with a row or a column in [lo, lo + S): the products
-    # whose full C would not fit on one GPU, one node at a time
-    node = None
-    if args.node_side:
-        S = args.node_side
-        nbk_full = -(-(npts * 5) // bs)
-        lo_b = args.node_at if args.node_at is not None else (nbk_full // 2) // S * S
-        if S & (S - 1) or lo_b % S or lo_b >= nbk_full:
-            raise SystemExit("--node-side must be a power of two and --node-at a multiple of it")
-        node = (lo_b, min(lo_b + S, nbk_full))
-        args.sym = False
     n, r, c, v = sd.decay(npts, bs, synth.BASE_SEED + 2, dev, cross=node)
     nbk = -(-n // bs)
     A = bsm.bsm_build(n, n, bs, r, c, v)
     U = None
-    if args.sym:
+    if any(g["sym"] for g in legs):
         up = r <= c
         U = bsm.bsm_build(n, n, bs, r[up].contiguous(), c[up].contiguous(), v[up].contiguous())
         del up
     torch.cuda.synchronize()
     gen_s = time.time() - t0
     nblk = A.nblk
-    # structure of C by definition: the block-pattern product of A's stored
-    # blocks (the generator's all-zero blocks are not stored)
+    # C's structure by definition: the block-pattern product of A's stored
+    # blocks (the generator's all-zero blocks are not stored); K[i, j] is the
+    # number of block products of C block (i, j)
     ar = torch.empty(max(nblk, 1), dtype=torch.int32, device=dev)
     ac = torch.empty(max(nblk, 1), dtype=torch.int32, device=dev)
     cnt = ctypes.c_int64(nblk)
@@ -541,29 +642,49 @@ def run_decay(args):
     Pm = torch.zeros((nbk, nbk), dtype=torch.float32, device=dev)
     Pm[ar[:nblk].long(), ac[:nblk].long()] = 1.0
     del ar, ac
-    if node is None:
-        pat = (Pm @ Pm) > 0.5
-        ci, cj = torch.nonzero(pat, as_tuple=True)
-    else:  # the node's rows and columns need all of K: present in the cross
-        a0, a1 = node
-        pat = (Pm[a0:a1] @ Pm[:, a0:a1]) > 0.5
-        ci, cj = torch.nonzero(pat, as_tuple=True)
-        ci, cj = ci + a0, cj + a0
-    del Pm, pat
+    a0, a1 = node if node is not None else (0, nbk)
+    K = Pm[a0:a1] @ Pm[:, a0:a1]   # exact: counts below 2^24
+    del Pm
+    ci, cj = torch.nonzero(K > 0.5, as_tuple=True)
     nc_def = int(ci.numel())
-    nc_def_upper = int((ci <= cj).sum())
     g = torch.Generator(device="cpu").manual_seed(synth.BASE_SEED)
+    cic, cjc = ci.cpu() + a0, cj.cpu() + a0
     if node is None:
-        pick = torch.randperm(nc_def, generator=g)[:1000]
+        pick = torch.randperm(nc_def, generator=g)[:nsample]
     else:
         # a grid of 32 block rows x 32 block columns of the node (about 1000
         # blocks) keeps the oracle's restricted operands small
         side = node[1] - node[0]
         gr = node[0] + torch.randperm(side, generator=g)[:32]
-        gc = node[0] + torch.randperm(side, generator=g)[:32]
-        cic, cjc = ci.cpu(), cj.cpu()
-        pick = torch.nonzero(torch.isin(cic, gr) & torch.isin(cjc, gc)).flatten()
-    si, sj = ci.cpu()[pick].numpy(), cj.cpu()[pick].numpy()
+        gcl = node[0] + torch.randperm(side, generator=g)[:32]
+        pick = torch.nonzero(torch.isin(cic, gr) & torch.isin(cjc, gcl)).flatten()
+    picks = [pick]
+    for lg in legs:   # extra samples inside every node range of a leg
+        if lg.get("range") and node is None:
+            lo_b, side = lg["range"]
+            inr = torch.nonzero((cic >= lo_b) & (cic < lo_b + side) & (cjc >= lo_b) &
+                                (cjc < lo_b + side)).flatten()
+            picks.append(inr[torch.randperm(int(inr.numel()), generator=g)[:range_sample]])
+    pick = torch.unique(torch.cat(picks))
+    si, sj = cic[pick].numpy(), cjc[pick].numpy()
+    nprod_s = K[torch.from_numpy(si - a0).to(dev), torch.from_numpy(sj - a0).to(dev)]
+    sampled_flops = metrics.block_flops(bs, int(nprod_s.sum().item()))
+
+    def useful(rng, sym):
+        """Block products of the leg's C blocks, from the pattern counts."""
+        Kr = K
+        off = a0
+        if rng is not None:
+            lo_b, side = rng
+            Kr = K[lo_b - a0:lo_b - a0 + side, lo_b - a0:lo_b - a0 + side]
+            off = lo_b
+        if sym:
+            ii = torch.arange(Kr.shape[0], device=dev)[:, None] + off
+            jj = torch.arange(Kr.shape[1], device=dev)[None, :] + off
+            Kr = torch.where(ii <= jj, Kr, torch.zeros_like(Kr))
+        return int(Kr.sum(dtype=torch.float64).item()), int((Kr > 0.5).sum().item())
+
+    total_triples, _ = useful(None, False)
     # oracle operands restricted to the sampled rows (left) and columns (right)
     rows_keep = torch.isin(r, torch.from_numpy(si).to(dev).to(torch.int32))
     cols_keep = torch.isin(c, torch.from_numpy(sj).to(dev).to(torch.int32))
@@ -573,49 +694,45 @@ def run_decay(args):
                            v[cols_keep].cpu().numpy())
     del r, c, v, rows_keep, cols_keep
     torch.cuda.empty_cache()
-    t1 = time.time()
     L = oracle.common_depth(left, right)
     tl, tr = oracle.tree(left, L), oracle.tree(right, L)
+    t1 = time.perf_counter()
     refs = [oracle.block_product(tl, tr, i, j) for i, j in zip(si, sj)]
+    oracle_s = time.perf_counter() - t1
     ref = np.stack([x[1] for x in refs])
     ref_nonzero = np.array([bool(np.any(x[1] != 0.0)) for x in refs])
-    oracle_s = time.time() - t1
-    del tl, tr, left, right
+    del tl, tr, left, right, refs
+    oracle_rate = sampled_flops / oracle_s
     log(f"decay: n={n} blocks={nblk} C(def)={nc_def}; generation {gen_s:.1f} s, "
         f"oracle on {len(si)} blocks {oracle_s:.1f} s")
-    bsm.bsm_set_timing(True)
     out = {"workload": f"decay A*A, {npts} points (N={n}), bs {bs}", "a_blocks": nblk,
-           "c_blocks_definition": nc_def, "sampled_blocks_exactly_zero": int((~ref_nonzero).sum())}
-    key_range = None
+           "c_blocks_definition": nc_def, "block_products": total_triples,
+           "useful_gflop": metrics.block_flops(bs, total_triples) / 1e9,
+           "sampled_blocks": int(len(si)),
+           "sampled_blocks_exactly_zero": int((~ref_nonzero).sum()),
+           "oracle": {"kind": "oracle", "cores": 1, "sampled_blocks": int(len(si)),
+                      "seconds": oracle_s, "gflops": oracle_rate / 1e9,
+                      "full_product_s_extrapolated": metrics.block_flops(bs, total_triples)
+                      / oracle_rate,
+                      "how": "the oracle's single-threaded time on the sampled C blocks, "
+                             "extrapolated to the whole product by the flop ratio"}}
     if node is not None:
-        from paper_1501_07800_gb300 import shard as sh
-        klo = int(sh.morton(node[0], node[0]))
-        key_range = (klo, klo + args.node_side * args.node_side)
-        out["workload"] += (f": the C blocks of the diagonal quadtree node [{node[0]}, {node[1]})^2 "
-                            f"of {nbk}^2 block positions, operands restricted to its rows and "
-                            f"columns (bsm_multiply_range)")
-    peaks, which = measured_peaks()
-    fp64_peak = peaks["bf16_tflops"] * FP64_NOMINAL_RATIO
-    slices = [int(x) for x in args.slices.split(",") if x]
-    legs = [(f"split_bf16x{k}", False, bsm.BSM_SPLIT_BF16, k, args.steps) for k in slices]
-    legs += [(f"split_fp8x{k}", False, bsm.BSM_SPLIT_FP8, int(k), args.steps)
-             for k in args.fp8_slices.split(",") if k]
-    if not args.no_fp64:
-        legs.append(("fp64", False, bsm.BSM_FP64, 0, 1))
-    if args.sym:
-        legs += [(f"sym_square_split_bf16x{slices[-1]}", True, bsm.BSM_SPLIT_BF16, slices[-1],
-                  args.steps)]
-        if not args.no_fp64:
-            legs.append(("sym_square_fp64", True, bsm.BSM_FP64, 0, 1))
-    # FP64 first: its statistics are the product's own at this block size (a
-    # split product at a width its kernel does not take runs on re-cut blocks,
-    # and its statistics are those of the re-cut product)
-    legs.sort(key=lambda g: (g[1], g[2] != bsm.BSM_FP64))
-    useful = {}
-    for name, sym, prec, nsl, reps in legs:
+        out["workload"] += (f": the C blocks of the diagonal quadtree node [{node[0]}, "
+                            f"{node[1]})^2 of {nbk}^2 block positions, operands restricted to "
+                            f"its rows and columns (bsm_multiply_range)")
+    for lg in legs:
+        name, prec, nsl, sym = lg["name"], lg["prec"], lg["slices"], lg["sym"]
+        rng = lg.get("range")
+        if node is not None:
+            rng = (node[0], node[1] - node[0])
+        key_range = None
+        if rng is not None:
+            klo = _morton(rng[0], rng[0])
+            key_range = (klo, klo + rng[1] * rng[1])
         times = []
         C = None
-        for k in range(reps + (1 if prec != bsm.BSM_FP64 else 0)):
+        warm = 0 if prec == bsm.BSM_FP64 else 1
+        for k in range(lg.get("steps", steps) + warm):
             C = None
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -624,60 +741,110 @@ def run_decay(args):
                  if key_range else bsm.bsm_multiply(A, A, prec=prec, slices=nsl))
             e1.record(stream)
             torch.cuda.synchronize()
-            if prec == bsm.BSM_FP64 or k > 0:  # split: first run is a warm-up
+            if k >= warm:
                 times.append(e0.elapsed_time(e1))
         ms, _ = bsm.bsm_last_phase_ms()
-        _, triples, ncs = bsm.bsm_last_stats()
-        recut = prec != bsm.BSM_FP64 and (bs == 64 or prec == bsm.BSM_SPLIT_FP8) and bs != 32
-        if prec == bsm.BSM_FP64:
-            useful[sym] = (triples, ncs)
-        if recut:  # useful work of the product at the operands' block size
-            triples, ncs = useful.get(sym, (None, None))
-        flops = metrics.block_flops(bs, triples) if triples is not None else float("nan")
+        _, triples_run, ncs = bsm.bsm_last_stats()
+        triples, nc_leg = useful(rng if node is None else None, sym)
+        flops = metrics.block_flops(bs, triples)
         nr, ncol, _, ncb = bsm.bsm_info(C)
         cr = torch.empty(max(ncb, 1), dtype=torch.int32, device=dev)
         cc = torch.empty(max(ncb, 1), dtype=torch.int32, device=dev)
         cnt = ctypes.c_int64(ncb)
-        code = bsm.load().bsm_to_blocks(C.handle, ctypes.byref(cnt), cr.data_ptr(), cc.data_ptr(),
-                                        None, 1, stream.cuda_stream)
-        assert code == 0
+        assert bsm.load().bsm_to_blocks(C.handle, ctypes.byref(cnt), cr.data_ptr(),
+                                        cc.data_ptr(), None, 1, stream.cuda_stream) == 0
         key_gpu = cr[:ncb].long() * nbk + cc[:ncb].long()   # row-major: ascending
-        # sampled blocks: a symmetric result holds (min, max); C_ji = C_ij^T
+        # the sampled blocks this leg computes; a symmetric result holds
+        # (min, max), and C_ji = C_ij^T
+        mine = np.ones(len(si), bool)
+        if rng is not None and node is None:
+            mine = (si >= rng[0]) & (si < rng[0] + rng[1]) & (sj >= rng[0]) & (sj < rng[0] + rng[1])
         lo, hi = (np.minimum(si, sj), np.maximum(si, sj)) if sym else (si, sj)
-        want = torch.from_numpy(lo.astype(np.int64) * nbk + hi).to(dev)
+        want = torch.from_numpy(lo[mine].astype(np.int64) * nbk + hi[mine]).to(dev)
         pos = torch.searchsorted(key_gpu, want).clamp(max=max(ncb - 1, 0))
-        present = (key_gpu[pos] == want).cpu().numpy() if ncb else np.zeros(len(si), bool)
+        present = ((key_gpu[pos] == want).cpu().numpy() if ncb else
+                   np.zeros(int(mine.sum()), bool))
         bsm.bsm_release_memory()  # cached pool memory is not PyTorch's to use
         _, _, cv = bsm.bsm_to_blocks(C, device=True)
-        got = cv[pos].cpu().numpy() if ncb else np.zeros_like(ref)
+        got = cv[pos].cpu().numpy() if ncb else np.zeros_like(ref[mine])
         got[~present] = 0.0
         if sym:
-            flip = si > sj
+            flip = si[mine] > sj[mine]
             got[flip] = got[flip].transpose(0, 2, 1)
         del cv, cr, cc, key_gpu
-        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-        t_num = ms[1] / 1e3
-        res = {"ms_per_product": statistics.mean(times),
+        err = float(np.linalg.norm(got - ref[mine]) / np.linalg.norm(ref[mine]))
+        recut = prec != bsm.BSM_FP64 and bs != 32
+        res = {"ms_per_product": statistics.mean(times), "steps": len(times),
                "gflops": flops / (statistics.mean(times) / 1e3) / 1e9,
-               "phase_ms": [float(x) for x in ms], "chunks": bsm.bsm_last_chunks(),
-               "computed_at_bs": 32 if recut else bs,
-               "triples": triples, "c_blocks_symbolic": ncs, "c_blocks": ncb,
-               "symbolic_structure_matches_definition":
-                   None if recut else ncs == (nc_def_upper if sym else nc_def),
-               "sampled_presence_matches_oracle": bool(np.array_equal(present, ref_nonzero)),
-               "rel_err_vs_oracle_sampled_blocks": err, "sampled_blocks": int(len(si))}
-        if prec == bsm.BSM_FP64:
+               "block_products": triples, "phase_ms": [float(x) for x in ms],
+               "chunks": bsm.bsm_last_chunks(), "computed_at_bs": 32 if recut else bs,
+               "c_blocks_symbolic": ncs, "c_blocks": ncb,
+               "symbolic_structure_matches_definition": None if recut else ncs == nc_leg,
+               "sampled_presence_matches_oracle": bool(np.array_equal(present,
+                                                                      ref_nonzero[mine])),
+               "rel_err_vs_oracle_sampled_blocks": err, "sampled_blocks": int(mine.sum())}
+        if rng is not None and node is None:
+            res["c_range"] = (f"diagonal quadtree node [{rng[0]}, {rng[0] + rng[1]})^2, "
+                              f"Morton keys [{key_range[0]}, {key_range[1]})")
+        if prec == bsm.BSM_FP64 and peak is not None and ms[1] > 0:
+            t_num = ms[1] / 1e3   # the numeric phase of the last timed product
             res["numeric_tflops"] = flops / t_num / 1e12
-            res["frac_of_fp64_peak"] = flops / t_num / 1e12 / fp64_peak
-            res["peak"] = f"{fp64_peak:.4f} TFLOP/s ({which} bf16 x 1.25/2250)"
+            res["frac_of_fp64_peak"] = flops / t_num / 1e12 / peak["tflops"]
+            res["peak"] = peak["source"]
         out[name] = res
         del C
+        bsm.bsm_release_memory()
         torch.cuda.empty_cache()
         log(f"{name}: {res}")
+    del A, U, K
+    bsm.bsm_release_memory()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_decay(args):
+    """--workload decay: the decay-type product A*A with the requested legs
+    (one JSON line)."""
+    import torch
+
+    import paper_1501_07800_gb300 as bsm
+
+    torch.cuda.set_device(0)
+    bsm.load()
+    bsm.bsm_set_timing(True)
+    npts, bs = args.points, args.bs
+    node = None
+    if args.node_side:
+        S = args.node_side
+        nbk_full = -(-(npts * 5) // bs)
+        lo_b = args.node_at if args.node_at is not None else (nbk_full // 2) // S * S
+        if S & (S - 1) or lo_b % S or lo_b >= nbk_full:
+            raise SystemExit("--node-side must be a power of two and --node-at a multiple of it")
+        node = (lo_b, min(lo_b + S, nbk_full))
+        args.sym = False
+    slices = [int(x) for x in args.slices.split(",") if x]
+    legs = [dict(name=f"split_bf16x{k}", prec=bsm.BSM_SPLIT_BF16, slices=k, sym=False)
+            for k in slices]
+    legs += [dict(name=f"split_fp8x{k}", prec=bsm.BSM_SPLIT_FP8, slices=int(k), sym=False)
+             for k in args.fp8_slices.split(",") if k]
+    if not args.no_fp64:
+        fr = None
+        if args.fp64_node_side:
+            fr = (args.fp64_node_at, args.fp64_node_side)
+        legs.append(dict(name="fp64", prec=bsm.BSM_FP64, slices=0, sym=False, range=fr,
+                         steps=1))
+    if args.sym:
+        legs.append(dict(name=f"sym_square_split_bf16x{slices[-1]}", prec=bsm.BSM_SPLIT_BF16,
+                         slices=slices[-1], sym=True))
+        if not args.no_fp64:
+            legs.append(dict(name="sym_square_fp64", prec=bsm.BSM_FP64, slices=0, sym=True,
+                             steps=1))
+    peak = fp64_peak_measured(bsm) if not args.no_fp64 else None
+    out = decay_product(bsm, torch, npts, bs, legs, args.steps, node=node, peak=peak)
     best = f"split_bf16x{max(slices)}" if slices else None
-    if best and "fp64" in out:
+    if best and "fp64" in out and out["fp64"].get("c_range") is None:
         out["split_speedup_vs_fp64"] = out["fp64"]["ms_per_product"] / out[best]["ms_per_product"]
-    if args.sym and "sym_square_fp64" in out:
+    if args.sym and "sym_square_fp64" in out and "fp64" in out:
         out["sym_square_speedup_vs_full_fp64"] = (out["fp64"]["ms_per_product"] /
                                                   out["sym_square_fp64"]["ms_per_product"])
     print(json.dumps(out), flush=True)
@@ -767,6 +934,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-decay", action="store_true",
+                    help="skip the 20,000-point decay product of the default run")
     ap.add_argument("--workload", default="random", choices=["random", "decay", "rmat"],
                     help="decay: the decay-type A*A product (separate JSON line)")
     ap.add_argument("--points", type=int, default=20000, help="decay workload: number of points")
@@ -775,6 +944,11 @@ def main():
     ap.add_argument("--slices", default="7", help="decay workload: split slice counts, e.g. 3,5,7")
     ap.add_argument("--fp8-slices", default="", help="decay workload: FP8 split slice counts")
     ap.add_argument("--no-fp64", action="store_true", help="decay workload: skip the FP64 legs")
+    ap.add_argument("--fp64-node-side", type=int, default=0,
+                    help="decay workload: the FP64 leg on one diagonal quadtree node of C of this "
+                         "side (blocks), the split legs on the whole product")
+    ap.add_argument("--fp64-node-at", type=int, default=0,
+                    help="decay workload: first block row/column of the FP64 leg's node")
     ap.add_argument("--node-side", type=int, default=0,
                     help="decay workload: compute only the C blocks of one diagonal quadtree "
                          "node of this side (blocks, a power of two)")
