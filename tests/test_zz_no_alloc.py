@@ -196,8 +196,8 @@ def test_noalloc_argument_checks():
                                                ctypes.byref(n), None) == -3
     # the binding checks, and does not convert (a conversion would allocate)
     dev = torch.device("cuda", torch.cuda.current_device())
-    seg = torch.zeros(2, dtype=torch.int32, device=dev)
-    t = torch.zeros(0, dtype=torch.int32, device=dev)
+    seg = torch.zeros(2, dtype=torch.int32, device=dev)   # one C block with no products
+    t = torch.zeros(1, dtype=torch.int32, device=dev)     # (index arrays must not be empty)
     blk = torch.zeros((1, 32, 32), dtype=torch.float64, device=dev)
     nnz = torch.zeros(1, dtype=torch.int64, device=dev)
     with pytest.raises(ValueError):
