@@ -61,6 +61,7 @@
 
 #include "bsm_batch.cuh"
 #include "bsm_ptx.cuh"
+#include "bsm_split_round.cuh"
 
 namespace {
 
@@ -412,11 +413,11 @@ __device__ __forceinline__ int32_t f32_int_exact(uint32_t b) {
 struct __align__(16) Meta {
   int64_t c;            // C block index within its product (pairs: the even sibling, or -1)
   int64_t c1;           // pairs: the odd sibling, or -1
-  uint64_t key;
   double *cv;           // the product's C blocks
   int32_t *nz;          // the product's nonzero flags
   const int *rowexp;    // the product's row / column scale exponents
   const int *colexp;
+  int32_t bi, bj;       // block row and block column of the (even) C block
   int32_t nk;
   int32_t pad[1];
 };
@@ -488,6 +489,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
   constexpr int kTeam = kTeamWarps * 32;         // threads per epilogue team
   constexpr int NB = NP * BS;                    // MMA N: output columns per item
   constexpr int BETA = Fmt<F>::BETA, TS = Fmt<F>::TSPLIT;
+  // one narrow flush: the diagonal sums' FP32 bit patterns go to shared
+  // memory as they are and are combined in wrapping 64-bit arithmetic, when
+  // the digit bounds keep the combined integer below 2^63
+  constexpr bool kNarrow64 = narrow_fits_int64<S, BETA>(narrow_max_elems<S, BETA>());
   // instruction descriptors for N = NB, 2 NB, 3 NB (one to three diagonal groups)
   constexpr uint32_t IDESC1 = F == 0 ? idesc_bf16_f32(128, NB) : idesc_e4m3_f32(128, NB);
   constexpr uint32_t IDESC2 = F == 0 ? idesc_bf16_f32(128, 2 * NB) : idesc_e4m3_f32(128, 2 * NB);
@@ -558,7 +563,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
     bool pend[C::NST] = {};
     uint32_t ppar[C::NST] = {};
     bool stop = false;
-    auto put_meta = [&](int64_t c, int64_t c1, uint64_t key, int nk, const ProdDesc *pd) -> bool {
+    auto put_meta = [&](int64_t c, int64_t c1, int32_t bi, int32_t bj, int nk,
+                        const ProdDesc *pd) -> bool {
       const int m = q % kMeta;
       int okw = 1;
       if (lane == 0) {
@@ -569,7 +575,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         } else {
           meta[m].c = c;
           meta[m].c1 = c1;
-          meta[m].key = key;
+          meta[m].bi = bi;
+          meta[m].bj = bj;
           meta[m].cv = pd ? pd->cv : nullptr;
           meta[m].nz = pd ? pd->nz : nullptr;
           meta[m].rowexp = pd ? pd->rowexp : nullptr;
@@ -596,7 +603,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
       int64_t ci = 0;
       int32_t s0 = 0, s1 = 0;
       int64_t e0 = 0, e1 = -1;  // the item's C blocks (e1: a pair's odd sibling)
-      uint64_t key = 0;
+      int32_t kbi = 0, kbj = 0;  // block row and column of the item's C block
       if (lane < n) {
         if (P.items) {
           const uint64_t it = P.items[base + lane];
@@ -608,7 +615,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         const ProdDesc *pd = &P.prods[pi];
         s0 = pd->seg[ci];
         s1 = pd->seg[ci + 1];
-        key = pd->ckeys[ci];
+        const uint64_t key = pd->ckeys[ci];
+        kbi = (int32_t)morton_compact(key >> 1);
+        kbj = (int32_t)morton_compact(key);
         if (NP == 2) {
           e0 = pd->pairc[2 * ci];
           e1 = pd->pairc[2 * ci + 1];
@@ -621,10 +630,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         const ProdDesc *pd = &P.prods[p];
         const int64_t c = __shfl_sync(0xffffffffu, e0, i);
         const int64_t c1 = __shfl_sync(0xffffffffu, e1, i);
-        const uint64_t kk = __shfl_sync(0xffffffffu, key, i);
+        const int32_t ibi = __shfl_sync(0xffffffffu, kbi, i);
+        const int32_t ibj = __shfl_sync(0xffffffffu, kbj, i);
         const int32_t k0 = __shfl_sync(0xffffffffu, s0, i);
         const int32_t nk = __shfl_sync(0xffffffffu, s1, i) - k0;
-        if (!put_meta(c, c1, kk, nk, pd)) {
+        if (!put_meta(c, c1, ibi, ibj, nk, pd)) {
           stop = true;
           break;
         }
@@ -672,7 +682,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
     // end markers: one for the MMA thread and each epilogue team (the MMA
     // thread stops at the first)
     if (!stop)
-      for (int t = 0; t < NTEAM; t++) put_meta(-1, -1, 0, -1, nullptr);
+      for (int t = 0; t < NTEAM; t++) put_meta(-1, -1, 0, 0, -1, nullptr);
     // copies still in flight must land before the CTA exits
     if (lane == 0)
       for (int st = 0; st < C::NST; st++)
@@ -810,7 +820,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
       const int64_t cblk[2] = {meta[m].c, meta[m].c1};
       double *const cvp = meta[m].cv;
       int32_t *const nzp = meta[m].nz;
-      const uint64_t ckey = meta[m].key;
+      const int64_t crow = (int64_t)meta[m].bi * BS, ccol = (int64_t)meta[m].bj * BS;
       const int *const rowexp = meta[m].rowexp, *const colexp = meta[m].colexp;
       mbar_arrive(&meta_empty[m]);
       if (nk < 0) break;  // end marker
@@ -819,8 +829,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
       // kTeam; for a pair the columns continue into the odd sibling, whose
       // block column follows), loaded here so that their latency hides behind
       // the first flush
-      const int64_t crow = (int64_t)morton_compact(ckey >> 1) * BS;
-      const int64_t ccol = (int64_t)morton_compact(ckey) * BS;
       int erow[GRP];
       int4 fcol[GRP];
 #pragma unroll
@@ -863,7 +871,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
 #pragma unroll
               for (int x = 0; x < HC; x += 4) {
                 int4 val;
-                if (!wide) {
+                if (kNarrow64 && !wide) {  // bit patterns of D + 1.5 2^23 (one flush)
+                  val = make_int4((int32_t)__float_as_uint(__uint_as_float(v[x]) + kMagicF),
+                                  (int32_t)__float_as_uint(__uint_as_float(v[x + 1]) + kMagicF),
+                                  (int32_t)__float_as_uint(__uint_as_float(v[x + 2]) + kMagicF),
+                                  (int32_t)__float_as_uint(__uint_as_float(v[x + 3]) + kMagicF));
+                } else if (!wide) {
                   val = make_int4(
                       (int32_t)(__float_as_uint(__uint_as_float(v[x]) + kMagicF) - kMagic),
                       (int32_t)(__float_as_uint(__uint_as_float(v[x + 1]) + kMagicF) - kMagic),
@@ -939,21 +952,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         for (int d = 0; d < S; d++)
           dv[d] = *reinterpret_cast<const int4 *>(tcomb + (d * BS + rr) * C::CROW + c4);
         double out[4];
+        if (kNarrow64 && !wide) {
 #pragma unroll
-        for (int x = 0; x < 4; x++) {
-          int32_t dg[S];
+          for (int x = 0; x < 4; x++) {
+            uint32_t pat[S];
 #pragma unroll
-          for (int d = 0; d < S; d++) dg[d] = x == 0 ? dv[d].x : x == 1 ? dv[d].y : x == 2 ? dv[d].z : dv[d].w;
-          int64_t hi, lo;
-          combine_digits<S, BETA, TS>(dg, hi, lo);
-          if (nfl > kf) {
-            const int64_t *fp = fold + (rr * NB + c4 + x) * 2;
-            hi += fp[0];
-            lo += fp[1];
+            for (int d = 0; d < S; d++)
+              pat[d] = (uint32_t)(x == 0 ? dv[d].x : x == 1 ? dv[d].y : x == 2 ? dv[d].z : dv[d].w);
+            const int64_t vv = narrow_combine<S, BETA>(pat);
+            const int fx = x == 0 ? fcol[i].x : x == 1 ? fcol[i].y : x == 2 ? fcol[i].z : fcol[i].w;
+            const int X = erow[i] + fx - XS;
+            if (!int64_scaled_to_double(vv, X, out[x]))  // subnormal or overflow range
+              out[x] = split_to_double_slow(vv >> TS, vv & ((1ll << TS) - 1), TS, X);
+            any[blk] |= nonzero_f64(out[x]);
           }
-          const int fx = x == 0 ? fcol[i].x : x == 1 ? fcol[i].y : x == 2 ? fcol[i].z : fcol[i].w;
-          out[x] = split_to_double<TS>(hi, lo, erow[i] + fx - XS);
-          any[blk] |= nonzero_f64(out[x]);
+        } else {
+#pragma unroll
+          for (int x = 0; x < 4; x++) {
+            int32_t dg[S];
+#pragma unroll
+            for (int d = 0; d < S; d++)
+              dg[d] = x == 0 ? dv[d].x : x == 1 ? dv[d].y : x == 2 ? dv[d].z : dv[d].w;
+            int64_t hi, lo;
+            combine_digits<S, BETA, TS>(dg, hi, lo);
+            if (nfl > kf) {
+              const int64_t *fp = fold + (rr * NB + c4 + x) * 2;
+              hi += fp[0];
+              lo += fp[1];
+            }
+            const int fx = x == 0 ? fcol[i].x : x == 1 ? fcol[i].y : x == 2 ? fcol[i].z : fcol[i].w;
+            out[x] = split_to_double<TS>(hi, lo, erow[i] + fx - XS);
+            any[blk] |= nonzero_f64(out[x]);
+          }
         }
         if (cblk[blk] >= 0) {  // a pair's absent sibling is computed as zero and dropped
           double2 *dst = reinterpret_cast<double2 *>(cvp + cblk[blk] * (int64_t)BS * BS + rr * BS + cc);
