@@ -3,9 +3,8 @@
 // batched forms and the allocation-free entry point), so that there is one
 // copy of its copy ring, bounds check, timeout unwind and epilogue.
 //
-// One CTA of 128 threads (2 x 2 warps, each a BS/2 x BS/2 warp tile of 8x8
-// DMMA tiles) sums the block products seg[c] .. seg[c+1]-1 of C block c in
-// ascending list order: each (A_IK, B_KJ) pair is staged into shared memory
+// One CTA of 128 threads sums the block products seg[c] .. seg[c+1]-1 of C
+// block c in ascending list order: each (A_IK, B_KJ) pair is staged into shared memory
 // by two 1-D bulk copies completing on an mbarrier, a kFp64Stages-deep ring
 // overlaps the next pair's copies with the current pair's DMMAs, and the sum
 // stays in registers until one store (Sec. 4.1, Fig. 3: the leaf multiply as
@@ -28,7 +27,12 @@ __device__ __forceinline__ void dmma_8x8x4(double (&c)[2], double a, double b) {
 // the CTA).  use0 / use1 count the completed phases of the two stage barriers
 // across calls.  Returns false (after recording the error) on a bad index or a
 // timed-out wait; every thread returns the same value.
-template <int BS>
+// Two forms of the arithmetic, bit-compatible with nothing but themselves:
+// MODE 0 sums on the FP64 tensor pipe (mma.sync m8n8k4, 2 x 2 warps of 8 x 8
+// tiles); MODE 1 with scalar DFMA, each thread a (BS/16) x (BS/8) tile of
+// outputs summed one k at a time in ascending order (a plain dot product of
+// fused multiply-adds).
+template <int BS, int MODE>
 __device__ bool cblock_fp64(const int32_t *__restrict__ seg, const int32_t *__restrict__ ta,
                             const int32_t *__restrict__ tb, int64_t c, int64_t na, int64_t nb,
                             const double *__restrict__ Av, const double *__restrict__ Bv,
@@ -64,6 +68,14 @@ __device__ bool cblock_fp64(const int32_t *__restrict__ seg, const int32_t *__re
   for (int i = 0; i < TW; i++)
 #pragma unroll
     for (int j = 0; j < TW; j++) acc[i][j][0] = acc[i][j][1] = 0.0;
+  // DFMA form: rows i * 16 + tid / 8, columns (tid % 8) * TC + x
+  constexpr int TR = BS / 16, TC = BS / 8;
+  double fac[TR][TC];
+#pragma unroll
+  for (int i = 0; i < TR; i++)
+#pragma unroll
+    for (int x = 0; x < TC; x++) fac[i][x] = 0.0;
+  const int frow = tid >> 3, fcol = (tid & 7) * TC;
 
   const int ar = lane >> 2, ak = lane & 3;
   bool ok = true;
@@ -84,6 +96,24 @@ __device__ bool cblock_fp64(const int32_t *__restrict__ seg, const int32_t *__re
       use1++;
     const double *sa = smem + (size_t)s * 2 * BB;
     const double *sb = sa + BB;
+    if constexpr (MODE == 1) {
+#pragma unroll 4
+      for (int kk = 0; kk < BS; kk++) {
+        double a[TR], b[TC];
+#pragma unroll
+        for (int i = 0; i < TR; i++) a[i] = sa[(i * 16 + frow) * BS + kk];
+#pragma unroll
+        for (int x = 0; x < TC; x += 2) {
+          const double2 v = *reinterpret_cast<const double2 *>(sb + kk * BS + fcol + x);
+          b[x] = v.x;
+          b[x + 1] = v.y;
+        }
+#pragma unroll
+        for (int i = 0; i < TR; i++)
+#pragma unroll
+          for (int x = 0; x < TC; x++) fac[i][x] = fma(a[i], b[x], fac[i][x]);
+      }
+    } else {
 #pragma unroll 2
     for (int kk = 0; kk < BS; kk += 4) {
       double a[TW], b[TW];
@@ -95,6 +125,7 @@ __device__ bool cblock_fp64(const int32_t *__restrict__ seg, const int32_t *__re
       for (int i = 0; i < TW; i++)
 #pragma unroll
         for (int q = 0; q < TW; q++) dmma_8x8x4(acc[i][q], a[i], b[q]);
+    }
     }
     __syncthreads();  // stage s fully consumed
     if (tid == 0 && j + kFp64Stages < nk) issue(j + kFp64Stages);
@@ -112,6 +143,16 @@ __device__ bool cblock_fp64(const int32_t *__restrict__ seg, const int32_t *__re
   }
   bool any = false;
   double *cb = Cv + c * BB;
+  if constexpr (MODE == 1) {
+#pragma unroll
+    for (int i = 0; i < TR; i++)
+#pragma unroll
+      for (int x = 0; x < TC; x += 2) {
+        any |= nonzero_f64(fac[i][x]) | nonzero_f64(fac[i][x + 1]);
+        *reinterpret_cast<double2 *>(cb + (i * 16 + frow) * BS + fcol + x) =
+            make_double2(fac[i][x], fac[i][x + 1]);
+      }
+  } else {
 #pragma unroll
   for (int i = 0; i < TW; i++)
 #pragma unroll
@@ -120,6 +161,7 @@ __device__ bool cblock_fp64(const int32_t *__restrict__ seg, const int32_t *__re
       int row = wr * WT + i * 8 + ar, col = wc * WT + q * 8 + 2 * ak;
       *reinterpret_cast<double2 *>(cb + row * BS + col) = make_double2(acc[i][q][0], acc[i][q][1]);
     }
+  }
   int nzb = __syncthreads_or(any);
   if (tid == 0) nzflag[c] = nzb;
   return true;

@@ -275,6 +275,8 @@ LastStats &last_stats();
 int64_t &launch_counter();
 inline void count_launch(int n = 1) { launch_counter() += n; }
 bool timing_enabled();
+// Arithmetic form of the FP64 numeric phase: 0 DMMA, 1 DFMA (bsm_numeric_fp64.cu).
+int fp64_mode();
 // Deferred per-phase timing of the last product on the calling thread (when
 // timing is enabled): a product records CUDA events on its stream and never
 // waits for them; bsm_last_phase_ms resolves them when it is called.

@@ -33,7 +33,7 @@ static __device__ __align__(256) int32_t g_scratch[BSM_NOALLOC_MAX_CBLOCKS + kEr
 // DMMA, bounds check and bounded waits); the nonzero flag goes to the
 // scratch array, and a C block whose CTA gave up (bad index or timed-out
 // wait) has its flag cleared, so that only the error word reports it.
-template <int BS>
+template <int BS, int MODE>
 __global__ void __launch_bounds__(128) k_products_fp64_noalloc(
     const int32_t *__restrict__ seg, const int32_t *__restrict__ ta, const int32_t *__restrict__ tb,
     int64_t nc, int64_t na, int64_t nb, const double *__restrict__ Av,
@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(128) k_products_fp64_noalloc(
   }
   __syncthreads();
   uint32_t use0 = 0, use1 = 0;
-  if (!cblock_fp64<BS>(seg, ta, tb, c, na, nb, Av, Bv, Cv, flags, err, smem, full, use0, use1) &&
+  if (!cblock_fp64<BS, MODE>(seg, ta, tb, c, na, nb, Av, Bv, Cv, flags, err, smem, full, use0,
+                             use1) &&
       threadIdx.x == 0)
     flags[c] = 0;
 }
@@ -96,13 +97,22 @@ bsm_status setup_current_device(int32_t **out) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess || !p) return cuda_status(e == cudaSuccess ? cudaErrorUnknown : e);
-    BSM_CUDA(cudaFuncSetAttribute(k_products_fp64_noalloc<16>,
+    BSM_CUDA(cudaFuncSetAttribute(k_products_fp64_noalloc<16, 0>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_bytes<16>()));
-    BSM_CUDA(cudaFuncSetAttribute(k_products_fp64_noalloc<32>,
+    BSM_CUDA(cudaFuncSetAttribute(k_products_fp64_noalloc<32, 0>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_bytes<32>()));
-    BSM_CUDA(cudaFuncSetAttribute(k_products_fp64_noalloc<64>,
+    BSM_CUDA(cudaFuncSetAttribute(k_products_fp64_noalloc<64, 0>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_bytes<64>()));
+    BSM_CUDA(cudaFuncSetAttribute(k_products_fp64_noalloc<16, 1>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_bytes<16>()));
+    BSM_CUDA(cudaFuncSetAttribute(k_products_fp64_noalloc<32, 1>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_bytes<32>()));
+    BSM_CUDA(cudaFuncSetAttribute(k_products_fp64_noalloc<64, 1>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_bytes<64>()));
     cudaFuncAttributes fa;
@@ -117,8 +127,11 @@ template <int BS>
 bsm_status launch(int64_t nc, const int32_t *seg, const int32_t *ta, const int32_t *tb,
                   const double *a, int64_t na, const double *b, int64_t nb, double *c,
                   int32_t *flags, unsigned *err, cudaStream_t s) {
-  if (nc > 0)
-    k_products_fp64_noalloc<BS><<<(unsigned)nc, 128, smem_bytes<BS>(), s>>>(
+  if (nc > 0 && fp64_mode() == 1)
+    k_products_fp64_noalloc<BS, 1><<<(unsigned)nc, 128, smem_bytes<BS>(), s>>>(
+        seg, ta, tb, nc, na, nb, a, b, c, flags, err);
+  else if (nc > 0)
+    k_products_fp64_noalloc<BS, 0><<<(unsigned)nc, 128, smem_bytes<BS>(), s>>>(
         seg, ta, tb, nc, na, nb, a, b, c, flags, err);
   return cuda_status(cudaGetLastError());
 }
