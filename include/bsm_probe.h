@@ -28,7 +28,9 @@ enum {
   BSM_PROBE_DMMA_M16N8K4 = 1,
   BSM_PROBE_DMMA_M16N8K8 = 2,
   BSM_PROBE_DMMA_M16N8K16 = 3,
-  BSM_PROBE_DFMA = 4
+  BSM_PROBE_DFMA = 4,
+  BSM_PROBE_MIXED = 5 /* half the warps DMMA m8n8k4, half DFMA (8 rounds per DMMA round):
+                         whether the two share one FP64 pipe */
 };
 
 /*

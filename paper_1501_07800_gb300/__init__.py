@@ -312,13 +312,19 @@ def bsm_info(M: Matrix):
     return nr.value, nc.value, bs.value, nb.value
 
 
-def bsm_to_blocks(M: Matrix, device: bool = False, stream=None, out=None):
+def bsm_to_blocks(M: Matrix, device: bool = False, stream=None, out=None,
+                  asynchronous: bool = False):
     """Stored blocks in row-major (I, J) order: (brow, bcol, vals).
 
     device=False: numpy arrays (the call synchronises the stream);
     device=True: torch CUDA tensors on the current device.  `out` may supply
-    preallocated (brow, bcol, vals) buffers of either kind.
+    preallocated (brow, bcol, vals) buffers of either kind.  asynchronous=True
+    (host output into page-locked `out` buffers): the copy is queued on the
+    stream and the call returns at once; synchronise the stream before reading
+    the buffers, and keep M alive until then.
     """
+    if asynchronous and (device or out is None):
+        raise ValueError("asynchronous output needs page-locked host buffers in `out`")
     lib = load()
     nr, nc, bs, n = bsm_info(M)
     if out is not None:
@@ -346,7 +352,8 @@ def bsm_to_blocks(M: Matrix, device: bool = False, stream=None, out=None):
         if out is None:
             out = (np.empty(n, np.int32), np.empty(n, np.int32), np.empty((n, bs, bs), np.float64))
         ptrs = [o.data_ptr() if hasattr(o, "data_ptr") else o.ctypes.data for o in out]
-        code = lib.bsm_to_blocks(M.handle, ctypes.byref(cnt), *ptrs, 0, _stream_ptr(stream))
+        code = lib.bsm_to_blocks(M.handle, ctypes.byref(cnt), *ptrs, 2 if asynchronous else 0,
+                                 _stream_ptr(stream))
     _check(code, "bsm_to_blocks")
     return out
 
@@ -457,6 +464,7 @@ BSM_PROBE_DMMA_M16N8K4 = 1
 BSM_PROBE_DMMA_M16N8K8 = 2
 BSM_PROBE_DMMA_M16N8K16 = 3
 BSM_PROBE_DFMA = 4
+BSM_PROBE_MIXED = 5
 
 
 def bsm_probe_fp64(kind: int, iters: int, stream=None):

@@ -117,6 +117,37 @@ __global__ void __launch_bounds__(256) k_probe_dfma(const double *__restrict__ i
   out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// Even warps DMMA m8n8k4, odd warps DFMA (`ratio` DFMA rounds per DMMA
+// round): whether the two share one FP64 pipe.
+__global__ void __launch_bounds__(256) k_probe_mixed(const double *__restrict__ in, int64_t iters,
+                                                     int ratio, double *__restrict__ out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double s = 0.0;
+  if ((warp & 1) == 0) {
+    double a[1] = {in[lane]}, b[1] = {in[32 + lane]}, c[kChains][2];
+#pragma unroll
+    for (int q = 0; q < kChains; q++) c[q][0] = c[q][1] = 0.0;
+    for (int64_t it = 0; it < iters; it++) {
+#pragma unroll
+      for (int q = 0; q < kChains; q++) Dmma<0>::mma(c[q], a, b);
+    }
+#pragma unroll
+    for (int q = 0; q < kChains; q++) s += c[q][0] + c[q][1];
+  } else {
+    const double x = in[lane], y = in[32 + lane];
+    double c[kChains];
+#pragma unroll
+    for (int q = 0; q < kChains; q++) c[q] = in[q];
+    for (int64_t it = 0; it < iters * ratio; it++) {
+#pragma unroll
+      for (int q = 0; q < kChains; q++) c[q] = fma(x, c[q], y);
+    }
+#pragma unroll
+    for (int q = 0; q < kChains; q++) s += c[q];
+  }
+  out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // One CTA per SM: warp 0 allocates TMEM; thread 0 issues `iters` groups of
 // four MMAs (M = 128, N = n) alternating between two accumulators, then
 // commits and waits (bounded) for the tensor core to finish.
@@ -251,7 +282,7 @@ int64_t fp64_grid(K kernel) {
 
 extern "C" bsm_status bsm_probe_fp64(int kind, int64_t iters, double *flops, float *ms,
                                      void *stream) {
-  if (kind < BSM_PROBE_DMMA_M8N8K4 || kind > BSM_PROBE_DFMA || iters < 1 || !flops || !ms)
+  if (kind < BSM_PROBE_DMMA_M8N8K4 || kind > BSM_PROBE_MIXED || iters < 1 || !flops || !ms)
     return BSM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   double *in = nullptr, *out = nullptr;
@@ -265,8 +296,10 @@ extern "C" bsm_status bsm_probe_fp64(int kind, int64_t iters, double *flops, flo
     case BSM_PROBE_DMMA_M16N8K4: grid = fp64_grid(k_probe_dmma<1>); per_thread = Dmma<1>::FLOPS / 32; break;
     case BSM_PROBE_DMMA_M16N8K8: grid = fp64_grid(k_probe_dmma<2>); per_thread = Dmma<2>::FLOPS / 32; break;
     case BSM_PROBE_DMMA_M16N8K16: grid = fp64_grid(k_probe_dmma<3>); per_thread = Dmma<3>::FLOPS / 32; break;
-    default: grid = fp64_grid(k_probe_dfma); per_thread = 2; break;
+    case BSM_PROBE_DFMA: grid = fp64_grid(k_probe_dfma); per_thread = 2; break;
+    default: grid = fp64_grid(k_probe_mixed); break;
   }
+  constexpr int kRatio = 8;  // DFMA rounds per DMMA round in the mixed probe
   if (st == BSM_OK) st = dev_alloc((void **)&out, (size_t)grid * 256 * sizeof(double), s);
   if (st == BSM_OK) {
     count_launch();
@@ -277,12 +310,15 @@ extern "C" bsm_status bsm_probe_fp64(int kind, int64_t iters, double *flops, flo
             case BSM_PROBE_DMMA_M16N8K4: k_probe_dmma<1><<<(unsigned)grid, 256, 0, s>>>(in, iters, out); break;
             case BSM_PROBE_DMMA_M16N8K8: k_probe_dmma<2><<<(unsigned)grid, 256, 0, s>>>(in, iters, out); break;
             case BSM_PROBE_DMMA_M16N8K16: k_probe_dmma<3><<<(unsigned)grid, 256, 0, s>>>(in, iters, out); break;
-            default: k_probe_dfma<<<(unsigned)grid, 256, 0, s>>>(in, iters, out); break;
+            case BSM_PROBE_DFMA: k_probe_dfma<<<(unsigned)grid, 256, 0, s>>>(in, iters, out); break;
+            default: k_probe_mixed<<<(unsigned)grid, 256, 0, s>>>(in, iters, kRatio, out); break;
           }
         },
         nullptr, ms, s);
   }
-  *flops = (double)grid * 256 * (double)iters * kChains * (double)per_thread;
+  *flops = kind == BSM_PROBE_MIXED
+               ? (double)grid * 128 * (double)iters * kChains * (Dmma<0>::FLOPS / 32 + 2.0 * kRatio)
+               : (double)grid * 256 * (double)iters * kChains * (double)per_thread;
   dev_free(out, s);
   dev_free(in, s);
   return st;
