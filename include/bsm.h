@@ -291,7 +291,14 @@ bsm_status bsm_multiply_batched(int n, const bsm_matrix *A, const bsm_matrix *B,
  *   vals        float64[capacity][bs][bs] or NULL
  *   on_device   0: host buffers (the call synchronises `stream`);
  *               1: device buffers of the handle's device (vals 16-byte
- *               aligned, brow/bcol 4-byte aligned)
+ *               aligned, brow/bcol 4-byte aligned);
+ *               2: page-locked, device-mapped host buffers (cudaHostAlloc /
+ *               cudaHostRegister with mapping; vals 16-byte aligned), written
+ *               asynchronously: the call returns with the copy queued on
+ *               `stream`, so it can overlap later work on other streams; the
+ *               caller synchronises `stream` before reading the buffers and
+ *               keeps M alive until then (INVALID_ARG if a buffer is not
+ *               such memory)
  * With all three buffers NULL the call only reports the block count.
  * Errors: INVALID_ARG, BUFFER_TOO_SMALL (count still reported), OOM, CUDA.
  */

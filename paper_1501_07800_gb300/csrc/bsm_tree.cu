@@ -365,7 +365,7 @@ extern "C" bsm_status bsm_build(int64_t nrows, int64_t ncols, int bs, int64_t nb
 extern "C" bsm_status bsm_to_blocks(bsm_matrix M, int64_t *nblk_inout, int32_t *brow,
                                     int32_t *bcol, double *vals, int on_device, void *stream) {
   NvtxRange range("bsm_to_blocks");
-  if (!M || !nblk_inout || (on_device != 0 && on_device != 1)) return BSM_ERR_INVALID_ARG;
+  if (!M || !nblk_inout || on_device < 0 || on_device > 2) return BSM_ERR_INVALID_ARG;
   int64_t cap = *nblk_inout;
   *nblk_inout = M->nblk;
   if (!brow && !bcol && !vals) return BSM_OK;
@@ -374,6 +374,30 @@ extern "C" bsm_status bsm_to_blocks(bsm_matrix M, int64_t *nblk_inout, int32_t *
   // device outputs are written with 16-byte vector stores
   if (on_device && (((uintptr_t)vals & 15) || ((uintptr_t)brow & 3) || ((uintptr_t)bcol & 3)))
     return BSM_ERR_INVALID_ARG;
+  // host output into pinned (page-locked, device-mapped) buffers: the gather
+  // and coordinate kernels write straight into them over the host link, with
+  // no staging copy
+  auto mapped = [](void *p, uintptr_t align) -> void * {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return (uintptr_t)a.devicePointer % align ? nullptr : a.devicePointer;
+  };
+  double *mv = nullptr;
+  int32_t *mr = nullptr, *mc = nullptr;
+  bool all_mapped = false;
+  if (on_device != 1) {
+    mv = (double *)mapped(vals, 16);
+    mr = (int32_t *)mapped(brow, 4);
+    mc = (int32_t *)mapped(bcol, 4);
+    all_mapped = (!vals || mv) && (!brow || mr) && (!bcol || mc);
+  }
+  // asynchronous host output needs page-locked buffers (checked before any work)
+  if (on_device == 2 && !all_mapped) return BSM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   int64_t n = M->nblk;
   int bs = M->bs;
@@ -399,7 +423,7 @@ extern "C" bsm_status bsm_to_blocks(bsm_matrix M, int64_t *nblk_inout, int32_t *
     cleanup();
     return st;
   }
-  if (on_device) {
+  if (on_device == 1) {
     count_launch();
     k_rowmajor_coords<<<nblocks_for(n, 256), 256, 0, s>>>(rms, 0, n, brow, bcol);
     if (vals) launch_gather_blocks(M->vals, sidx, vals, n, bs, s);
@@ -407,28 +431,14 @@ extern "C" bsm_status bsm_to_blocks(bsm_matrix M, int64_t *nblk_inout, int32_t *
     cleanup();
     return st;
   }
-  // host output into pinned (page-locked, device-mapped) buffers: the gather
-  // and coordinate kernels write straight into them over the host link, with
-  // no staging copy
-  auto mapped = [](void *p, uintptr_t align) -> void * {
-    if (!p) return nullptr;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
-    return (uintptr_t)a.devicePointer % align ? nullptr : a.devicePointer;
-  };
-  double *mv = (double *)mapped(vals, 16);
-  int32_t *mr = (int32_t *)mapped(brow, 4), *mc = (int32_t *)mapped(bcol, 4);
-  if ((!vals || mv) && (!brow || mr) && (!bcol || mc)) {
+  if (all_mapped) {
     if (brow || bcol) {
       count_launch();
       k_rowmajor_coords<<<nblocks_for(n, 256), 256, 0, s>>>(rms, 0, n, mr, mc);
     }
     if (vals) launch_gather_blocks(M->vals, sidx, mv, n, bs, s);
-    cudaError_t e = cudaStreamSynchronize(s);
+    // asynchronous: the temporaries are freed stream-ordered, after the gather
+    cudaError_t e = on_device == 2 ? cudaSuccess : cudaStreamSynchronize(s);
     cleanup();
     return cuda_status(e == cudaSuccess ? cudaGetLastError() : e);
   }

@@ -63,6 +63,29 @@ def test_to_blocks_into_pinned_host_buffers():
     assert np.array_equal(r2, E.brow) and np.array_equal(v2, E.vals)
 
 
+def test_to_blocks_asynchronous_into_pinned_buffers():
+    """on_device = 2: the copy into page-locked buffers is queued on the stream
+    and the call returns at once; after a synchronisation the buffers equal the
+    synchronous result.  Pageable buffers are refused before any work."""
+    import torch
+    A = synth.random_blocks(3000, 32, 0.05, 18)
+    M = to_bsm(A)
+    n = M.nblk
+    s = torch.cuda.Stream()
+    pinned = (torch.empty(n, dtype=torch.int32, pin_memory=True).numpy(),
+              torch.empty(n, dtype=torch.int32, pin_memory=True).numpy(),
+              torch.empty((n, 32, 32), dtype=torch.float64, pin_memory=True).numpy())
+    bsm.bsm_to_blocks(M, out=pinned, stream=s, asynchronous=True)
+    s.synchronize()
+    E = A.sorted()
+    assert np.array_equal(pinned[0], E.brow) and np.array_equal(pinned[1], E.bcol)
+    assert np.array_equal(pinned[2], E.vals)
+    with pytest.raises(bsm.BsmError) as e:
+        bsm.bsm_to_blocks(M, out=(np.empty(n, np.int32), np.empty(n, np.int32),
+                                  np.empty((n, 32, 32))), asynchronous=True)
+    assert e.value.name == "BSM_ERR_INVALID_ARG"
+
+
 def test_build_drops_zero_blocks_and_rejects_bad_input():
     bs = 16
     A = synth.random_blocks(200, bs, 0.3, 6)
