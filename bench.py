@@ -77,30 +77,43 @@ def ClockSampler(dev: int):
 
 
 def fp64_peak_measured(bsm, seconds: float = 1.0) -> dict:
-    """The FP64 tensor-pipe peak measured now by the library's probe
-    (bsm_probe_fp64, mma.sync m8n8k4 -- the FP64 kernel's instruction -- on
-    every SM, best of two launches of about a second), with its clock."""
+    """The chip's FP64 peak measured now by the library's probe
+    (bsm_probe_fp64 on every SM, best of two launches of about a second each
+    for scalar DFMA -- the FP64 kernel's arithmetic -- and for the FP64 tensor
+    path, mma.sync m8n8k4), with its clock."""
     from paper_1501_07800_gb300 import probe
     p = probe.fp64_peak(seconds)
     clk = p["clocks"]
-    return {"tflops": p["tflops"], "clocks": clk, "runs": p["runs"],
-            "source": (f"measured in this run by bsm_probe_fp64 (DMMA m8n8k4, every SM; "
-                       f"paper_1501_07800_gb300/csrc/bsm_probe.cu): {p['tflops']:.4f} TFLOP/s "
-                       f"at median SM clock {clk.get('sm_mhz')} MHz")}
+    return {"tflops": p["tflops"], "clocks": clk, "runs": p["runs"], "kind": p["kind"],
+            "dmma_tflops": p["dmma"], "dfma_tflops": p["dfma"],
+            "source": (f"measured in this run by bsm_probe_fp64 "
+                       f"(paper_1501_07800_gb300/csrc/bsm_probe.cu, every SM): FP64 peak "
+                       f"{p['tflops']:.4f} TFLOP/s ({p['kind']}; DFMA {p['dfma']:.4f}, DMMA "
+                       f"m8n8k4 {p['dmma']:.4f}) at median SM clock {clk.get('sm_mhz')} MHz")}
 
 
 # ------------------------------------------------------------ traffic table
-def recorded_traffic(kernel: str, src: str):
+def source_sha(srcs) -> str:
+    h = hashlib.sha256()
+    for src in srcs:
+        h.update(open(os.path.join(ROOT, src), "rb").read())
+    return h.hexdigest()[:16]
+
+
+FP64_SOURCES = ("paper_1501_07800_gb300/csrc/bsm_numeric_fp64.cu",
+                "paper_1501_07800_gb300/csrc/bsm_fp64_body.cuh")
+
+
+def recorded_traffic(kernel: str, srcs):
     """Per-launch DRAM bytes from an ncu capture, valid only while the kernel's
-    source file is unchanged since the capture (else None)."""
+    source files are unchanged since the capture (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(kernel)
     if not d:
         return None
-    sha = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
-    return d.get("bytes_per_launch") if d.get("src_sha") == sha else None
+    return d.get("bytes_per_launch") if d.get("src_sha") == source_sha(srcs) else None
 
 
 # ------------------------------------------------------------ CPU baseline
@@ -362,7 +375,7 @@ def run_gpu(args):
     peaks, which = measured_peaks()
     t_num = statistics.mean(numeric_ms) / 1e3
     if prec == bsm.BSM_FP64:
-        roofline = {"bound": "tensor", "kernel": "k_numeric_fp64 (DMMA f64)",
+        roofline = {"bound": "alu", "kernel": "k_numeric_fp64 (FP64 DFMA)",
                     "achieved": flops / t_num / 1e12, "peak": peak["tflops"],
                     "unit": "TFLOP/s", "frac": flops / t_num / 1e12 / peak["tflops"],
                     "peak_source": peak["source"], "peak_runs_tflops": peak["runs"],
@@ -374,8 +387,7 @@ def run_gpu(args):
                     "unit": "TFLOP/s",
                     "frac": flops * 28 / t_num / 1e12 / peaks["bf16_tflops_sustained"],
                     "peak_source": f"{which} bf16 sustained"}
-    roofline["traffic"] = recorded_traffic("k_numeric_fp64",
-                                           "paper_1501_07800_gb300/csrc/bsm_numeric_fp64.cu")
+    roofline["traffic"] = recorded_traffic("k_numeric_fp64", FP64_SOURCES)
 
     # split-precision mode on the same inputs, same timing protocol
     split = None
@@ -400,12 +412,13 @@ def run_gpu(args):
 
     # end to end through the public API with host buffers (pinned)
     if not args.no_e2e:
-        e2e = run_e2e(bsm, torch, A, B, prec, max(1, min(args.steps, 3)))
+        e2e = run_e2e(bsm, torch, A, B, prec, max(2, min(args.steps, 5)))
         e2e_v = allsum(flops * e2e["steps"]) / allmax(e2e["seconds"]) / 1e9
         if line is not None:
             line["e2e"] = {"value": e2e_v, "unit": "GFLOP/s",
                            "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
-                           "ms_per_step": 1e3 * e2e["seconds"] / e2e["steps"]}
+                           "ms_per_step": 1e3 * e2e["seconds"] / e2e["steps"],
+                           "steps": e2e["steps"], "overlap": e2e["overlap"]}
     if line is not None and not args.no_batched:
         line["batched"] = run_batched(bsm, torch, args, stream)
     if line is not None and world == 1 and not args.no_decay:
@@ -851,6 +864,214 @@ def run_decay(args):
     return 0
 
 
+def run_decay_nodes(args):
+    """--workload decay --all-nodes: the decay-type product A*A over the whole
+    of C, one quadtree node of C (side --node-side blocks, row by row) at a
+    time, for products whose operands and C do not fit on one GPU together
+    (80,000 points, bs 64: A 171 GB, C about 927 GB).  Per node, only the
+    operand blocks with a row or a column in the node's rows and columns are
+    generated on the device; each split mode computes the node's C blocks
+    (bsm_multiply_range, one product per node and mode, timed with CUDA
+    events, the first node after a warm-up), and FP64 runs on --fp64-nodes
+    nodes (evenly spaced along the diagonal), its time for the whole product
+    extrapolated by the block-product ratio.  Errors: against the oracle on a
+    grid of 38 block rows x 38 block columns drawn uniformly (every grid
+    position in C's structure), from the operand blocks of those rows and
+    columns."""
+    import ctypes
+
+    import torch
+
+    import oracle
+    import paper_1501_07800_gb300 as bsm
+    from paper_1501_07800_gb300 import shard as sh
+    from synth import device as sd
+
+    torch.cuda.set_device(0)
+    bsm.load()
+    bsm.bsm_set_timing(True)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    npts, bs, S = args.points, args.bs, args.node_side or 512
+    seed = synth.BASE_SEED + 2
+    n = npts * 5
+    nbk = -(-n // bs)
+    pts = synth.decay_points(npts, seed)
+    modes = [(f"split_bf16x{k}", bsm.BSM_SPLIT_BF16, int(k)) for k in args.slices.split(",") if k]
+    modes += [(f"split_fp8x{k}", bsm.BSM_SPLIT_FP8, int(k)) for k in args.fp8_slices.split(",") if k]
+    side_nodes = -(-nbk // S)
+    nodes = [(i * S, j * S) for i in range(side_nodes) for j in range(side_nodes)]
+    if args.max_nodes:
+        nodes = nodes[:args.max_nodes]
+    diag = [(i * S, i * S) for i in range(side_nodes)]
+    nf = max(0, args.fp64_nodes)
+    fp64_nodes = set(diag[(k * len(diag)) // (nf + 1) + len(diag) // (2 * (nf + 1))]
+                     for k in range(nf)) if nf else set()
+    peak = fp64_peak_measured(bsm) if nf else None
+
+    # the oracle on a grid of block rows x block columns drawn uniformly
+    g = torch.Generator(device="cpu").manual_seed(synth.BASE_SEED)
+    grows = torch.sort(torch.randperm(nbk, generator=g)[:38]).values
+    gcols = torch.sort(torch.randperm(nbk, generator=g)[:38]).values
+    rmask = torch.zeros(nbk, dtype=torch.bool, device=dev)
+    cmask = torch.zeros(nbk, dtype=torch.bool, device=dev)
+    rmask[grows.to(dev)] = True
+    cmask[gcols.to(dev)] = True
+    t0 = time.time()
+    _, r, c, v = sd.decay(npts, bs, seed, dev, keep=(rmask, cmask), points=pts)
+    lk, rk = rmask[r.long()], cmask[c.long()]
+    left = synth.BlockCOO(n, n, bs, r[lk].cpu().numpy(), c[lk].cpu().numpy(), v[lk].cpu().numpy())
+    right = synth.BlockCOO(n, n, bs, r[rk].cpu().numpy(), c[rk].cpu().numpy(), v[rk].cpu().numpy())
+    del r, c, v, lk, rk
+    torch.cuda.empty_cache()
+    L = oracle.common_depth(left, right)
+    tl, tr = oracle.tree(left, L), oracle.tree(right, L)
+    gi, gj = np.meshgrid(grows.numpy(), gcols.numpy(), indexing="ij")
+    gi, gj = gi.ravel(), gj.ravel()
+    # grid positions in C's structure: some K has A_iK and A_Kj stored
+    pa = {}
+    for i, k in zip(left.brow, left.bcol):
+        pa.setdefault(int(i), set()).add(int(k))
+    pb = {}
+    for k, j in zip(right.brow, right.bcol):
+        pb.setdefault(int(j), set()).add(int(k))
+    inc = np.array([bool(pa.get(int(i), set()) & pb.get(int(j), set())) for i, j in zip(gi, gj)])
+    gi, gj = gi[inc], gj[inc]
+    nprod_grid = sum(len(pa[int(i)] & pb[int(j)]) for i, j in zip(gi, gj))
+    t1 = time.perf_counter()
+    refs = [oracle.block_product(tl, tr, int(i), int(j)) for i, j in zip(gi, gj)]
+    oracle_s = time.perf_counter() - t1
+    ref = np.stack([x[1] for x in refs])
+    ref_nz = np.array([bool(np.any(x[1] != 0.0)) for x in refs])
+    del tl, tr, left, right, refs
+    gkey = gi.astype(np.int64) * nbk + gj
+    log(f"decay nodes: n={n}, {len(nodes)} nodes of side {S}; oracle on {len(gi)} grid blocks "
+        f"{oracle_s:.1f} s (setup {time.time() - t0:.1f} s)")
+
+    acc = {name: {"ms": 0.0, "num": 0.0, "den": 0.0, "presence_ok": True, "blocks": 0,
+                  "c_blocks": 0} for name, _, _ in modes}
+    fp64 = {"ms": 0.0, "products": 0, "nodes": [], "num": 0.0, "den": 0.0, "numeric_ms": 0.0}
+    total_products, gen_s, t_all = 0, 0.0, time.time()
+    for ni, (r0, c0) in enumerate(nodes):
+        tg = time.time()
+        rm = torch.zeros(nbk, dtype=torch.bool, device=dev)
+        cm = torch.zeros(nbk, dtype=torch.bool, device=dev)
+        rm[r0:r0 + S] = True
+        cm[c0:c0 + S] = True
+        _, r, c, v = sd.decay(npts, bs, seed, dev, keep=(rm, cm), points=pts)
+        Ar = bsm.bsm_build(n, n, bs, r, c, v)
+        del r, c, v
+        # block products of the node by definition, from the stored blocks
+        nb_ = Ar.nblk
+        sr = torch.empty(max(nb_, 1), dtype=torch.int32, device=dev)
+        sc = torch.empty(max(nb_, 1), dtype=torch.int32, device=dev)
+        cnt = ctypes.c_int64(nb_)
+        assert bsm.load().bsm_to_blocks(Ar.handle, ctypes.byref(cnt), sr.data_ptr(),
+                                        sc.data_ptr(), None, 1, stream.cuda_stream) == 0
+        sr, sc = sr[:nb_].long(), sc[:nb_].long()
+        lsel, rsel = (sr >= r0) & (sr < r0 + S), (sc >= c0) & (sc < c0 + S)
+        Pl = torch.zeros((S, nbk), dtype=torch.float32, device=dev)
+        Pr = torch.zeros((nbk, S), dtype=torch.float32, device=dev)
+        Pl[sr[lsel] - r0, sc[lsel]] = 1.0
+        Pr[sr[rsel], sc[rsel] - c0] = 1.0
+        node_products = int((Pl @ Pr).sum(dtype=torch.float64).item())
+        del Pl, Pr, sr, sc, lsel, rsel
+        total_products += node_products
+        torch.cuda.synchronize()
+        gen_s += time.time() - tg
+        klo = int(sh.morton(r0, c0))
+        kr = (klo, klo + S * S)
+        sel = (gi >= r0) & (gi < r0 + S) & (gj >= c0) & (gj < c0 + S)
+        todo = [(name, prec, sl) for name, prec, sl in modes]
+        if (r0, c0) in fp64_nodes:
+            todo.append(("fp64", bsm.BSM_FP64, 0))
+        for name, prec, sl in todo:
+            reps = 2 if ni == 0 and prec != bsm.BSM_FP64 else 1   # first node: a warm-up run
+            for k in range(reps):
+                C = None
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                C = bsm.bsm_multiply_range(Ar, Ar, kr[0], kr[1], prec=prec, slices=sl)
+                e1.record(stream)
+                torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            ncb = bsm.bsm_info(C)[3]
+            nerr = dden = 0.0
+            pres_ok = True
+            if sel.any() and ncb:
+                bsm.bsm_release_memory()
+                cr, cc, cv = bsm.bsm_to_blocks(C, device=True)
+                ck = cr.long() * nbk + cc.long()
+                want = torch.from_numpy(gkey[sel]).to(dev)
+                pos = torch.searchsorted(ck, want).clamp(max=ncb - 1)
+                present = (ck[pos] == want).cpu().numpy()
+                got = cv[pos].cpu().numpy()
+                got[~present] = 0.0
+                nerr = float(np.sum((got - ref[sel]) ** 2))
+                dden = float(np.sum(ref[sel] ** 2))
+                pres_ok = bool(np.array_equal(present, ref_nz[sel]))
+                del cr, cc, cv, ck
+            del C
+            if name == "fp64":
+                fp64["ms"] += ms
+                fp64["products"] += node_products
+                fp64["nodes"].append([r0, c0])
+                fp64["numeric_ms"] += float(bsm.bsm_last_phase_ms()[0][1])
+                fp64["num"] += nerr
+                fp64["den"] += dden
+            else:
+                a = acc[name]
+                a["ms"] += ms
+                a["num"] += nerr
+                a["den"] += dden
+                a["presence_ok"] &= pres_ok
+                a["blocks"] += int(sel.sum())
+                a["c_blocks"] += ncb
+        del Ar
+        bsm.bsm_release_memory()
+        torch.cuda.empty_cache()
+        if ni % 10 == 0:
+            log(f"node {ni + 1}/{len(nodes)} at ({r0}, {c0}): {node_products} block products; "
+                f"{time.time() - t_all:.0f} s")
+    flops_total = metrics.block_flops(bs, total_products)
+    out = {"workload": f"decay A*A, {npts} points (N={n}), bs {bs}, whole product node by node "
+                       f"({len(nodes)} quadtree nodes of C of side {S} blocks)",
+           "nodes": len(nodes), "block_products": total_products,
+           "useful_pflop": flops_total / 1e15, "operand_generation_s": gen_s,
+           "grid": {"rows": 38, "cols": 38, "blocks_in_c": int(len(gi)),
+                    "exactly_zero": int((~ref_nz).sum()), "oracle_s": oracle_s,
+                    "oracle_block_products": nprod_grid}}
+    for name, _, _ in modes:
+        a = acc[name]
+        out[name] = {"seconds": a["ms"] / 1e3,
+                     "useful_tflops": flops_total / (a["ms"] / 1e3) / 1e12,
+                     "rel_err_vs_oracle_grid": (a["num"] / a["den"]) ** 0.5 if a["den"] else None,
+                     "grid_blocks_compared": a["blocks"],
+                     "grid_presence_matches_oracle": a["presence_ok"], "c_blocks": a["c_blocks"]}
+    if fp64["products"]:
+        rate = metrics.block_flops(bs, fp64["products"]) / (fp64["ms"] / 1e3)
+        out["fp64"] = {"nodes": fp64["nodes"], "seconds_measured": fp64["ms"] / 1e3,
+                       "block_products_measured": fp64["products"],
+                       "useful_tflops": rate / 1e12,
+                       "numeric_frac_of_fp64_peak": metrics.block_flops(bs, fp64["products"]) /
+                       (fp64["numeric_ms"] / 1e3) / 1e12 / peak["tflops"],
+                       "peak": peak["source"],
+                       "whole_product_s_extrapolated": flops_total / rate,
+                       "label": "extrapolated by the block-product ratio",
+                       "rel_err_vs_oracle_grid": (fp64["num"] / fp64["den"]) ** 0.5
+                       if fp64["den"] else None}
+        for name, _, _ in modes:
+            out[name]["speedup_vs_fp64_extrapolated"] = (out["fp64"]["whole_product_s_extrapolated"]
+                                                        / out[name]["seconds"])
+    oracle_rate = metrics.block_flops(bs, nprod_grid) / oracle_s
+    out["oracle_extrapolated"] = {"single_thread_s": flops_total / oracle_rate,
+                                  "gflops": oracle_rate / 1e9, "label": "extrapolated",
+                                  "how": "the oracle's time on the grid blocks, scaled by the "
+                                         "flop ratio"}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_rmat(args):
     """Locality sweep on R-MAT graph matrices (N = 8192, 5 edge draws per row,
     b = c = d = (1 - a) / 3): per-level multiply-task counts of A*A (the
@@ -886,8 +1107,12 @@ def run_rmat(args):
 
 
 def run_e2e(bsm, torch, A, B, prec, steps):
-    """Host COO in pinned memory -> bsm_build x2 -> bsm_multiply -> bsm_to_blocks
-    into pinned host buffers, every step."""
+    """Host COO in pinned memory -> bsm_build x2 -> bsm_multiply -> C's blocks
+    into pinned host buffers, every step, through the public API.  Consecutive
+    steps alternate between two streams and two sets of result buffers: step
+    i's download of C over the host link (queued with bsm_to_blocks'
+    asynchronous mode) overlaps step i+1's upload and product.  The timed
+    region ends when the last download has landed."""
     def pinned(a: np.ndarray) -> np.ndarray:
         t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
         t.numpy()[...] = a
@@ -896,31 +1121,50 @@ def run_e2e(bsm, torch, A, B, prec, steps):
     pa = [pinned(x) for x in (A.brow, A.bcol, A.vals)]
     pb = [pinned(x) for x in (B.brow, B.bcol, B.vals)]
     h2d = sum(x.nbytes for x in pa + pb)
-    out = None
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    bufs = [None, None]       # the caller's result buffers (pinned), one set per stream
+    pending = [None, None]    # (C, event): C stays alive until its download has landed
 
-    def step():
-        nonlocal out
-        ga = bsm.bsm_build(A.nrows, A.ncols, A.bs, *pa)
-        gb = bsm.bsm_build(B.nrows, B.ncols, B.bs, *pb)
-        C = bsm.bsm_multiply(ga, gb, prec=prec)
+    def step(i):
+        k = i % 2
+        s = streams[k]
+        if pending[k] is not None:   # this buffer set's previous download
+            pending[k][1].synchronize()
+            pending[k] = None
+        ga = bsm.bsm_build(A.nrows, A.ncols, A.bs, *pa, stream=s)
+        gb = bsm.bsm_build(B.nrows, B.ncols, B.bs, *pb, stream=s)
+        C = bsm.bsm_multiply(ga, gb, prec=prec, stream=s)
+        del ga, gb
         n = C.nblk
-        if out is None or out[0].shape[0] < n:
-            # the caller's result buffers (pinned), allocated once outside the timing
-            out = (torch.empty(n, dtype=torch.int32, pin_memory=True).numpy(),
-                   torch.empty(n, dtype=torch.int32, pin_memory=True).numpy(),
-                   torch.empty((n, A.bs, A.bs), dtype=torch.float64, pin_memory=True).numpy())
-        bsm.bsm_to_blocks(C, out=out)
+        if bufs[k] is None or bufs[k][0].shape[0] < n:
+            # allocated in the untimed warm-up steps (one per buffer set)
+            bufs[k] = (torch.empty(n, dtype=torch.int32, pin_memory=True).numpy(),
+                       torch.empty(n, dtype=torch.int32, pin_memory=True).numpy(),
+                       torch.empty((n, A.bs, A.bs), dtype=torch.float64,
+                                   pin_memory=True).numpy())
+        bsm.bsm_to_blocks(C, out=bufs[k], stream=s, asynchronous=True)
+        ev = torch.cuda.Event()
+        ev.record(s)
+        pending[k] = (C, ev)
         return n * (8 + 8 * A.bs * A.bs)
 
-    step()  # untimed: sizes and pins the result buffers
+    step(0)   # untimed: sizes and pins both buffer sets
+    step(1)
+    for p in pending:
+        p[1].synchronize()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     d2h = 0
-    for _ in range(steps):
-        d2h = step()
-    torch.cuda.synchronize()
+    for i in range(steps):
+        d2h = step(i)
+    for p in pending:
+        if p is not None:
+            p[1].synchronize()
     dt = time.perf_counter() - t0
-    return {"seconds": dt, "steps": steps, "h2d": h2d, "d2h": d2h}
+    pending[0] = pending[1] = None
+    return {"seconds": dt, "steps": steps, "h2d": h2d, "d2h": d2h,
+            "overlap": "two streams: each step's download overlaps the next step's upload and "
+                       "product"}
 
 
 def main():
@@ -954,6 +1198,13 @@ def main():
                          "node of this side (blocks, a power of two)")
     ap.add_argument("--node-at", type=int, default=None,
                     help="decay workload: first block row/column of that node")
+    ap.add_argument("--all-nodes", action="store_true",
+                    help="decay workload: the whole product node by node (side --node-side, "
+                         "default 512 blocks)")
+    ap.add_argument("--fp64-nodes", type=int, default=1,
+                    help="decay --all-nodes: FP64 on this many diagonal nodes")
+    ap.add_argument("--max-nodes", type=int, default=0,
+                    help="decay --all-nodes: stop after this many nodes (testing)")
     ap.add_argument("--sym", action="store_true",
                     help="decay workload: also the symmetric square from the upper triangle")
     ap.add_argument("--shard", action="store_true",
@@ -978,6 +1229,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "decay" and args.all_nodes:
+        return run_decay_nodes(args)
     if args.workload == "decay":
         return run_decay(args)
     if args.workload == "rmat":

@@ -80,19 +80,23 @@ def to_host(n: int, bs: int, brow, bcol, vals) -> BlockCOO:
 
 def decay(npoints: int, bs: int, seed: int, device, nfun: int = 5, alpha: float = 0.5,
           cutoff: float = 1e-6, density: float = 0.1, chunk_blocks: int | None = None,
-          cross: tuple[int, int] | None = None):
+          cross: tuple[int, int] | None = None, keep=None, points=None):
     """Device tensors (n, brow, bcol, vals) of the decay-type matrix of
     synth.decay: points from synth.decay_points (host, recursive bisection
     order), blocks whose bounding boxes come within the cutoff radius, entries
     s_ij exp(-alpha r_ij) below `cutoff` set to zero.  Entries may differ from
     the numpy generator in the last bit (exp on the device).  cross=(lo, hi):
     only the blocks whose block row or block column lies in [lo, hi) (the
-    operands of the C blocks [lo, hi)^2 of A*A)."""
+    operands of the C blocks [lo, hi)^2 of A*A).  keep=(row_mask, col_mask),
+    boolean device tensors over the block rows / columns: only the blocks
+    whose row is in row_mask or whose column is in col_mask (the operands of
+    the C blocks of those rows and columns).  points: the host array of
+    decay_points(npoints, seed, density), if already made."""
     import math
 
     from . import decay_points
 
-    pts_np = decay_points(npoints, seed, density)
+    pts_np = decay_points(npoints, seed, density) if points is None else points
     pts = torch.from_numpy(pts_np).to(device)
     n = npoints * nfun
     nbk = -(-n // bs)
@@ -114,6 +118,8 @@ def decay(npoints: int, bs: int, seed: int, device, nfun: int = 5, alpha: float 
         near = (gap * gap).sum(-1).sqrt() <= rcut
         if cross is not None:
             near &= incross[r0:r1, None] | incross[None, :]
+        if keep is not None:
+            near &= keep[0][r0:r1, None] | keep[1][None, :]
         bi, bj = torch.nonzero(near, as_tuple=True)
         rows.append(bi + r0)
         cols.append(bj)
