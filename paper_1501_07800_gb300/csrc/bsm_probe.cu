@@ -152,14 +152,16 @@ __global__ void __launch_bounds__(256) k_probe_mixed(const double *__restrict__ 
 // four MMAs (M = 128, N = n) alternating between two accumulators, then
 // commits and waits (bounded) for the tensor core to finish.
 template <int F>
-__global__ void __launch_bounds__(128, 1) k_probe_tc(int n, int64_t iters, unsigned *err) {
-  extern __shared__ __align__(1024) uint8_t smem[];  // A: 4 KiB, B: n * 32 bytes
+__global__ void __launch_bounds__(128, 1) k_probe_tc(int n, int tiles, int64_t iters,
+                                                    unsigned *err) {
+  // `tiles` operand pairs: A tile t at t * 4 KiB, B tile t after all A tiles
+  extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tbase_sh;
   // small integer operands, as the split kernel's digits: the bytes 0x40
   // read as BF16 (0x4040) are 3.0, read as E4M3 2.0
   const uint32_t word = 0x40404040u;
-  const int bytes = 4096 + n * 32;
+  const int bytes = tiles * (4096 + n * 32);
   for (int i = threadIdx.x; i < bytes / 4; i += blockDim.x)
     reinterpret_cast<uint32_t *>(smem)[i] = word;
   fence_proxy_async_smem();
@@ -180,17 +182,21 @@ __global__ void __launch_bounds__(128, 1) k_probe_tc(int n, int64_t iters, unsig
     // K 128 bytes apart, 8-row groups 256 bytes apart
     const uint32_t sa = smem_u32(smem);
     const uint64_t ad = smem_desc(sa, 128, 256);
-    const uint64_t bd = smem_desc(sa + 4096, 128, 256);
+    const uint64_t bd = smem_desc(sa + tiles * 4096, 128, 256);
     const uint32_t idesc = F == 0 ? idesc_bf16_f32(128, n) : idesc_e4m3_f32(128, n);
+    int t = 0;
     for (int64_t it = 0; it < iters; it++) {
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         const uint32_t d = tbase + (uint32_t)((u & 1) * n);
         const uint32_t acc = (it > 0 || u > 1) ? 1u : 0u;
+        // descriptor start addresses are in 16-byte units
+        const uint64_t at = ad + (uint64_t)(t * 256), bt = bd + (uint64_t)(t * n * 2);
         if (F == 0)
-          tc_mma_bf16(d, ad, bd, idesc, acc);
+          tc_mma_bf16(d, at, bt, idesc, acc);
         else
-          tc_mma_f8(d, ad, bd, idesc, acc);
+          tc_mma_f8(d, at, bt, idesc, acc);
+        t = t + 1 == tiles ? 0 : t + 1;
       }
     }
     tc_commit(&bar);
@@ -324,9 +330,10 @@ extern "C" bsm_status bsm_probe_fp64(int kind, int64_t iters, double *flops, flo
   return st;
 }
 
-extern "C" bsm_status bsm_probe_tcgen05(int fmt, int n, int64_t iters, double *flops, float *ms,
-                                        void *stream) {
-  if ((fmt != 0 && fmt != 1) || n < 16 || n > 256 || n % 16 || iters < 1 || !flops || !ms)
+extern "C" bsm_status bsm_probe_tcgen05(int fmt, int n, int tiles, int64_t iters, double *flops,
+                                        float *ms, void *stream) {
+  if ((fmt != 0 && fmt != 1) || n < 16 || n > 256 || n % 16 || tiles < 1 || tiles > 8 ||
+      iters < 1 || !flops || !ms)
     return BSM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   // more shared memory than two CTAs could share: one CTA (one issuing
@@ -339,7 +346,8 @@ extern "C" bsm_status bsm_probe_tcgen05(int fmt, int n, int64_t iters, double *f
   cudaMemsetAsync(err, 0, sizeof(unsigned), s);
   const int grid = sm_count();
   count_launch();
-  bsm_status st = timed_launch([&] { kern<<<grid, 128, smem, s>>>(n, iters, err); }, err, ms, s);
+  bsm_status st =
+      timed_launch([&] { kern<<<grid, 128, smem, s>>>(n, tiles, iters, err); }, err, ms, s);
   const double k = fmt == 0 ? 16 : 32;
   *flops = (double)grid * (double)iters * 4 * 2.0 * 128 * n * k;
   dev_free(err, s);

@@ -108,11 +108,19 @@ def fp64(kind: str = "dmma_m8n8k4", seconds: float = 1.0) -> dict:
     return {"tflops": work / ms / 1e9, "ms": ms, "iters": iters, "clocks": clk}
 
 
-def tcgen05(fmt: int, n: int, seconds: float = 0.5) -> dict:
-    """tcgen05.mma rate at M = 128 and N = n (TFLOP/s); fmt 0 BF16, 1 E4M3."""
-    work, ms, iters, clk = _calibrated(lambda it: bsm.bsm_probe_tcgen05(fmt, n, it), seconds,
-                                       20000)
-    return {"tflops": work / ms / 1e9, "ms": ms, "iters": iters, "clocks": clk}
+def tcgen05(fmt: int, n: int, seconds: float = 0.5, tiles: int = 1) -> dict:
+    """tcgen05.mma rate at M = 128 and N = n (TFLOP/s); fmt 0 BF16, 1 E4M3;
+    consecutive instructions on `tiles` distinct operand pairs.  cycles: SM
+    cycles per instruction at the sampled clock."""
+    work, ms, iters, clk = _calibrated(lambda it: bsm.bsm_probe_tcgen05(fmt, n, it, tiles),
+                                       seconds, 20000)
+    out = {"tflops": work / ms / 1e9, "ms": ms, "iters": iters, "clocks": clk}
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    if clk.get("sm_mhz"):
+        per_inst = 2.0 * 128 * n * (16 if fmt == 0 else 32)
+        out["cycles_per_instruction"] = per_inst / (work / ms * 1e3 / sms / (clk["sm_mhz"] * 1e6))
+    return out
 
 
 def bulk_copy(nbytes: int = 8 << 30, stage_bytes: int = 32768, stages: int = 4) -> dict:
@@ -140,6 +148,11 @@ def measure_all(seconds: float = 0.5) -> dict:
     out = {"fp64": {k: fp64(k, seconds) for k in FP64_KINDS}}
     out["tcgen05_bf16"] = {str(n): tcgen05(0, n, seconds) for n in (32, 64, 96, 128, 256)}
     out["tcgen05_e4m3"] = {str(n): tcgen05(1, n, seconds) for n in (32, 64, 96, 128, 256)}
+    # distinct operands per instruction, as in the split kernel
+    out["tcgen05_bf16_distinct_tiles"] = {str(n): tcgen05(0, n, seconds, tiles=8)
+                                          for n in (32, 64, 128)}
+    out["tcgen05_e4m3_distinct_tiles"] = {str(n): tcgen05(1, n, seconds, tiles=8)
+                                          for n in (32, 64, 128)}
     out["bulk_copy"] = [bulk_copy(stage_bytes=sb, stages=st)
                         for sb, st in ((16384, 4), (32768, 4), (36864, 4), (65536, 3))]
     return out
