@@ -439,6 +439,19 @@ bsm_status bsm_plan_results(bsm_plan plan, bsm_matrix *C, void *stream);
 bsm_status bsm_plan_info(bsm_plan plan, int *order, int *chunk, int *ctas_per_sm,
                          int64_t *nitems);
 
+/* bsm_plan_tile -- the arithmetic tile of the plan's numeric phase (the FP64
+ * thread tile is chosen by measurement with BSM_FLAG_AUTOTUNE):
+ *   form           1: FP64 on scalar DFMA -- each of a C block's 128 threads
+ *                  sums a tile_m x tile_n tile of outputs (tile_n consecutive
+ *                  columns), one k at a time;
+ *                  0: FP64 on the tensor path (BSM_FP64_MODE=dmma) -- 8 x 8
+ *                  mma.sync m8n8k4 tiles, 2 x 2 warps per C block;
+ *                  2: split modes -- tcgen05 MMAs of tile_m = 128 rows and
+ *                  tile_n = N columns (bs: one C block per work item, 2 bs:
+ *                  sibling pairs of C blocks sharing every A tile)
+ * Outputs may be NULL.  Errors: INVALID_ARG. */
+bsm_status bsm_plan_tile(bsm_plan plan, int *form, int *tile_m, int *tile_n);
+
 /* bsm_plan_destroy -- free a plan (NULL accepted). */
 bsm_status bsm_plan_destroy(bsm_plan plan);
 

@@ -70,6 +70,7 @@ _PROTOS = {
     "bsm_plan_results": (_I32, [_P, _P, _P]),
     "bsm_plan_info": (_I32, [_P, _P, _P, _P, _P]),
     "bsm_plan_block_size": (_I32, [_P, _P]),
+    "bsm_plan_tile": (_I32, [_P, _P, _P, _P]),
     "bsm_plan_destroy": (_I32, [_P]),
     "bsm_destroy": (_I32, [_P]),
     "bsm_status_string": (ctypes.c_char_p, [_I32]),
@@ -565,6 +566,15 @@ def bsm_plan_info(plan: Plan):
     _check(load().bsm_plan_info(plan.handle, ctypes.byref(o), ctypes.byref(c), ctypes.byref(k),
                                 ctypes.byref(n)), "bsm_plan_info")
     return o.value, c.value, k.value, n.value
+
+
+def bsm_plan_tile(plan: Plan):
+    """(form, tile_m, tile_n): 1 = FP64 DFMA, a thread's tile_m x tile_n
+    outputs; 0 = FP64 mma.sync 8 x 8 tiles; 2 = split, tcgen05 M x N."""
+    f, m, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().bsm_plan_tile(plan.handle, ctypes.byref(f), ctypes.byref(m), ctypes.byref(n)),
+           "bsm_plan_tile")
+    return f.value, m.value, n.value
 
 
 def bsm_plan_block_size(plan: Plan) -> int:

@@ -29,9 +29,23 @@ __device__ __forceinline__ void dmma_8x8x4(double (&c)[2], double a, double b) {
 // timed-out wait; every thread returns the same value.
 // Two forms of the arithmetic, bit-compatible with nothing but themselves:
 // MODE 0 sums on the FP64 tensor pipe (mma.sync m8n8k4, 2 x 2 warps of 8 x 8
-// tiles); MODE 1 with scalar DFMA, each thread a (BS/16) x (BS/8) tile of
-// outputs summed one k at a time in ascending order (a plain dot product of
-// fused multiply-adds).
+// tiles); MODE >= 1 with scalar DFMA, every output summed one k at a time in
+// ascending order (a plain dot product of fused multiply-adds), each thread a
+// tile of TR x TC outputs: TC = BS/8 (MODE 1), BS/16 (MODE 2) or BS/4
+// (MODE 3; at most BS^2/128, one row per thread) consecutive columns of
+// TR = BS^2 / (128 TC) rows 128 TC / BS apart.  The DFMA tiles give identical
+// results (same order per output).
+template <int BS, int MODE>
+struct DfmaTile {
+  static constexpr int TC = MODE == 2 ? BS / 16
+                                      : (MODE == 3 ? (BS / 4 < BS * BS / 128 ? BS / 4 : BS * BS / 128)
+                                                   : BS / 8);
+  static constexpr int TPR = BS / TC;       // threads per row
+  static constexpr int RS = 128 / TPR;      // row stride between a thread's rows
+  static constexpr int TR = BS / RS;
+  static_assert(TR >= 1 && TR * RS == BS && TC * TPR == BS, "thread tile");
+};
+
 template <int BS, int MODE>
 __device__ bool cblock_fp64(const int32_t *__restrict__ seg, const int32_t *__restrict__ ta,
                             const int32_t *__restrict__ tb, int64_t c, int64_t na, int64_t nb,
@@ -68,14 +82,15 @@ __device__ bool cblock_fp64(const int32_t *__restrict__ seg, const int32_t *__re
   for (int i = 0; i < TW; i++)
 #pragma unroll
     for (int j = 0; j < TW; j++) acc[i][j][0] = acc[i][j][1] = 0.0;
-  // DFMA form: rows i * 16 + tid / 8, columns (tid % 8) * TC + x
-  constexpr int TR = BS / 16, TC = BS / 8;
+  // DFMA form: rows i * RS + tid / TPR, columns (tid % TPR) * TC + x
+  using DT = DfmaTile<BS, MODE>;
+  constexpr int TR = DT::TR, TC = DT::TC, RS = DT::RS, TPR = DT::TPR;
   double fac[TR][TC];
 #pragma unroll
   for (int i = 0; i < TR; i++)
 #pragma unroll
     for (int x = 0; x < TC; x++) fac[i][x] = 0.0;
-  const int frow = tid >> 3, fcol = (tid & 7) * TC;
+  const int frow = tid / TPR, fcol = (tid % TPR) * TC;
 
   const int ar = lane >> 2, ak = lane & 3;
   bool ok = true;
@@ -96,17 +111,22 @@ __device__ bool cblock_fp64(const int32_t *__restrict__ seg, const int32_t *__re
       use1++;
     const double *sa = smem + (size_t)s * 2 * BB;
     const double *sb = sa + BB;
-    if constexpr (MODE == 1) {
+    if constexpr (MODE >= 1) {
 #pragma unroll 4
       for (int kk = 0; kk < BS; kk++) {
         double a[TR], b[TC];
 #pragma unroll
-        for (int i = 0; i < TR; i++) a[i] = sa[(i * 16 + frow) * BS + kk];
+        for (int i = 0; i < TR; i++) a[i] = sa[(i * RS + frow) * BS + kk];
+        if constexpr (TC % 2 == 0) {
 #pragma unroll
-        for (int x = 0; x < TC; x += 2) {
-          const double2 v = *reinterpret_cast<const double2 *>(sb + kk * BS + fcol + x);
-          b[x] = v.x;
-          b[x + 1] = v.y;
+          for (int x = 0; x < TC; x += 2) {
+            const double2 v = *reinterpret_cast<const double2 *>(sb + kk * BS + fcol + x);
+            b[x] = v.x;
+            b[x + 1] = v.y;
+          }
+        } else {
+#pragma unroll
+          for (int x = 0; x < TC; x++) b[x] = sb[kk * BS + fcol + x];
         }
 #pragma unroll
         for (int i = 0; i < TR; i++)
@@ -143,15 +163,24 @@ __device__ bool cblock_fp64(const int32_t *__restrict__ seg, const int32_t *__re
   }
   bool any = false;
   double *cb = Cv + c * BB;
-  if constexpr (MODE == 1) {
+  if constexpr (MODE >= 1) {
 #pragma unroll
-    for (int i = 0; i < TR; i++)
+    for (int i = 0; i < TR; i++) {
+      if constexpr (TC % 2 == 0) {
 #pragma unroll
-      for (int x = 0; x < TC; x += 2) {
-        any |= nonzero_f64(fac[i][x]) | nonzero_f64(fac[i][x + 1]);
-        *reinterpret_cast<double2 *>(cb + (i * 16 + frow) * BS + fcol + x) =
-            make_double2(fac[i][x], fac[i][x + 1]);
+        for (int x = 0; x < TC; x += 2) {
+          any |= nonzero_f64(fac[i][x]) | nonzero_f64(fac[i][x + 1]);
+          *reinterpret_cast<double2 *>(cb + (i * RS + frow) * BS + fcol + x) =
+              make_double2(fac[i][x], fac[i][x + 1]);
+        }
+      } else {
+#pragma unroll
+        for (int x = 0; x < TC; x++) {
+          any |= nonzero_f64(fac[i][x]);
+          cb[(i * RS + frow) * BS + fcol + x] = fac[i][x];
+        }
       }
+    }
   } else {
 #pragma unroll
   for (int i = 0; i < TW; i++)

@@ -197,7 +197,7 @@ ProdDesc make_desc(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, double
                    int32_t *nz);
 bsm_status numeric_fp64_batched(int bs, const ProdDesc *prods, const uint64_t *items,
                                 int64_t nitems, unsigned long long *counter, unsigned *errword,
-                                int ctas_per_sm, cudaStream_t s);
+                                int ctas_per_sm, cudaStream_t s, int form = -1);
 bsm_status split_supported(int bs, int slices);
 int split_flush_group(int bs, int spec, int bound_log2);
 bsm_status split_prepare(bsm_matrix A, bsm_matrix B, int slices, unsigned *errword, ProdDesc &d,

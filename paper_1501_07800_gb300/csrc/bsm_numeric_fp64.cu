@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(128) k_numeric_fp64(
 
 // Persistent form over a global work list of (product, C block) items.
 template <int BS, int MODE>
-__global__ void __launch_bounds__(128) k_numeric_fp64_batched(const ProdDesc *__restrict__ prods,
+__global__ void __launch_bounds__(128, 4) k_numeric_fp64_batched(const ProdDesc *__restrict__ prods,
                                                               const uint64_t *__restrict__ items,
                                                               int64_t nitems,
                                                               unsigned long long *counter,
@@ -156,12 +156,15 @@ bsm_status numeric_fp64(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, d
 
 bsm_status numeric_fp64_batched(int bs, const ProdDesc *prods, const uint64_t *items,
                                 int64_t nitems, unsigned long long *counter, unsigned *errword,
-                                int ctas_per_sm, cudaStream_t s) {
+                                int ctas_per_sm, cudaStream_t s, int form) {
   if (nitems == 0) return BSM_OK;
-  const bool f = fp64_mode() == 1;
-#define BSM_LB(B)                                                                           \
-  return f ? launch_batched<B, 1>(prods, items, nitems, counter, errword, ctas_per_sm, s) \
-           : launch_batched<B, 0>(prods, items, nitems, counter, errword, ctas_per_sm, s)
+  // form: 0 DMMA; 1, 2, 3 DFMA tiles of BS/8, BS/16, BS/4 columns per thread
+  const int f = form < 0 ? fp64_mode() : form;
+#define BSM_LB(B)                                                                                \
+  return f == 1   ? launch_batched<B, 1>(prods, items, nitems, counter, errword, ctas_per_sm, s) \
+         : f == 2 ? launch_batched<B, 2>(prods, items, nitems, counter, errword, ctas_per_sm, s) \
+         : f == 3 ? launch_batched<B, 3>(prods, items, nitems, counter, errword, ctas_per_sm, s) \
+                  : launch_batched<B, 0>(prods, items, nitems, counter, errword, ctas_per_sm, s)
   switch (bs) {
     case 16: BSM_LB(16);
     case 32: BSM_LB(32);

@@ -18,8 +18,12 @@
 // of products, and the magnitudes of the C-block count and of the mean and
 // largest product-list length) the tuner times each candidate launch
 // configuration -- work order (longest product list first, or product by
-// product in Morton order), work items claimed per atomic (split kernel) and
-// CTAs per SM (FP64 kernel) -- and caches the fastest for the process.
+// product in Morton order), work items claimed per atomic (split kernel), the
+// FP64 kernel's thread tile (DFMA: bs/8, bs/16 or bs/4 consecutive output
+// columns per thread, with the rows to fill a C block among 128 threads; every
+// tile sums each output in the same order, so the choice never changes a
+// result) -- and caches the fastest for the process.
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -47,6 +51,7 @@ struct bsm_plan_s {
   // chosen configuration
   int order = 0;  // 0: longest first, 1: product-major Morton
   int chunk = 32, ctas_per_sm = 0;
+  int form = -1;  // FP64 tile: 0 DMMA; 1, 2, 3 DFMA thread tiles (-1: the process default)
   bool tuned = false;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -81,7 +86,7 @@ struct TuneKey {
   }
 };
 struct TuneVal {
-  int order, chunk, ctas;
+  int order, chunk, ctas, form;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
@@ -97,13 +102,15 @@ int ilog2(int64_t x) {
 
 // The numeric phase of the plan with a given configuration (no allocation:
 // it may be captured).
-bsm_status enqueue_numeric(bsm_plan P, int order, int chunk, int ctas, cudaStream_t s) {
+bsm_status enqueue_numeric(bsm_plan P, int order, int chunk, int ctas, int form,
+                           cudaStream_t s) {
   cudaMemsetAsync(P->scr + 2, 0, 8, s);  // work counter
   cudaMemsetAsync(P->err, 0, sizeof(unsigned), s);
   const uint64_t *items = order == 0 ? P->items_lpt : P->items_morton;
   unsigned long long *counter = reinterpret_cast<unsigned long long *>(P->scr + 2);
   if (P->prec == BSM_FP64)
-    return numeric_fp64_batched(P->bs, P->table, items, P->nitems, counter, P->err, ctas, s);
+    return numeric_fp64_batched(P->bs, P->table, items, P->nitems, counter, P->err, ctas, s,
+                                form);
   for (int i = 0; i < P->n; i++)
     if (P->sym[i].nc > 0)
       BSM_TRY(split_compute(P->A[i], P->B[i], P->slices, P->desc[i], P->err, s,
@@ -139,14 +146,14 @@ void destroy_plan(bsm_plan P) {
 }
 
 // Times one configuration (best of `reps` runs), in ms.
-float time_config(bsm_plan P, int order, int chunk, int ctas, int reps) {
+float time_config(bsm_plan P, int order, int chunk, int ctas, int form, int reps) {
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   float best = 1e30f;
   for (int r = 0; r < reps; r++) {
     cudaEventRecord(a, P->stream);
-    if (enqueue_numeric(P, order, chunk, ctas, P->stream) != BSM_OK) break;
+    if (enqueue_numeric(P, order, chunk, ctas, form, P->stream) != BSM_OK) break;
     cudaEventRecord(b, P->stream);
     if (cudaEventSynchronize(b) != cudaSuccess) break;
     float ms = 0;
@@ -177,33 +184,43 @@ bsm_status autotune(bsm_plan P) {
       P->order = it->second.order;
       P->chunk = it->second.chunk;
       P->ctas_per_sm = it->second.ctas;
+      P->form = it->second.form;
       P->tuned = true;
       return BSM_OK;
     }
   }
   // FP64 runs at the FP64 pipe's rate whatever the schedule, and one run of a
-  // large batch takes seconds: only the work order is measured there.
+  // large batch takes seconds: the arithmetic tile is measured in the default
+  // order, then the other order with the better tile.
   std::vector<TuneVal> cands;
-  for (int order : {0, 1}) {
-    if (P->prec == BSM_FP64)
-      cands.push_back({order, 32, 0});
-    else
-      for (int chunk : {32, 8, 1}) cands.push_back({order, chunk, 0});
+  if (P->prec == BSM_FP64) {
+    if (fp64_mode() == 0) {
+      cands.push_back({0, 32, 0, 0});  // the tensor form has one tile
+    } else {
+      for (int form : {1, 2, 3}) cands.push_back({0, 32, 0, form});
+    }
+  } else {
+    for (int order : {0, 1})
+      for (int chunk : {32, 8, 1}) cands.push_back({order, chunk, 0, -1});
   }
   const int reps = P->prec == BSM_FP64 ? 1 : 2;
-  enqueue_numeric(P, cands[0].order, cands[0].chunk, cands[0].ctas, P->stream);  // warm-up
+  enqueue_numeric(P, cands[0].order, cands[0].chunk, cands[0].ctas, cands[0].form,
+                  P->stream);  // warm-up
   float best = 1e30f;
   TuneVal pick = cands[0];
-  for (const TuneVal &c : cands) {
-    float ms = time_config(P, c.order, c.chunk, c.ctas, reps);
+  auto measure = [&](const TuneVal &c) {
+    float ms = time_config(P, c.order, c.chunk, c.ctas, c.form, reps);
     if (ms < best) {
       best = ms;
       pick = c;
     }
-  }
+  };
+  for (const TuneVal &c : cands) measure(c);
+  if (P->prec == BSM_FP64) measure({1, 32, 0, pick.form});
   P->order = pick.order;
   P->chunk = pick.chunk;
   P->ctas_per_sm = pick.ctas;
+  P->form = pick.form;
   P->tuned = true;
   std::lock_guard<std::mutex> g(g_tune_mu);
   g_tune_cache[key] = pick;
@@ -453,14 +470,15 @@ extern "C" bsm_status bsm_plan_create(int n, const bsm_matrix *A, const bsm_matr
   // one eager run: kernel attributes are set up outside the capture, and the
   // chosen configuration is known to launch
   if (st == BSM_OK && P->nitems > 0) {
-    st = enqueue_numeric(P, P->order, P->chunk, P->ctas_per_sm, s);
+    st = enqueue_numeric(P, P->order, P->chunk, P->ctas_per_sm, P->form, s);
     if (st == BSM_OK) st = cuda_status(cudaStreamSynchronize(s));
   }
   // capture the numeric phase
   if (st == BSM_OK) {
     st = cuda_status(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
     if (st == BSM_OK) {
-      bsm_status st2 = P->nitems > 0 ? enqueue_numeric(P, P->order, P->chunk, P->ctas_per_sm, s)
+      bsm_status st2 = P->nitems > 0 ? enqueue_numeric(P, P->order, P->chunk, P->ctas_per_sm,
+                                                       P->form, s)
                                      : cuda_status(cudaMemsetAsync(P->err, 0, 4, s));
       cudaError_t e = cudaStreamEndCapture(s, &P->graph);
       st = st2 != BSM_OK ? st2 : cuda_status(e);
@@ -532,6 +550,27 @@ extern "C" bsm_status bsm_plan_results(bsm_plan P, bsm_matrix *C, void *stream) 
 extern "C" bsm_status bsm_plan_block_size(bsm_plan P, int *bs) {
   if (!P || !bs) return BSM_ERR_INVALID_ARG;
   *bs = P->bs;
+  return BSM_OK;
+}
+
+extern "C" bsm_status bsm_plan_tile(bsm_plan P, int *form, int *tile_m, int *tile_n) {
+  if (!P) return BSM_ERR_INVALID_ARG;
+  if (P->inner) return bsm_plan_tile(P->inner, form, tile_m, tile_n);
+  int f = 2, m = 128, nn = P->bs * P->np;
+  if (P->prec == BSM_FP64) {
+    const int fm = P->form < 0 ? fp64_mode() : P->form;
+    if (fm == 0) {  // a warp's 8 x 8 mma.sync tiles
+      f = 0;
+      m = nn = 8;
+    } else {        // a thread's outputs
+      f = 1;
+      nn = fm == 2 ? P->bs / 16 : (fm == 3 ? std::min(P->bs / 4, P->bs * P->bs / 128) : P->bs / 8);
+      m = P->bs * P->bs / (128 * nn);
+    }
+  }
+  if (form) *form = f;
+  if (tile_m) *tile_m = m;
+  if (tile_n) *tile_n = nn;
   return BSM_OK;
 }
 

@@ -35,12 +35,18 @@ def test_plan_equals_batched_and_replays(prec, autotune):
     order, chunk, ctas, nitems = bsm.bsm_plan_info(plan)
     assert order in (0, 1) and 1 <= chunk <= 32 and ctas >= 0
     assert nitems == sum(r.nblk for r in ref)   # generic data: nothing cancels
+    form, tm, tn = bsm.bsm_plan_tile(plan)
+    bs = pairs[0][0].bs
+    if prec == bsm.BSM_FP64:   # a thread's DFMA tile covers the C block among 128 threads
+        assert form == 1 and tm * tn * 128 == bs * bs and tn in (bs // 16, bs // 8, bs // 4)
+    else:
+        assert form == 2 and tm == 128 and tn in (bs, 2 * bs)
     for _ in range(2):                           # graph replays are idempotent
         bsm.bsm_plan_execute(plan)
         got = [from_bsm(c) for c in bsm.bsm_plan_results(plan)]
         for g, r in zip(got, ref):
             assert_same_structure(g, r)
-            assert np.array_equal(g.vals, r.vals)
+            assert np.array_equal(g.vals, r.vals)   # every thread tile sums in one order
 
 
 @pytest.mark.parametrize("prec,tol", [(bsm.BSM_FP64, 1e-12), (bsm.BSM_SPLIT_BF16, 1e-11)])
