@@ -489,10 +489,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
   constexpr int kTeam = kTeamWarps * 32;         // threads per epilogue team
   constexpr int NB = NP * BS;                    // MMA N: output columns per item
   constexpr int BETA = Fmt<F>::BETA, TS = Fmt<F>::TSPLIT;
-  // one narrow flush: the diagonal sums' FP32 bit patterns go to shared
-  // memory as they are and are combined in wrapping 64-bit arithmetic, when
-  // the digit bounds keep the combined integer below 2^63
-  constexpr bool kNarrow64 = narrow_fits_int64<S, BETA>(narrow_max_elems<S, BETA>());
+  // one narrow flush of at most kFast block products: the diagonal sums' FP32
+  // bit patterns go to shared memory as they are and are combined in wrapping
+  // 64-bit arithmetic (the digit bounds keep the combined integer below 2^63)
+  constexpr int kFast = narrow_int64_products<S, BETA, BS>();
   // instruction descriptors for N = NB, 2 NB, 3 NB (one to three diagonal groups)
   constexpr uint32_t IDESC1 = F == 0 ? idesc_bf16_f32(128, NB) : idesc_e4m3_f32(128, NB);
   constexpr uint32_t IDESC2 = F == 0 ? idesc_bf16_f32(128, 2 * NB) : idesc_e4m3_f32(128, 2 * NB);
@@ -840,6 +840,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
       const FlushPlan fplan = flush_plan(nk, P.flushk, P.flushk_wide);
       const int nfl = fplan.nfl, kf = fplan.kf;
       const bool wide = fplan.wide;
+      const bool fast = !wide && nk <= kFast;  // uniform over the team
       int64_t *const fold = P.fold + ((int64_t)blockIdx.x * 2 + team) * (NB * BS * 2);
       bool ok = true;
       // Every warp runs all nfl iterations (doing no work once `ok` is false)
@@ -871,7 +872,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
 #pragma unroll
               for (int x = 0; x < HC; x += 4) {
                 int4 val;
-                if (kNarrow64 && !wide) {  // bit patterns of D + 1.5 2^23 (one flush)
+                if (fast) {  // bit patterns of D + 1.5 2^23 (one flush)
                   val = make_int4((int32_t)__float_as_uint(__uint_as_float(v[x]) + kMagicF),
                                   (int32_t)__float_as_uint(__uint_as_float(v[x + 1]) + kMagicF),
                                   (int32_t)__float_as_uint(__uint_as_float(v[x + 2]) + kMagicF),
@@ -952,7 +953,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         for (int d = 0; d < S; d++)
           dv[d] = *reinterpret_cast<const int4 *>(tcomb + (d * BS + rr) * C::CROW + c4);
         double out[4];
-        if (kNarrow64 && !wide) {
+        if (kFast > 0 && fast) {
 #pragma unroll
           for (int x = 0; x < 4; x++) {
             uint32_t pat[S];

@@ -80,6 +80,16 @@ __host__ __device__ constexpr int narrow_max_elems() {
   return a < b ? a : b;
 }
 
+// Most block products (of BS inner elements each) of one narrow flush for
+// which |V| < 2^63 is guaranteed: the largest n = products * BS that passes
+// narrow_fits_int64, capped by the narrow flush itself.
+template <int S, int B, int BS>
+__host__ __device__ constexpr int narrow_int64_products() {
+  int k = 0;
+  while ((k + 1) * BS <= narrow_max_elems<S, B>() && narrow_fits_int64<S, B>((k + 1) * BS)) k++;
+  return k;
+}
+
 // Correctly rounded v 2^X (to nearest, ties to even) when the result is a
 // normal double; false otherwise (zero is returned as +0.0 and true).
 __host__ __device__ __forceinline__ bool int64_scaled_to_double(int64_t v, int X, double &out) {
