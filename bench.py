@@ -561,6 +561,8 @@ def run_batched(bsm, torch, args, stream, nprod=64):
             c = bsm.bsm_multiply_batched(As, Bs, prec=prec)
             del c
         full_ms = timed(full, steps)
+        full()  # one more call for the phase split (symbolic + work list, numeric, C assembly)
+        phases = [float(x) for x in bsm.bsm_last_phase_ms()[0]]
         t1 = time.time()
         # the autotuner picks the leaf size (re-blocked copies of the
         # operands, refreshed at every replay) and the launch schedule
@@ -571,7 +573,7 @@ def run_batched(bsm, torch, args, stream, nprod=64):
         bsm.bsm_plan_execute(plan)
         replay_ms = timed(lambda: bsm.bsm_plan_execute(plan), steps)
         del plan  # one plan's buffers (all C blocks) at a time
-        out[name] = {"full_call_ms": statistics.mean(full_ms),
+        out[name] = {"full_call_ms": statistics.mean(full_ms), "full_call_phase_ms": phases,
                      "full_call_gflops": flops / (statistics.mean(full_ms) / 1e3) / 1e9,
                      "graph_replay_ms": statistics.mean(replay_ms),
                      "graph_replay_gflops": flops / (statistics.mean(replay_ms) / 1e3) / 1e9,

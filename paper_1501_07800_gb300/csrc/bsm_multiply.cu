@@ -1,5 +1,9 @@
 // C = A*B: symbolic phase, numeric phase, exact-zero block removal, C levels.
 #include <cstring>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "bsm_internal.cuh"
@@ -439,9 +443,112 @@ __global__ void k_batch_items(const int32_t *__restrict__ seg, int64_t nc, uint3
   items[c] = make_item(p, (uint64_t)c);
 }
 
-// Products of one block size: symbolic phases one by one, then one persistent
-// numeric launch over all their C blocks in longest-first order, then zero
-// removal and level build per product.
+// A fixed pool of host threads for per-product host work (created on first
+// use, never torn down: its threads idle on a condition variable until the
+// process exits, so no thread-local CUDA state is released during static
+// destruction).  run(nw, job) calls job(w) for w < nw on the pool's threads
+// and returns when all have finished; one job runs at a time.
+class WorkerPool {
+ public:
+  static constexpr int kThreads = 8;
+  static WorkerPool &get() {
+    static WorkerPool *pool = new WorkerPool();
+    return *pool;
+  }
+  void run(int nw, const std::function<void(int)> &job) {
+    std::lock_guard<std::mutex> one(run_mu_);
+    std::unique_lock<std::mutex> lk(mu_);
+    job_ = &job;
+    njob_ = nw;
+    next_ = 0;
+    pending_ = nw;
+    gen_++;
+    cv_.notify_all();
+    done_cv_.wait(lk, [&] { return pending_ == 0; });
+    job_ = nullptr;
+  }
+
+ private:
+  WorkerPool() {
+    for (int t = 0; t < kThreads; t++) std::thread([this] { loop(); }).detach();
+  }
+  void loop() {
+    uint64_t seen = 0;
+    std::unique_lock<std::mutex> lk(mu_);
+    for (;;) {
+      cv_.wait(lk, [&] { return gen_ != seen && next_ < njob_; });
+      seen = gen_;
+      while (next_ < njob_) {
+        const int w = next_++;
+        const std::function<void(int)> *job = job_;
+        lk.unlock();
+        (*job)(w);
+        lk.lock();
+        if (--pending_ == 0) done_cv_.notify_all();
+      }
+    }
+  }
+  std::mutex run_mu_, mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(int)> *job_ = nullptr;
+  int njob_ = 0, next_ = 0, pending_ = 0;
+  uint64_t gen_ = 0;
+};
+
+// Runs f(i, stream) for the products i < n on up to WorkerPool::kThreads host
+// threads, each worker with its own stream that starts after the work queued
+// so far on `s` and that `s` waits for at the end (events), so that the
+// per-product host round trips of the symbolic phase and of C's assembly
+// overlap.  Returns the first error; the work of every product that ran stays
+// ordered before later work on `s`.
+template <typename F>
+static bsm_status parallel_products(int n, cudaStream_t s, F f) {
+  const int nw = n < WorkerPool::kThreads ? n : WorkerPool::kThreads;
+  if (nw <= 1) {
+    for (int i = 0; i < n; i++) BSM_TRY(f(i, s));
+    return BSM_OK;
+  }
+  int dev = 0;
+  BSM_CUDA(cudaGetDevice(&dev));
+  cudaEvent_t ready = nullptr;
+  BSM_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  cudaEventRecord(ready, s);
+  std::vector<cudaStream_t> ws(nw, nullptr);
+  std::vector<cudaEvent_t> done(nw, nullptr);
+  std::vector<bsm_status> res(nw, BSM_OK);
+  std::vector<int64_t> launches(nw, 0);
+  bsm_status st = BSM_OK;
+  for (int w = 0; w < nw && st == BSM_OK; w++) {
+    st = cuda_status(cudaStreamCreateWithFlags(&ws[w], cudaStreamNonBlocking));
+    if (st == BSM_OK) st = cuda_status(cudaEventCreateWithFlags(&done[w], cudaEventDisableTiming));
+    if (st == BSM_OK) cudaStreamWaitEvent(ws[w], ready, 0);
+  }
+  if (st == BSM_OK) {
+    WorkerPool::get().run(nw, [&](int w) {
+      cudaSetDevice(dev);
+      const int64_t l0 = launch_counter();
+      for (int i = w; i < n && res[w] == BSM_OK; i += nw) res[w] = f(i, ws[w]);
+      launches[w] = launch_counter() - l0;
+      cudaEventRecord(done[w], ws[w]);
+    });
+    for (int w = 0; w < nw; w++) {
+      cudaStreamWaitEvent(s, done[w], 0);
+      count_launch(launches[w]);
+      if (st == BSM_OK) st = res[w];
+    }
+  }
+  for (int w = 0; w < nw; w++) {
+    if (ws[w]) cudaStreamDestroy(ws[w]);  // released once its work is done
+    if (done[w]) cudaEventDestroy(done[w]);
+  }
+  cudaEventDestroy(ready);
+  return st;
+}
+
+// Products of one block size: the symbolic phases (concurrently, one host
+// thread and stream per worker), then one persistent numeric launch over all
+// their C blocks in longest-first order, then zero removal and level build
+// per product (concurrently again).
 static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A,
                                 const bsm_matrix *B, bsm_matrix *C, int prec, int slices,
                                 cudaStream_t s) {
@@ -468,10 +575,11 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
     for (void *p : owned) dev_free(p, s);
     dev_free(err, s);
   };
+  st = parallel_products(n, s, [&](int i, cudaStream_t ws) {
+    return symbolic_multiply(A[idx[i]], B[idx[i]], &sym[i], ws);
+  });
   for (int i = 0; i < n && st == BSM_OK; i++) {
     bsm_matrix a = A[idx[i]], b = B[idx[i]];
-    st = symbolic_multiply(a, b, &sym[i], s);
-    if (st != BSM_OK) break;
     if (sym[i].nc > 0xFFFFFFFFFFll) st = BSM_ERR_UNSUPPORTED;
     int64_t side = a->mb > b->nb ? a->mb : b->nb;
     shells[i] = new_matrix_shell(a->nrows, b->ncols, bs, ceil_log2_i64(side < 1 ? 1 : side));
@@ -568,14 +676,13 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
     }
   }
   const int t2 = timing_mark(s);
-  for (int i = 0; i < n && st == BSM_OK; i++) {
-    if (sym[i].nc == 0) {
-      st = build_levels(shells[i], s);
-    } else {
-      st = finish_product(shells[i], &sym[i], cv[i], nz[i], err, s);  // owns cv[i]
+  if (st == BSM_OK)
+    st = parallel_products(n, s, [&](int i, cudaStream_t ws) {
+      if (sym[i].nc == 0) return build_levels(shells[i], ws);
+      double *c = cv[i];
       cv[i] = nullptr;
-    }
-  }
+      return finish_product(shells[i], &sym[i], c, nz[i], err, ws);  // owns c
+    });
   const int t3 = timing_mark(s);
   if (st != BSM_OK) {
     cleanup(false);
