@@ -49,19 +49,21 @@ bsm_status bsm_probe_fp64(int kind, int64_t iters, double *flops, float *ms, voi
  * bsm_probe_tcgen05 -- tcgen05.mma issue rate at M = 128 and a given N, as
  * the split kernel issues them: operands in shared memory (K-major core
  * matrices, no swizzle; an A tile is 4 KiB, a B tile n * 32 bytes), FP32
- * accumulators in TMEM, one issuing thread per SM, `iters` rounds of four
- * instructions alternating between two accumulators.
+ * accumulators in TMEM, one CTA per SM, `iters` rounds of four instructions
+ * per issuing thread alternating between two accumulators.
  *   fmt     0: kind::f16 BF16 x BF16 (K = 16 per instruction);
  *           1: kind::f8f6f4 E4M3 x E4M3 (K = 32)
  *   n       16..256, a multiple of 16
  *   tiles   1..8: consecutive instructions cycle through this many distinct
  *           (A, B) tile pairs (1: every instruction reads the same pair)
+ *   issuers 1..4 threads (lane 0 of warps 0..issuers-1) each issue `iters`
+ *           rounds into their own two accumulators (2 issuers n <= 512)
  *   flops   receives 2 * 128 * n * K * instructions
  *   ms      receives the launch's duration
  * Errors: INVALID_ARG, OOM, TIMEOUT, CUDA.
  */
-bsm_status bsm_probe_tcgen05(int fmt, int n, int tiles, int64_t iters, double *flops, float *ms,
-                             void *stream);
+bsm_status bsm_probe_tcgen05(int fmt, int n, int tiles, int issuers, int64_t iters, double *flops,
+                             float *ms, void *stream);
 
 /*
  * bsm_probe_bulk_copy -- HBM read rate of 1-D bulk copies (cp.async.bulk)

@@ -62,7 +62,7 @@ _PROTOS = {
                                                 _P, _P]),
     "bsm_selftest_wait_timeout": (_I32, [_I32, _P]),
     "bsm_probe_fp64": (_I32, [_I32, _I64, _P, _P, _P]),
-    "bsm_probe_tcgen05": (_I32, [_I32, _I32, _I32, _I64, _P, _P, _P]),
+    "bsm_probe_tcgen05": (_I32, [_I32, _I32, _I32, _I32, _I64, _P, _P, _P]),
     "bsm_probe_bulk_copy": (_I32, [_I64, _I32, _I32, _P, _P, _P]),
     "bsm_update_values": (_I32, [_P, _I64, _P, _P, _P, _I32, _P]),
     "bsm_plan_create": (_I32, [_I32, _P, _P, _P, _P, _P]),
@@ -476,12 +476,15 @@ def bsm_probe_fp64(kind: int, iters: int, stream=None):
     return f.value, ms.value
 
 
-def bsm_probe_tcgen05(fmt: int, n: int, iters: int, tiles: int = 1, stream=None):
+def bsm_probe_tcgen05(fmt: int, n: int, iters: int, tiles: int = 1, issuers: int = 1,
+                      stream=None):
     """(flops, ms) of one tcgen05.mma probe launch: fmt 0 BF16, 1 E4M3; M = 128;
-    consecutive instructions cycle through `tiles` distinct operand pairs."""
+    consecutive instructions cycle through `tiles` distinct operand pairs;
+    `issuers` threads per SM issue concurrently."""
     f, ms = ctypes.c_double(), ctypes.c_float()
-    _check(load().bsm_probe_tcgen05(int(fmt), int(n), int(tiles), int(iters), ctypes.byref(f),
-                                    ctypes.byref(ms), _stream_ptr(stream)), "bsm_probe_tcgen05")
+    _check(load().bsm_probe_tcgen05(int(fmt), int(n), int(tiles), int(issuers), int(iters),
+                                    ctypes.byref(f), ctypes.byref(ms), _stream_ptr(stream)),
+           "bsm_probe_tcgen05")
     return f.value, ms.value
 
 

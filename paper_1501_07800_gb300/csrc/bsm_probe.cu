@@ -152,11 +152,11 @@ __global__ void __launch_bounds__(256) k_probe_mixed(const double *__restrict__ 
 // four MMAs (M = 128, N = n) alternating between two accumulators, then
 // commits and waits (bounded) for the tensor core to finish.
 template <int F>
-__global__ void __launch_bounds__(128, 1) k_probe_tc(int n, int tiles, int64_t iters,
+__global__ void __launch_bounds__(128, 1) k_probe_tc(int n, int tiles, int issuers, int64_t iters,
                                                     unsigned *err) {
   // `tiles` operand pairs: A tile t at t * 4 KiB, B tile t after all A tiles
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar[4];
   __shared__ uint32_t tbase_sh;
   // small integer operands, as the split kernel's digits: the bytes 0x40
   // read as BF16 (0x4040) are 3.0, read as E4M3 2.0
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(128, 1) k_probe_tc(int n, int tiles, int64_t i
     reinterpret_cast<uint32_t *>(smem)[i] = word;
   fence_proxy_async_smem();
   if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
+    for (int w = 0; w < 4; w++) mbar_init(&bar[w], 1);
     fence_mbar_init();
   }
   if (threadIdx.x < 32) {
@@ -177,7 +177,8 @@ __global__ void __launch_bounds__(128, 1) k_probe_tc(int n, int tiles, int64_t i
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tbase_sh;
-  if (threadIdx.x == 0) {
+  const int wi = threadIdx.x >> 5;  // issuing warps 0 .. issuers-1, lane 0 each
+  if ((threadIdx.x & 31) == 0 && wi < issuers) {
     // K-major, no swizzle: core matrices of 8 rows x 16 bytes, the two along
     // K 128 bytes apart, 8-row groups 256 bytes apart
     const uint32_t sa = smem_u32(smem);
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(128, 1) k_probe_tc(int n, int tiles, int64_t i
     for (int64_t it = 0; it < iters; it++) {
 #pragma unroll
       for (int u = 0; u < 4; u++) {
-        const uint32_t d = tbase + (uint32_t)((u & 1) * n);
+        const uint32_t d = tbase + (uint32_t)((2 * wi + (u & 1)) * n);
         const uint32_t acc = (it > 0 || u > 1) ? 1u : 0u;
         // descriptor start addresses are in 16-byte units
         const uint64_t at = ad + (uint64_t)(t * 256), bt = bd + (uint64_t)(t * n * 2);
@@ -199,8 +200,8 @@ __global__ void __launch_bounds__(128, 1) k_probe_tc(int n, int tiles, int64_t i
         t = t + 1 == tiles ? 0 : t + 1;
       }
     }
-    tc_commit(&bar);
-    if (!mbar_wait(&bar, 0)) set_err(err, DERR_TIMEOUT);
+    tc_commit(&bar[wi]);
+    if (!mbar_wait(&bar[wi], 0)) set_err(err, DERR_TIMEOUT);
   }
   tc_fence_before();
   __syncthreads();
@@ -330,10 +331,10 @@ extern "C" bsm_status bsm_probe_fp64(int kind, int64_t iters, double *flops, flo
   return st;
 }
 
-extern "C" bsm_status bsm_probe_tcgen05(int fmt, int n, int tiles, int64_t iters, double *flops,
-                                        float *ms, void *stream) {
+extern "C" bsm_status bsm_probe_tcgen05(int fmt, int n, int tiles, int issuers, int64_t iters,
+                                        double *flops, float *ms, void *stream) {
   if ((fmt != 0 && fmt != 1) || n < 16 || n > 256 || n % 16 || tiles < 1 || tiles > 8 ||
-      iters < 1 || !flops || !ms)
+      issuers < 1 || issuers > 4 || 2 * issuers * n > 512 || iters < 1 || !flops || !ms)
     return BSM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   // more shared memory than two CTAs could share: one CTA (one issuing
@@ -347,9 +348,10 @@ extern "C" bsm_status bsm_probe_tcgen05(int fmt, int n, int tiles, int64_t iters
   const int grid = sm_count();
   count_launch();
   bsm_status st =
-      timed_launch([&] { kern<<<grid, 128, smem, s>>>(n, tiles, iters, err); }, err, ms, s);
+      timed_launch([&] { kern<<<grid, 128, smem, s>>>(n, tiles, issuers, iters, err); }, err, ms,
+                   s);
   const double k = fmt == 0 ? 16 : 32;
-  *flops = (double)grid * (double)iters * 4 * 2.0 * 128 * n * k;
+  *flops = (double)grid * issuers * (double)iters * 4 * 2.0 * 128 * n * k;
   dev_free(err, s);
   return st;
 }

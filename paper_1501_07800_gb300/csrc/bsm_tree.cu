@@ -398,6 +398,7 @@ extern "C" bsm_status bsm_to_blocks(bsm_matrix M, int64_t *nblk_inout, int32_t *
   }
   // asynchronous host output needs page-locked buffers (checked before any work)
   if (on_device == 2 && !all_mapped) return BSM_ERR_INVALID_ARG;
+  const bool async_host = on_device == 2;
   cudaStream_t s = (cudaStream_t)stream;
   int64_t n = M->nblk;
   int bs = M->bs;
@@ -431,14 +432,40 @@ extern "C" bsm_status bsm_to_blocks(bsm_matrix M, int64_t *nblk_inout, int32_t *
     cleanup();
     return st;
   }
+  if (async_host) {
+    // gather on the device into a staging buffer, then one copy-engine
+    // transfer into the caller's page-locked buffers: the transfer occupies
+    // no SM, so later kernels on other streams run beside it.  Everything is
+    // freed stream-ordered after the copies; nothing waits here.
+    size_t bblk = sizeof(double) * bs * bs;
+    double *stage = nullptr;
+    int32_t *crd = nullptr;
+    if ((st = dev_alloc((void **)&stage, vals ? bblk * n : 16, s)) ||
+        (st = dev_alloc((void **)&crd, 8 * n, s))) {
+      dev_free(stage, s);
+      cleanup();
+      return st;
+    }
+    count_launch();
+    k_rowmajor_coords<<<nblocks_for(n, 256), 256, 0, s>>>(rms, 0, n, crd, crd + n);
+    if (brow) cudaMemcpyAsync(brow, crd, 4 * n, cudaMemcpyDeviceToHost, s);
+    if (bcol) cudaMemcpyAsync(bcol, crd + n, 4 * n, cudaMemcpyDeviceToHost, s);
+    if (vals) {
+      launch_gather_blocks(M->vals, sidx, stage, n, bs, s);
+      cudaMemcpyAsync(vals, stage, bblk * n, cudaMemcpyDeviceToHost, s);
+    }
+    dev_free(stage, s);
+    dev_free(crd, s);
+    cleanup();
+    return cuda_status(cudaGetLastError());
+  }
   if (all_mapped) {
     if (brow || bcol) {
       count_launch();
       k_rowmajor_coords<<<nblocks_for(n, 256), 256, 0, s>>>(rms, 0, n, mr, mc);
     }
     if (vals) launch_gather_blocks(M->vals, sidx, mv, n, bs, s);
-    // asynchronous: the temporaries are freed stream-ordered, after the gather
-    cudaError_t e = on_device == 2 ? cudaSuccess : cudaStreamSynchronize(s);
+    cudaError_t e = cudaStreamSynchronize(s);
     cleanup();
     return cuda_status(e == cudaSuccess ? cudaGetLastError() : e);
   }

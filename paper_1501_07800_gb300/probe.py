@@ -108,12 +108,13 @@ def fp64(kind: str = "dmma_m8n8k4", seconds: float = 1.0) -> dict:
     return {"tflops": work / ms / 1e9, "ms": ms, "iters": iters, "clocks": clk}
 
 
-def tcgen05(fmt: int, n: int, seconds: float = 0.5, tiles: int = 1) -> dict:
+def tcgen05(fmt: int, n: int, seconds: float = 0.5, tiles: int = 1, issuers: int = 1) -> dict:
     """tcgen05.mma rate at M = 128 and N = n (TFLOP/s); fmt 0 BF16, 1 E4M3;
-    consecutive instructions on `tiles` distinct operand pairs.  cycles: SM
-    cycles per instruction at the sampled clock."""
-    work, ms, iters, clk = _calibrated(lambda it: bsm.bsm_probe_tcgen05(fmt, n, it, tiles),
-                                       seconds, 20000)
+    consecutive instructions on `tiles` distinct operand pairs, `issuers`
+    issuing threads per SM.  cycles: SM cycles per instruction at the sampled
+    clock."""
+    work, ms, iters, clk = _calibrated(
+        lambda it: bsm.bsm_probe_tcgen05(fmt, n, it, tiles, issuers), seconds, 20000)
     out = {"tflops": work / ms / 1e9, "ms": ms, "iters": iters, "clocks": clk}
     import torch
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
@@ -153,6 +154,9 @@ def measure_all(seconds: float = 0.5) -> dict:
                                           for n in (32, 64, 128)}
     out["tcgen05_e4m3_distinct_tiles"] = {str(n): tcgen05(1, n, seconds, tiles=8)
                                           for n in (32, 64, 128)}
+    # issue rate: several threads issuing to their own accumulators
+    out["tcgen05_bf16_issuers"] = {f"n{n}_x{k}": tcgen05(0, n, seconds, tiles=8, issuers=k)
+                                   for n in (32, 64) for k in (1, 2, 4)}
     out["bulk_copy"] = [bulk_copy(stage_bytes=sb, stages=st)
                         for sb, st in ((16384, 4), (32768, 4), (36864, 4), (65536, 3))]
     return out

@@ -94,9 +94,10 @@ def test_argument_checks_before_any_device_work(lib):
     f, ms = ctypes.c_double(), ctypes.c_float()
     assert lib.bsm_probe_fp64(99, 1, ctypes.byref(f), ctypes.byref(ms), None) == -1
     assert lib.bsm_probe_fp64(0, 0, ctypes.byref(f), ctypes.byref(ms), None) == -1
-    assert lib.bsm_probe_tcgen05(2, 64, 1, 1, ctypes.byref(f), ctypes.byref(ms), None) == -1
-    assert lib.bsm_probe_tcgen05(0, 40, 1, 1, ctypes.byref(f), ctypes.byref(ms), None) == -1
-    assert lib.bsm_probe_tcgen05(0, 64, 9, 1, ctypes.byref(f), ctypes.byref(ms), None) == -1
+    assert lib.bsm_probe_tcgen05(2, 64, 1, 1, 1, ctypes.byref(f), ctypes.byref(ms), None) == -1
+    assert lib.bsm_probe_tcgen05(0, 40, 1, 1, 1, ctypes.byref(f), ctypes.byref(ms), None) == -1
+    assert lib.bsm_probe_tcgen05(0, 64, 9, 1, 1, ctypes.byref(f), ctypes.byref(ms), None) == -1
+    assert lib.bsm_probe_tcgen05(0, 128, 1, 3, 1, ctypes.byref(f), ctypes.byref(ms), None) == -1
     assert lib.bsm_probe_bulk_copy(1 << 20, 100, 4, ctypes.byref(f), ctypes.byref(ms),
                                    None) == -1
     assert lib.bsm_probe_bulk_copy(1 << 30, 65536, 8, ctypes.byref(f), ctypes.byref(ms),
