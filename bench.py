@@ -920,7 +920,9 @@ def run_decay_nodes(args):
     rmask[grows.to(dev)] = True
     cmask[gcols.to(dev)] = True
     t0 = time.time()
-    _, r, c, v = sd.decay(npts, bs, seed, dev, keep=(rmask, cmask), points=pts)
+    # the candidate blocks of the whole matrix (structure only), once
+    cand = sd.decay_blocks(npts, bs, seed, dev, points=pts)
+    _, r, c, v = sd.decay(npts, bs, seed, dev, keep=(rmask, cmask), points=pts, blocks=cand)
     lk, rk = rmask[r.long()], cmask[c.long()]
     left = synth.BlockCOO(n, n, bs, r[lk].cpu().numpy(), c[lk].cpu().numpy(), v[lk].cpu().numpy())
     right = synth.BlockCOO(n, n, bs, r[rk].cpu().numpy(), c[rk].cpu().numpy(), v[rk].cpu().numpy())
@@ -952,6 +954,10 @@ def run_decay_nodes(args):
 
     acc = {name: {"ms": 0.0, "num": 0.0, "den": 0.0, "presence_ok": True, "blocks": 0,
                   "c_blocks": 0} for name, _, _ in modes}
+    # output buffers for a node's C blocks (at most S^2), allocated once
+    ob = (torch.empty(S * S, dtype=torch.int32, device=dev),
+          torch.empty(S * S, dtype=torch.int32, device=dev),
+          torch.empty((S * S, bs, bs), dtype=torch.float64, device=dev))
     fp64 = {"ms": 0.0, "products": 0, "nodes": [], "num": 0.0, "den": 0.0, "numeric_ms": 0.0}
     total_products, gen_s, t_all = 0, 0.0, time.time()
     for ni, (r0, c0) in enumerate(nodes):
@@ -960,7 +966,7 @@ def run_decay_nodes(args):
         cm = torch.zeros(nbk, dtype=torch.bool, device=dev)
         rm[r0:r0 + S] = True
         cm[c0:c0 + S] = True
-        _, r, c, v = sd.decay(npts, bs, seed, dev, keep=(rm, cm), points=pts)
+        _, r, c, v = sd.decay(npts, bs, seed, dev, keep=(rm, cm), points=pts, blocks=cand)
         Ar = bsm.bsm_build(n, n, bs, r, c, v)
         del r, c, v
         # block products of the node by definition, from the stored blocks
@@ -1001,8 +1007,8 @@ def run_decay_nodes(args):
             nerr = dden = 0.0
             pres_ok = True
             if sel.any() and ncb:
-                bsm.bsm_release_memory()
-                cr, cc, cv = bsm.bsm_to_blocks(C, device=True)
+                bsm.bsm_to_blocks(C, device=True, out=ob)
+                cr, cc, cv = ob[0][:ncb], ob[1][:ncb], ob[2]
                 ck = cr.long() * nbk + cc.long()
                 want = torch.from_numpy(gkey[sel]).to(dev)
                 pos = torch.searchsorted(ck, want).clamp(max=ncb - 1)
@@ -1030,8 +1036,6 @@ def run_decay_nodes(args):
                 a["blocks"] += int(sel.sum())
                 a["c_blocks"] += ncb
         del Ar
-        bsm.bsm_release_memory()
-        torch.cuda.empty_cache()
         if ni % 10 == 0:
             log(f"node {ni + 1}/{len(nodes)} at ({r0}, {c0}): {node_products} block products; "
                 f"{time.time() - t_all:.0f} s")

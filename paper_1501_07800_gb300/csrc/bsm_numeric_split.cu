@@ -39,14 +39,16 @@
 // slices of the two sibling B blocks sit side by side (a pair slot), so each
 // A tile feeds both C blocks.
 //
-// Roles (576 threads, one CTA per SM, persistent over items):
+// Roles (608 threads, or 576 with one team; one CTA per SM, persistent):
 //   warp 16:       producer -- all lanes prefetch work descriptors and block
 //                  indices; lane 0 issues the 1-D bulk copies of the A and B
 //                  slices of each k-product into a ring of stages (mbarrier
 //                  complete_tx) and hands per-C-block descriptors to the other
 //                  roles through a shared-memory ring;
-//   warp 17 lane 0: issues the MMAs of each k-product, commits the stage back
-//                  to the producer and each finished flush to the epilogue;
+//   warps 17, 18 lane 0: issue the MMAs of each k-product of the items of
+//                  epilogue team 0 / 1 (one issuer with a single team),
+//                  commit the stage back to the producer and each finished
+//                  flush to the epilogue;
 //   warps 0-15:    epilogue, two teams of eight warps taking alternate C
 //                  blocks, each with its own TMEM accumulator buffer -- drain
 //                  TMEM (two warps per lane quadrant) into exact integer
@@ -476,11 +478,19 @@ __device__ __forceinline__ double split_to_double(int64_t hi, int64_t lo, int X)
 }
 
 constexpr int kEpiWarps = 16;                // epilogue warps (4 per lane quadrant)
+// One MMA-issuing thread per epilogue team, each in a warp of its own: a
+// thread issues tcgen05.mma instructions no faster than one per ~50 cycles
+// (measured), so a second issuer doubles the rate at which the short
+// instructions of this kernel (N = 32 or 64) reach the tensor core.
 constexpr int kProdWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
-constexpr int kThreads = (kEpiWarps + 2) * 32;
+constexpr int kMaxThreads = (kEpiWarps + 3) * 32;
+template <int NTEAM>
+constexpr int threads_for() {
+  return (kEpiWarps + 1 + NTEAM) * 32;
+}
 
 template <int BS, int S, int F, int NP>
-__global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
+__global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
   using C = Cfg<BS, S, F, NP>;
   constexpr int DPG = C::DPG;
   constexpr int G = C::G;
@@ -536,9 +546,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
     }
     for (int i = 0; i < kMeta; i++) {
       mbar_init(&meta_full[i], 1);
-      mbar_init(&meta_empty[i], kTeam + 1);  // MMA thread + the owning team
+      mbar_init(&meta_empty[i], kTeam + NTEAM);  // the MMA threads + the owning team
     }
-    mbar_init(&done, 1);
+    mbar_init(&done, NTEAM);
     abort_flag = 0;
     fence_mbar_init();
   }
@@ -687,11 +697,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
     if (lane == 0)
       for (int st = 0; st < C::NST; st++)
         if (pend[st]) mbar_wait(&full[st], ppar[st]);
-  } else if (warp == kMmaWarp) {
-    // ---------------------------------------------------------- MMA issuer
+  } else if (warp >= kMmaWarp && warp < kMmaWarp + NTEAM) {
+    // ---------------------------------------------------------- MMA issuers
+    // Thread b issues the MMAs of team b's items (items alternate between
+    // the teams).  Both read every work descriptor: the producer fills the
+    // ring in item order, so a product's stage follows from the count of all
+    // products before it.
     if (lane == 0) {
+      const int b = warp - kMmaWarp;
       uint32_t it = 0, q = 0;
-      uint32_t fcb0 = 0, fcb1 = 0;  // flushes issued for team 0 / 1
+      uint32_t fcb = 0;  // flushes issued for team b
       const uint32_t sbase = smem_u32(stages);
       for (;; q++) {
         int m = q % kMeta;
@@ -703,12 +718,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_numeric_split(SplitArgs P) {
         const int nk = meta[m].nk;
         mbar_arrive(&meta_empty[m]);
         if (nk < 0 || abort_flag) break;  // end marker
+        if ((int)(q % NTEAM) != b) {      // the other team's item: skip its stages
+          it += (uint32_t)nk;
+          continue;
+        }
         const FlushPlan fp = flush_plan(nk, P.flushk, P.flushk_wide);
         const int nfl = fp.nfl;
-        const int b = q % NTEAM;  // items alternate between the teams
         for (int f = 0; f < nfl && !abort_flag; f++) {
-          const uint32_t fb = b ? fcb1 : fcb0;
-          if (b) fcb1++; else fcb0++;
+          const uint32_t fb = fcb++;
           const uint32_t u = fb % NBUF, use = fb / NBUF;  // buffer and its use count
           if (!mbar_wait(&tempty[2 * b + u], (use & 1u) ^ 1u)) {
             set_err(P.err, DERR_TIMEOUT);
@@ -1027,7 +1044,7 @@ bsm_status launch_split(const SplitArgs &a, cudaStream_t s) {
   if (grid < 1) return BSM_OK;
   if (!a.fold) return BSM_ERR_INVALID_ARG;  // sized by split_fold_bytes: grid <= SM count
   count_launch();
-  k_numeric_split<BS, S, F, NP><<<(unsigned)grid, kThreads, C::SMEM, s>>>(a);
+  k_numeric_split<BS, S, F, NP><<<(unsigned)grid, threads_for<C::NTEAM>(), C::SMEM, s>>>(a);
   return cuda_status(cudaGetLastError());
 }
 

@@ -30,6 +30,12 @@ static void configure_pool_once(int dev) {
     // driver at every synchronisation
     uint64_t thr = ~0ull;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    // memory freed on one stream is never handed to an allocation on another
+    // stream by making that stream wait: work on different streams (batched
+    // products' workers, a download beside the next product) stays
+    // independent, at the price of a larger pool
+    int no = 0;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
   }
   done[dev] = true;
 }

@@ -80,7 +80,7 @@ def to_host(n: int, bs: int, brow, bcol, vals) -> BlockCOO:
 
 def decay(npoints: int, bs: int, seed: int, device, nfun: int = 5, alpha: float = 0.5,
           cutoff: float = 1e-6, density: float = 0.1, chunk_blocks: int | None = None,
-          cross: tuple[int, int] | None = None, keep=None, points=None):
+          cross: tuple[int, int] | None = None, keep=None, points=None, blocks=None):
     """Device tensors (n, brow, bcol, vals) of the decay-type matrix of
     synth.decay: points from synth.decay_points (host, recursive bisection
     order), blocks whose bounding boxes come within the cutoff radius, entries
@@ -92,6 +92,28 @@ def decay(npoints: int, bs: int, seed: int, device, nfun: int = 5, alpha: float 
     whose row is in row_mask or whose column is in col_mask (the operands of
     the C blocks of those rows and columns).  points: the host array of
     decay_points(npoints, seed, density), if already made."""
+    from . import decay_points
+
+    pts_np = decay_points(npoints, seed, density) if points is None else points
+    pts = torch.from_numpy(pts_np).to(device)
+    n = npoints * nfun
+    if blocks is None:
+        brow, bcol = decay_blocks(npoints, bs, seed, device, nfun, alpha, cutoff, density,
+                                  cross, keep, pts_np)
+    else:   # the candidate blocks of decay_blocks, filtered by `keep`
+        brow, bcol = blocks
+        if keep is not None:
+            sel = keep[0][brow] | keep[1][bcol]
+            brow, bcol = brow[sel], bcol[sel]
+    return n, brow.to(torch.int32), bcol.to(torch.int32), decay_values(
+        pts, brow, bcol, bs, n, npoints, seed, nfun, alpha, cutoff, chunk_blocks)
+
+
+def decay_blocks(npoints: int, bs: int, seed: int, device, nfun: int = 5, alpha: float = 0.5,
+                 cutoff: float = 1e-6, density: float = 0.1, cross=None, keep=None, points=None):
+    """Candidate blocks (brow, bcol: int64 device tensors, row-major) of the
+    decay-type matrix: block pairs whose point groups' bounding boxes come
+    within the cutoff radius (their entries may still all fall below it)."""
     import math
 
     from . import decay_points
@@ -106,8 +128,6 @@ def decay(npoints: int, bs: int, seed: int, device, nfun: int = 5, alpha: float 
     lo, hi = bp.min(1).values, bp.max(1).values
     rows, cols = [], []
     step = max(1, (1 << 24) // nbk)
-    if chunk_blocks is None:
-        chunk_blocks = max(1, (1 << 27) // (bs * bs))  # 2^27 entries per chunk
     if cross is not None:
         incross = torch.zeros(nbk, dtype=torch.bool, device=device)
         incross[cross[0]:cross[1]] = True
@@ -123,8 +143,18 @@ def decay(npoints: int, bs: int, seed: int, device, nfun: int = 5, alpha: float 
         bi, bj = torch.nonzero(near, as_tuple=True)
         rows.append(bi + r0)
         cols.append(bj)
-    brow = torch.cat(rows).to(torch.int64)
-    bcol = torch.cat(cols).to(torch.int64)
+    return torch.cat(rows).to(torch.int64), torch.cat(cols).to(torch.int64)
+
+
+def decay_values(pts, brow, bcol, bs: int, n: int, npoints: int, seed: int, nfun: int = 5,
+                 alpha: float = 0.5, cutoff: float = 1e-6, chunk_blocks: int | None = None):
+    """Entries s_ij exp(-alpha r_ij) of the given blocks (dropped below
+    `cutoff`), pts the device tensor of the points."""
+    device = pts.device
+    brow = brow.to(torch.int64)
+    bcol = bcol.to(torch.int64)
+    if chunk_blocks is None:
+        chunk_blocks = max(1, (1 << 27) // (bs * bs))  # 2^27 entries per chunk
     nb_ = brow.numel()
     vals = torch.empty((nb_, bs, bs), dtype=torch.float64, device=device)
     r = torch.arange(bs, dtype=torch.int64, device=device)
@@ -144,4 +174,4 @@ def decay(npoints: int, bs: int, seed: int, device, nfun: int = 5, alpha: float 
         v = torch.where(v.abs() < cutoff, torch.zeros_like(v), v)
         v = torch.where((gi < n) & (gj < n), v, torch.zeros_like(v))
         vals[t0:t1] = v
-    return n, brow.to(torch.int32), bcol.to(torch.int32), vals
+    return vals
