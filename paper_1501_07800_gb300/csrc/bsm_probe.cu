@@ -185,19 +185,33 @@ __global__ void __launch_bounds__(128, 1) k_probe_tc(int n, int tiles, int issue
     const uint64_t ad = smem_desc(sa, 128, 256);
     const uint64_t bd = smem_desc(sa + tiles * 4096, 128, 256);
     const uint32_t idesc = F == 0 ? idesc_bf16_f32(128, n) : idesc_e4m3_f32(128, n);
-    int t = 0;
-    for (int64_t it = 0; it < iters; it++) {
+    if (tiles == 1) {  // one operand pair: nothing computed between instructions
+      for (int64_t it = 0; it < iters; it++) {
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const uint32_t d = tbase + (uint32_t)((2 * wi + (u & 1)) * n);
-        const uint32_t acc = (it > 0 || u > 1) ? 1u : 0u;
-        // descriptor start addresses are in 16-byte units
-        const uint64_t at = ad + (uint64_t)(t * 256), bt = bd + (uint64_t)(t * n * 2);
-        if (F == 0)
-          tc_mma_bf16(d, at, bt, idesc, acc);
-        else
-          tc_mma_f8(d, at, bt, idesc, acc);
-        t = t + 1 == tiles ? 0 : t + 1;
+        for (int u = 0; u < 4; u++) {
+          const uint32_t d = tbase + (uint32_t)((2 * wi + (u & 1)) * n);
+          const uint32_t acc = (it > 0 || u > 1) ? 1u : 0u;
+          if (F == 0)
+            tc_mma_bf16(d, ad, bd, idesc, acc);
+          else
+            tc_mma_f8(d, ad, bd, idesc, acc);
+        }
+      }
+    } else {
+      int t = 0;
+      for (int64_t it = 0; it < iters; it++) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const uint32_t d = tbase + (uint32_t)((2 * wi + (u & 1)) * n);
+          const uint32_t acc = (it > 0 || u > 1) ? 1u : 0u;
+          // descriptor start addresses are in 16-byte units
+          const uint64_t at = ad + (uint64_t)(t * 256), bt = bd + (uint64_t)(t * n * 2);
+          if (F == 0)
+            tc_mma_bf16(d, at, bt, idesc, acc);
+          else
+            tc_mma_f8(d, at, bt, idesc, acc);
+          t = t + 1 == tiles ? 0 : t + 1;
+        }
       }
     }
     tc_commit(&bar[wi]);

@@ -157,6 +157,8 @@ def measure_all(seconds: float = 0.5) -> dict:
     # issue rate: several threads issuing to their own accumulators
     out["tcgen05_bf16_issuers"] = {f"n{n}_x{k}": tcgen05(0, n, seconds, tiles=8, issuers=k)
                                    for n in (32, 64) for k in (1, 2, 4)}
+    out["tcgen05_e4m3_issuers"] = {f"n{n}_x{k}": tcgen05(1, n, seconds, tiles=8, issuers=k)
+                                   for n in (32, 64) for k in (1, 2)}
     out["bulk_copy"] = [bulk_copy(stage_bytes=sb, stages=st)
                         for sb, st in ((16384, 4), (32768, 4), (36864, 4), (65536, 3))]
     return out
