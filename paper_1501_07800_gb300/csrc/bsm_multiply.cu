@@ -1,5 +1,6 @@
 // C = A*B: symbolic phase, numeric phase, exact-zero block removal, C levels.
 #include <cstring>
+#include <algorithm>
 #include <condition_variable>
 #include <functional>
 #include <mutex>
@@ -545,10 +546,147 @@ static bsm_status parallel_products(int n, cudaStream_t s, F f) {
   return st;
 }
 
-// Products of one block size: the symbolic phases (concurrently, one host
-// thread and stream per worker), then one persistent numeric launch over all
-// their C blocks in longest-first order, then zero removal and level build
-// per product (concurrently again).
+// ------------------------------------------- one symbolic pass for a batch
+// The operands of all products are placed on the diagonal of one quadtree:
+// product i's matrices at block offset i * 2^lmax in both coordinates (lmax:
+// the largest operand depth), so that their keys are the products' own keys
+// with the product index, Morton-spread, in the bits above 2 lmax.  The plain
+// level-by-level expansion of this pair of block-diagonal matrices then pairs
+// every product's nodes in the same launches (the nodes of different
+// products meet only as NIL pairs and are never expanded), and its leaf task
+// list is every product's, in product order.
+
+__global__ void k_offset_keys(const uint64_t *__restrict__ src, int64_t n, uint64_t add,
+                              uint64_t *__restrict__ dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i] + add;  // no carry: the local keys are below 4^lmax
+}
+
+// First C block and first product of every product i <= n in the combined
+// list (binary search for the product's first key).
+__global__ void k_product_bounds(const uint64_t *__restrict__ ckeys, int64_t nc,
+                                 const int32_t *__restrict__ seg, int n, int lmax,
+                                 int64_t *__restrict__ cb, int64_t *__restrict__ tb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  const uint64_t lo = i < n ? morton_key((uint64_t)i, (uint64_t)i) << (2 * lmax) : ~0ull;
+  int64_t a = 0, b = nc;
+  while (a < b) {
+    const int64_t m = (a + b) / 2;
+    if (ckeys[m] < lo) a = m + 1; else b = m;
+  }
+  cb[i] = a;
+  tb[i] = seg[a];
+}
+
+// Back to each product's own numbering: C keys without the product bits, A and
+// B block indices relative to the product's first block.
+__global__ void k_localize(uint64_t *__restrict__ ckeys, const int32_t *__restrict__ seg,
+                           int32_t *__restrict__ ta, int32_t *__restrict__ tb, int64_t nc,
+                           int lmax, const int64_t *__restrict__ aoff,
+                           const int64_t *__restrict__ boff) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const uint64_t k = ckeys[c];
+  const int p = (int)morton_compact(k >> (2 * lmax + 1));
+  ckeys[c] = k & ((1ull << (2 * lmax)) - 1);
+  const int32_t da = (int32_t)aoff[p], db = (int32_t)boff[p];
+  for (int32_t t = seg[c]; t < seg[c + 1]; t++) {
+    ta[t] -= da;
+    tb[t] -= db;
+  }
+}
+
+// The symbolic phase of the products idx[0..n) of one block size in one pass.
+// On success sym[i] describe product i: nc, nt and ckeys its own (ckeys an
+// allocation of its own), seg a view into the combined list (its entries
+// index the combined ta / tb, which hold the product's own block indices);
+// `whole` owns the combined seg / ta / tb (freed by the caller after the
+// numeric phase) and *bound is the length of the combined ta / tb.
+static bsm_status batched_symbolic(const std::vector<int> &idx, const bsm_matrix *A,
+                                   const bsm_matrix *B, std::vector<SymbolicResult> &sym,
+                                   SymbolicResult *whole, int64_t *bound, cudaStream_t s) {
+  const int n = (int)idx.size();
+  const int bs = A[idx[0]]->bs;
+  int lmax = 0;
+  int64_t na = 0, nb = 0;
+  std::vector<int64_t> aoff(n + 1, 0), boff(n + 1, 0);
+  for (int i = 0; i < n; i++) {
+    const bsm_matrix a = A[idx[i]], b = B[idx[i]];
+    lmax = std::max(lmax, std::max(a->L, b->L));
+    aoff[i] = na;
+    boff[i] = nb;
+    na += a->nblk;
+    nb += b->nblk;
+  }
+  aoff[n] = na;
+  boff[n] = nb;
+  const int lsup = lmax + ceil_log2_i64(n);
+  if (lsup > BSM_MAXH || na > INT32_MAX || nb > INT32_MAX) return BSM_ERR_UNSUPPORTED;
+  const int64_t side = (int64_t)n << lmax;  // blocks per side of the combined matrices
+  bsm_matrix SA = new_matrix_shell(side * bs, side * bs, bs, lsup);
+  bsm_matrix SB = new_matrix_shell(side * bs, side * bs, bs, lsup);
+  bsm_status st = BSM_OK;
+  auto keys_of = [&](bsm_matrix S, int64_t tot, bool left) -> bsm_status {
+    BSM_TRY(dev_alloc((void **)&S->keys, 8 * (tot > 0 ? tot : 1), s));
+    S->owned.push_back(S->keys);
+    for (int i = 0; i < n; i++) {
+      const bsm_matrix M = left ? A[idx[i]] : B[idx[i]];
+      if (M->nblk == 0) continue;
+      const uint64_t add = morton_key((uint64_t)i, (uint64_t)i) << (2 * lmax);
+      count_launch();
+      k_offset_keys<<<grid_for(M->nblk, 256), 256, 0, s>>>(M->keys, M->nblk, add,
+                                                            S->keys + (left ? aoff[i] : boff[i]));
+    }
+    S->nblk = tot;
+    return build_levels(S, s);
+  };
+  st = keys_of(SA, na, true);
+  if (st == BSM_OK) st = keys_of(SB, nb, false);
+  if (st == BSM_OK) st = symbolic_multiply(SA, SB, whole, s);
+  free_matrix_shell(SA, s);
+  free_matrix_shell(SB, s);
+  if (st != BSM_OK) return st;
+  *bound = whole->nt;
+  int64_t *dv = nullptr;  // [cb (n+1) | tb (n+1) | aoff (n+1) | boff (n+1)]
+  BSM_TRY(dev_alloc((void **)&dv, 8 * 4 * (n + 1), s));
+  int64_t *h = (int64_t *)host_scratch().get(8 * 4 * (n + 1));
+  if (!h) st = BSM_ERR_OOM;
+  if (st == BSM_OK) {
+    memcpy(h + 2 * (n + 1), aoff.data(), 8 * (n + 1));
+    memcpy(h + 3 * (n + 1), boff.data(), 8 * (n + 1));
+    cudaMemcpyAsync(dv + 2 * (n + 1), h + 2 * (n + 1), 16 * (n + 1), cudaMemcpyHostToDevice, s);
+    count_launch(2);
+    k_product_bounds<<<grid_for(n + 1, 128), 128, 0, s>>>(whole->ckeys, whole->nc, whole->seg, n,
+                                                          lmax, dv, dv + (n + 1));
+    if (whole->nc > 0)
+      k_localize<<<grid_for(whole->nc, 256), 256, 0, s>>>(whole->ckeys, whole->seg, whole->ta,
+                                                          whole->tb, whole->nc, lmax,
+                                                          dv + 2 * (n + 1), dv + 3 * (n + 1));
+    cudaMemcpyAsync(h, dv, 16 * (n + 1), cudaMemcpyDeviceToHost, s);
+    st = cuda_status(cudaStreamSynchronize(s));  // the host copy of aoff/boff is reused below
+  }
+  dev_free(dv, s);
+  for (int i = 0; i < n && st == BSM_OK; i++) {
+    SymbolicResult &r = sym[i];
+    r = SymbolicResult();
+    r.nc = h[i + 1] - h[i];
+    r.nt = h[(n + 1) + i + 1] - h[(n + 1) + i];
+    r.seg = whole->seg + h[i];
+    r.ta = whole->ta;
+    r.tb = whole->tb;
+    r.H = whole->H;
+    if (r.nc == 0) continue;
+    if ((st = dev_alloc((void **)&r.ckeys, 8 * r.nc, s)) != BSM_OK) break;
+    cudaMemcpyAsync(r.ckeys, whole->ckeys + h[i], 8 * r.nc, cudaMemcpyDeviceToDevice, s);
+  }
+  return st;
+}
+
+// Products of one block size: one symbolic pass over all of them, then one
+// persistent numeric launch over all their C blocks in longest-first order,
+// then zero removal and level build per product (concurrently, one host
+// thread and stream per worker).
 static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A,
                                 const bsm_matrix *B, bsm_matrix *C, int prec, int slices,
                                 cudaStream_t s) {
@@ -563,8 +701,13 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
   std::vector<void *> owned;
   unsigned *err = nullptr;
   bsm_status st = BSM_OK;
+  SymbolicResult whole;  // the group's combined task list (owns seg / ta / tb)
+  int64_t bound = 0;     // its length: the extent of ta / tb for every product
+  bool views = false;    // sym[i].seg / ta / tb point into `whole`
   auto cleanup = [&](bool keep_results) {
+    free_symbolic(&whole, s);
     for (int i = 0; i < n; i++) {
+      if (views) sym[i].seg = sym[i].ta = sym[i].tb = nullptr;
       free_symbolic(&sym[i], s);
       if (!keep_results) {
         if (shells[i]) free_matrix_shell(shells[i], s);
@@ -575,9 +718,18 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
     for (void *p : owned) dev_free(p, s);
     dev_free(err, s);
   };
-  st = parallel_products(n, s, [&](int i, cudaStream_t ws) {
-    return symbolic_multiply(A[idx[i]], B[idx[i]], &sym[i], ws);
-  });
+  // one symbolic pass over the whole group; sym[i].seg / ta / tb are views
+  // into `whole`, which owns them.  A group whose combined expansion exceeds
+  // 32-bit pair indices at some level falls back to one pass per product.
+  st = batched_symbolic(idx, A, B, sym, &whole, &bound, s);
+  views = whole.seg != nullptr;  // the products' views exist (even if a later step failed)
+  if (st == BSM_ERR_UNSUPPORTED && !views) {
+    free_symbolic(&whole, s);
+    for (int i = 0; i < n; i++) free_symbolic(&sym[i], s);
+    st = parallel_products(n, s, [&](int i, cudaStream_t ws) {
+      return symbolic_multiply(A[idx[i]], B[idx[i]], &sym[i], ws);
+    });
+  }
   for (int i = 0; i < n && st == BSM_OK; i++) {
     bsm_matrix a = A[idx[i]], b = B[idx[i]];
     if (sym[i].nc > 0xFFFFFFFFFFll) st = BSM_ERR_UNSUPPORTED;
@@ -605,6 +757,7 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
   std::vector<int32_t *> bslot(n, nullptr);
   for (int i = 0; i < n && st == BSM_OK; i++) {
     h[i] = make_desc(A[idx[i]], B[idx[i]], sym[i], cv[i], nz[i]);
+    if (views) h[i].nt = bound;  // seg entries index the combined ta / tb
     if (prec == BSM_FP64 || sym[i].nc == 0) continue;
     if (np == 2) {
       st = split_pairs_prepare(A[idx[i]], B[idx[i]], sym[i], slices, h[i], &bslot[i], owned, s);
