@@ -959,7 +959,7 @@ def run_decay_nodes(args):
           torch.empty(S * S, dtype=torch.int32, device=dev),
           torch.empty((S * S, bs, bs), dtype=torch.float64, device=dev))
     fp64 = {"ms": 0.0, "products": 0, "nodes": [], "num": 0.0, "den": 0.0, "numeric_ms": 0.0}
-    total_products, gen_s, t_all = 0, 0.0, time.time()
+    total_products, gen_s, t_all, prod_s = 0, 0.0, time.time(), 0.0
     for ni, (r0, c0) in enumerate(nodes):
         tg = time.time()
         rm = torch.zeros(nbk, dtype=torch.bool, device=dev)
@@ -969,6 +969,9 @@ def run_decay_nodes(args):
         _, r, c, v = sd.decay(npts, bs, seed, dev, keep=(rm, cm), points=pts, blocks=cand)
         Ar = bsm.bsm_build(n, n, bs, r, c, v)
         del r, c, v
+        # the generator's memory back to the driver; the library keeps its own
+        # pool (its peak is reached at the first node and then reused)
+        torch.cuda.empty_cache()
         # block products of the node by definition, from the stored blocks
         nb_ = Ar.nblk
         sr = torch.empty(max(nb_, 1), dtype=torch.int32, device=dev)
@@ -1003,6 +1006,7 @@ def run_decay_nodes(args):
                 e1.record(stream)
                 torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
+            prod_s += ms / 1e3
             ncb = bsm.bsm_info(C)[3]
             nerr = dden = 0.0
             pres_ok = True
@@ -1038,7 +1042,7 @@ def run_decay_nodes(args):
         del Ar
         if ni % 10 == 0:
             log(f"node {ni + 1}/{len(nodes)} at ({r0}, {c0}): {node_products} block products; "
-                f"{time.time() - t_all:.0f} s")
+                f"{time.time() - t_all:.0f} s (operands {gen_s:.0f} s, products {prod_s:.0f} s)")
     flops_total = metrics.block_flops(bs, total_products)
     out = {"workload": f"decay A*A, {npts} points (N={n}), bs {bs}, whole product node by node "
                        f"({len(nodes)} quadtree nodes of C of side {S} blocks)",

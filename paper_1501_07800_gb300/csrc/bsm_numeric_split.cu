@@ -477,6 +477,25 @@ __device__ __forceinline__ double split_to_double(int64_t hi, int64_t lo, int X)
   return split_to_double_slow(hi, lo, T, X);
 }
 
+// Bounded wait until the shared counter reaches `want` (or an abort); the
+// reads after it see the writes made before the counter's update.
+__device__ __forceinline__ bool wait_issued(volatile uint32_t *cnt, uint32_t want,
+                                            volatile int *abort) {
+  if (*cnt >= want) {
+    __threadfence_block();
+    return true;
+  }
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    __nanosleep(32);
+    if (*cnt >= want) {
+      __threadfence_block();
+      return true;
+    }
+    if (*abort || globaltimer_ns() - t0 > BSM_WAIT_NS) return false;
+  }
+}
+
 constexpr int kEpiWarps = 16;                // epilogue warps (4 per lane quadrant)
 // One MMA-issuing thread per epilogue team, each in a warp of its own: a
 // thread issues tcgen05.mma instructions no faster than one per ~50 cycles
@@ -525,6 +544,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
   __shared__ uint32_t tmem_base_sh;
   __shared__ int warp_any[2][2][16];  // [team][block of the item][warp]
   __shared__ volatile int abort_flag;
+  // products whose stage fill the producer has issued (two MMA issuers: a
+  // stage's next fill may belong to either, so an issuer first waits until
+  // its product's fill was issued -- only then does the stage's full barrier
+  // stand at that fill's phase, and its parity test cannot be passed by the
+  // stage's previous, still incomplete, phase)
+  __shared__ volatile uint32_t issued;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t *stages = smem;
@@ -550,6 +575,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
     }
     mbar_init(&done, NTEAM);
     abort_flag = 0;
+    issued = 0;
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -680,6 +706,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
                 bulk_g2s(sa + (DPG - 1) * C::SLICE, asl + (int64_t)aa * BYTES, BYTES, &full[st]);
                 bulk_g2s(sb, bsl + (int64_t)bb * BYTES_B, BYTES_B, &full[st]);
               }
+              if (NTEAM > 1) {
+                __threadfence_block();
+                issued = it + 1;
+              }
             }
           }
           if (!__shfl_sync(0xffffffffu, okc, 0)) {
@@ -736,6 +766,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
           int jend = min(nk, (f + 1) * fp.fk);
           for (int j = f * fp.fk; j < jend; j++, it++) {
             int st = it % C::NST;
+            if (NTEAM > 1 && !wait_issued(&issued, it + 1, &abort_flag)) {
+              set_err(P.err, DERR_TIMEOUT);
+              abort_flag = 1;
+              break;
+            }
             if (!mbar_wait(&full[st], (it / C::NST) & 1u)) {
               set_err(P.err, DERR_TIMEOUT);
               abort_flag = 1;
