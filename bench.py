@@ -390,9 +390,12 @@ def run_gpu(args):
     roofline["traffic"] = recorded_traffic("k_numeric_fp64", FP64_SOURCES)
 
     # split-precision mode on the same inputs, same timing protocol
-    split = None
+    split = split6 = None
     if not args.no_split and args.mode == "fp64":
         split = run_split(bsm, torch, ga, gb, args, stream, flops, triples, A, B, rank)
+        # the fewest BF16 slices that keep the error below 1e-11 on this product
+        split6 = run_split(bsm, torch, ga, gb, args, stream, flops, triples, A, B, rank,
+                           slices=6)
 
     line = None
     if rank == 0:
@@ -409,6 +412,8 @@ def run_gpu(args):
                 "roofline": roofline, "gpu_launches": launches, "clocks": clk}
         if split is not None:
             line["split_bf16"] = split
+        if split6 is not None:
+            line["split_bf16x6"] = split6
 
     # end to end through the public API with host buffers (pinned)
     if not args.no_e2e:
