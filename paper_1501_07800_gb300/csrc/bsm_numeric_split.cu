@@ -90,7 +90,11 @@ constexpr float kMagicF = 12582912.0f;
 // NP: C blocks per work item.  1: one C block (N = bs per MMA), two epilogue
 // teams.  2: a pair of sibling C blocks (I, 2y), (I, 2y+1) sharing every A
 // tile (N = 2 bs per MMA, half the A-operand traffic per output), one team.
-template <int BS, int S, int F, int NP = 1>
+// NQ (with NP = 1): up to NQ C blocks of short product lists per work item,
+// each list multiplied into its own TMEM columns, drained and combined in one
+// epilogue pass (grouped items: the per-item work of every role shared by NQ
+// C blocks of 16 x 16).
+template <int BS, int S, int F, int NP = 1, int NQ = 1>
 struct Cfg {
   static constexpr int DPG = 128 / BS;                       // diagonals per group
   static constexpr int G = (S + DPG - 1) / DPG;              // diagonal groups
@@ -99,10 +103,12 @@ struct Cfg {
   static constexpr int BSLOTS = NP * S;                      // B slices (a pair interleaved)
   static constexpr int STAGE = (ASLOTS + BSLOTS) * SLICE;
   static constexpr int NTEAM = NP == 2 ? 1 : 2;              // epilogue teams
-  static constexpr int CROW = NP * BS + 4;                   // padded int32 row (combine)
+  static constexpr int NW = NP * BS * NQ;                    // output columns of an item
+  static constexpr int CROW = NW + 4;                        // padded int32 row (combine)
   static constexpr int COMB = S * BS * CROW * 4;             // combine buffer bytes (per team)
   // ring depth: up to 4 (bs 32) / 8 (bs 16) stages within 227 KiB of shared
-  // memory, 8 KiB of it left for the static barriers and descriptor ring
+  // memory, 8 KiB of it left for the static barriers and descriptor ring (16
+  // stages at bs 16 measured slower than 8)
   static constexpr int BUDGET = 227 * 1024 - 8 * 1024 - NTEAM * COMB;
   static constexpr int NSTMAX = BS == 32 ? (F ? 6 : 4) : 8;
   static constexpr int NST = BUDGET / STAGE < NSTMAX ? BUDGET / STAGE : NSTMAX;
@@ -301,6 +307,10 @@ inline bool pair_compiled(int bs, int fmt, int slices) {
   return bs == 32 && (slices == 4 || slices == 6 || slices == 8 || slices == 12);
 }
 
+inline bool group_compiled(int bs, int fmt, int slices) {
+  return bs == 16 && fmt == 0 && slices >= 3 && slices <= 8;
+}
+
 // Slice counts with a compiled kernel: 1..8 for BF16, {2,3,4,6,8,12} for E4M3.
 inline bool spec_compiled(int fmt, int slices) {
   if (fmt == 0) return slices >= 1 && slices <= 8;
@@ -408,20 +418,20 @@ __device__ __forceinline__ int32_t f32_int_exact(uint32_t b) {
   return (b >> 31) ? -mag : mag;
 }
 
-// Per-C-block work descriptor handed from the producer warp to the MMA thread
+// Per-item work descriptor handed from the producer warp to the MMA threads
 // and the epilogue through a shared-memory ring.
-// The exponent arrays are read with 16-byte vector loads: keep them first in
-// a 16-byte aligned struct whose size is a multiple of 16.
+constexpr int kSub = 4;  // most C blocks of a work item
 struct __align__(16) Meta {
-  int64_t c;            // C block index within its product (pairs: the even sibling, or -1)
-  int64_t c1;           // pairs: the odd sibling, or -1
+  int64_t c[kSub];      // C block index within its product of each of the item's
+                        // C blocks (pairs: even, odd sibling), -1: absent
   double *cv;           // the product's C blocks
   int32_t *nz;          // the product's nonzero flags
   const int *rowexp;    // the product's row / column scale exponents
   const int *colexp;
-  int32_t bi, bj;       // block row and block column of the (even) C block
-  int32_t nk;
-  int32_t pad[1];
+  int32_t bi[kSub], bj[kSub];  // block row and block column of each C block
+  int32_t nkq[kSub];    // grouped items: block products of each C block
+  int32_t nk;           // block products of the item (all its lists)
+  int32_t nq;           // grouped items: lists multiplied one after another; else 1
 };
 static_assert(sizeof(Meta) % 16 == 0, "Meta alignment");
 constexpr int kMeta = 8;
@@ -508,15 +518,18 @@ constexpr int threads_for() {
   return (kEpiWarps + 1 + NTEAM) * 32;
 }
 
-template <int BS, int S, int F, int NP>
+template <int BS, int S, int F, int NP, int NQ>
 __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
-  using C = Cfg<BS, S, F, NP>;
+  using C = Cfg<BS, S, F, NP, NQ>;
   constexpr int DPG = C::DPG;
   constexpr int G = C::G;
   constexpr int NTEAM = C::NTEAM;
   constexpr int kTeamWarps = kEpiWarps / NTEAM;  // 8 (two teams) or 16 (one)
   constexpr int kTeam = kTeamWarps * 32;         // threads per epilogue team
-  constexpr int NB = NP * BS;                    // MMA N: output columns per item
+  constexpr int NB = NP * BS;                    // MMA N: output columns of one list
+  constexpr int NW = C::NW;                      // output columns of an item
+  constexpr int NSUB = NP * NQ;                  // C blocks of an item
+  static_assert(NSUB <= kSub && (NP == 1 || NQ == 1), "item shape");
   constexpr int BETA = Fmt<F>::BETA, TS = Fmt<F>::TSPLIT;
   // one narrow flush of at most kFast block products: the diagonal sums' FP32
   // bit patterns go to shared memory as they are and are combined in wrapping
@@ -527,11 +540,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
   constexpr uint32_t IDESC2 = F == 0 ? idesc_bf16_f32(128, 2 * NB) : idesc_e4m3_f32(128, 2 * NB);
   constexpr uint32_t IDESC3 = F == 0 ? idesc_bf16_f32(128, 3 * NB) : idesc_e4m3_f32(128, 3 * NB);
   static_assert(G <= 3 && G * NB <= 256, "one MMA spans at most three groups, N <= 256");
-  // TMEM accumulators: each team owns NBUF buffers of G*NB columns, two when
-  // they fit in the 256 columns we allocate, so that the MMAs of an item's
-  // next flush run while the team drains the previous one
-  constexpr int NBUF = NTEAM * 2 * G * NB <= 256 ? 2 : 1;
-  constexpr int TCOLS = NTEAM * NBUF * G * NB;
+  // TMEM accumulators: each team owns NBUF buffers of NQ*G*NB columns (list
+  // q's group g at (q G + g) NB), two when they fit in the 256 columns we
+  // allocate, so that the MMAs of an item's next flush run while the team
+  // drains the previous one
+  constexpr int NBUF = NTEAM * 2 * NQ * G * NB <= 256 ? 2 : 1;
+  constexpr int TCOLS = NTEAM * NBUF * NQ * G * NB;
   static_assert(TCOLS <= 256, "TMEM columns");
   constexpr int NCOLS = TCOLS <= 32 ? 32 : (TCOLS <= 64 ? 64 : (TCOLS <= 128 ? 128 : 256));
   constexpr uint32_t BYTES = (uint32_t)S * C::SLICE;          // one A block's slices
@@ -542,7 +556,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
   __shared__ __align__(8) uint64_t meta_full[kMeta], meta_empty[kMeta];
   __shared__ Meta meta[kMeta];
   __shared__ uint32_t tmem_base_sh;
-  __shared__ int warp_any[2][2][16];  // [team][block of the item][warp]
+  __shared__ int warp_any[2][kSub][16];  // [team][C block of the item][warp]
   __shared__ volatile int abort_flag;
   // products whose stage fill the producer has issued (two MMA issuers: a
   // stage's next fill may belong to either, so an issuer first waits until
@@ -599,8 +613,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
     bool pend[C::NST] = {};
     uint32_t ppar[C::NST] = {};
     bool stop = false;
-    auto put_meta = [&](int64_t c, int64_t c1, int32_t bi, int32_t bj, int nk,
-                        const ProdDesc *pd) -> bool {
+    // one item's descriptor: its C blocks, their coordinates, its lists
+    struct ItemDesc {
+      int64_t c[kSub];
+      int32_t bi[kSub], bj[kSub], k0[kSub], nkq[kSub];
+      int nq, nk;
+    };
+    auto put_meta = [&](const ItemDesc &d, const ProdDesc *pd) -> bool {
       const int m = q % kMeta;
       int okw = 1;
       if (lane == 0) {
@@ -609,15 +628,19 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
           set_err(P.err, DERR_TIMEOUT);
           abort_flag = 1;
         } else {
-          meta[m].c = c;
-          meta[m].c1 = c1;
-          meta[m].bi = bi;
-          meta[m].bj = bj;
+#pragma unroll
+          for (int b = 0; b < kSub; b++) {
+            meta[m].c[b] = d.c[b];
+            meta[m].bi[b] = d.bi[b];
+            meta[m].bj[b] = d.bj[b];
+            meta[m].nkq[b] = d.nkq[b];
+          }
           meta[m].cv = pd ? pd->cv : nullptr;
           meta[m].nz = pd ? pd->nz : nullptr;
           meta[m].rowexp = pd ? pd->rowexp : nullptr;
           meta[m].colexp = pd ? pd->colexp : nullptr;
-          meta[m].nk = nk;
+          meta[m].nk = d.nk;
+          meta[m].nq = d.nq;
           mbar_arrive(&meta_full[m]);  // release: the descriptor is visible
         }
       }
@@ -625,6 +648,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
       q++;
       return okw != 0;
     };
+    // grouped items: C blocks of at most gmax products (one narrow flush on
+    // the fast combine path) of one product, consecutive in the work list
+    const int gmax = NQ > 1 ? min(P.flushk, kFast) : 0;
     // window of 32 consecutive products (ta, tb) of one product table entry
     int wp = -1;
     int32_t tw = 0, ta_w = 0, tb_w = 0;
@@ -661,23 +687,61 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
           e0 = ci;
         }
       }
-      for (int i = 0; i < n && !stop; i++) {
+      for (int i = 0; i < n && !stop;) {
         const int p = __shfl_sync(0xffffffffu, pi, i);
         const ProdDesc *pd = &P.prods[p];
-        const int64_t c = __shfl_sync(0xffffffffu, e0, i);
-        const int64_t c1 = __shfl_sync(0xffffffffu, e1, i);
-        const int32_t ibi = __shfl_sync(0xffffffffu, kbi, i);
-        const int32_t ibj = __shfl_sync(0xffffffffu, kbj, i);
-        const int32_t k0 = __shfl_sync(0xffffffffu, s0, i);
-        const int32_t nk = __shfl_sync(0xffffffffu, s1, i) - k0;
-        if (!put_meta(c, c1, ibi, ibj, nk, pd)) {
+        ItemDesc d;
+#pragma unroll
+        for (int b = 0; b < kSub; b++) {
+          d.c[b] = -1;
+          d.bi[b] = d.bj[b] = d.k0[b] = d.nkq[b] = 0;
+        }
+        d.nq = 1;
+        {
+          const int32_t k0 = __shfl_sync(0xffffffffu, s0, i);
+          d.k0[0] = k0;
+          d.nkq[0] = __shfl_sync(0xffffffffu, s1, i) - k0;
+          d.c[0] = __shfl_sync(0xffffffffu, e0, i);
+          d.bi[0] = __shfl_sync(0xffffffffu, kbi, i);
+          d.bj[0] = __shfl_sync(0xffffffffu, kbj, i);
+        }
+        if (NP == 2) {  // the pair's odd sibling: same row, next column
+          d.c[1] = __shfl_sync(0xffffffffu, e1, i);
+          d.bi[1] = d.bi[0];
+          d.bj[1] = d.bj[0] + 1;
+        }
+        if (NQ > 1 && d.nkq[0] >= 1 && d.nkq[0] <= gmax) {
+          // grouped item: the following items of the same product with short
+          // lists (every lane takes the same decisions)
+          while (d.nq < NQ && i + d.nq < n) {
+            const int j2 = i + d.nq;
+            const int p2 = __shfl_sync(0xffffffffu, pi, j2);
+            const int32_t k2 = __shfl_sync(0xffffffffu, s0, j2);
+            const int32_t n2 = __shfl_sync(0xffffffffu, s1, j2) - k2;
+            const int64_t c2 = __shfl_sync(0xffffffffu, e0, j2);
+            const int32_t bi2 = __shfl_sync(0xffffffffu, kbi, j2);
+            const int32_t bj2 = __shfl_sync(0xffffffffu, kbj, j2);
+            if (p2 != p || n2 < 1 || n2 > gmax) break;
+            d.c[d.nq] = c2;
+            d.bi[d.nq] = bi2;
+            d.bj[d.nq] = bj2;
+            d.k0[d.nq] = k2;
+            d.nkq[d.nq] = n2;
+            d.nq++;
+          }
+        }
+        d.nk = 0;
+        for (int b = 0; b < d.nq; b++) d.nk += d.nkq[b];
+        i += d.nq;
+        if (!put_meta(d, pd)) {
           stop = true;
           break;
         }
         const uint8_t *asl = pd->asl, *bsl = pd->bsl;
         const int64_t na = pd->na, nb = pd->nb, nt = pd->nt;
-        for (int j = 0; j < nk; j++, it++) {
-          const int32_t t = k0 + j;
+        for (int lq = 0; lq < d.nq && !stop; lq++)  // the item's lists in order
+        for (int j = 0; j < d.nkq[lq]; j++, it++) {
+          const int32_t t = d.k0[lq] + j;
           if (p != wp || t < tw || t >= tw + 32) {  // refill the window (loads stay below nt)
             wp = p;
             tw = t;
@@ -721,8 +785,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
     }
     // end markers: one for the MMA thread and each epilogue team (the MMA
     // thread stops at the first)
-    if (!stop)
-      for (int t = 0; t < NTEAM; t++) put_meta(-1, -1, 0, 0, -1, nullptr);
+    if (!stop) {
+      ItemDesc e;
+      for (int b = 0; b < kSub; b++) {
+        e.c[b] = -1;
+        e.bi[b] = e.bj[b] = e.k0[b] = e.nkq[b] = 0;
+      }
+      e.nq = 1;
+      e.nk = -1;
+      for (int t = 0; t < NTEAM; t++) put_meta(e, nullptr);
+    }
     // copies still in flight must land before the CTA exits
     if (lane == 0)
       for (int st = 0; st < C::NST; st++)
@@ -745,16 +817,66 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
           abort_flag = 1;
           break;
         }
-        const int nk = meta[m].nk;
+        // (single blocks and pairs: one list, known at compile time)
+        const int nk = meta[m].nk, nq = NQ > 1 ? meta[m].nq : 1;
+        int nkq[NQ];
+#pragma unroll
+        for (int x = 0; x < NQ; x++) nkq[x] = NQ > 1 ? meta[m].nkq[x] : nk;
         mbar_arrive(&meta_empty[m]);
         if (nk < 0 || abort_flag) break;  // end marker
         if ((int)(q % NTEAM) != b) {      // the other team's item: skip its stages
           it += (uint32_t)nk;
           continue;
         }
-        const FlushPlan fp = flush_plan(nk, P.flushk, P.flushk_wide);
-        const int nfl = fp.nfl;
-        for (int f = 0; f < nfl && !abort_flag; f++) {
+        // the MMAs of the next stage (one block product) into buffer u,
+        // list lq's columns; first: the flush's first product
+        auto stage_mmas = [&](uint32_t u, int lq, uint32_t first) -> bool {
+          const int st = it % C::NST;
+          if (NTEAM > 1 && !wait_issued(&issued, it + 1, &abort_flag)) return false;
+          if (!mbar_wait(&full[st], (it / C::NST) & 1u)) return false;
+          tc_fence_after();
+          // descriptors differ only in the start-address field (16-byte
+          // units, < 2^14 inside shared memory): build them once per stage
+          const uint32_t sa = sbase + st * C::STAGE;
+          const uint64_t ad0 = smem_desc(sa, C::LBO, C::SBO);
+          const uint64_t bd0 = smem_desc(sa + C::ASLOTS * C::SLICE, C::LBO, C::SBO);
+          // (g, t): Toeplitz A tile of group g at offset t times the nbk B
+          // slices of residue t, into groups g .. g + nbk - 1.  The first
+          // instruction (g = t = h = 0) spans every group and starts the
+          // accumulation of a flush.
+#pragma unroll
+          for (int g = 0; g < G; g++) {
+            const uint32_t dt = tbase + (uint32_t)((((b * NBUF + u) * NQ + lq) * G + g) * NB);
+#pragma unroll
+            for (int t = 0; t < DPG; t++) {
+              const int nbk = b_count(S, DPG, t) < G - g ? b_count(S, DPG, t) : G - g;
+              if (nbk <= 0 || g * DPG - t >= S) continue;  // B slices or A rows all zero
+              const uint32_t idesc = nbk == 1 ? IDESC1 : (nbk == 2 ? IDESC2 : IDESC3);
+#pragma unroll
+              for (int h = 0; h < BS / Fmt<F>::KPI; h++) {
+                // one instruction's K = two core matrices = 256 bytes
+                const uint64_t aoff = (uint64_t)(((DPG - 1 + g * DPG - t) * C::SLICE + h * 256) >> 4);
+                // B: positions b_off(t) .. + nbk - 1, each one block's slice
+                // or a pair's two slices side by side (N rows 0..bs-1 and
+                // bs..2bs-1 of each position)
+                const uint64_t boff =
+                    (uint64_t)((NP * b_off(S, DPG, t) * C::SLICE + h * 256) >> 4);
+                const uint32_t acc = (g | t | h) ? 1u : first;
+                if (F == 0)
+                  tc_mma_bf16(dt, ad0 + aoff, bd0 + boff, idesc, acc);
+                else
+                  tc_mma_f8(dt, ad0 + aoff, bd0 + boff, idesc, acc);
+              }
+            }
+          }
+          tc_commit(&empty[st]);  // stage reusable once these MMAs are done
+          it++;
+          return true;
+        };
+        // a grouped item is one flush: list lq into its own columns
+        const FlushPlan fp = nq > 1 ? FlushPlan{false, nk, 1, 1}
+                                    : flush_plan(nk, P.flushk, P.flushk_wide);
+        for (int f = 0; f < fp.nfl && !abort_flag; f++) {
           const uint32_t fb = fcb++;
           const uint32_t u = fb % NBUF, use = fb / NBUF;  // buffer and its use count
           if (!mbar_wait(&tempty[2 * b + u], (use & 1u) ^ 1u)) {
@@ -763,56 +885,20 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
             break;
           }
           tc_fence_after();
-          int jend = min(nk, (f + 1) * fp.fk);
-          for (int j = f * fp.fk; j < jend; j++, it++) {
-            int st = it % C::NST;
-            if (NTEAM > 1 && !wait_issued(&issued, it + 1, &abort_flag)) {
-              set_err(P.err, DERR_TIMEOUT);
-              abort_flag = 1;
-              break;
-            }
-            if (!mbar_wait(&full[st], (it / C::NST) & 1u)) {
-              set_err(P.err, DERR_TIMEOUT);
-              abort_flag = 1;
-              break;
-            }
-            tc_fence_after();
-            // descriptors differ only in the start-address field (16-byte
-            // units, < 2^14 inside shared memory): build them once per stage
-            const uint32_t sa = sbase + st * C::STAGE;
-            const uint64_t ad0 = smem_desc(sa, C::LBO, C::SBO);
-            const uint64_t bd0 = smem_desc(sa + C::ASLOTS * C::SLICE, C::LBO, C::SBO);
-            const uint32_t first = (j == f * fp.fk) ? 0u : 1u;
-            // (g, t): Toeplitz A tile of group g at offset t times the nbk B
-            // slices of residue t, into groups g .. g + nbk - 1.  The first
-            // instruction (g = t = h = 0) spans every group and starts the
-            // accumulation of a flush.
+          bool ok = true;
+          if (NQ > 1 && nq > 1) {
 #pragma unroll
-            for (int g = 0; g < G; g++) {
-              const uint32_t dt = tbase + (uint32_t)(((b * NBUF + u) * G + g) * NB);
-#pragma unroll
-              for (int t = 0; t < DPG; t++) {
-                const int nbk = b_count(S, DPG, t) < G - g ? b_count(S, DPG, t) : G - g;
-                if (nbk <= 0 || g * DPG - t >= S) continue;  // B slices or A rows all zero
-                const uint32_t idesc = nbk == 1 ? IDESC1 : (nbk == 2 ? IDESC2 : IDESC3);
-#pragma unroll
-                for (int h = 0; h < BS / Fmt<F>::KPI; h++) {
-                  // one instruction's K = two core matrices = 256 bytes
-                  const uint64_t aoff = (uint64_t)(((DPG - 1 + g * DPG - t) * C::SLICE + h * 256) >> 4);
-                  // B: positions b_off(t) .. + nbk - 1, each one block's slice
-                  // or a pair's two slices side by side (N rows 0..bs-1 and
-                  // bs..2bs-1 of each position)
-                  const uint64_t boff =
-                      (uint64_t)((NP * b_off(S, DPG, t) * C::SLICE + h * 256) >> 4);
-                  const uint32_t acc = (g | t | h) ? 1u : first;
-                  if (F == 0)
-                    tc_mma_bf16(dt, ad0 + aoff, bd0 + boff, idesc, acc);
-                  else
-                    tc_mma_f8(dt, ad0 + aoff, bd0 + boff, idesc, acc);
-                }
-              }
-            }
-            tc_commit(&empty[st]);  // stage reusable once these MMAs are done
+            for (int lq = 0; lq < NQ; lq++)
+              for (int j = 0; lq < nq && j < nkq[lq] && ok; j++)
+                ok = stage_mmas(u, lq, j == 0 ? 0u : 1u);
+          } else {
+            const int jend = min(nk, (f + 1) * fp.fk);
+            for (int j = f * fp.fk; j < jend && ok; j++)
+              ok = stage_mmas(u, 0, j == f * fp.fk ? 0u : 1u);
+          }
+          if (!ok) {
+            set_err(P.err, DERR_TIMEOUT);
+            abort_flag = 1;
           }
           tc_commit(&tfull[2 * b + u]);  // flush ready for the epilogue
         }
@@ -831,8 +917,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
     // the diagonals of each output element.  With two teams one team's
     // recombination overlaps the other team's drain and the MMAs.
     constexpr int HC = NB / (kTeamWarps / 4);       // 16 columns per warp at bs 32
-    constexpr int NG4 = NB * BS / 4;                // 4-column groups per item
+    constexpr int LG4 = NB * BS / 4;                // 4-column groups of one list
+    constexpr int NG4 = NQ * LG4;                   // ... of an item
     constexpr int GRP = (NG4 + kTeam - 1) / kTeam;  // combine: groups per thread
+    static_assert(NQ == 1 || G == 1, "grouped items: one diagonal group");
     const int team = warp / kTeamWarps, tw = warp % kTeamWarps, ttid = tid % kTeam;
     const int wq = tw & 3;
     const int row = wq * 32 + lane;       // TMEM lane = operand row
@@ -845,7 +933,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
     // nonzero flags of the team's previous item, written by thread 0 of the
     // team once the next item's first barrier shows every warp's flag
     int32_t *prev_nz = nullptr;
-    int64_t prev_c[2] = {-1, -1};
+    int64_t prev_c[NSUB];
+#pragma unroll
+    for (int x = 0; x < NSUB; x++) prev_c[x] = -1;
     for (uint32_t q = team;; q += NTEAM) {
       int m = q % kMeta;
       bool okm = mbar_wait(&meta_full[m], (q / kMeta) & 1u);
@@ -860,39 +950,58 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
       }
       if (ttid == 0 && prev_nz) {
 #pragma unroll
-        for (int b = 0; b < NP; b++) {
+        for (int x = 0; x < NSUB; x++) {
           int nzv = 0;
-          for (int w = 0; w < kTeamWarps; w++) nzv |= warp_any[team][b][w];
-          if (prev_c[b] >= 0) prev_nz[prev_c[b]] = nzv;
+          for (int w = 0; w < kTeamWarps; w++) nzv |= warp_any[team][x][w];
+          if (prev_c[x] >= 0) prev_nz[prev_c[x]] = nzv;
         }
       }
       // (the flags are rewritten only after the next barrier, which thread 0
       // reaches after reading them)
-      const int nk = meta[m].nk;
-      const int64_t cblk[2] = {meta[m].c, meta[m].c1};
+      const int nk = meta[m].nk, nq = NQ > 1 ? meta[m].nq : 1;
+      if (nk < 0) {  // end marker
+        mbar_arrive(&meta_empty[m]);
+        break;
+      }
+      int64_t cblk[NSUB];
+#pragma unroll
+      for (int x = 0; x < NSUB; x++) cblk[x] = meta[m].c[x];
       double *const cvp = meta[m].cv;
       int32_t *const nzp = meta[m].nz;
-      const int64_t crow = (int64_t)meta[m].bi * BS, ccol = (int64_t)meta[m].bj * BS;
       const int *const rowexp = meta[m].rowexp, *const colexp = meta[m].colexp;
-      mbar_arrive(&meta_empty[m]);
-      if (nk < 0) break;  // end marker
-      // scale exponents of this thread's output elements (thread handles
-      // item columns 4*(g4 % (NB/4)) .. +3 of row g4 / (NB/4), g4 = ttid + i
-      // kTeam; for a pair the columns continue into the odd sibling, whose
-      // block column follows), loaded here so that their latency hides behind
-      // the first flush
-      int erow[GRP];
+      // this thread's output elements: 4-column group g4 = ttid + i kTeam is
+      // list g4 / LG4, row rr and list columns cn .. cn + 3 of it; item column
+      // c4 = list * NB + cn lies in C block blk = c4 / BS of the item (a
+      // pair's odd sibling follows the even one), at its column cc.  The
+      // scale exponents are loaded here so that their latency hides behind
+      // the first flush.
+      int erow[GRP], oblk[GRP];
       int4 fcol[GRP];
 #pragma unroll
       for (int i = 0; i < GRP; i++) {
         const int g4 = min(ttid + i * kTeam, NG4 - 1);
-        erow[i] = rowexp[crow + g4 / (NB / 4)];
-        fcol[i] = *reinterpret_cast<const int4 *>(colexp + ccol + (g4 % (NB / 4)) * 4);
+        const int rem = g4 % LG4, rr = rem / (NB / 4);
+        const int c4 = (g4 / LG4) * NB + (rem % (NB / 4)) * 4, blk = c4 / BS;
+        int32_t bi = meta[m].bi[0], bj = meta[m].bj[0];
+#pragma unroll
+        for (int x = 1; x < NSUB; x++)
+          if (blk == x) {
+            bi = meta[m].bi[x];
+            bj = meta[m].bj[x];
+          }
+        oblk[i] = blk;
+        erow[i] = rowexp[(int64_t)bi * BS + rr];
+        fcol[i] = *reinterpret_cast<const int4 *>(colexp + (int64_t)bj * BS + c4 % BS);
       }
-      const FlushPlan fplan = flush_plan(nk, P.flushk, P.flushk_wide);
+      mbar_arrive(&meta_empty[m]);
+      // a grouped item is one narrow flush on the fast path (every list has
+      // at most kFast products)
+      const FlushPlan fplan = nq > 1 ? FlushPlan{false, nk, 1, 1}
+                                     : flush_plan(nk, P.flushk, P.flushk_wide);
       const int nfl = fplan.nfl, kf = fplan.kf;
       const bool wide = fplan.wide;
-      const bool fast = !wide && nk <= kFast;  // uniform over the team
+      const bool fast = nq > 1 || (!wide && nk <= kFast);  // uniform over the team
+      const int ng4 = nq * LG4;                            // the item's groups
       int64_t *const fold = P.fold + ((int64_t)blockIdx.x * 2 + team) * (NB * BS * 2);
       bool ok = true;
       // Every warp runs all nfl iterations (doing no work once `ok` is false)
@@ -908,45 +1017,49 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
         }
         if (ok) {
           tc_fence_after();
+          for (int lq = 0; lq < nq; lq++) {
 #pragma unroll
-          for (int g = 0; g < G; g++) {
-            uint32_t v[HC];
-            if constexpr (HC == 16)
-              tmem_ld16(tbase + lane_addr + (uint32_t)(((team * NBUF + fct % NBUF) * G + g) * NB + c0), v);
-            else
-              tmem_ld8(tbase + lane_addr + (uint32_t)(((team * NBUF + fct % NBUF) * G + g) * NB + c0), v);
-            tmem_ld_wait();
-            const int d = g * DPG + L;
-            if (d < S) {
-              // exact integer value of each FP32 sum (|D| < 2^22: magic add;
-              // wide flushes, |D| <= 2^24: from the bits)
-              int32_t *dst = tcomb + (d * BS + r) * C::CROW + c0;
+            for (int g = 0; g < G; g++) {
+              uint32_t v[HC];
+              const uint32_t col =
+                  (uint32_t)((((team * NBUF + fct % NBUF) * NQ + lq) * G + g) * NB + c0);
+              if constexpr (HC == 16)
+                tmem_ld16(tbase + lane_addr + col, v);
+              else
+                tmem_ld8(tbase + lane_addr + col, v);
+              tmem_ld_wait();
+              const int d = g * DPG + L;
+              if (d < S) {
+                // exact integer value of each FP32 sum (|D| < 2^22: magic add;
+                // wide flushes, |D| <= 2^24: from the bits)
+                int32_t *dst = tcomb + (d * BS + r) * C::CROW + lq * NB + c0;
 #pragma unroll
-              for (int x = 0; x < HC; x += 4) {
-                int4 val;
-                if (fast) {  // bit patterns of D + 1.5 2^23 (one flush)
-                  val = make_int4((int32_t)__float_as_uint(__uint_as_float(v[x]) + kMagicF),
-                                  (int32_t)__float_as_uint(__uint_as_float(v[x + 1]) + kMagicF),
-                                  (int32_t)__float_as_uint(__uint_as_float(v[x + 2]) + kMagicF),
-                                  (int32_t)__float_as_uint(__uint_as_float(v[x + 3]) + kMagicF));
-                } else if (!wide) {
-                  val = make_int4(
-                      (int32_t)(__float_as_uint(__uint_as_float(v[x]) + kMagicF) - kMagic),
-                      (int32_t)(__float_as_uint(__uint_as_float(v[x + 1]) + kMagicF) - kMagic),
-                      (int32_t)(__float_as_uint(__uint_as_float(v[x + 2]) + kMagicF) - kMagic),
-                      (int32_t)(__float_as_uint(__uint_as_float(v[x + 3]) + kMagicF) - kMagic));
-                } else {
-                  val = make_int4(f32_int_exact(v[x]), f32_int_exact(v[x + 1]),
-                                  f32_int_exact(v[x + 2]), f32_int_exact(v[x + 3]));
+                for (int x = 0; x < HC; x += 4) {
+                  int4 val;
+                  if (fast) {  // bit patterns of D + 1.5 2^23 (one flush)
+                    val = make_int4((int32_t)__float_as_uint(__uint_as_float(v[x]) + kMagicF),
+                                    (int32_t)__float_as_uint(__uint_as_float(v[x + 1]) + kMagicF),
+                                    (int32_t)__float_as_uint(__uint_as_float(v[x + 2]) + kMagicF),
+                                    (int32_t)__float_as_uint(__uint_as_float(v[x + 3]) + kMagicF));
+                  } else if (!wide) {
+                    val = make_int4(
+                        (int32_t)(__float_as_uint(__uint_as_float(v[x]) + kMagicF) - kMagic),
+                        (int32_t)(__float_as_uint(__uint_as_float(v[x + 1]) + kMagicF) - kMagic),
+                        (int32_t)(__float_as_uint(__uint_as_float(v[x + 2]) + kMagicF) - kMagic),
+                        (int32_t)(__float_as_uint(__uint_as_float(v[x + 3]) + kMagicF) - kMagic));
+                  } else {
+                    val = make_int4(f32_int_exact(v[x]), f32_int_exact(v[x + 1]),
+                                    f32_int_exact(v[x + 2]), f32_int_exact(v[x + 3]));
+                  }
+                  if (f % kf != 0) {
+                    const int4 old = *reinterpret_cast<const int4 *>(dst + x);
+                    val.x += old.x;
+                    val.y += old.y;
+                    val.z += old.z;
+                    val.w += old.w;
+                  }
+                  *reinterpret_cast<int4 *>(dst + x) = val;
                 }
-                if (f % kf != 0) {
-                  const int4 old = *reinterpret_cast<const int4 *>(dst + x);
-                  val.x += old.x;
-                  val.y += old.y;
-                  val.z += old.z;
-                  val.w += old.w;
-                }
-                *reinterpret_cast<int4 *>(dst + x) = val;
               }
             }
           }
@@ -955,14 +1068,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
         }
         if ((f + 1) % kf == 0 && f + 1 < nfl) {
           // the 32-bit sums are full: fold them into this thread's (hi, lo)
-          // pairs.  The barrier's OR makes `ok` uniform across the team.
+          // pairs (items of several flushes have one list: c4 = cn < NB).
+          // The barrier's OR makes `ok` uniform across the team.
           if (named_bar_or(bar_id, kTeam, !ok || abort_flag != 0)) {
             ok = false;
           } else {
 #pragma unroll
             for (int i = 0; i < GRP; i++) {
               const int g4 = ttid + i * kTeam;
-              if (NG4 % kTeam != 0 && g4 >= NG4) break;
+              if (g4 >= LG4) break;
               const int rr = g4 / (NB / 4), c4 = (g4 % (NB / 4)) * 4;
               int4 dv[S];
 #pragma unroll
@@ -992,19 +1106,21 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
         }
       }
       if (named_bar_or(bar_id, kTeam, !ok || abort_flag != 0)) break;
-      bool any[2] = {false, false};
+      uint32_t any = 0;  // bit x: C block x of the item has an entry != 0
       constexpr int XS = BETA * (S + 1);
 #pragma unroll
       for (int i = 0; i < GRP; i++) {
         const int g4 = ttid + i * kTeam;
-        if (NG4 % kTeam != 0 && g4 >= NG4) break;  // bs 16: part of the team idles here
-        const int rr = g4 / (NB / 4), c4 = (g4 % (NB / 4)) * 4;
-        const int blk = c4 / BS, cc = c4 % BS;     // C block of the item, its column
+        if (g4 >= ng4) break;  // bs 16: part of the team idles here
+        const int rem = g4 % LG4, rr = rem / (NB / 4);
+        const int c4 = (g4 / LG4) * NB + (rem % (NB / 4)) * 4, cc = c4 % BS;
+        const int blk = oblk[i];
         int4 dv[S];
 #pragma unroll
         for (int d = 0; d < S; d++)
           dv[d] = *reinterpret_cast<const int4 *>(tcomb + (d * BS + rr) * C::CROW + c4);
         double out[4];
+        bool nzq = false;
         if (kFast > 0 && fast) {
 #pragma unroll
           for (int x = 0; x < 4; x++) {
@@ -1017,7 +1133,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
             const int X = erow[i] + fx - XS;
             if (!int64_scaled_to_double(vv, X, out[x]))  // subnormal or overflow range
               out[x] = split_to_double_slow(vv >> TS, vv & ((1ll << TS) - 1), TS, X);
-            any[blk] |= nonzero_f64(out[x]);
+            nzq |= nonzero_f64(out[x]);
           }
         } else {
 #pragma unroll
@@ -1035,23 +1151,28 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
             }
             const int fx = x == 0 ? fcol[i].x : x == 1 ? fcol[i].y : x == 2 ? fcol[i].z : fcol[i].w;
             out[x] = split_to_double<TS>(hi, lo, erow[i] + fx - XS);
-            any[blk] |= nonzero_f64(out[x]);
+            nzq |= nonzero_f64(out[x]);
           }
         }
-        if (cblk[blk] >= 0) {  // a pair's absent sibling is computed as zero and dropped
-          double2 *dst = reinterpret_cast<double2 *>(cvp + cblk[blk] * (int64_t)BS * BS + rr * BS + cc);
+        int64_t cb = cblk[0];
+#pragma unroll
+        for (int x = 1; x < NSUB; x++)
+          if (blk == x) cb = cblk[x];
+        any |= (uint32_t)nzq << blk;
+        if (cb >= 0) {  // a pair's absent sibling is computed as zero and dropped
+          double2 *dst = reinterpret_cast<double2 *>(cvp + cb * (int64_t)BS * BS + rr * BS + cc);
           dst[0] = make_double2(out[0], out[1]);
           dst[1] = make_double2(out[2], out[3]);
         }
       }
 #pragma unroll
-      for (int b = 0; b < NP; b++) {
-        const bool a = __any_sync(0xffffffffu, any[b]);
-        if (lane == 0) warp_any[team][b][tw] = a;
+      for (int x = 0; x < NSUB; x++) {
+        const bool a = __any_sync(0xffffffffu, (any >> x) & 1u);
+        if (lane == 0) warp_any[team][x][tw] = a;
       }
       prev_nz = nzp;
-      prev_c[0] = cblk[0];
-      prev_c[1] = cblk[1];
+#pragma unroll
+      for (int x = 0; x < NSUB; x++) prev_c[x] = x < nq * NP ? cblk[x] : -1;
     }
   }
   __syncthreads();
@@ -1063,13 +1184,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
 
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-template <int BS, int S, int F, int NP>
+template <int BS, int S, int F, int NP, int NQ = 1>
 bsm_status launch_split(const SplitArgs &a, cudaStream_t s) {
-  using C = Cfg<BS, S, F, NP>;
+  using C = Cfg<BS, S, F, NP, NQ>;
   static std::atomic<uint64_t> attr{0};
   BSM_TRY(once_per_device(attr, [&] {
     return cuda_status(cudaFuncSetAttribute(
-        k_numeric_split<BS, S, F, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+        k_numeric_split<BS, S, F, NP, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
   }));
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -1079,7 +1200,7 @@ bsm_status launch_split(const SplitArgs &a, cudaStream_t s) {
   if (grid < 1) return BSM_OK;
   if (!a.fold) return BSM_ERR_INVALID_ARG;  // sized by split_fold_bytes: grid <= SM count
   count_launch();
-  k_numeric_split<BS, S, F, NP><<<(unsigned)grid, threads_for<C::NTEAM>(), C::SMEM, s>>>(a);
+  k_numeric_split<BS, S, F, NP, NQ><<<(unsigned)grid, threads_for<C::NTEAM>(), C::SMEM, s>>>(a);
   return cuda_status(cudaGetLastError());
 }
 
@@ -1089,6 +1210,8 @@ bsm_status launch_split_s(const SplitArgs &a, int fmt, int slices, int np, cudaS
   if (np == 1 && fmt == F && slices == S) return launch_split<BS, S, F, 1>(a, s);
 #define BSM_LP(F, S) \
   if (np == 2 && fmt == F && slices == S) return launch_split<BS, S, F, 2>(a, s);
+#define BSM_LG(F, S) \
+  if (np == 4 && fmt == F && slices == S) return launch_split<BS, S, F, 1, 4>(a, s);
   BSM_LS(0, 1) BSM_LS(0, 2) BSM_LS(0, 3) BSM_LS(0, 4) BSM_LS(0, 5) BSM_LS(0, 6) BSM_LS(0, 7)
   BSM_LS(0, 8)
   if constexpr (BS == 32) {
@@ -1098,9 +1221,11 @@ bsm_status launch_split_s(const SplitArgs &a, int fmt, int slices, int np, cudaS
   }
   if constexpr (BS == 16) {
     BSM_LP(0, 3) BSM_LP(0, 4) BSM_LP(0, 5) BSM_LP(0, 6) BSM_LP(0, 7) BSM_LP(0, 8)
+    BSM_LG(0, 3) BSM_LG(0, 4) BSM_LG(0, 5) BSM_LG(0, 6) BSM_LG(0, 7) BSM_LG(0, 8)
   }
 #undef BSM_LS
 #undef BSM_LP
+#undef BSM_LG
   return BSM_ERR_INVALID_ARG;
 }
 
@@ -1298,6 +1423,7 @@ bsm_status split_launch(int bs, int spec, const ProdDesc *prods_dev, const uint6
   a.flushk_wide = split_flush_group(bs, spec, 24);
   a.err = errword;
   a.work = work;
+  if (np == 1 && split_use_groups(bs, spec)) np = 4;
   return bs == 16 ? launch_split_s<16>(a, fmt, slices, np, s)
                   : launch_split_s<32>(a, fmt, slices, np, s);
 }
@@ -1318,6 +1444,16 @@ ProdDesc make_desc(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, double
   d.nc = sym.nc;
   d.nt = sym.nt;
   return d;
+}
+
+// Grouped items (up to four C blocks of at most one narrow flush each share
+// one work item) wherever compiled; the producer groups only C blocks of short
+// lists, so the kernel is the single-block kernel for the others.
+// BSM_SPLIT_GROUPS=0 in the environment turns them off.
+bool split_use_groups(int bs, int spec) {
+  if (!group_compiled(bs, split_spec_fmt(spec), split_spec_slices(spec))) return false;
+  const char *e = getenv("BSM_SPLIT_GROUPS");
+  return !(e && e[0] == '0');
 }
 
 // Pair items (two sibling C blocks per MMA, N = 2 bs) for long product lists:

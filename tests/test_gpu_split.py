@@ -15,6 +15,7 @@ import oracle
 import paper_1501_07800_gb300 as bsm
 import synth
 from helpers import assert_same_structure, from_bsm, relerr, to_bsm
+from oracle import split as osplit
 
 pytestmark = pytest.mark.gpu
 TOL_SPLIT = 1e-11
@@ -452,3 +453,80 @@ def test_recut_batched_and_plan_equal_single(prec, slices, bs):
     E = oracle.multiply(*pairs[0]).C
     assert_same_structure(single[0], E)
     assert relerr(single[0].vals, E.vals) < TOL_SPLIT
+
+
+# ------------------------------------------------ grouped items (bs 16)
+def with_env(name, flag, fn):
+    import os
+    old = os.environ.get(name)
+    os.environ[name] = flag
+    try:
+        return fn()
+    finally:
+        if old is None:
+            os.environ.pop(name, None)
+        else:
+            os.environ[name] = old
+
+
+def grouped_and_single(fn):
+    """fn() with grouped items (the default at bs 16) and without; pair items off."""
+    run = lambda flag: with_env("BSM_SPLIT_PAIRS", "0",
+                                lambda: with_env("BSM_SPLIT_GROUPS", flag, fn))
+    return run("1"), run("0")
+
+
+@pytest.mark.parametrize("slices", [3, 5, 7, 8])
+def test_groups_equal_single_blocks(slices):
+    """Up to four C blocks of short product lists per work item, each list in
+    its own TMEM columns, give the bits of one C block per item: on a product
+    of short lists only (one product per C block for most) and on one that
+    mixes short lists with lists longer than one narrow flush."""
+    bs = 16
+    short = (synth.random_blocks(1000, bs, 0.06, 670 + slices),
+             synth.random_blocks(1000, bs, 0.06, 680 + slices, ncols=1000 + 37))
+    A = synth.decay(260, bs, 690)
+    mixed = (A, synth.random_blocks(A.ncols, bs, 0.3, 691, ncols=A.ncols + 70))
+    for a, b in (short, mixed):
+        ga, gb = to_bsm(a), to_bsm(b)
+        g, one = grouped_and_single(lambda: from_bsm(
+            bsm.bsm_multiply(ga, gb, prec=bsm.BSM_SPLIT_BF16, slices=slices)))
+        assert_same_structure(g, one)
+        assert np.array_equal(g.vals, one.vals)
+    # and the split oracle's bits on a small product of short lists
+    a = synth.random_blocks(12 * bs + 7, bs, 0.25, 700 + slices)
+    b = synth.random_blocks(12 * bs + 7, bs, 0.25, 710 + slices)
+    want = osplit.multiply(a, b, "bf16", slices)
+    g, _ = grouped_and_single(lambda: from_bsm(
+        bsm.bsm_multiply(to_bsm(a), to_bsm(b), prec=bsm.BSM_SPLIT_BF16, slices=slices)))
+    assert_same_structure(g, want)
+    assert np.array_equal(g.vals, want.vals)
+
+
+def test_groups_batched_and_plan_equal_single():
+    """Batched products and plans at bs 16: groups never span two products
+    (the work list interleaves them), and the bits equal single products."""
+    bs = 16
+    prods = synth.batched(5, 720, bs=bs, nmin=8 * bs, nmax=60 * bs, dmin=0.02, dmax=0.3)
+    As = [to_bsm(a) for a, _ in prods]
+    Bs = [to_bsm(b) for _, b in prods]
+
+    def run():
+        single = [from_bsm(bsm.bsm_multiply(a, b, prec=bsm.BSM_SPLIT_BF16))
+                  for a, b in zip(As, Bs)]
+        batched = [from_bsm(c) for c in
+                   bsm.bsm_multiply_batched(As, Bs, prec=bsm.BSM_SPLIT_BF16)]
+        plan = bsm.bsm_plan_create(As, Bs, prec=bsm.BSM_SPLIT_BF16)
+        bsm.bsm_plan_execute(plan)
+        planned = [from_bsm(c) for c in bsm.bsm_plan_results(plan)]
+        bsm.bsm_plan_destroy(plan)
+        return single, batched, planned
+
+    (gs, gb, gp), (os_, _, _) = grouped_and_single(run)
+    for i, one in enumerate(os_):
+        for x in (gs[i], gb[i], gp[i]):
+            assert_same_structure(x, one)
+            assert np.array_equal(x.vals, one.vals)
+    E = oracle.multiply(*prods[0]).C
+    assert_same_structure(gb[0], E)
+    assert relerr(gb[0].vals, E.vals) < TOL_SPLIT
