@@ -109,7 +109,11 @@ typedef struct {
  *   brow, bcol    int32[nblk] block coordinates, 0 <= brow < ceil(nrows/bs),
  *                 0 <= bcol < ceil(ncols/bs); any order; duplicates rejected
  *   vals          float64[nblk][bs][bs], block t row-major at vals + t*bs*bs
- *   on_device     0: the three arrays are host memory (copied in this call);
+ *   on_device     0: the three arrays are host memory (copied in this call;
+ *                 pinned, device-mapped arrays -- brow/bcol 4-byte and vals
+ *                 16-byte aligned in the device's view -- are read in place
+ *                 by the build kernels over the host link instead, with no
+ *                 staging buffer and no copy-engine upload);
  *                 1: they are device memory of the current device (vals
  *                 16-byte aligned, brow/bcol 4-byte aligned)
  *   stream        cudaStream_t or NULL

@@ -321,6 +321,19 @@ static bsm_status build_from_device(int64_t nrows, int64_t ncols, int bs, int64_
   return BSM_OK;
 }
 
+// The device address of a pinned (page-locked, device-mapped) host buffer,
+// if it has one with the given alignment; nullptr for any other pointer.
+static void *mapped_device_ptr(const void *p, uintptr_t align) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return (uintptr_t)a.devicePointer % align ? nullptr : a.devicePointer;
+}
+
 extern "C" bsm_status bsm_build(int64_t nrows, int64_t ncols, int bs, int64_t nblk,
                                 const int32_t *brow, const int32_t *bcol, const double *vals,
                                 int on_device, void *stream, bsm_matrix *out) {
@@ -339,7 +352,24 @@ extern "C" bsm_status bsm_build(int64_t nrows, int64_t ncols, int bs, int64_t nb
   cudaStream_t s = (cudaStream_t)stream;
   if (on_device || nblk == 0)
     return build_from_device(nrows, ncols, bs, nblk, brow, bcol, vals, s, out);
-  // host input: stage on the device
+  // pinned host input: the build kernels read it in place over the host link
+  // -- no staging buffer and no copy-engine upload (which would queue behind
+  // other streams' copies) -- and the call returns once the last read is done
+  {
+    const int32_t *mr = (const int32_t *)mapped_device_ptr(brow, 4);
+    const int32_t *mc = (const int32_t *)mapped_device_ptr(bcol, 4);
+    const double *mv = (const double *)mapped_device_ptr(vals, 16);
+    if (mr && mc && mv) {
+      bsm_status st = build_from_device(nrows, ncols, bs, nblk, mr, mc, mv, s, out);
+      if (st == BSM_OK) st = cuda_status(cudaStreamSynchronize(s));
+      if (st != BSM_OK && *out) {
+        destroy_matrix(*out, s);
+        *out = nullptr;
+      }
+      return st;
+    }
+  }
+  // other host input: stage on the device
   int32_t *dr = nullptr, *dc = nullptr;
   double *dv = nullptr;
   size_t vb = sizeof(double) * bs * bs * nblk;
@@ -377,16 +407,7 @@ extern "C" bsm_status bsm_to_blocks(bsm_matrix M, int64_t *nblk_inout, int32_t *
   // host output into pinned (page-locked, device-mapped) buffers: the gather
   // and coordinate kernels write straight into them over the host link, with
   // no staging copy
-  auto mapped = [](void *p, uintptr_t align) -> void * {
-    if (!p) return nullptr;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
-    return (uintptr_t)a.devicePointer % align ? nullptr : a.devicePointer;
-  };
+  auto mapped = [](void *p, uintptr_t align) -> void * { return mapped_device_ptr(p, align); };
   double *mv = nullptr;
   int32_t *mr = nullptr, *mc = nullptr;
   bool all_mapped = false;

@@ -42,6 +42,50 @@ def test_build_roundtrip(device):
     assert np.array_equal(R.vals, E.vals)
 
 
+def test_build_from_pinned_host_inputs():
+    """Pinned host COO arrays are read in place by the build kernels: the same
+    matrix as from pageable arrays (exactly-zero blocks dropped), the same
+    errors, and the caller may overwrite its buffers once the call returns.
+    A pinned values array the device sees misaligned goes through the staged
+    copy."""
+    import torch
+    A = synth.random_blocks(2000, 32, 0.08, 31)
+    A.vals[::7] = 0.0                                  # some exactly-zero blocks
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+        t.numpy()[...] = a
+        return t, t.numpy()
+
+    keep = [pinned(x) for x in (A.brow, A.bcol, A.vals)]
+    r, c, v = (x for _, x in keep)
+    M = bsm.bsm_build(A.nrows, A.ncols, 32, r, c, v)
+    v[...] = np.nan                                    # after the call: no effect on M
+    R, E = from_bsm(M), from_bsm(to_bsm(A))
+    assert R.nblk == E.nblk < A.nblk
+    assert_same_structure(R, E)
+    assert np.array_equal(R.vals, E.vals)
+    v[...] = A.vals
+    bad = r.copy()
+    r[3] = r[5]
+    c[3] = c[5]                                        # a duplicate coordinate
+    with pytest.raises(bsm.BsmError, match="DUPLICATE"):
+        bsm.bsm_build(A.nrows, A.ncols, 32, r, c, v)
+    r[...] = bad
+    c[...] = A.bcol
+    r[0] = 10 ** 6                                     # out of range
+    with pytest.raises(bsm.BsmError, match="OUT_OF_RANGE"):
+        bsm.bsm_build(A.nrows, A.ncols, 32, r, c, v)
+    r[...] = A.brow
+    # values starting 8 bytes into a pinned buffer: staged
+    tv = torch.empty(A.vals.size + 1, dtype=torch.float64, pin_memory=True)
+    v8 = tv.numpy()[1:].reshape(A.vals.shape)
+    v8[...] = A.vals
+    R8 = from_bsm(bsm.bsm_build(A.nrows, A.ncols, 32, r, c, v8))
+    assert_same_structure(R8, E)
+    assert np.array_equal(R8.vals, E.vals)
+
+
 def test_to_blocks_into_pinned_host_buffers():
     """Pinned host buffers are written directly by the gather kernels; the
     result equals the staged copy into pageable buffers."""
