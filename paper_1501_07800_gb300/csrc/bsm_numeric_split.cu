@@ -102,18 +102,25 @@ struct Cfg {
   static constexpr int ASLOTS = (DPG - 1) + G * DPG;         // zero pad + slices + pad
   static constexpr int BSLOTS = NP * S;                      // B slices (a pair interleaved)
   static constexpr int STAGE = (ASLOTS + BSLOTS) * SLICE;
-  static constexpr int NTEAM = NP == 2 ? 1 : 2;              // epilogue teams
   static constexpr int NW = NP * BS * NQ;                    // output columns of an item
   static constexpr int CROW = NW + 4;                        // padded int32 row (combine)
   static constexpr int COMB = S * BS * CROW * 4;             // combine buffer bytes (per team)
   // ring depth: up to 4 (bs 32) / 8 (bs 16) stages within 227 KiB of shared
-  // memory, 8 KiB of it left for the static barriers and descriptor ring (16
-  // stages at bs 16 measured slower than 8)
-  static constexpr int BUDGET = 227 * 1024 - 8 * 1024 - NTEAM * COMB;
+  // memory, 8 KiB of it left for the static barriers and descriptor rings (16
+  // stages at bs 16 measured slower than 8), split evenly between the
+  // pipelines
   static constexpr int NSTMAX = BS == 32 ? (F ? 6 : 4) : 8;
-  static constexpr int NST = BUDGET / STAGE < NSTMAX ? BUDGET / STAGE : NSTMAX;
+  static constexpr int stages_for(int teams) {
+    return (227 * 1024 - 8 * 1024 - teams * COMB) / STAGE < NSTMAX
+               ? (227 * 1024 - 8 * 1024 - teams * COMB) / STAGE
+               : NSTMAX;
+  }
+  // epilogue teams = pipelines: one for pairs (a team of sixteen warps), and
+  // where two would leave a pipeline fewer than two stages (BF16 x 8 at bs 32)
+  static constexpr int NTEAM = (NP == 2 || stages_for(2) < 4) ? 1 : 2;
+  static constexpr int NST = stages_for(NTEAM) / NTEAM * NTEAM;
   static constexpr int SMEM = NST * STAGE + NTEAM * COMB;
-  static_assert(NST >= 2, "shared memory too small for two stages");
+  static_assert(NST >= 2 * NTEAM, "shared memory too small for two stages per pipeline");
   static constexpr uint32_t SBO = BS * 8 * Fmt<F>::EB;       // 8-row group stride
   static constexpr uint32_t LBO = 128;                       // K core-matrix stride
 };
@@ -487,35 +494,19 @@ __device__ __forceinline__ double split_to_double(int64_t hi, int64_t lo, int X)
   return split_to_double_slow(hi, lo, T, X);
 }
 
-// Bounded wait until the shared counter reaches `want` (or an abort); the
-// reads after it see the writes made before the counter's update.
-__device__ __forceinline__ bool wait_issued(volatile uint32_t *cnt, uint32_t want,
-                                            volatile int *abort) {
-  if (*cnt >= want) {
-    __threadfence_block();
-    return true;
-  }
-  const uint64_t t0 = globaltimer_ns();
-  for (;;) {
-    __nanosleep(32);
-    if (*cnt >= want) {
-      __threadfence_block();
-      return true;
-    }
-    if (*abort || globaltimer_ns() - t0 > BSM_WAIT_NS) return false;
-  }
-}
-
 constexpr int kEpiWarps = 16;                // epilogue warps (4 per lane quadrant)
-// One MMA-issuing thread per epilogue team, each in a warp of its own: a
-// thread issues tcgen05.mma instructions no faster than one per ~50 cycles
-// (measured), so a second issuer doubles the rate at which the short
-// instructions of this kernel (N = 32 or 64) reach the tensor core.
-constexpr int kProdWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
-constexpr int kMaxThreads = (kEpiWarps + 3) * 32;
+// Each epilogue team is the end of a pipeline of its own: a producer warp
+// (work claims, descriptors, stage copies), an MMA-issuing thread in a warp
+// of its own, and the team.  A thread issues tcgen05.mma instructions no
+// faster than one per ~50 cycles (measured), so a second issuer doubles the
+// rate at which the short instructions of this kernel (N = 32 or 64) reach
+// the tensor core; a second producer halves the per-item work of the warp
+// that otherwise paces the kernel on short product lists (one producer warp
+// shares its scheduler with four busy epilogue warps).
+constexpr int kMaxThreads = (kEpiWarps + 4) * 32;
 template <int NTEAM>
 constexpr int threads_for() {
-  return (kEpiWarps + 1 + NTEAM) * 32;
+  return (kEpiWarps + 2 * NTEAM) * 32;
 }
 
 template <int BS, int S, int F, int NP, int NQ>
@@ -527,7 +518,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
   constexpr int kTeamWarps = kEpiWarps / NTEAM;  // 8 (two teams) or 16 (one)
   constexpr int kTeam = kTeamWarps * 32;         // threads per epilogue team
   constexpr int NB = NP * BS;                    // MMA N: output columns of one list
-  constexpr int NW = C::NW;                      // output columns of an item
   constexpr int NSUB = NP * NQ;                  // C blocks of an item
   static_assert(NSUB <= kSub && (NP == 1 || NQ == 1), "item shape");
   constexpr int BETA = Fmt<F>::BETA, TS = Fmt<F>::TSPLIT;
@@ -550,20 +540,19 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
   constexpr int NCOLS = TCOLS <= 32 ? 32 : (TCOLS <= 64 ? 64 : (TCOLS <= 128 ? 128 : 256));
   constexpr uint32_t BYTES = (uint32_t)S * C::SLICE;          // one A block's slices
   constexpr uint32_t BYTES_B = (uint32_t)NP * S * C::SLICE;   // B block (pair) slices
+  // pipeline b (one per team): stages b NSTP .. b NSTP + NSTP - 1 of the
+  // ring and descriptor ring b, each filled and consumed strictly in order
+  constexpr int NSTP = C::NST / NTEAM;
+  static_assert(NSTP <= 32, "stages per pipeline");
+  constexpr int kProd0 = kEpiWarps, kMma0 = kEpiWarps + NTEAM;  // warps of pipeline 0
   extern __shared__ __align__(1024) uint8_t smem[];
   // tfull / tempty: per (team, buffer), index 2 * team + buffer
   __shared__ __align__(8) uint64_t full[C::NST], empty[C::NST], tfull[4], tempty[4], done;
-  __shared__ __align__(8) uint64_t meta_full[kMeta], meta_empty[kMeta];
-  __shared__ Meta meta[kMeta];
+  __shared__ __align__(8) uint64_t meta_full[2][kMeta], meta_empty[2][kMeta];
+  __shared__ Meta meta[2][kMeta];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int warp_any[2][kSub][16];  // [team][C block of the item][warp]
   __shared__ volatile int abort_flag;
-  // products whose stage fill the producer has issued (two MMA issuers: a
-  // stage's next fill may belong to either, so an issuer first waits until
-  // its product's fill was issued -- only then does the stage's full barrier
-  // stand at that fill's phase, and its parity test cannot be passed by the
-  // stage's previous, still incomplete, phase)
-  __shared__ volatile uint32_t issued;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t *stages = smem;
@@ -583,13 +572,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
       mbar_init(&tfull[i], 1);
       mbar_init(&tempty[i], kTeam);  // buffers 2t, 2t+1 belong to team t
     }
-    for (int i = 0; i < kMeta; i++) {
-      mbar_init(&meta_full[i], 1);
-      mbar_init(&meta_empty[i], kTeam + NTEAM);  // the MMA threads + the owning team
-    }
+    for (int b = 0; b < 2; b++)
+      for (int i = 0; i < kMeta; i++) {
+        mbar_init(&meta_full[b][i], 1);
+        mbar_init(&meta_empty[b][i], kTeam + 1);  // the pipeline's MMA thread and team
+      }
     mbar_init(&done, NTEAM);
     abort_flag = 0;
-    issued = 0;
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -601,7 +590,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
   tc_fence_after();
   const uint32_t tbase = tmem_base_sh;
 
-  if (warp == kProdWarp) {
+  if (warp >= kProd0 && warp < kProd0 + NTEAM) {
     // --------------------------------------------------------- producer warp
     // Claims chunks of kChunk consecutive C blocks (Morton order) from a
     // global counter; the chunk's descriptors and its contiguous range of
@@ -609,39 +598,48 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
     // the barrier work and issues the copies.  Two sentinel descriptors
     // (nk = -1) end the consumers.  The epilogue loads the scale exponents
     // itself.
+    const int b = warp - kProd0;  // the pipeline
+    uint64_t *const mfull = meta_full[b], *const mempty = meta_empty[b];
+    Meta *const mring = meta[b];
     uint32_t it = 0, q = 0;
-    bool pend[C::NST] = {};
-    uint32_t ppar[C::NST] = {};
+    uint32_t pend = 0, ppar = 0;  // bit s: local stage s has a fill issued / its phase parity
     bool stop = false;
-    // one item's descriptor: its C blocks, their coordinates, its lists
-    struct ItemDesc {
-      int64_t c[kSub];
-      int32_t bi[kSub], bj[kSub], k0[kSub], nkq[kSub];
-      int nq, nk;
-    };
-    auto put_meta = [&](const ItemDesc &d, const ProdDesc *pd) -> bool {
+    // the current product's descriptor fields, reloaded when it changes
+    int pc = -1;
+    const uint8_t *asl = nullptr, *bsl = nullptr;
+    const int32_t *tap = nullptr, *tbp = nullptr;
+    int64_t na = 0, nb = 0, nt = 0;
+    double *cvp = nullptr;
+    int32_t *nzp = nullptr;
+    const int *rexp = nullptr, *cexp = nullptr;
+    // one work item's descriptor into the ring (lane 0 writes; every lane
+    // returns whether it was written).  x-th C block: a pair's siblings, or
+    // the C blocks of lanes i .. i + nq - 1 (grouped items).
+    auto put_meta = [&](const int64_t (&c)[NSUB], const int32_t (&bi)[NSUB],
+                        const int32_t (&bj)[NSUB], const int32_t (&nkq)[NSUB], int nq,
+                        int nk) -> bool {
       const int m = q % kMeta;
       int okw = 1;
       if (lane == 0) {
-        okw = mbar_wait(&meta_empty[m], ((q / kMeta) & 1u) ^ 1u) && !abort_flag;
+        okw = mbar_wait(&mempty[m], ((q / kMeta) & 1u) ^ 1u) && !abort_flag;
         if (!okw) {
           set_err(P.err, DERR_TIMEOUT);
           abort_flag = 1;
         } else {
 #pragma unroll
-          for (int b = 0; b < kSub; b++) {
-            meta[m].c[b] = d.c[b];
-            meta[m].bi[b] = d.bi[b];
-            meta[m].bj[b] = d.bj[b];
-            meta[m].nkq[b] = d.nkq[b];
+          for (int x = 0; x < NSUB; x++) {
+            mring[m].c[x] = c[x];
+            mring[m].bi[x] = bi[x];
+            mring[m].bj[x] = bj[x];
+            if (NQ > 1) mring[m].nkq[x] = nkq[x];
           }
-          meta[m].cv = pd ? pd->cv : nullptr;
-          meta[m].nz = pd ? pd->nz : nullptr;
-          meta[m].rowexp = pd ? pd->rowexp : nullptr;
-          meta[m].colexp = pd ? pd->colexp : nullptr;
-          meta[m].nk = d.nk;
-          meta[m].nq = d.nq;
-          mbar_arrive(&meta_full[m]);  // release: the descriptor is visible
+          mring[m].cv = cvp;
+          mring[m].nz = nzp;
+          mring[m].rowexp = rexp;
+          mring[m].colexp = cexp;
+          mring[m].nk = nk;
+          mring[m].nq = nq;
+          mbar_arrive(&mfull[m]);  // release: the descriptor is visible
         }
       }
       okw = __shfl_sync(0xffffffffu, okw, 0);
@@ -689,151 +687,147 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
       }
       for (int i = 0; i < n && !stop;) {
         const int p = __shfl_sync(0xffffffffu, pi, i);
-        const ProdDesc *pd = &P.prods[p];
-        ItemDesc d;
-#pragma unroll
-        for (int b = 0; b < kSub; b++) {
-          d.c[b] = -1;
-          d.bi[b] = d.bj[b] = d.k0[b] = d.nkq[b] = 0;
+        if (p != pc) {  // every lane keeps the product's fields
+          const ProdDesc *pd = &P.prods[p];
+          pc = p;
+          asl = pd->asl;
+          bsl = pd->bsl;
+          tap = pd->ta;
+          tbp = pd->tb;
+          na = pd->na;
+          nb = pd->nb;
+          nt = pd->nt;
+          cvp = pd->cv;
+          nzp = pd->nz;
+          rexp = pd->rowexp;
+          cexp = pd->colexp;
         }
-        d.nq = 1;
-        {
-          const int32_t k0 = __shfl_sync(0xffffffffu, s0, i);
-          d.k0[0] = k0;
-          d.nkq[0] = __shfl_sync(0xffffffffu, s1, i) - k0;
-          d.c[0] = __shfl_sync(0xffffffffu, e0, i);
-          d.bi[0] = __shfl_sync(0xffffffffu, kbi, i);
-          d.bj[0] = __shfl_sync(0xffffffffu, kbj, i);
-        }
-        if (NP == 2) {  // the pair's odd sibling: same row, next column
-          d.c[1] = __shfl_sync(0xffffffffu, e1, i);
-          d.bi[1] = d.bi[0];
-          d.bj[1] = d.bj[0] + 1;
-        }
-        if (NQ > 1 && d.nkq[0] >= 1 && d.nkq[0] <= gmax) {
-          // grouped item: the following items of the same product with short
-          // lists (every lane takes the same decisions)
-          while (d.nq < NQ && i + d.nq < n) {
-            const int j2 = i + d.nq;
+        // grouped item: the following items of the same product with short
+        // lists (every lane takes the same decisions)
+        const int32_t nk0 = __shfl_sync(0xffffffffu, s1, i) - __shfl_sync(0xffffffffu, s0, i);
+        int nq = 1;
+        if (NQ > 1 && nk0 >= 1 && nk0 <= gmax) {
+          while (nq < NQ && i + nq < n) {
+            const int j2 = i + nq;
             const int p2 = __shfl_sync(0xffffffffu, pi, j2);
-            const int32_t k2 = __shfl_sync(0xffffffffu, s0, j2);
-            const int32_t n2 = __shfl_sync(0xffffffffu, s1, j2) - k2;
-            const int64_t c2 = __shfl_sync(0xffffffffu, e0, j2);
-            const int32_t bi2 = __shfl_sync(0xffffffffu, kbi, j2);
-            const int32_t bj2 = __shfl_sync(0xffffffffu, kbj, j2);
+            const int32_t n2 = __shfl_sync(0xffffffffu, s1, j2) - __shfl_sync(0xffffffffu, s0, j2);
             if (p2 != p || n2 < 1 || n2 > gmax) break;
-            d.c[d.nq] = c2;
-            d.bi[d.nq] = bi2;
-            d.bj[d.nq] = bj2;
-            d.k0[d.nq] = k2;
-            d.nkq[d.nq] = n2;
-            d.nq++;
+            nq++;
           }
         }
-        d.nk = 0;
-        for (int b = 0; b < d.nq; b++) d.nk += d.nkq[b];
-        i += d.nq;
-        if (!put_meta(d, pd)) {
+        int64_t c[NSUB];
+        int32_t bi[NSUB], bj[NSUB], nkq[NSUB];
+        int nk = 0;
+#pragma unroll
+        for (int x = 0; x < NSUB; x++) {
+          const int src = NP == 2 ? i : min(i + x, 31);
+          const int64_t cx = __shfl_sync(0xffffffffu, NP == 2 && x == 1 ? e1 : e0, src);
+          bi[x] = __shfl_sync(0xffffffffu, kbi, src);
+          bj[x] = __shfl_sync(0xffffffffu, kbj, src) + (NP == 2 ? x : 0);  // the odd sibling
+          nkq[x] = __shfl_sync(0xffffffffu, s1, src) - __shfl_sync(0xffffffffu, s0, src);
+          const bool in = NP == 2 || x < nq;
+          c[x] = in ? cx : -1;
+          if (!in) nkq[x] = bi[x] = bj[x] = 0;  // (another product's lane)
+          if (NP == 2 ? x == 0 : in) nk += nkq[x];
+        }
+        if (!put_meta(c, bi, bj, nkq, nq, nk)) {
           stop = true;
           break;
         }
-        const uint8_t *asl = pd->asl, *bsl = pd->bsl;
-        const int64_t na = pd->na, nb = pd->nb, nt = pd->nt;
-        for (int lq = 0; lq < d.nq && !stop; lq++)  // the item's lists in order
-        for (int j = 0; j < d.nkq[lq]; j++, it++) {
-          const int32_t t = d.k0[lq] + j;
-          if (p != wp || t < tw || t >= tw + 32) {  // refill the window (loads stay below nt)
-            wp = p;
-            tw = t;
-            ta_w = tw + lane < nt ? pd->ta[tw + lane] : 0;
-            tb_w = tw + lane < nt ? pd->tb[tw + lane] : 0;
-          }
-          const int32_t aa = __shfl_sync(0xffffffffu, ta_w, t - tw);
-          const int32_t bb = __shfl_sync(0xffffffffu, tb_w, t - tw);
-          int okc = 1;
-          if (lane == 0) {
-            const int st = it % C::NST;
-            if (!mbar_wait(&empty[st], ((it / C::NST) & 1u) ^ 1u) || abort_flag) {
-              set_err(P.err, DERR_TIMEOUT);
-              abort_flag = 1;
-              okc = 0;
-            } else {
-              uint8_t *sa = stages + (size_t)st * C::STAGE;
-              uint8_t *sb = sa + C::ASLOTS * C::SLICE;
-              pend[st] = true;
-              ppar[st] = (it / C::NST) & 1u;
-              if (aa < 0 || aa >= na || bb < 0 || bb >= nb) {
-                set_err(P.err, DERR_BOUNDS);  // complete the stage without data
-                mbar_arrive(&full[st]);
+        // the item's lists in order, one stage per block product; lane 0
+        // issues (a failure stops it and ends the chunk after the item)
+        int okc = 1;
+        for (int lq = 0; lq < nq; lq++) {
+          const int32_t k0 = __shfl_sync(0xffffffffu, s0, i + lq);
+          int32_t nkx = NQ > 1 ? nkq[0] : nk;
+#pragma unroll
+          for (int x = 1; x < NSUB; x++)
+            if (NQ > 1 && lq == x) nkx = nkq[x];
+          for (int j = 0; j < nkx; j++, it++) {
+            const int32_t t = k0 + j;
+            if (p != wp || t < tw || t >= tw + 32) {  // refill the window (loads stay below nt)
+              wp = p;
+              tw = t;
+              ta_w = tw + lane < nt ? tap[tw + lane] : 0;
+              tb_w = tw + lane < nt ? tbp[tw + lane] : 0;
+            }
+            const int32_t aa = __shfl_sync(0xffffffffu, ta_w, t - tw);
+            const int32_t bb = __shfl_sync(0xffffffffu, tb_w, t - tw);
+            if (lane == 0 && okc) {
+              const int sl = it % NSTP, st = b * NSTP + sl;  // local and ring stage
+              if (!mbar_wait(&empty[st], ((it / NSTP) & 1u) ^ 1u) || abort_flag) {
+                set_err(P.err, DERR_TIMEOUT);
+                abort_flag = 1;
+                okc = 0;
               } else {
-                mbar_expect_tx(&full[st], BYTES + BYTES_B);
-                bulk_g2s(sa + (DPG - 1) * C::SLICE, asl + (int64_t)aa * BYTES, BYTES, &full[st]);
-                bulk_g2s(sb, bsl + (int64_t)bb * BYTES_B, BYTES_B, &full[st]);
-              }
-              if (NTEAM > 1) {
-                __threadfence_block();
-                issued = it + 1;
+                uint8_t *sa = stages + (size_t)st * C::STAGE;
+                uint8_t *sb = sa + C::ASLOTS * C::SLICE;
+                pend |= 1u << sl;
+                ppar = (ppar & ~(1u << sl)) | (((it / NSTP) & 1u) << sl);
+                if (aa < 0 || aa >= na || bb < 0 || bb >= nb) {
+                  set_err(P.err, DERR_BOUNDS);  // complete the stage without data
+                  mbar_arrive(&full[st]);
+                } else {
+                  mbar_expect_tx(&full[st], BYTES + BYTES_B);
+                  bulk_g2s(sa + (DPG - 1) * C::SLICE, asl + (int64_t)aa * BYTES, BYTES, &full[st]);
+                  bulk_g2s(sb, bsl + (int64_t)bb * BYTES_B, BYTES_B, &full[st]);
+                }
               }
             }
           }
-          if (!__shfl_sync(0xffffffffu, okc, 0)) {
-            stop = true;
-            break;
-          }
         }
+        if (!__shfl_sync(0xffffffffu, okc, 0)) {
+          stop = true;
+          break;
+        }
+        i += nq;
       }
     }
-    // end markers: one for the MMA thread and each epilogue team (the MMA
-    // thread stops at the first)
+    // end marker for the pipeline's MMA thread and team
     if (!stop) {
-      ItemDesc e;
-      for (int b = 0; b < kSub; b++) {
-        e.c[b] = -1;
-        e.bi[b] = e.bj[b] = e.k0[b] = e.nkq[b] = 0;
+      int64_t c[NSUB];
+      int32_t z[NSUB];
+#pragma unroll
+      for (int x = 0; x < NSUB; x++) {
+        c[x] = -1;
+        z[x] = 0;
       }
-      e.nq = 1;
-      e.nk = -1;
-      for (int t = 0; t < NTEAM; t++) put_meta(e, nullptr);
+      put_meta(c, z, z, z, 1, -1);
     }
     // copies still in flight must land before the CTA exits
     if (lane == 0)
-      for (int st = 0; st < C::NST; st++)
-        if (pend[st]) mbar_wait(&full[st], ppar[st]);
-  } else if (warp >= kMmaWarp && warp < kMmaWarp + NTEAM) {
+      for (int sl = 0; sl < NSTP; sl++)
+        if ((pend >> sl) & 1u) mbar_wait(&full[b * NSTP + sl], (ppar >> sl) & 1u);
+  } else if (warp >= kMma0 && warp < kMma0 + NTEAM) {
     // ---------------------------------------------------------- MMA issuers
-    // Thread b issues the MMAs of team b's items (items alternate between
-    // the teams).  Both read every work descriptor: the producer fills the
-    // ring in item order, so a product's stage follows from the count of all
-    // products before it.
+    // Thread b issues the MMAs of pipeline b's items, whose stages it meets
+    // in the order its producer filled them.
     if (lane == 0) {
-      const int b = warp - kMmaWarp;
+      const int b = warp - kMma0;
+      uint64_t *const mfull = meta_full[b], *const mempty = meta_empty[b];
+      const Meta *const mring = meta[b];
       uint32_t it = 0, q = 0;
       uint32_t fcb = 0;  // flushes issued for team b
       const uint32_t sbase = smem_u32(stages);
       for (;; q++) {
         int m = q % kMeta;
-        if (!mbar_wait(&meta_full[m], (q / kMeta) & 1u)) {
+        if (!mbar_wait(&mfull[m], (q / kMeta) & 1u)) {
           set_err(P.err, DERR_TIMEOUT);
           abort_flag = 1;
           break;
         }
         // (single blocks and pairs: one list, known at compile time)
-        const int nk = meta[m].nk, nq = NQ > 1 ? meta[m].nq : 1;
+        const int nk = mring[m].nk, nq = NQ > 1 ? mring[m].nq : 1;
         int nkq[NQ];
 #pragma unroll
-        for (int x = 0; x < NQ; x++) nkq[x] = NQ > 1 ? meta[m].nkq[x] : nk;
-        mbar_arrive(&meta_empty[m]);
+        for (int x = 0; x < NQ; x++) nkq[x] = NQ > 1 ? mring[m].nkq[x] : nk;
+        mbar_arrive(&mempty[m]);
         if (nk < 0 || abort_flag) break;  // end marker
-        if ((int)(q % NTEAM) != b) {      // the other team's item: skip its stages
-          it += (uint32_t)nk;
-          continue;
-        }
         // the MMAs of the next stage (one block product) into buffer u,
         // list lq's columns; first: the flush's first product
         auto stage_mmas = [&](uint32_t u, int lq, uint32_t first) -> bool {
-          const int st = it % C::NST;
-          if (NTEAM > 1 && !wait_issued(&issued, it + 1, &abort_flag)) return false;
-          if (!mbar_wait(&full[st], (it / C::NST) & 1u)) return false;
+          const int st = b * NSTP + it % NSTP;
+          if (!mbar_wait(&full[st], (it / NSTP) & 1u)) return false;
           tc_fence_after();
           // descriptors differ only in the start-address field (16-byte
           // units, < 2^14 inside shared memory): build them once per stage
@@ -909,9 +903,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
     }
   } else {
     // ----------------------------------------------------------- epilogue
-    // Single C blocks: two teams of eight warps take alternate items (team t:
-    // local item index q with q % 2 == t) and their own TMEM buffers; pairs:
-    // one team of sixteen warps.  Warp w of a team drains lane quadrant w % 4,
+    // Single C blocks: two teams of eight warps, each at the end of its own
+    // pipeline (its producer's items, its own TMEM buffers); pairs: one team
+    // of sixteen warps.  Warp w of a team drains lane quadrant w % 4,
     // a slice of HC columns, and accumulates the exact diagonal sums straight
     // into the team's shared-memory buffer [d][r][c]; the team then combines
     // the diagonals of each output element.  With two teams one team's
@@ -936,9 +930,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
     int64_t prev_c[NSUB];
 #pragma unroll
     for (int x = 0; x < NSUB; x++) prev_c[x] = -1;
-    for (uint32_t q = team;; q += NTEAM) {
+    uint64_t *const mfull = meta_full[team], *const mempty = meta_empty[team];
+    const Meta *const mring = meta[team];
+    for (uint32_t q = 0;; q++) {
       int m = q % kMeta;
-      bool okm = mbar_wait(&meta_full[m], (q / kMeta) & 1u);
+      bool okm = mbar_wait(&mfull[m], (q / kMeta) & 1u);
       // every decision below is uniform across the warp (tcgen05.ld is
       // .sync.aligned) and, at the named barriers, across the team.  This
       // barrier also ends the previous item: its warp flags are complete and
@@ -958,17 +954,17 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
       }
       // (the flags are rewritten only after the next barrier, which thread 0
       // reaches after reading them)
-      const int nk = meta[m].nk, nq = NQ > 1 ? meta[m].nq : 1;
+      const int nk = mring[m].nk, nq = NQ > 1 ? mring[m].nq : 1;
       if (nk < 0) {  // end marker
-        mbar_arrive(&meta_empty[m]);
+        mbar_arrive(&mempty[m]);
         break;
       }
       int64_t cblk[NSUB];
 #pragma unroll
-      for (int x = 0; x < NSUB; x++) cblk[x] = meta[m].c[x];
-      double *const cvp = meta[m].cv;
-      int32_t *const nzp = meta[m].nz;
-      const int *const rowexp = meta[m].rowexp, *const colexp = meta[m].colexp;
+      for (int x = 0; x < NSUB; x++) cblk[x] = mring[m].c[x];
+      double *const cvp = mring[m].cv;
+      int32_t *const nzp = mring[m].nz;
+      const int *const rowexp = mring[m].rowexp, *const colexp = mring[m].colexp;
       // this thread's output elements: 4-column group g4 = ttid + i kTeam is
       // list g4 / LG4, row rr and list columns cn .. cn + 3 of it; item column
       // c4 = list * NB + cn lies in C block blk = c4 / BS of the item (a
@@ -982,18 +978,18 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
         const int g4 = min(ttid + i * kTeam, NG4 - 1);
         const int rem = g4 % LG4, rr = rem / (NB / 4);
         const int c4 = (g4 / LG4) * NB + (rem % (NB / 4)) * 4, blk = c4 / BS;
-        int32_t bi = meta[m].bi[0], bj = meta[m].bj[0];
+        int32_t bi = mring[m].bi[0], bj = mring[m].bj[0];
 #pragma unroll
         for (int x = 1; x < NSUB; x++)
           if (blk == x) {
-            bi = meta[m].bi[x];
-            bj = meta[m].bj[x];
+            bi = mring[m].bi[x];
+            bj = mring[m].bj[x];
           }
         oblk[i] = blk;
         erow[i] = rowexp[(int64_t)bi * BS + rr];
         fcol[i] = *reinterpret_cast<const int4 *>(colexp + (int64_t)bj * BS + c4 % BS);
       }
-      mbar_arrive(&meta_empty[m]);
+      mbar_arrive(&mempty[m]);
       // a grouped item is one narrow flush on the fast path (every list has
       // at most kFast products)
       const FlushPlan fplan = nq > 1 ? FlushPlan{false, nk, 1, 1}
@@ -1501,12 +1497,12 @@ bsm_status split_pairs_prepare(bsm_matrix A, bsm_matrix B, const SymbolicResult 
   BSM_TRY(scan_exclusive_i32(chead, cpos, nc, s));
   h32[0] = h32[1] = h32[2] = h32[3] = 0;
   if (nb) {
-    cudaMemcpyAsync(h32 + 0, bpos + nb - 1, 4, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(h32 + 1, bhead + nb - 1, 4, cudaMemcpyDeviceToHost, s);
+    readback(h32 + 0, bpos + nb - 1, 4, s);
+    readback(h32 + 1, bhead + nb - 1, 4, s);
   }
   if (nc) {
-    cudaMemcpyAsync(h32 + 2, cpos + nc - 1, 4, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(h32 + 3, chead + nc - 1, 4, cudaMemcpyDeviceToHost, s);
+    readback(h32 + 2, cpos + nc - 1, 4, s);
+    readback(h32 + 3, chead + nc - 1, 4, s);
   }
   BSM_CUDA(cudaStreamSynchronize(s));
   const int64_t npb = (int64_t)h32[0] + h32[1], npc = (int64_t)h32[2] + h32[3];
@@ -1527,7 +1523,7 @@ bsm_status split_pairs_prepare(bsm_matrix A, bsm_matrix B, const SymbolicResult 
                                                     bslot, cnt, nullptr, nullptr, nullptr, 0);
   }
   BSM_TRY(scan_exclusive_i32(cnt, mseg, npc + 1, s));
-  cudaMemcpyAsync(h32, mseg + npc, 4, cudaMemcpyDeviceToHost, s);
+  readback(h32, mseg + npc, 4, s);
   BSM_CUDA(cudaStreamSynchronize(s));
   const int64_t mt = h32[0];
   BSM_TRY(grab((void **)&mta, 4 * mt));

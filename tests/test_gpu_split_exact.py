@@ -25,7 +25,10 @@ def _cuda():
 
 
 @pytest.mark.parametrize("fmt,slices,bs", [("bf16", 3, 32), ("bf16", 7, 32), ("bf16", 7, 16),
-                                           ("fp8", 6, 32), ("fp8", 12, 32)])
+                                           ("fp8", 6, 32), ("fp8", 12, 32),
+                                           # one pipeline (its shared memory fits no two)
+                                           ("bf16", 8, 32),
+                                           ("bf16", 2, 32), ("bf16", 5, 16), ("fp8", 2, 32)])
 def test_random_equals_split_oracle_bit_for_bit(fmt, slices, bs):
     A = synth.random_blocks(3 * bs + 5, bs, 0.4, 801 + bs)
     B = synth.random_blocks(3 * bs + 5, bs, 0.4, 802 + bs)
