@@ -124,6 +124,13 @@ struct HostScratch {
   ~HostScratch();
 };
 HostScratch &host_scratch();
+// Reads `bytes` (a multiple of 4, small: counts, flags, error words) from
+// device memory into page-locked host memory, stream-ordered on s, with a
+// one-block kernel writing the host memory's device-mapped address: a
+// copy-engine transfer would queue behind any large device-to-host copy in
+// flight on another stream (a download overlapping this work).  Other host
+// memory falls back to cudaMemcpyAsync.  The host reads after synchronising s.
+bsm_status readback(void *host, const void *dev, size_t bytes, cudaStream_t s);
 
 // Exclusive prefix sums on the device (CUB), sized on first use.
 bsm_status scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);

@@ -66,9 +66,9 @@ bsm_status finish_product(bsm_matrix C, SymbolicResult *sym, double *cvals, int3
   int32_t *h = (int32_t *)host_scratch().get(16);
   if (st == BSM_OK && !h) st = BSM_ERR_OOM;
   if (st == BSM_OK) {
-    cudaMemcpyAsync(h, pos + nc - 1, 4, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(h + 1, nz + nc - 1, 4, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(h + 2, err, 4, cudaMemcpyDeviceToHost, s);
+    readback(h, pos + nc - 1, 4, s);
+    readback(h + 1, nz + nc - 1, 4, s);
+    readback(h + 2, err, 4, s);
     st = cuda_status(cudaStreamSynchronize(s));
   }
   if (st == BSM_OK && h[2] == DERR_TIMEOUT) st = BSM_ERR_TIMEOUT;
@@ -126,9 +126,9 @@ bsm_status finish_product_copy(bsm_matrix C, const SymbolicResult &sym, const do
   int32_t *h = (int32_t *)host_scratch().get(16);
   if (st == BSM_OK && !h) st = BSM_ERR_OOM;
   if (st == BSM_OK) {
-    cudaMemcpyAsync(h, pos + nc - 1, 4, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(h + 1, nz + nc - 1, 4, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(h + 2, err, 4, cudaMemcpyDeviceToHost, s);
+    readback(h, pos + nc - 1, 4, s);
+    readback(h + 1, nz + nc - 1, 4, s);
+    readback(h + 2, err, 4, s);
     st = cuda_status(cudaStreamSynchronize(s));
   }
   if (st == BSM_OK && h[2] == DERR_TIMEOUT) st = BSM_ERR_TIMEOUT;
@@ -175,9 +175,9 @@ static bsm_status compact_chunk(SymbolicResult &r, double *&cvals, const int32_t
   int32_t *h = (int32_t *)host_scratch().get(16);
   if (st == BSM_OK && !h) st = BSM_ERR_OOM;
   if (st == BSM_OK) {
-    cudaMemcpyAsync(h, pos + nc - 1, 4, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(h + 1, nz + nc - 1, 4, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(h + 2, err, 4, cudaMemcpyDeviceToHost, s);
+    readback(h, pos + nc - 1, 4, s);
+    readback(h + 1, nz + nc - 1, 4, s);
+    readback(h + 2, err, 4, s);
     st = cuda_status(cudaStreamSynchronize(s));
   }
   if (st == BSM_OK && h[2] == DERR_TIMEOUT) st = BSM_ERR_TIMEOUT;
@@ -663,7 +663,7 @@ static bsm_status batched_symbolic(const std::vector<int> &idx, const bsm_matrix
       k_localize<<<grid_for(whole->nc, 256), 256, 0, s>>>(whole->ckeys, whole->seg, whole->ta,
                                                           whole->tb, whole->nc, lmax,
                                                           dv + 2 * (n + 1), dv + 3 * (n + 1));
-    cudaMemcpyAsync(h, dv, 16 * (n + 1), cudaMemcpyDeviceToHost, s);
+    readback(h, dv, 16 * (n + 1), s);
     st = cuda_status(cudaStreamSynchronize(s));  // the host copy of aoff/boff is reused below
   }
   dev_free(dv, s);

@@ -266,13 +266,13 @@ extern "C" bsm_status bsm_truncate(bsm_matrix M, double tau, bsm_matrix *out, in
       st = scan_exclusive_i32(keep, pos, n, s);
     }
     if (st == BSM_OK) {
-      cudaMemcpyAsync(h + 1, first, 8, cudaMemcpyDeviceToHost, s);
+      readback(h + 1, first, 8, s);
       st = cuda_status(cudaStreamSynchronize(s));
       if (all && h[1] == ~0ull) h[1] = (uint64_t)n;  // no NaN norms: everything goes
       nrem = (int64_t)h[1];
       nkeep = n - nrem;
       if (st == BSM_OK && !all && nrem > 0) {
-        cudaMemcpyAsync(h + 2, k0 + nrem - 1, 8, cudaMemcpyDeviceToHost, s);
+        readback(h + 2, k0 + nrem - 1, 8, s);
         st = cuda_status(cudaStreamSynchronize(s));
         bnd = std::ldexp((double)h[2], e);
       }

@@ -203,8 +203,8 @@ extern "C" bsm_status bsm_add(bsm_matrix A, bsm_matrix B, bsm_matrix *out, void 
     int32_t *h = (int32_t *)host_scratch().get(16);
     if (st == BSM_OK && !h) st = BSM_ERR_OOM;
     if (st == BSM_OK) {
-      cudaMemcpyAsync(h, hpos + n - 1, 4, cudaMemcpyDeviceToHost, s);
-      cudaMemcpyAsync(h + 1, head + n - 1, 4, cudaMemcpyDeviceToHost, s);
+      readback(h, hpos + n - 1, 4, s);
+      readback(h + 1, head + n - 1, 4, s);
       st = cuda_status(cudaStreamSynchronize(s));
       nu = (int64_t)h[0] + h[1];
     }
@@ -218,8 +218,8 @@ extern "C" bsm_status bsm_add(bsm_matrix A, bsm_matrix B, bsm_matrix *out, void 
       st = scan_exclusive_i32(nz, pos, nu, s);
     }
     if (st == BSM_OK) {
-      cudaMemcpyAsync(h, pos + nu - 1, 4, cudaMemcpyDeviceToHost, s);
-      cudaMemcpyAsync(h + 1, nz + nu - 1, 4, cudaMemcpyDeviceToHost, s);
+      readback(h, pos + nu - 1, 4, s);
+      readback(h + 1, nz + nu - 1, 4, s);
       st = cuda_status(cudaStreamSynchronize(s));
       nkeep = (int64_t)h[0] + h[1];
     }
@@ -392,8 +392,8 @@ bsm_status reblock_impl(bsm_matrix A, int bs, int keep_all, bsm_matrix *out, int
       st = scan_exclusive_i32(flag, pos, m, s);
     }
     if (st == BSM_OK) {
-      cudaMemcpyAsync(h, pos + m - 1, 4, cudaMemcpyDeviceToHost, s);
-      cudaMemcpyAsync(h + 1, flag + m - 1, 4, cudaMemcpyDeviceToHost, s);
+      readback(h, pos + m - 1, 4, s);
+      readback(h + 1, flag + m - 1, 4, s);
       st = cuda_status(cudaStreamSynchronize(s));
       nout = (int64_t)h[0] + h[1];
     }
@@ -416,8 +416,8 @@ bsm_status reblock_impl(bsm_matrix A, int bs, int keep_all, bsm_matrix *out, int
       st = scan_exclusive_i32(flag, pos, n, s);
     }
     if (st == BSM_OK) {
-      cudaMemcpyAsync(h, pos + n - 1, 4, cudaMemcpyDeviceToHost, s);
-      cudaMemcpyAsync(h + 1, flag + n - 1, 4, cudaMemcpyDeviceToHost, s);
+      readback(h, pos + n - 1, 4, s);
+      readback(h + 1, flag + n - 1, 4, s);
       st = cuda_status(cudaStreamSynchronize(s));
       nout = (int64_t)h[0] + h[1];
     }

@@ -172,7 +172,7 @@ bsm_status autotune(bsm_plan P) {
   if (!h) return BSM_ERR_OOM;
   cudaMemsetAsync(P->scr, 0, 4, P->stream);
   for (int i = 0; i < P->n; i++) launch_max_seg(P->sym[i], P->scr, P->stream);
-  cudaMemcpyAsync(h, P->scr, 4, cudaMemcpyDeviceToHost, P->stream);
+  readback(h, P->scr, 4, P->stream);
   BSM_CUDA(cudaStreamSynchronize(P->stream));
   max_nk = h[0];
   TuneKey key{P->prec, P->bs, P->slices, P->np, P->n, ilog2(P->nitems),

@@ -37,7 +37,7 @@ extern "C" bsm_status bsm_selftest_wait_timeout(int limit_ms, void *stream) {
   unsigned *h = (unsigned *)host_scratch().get(16);
   bsm_status st = h ? cuda_status(cudaGetLastError()) : BSM_ERR_OOM;
   if (st == BSM_OK) {
-    cudaMemcpyAsync(h, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    readback(h, err, sizeof(unsigned), s);
     st = cuda_status(cudaStreamSynchronize(s));
   }
   dev_free(err, s);

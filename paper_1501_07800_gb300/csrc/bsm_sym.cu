@@ -77,9 +77,9 @@ static bsm_status sym_full(bsm_matrix U, bsm_matrix *out, cudaStream_t s) {
     int32_t *h = (int32_t *)host_scratch().get(16);
     if (st == BSM_OK && !h) st = BSM_ERR_OOM;
     if (st == BSM_OK) {
-      cudaMemcpyAsync(h, pos + n - 1, 4, cudaMemcpyDeviceToHost, s);
-      cudaMemcpyAsync(h + 1, f + n - 1, 4, cudaMemcpyDeviceToHost, s);
-      cudaMemcpyAsync(h + 2, bad, 4, cudaMemcpyDeviceToHost, s);
+      readback(h, pos + n - 1, 4, s);
+      readback(h + 1, f + n - 1, 4, s);
+      readback(h + 2, bad, 4, s);
       st = cuda_status(cudaStreamSynchronize(s));
     }
     if (st == BSM_OK && h[2]) st = BSM_ERR_OUT_OF_RANGE;  // a block below the diagonal

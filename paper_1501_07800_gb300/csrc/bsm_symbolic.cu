@@ -274,7 +274,7 @@ struct Expander {
   bsm_status read_sst(const Level &L, int64_t idx, int32_t *out) {
     int32_t *h = (int32_t *)host_scratch().get(16);
     if (!h) return BSM_ERR_OOM;
-    cudaMemcpyAsync(h, L.sst + idx, 4, cudaMemcpyDeviceToHost, s);
+    readback(h, L.sst + idx, 4, s);
     BSM_CUDA(cudaStreamSynchronize(s));
     *out = h[0];
     return BSM_OK;
@@ -344,7 +344,7 @@ struct Expander {
     unsigned long long *ht = (unsigned long long *)host_scratch().get(16);
     if (!ht) st = BSM_ERR_OOM;
     if (st == BSM_OK) {
-      cudaMemcpyAsync(ht, tot, 8, cudaMemcpyDeviceToHost, s);
+      readback(ht, tot, 8, s);
       st = cuda_status(cudaStreamSynchronize(s));
     }
     const int64_t total = st == BSM_OK ? (int64_t)ht[0] : 0;
@@ -405,7 +405,7 @@ struct Expander {
     if ((st = scan_exclusive_i32(nnz, nbase, L.ns + 1, s)) != BSM_OK) return fail(st);
     int32_t *hn = (int32_t *)host_scratch().get(16);
     if (!hn) return fail(BSM_ERR_OOM);
-    cudaMemcpyAsync(hn, nbase + L.ns, 4, cudaMemcpyDeviceToHost, s);
+    readback(hn, nbase + L.ns, 4, s);
     if ((st = cuda_status(cudaStreamSynchronize(s))) != BSM_OK) return fail(st);
     N.ns = hn[0];
     const bool last = (N.h == 0);

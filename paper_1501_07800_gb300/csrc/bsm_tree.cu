@@ -201,7 +201,7 @@ bsm_status build_levels(bsm_matrix M, cudaStream_t s) {
   BSM_CUDA(cudaGetLastError());
   int64_t *hc = (int64_t *)host_scratch().get(sizeof(int64_t) * (L + 1));
   if (!hc) return BSM_ERR_OOM;
-  BSM_CUDA(cudaMemcpyAsync(hc, dcount, sizeof(int64_t) * (L + 1), cudaMemcpyDeviceToHost, s));
+  BSM_TRY(readback(hc, dcount, sizeof(int64_t) * (L + 1), s));
   BSM_CUDA(cudaStreamSynchronize(s));
   for (int h = 0; h <= L; h++) M->nlev[h] = hc[h];
   return BSM_OK;
@@ -278,9 +278,9 @@ static bsm_status build_from_device(int64_t nrows, int64_t ncols, int bs, int64_
       int32_t *h = (int32_t *)host_scratch().get(16);
       if (!h) st = BSM_ERR_OOM;
       if (st == BSM_OK) {
-        cudaMemcpyAsync(h, pos + nblk - 1, 4, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(h + 1, keep + nblk - 1, 4, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(h + 2, err, 4, cudaMemcpyDeviceToHost, s);
+        readback(h, pos + nblk - 1, 4, s);
+        readback(h + 1, keep + nblk - 1, 4, s);
+        readback(h + 2, err, 4, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_status(e);
         unsigned derr = (unsigned)h[2];
@@ -578,7 +578,7 @@ extern "C" bsm_status bsm_update_values(bsm_matrix M, int64_t nblk, const int32_
     unsigned *h = (unsigned *)host_scratch().get(16);
     if (!h) st = BSM_ERR_OOM;
     if (st == BSM_OK) {
-      cudaMemcpyAsync(h, err, 4, cudaMemcpyDeviceToHost, s);
+      readback(h, err, 4, s);
       st = cuda_status(cudaStreamSynchronize(s));
     }
     if (st == BSM_OK && h[0] == DERR_OUT_OF_RANGE) st = BSM_ERR_OUT_OF_RANGE;

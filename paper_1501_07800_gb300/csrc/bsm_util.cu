@@ -95,6 +95,27 @@ HostScratch &host_scratch() {
   return h;
 }
 
+// One block copies `n` 32-bit words from device memory to the device-mapped
+// address of page-locked host memory.
+__global__ void k_readback(uint32_t *__restrict__ dst, const uint32_t *__restrict__ src,
+                           int64_t n) {
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+bsm_status readback(void *host, const void *dev, size_t bytes, cudaStream_t s) {
+  void *hd = nullptr;
+  if (bytes % 4 == 0 && (uintptr_t)host % 4 == 0 && (uintptr_t)dev % 4 == 0 &&
+      cudaHostGetDevicePointer(&hd, host, 0) == cudaSuccess && hd) {
+    if (bytes == 0) return BSM_OK;
+    count_launch();
+    k_readback<<<1, 256, 0, s>>>(static_cast<uint32_t *>(hd), static_cast<const uint32_t *>(dev),
+                                 (int64_t)(bytes / 4));
+    return cuda_status(cudaGetLastError());
+  }
+  cudaGetLastError();
+  return cuda_status(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, s));
+}
+
 LastStats &last_stats() {
   static thread_local LastStats st;
   return st;
