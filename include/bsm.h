@@ -454,7 +454,12 @@ bsm_status bsm_plan_info(bsm_plan plan, int *order, int *chunk, int *ctas_per_sm
  *                  mma.sync m8n8k4 tiles, 2 x 2 warps per C block;
  *                  2: split modes -- tcgen05 MMAs of tile_m = 128 rows and
  *                  tile_n = N columns (bs: one C block per work item, 2 bs:
- *                  sibling pairs of C blocks sharing every A tile)
+ *                  sibling pairs of C blocks sharing every A tile);
+ *                  3: split modes at bs 16 with grouped items -- as 2 with
+ *                  tile_n = bs, up to four C blocks of short product lists
+ *                  per work item, each in accumulator columns of its own
+ * With BSM_FLAG_AUTOTUNE the split item shape (grouped or single C blocks,
+ * where both exist) is chosen by measurement as well.
  * Outputs may be NULL.  Errors: INVALID_ARG. */
 bsm_status bsm_plan_tile(bsm_plan plan, int *form, int *tile_m, int *tile_n);
 

@@ -212,7 +212,8 @@ bsm_status split_prepare(bsm_matrix A, bsm_matrix B, int slices, unsigned *errwo
 // fold: device scratch of split_fold_bytes(bs) bytes, private to the launch
 // (C blocks with very long product lists park exact partial sums there).
 // np = 2: items are pairs of sibling C blocks (ProdDesc.pairc, B slices in
-// pair slots); np = 1: single C blocks, grouped where split_use_groups.
+// pair slots); np = 1: single C blocks, grouped where split_use_groups;
+// np = -1: single C blocks, never grouped; np = 4: grouped where compiled.
 bsm_status split_launch(int bs, int slices, const ProdDesc *prods_dev, const uint64_t *items,
                         int64_t nitems, unsigned long long *work, unsigned *errword,
                         int64_t *fold, cudaStream_t s, int chunk = 32, int np = 1);
@@ -221,6 +222,8 @@ size_t split_fold_bytes(int bs);
 bool split_use_pairs(int bs, int spec, int64_t nt, int64_t nc);
 // Grouped items (several short-list C blocks per item) for this format?
 bool split_use_groups(int bs, int spec);
+// Is there a grouped-item kernel for this leaf size and format?
+bool split_groups_compiled(int bs, int spec);
 // Pair-item structures of one product (task-list fields of d, A slices, B
 // slices in pair slots, padded exponents); *bslot: B pair slot per B block.
 bsm_status split_pairs_prepare(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, int spec,

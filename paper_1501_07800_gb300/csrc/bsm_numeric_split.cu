@@ -1419,7 +1419,12 @@ bsm_status split_launch(int bs, int spec, const ProdDesc *prods_dev, const uint6
   a.flushk_wide = split_flush_group(bs, spec, 24);
   a.err = errword;
   a.work = work;
-  if (np == 1 && split_use_groups(bs, spec)) np = 4;
+  // item shape: 1 the default (grouped where split_use_groups), -1 single C
+  // blocks, 4 grouped where compiled, 2 sibling pairs
+  const bool gc = group_compiled(bs, fmt, slices);
+  if (np == 1) np = split_use_groups(bs, spec) ? 4 : 1;
+  else if (np == 4) np = gc ? 4 : 1;
+  else if (np == -1) np = 1;
   return bs == 16 ? launch_split_s<16>(a, fmt, slices, np, s)
                   : launch_split_s<32>(a, fmt, slices, np, s);
 }
@@ -1446,8 +1451,11 @@ ProdDesc make_desc(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, double
 // one work item) wherever compiled; the producer groups only C blocks of short
 // lists, so the kernel is the single-block kernel for the others.
 // BSM_SPLIT_GROUPS=0 in the environment turns them off.
+bool split_groups_compiled(int bs, int spec) {
+  return group_compiled(bs, split_spec_fmt(spec), split_spec_slices(spec));
+}
 bool split_use_groups(int bs, int spec) {
-  if (!group_compiled(bs, split_spec_fmt(spec), split_spec_slices(spec))) return false;
+  if (!split_groups_compiled(bs, spec)) return false;
   const char *e = getenv("BSM_SPLIT_GROUPS");
   return !(e && e[0] == '0');
 }

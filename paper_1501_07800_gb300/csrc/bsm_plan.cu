@@ -51,7 +51,9 @@ struct bsm_plan_s {
   // chosen configuration
   int order = 0;  // 0: longest first, 1: product-major Morton
   int chunk = 32, ctas_per_sm = 0;
-  int form = -1;  // FP64 tile: 0 DMMA; 1, 2, 3 DFMA thread tiles (-1: the process default)
+  // FP64 tile: 0 DMMA; 1, 2, 3 DFMA thread tiles.  Split item shape: 1 single
+  // C blocks, 4 grouped C blocks (bs 16).  -1: the process default.
+  int form = -1;
   bool tuned = false;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -116,7 +118,7 @@ bsm_status enqueue_numeric(bsm_plan P, int order, int chunk, int ctas, int form,
       BSM_TRY(split_compute(P->A[i], P->B[i], P->slices, P->desc[i], P->err, s,
                             P->np == 2 ? P->bslot[i] : nullptr));
   return split_launch(P->bs, P->slices, P->table, items, P->nitems, counter, P->err, P->fold, s,
-                      chunk, P->np);
+                      chunk, P->np == 2 ? 2 : (form == 1 ? -1 : (form == 4 ? 4 : 1)));
 }
 
 void destroy_plan(bsm_plan P) {
@@ -199,6 +201,11 @@ bsm_status autotune(bsm_plan P) {
     } else {
       for (int form : {1, 2, 3}) cands.push_back({0, 32, 0, form});
     }
+  } else if (P->np != 2 && split_groups_compiled(P->bs, P->slices)) {
+    // the item shape first (grouped or single C blocks), then the schedule
+    // with the better one
+    cands.push_back({0, 32, 0, 4});
+    cands.push_back({0, 32, 0, 1});
   } else {
     for (int order : {0, 1})
       for (int chunk : {32, 8, 1}) cands.push_back({order, chunk, 0, -1});
@@ -216,7 +223,14 @@ bsm_status autotune(bsm_plan P) {
     }
   };
   for (const TuneVal &c : cands) measure(c);
-  if (P->prec == BSM_FP64) measure({1, 32, 0, pick.form});
+  if (P->prec == BSM_FP64) {
+    measure({1, 32, 0, pick.form});
+  } else if (cands.size() == 2) {
+    const int f = pick.form;
+    for (int order : {0, 1})
+      for (int chunk : {32, 8, 1})
+        if (order != 0 || chunk != 32) measure({order, chunk, 0, f});
+  }
   P->order = pick.order;
   P->chunk = pick.chunk;
   P->ctas_per_sm = pick.ctas;
@@ -557,6 +571,9 @@ extern "C" bsm_status bsm_plan_tile(bsm_plan P, int *form, int *tile_m, int *til
   if (!P) return BSM_ERR_INVALID_ARG;
   if (P->inner) return bsm_plan_tile(P->inner, form, tile_m, tile_n);
   int f = 2, m = 128, nn = P->bs * P->np;
+  if (P->prec != BSM_FP64 && P->np != 2 && split_groups_compiled(P->bs, P->slices) &&
+      (P->form == 4 || (P->form < 0 && split_use_groups(P->bs, P->slices))))
+    f = 3;  // grouped items: N = bs per MMA, up to four C blocks per item
   if (P->prec == BSM_FP64) {
     const int fm = P->form < 0 ? fp64_mode() : P->form;
     if (fm == 0) {  // a warp's 8 x 8 mma.sync tiles

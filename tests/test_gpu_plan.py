@@ -49,6 +49,29 @@ def test_plan_equals_batched_and_replays(prec, autotune):
             assert np.array_equal(g.vals, r.vals)   # every thread tile sums in one order
 
 
+@pytest.mark.parametrize("autotune", [False, True])
+def test_plan_item_shape_bs16(autotune):
+    """At bs 16 the split item shape (grouped or single C blocks) is a tuned
+    parameter: whichever the plan picks, its results are the batched call's
+    bits, and bsm_plan_tile reports it (3: grouped, 2: single)."""
+    pairs = synth.batched(6, 37, bs=16, nmin=256, nmax=2500, dmin=0.02, dmax=0.2)
+    As = [to_bsm(a) for a, _ in pairs]
+    Bs = [to_bsm(b) for _, b in pairs]
+    ref = [from_bsm(c) for c in bsm.bsm_multiply_batched(As, Bs, prec=bsm.BSM_SPLIT_BF16)]
+    plan = bsm.bsm_plan_create(As, Bs, prec=bsm.BSM_SPLIT_BF16, autotune=autotune)
+    assert bsm.bsm_plan_block_size(plan) == 16
+    form, tm, tn = bsm.bsm_plan_tile(plan)
+    assert form in (2, 3) and tm == 128 and tn == 16
+    if not autotune:
+        assert form == 3   # the default: grouped items where compiled
+    bsm.bsm_plan_execute(plan)
+    got = [from_bsm(c) for c in bsm.bsm_plan_results(plan)]
+    for g, r in zip(got, ref):
+        assert_same_structure(g, r)
+        assert np.array_equal(g.vals, r.vals)
+    bsm.bsm_plan_destroy(plan)
+
+
 @pytest.mark.parametrize("prec,tol", [(bsm.BSM_FP64, 1e-12), (bsm.BSM_SPLIT_BF16, 1e-11)])
 def test_plan_after_value_update(prec, tol):
     pairs = batch(nprod=5, seed=41)
