@@ -135,7 +135,7 @@ bsm_status readback(void *host, const void *dev, size_t bytes, cudaStream_t s);
 // Exclusive prefix sums on the device (CUB), sized on first use.
 bsm_status scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
 bsm_status scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
-bsm_status scan_exclusive_int4(const int4 *in, int4 *out, int64_t n, cudaStream_t s);
+bsm_status scan_exclusive_u64(const uint64_t *in, uint64_t *out, int64_t n, cudaStream_t s);
 // Inclusive prefix sums of uint64 values, saturating at 2^64 - 1.
 bsm_status scan_inclusive_u64_sat(const uint64_t *in, uint64_t *out, int64_t n, cudaStream_t s);
 bsm_status sort_keys_u64(const uint64_t *kin, uint64_t *kout, const int32_t *vin, int32_t *vout,

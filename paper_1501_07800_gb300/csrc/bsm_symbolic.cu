@@ -90,18 +90,34 @@ __device__ __forceinline__ unsigned pair_qmask(const CView &u, int64_t p, unsign
   return qmask;
 }
 
+// The four per-quadrant counts of a pair are kept as two 64-bit words,
+// quadrants (0, 1) in cxy and (2, 3) in czw, each count in a 32-bit half:
+// prefix sums of the words are the halves' prefix sums, because no
+// per-quadrant prefix reaches 2^32 (a level holds fewer than 2^31 pairs), so
+// the scans are plain 64-bit sums.
+__device__ __forceinline__ uint64_t pack2(int32_t lo, int32_t hi) {
+  return (uint64_t)(uint32_t)lo | ((uint64_t)(uint32_t)hi << 32);
+}
+__device__ __forceinline__ int4 counts_at(const uint64_t *__restrict__ cxy,
+                                          const uint64_t *__restrict__ czw, int64_t i) {
+  const uint64_t a = cxy[i], b = czw[i];
+  return make_int4((int32_t)(uint32_t)a, (int32_t)(a >> 32), (int32_t)(uint32_t)b,
+                   (int32_t)(b >> 32));
+}
+
 // Per pair: child counts of the quadrants in qmask; the level's exact total
 // is accumulated in 64 bits: per thread over a grid-stride loop, per block in
 // shared memory, one atomic per block.
 __global__ void k_sym_count(const int32_t *__restrict__ pa, const int32_t *__restrict__ pb,
                             int64_t np, LevelView va, LevelView vb, unsigned qmask, CView up,
-                            int4 *__restrict__ cnt, unsigned long long *__restrict__ total) {
+                            uint64_t *__restrict__ cxy, uint64_t *__restrict__ czw,
+                            unsigned long long *__restrict__ total) {
   __shared__ unsigned long long wsum[32];
   unsigned long long mine = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= np; p += stride) {
     if (p == np) {
-      cnt[p] = make_int4(0, 0, 0, 0);  // sentinel: the exclusive scan then ends with the total
+      cxy[p] = czw[p] = 0;  // sentinel: the exclusive scans then end with the totals
       continue;
     }
     unsigned ma, mb;
@@ -113,7 +129,8 @@ __global__ void k_sym_count(const int32_t *__restrict__ pa, const int32_t *__res
                        (qm & 2u) ? quad_count(ma, mb, 0, 1) : 0,
                        (qm & 4u) ? quad_count(ma, mb, 1, 0) : 0,
                        (qm & 8u) ? quad_count(ma, mb, 1, 1) : 0);
-    cnt[p] = c;
+    cxy[p] = pack2(c.x, c.y);
+    czw[p] = pack2(c.z, c.w);
     mine += (unsigned)(c.x + c.y + c.z + c.w);
   }
   for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
@@ -133,25 +150,27 @@ __device__ __forceinline__ int q_of(const int4 &v, int q) {
 // Segment starts sst[] are stored offset by poff (pair index of the first
 // pair of this part of the level); P is indexed from that first pair.
 __global__ void k_sym_seg_count(const int32_t *__restrict__ sst, int32_t poff, int64_t ns,
-                                const int4 *__restrict__ P, int32_t *__restrict__ nnz) {
+                                const uint64_t *__restrict__ Pxy,
+                                const uint64_t *__restrict__ Pzw, int32_t *__restrict__ nnz) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s > ns) return;
   if (s == ns) {
     nnz[s] = 0;
     return;
   }
-  int4 a = P[sst[s] - poff], b = P[sst[s + 1] - poff];
+  const int4 a = counts_at(Pxy, Pzw, sst[s] - poff), b = counts_at(Pxy, Pzw, sst[s + 1] - poff);
   nnz[s] = (b.x > a.x) + (b.y > a.y) + (b.z > a.z) + (b.w > a.w);
 }
 
 // New segments: key 4*ckey + q and start offset for each non-empty quadrant.
 __global__ void k_sym_seg_write(const uint64_t *__restrict__ sck, const int32_t *__restrict__ sst,
-                                int32_t poff, int64_t ns, const int4 *__restrict__ P,
+                                int32_t poff, int64_t ns, const uint64_t *__restrict__ Pxy,
+                                const uint64_t *__restrict__ Pzw,
                                 const int32_t *__restrict__ nbase, uint64_t *__restrict__ nck,
                                 int32_t *__restrict__ nst) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= ns) return;
-  int4 a = P[sst[s] - poff], b = P[sst[s + 1] - poff];
+  const int4 a = counts_at(Pxy, Pzw, sst[s] - poff), b = counts_at(Pxy, Pzw, sst[s + 1] - poff);
   int32_t off = a.x + a.y + a.z + a.w;  // children of all earlier segments
   int32_t j = nbase[s];
   for (int q = 0; q < 4; q++) {
@@ -171,7 +190,8 @@ __global__ void k_sym_seg_write(const uint64_t *__restrict__ sck, const int32_t 
 __global__ void k_sym_fill(const int32_t *__restrict__ pa, const int32_t *__restrict__ pb,
                            const int32_t *__restrict__ pseg, int32_t soff, int64_t np,
                            const int32_t *__restrict__ sst, int32_t poff,
-                           const int4 *__restrict__ P, const int32_t *__restrict__ nbase,
+                           const uint64_t *__restrict__ Pxy, const uint64_t *__restrict__ Pzw,
+                           const int32_t *__restrict__ nbase,
                            LevelView va, LevelView vb, unsigned qmask, CView up,
                            int32_t *__restrict__ npa, int32_t *__restrict__ npb,
                            int32_t *__restrict__ npseg) {
@@ -179,7 +199,8 @@ __global__ void k_sym_fill(const int32_t *__restrict__ pa, const int32_t *__rest
   if (p >= np) return;
   qmask = pair_qmask(up, p, qmask);
   int32_t s = pseg[p] - soff;
-  int4 a = P[sst[s] - poff], b = P[sst[s + 1] - poff], me = P[p];
+  const int4 a = counts_at(Pxy, Pzw, sst[s] - poff), b = counts_at(Pxy, Pzw, sst[s + 1] - poff),
+             me = counts_at(Pxy, Pzw, p);
   unsigned ma, mb;
   int32_t ca, cb;
   node_info(va, pa[p], ma, ca);
@@ -320,10 +341,11 @@ struct Expander {
   bsm_status process(Level &L, unsigned qmask) {
     if (L.h == 0) return leaf(L);
     LevelView va = view_of(A, L.h), vb = view_of(B, L.h);
-    int4 *P = nullptr;
+    uint64_t *P = nullptr;  // per-pair counts: quadrants (0, 1) at P, (2, 3) at P + np + 1
     unsigned long long *tot = nullptr;
     bsm_status st;
-    if ((st = dev_alloc((void **)&P, sizeof(int4) * (L.np + 1), s)) != BSM_OK) return st;
+    if ((st = dev_alloc((void **)&P, 2 * sizeof(uint64_t) * (L.np + 1), s)) != BSM_OK) return st;
+    uint64_t *const Pzw = P + L.np + 1;
     if ((st = dev_alloc((void **)&tot, 8, s)) != BSM_OK) {
       dev_free(P, s);
       return st;
@@ -339,7 +361,7 @@ struct Expander {
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       const int64_t want = (L.np + 1 + 255) / 256, cap = (int64_t)(sms > 0 ? sms : 1) * 16;
       k_sym_count<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(L.pa, L.pb, L.np, va, vb,
-                                                                        qmask, up, P, tot);
+                                                                        qmask, up, P, Pzw, tot);
     }
     unsigned long long *ht = (unsigned long long *)host_scratch().get(16);
     if (!ht) st = BSM_ERR_OOM;
@@ -396,12 +418,14 @@ struct Expander {
       free_level(N, s);
       return e;
     };
-    if ((st = scan_exclusive_int4(P, P, L.np + 1, s)) != BSM_OK) return fail(st);
+    if ((st = scan_exclusive_u64(P, P, L.np + 1, s)) != BSM_OK ||
+        (st = scan_exclusive_u64(Pzw, Pzw, L.np + 1, s)) != BSM_OK)
+      return fail(st);
     if ((st = dev_alloc((void **)&nnz, 4 * (L.ns + 1), s)) ||
         (st = dev_alloc((void **)&nbase, 4 * (L.ns + 1), s)))
       return fail(st);
     count_launch();
-    k_sym_seg_count<<<grid_for(L.ns + 1, 256), 256, 0, s>>>(L.sst, L.poff, L.ns, P, nnz);
+    k_sym_seg_count<<<grid_for(L.ns + 1, 256), 256, 0, s>>>(L.sst, L.poff, L.ns, P, Pzw, nnz);
     if ((st = scan_exclusive_i32(nnz, nbase, L.ns + 1, s)) != BSM_OK) return fail(st);
     int32_t *hn = (int32_t *)host_scratch().get(16);
     if (!hn) return fail(BSM_ERR_OOM);
@@ -416,10 +440,10 @@ struct Expander {
         (st = dev_alloc((void **)&N.sst, 4 * (N.ns + 1), s)))
       return fail(st);
     count_launch(2);
-    k_sym_seg_write<<<grid_for(L.ns, 256), 256, 0, s>>>(L.sck, L.sst, L.poff, L.ns, P, nbase,
-                                                        N.sck, N.sst);
+    k_sym_seg_write<<<grid_for(L.ns, 256), 256, 0, s>>>(L.sck, L.sst, L.poff, L.ns, P, Pzw,
+                                                        nbase, N.sck, N.sst);
     k_sym_fill<<<grid_for(L.np, 256), 256, 0, s>>>(L.pa, L.pb, L.pseg, L.soff, L.np, L.sst, L.poff,
-                                                   P, nbase, va, vb, qmask, up, N.pa, N.pb,
+                                                   P, Pzw, nbase, va, vb, qmask, up, N.pa, N.pb,
                                                    N.pseg);
     st = cuda_status(cudaGetLastError());
     dev_free(P, s);

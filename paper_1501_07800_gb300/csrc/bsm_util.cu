@@ -241,11 +241,7 @@ extern "C" bsm_status bsm_last_phase_ms(double *ms, int cap, int *nphase, int64_
   return BSM_OK;
 }
 
-struct Int4Sum {
-  __host__ __device__ int4 operator()(const int4 &a, const int4 &b) const {
-    return make_int4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
-  }
-};
+
 
 template <typename F>
 static bsm_status run_cub(F f, cudaStream_t s) {
@@ -274,11 +270,11 @@ bsm_status scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaSt
   }, s);
 }
 
-bsm_status scan_exclusive_int4(const int4 *in, int4 *out, int64_t n, cudaStream_t s) {
+bsm_status scan_exclusive_u64(const uint64_t *in, uint64_t *out, int64_t n, cudaStream_t s) {
   if (n <= 0) return BSM_OK;
   count_launch(2);
   return run_cub([&](void *t, size_t &b) {
-    return cub::DeviceScan::ExclusiveScan(t, b, in, out, Int4Sum(), make_int4(0, 0, 0, 0), n, s);
+    return cub::DeviceScan::ExclusiveSum(t, b, in, out, n, s);
   }, s);
 }
 
