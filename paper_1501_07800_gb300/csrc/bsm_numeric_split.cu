@@ -237,8 +237,10 @@ __device__ __forceinline__ uint32_t small_int_to_e4m3(int v) {
 // matrices 128 B apart, 8-row groups SBO apart).  TRANS = 0: A block, operand
 // rows = block rows, K = block columns, row scales.  TRANS = 1: B block,
 // operand rows = block columns, K = block rows, column scales.  A CTA stages
-// one block in shared memory; each thread makes one core-matrix row (16 bytes
-// per slice), so a warp writes 512 contiguous bytes per slice.
+// BPI blocks in shared memory at a time (as many as its 128 threads have
+// core-matrix rows to make: one at bs 32 BF16, four at bs 16); each thread
+// makes one core-matrix row (16 bytes per slice), so a warp writes 512
+// contiguous bytes per slice.
 // B slices are stored in the operand order of b_pos.  pslot (B only, NULL
 // otherwise): the pair slot of each block; the slices of the two sibling
 // blocks (I, 2y), (I, 2y+1) of a slot are then interleaved, position p of the
@@ -253,15 +255,22 @@ __global__ void __launch_bounds__(128) k_slice(const double *__restrict__ vals,
   constexpr int B = Fmt<F>::BETA;
   constexpr int EPR = 16 / Fmt<F>::EB;  // elements per core-matrix row
   constexpr int KG = BS / EPR;
-  __shared__ double blk[BS * (BS + 1)];
-  for (int64_t t = blockIdx.x; t < n; t += gridDim.x) {
-    const double *src = vals + t * (int64_t)BS * BS;
-    for (int e = threadIdx.x; e < BS * BS; e += blockDim.x)
-      blk[(e / BS) * (BS + 1) + e % BS] = src[e];
+  constexpr int TASKS = BS * KG;                       // core-matrix rows per block
+  constexpr int BPI = TASKS >= 128 ? 1 : 128 / TASKS;  // blocks per iteration
+  __shared__ double stage[BPI][BS * (BS + 1)];
+  for (int64_t t0 = (int64_t)blockIdx.x * BPI; t0 < n; t0 += (int64_t)gridDim.x * BPI) {
+    for (int e = threadIdx.x; e < BPI * BS * BS; e += blockDim.x) {
+      const int u = e / (BS * BS), f = e % (BS * BS);
+      if (t0 + u < n) stage[u][(f / BS) * (BS + 1) + f % BS] = vals[(t0 + u) * BS * BS + f];
+    }
     __syncthreads();
-    const uint64_t key = keys[t];
+    const int u = BPI > 1 ? (int)threadIdx.x / TASKS : 0;  // this thread's block
+    const int64_t t = t0 + u;
+    const double *blk = stage[u];
+    const uint64_t key = t < n ? keys[t] : 0;
     const int64_t rc = TRANS == 0 ? (int64_t)morton_compact(key >> 1) : (int64_t)morton_compact(key);
-    for (int task = threadIdx.x; task < BS * KG; task += blockDim.x) {
+    for (int task = BPI > 1 ? (int)threadIdx.x % TASKS : (int)threadIdx.x;
+         t < n && task < TASKS; task += BPI > 1 ? TASKS : (int)blockDim.x) {
       const int kg = task % KG, mrow = task / KG;
       const int E = exps[rc * BS + mrow];
       uint32_t w[S][4] = {};
@@ -297,7 +306,12 @@ __global__ void __launch_bounds__(128) k_slice(const double *__restrict__ vals,
 template <int BS, int S, int F>
 void launch_slices(bsm_matrix A, bsm_matrix B, const int *rowexp, const int *colexp,
                    uint8_t *asl, uint8_t *bsl, const int32_t *bslot, cudaStream_t s) {
-  auto grid = [](int64_t n) { return (unsigned)(n < 152 * 16 ? n : 152 * 16); };
+  // (blocks per CTA iteration: 128 / core-matrix rows per block, at least 1)
+  constexpr int BPI = BS * (BS / (16 / Fmt<F>::EB)) >= 128 ? 1 : 128 / (BS * (BS / (16 / Fmt<F>::EB)));
+  auto grid = [](int64_t n) {
+    const int64_t c = (n + BPI - 1) / BPI;
+    return (unsigned)(c < 152 * 16 ? c : 152 * 16);
+  };
   count_launch(2);
   if (A->nblk)
     k_slice<BS, S, 0, F><<<grid(A->nblk), 128, 0, s>>>(A->vals, A->keys, A->nblk, rowexp,
@@ -971,8 +985,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
       // pair's odd sibling follows the even one), at its column cc.  The
       // scale exponents are loaded here so that their latency hides behind
       // the first flush.
+      // The descriptor's fields go to registers first and the slot is
+      // released before the exponent loads: the arrive has release semantics
+      // and would wait for every earlier load, the global ones included.
       int erow[GRP], oblk[GRP];
       int4 fcol[GRP];
+      int64_t eoff[GRP], foff[GRP];
 #pragma unroll
       for (int i = 0; i < GRP; i++) {
         const int g4 = min(ttid + i * kTeam, NG4 - 1);
@@ -986,10 +1004,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
             bj = mring[m].bj[x];
           }
         oblk[i] = blk;
-        erow[i] = rowexp[(int64_t)bi * BS + rr];
-        fcol[i] = *reinterpret_cast<const int4 *>(colexp + (int64_t)bj * BS + c4 % BS);
+        eoff[i] = (int64_t)bi * BS + rr;
+        foff[i] = (int64_t)bj * BS + c4 % BS;
       }
       mbar_arrive(&mempty[m]);
+#pragma unroll
+      for (int i = 0; i < GRP; i++) {
+        erow[i] = rowexp[eoff[i]];
+        fcol[i] = *reinterpret_cast<const int4 *>(colexp + foff[i]);
+      }
       // a grouped item is one narrow flush on the fast path (every list has
       // at most kFast products)
       const FlushPlan fplan = nq > 1 ? FlushPlan{false, nk, 1, 1}
