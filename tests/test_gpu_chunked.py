@@ -29,7 +29,24 @@ CASES = {
     "rect": lambda: (synth.random_blocks(900, 16, 0.2, 5, ncols=2000),
                      synth.random_blocks(2000, 16, 0.2, 6, ncols=700)),
     "dense_node": lambda: (synth.random_blocks(512, 32, 1.0, 7), synth.random_blocks(512, 32, 1.0, 8)),
+    # a dense corner (long product lists: sibling-pair items in split mode)
+    # in a sparse matrix (short lists: one C block per item), so that one
+    # product's chunks use both operand layouts
+    "mixed": lambda: (dense_corner(3000, 32, 0.03, 9), dense_corner(3000, 32, 0.03, 10)),
 }
+
+
+def dense_corner(n, bs, p, seed, corner=24):
+    """Random blocks of density p plus every block of the top-left corner x corner blocks."""
+    M = synth.random_blocks(n, bs, p, seed)
+    keep = ~((M.brow < corner) & (M.bcol < corner))
+    I, J = np.meshgrid(np.arange(corner, dtype=np.int32), np.arange(corner, dtype=np.int32),
+                       indexing="ij")
+    rng = np.random.default_rng(seed)
+    vals = rng.standard_normal((corner * corner, bs, bs))
+    return synth.BlockCOO(M.nrows, M.ncols, bs, np.concatenate([M.brow[keep], I.ravel()]),
+                          np.concatenate([M.bcol[keep], J.ravel()]),
+                          np.concatenate([M.vals[keep], vals]))
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
