@@ -55,7 +55,7 @@ typedef enum {
   BSM_ERR_CUDA = -7,             /* a CUDA runtime error */
   BSM_ERR_TIMEOUT = -8,          /* a bounded device wait gave up */
   BSM_ERR_BUFFER_TOO_SMALL = -9, /* caller buffer smaller than the result */
-  BSM_ERR_UNSUPPORTED = -10      /* valid request this build cannot run */
+  BSM_ERR_UNSUPPORTED = -10      /* a valid request the library does not support */
 } bsm_status;
 
 typedef enum {
