@@ -823,9 +823,12 @@ static bsm_status batched_group(const std::vector<int> &idx, const bsm_matrix *A
     if (st == BSM_OK) {
       if (prec == BSM_FP64)
         st = numeric_fp64_batched(bs, table, v1, total, counter, err, 0, s);
-      else
+      else {
+        for (int i = 0; i < n; i++)  // the split kernel marks the nonzero C blocks
+          if (sym[i].nc > 0) cudaMemsetAsync(nz[i], 0, 4 * sym[i].nc, s);
         st = split_launch(bs, slices, table, v1, total_items, counter, err, fold, s,
                           split_chunk_for(total_item_nt, total_items), np);
+      }
     }
   }
   const int t2 = timing_mark(s);

@@ -453,6 +453,9 @@ struct __align__(16) Meta {
   int32_t nkq[kSub];    // grouped items: block products of each C block
   int32_t nk;           // block products of the item (all its lists)
   int32_t nq;           // grouped items: lists multiplied one after another; else 1
+  int32_t nfl;          // the item's flushes (flush plan, made once by the producer)
+  int16_t fk;           // block products per flush
+  int8_t wide, pad;     // wide flushes (partial sums up to 2^24)
 };
 static_assert(sizeof(Meta) % 16 == 0, "Meta alignment");
 constexpr int kMeta = 8;
@@ -565,7 +568,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
   __shared__ __align__(8) uint64_t meta_full[2][kMeta], meta_empty[2][kMeta];
   __shared__ Meta meta[2][kMeta];
   __shared__ uint32_t tmem_base_sh;
-  __shared__ int warp_any[2][kSub][16];  // [team][C block of the item][warp]
   __shared__ volatile int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -653,6 +655,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
           mring[m].colexp = cexp;
           mring[m].nk = nk;
           mring[m].nq = nq;
+          // a grouped item is one narrow flush: list lq into its own columns
+          const FlushPlan fp = nq > 1 || nk < 0 ? FlushPlan{false, nk, 1, 1}
+                                               : flush_plan(nk, P.flushk, P.flushk_wide);
+          mring[m].nfl = fp.nfl;
+          mring[m].fk = (int16_t)fp.fk;
+          mring[m].wide = fp.wide ? 1 : 0;
           mbar_arrive(&mfull[m]);  // release: the descriptor is visible
         }
       }
@@ -832,6 +840,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
         }
         // (single blocks and pairs: one list, known at compile time)
         const int nk = mring[m].nk, nq = NQ > 1 ? mring[m].nq : 1;
+        const bool fwide = mring[m].wide != 0;
+        const FlushPlan fp{fwide, mring[m].fk, mring[m].nfl, fwide ? kFoldWide : kFold};
         int nkq[NQ];
 #pragma unroll
         for (int x = 0; x < NQ; x++) nkq[x] = NQ > 1 ? mring[m].nkq[x] : nk;
@@ -881,9 +891,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
           it++;
           return true;
         };
-        // a grouped item is one flush: list lq into its own columns
-        const FlushPlan fp = nq > 1 ? FlushPlan{false, nk, 1, 1}
-                                    : flush_plan(nk, P.flushk, P.flushk_wide);
         for (int f = 0; f < fp.nfl && !abort_flag; f++) {
           const uint32_t fb = fcb++;
           const uint32_t u = fb % NBUF, use = fb / NBUF;  // buffer and its use count
@@ -938,12 +945,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
     int32_t *tcomb = comb + team * (C::COMB / 4);
     const int bar_id = 1 + team;
     uint32_t fct = 0;                     // flushes drained by this team
-    // nonzero flags of the team's previous item, written by thread 0 of the
-    // team once the next item's first barrier shows every warp's flag
-    int32_t *prev_nz = nullptr;
-    int64_t prev_c[NSUB];
-#pragma unroll
-    for (int x = 0; x < NSUB; x++) prev_c[x] = -1;
     uint64_t *const mfull = meta_full[team], *const mempty = meta_empty[team];
     const Meta *const mring = meta[team];
     for (uint32_t q = 0;; q++) {
@@ -951,28 +952,20 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
       bool okm = mbar_wait(&mfull[m], (q / kMeta) & 1u);
       // every decision below is uniform across the warp (tcgen05.ld is
       // .sync.aligned) and, at the named barriers, across the team.  This
-      // barrier also ends the previous item: its warp flags are complete and
-      // its shared-memory diagonal buffer is free.
+      // barrier also ends the previous item: its shared-memory diagonal
+      // buffer is free.
       if (named_bar_or(bar_id, kTeam, !okm || abort_flag != 0)) {
         set_err(P.err, DERR_TIMEOUT);
         abort_flag = 1;
         break;
       }
-      if (ttid == 0 && prev_nz) {
-#pragma unroll
-        for (int x = 0; x < NSUB; x++) {
-          int nzv = 0;
-          for (int w = 0; w < kTeamWarps; w++) nzv |= warp_any[team][x][w];
-          if (prev_c[x] >= 0) prev_nz[prev_c[x]] = nzv;
-        }
-      }
-      // (the flags are rewritten only after the next barrier, which thread 0
-      // reaches after reading them)
       const int nk = mring[m].nk, nq = NQ > 1 ? mring[m].nq : 1;
       if (nk < 0) {  // end marker
         mbar_arrive(&mempty[m]);
         break;
       }
+      const bool fwide = mring[m].wide != 0;
+      const FlushPlan fplan{fwide, mring[m].fk, mring[m].nfl, fwide ? kFoldWide : kFold};
       int64_t cblk[NSUB];
 #pragma unroll
       for (int x = 0; x < NSUB; x++) cblk[x] = mring[m].c[x];
@@ -1013,10 +1006,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
         erow[i] = rowexp[eoff[i]];
         fcol[i] = *reinterpret_cast<const int4 *>(colexp + foff[i]);
       }
-      // a grouped item is one narrow flush on the fast path (every list has
+      // (a grouped item is one narrow flush on the fast path: every list has
       // at most kFast products)
-      const FlushPlan fplan = nq > 1 ? FlushPlan{false, nk, 1, 1}
-                                     : flush_plan(nk, P.flushk, P.flushk_wide);
       const int nfl = fplan.nfl, kf = fplan.kf;
       const bool wide = fplan.wide;
       const bool fast = nq > 1 || (!wide && nk <= kFast);  // uniform over the team
@@ -1184,14 +1175,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_numeric_split(SplitArgs P) {
           dst[1] = make_double2(out[2], out[3]);
         }
       }
+      // nonzero flags (zeroed before the launch): any warp that saw an entry
+      // != 0 of a C block marks it
 #pragma unroll
       for (int x = 0; x < NSUB; x++) {
         const bool a = __any_sync(0xffffffffu, (any >> x) & 1u);
-        if (lane == 0) warp_any[team][x][tw] = a;
+        if (lane == 0 && a && cblk[x] >= 0) nzp[cblk[x]] = 1;
       }
-      prev_nz = nzp;
-#pragma unroll
-      for (int x = 0; x < NSUB; x++) prev_c[x] = x < nq * NP ? cblk[x] : -1;
     }
   }
   __syncthreads();
@@ -1617,10 +1607,12 @@ static bsm_status numeric_split_pairs(bsm_matrix A, bsm_matrix B, const Symbolic
     cudaMemcpyAsync(scr + 4, h, sizeof(ProdDesc), cudaMemcpyHostToDevice, s);
     st = cuda_status(cudaStreamSynchronize(s));  // the host staging buffer is reused
   }
-  if (st == BSM_OK)
+  if (st == BSM_OK) {
+    cudaMemsetAsync(nzflag, 0, 4 * sym.nc, s);  // the kernel marks the nonzero C blocks
     st = split_launch(bs, spec, reinterpret_cast<const ProdDesc *>(scr + 4), nullptr, d.nc,
                       reinterpret_cast<unsigned long long *>(scr + 2), errword, fold, s,
                       split_chunk_for(d.nt, d.nc), 2);
+  }
   cleanup();
   return st;
 }
@@ -1654,10 +1646,12 @@ bsm_status numeric_split(bsm_matrix A, bsm_matrix B, const SymbolicResult &sym, 
   int64_t *fold = nullptr;
   if (st == BSM_OK && (st = dev_alloc((void **)&fold, split_fold_bytes(bs), s)) == BSM_OK)
     owned.push_back(fold);
-  if (st == BSM_OK)
+  if (st == BSM_OK) {
+    cudaMemsetAsync(nzflag, 0, 4 * sym.nc, s);  // the kernel marks the nonzero C blocks
     st = split_launch(bs, slices, reinterpret_cast<const ProdDesc *>(scr + 4), nullptr, sym.nc,
                       reinterpret_cast<unsigned long long *>(scr + 2), errword, fold, s,
                       split_chunk_for(sym.nt, sym.nc));
+  }
   cleanup();
   return st;
 }

@@ -114,9 +114,11 @@ bsm_status enqueue_numeric(bsm_plan P, int order, int chunk, int ctas, int form,
     return numeric_fp64_batched(P->bs, P->table, items, P->nitems, counter, P->err, ctas, s,
                                 form);
   for (int i = 0; i < P->n; i++)
-    if (P->sym[i].nc > 0)
+    if (P->sym[i].nc > 0) {
       BSM_TRY(split_compute(P->A[i], P->B[i], P->slices, P->desc[i], P->err, s,
                             P->np == 2 ? P->bslot[i] : nullptr));
+      cudaMemsetAsync(P->nz[i], 0, 4 * P->sym[i].nc, s);  // the kernel marks nonzero blocks
+    }
   return split_launch(P->bs, P->slices, P->table, items, P->nitems, counter, P->err, P->fold, s,
                       chunk, P->np == 2 ? 2 : (form == 1 ? -1 : (form == 4 ? 4 : 1)));
 }
