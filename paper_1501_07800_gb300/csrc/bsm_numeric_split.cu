@@ -37,23 +37,24 @@
 // Items: one C block, or (long product lists) a pair of sibling C blocks
 // (I, 2y), (I, 2y+1) whose merged product list runs as 128 x 2bs MMAs: the B
 // slices of the two sibling B blocks sit side by side (a pair slot), so each
-// A tile feeds both C blocks.
+// A tile feeds both C blocks; at bs 16 up to four consecutive C blocks of
+// short lists (grouped items), each list into accumulator columns of its own.
 //
-// Roles (608 threads, or 576 with one team; one CTA per SM, persistent):
-//   warp 16:       producer -- all lanes prefetch work descriptors and block
+// Roles (640 threads, or 576 with one team; one CTA per SM, persistent): two
+// independent pipelines (one with a single team), each
+//   a producer warp (16, 17) -- all lanes prefetch work descriptors and block
 //                  indices; lane 0 issues the 1-D bulk copies of the A and B
-//                  slices of each k-product into a ring of stages (mbarrier
-//                  complete_tx) and hands per-C-block descriptors to the other
-//                  roles through a shared-memory ring;
-//   warps 17, 18 lane 0: issue the MMAs of each k-product of the items of
-//                  epilogue team 0 / 1 (one issuer with a single team),
-//                  commit the stage back to the producer and each finished
-//                  flush to the epilogue;
-//   warps 0-15:    epilogue, two teams of eight warps taking alternate C
-//                  blocks, each with its own TMEM accumulator buffer -- drain
-//                  TMEM (two warps per lane quadrant) into exact integer
-//                  diagonal sums in shared memory, combine and round, store
-//                  C, raise the nonzero flag.
+//                  slices of each k-product into the pipeline's stages
+//                  (mbarrier complete_tx) and hands per-item descriptors to
+//                  the other roles through the pipeline's descriptor ring;
+//   an MMA warp (18, 19), lane 0: issues the MMAs of each k-product, commits
+//                  the stage back to the producer and each finished flush to
+//                  the epilogue;
+//   an epilogue team of eight warps (0-7, 8-15) with its own TMEM
+//                  accumulator buffers -- drain TMEM (two warps per lane
+//                  quadrant) into exact integer diagonal sums in shared
+//                  memory, combine and round, store C, mark the nonzero C
+//                  blocks.
 #include <climits>
 #include <cstddef>
 #include <cstring>
