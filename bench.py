@@ -360,7 +360,7 @@ def run_gpu(args):
 
     clocks = ClockSampler(local)
     barrier()
-    clocks.start()
+    clocks.start().wait_first()   # nvidia-smi's start-up stays outside the timed steps
     step_ms, numeric_ms, launches, nblk_c = timed_steps(args.steps, True)
     barrier()
     clk = clocks.stop()
@@ -456,7 +456,7 @@ def decay_c2(bsm, torch, peak, args) -> dict:
             dict(name="split_fp8x12", prec=bsm.BSM_SPLIT_FP8, slices=12, sym=False),
             dict(name="fp64_node", prec=bsm.BSM_FP64, slices=0, sym=False, range=(1024, 512),
                  steps=1)]
-    clk = ClockSampler(torch.cuda.current_device()).start()
+    clk = ClockSampler(torch.cuda.current_device()).start().wait_first()
     out = decay_product(bsm, torch, 20000, 32, legs, 2, peak=peak)
     out["clocks"] = clk.stop()
     f = out["fp64_node"]
@@ -480,7 +480,7 @@ def run_split(bsm, torch, ga, gb, args, stream, flops, triples, A, B, rank, slic
           for _ in range(args.steps)]
     num_ms = []
     clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
+    clocks.start().wait_first()
     for i in range(args.steps):
         ev[i][0].record(stream)
         C = bsm.bsm_multiply(ga, gb, prec=prec, slices=slices)

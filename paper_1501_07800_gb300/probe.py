@@ -59,6 +59,15 @@ class ClockSampler:
         for ln in self.proc.stdout:
             self.lines.append(ln.strip())
 
+    def wait_first(self, timeout: float = 2.0):
+        """Returns once the sampler has reported (or after `timeout` s), so that
+        starting nvidia-smi does not overlap what is sampled next."""
+        import time
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
+        return self
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
