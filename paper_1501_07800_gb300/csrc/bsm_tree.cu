@@ -13,20 +13,24 @@
 
 // ------------------------------------------------------------------ kernels
 // One warp per listed block: range check, key, and whether the block holds an
-// entry != 0.0.
+// entry != 0.0.  stage (or NULL): receives a copy of every block it reads (the
+// values of pinned host input then cross the host link once).
 __global__ void k_make_keys(const int32_t *__restrict__ brow, const int32_t *__restrict__ bcol,
                             const double *__restrict__ vals, int64_t n, int64_t mb, int64_t nb,
                             int bs, uint64_t *__restrict__ keys, int32_t *__restrict__ idx,
-                            uint8_t *__restrict__ nz, unsigned *__restrict__ err) {
+                            uint8_t *__restrict__ nz, unsigned *__restrict__ err,
+                            double *__restrict__ stage) {
   int64_t w = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   int lane = threadIdx.x & 31;
   if (w >= n) return;
   const double2 *b = reinterpret_cast<const double2 *>(vals + w * (int64_t)bs * bs);
   int n2 = bs * bs / 2;
   bool any = false;
+  double2 *st = stage ? reinterpret_cast<double2 *>(stage + w * (int64_t)bs * bs) : nullptr;
   for (int t = lane; t < n2; t += 32) {
     double2 v = b[t];
     any |= nonzero_f64(v.x) | nonzero_f64(v.y);
+    if (st) st[t] = v;
   }
   any = __any_sync(0xffffffffu, any);
   if (lane == 0) {
@@ -220,9 +224,11 @@ static void destroy_matrix(bsm_matrix M, cudaStream_t s) {
 static bool bs_supported(int bs) { return bs == 16 || bs == 32 || bs == 64; }
 
 // Allocates and fills a new handle from device COO arrays.
+// stage (or NULL): device buffer of nblk blocks that the key kernel fills
+// with the input values, the gather's source then (for pinned host input).
 static bsm_status build_from_device(int64_t nrows, int64_t ncols, int bs, int64_t nblk,
                                     const int32_t *brow, const int32_t *bcol, const double *vals,
-                                    cudaStream_t s, bsm_matrix *out) {
+                                    cudaStream_t s, bsm_matrix *out, double *stage = nullptr) {
   bsm_matrix M = new bsm_matrix_s();
   cudaGetDevice(&M->device);
   M->nrows = nrows;
@@ -267,7 +273,7 @@ static bsm_status build_from_device(int64_t nrows, int64_t ncols, int bs, int64_
     cudaMemsetAsync(err, 0, sizeof(unsigned), s);
     count_launch();
     k_make_keys<<<nblocks_for(nblk, 8), 256, 0, s>>>(brow, bcol, vals, nblk, M->mb, M->nb, bs,
-                                                     keys, idx, nz, err);
+                                                     keys, idx, nz, err, stage);
     st = sort_keys_u64(keys, skeys, idx, sidx, nblk, 2 * M->L, s);
     if (st == BSM_OK) {
       count_launch();
@@ -306,7 +312,7 @@ static bsm_status build_from_device(int64_t nrows, int64_t ncols, int bs, int64_
       count_launch();
       k_compact_keys<<<nblocks_for(nblk, 256), 256, 0, s>>>(skeys, sidx, keep, pos, nblk, M->keys,
                                                             idx);
-      launch_gather_blocks(vals, idx, M->vals, nkeep, bs, s);
+      launch_gather_blocks(stage ? stage : vals, idx, M->vals, nkeep, bs, s);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) st = cuda_status(e);
     }
@@ -352,15 +358,20 @@ extern "C" bsm_status bsm_build(int64_t nrows, int64_t ncols, int bs, int64_t nb
   cudaStream_t s = (cudaStream_t)stream;
   if (on_device || nblk == 0)
     return build_from_device(nrows, ncols, bs, nblk, brow, bcol, vals, s, out);
-  // pinned host input: the build kernels read it in place over the host link
-  // -- no staging buffer and no copy-engine upload (which would queue behind
-  // other streams' copies) -- and the call returns once the last read is done
+  // pinned host input: the key kernel reads it in place over the host link
+  // (no copy-engine upload, which would queue behind other streams' copies)
+  // and copies the values into a device buffer for the gather, so they cross
+  // the link once; the call returns once the last read is done
   {
     const int32_t *mr = (const int32_t *)mapped_device_ptr(brow, 4);
     const int32_t *mc = (const int32_t *)mapped_device_ptr(bcol, 4);
     const double *mv = (const double *)mapped_device_ptr(vals, 16);
     if (mr && mc && mv) {
-      bsm_status st = build_from_device(nrows, ncols, bs, nblk, mr, mc, mv, s, out);
+      double *stage = nullptr;
+      bsm_status st = dev_alloc((void **)&stage, sizeof(double) * bs * bs * nblk, s);
+      if (st != BSM_OK) return st;
+      st = build_from_device(nrows, ncols, bs, nblk, mr, mc, mv, s, out, stage);
+      dev_free(stage, s);
       if (st == BSM_OK) st = cuda_status(cudaStreamSynchronize(s));
       if (st != BSM_OK && *out) {
         destroy_matrix(*out, s);
