@@ -1128,8 +1128,8 @@ def run_e2e(bsm, torch, A, B, prec, steps):
     first builds its operands (from the pinned arrays, read in place while the
     link is otherwise idle -- an upload beside a 19 GB download crawls), then
     queues the previous product's download on a copy stream (bsm_to_blocks'
-    asynchronous mode: a device gather and the copy engine, no SMs held), then
-    multiplies.  Two sets of result buffers alternate.  The timed region ends
+    asynchronous mode: chunked device gathers and copy-engine transfers on the
+    library's highest-priority stream), then multiplies.  Two sets of result buffers alternate.  The timed region ends
     when the last download has landed."""
     def pinned(a: np.ndarray) -> np.ndarray:
         t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
@@ -1192,8 +1192,9 @@ def run_e2e(bsm, torch, A, B, prec, steps):
     dt = time.perf_counter() - t0
     inflight[0] = inflight[1] = None
     return {"seconds": dt, "steps": steps, "h2d": h2d, "d2h": d2h,
-            "overlap": "each step's product overlaps the previous step's download (copy "
-                       "engine, separate stream); uploads run while the link is idle"}
+            "overlap": "each step's product overlaps the previous step's download (chunked "
+                       "gather + copy engine on a high-priority stream); uploads run while "
+                       "the link is idle"}
 
 
 def main():

@@ -298,13 +298,15 @@ bsm_status bsm_multiply_batched(int n, const bsm_matrix *A, const bsm_matrix *B,
  *               aligned, brow/bcol 4-byte aligned);
  *               2: page-locked, device-mapped host buffers (cudaHostAlloc /
  *               cudaHostRegister with mapping; vals 16-byte aligned), written
- *               asynchronously: the blocks are gathered into a device staging
- *               buffer (as large as the output; freed stream-ordered) and
- *               moved by the copy engine, and the call returns with the work
- *               queued on `stream`, so the transfer can overlap later kernels
- *               on other streams; the caller synchronises `stream` before
- *               reading the buffers and keeps M alive until then
- *               (INVALID_ARG if a buffer is not such memory)
+ *               asynchronously: the blocks are gathered in 512 MB chunks into
+ *               a device staging buffer, each chunk moved by the copy engine,
+ *               on a library-owned stream of the greatest priority that
+ *               starts after the work queued on `stream` and that `stream`
+ *               waits for; the call returns with the work queued, so the
+ *               transfer overlaps later kernels on other streams.  The
+ *               caller synchronises `stream` before reading the buffers and
+ *               keeps M alive until then (INVALID_ARG if a buffer is not
+ *               such memory)
  * With all three buffers NULL the call only reports the block count.
  * Errors: INVALID_ARG, BUFFER_TOO_SMALL (count still reported), OOM, CUDA.
  */

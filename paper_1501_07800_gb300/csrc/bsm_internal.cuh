@@ -145,9 +145,10 @@ bsm_status sort_pairs_u32_u64(const uint32_t *kin, uint32_t *kout, const uint64_
 
 // Builds the level arrays of a handle whose keys are set (bsm_tree.cu).
 bsm_status build_levels(bsm_matrix M, cudaStream_t s);
-// Copies blocks: dst[t] = src[idx[t]] (bs*bs doubles each).
+// Copies blocks: dst[t] = src[idx[t]] (bs*bs doubles each), on at most
+// max_ctas CTAs (<= 0: a full-device grid).
 void launch_gather_blocks(const double *src, const int32_t *idx, double *dst, int64_t n, int bs,
-                          cudaStream_t s);
+                          cudaStream_t s, int64_t max_ctas = 0);
 
 // ---------------------------------------------------------- symbolic result
 // Leaf-level task list of one product: C blocks in Morton order, each with the

@@ -8,6 +8,7 @@
 // first child in level h-1.  Children of a node are contiguous because keys
 // are in Morton order.
 #include <cstring>
+#include <mutex>
 
 #include "bsm_internal.cuh"
 
@@ -77,9 +78,10 @@ __global__ void k_gather_blocks(const double *__restrict__ src, const int32_t *_
 }
 
 void launch_gather_blocks(const double *src, const int32_t *idx, double *dst, int64_t n, int bs,
-                          cudaStream_t s) {
+                          cudaStream_t s, int64_t max_ctas) {
   if (n <= 0) return;
-  int64_t grid = n < 152 * 32 ? n : 152 * 32;
+  const int64_t cap = max_ctas > 0 ? max_ctas : 152 * 32;
+  int64_t grid = n < cap ? n : cap;
   count_launch();
   k_gather_blocks<<<(unsigned)grid, 256, 0, s>>>(src, idx, dst, n, bs);
 }
@@ -403,6 +405,49 @@ extern "C" bsm_status bsm_build(int64_t nrows, int64_t ncols, int bs, int64_t nb
   return st;
 }
 
+// Asynchronous downloads run on a stream of the library's own, one per
+// device, at the device's greatest priority: the block scheduler then places
+// the download's short gather launches ahead of the pending CTAs of a long
+// kernel on another stream (a product), so the copy engine is kept fed while
+// the product runs.  The caller's stream is joined both ways by one event.
+struct SideStream {
+  cudaStream_t caller = nullptr, side = nullptr;
+  cudaEvent_t ev = nullptr;
+  bsm_status fork(cudaStream_t s) {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    int dev = 0, lo = 0, hi = 0;
+    BSM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return BSM_ERR_UNSUPPORTED;
+    {
+      std::lock_guard<std::mutex> g(mu);
+      if (!streams[dev]) {
+        BSM_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        BSM_CUDA(cudaStreamCreateWithPriority(&streams[dev], cudaStreamNonBlocking, hi));
+      }
+    }
+    BSM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    caller = s;
+    side = streams[dev];
+    cudaEventRecord(ev, caller);
+    cudaStreamWaitEvent(side, ev, 0);
+    return BSM_OK;
+  }
+  // everything queued on the side stream so far precedes later work on the
+  // caller's stream
+  ~SideStream() {
+    if (!ev) return;
+    cudaEventRecord(ev, side);
+    cudaStreamWaitEvent(caller, ev, 0);
+    cudaEventDestroy(ev);
+  }
+};
+
+// Blocks per chunk of an asynchronous download and CTAs of its gathers: one
+// 512 MB staging buffer, one CTA per SM.
+constexpr size_t kDownloadChunkBytes = (size_t)512 << 20;
+constexpr int64_t kDownloadGatherCtas = 152;
+
 extern "C" bsm_status bsm_to_blocks(bsm_matrix M, int64_t *nblk_inout, int32_t *brow,
                                     int32_t *bcol, double *vals, int on_device, void *stream) {
   NvtxRange range("bsm_to_blocks");
@@ -432,6 +477,11 @@ extern "C" bsm_status bsm_to_blocks(bsm_matrix M, int64_t *nblk_inout, int32_t *
   if (on_device == 2 && !all_mapped) return BSM_ERR_INVALID_ARG;
   const bool async_host = on_device == 2;
   cudaStream_t s = (cudaStream_t)stream;
+  SideStream side;
+  if (async_host) {
+    BSM_TRY(side.fork(s));
+    s = side.side;
+  }
   int64_t n = M->nblk;
   int bs = M->bs;
   uint64_t *rm = nullptr, *rms = nullptr;
@@ -465,14 +515,19 @@ extern "C" bsm_status bsm_to_blocks(bsm_matrix M, int64_t *nblk_inout, int32_t *
     return st;
   }
   if (async_host) {
-    // gather on the device into a staging buffer, then one copy-engine
-    // transfer into the caller's page-locked buffers: the transfer occupies
-    // no SM, so later kernels on other streams run beside it.  Everything is
-    // freed stream-ordered after the copies; nothing waits here.
+    // gather on the device in chunks through one small staging buffer, each
+    // chunk followed by a copy-engine transfer into the caller's page-locked
+    // buffers.  The gathers are short and narrow and the transfers hold no
+    // SM, so a product on another stream runs beside the download nearly
+    // undisturbed; the staging is a fixed 512 MB, not the size of the
+    // output.  All ordered on the side stream; nothing waits here.
     size_t bblk = sizeof(double) * bs * bs;
+    int64_t chunk = (int64_t)(kDownloadChunkBytes / bblk);
+    if (chunk < 1) chunk = 1;
+    if (chunk > n) chunk = n;
     double *stage = nullptr;
     int32_t *crd = nullptr;
-    if ((st = dev_alloc((void **)&stage, vals ? bblk * n : 16, s)) ||
+    if ((st = dev_alloc((void **)&stage, vals ? bblk * chunk : 16, s)) ||
         (st = dev_alloc((void **)&crd, 8 * n, s))) {
       dev_free(stage, s);
       cleanup();
@@ -482,10 +537,12 @@ extern "C" bsm_status bsm_to_blocks(bsm_matrix M, int64_t *nblk_inout, int32_t *
     k_rowmajor_coords<<<nblocks_for(n, 256), 256, 0, s>>>(rms, 0, n, crd, crd + n);
     if (brow) cudaMemcpyAsync(brow, crd, 4 * n, cudaMemcpyDeviceToHost, s);
     if (bcol) cudaMemcpyAsync(bcol, crd + n, 4 * n, cudaMemcpyDeviceToHost, s);
-    if (vals) {
-      launch_gather_blocks(M->vals, sidx, stage, n, bs, s);
-      cudaMemcpyAsync(vals, stage, bblk * n, cudaMemcpyDeviceToHost, s);
-    }
+    if (vals)
+      for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+        int64_t m = n - c0 < chunk ? n - c0 : chunk;
+        launch_gather_blocks(M->vals, sidx + c0, stage, m, bs, s, kDownloadGatherCtas);
+        cudaMemcpyAsync(vals + c0 * bs * bs, stage, bblk * m, cudaMemcpyDeviceToHost, s);
+      }
     dev_free(stage, s);
     dev_free(crd, s);
     cleanup();
