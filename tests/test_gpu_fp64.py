@@ -130,6 +130,36 @@ def test_to_blocks_asynchronous_into_pinned_buffers():
     assert e.value.name == "BSM_ERR_INVALID_ARG"
 
 
+def test_to_blocks_asynchronous_in_several_chunks():
+    """An asynchronous download larger than one 512 MB staging chunk (16384
+    blocks of 64 x 64): two full chunks and a ragged tail, each gathered and
+    copied in turn on the library's own stream.  An event recorded on the
+    caller's stream right after the call completes only once every chunk has
+    landed; the buffers then hold the input blocks in row-major order."""
+    import torch
+    import synth.device as sd
+    n, bs = 25600, 64
+    brow, bcol, vals = sd.random_blocks(n, bs, 0.25, 23, "cuda")
+    m = brow.shape[0]
+    assert m > 2 * 16384 and m % 16384 != 0
+    M = bsm.bsm_build(n, n, bs, brow, bcol, vals)
+    assert bsm.bsm_info(M)[3] == m
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    out = (torch.empty(m, dtype=torch.int32, pin_memory=True).numpy(),
+           torch.empty(m, dtype=torch.int32, pin_memory=True).numpy(),
+           torch.empty((m, bs, bs), dtype=torch.float64, pin_memory=True).numpy())
+    out[2][...] = np.nan  # every block must be overwritten
+    bsm.bsm_to_blocks(M, out=out, stream=s, asynchronous=True)
+    ev = torch.cuda.Event()
+    ev.record(s)
+    ev.synchronize()
+    r, c = brow.cpu().numpy(), bcol.cpu().numpy()
+    order = np.lexsort((c, r))
+    assert np.array_equal(out[0], r[order]) and np.array_equal(out[1], c[order])
+    assert np.array_equal(out[2], vals.cpu().numpy()[order])
+
+
 def test_build_drops_zero_blocks_and_rejects_bad_input():
     bs = 16
     A = synth.random_blocks(200, bs, 0.3, 6)
