@@ -356,24 +356,27 @@ bsm_status bsm_set_timing(int on);
 
 /*
  * bsm_release_memory -- return the device memory the library keeps cached to
- * the driver.  The library allocates stream-ordered from the current device's
- * default memory pool and keeps freed memory in the pool, so that repeated
- * products reuse it without new driver allocations; memory cached there is
- * not available to other allocators (cudaMalloc, PyTorch's allocator).  This
- * call synchronises the current device, then releases every cached byte not
- * backing a live allocation (handles, plans and their buffers stay valid).
+ * the driver.  The library allocates stream-ordered from two memory pools of
+ * the current device -- the device's default pool, and a pool of its own for
+ * allocations of 1 GiB and more, so that a large block freed by one product
+ * is reused whole by the next -- and keeps freed memory in them, so that
+ * repeated products reuse it without new driver allocations; memory cached
+ * there is not available to other allocators (cudaMalloc, PyTorch's
+ * allocator).  This call synchronises the current device, then releases every
+ * cached byte of both pools not backing a live allocation (handles, plans and
+ * their buffers stay valid).
  * Errors: CUDA if the synchronisation or the release fails.
  */
 bsm_status bsm_release_memory(void);
 
 /*
  * bsm_set_memory_limit -- cap the device memory the library's allocations
- * may hold in the current device's default pool: an allocation that would
- * take the pool's in-use bytes above `bytes` fails with OOM, and the call
+ * may hold in the current device's two pools: an allocation that would take
+ * their in-use bytes above `bytes` fails with OOM, and the call
  * that needed it returns OOM after freeing what it had allocated.  0 removes
  * the cap (the default).  Process-wide.  Meant for callers that share the
  * device and for fault injection in tests.
- * bsm_memory_in_use -- the pool's bytes in use by live allocations (handles,
+ * bsm_memory_in_use -- the pools' bytes in use by live allocations (handles,
  * plans, work in flight); synchronises the current device first.
  * Errors: INVALID_ARG (NULL bytes), CUDA.
  */

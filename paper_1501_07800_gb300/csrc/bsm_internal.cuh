@@ -111,7 +111,8 @@ inline int ceil_log2_i64(int64_t x) {
 }
 
 // ----------------------------------------------------------- host utilities
-// Stream-ordered allocation from the device's default memory pool.
+// Stream-ordered allocation from the device's default memory pool, or from
+// the library's own pool for allocations of 1 GiB and more.
 bsm_status dev_alloc(void **p, size_t bytes, cudaStream_t s);
 void dev_free(void *p, cudaStream_t s);
 bsm_status cuda_status(cudaError_t e);

@@ -19,25 +19,62 @@ bsm_status cuda_status(cudaError_t e) {
   return BSM_ERR_CUDA;
 }
 
+// Allocations of at least kBulkBytes (a product's C values, large staging
+// buffers) come from a second pool of the library's own, the rest from the
+// device's default pool.  With one pool, the short-lived buffers of the next
+// product (its symbolic arrays, a download's staging) were carved out of the
+// block a destroyed C had left, and the next C's allocation then waited
+// 16-30 ms on the host while the driver assembled a fresh range from the
+// pieces; kept apart, a bulk block is reused whole.
+constexpr size_t kBulkBytes = (size_t)1 << 30;
+static cudaMemPool_t g_bulk[64] = {};
+
+static void pool_attributes(cudaMemPool_t pool) {
+  // keep freed memory in this process's pool instead of returning it to the
+  // driver at every synchronisation
+  uint64_t thr = ~0ull;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  // memory freed on one stream is never handed to an allocation on another
+  // stream by making that stream wait: work on different streams (batched
+  // products' workers, a download beside the next product) stays
+  // independent, at the price of a larger pool
+  int no = 0;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+}
+
 static void configure_pool_once(int dev) {
   static std::mutex mu;
   static bool done[64] = {};
   std::lock_guard<std::mutex> g(mu);
   if (dev < 0 || dev >= 64 || done[dev]) return;
   cudaMemPool_t pool;
-  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-    // keep freed memory in this process's pool instead of returning it to the
-    // driver at every synchronisation
-    uint64_t thr = ~0ull;
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    // memory freed on one stream is never handed to an allocation on another
-    // stream by making that stream wait: work on different streams (batched
-    // products' workers, a download beside the next product) stays
-    // independent, at the price of a larger pool
-    int no = 0;
-    cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) pool_attributes(pool);
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t bulk = nullptr;
+  if (cudaMemPoolCreate(&bulk, &props) == cudaSuccess) {
+    pool_attributes(bulk);
+    g_bulk[dev] = bulk;
+  } else {
+    cudaGetLastError();  // every allocation then uses the default pool
   }
   done[dev] = true;
+}
+
+// Bytes in use by live allocations in both pools of a device.
+static bsm_status pools_in_use(int dev, uint64_t *used) {
+  configure_pool_once(dev);
+  cudaMemPool_t pool;
+  uint64_t a = 0, b = 0;
+  BSM_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  BSM_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &a));
+  if (dev >= 0 && dev < 64 && g_bulk[dev])
+    BSM_CUDA(cudaMemPoolGetAttribute(g_bulk[dev], cudaMemPoolAttrUsedMemCurrent, &b));
+  *used = a + b;
+  return BSM_OK;
 }
 
 // Cap on the pool's in-use bytes (bsm_set_memory_limit); 0 = none.
@@ -50,16 +87,15 @@ bsm_status dev_alloc(void **p, size_t bytes, cudaStream_t s) {
   cudaGetDevice(&dev);
   configure_pool_once(dev);
   if (const uint64_t cap = g_mem_limit.load(std::memory_order_relaxed)) {
-    cudaMemPool_t pool;
     uint64_t used = 0;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess ||
-        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) {
+    if (pools_in_use(dev, &used) != BSM_OK) {
       cudaGetLastError();
       return BSM_ERR_CUDA;
     }
     if (used + bytes > cap) return BSM_ERR_OOM;
   }
-  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  cudaMemPool_t bulk = bytes >= kBulkBytes && dev >= 0 && dev < 64 ? g_bulk[dev] : nullptr;
+  cudaError_t e = bulk ? cudaMallocFromPoolAsync(p, bytes, bulk, s) : cudaMallocAsync(p, bytes, s);
   if (e != cudaSuccess) {
     *p = nullptr;
     cudaGetLastError();
@@ -145,9 +181,11 @@ extern "C" bsm_status bsm_release_memory(void) {
   int dev = 0;
   BSM_CUDA(cudaGetDevice(&dev));
   BSM_CUDA(cudaDeviceSynchronize());
+  configure_pool_once(dev);
   cudaMemPool_t pool;
   BSM_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
   BSM_CUDA(cudaMemPoolTrimTo(pool, 0));
+  if (dev >= 0 && dev < 64 && g_bulk[dev]) BSM_CUDA(cudaMemPoolTrimTo(g_bulk[dev], 0));
   return BSM_OK;
 }
 
@@ -161,10 +199,9 @@ extern "C" bsm_status bsm_memory_in_use(uint64_t *bytes) {
   int dev = 0;
   BSM_CUDA(cudaGetDevice(&dev));
   BSM_CUDA(cudaDeviceSynchronize());
-  cudaMemPool_t pool;
-  BSM_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  if (dev < 0 || dev >= 64) return BSM_ERR_UNSUPPORTED;
   uint64_t used = 0;
-  BSM_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+  BSM_TRY(pools_in_use(dev, &used));
   *bytes = used;
   return BSM_OK;
 }
