@@ -300,10 +300,11 @@ bsm_status bsm_multiply_batched(int n, const bsm_matrix *A, const bsm_matrix *B,
  *               cudaHostRegister with mapping; vals 16-byte aligned), written
  *               asynchronously: the blocks are gathered in 512 MB chunks into
  *               a device staging buffer, each chunk moved by the copy engine,
- *               on a library-owned stream of the greatest priority that
- *               starts after the work queued on `stream` and that `stream`
- *               waits for; the call returns with the work queued, so the
- *               transfer overlaps later kernels on other streams.  The
+ *               on a library-owned stream of the greatest priority (one
+ *               per device, so concurrent downloads run one after another)
+ *               that starts after the work queued on `stream` and that
+ *               `stream` waits for; the call returns with the work queued,
+ *               so the transfer overlaps later kernels on other streams.  The
  *               caller synchronises `stream` before reading the buffers and
  *               keeps M alive until then (INVALID_ARG if a buffer is not
  *               such memory)
